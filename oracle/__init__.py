@@ -1,0 +1,198 @@
+"""CPU oracle for hybrid dealiased convolution (ctypes over plain C).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
+with the CUDA path and never imports it.
+
+Functions (complex arrays are numpy complex128; see hdc_oracle.c for the
+formula each one writes out):
+
+* ``conv_direct(f, g)``           -- Eq. 4 per axis, double-double sums (O1)
+* ``conv_direct_at(f, g, idx)``   -- the same at chosen flat output indices
+* ``conv_fft(f, g)``              -- explicitly zero-padded radix-2 FFT (O2)
+* ``conv_int_exact(fre, fim, gre, gim, method)`` -- exact integers (O3)
+* ``closed_form_exp(A, B, P, L)`` / ``closed_form_geom(...)`` -- (O4)
+* ``residue_forward / residue_backward / conv_hybrid`` -- Eq. 1, Eq. 2 (O5)
+* ``conv_hermitian_direct / conv_hermitian_fft`` -- centered Hermitian (O6)
+* ``dft(x, sign)``                -- the DFT by its definition
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+_i64 = C.c_int64
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int64)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        L.hdco_conv_direct.argtypes = [C.c_int, _ip, _dp, _dp, _dp]
+        L.hdco_conv_direct_at.argtypes = [C.c_int, _ip, _dp, _dp, _ip, _i64, _dp]
+        L.hdco_conv_fft.argtypes = [C.c_int, _ip, _dp, _dp, _dp]
+        L.hdco_dft.argtypes = [_dp, _i64, C.c_int, _dp]
+        L.hdco_dft.restype = None
+        L.hdco_conv_int_exact_1d.argtypes = [_ip, _ip, _ip, _ip, _i64, C.c_int, _ip, _ip]
+        L.hdco_closed_form_exp_1d.argtypes = [_i64, _i64, _i64, _i64, _dp]
+        L.hdco_closed_form_exp_1d.restype = None
+        L.hdco_closed_form_geom_1d.argtypes = [C.c_double, _i64, C.c_double, _i64, _i64, _i64, _dp]
+        L.hdco_closed_form_geom_1d.restype = None
+        L.hdco_residue_forward_1d.argtypes = [_dp, _i64, _i64, _i64, _i64, _dp]
+        L.hdco_residue_backward_1d.argtypes = [_dp, _i64, _i64, _i64, _i64, _dp]
+        L.hdco_conv_hybrid_1d.argtypes = [_dp, _dp, _i64, _i64, _i64, _i64, _dp]
+        L.hdco_conv_hermitian_2d_direct.argtypes = [_dp, _dp, _i64, _dp]
+        L.hdco_conv_hermitian_2d_fft.argtypes = [_dp, _dp, _i64, _dp]
+        L.hdco_root_of_unity.argtypes = [_i64, _i64, _dp]
+        L.hdco_root_of_unity.restype = None
+        L.hdco_num_threads.restype = C.c_int
+        L.hdco_set_num_threads.argtypes = [C.c_int]
+        L.hdco_set_num_threads.restype = None
+        _lib = L
+    return _lib
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _iptr(a):
+    return a.ctypes.data_as(_ip)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+def num_threads() -> int:
+    return int(lib().hdco_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    lib().hdco_set_num_threads(int(n))
+
+
+def root_of_unity(k: int, n: int) -> complex:
+    out = np.zeros(2)
+    lib().hdco_root_of_unity(int(k), int(n), _dptr(out))
+    return complex(out[0], out[1])
+
+
+def conv_direct(f, g):
+    f = _c128(f)
+    g = _c128(g)
+    assert f.shape == g.shape and 1 <= f.ndim <= 3
+    dims = np.array(f.shape, dtype=np.int64)
+    h = np.empty_like(f)
+    _check(lib().hdco_conv_direct(f.ndim, _iptr(dims), _dptr(f), _dptr(g), _dptr(h)), "conv_direct")
+    return h
+
+
+def conv_direct_at(f, g, idx):
+    f = _c128(f)
+    g = _c128(g)
+    dims = np.array(f.shape, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.empty(idx.size, dtype=np.complex128)
+    _check(lib().hdco_conv_direct_at(f.ndim, _iptr(dims), _dptr(f), _dptr(g), _iptr(idx),
+                                     idx.size, _dptr(out)), "conv_direct_at")
+    return out
+
+
+def conv_fft(f, g):
+    f = _c128(f)
+    g = _c128(g)
+    assert f.shape == g.shape and 1 <= f.ndim <= 3
+    dims = np.array(f.shape, dtype=np.int64)
+    h = np.empty_like(f)
+    _check(lib().hdco_conv_fft(f.ndim, _iptr(dims), _dptr(f), _dptr(g), _dptr(h)), "conv_fft")
+    return h
+
+
+def dft(x, sign=+1):
+    x = _c128(x)
+    X = np.empty_like(x)
+    lib().hdco_dft(_dptr(x), x.size, int(sign), _dptr(X))
+    return X
+
+
+def conv_int_exact(fre, fim, gre, gim, method: str = "auto"):
+    """Exact first-L convolution of complex integer sequences; returns
+    (re, im) int64 arrays.  method: 'direct', 'ntt' or 'auto'."""
+    arrs = [np.ascontiguousarray(a, dtype=np.int64) for a in (fre, fim, gre, gim)]
+    L = arrs[0].size
+    if method == "auto":
+        method = "direct" if L <= 4096 else "ntt"
+    hre = np.empty(L, dtype=np.int64)
+    him = np.empty(L, dtype=np.int64)
+    _check(lib().hdco_conv_int_exact_1d(*[_iptr(a) for a in arrs], L,
+                                        1 if method == "ntt" else 0, _iptr(hre), _iptr(him)),
+           "conv_int_exact")
+    return hre, him
+
+
+def closed_form_exp(A: int, B: int, P: int, L: int):
+    h = np.empty(L, dtype=np.complex128)
+    lib().hdco_closed_form_exp_1d(A, B, P, L, _dptr(h))
+    return h
+
+
+def closed_form_geom(ra: float, A: int, rb: float, B: int, P: int, L: int):
+    h = np.empty(L, dtype=np.complex128)
+    lib().hdco_closed_form_geom_1d(ra, A, rb, B, P, L, _dptr(h))
+    return h
+
+
+def residue_forward(x, L: int, m: int, p: int, q: int):
+    x = _c128(x)
+    F = np.empty(q * m, dtype=np.complex128)
+    _check(lib().hdco_residue_forward_1d(_dptr(x), L, m, p, q, _dptr(F)), "residue_forward")
+    return F
+
+
+def residue_backward(F, L: int, m: int, p: int, q: int):
+    F = _c128(F)
+    x = np.zeros(L, dtype=np.complex128)
+    _check(lib().hdco_residue_backward_1d(_dptr(F), L, m, p, q, _dptr(x)), "residue_backward")
+    return x
+
+
+def conv_hybrid(f, g, m: int, p: int, q: int):
+    f = _c128(f)
+    g = _c128(g)
+    h = np.empty_like(f)
+    _check(lib().hdco_conv_hybrid_1d(_dptr(f), _dptr(g), f.size, m, p, q, _dptr(h)), "conv_hybrid")
+    return h
+
+
+def conv_hermitian_direct(f, g):
+    f = _c128(f)
+    g = _c128(g)
+    K = f.shape[1]
+    assert f.shape == (2 * K - 1, K) == g.shape
+    h = np.empty_like(f)
+    _check(lib().hdco_conv_hermitian_2d_direct(_dptr(f), _dptr(g), K, _dptr(h)), "herm_direct")
+    return h
+
+
+def conv_hermitian_fft(f, g):
+    f = _c128(f)
+    g = _c128(g)
+    K = f.shape[1]
+    assert f.shape == (2 * K - 1, K) == g.shape
+    h = np.empty_like(f)
+    _check(lib().hdco_conv_hermitian_2d_fft(_dptr(f), _dptr(g), K, _dptr(h)), "herm_fft")
+    return h
