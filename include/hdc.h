@@ -1,0 +1,170 @@
+/*
+ * hdc.h -- hybrid dealiased convolution on GB300 (sm_103a): the C ABI.
+ *
+ * The library computes the first L outputs of the linear convolution of two
+ * length-L complex inputs per axis (Section 2.3, Eq. 4, read with inputs of
+ * length L, zero beyond):
+ *
+ *     h_k = sum_{j=0}^{k} f_j g_{k-j},            k = 0 .. L-1,
+ *
+ * in 1, 2 or 3 dimensions, by the residue decomposition of Section 2.2:
+ * with zeta_n = exp(2 pi i / n), N = q m, j = t m + s, k = q l + r,
+ *
+ *   forward (Eq. 1):  F_{q l + r} = sum_s zeta_m^{l s} zeta_N^{r s} sum_t zeta_q^{r t} f_{t m + s}
+ *   backward (Eq. 2): f_{t m + s} = (1/N) sum_r zeta_q^{-t r} zeta_N^{-s r} sum_l zeta_m^{-s l} F_{q l + r}
+ *
+ * i.e. for every residue r: a twiddled fold of the p input blocks, an m-point
+ * FFT, the pointwise product of the two transforms (the convolution theorem,
+ * Section 2.4), an m-point inverse FFT and a twiddled unfold that
+ * accumulates the first L outputs.  Explicit padding (m >= M, p = q = 1,
+ * Section 3.1), implicit padding (L = p m, M = q m, Section 3.2) and hybrid
+ * padding (Section 3.3) are parameter choices of the same call.
+ *
+ * Parameters per axis (Section 2.5): L (input length), M (padded length,
+ * M >= 2L-1 for an alias-free result), m (FFT size), p = ceil(L/m) and
+ * q = ceil(M/m) (pass 0 to derive them; larger values are accepted), D
+ * (residues computed per pass, 1..q; 0 means q), I (in place: h may alias f).
+ *
+ * Conventions for every entry point:
+ *  - Arrays are interleaved complex (re, im), row-major, last axis fastest:
+ *    HDC_C128 = complex<double> (16 B), HDC_C64 = complex<float> (8 B); the
+ *    memory layout of torch.complex128 / torch.complex64.  A batch of B
+ *    problems is B consecutive arrays.
+ *  - f, g, h and the workspace are DEVICE pointers owned by the caller,
+ *    16-byte aligned, on the current CUDA device.  f and g are read-only
+ *    unless inplace = 1, in which case h may equal f or g.
+ *  - The library allocates device memory only for its own twiddle tables
+ *    (zeta_n^k for exact integer k, made once per (n, dtype, device) with
+ *    FP64 sincospi and kept until hdc_release_caches()).  The caller
+ *    allocates the workspace; query its size with hdc_workspace_size().
+ *  - Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default)
+ *    and is asynchronous; nothing is synchronised.
+ *  - Every error is a return code (hdc_status).  Nothing throws across the
+ *    ABI, nothing traps on the device.  Invalid parameters are rejected on
+ *    the host before any launch.
+ */
+#ifndef HDC_H
+#define HDC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HDC_MAX_DIMS 3
+
+typedef enum hdc_status {
+    HDC_OK = 0,
+    HDC_ERR_PARAM = -1,            /* inconsistent (L, M, m, p, q, D) or bad pointer/size  */
+    HDC_ERR_ALIAS = -2,            /* M < 2L-1: the result would contain aliases (Section 3.1) */
+    HDC_ERR_UNSUPPORTED_SIZE = -3, /* m not of the form 2^a 3^b 5^c 7^d, or beyond the limits */
+    HDC_ERR_DTYPE = -4,            /* unknown hdc_dtype                                     */
+    HDC_ERR_ALLOC = -5,            /* twiddle-table allocation failed                       */
+    HDC_ERR_CUDA = -6,             /* a CUDA runtime call or kernel launch failed           */
+    HDC_ERR_TIMEOUT = -7,          /* a bounded device-side wait gave up                    */
+    HDC_ERR_NOT_TUNED = -8,        /* no tuning record / predictor for the request          */
+    HDC_ERR_WORKSPACE = -9         /* workspace missing or smaller than required            */
+} hdc_status;
+
+typedef enum hdc_dtype {
+    HDC_C64 = 0,   /* complex<float>  */
+    HDC_C128 = 1   /* complex<double> */
+} hdc_dtype;
+
+/* ------------------------------------------------------------ host helpers
+ * No GPU needed. */
+
+/* Human-readable text for an hdc_status. Never NULL. */
+const char* hdc_strerror(int status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int hdc_version(void);
+
+/* 1 if n >= 1 has no prime factor above 7 (an FFT size this library runs,
+ * the 2^a 3^b 5^c 7^d sizes of Section 3.1 and Section 5.1), else 0. */
+int hdc_is_good_size(int64_t n);
+
+/* Smallest 2^a 3^b 5^c 7^d >= n (n >= 1); -1 on overflow or n < 1. */
+int64_t hdc_next_good_size(int64_t n);
+
+/* Section 2.5: p = ceil(L/m), q = ceil(M/m), the smallest integers with
+ * p m >= L and q m >= M.  Returns HDC_ERR_PARAM for L, M, m < 1. */
+int hdc_derive_params(int64_t L, int64_t M, int64_t m, int64_t* p, int64_t* q);
+
+/* Explicit padding (Section 3.1): m = smallest good size >= M, p = q = 1. */
+int hdc_explicit_params(int64_t L, int64_t M, int64_t* m, int64_t* p, int64_t* q);
+
+/* Check one axis.  p, q, D may be 0 (derived: p = ceil(L/m), q = ceil(M/m),
+ * D = q); the resolved values are written back through p_out, q_out, D_out
+ * when those are non-NULL.  Errors: HDC_ERR_PARAM (L, M, m < 1, p m < L,
+ * q m < M, D > q), HDC_ERR_ALIAS (M < 2L-1), HDC_ERR_UNSUPPORTED_SIZE (m not
+ * 7-smooth, m or q m beyond hdc_max_fft_size / hdc_max_padded_size),
+ * HDC_ERR_DTYPE. */
+int hdc_validate_axis(int64_t L, int64_t M, int64_t m, int64_t p, int64_t q,
+                      int64_t D, int dtype, int64_t* p_out, int64_t* q_out,
+                      int64_t* D_out);
+
+/* Largest FFT size m and padded size q m accepted for a dtype. */
+int64_t hdc_max_fft_size(int dtype);
+int64_t hdc_max_padded_size(int dtype);
+
+/* Bytes of device workspace an N-D call needs (dims in 1..3; arrays of
+ * length dims; p/q/D entries may be 0 = derive).  Writes *bytes. */
+int hdc_workspace_size(int dims, const int64_t* L, const int64_t* M,
+                       const int64_t* m, const int64_t* p, const int64_t* q,
+                       const int64_t* D, int dtype, int64_t batch, int inplace,
+                       size_t* bytes);
+
+/* ---------------------------------------------------------- convolutions */
+
+/* 1-D (Section 2.2-3.3): `batch` independent convolutions of length L.
+ * f, g, h: batch x L complex.  Workspace of hdc_workspace_size(1, ...). */
+int hdc_conv1d(const void* f, const void* g, void* h, int64_t L, int64_t M,
+               int64_t m, int64_t p, int64_t q, int64_t D, int inplace,
+               int dtype, int64_t batch, void* workspace, size_t ws_bytes,
+               void* stream);
+
+/* 2-D (Section 3.6, recursion over axes): f, g, h: batch x L[0] x L[1].
+ * Axis 0 is transformed by residues first; the inner 1-D convolution along
+ * axis 1 runs on each of its m[0] transformed rows per residue. */
+int hdc_conv2d(const void* f, const void* g, void* h, const int64_t L[2],
+               const int64_t M[2], const int64_t m[2], const int64_t p[2],
+               const int64_t q[2], const int64_t D[2], int inplace, int dtype,
+               int64_t batch, void* workspace, size_t ws_bytes, void* stream);
+
+/* 3-D (Section 3.6): f, g, h: batch x L[0] x L[1] x L[2]. */
+int hdc_conv3d(const void* f, const void* g, void* h, const int64_t L[3],
+               const int64_t M[3], const int64_t m[3], const int64_t p[3],
+               const int64_t q[3], const int64_t D[3], int inplace, int dtype,
+               int64_t batch, void* workspace, size_t ws_bytes, void* stream);
+
+/* Any of the above by rank (dims in 1..3). */
+int hdc_convnd(int dims, const void* f, const void* g, void* h,
+               const int64_t* L, const int64_t* M, const int64_t* m,
+               const int64_t* p, const int64_t* q, const int64_t* D,
+               int inplace, int dtype, int64_t batch, void* workspace,
+               size_t ws_bytes, void* stream);
+
+/* Free the cached twiddle tables on every device (call with no work in
+ * flight that uses them). */
+int hdc_release_caches(void);
+
+/* ------------------------------------------------------------ measurement
+ * Vector FMA throughput probe: the arithmetic roofline of this path (it runs
+ * on the FP64/FP32 pipes, not on tensor cores).  Launches `blocks` x
+ * `threads` threads that each run 8 independent FMA chains for `iters`
+ * iterations in FP64 (dtype HDC_C128) or FP32 (HDC_C64) on `stream`; `out`
+ * is a device buffer of blocks*threads elements of that real type (written
+ * only to keep the chains live).  *flops receives 2 * 8 * iters * threads *
+ * blocks; the caller times the launch with events.  No paper counterpart:
+ * the paper names no hardware. */
+int hdc_probe_fma(int dtype, int64_t iters, int blocks, int threads, void* out,
+                  void* stream, double* flops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HDC_H */

@@ -1,1 +1,267 @@
-"""Hybrid dealiased convolution on GB300 (placeholder; binding added below)."""
+"""Hybrid dealiased convolution on GB300: Python binding of libhdc.so.
+
+Argument marshalling only.  Every step of the convolution runs in the CUDA
+kernels of ``libhdc.so`` (see ``include/hdc.h`` for the C ABI); PyTorch
+supplies device memory and streams.  There is no CPU fallback: if the
+library is missing or no GPU is present, the calls raise.
+
+    import torch, paper_2306_10016_gb300 as hdc
+    h = hdc.conv1d(f, g, m=512)              # f, g: (L,) or (B, L) complex cuda
+    h = hdc.conv2d(f, g, m=(1024, 1024))     # f, g: (Lx, Ly) or (B, Lx, Ly)
+
+Parameters follow Section 2.5 of the paper, per axis: M (padded length,
+default 2L-1), m (FFT size), p and q (0: ceil(L/m), ceil(M/m)), D (residues
+per pass, 0: q) and inplace (the result overwrites f).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build_ext as _build_ext
+
+HDC_C64 = 0
+HDC_C128 = 1
+
+HDC_OK = 0
+HDC_ERR_PARAM = -1
+HDC_ERR_ALIAS = -2
+HDC_ERR_UNSUPPORTED_SIZE = -3
+HDC_ERR_DTYPE = -4
+HDC_ERR_ALLOC = -5
+HDC_ERR_CUDA = -6
+HDC_ERR_TIMEOUT = -7
+HDC_ERR_NOT_TUNED = -8
+HDC_ERR_WORKSPACE = -9
+
+LIB_PATH = _build_ext.LIB
+
+_i64 = C.c_int64
+_i64p = C.POINTER(C.c_int64)
+_vp = C.c_void_p
+_sz = C.c_size_t
+
+# (name, restype, argtypes) of every entry point declared in include/hdc.h
+_SIGS = [
+    ("hdc_strerror", C.c_char_p, [C.c_int]),
+    ("hdc_version", C.c_int, []),
+    ("hdc_is_good_size", C.c_int, [_i64]),
+    ("hdc_next_good_size", _i64, [_i64]),
+    ("hdc_derive_params", C.c_int, [_i64, _i64, _i64, _i64p, _i64p]),
+    ("hdc_explicit_params", C.c_int, [_i64, _i64, _i64p, _i64p, _i64p]),
+    ("hdc_validate_axis", C.c_int, [_i64, _i64, _i64, _i64, _i64, _i64, C.c_int, _i64p, _i64p, _i64p]),
+    ("hdc_max_fft_size", _i64, [C.c_int]),
+    ("hdc_max_padded_size", _i64, [C.c_int]),
+    ("hdc_workspace_size", C.c_int, [C.c_int, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, C.c_int, _i64,
+                                     C.c_int, C.POINTER(_sz)]),
+    ("hdc_conv1d", C.c_int, [_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _i64, C.c_int, C.c_int, _i64,
+                             _vp, _sz, _vp]),
+    ("hdc_conv2d", C.c_int, [_vp, _vp, _vp, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, C.c_int, C.c_int,
+                             _i64, _vp, _sz, _vp]),
+    ("hdc_conv3d", C.c_int, [_vp, _vp, _vp, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, C.c_int, C.c_int,
+                             _i64, _vp, _sz, _vp]),
+    ("hdc_convnd", C.c_int, [C.c_int, _vp, _vp, _vp, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, C.c_int,
+                             C.c_int, _i64, _vp, _sz, _vp]),
+    ("hdc_release_caches", C.c_int, []),
+    ("hdc_probe_fma", C.c_int, [C.c_int, _i64, C.c_int, C.c_int, _vp, _vp, C.POINTER(C.c_double)]),
+]
+
+_lib = None
+
+
+class HDCError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = strerror(code) if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+
+
+def build(force: bool = False) -> str:
+    """Compile libhdc.so for sm_103a (nvcc) if it is missing or stale."""
+    return _build_ext.build(force=force)
+
+
+def lib() -> C.CDLL:
+    """The loaded libhdc.so.  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2306_10016_gb300.build() "
+                               "(there is no fallback implementation)")
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in _SIGS:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != HDC_OK:
+        raise HDCError(rc, what)
+
+
+def _arr(vals):
+    a = (C.c_int64 * len(vals))(*[int(v) for v in vals])
+    return a
+
+
+# ------------------------------------------------------------ host helpers
+
+def strerror(code: int) -> str:
+    return lib().hdc_strerror(int(code)).decode()
+
+
+def is_good_size(n: int) -> bool:
+    return bool(lib().hdc_is_good_size(int(n)))
+
+
+def next_good_size(n: int) -> int:
+    return int(lib().hdc_next_good_size(int(n)))
+
+
+def derive_params(L: int, M: int, m: int):
+    p, q = C.c_int64(), C.c_int64()
+    _check(lib().hdc_derive_params(L, M, m, C.byref(p), C.byref(q)), "derive_params")
+    return p.value, q.value
+
+
+def explicit_params(L: int, M: int):
+    m, p, q = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(lib().hdc_explicit_params(L, M, C.byref(m), C.byref(p), C.byref(q)), "explicit_params")
+    return m.value, p.value, q.value
+
+
+def validate_axis(L, M, m, p=0, q=0, D=0, dtype=HDC_C128):
+    """Returns the status code and the resolved (p, q, D)."""
+    po, qo, Do = C.c_int64(), C.c_int64(), C.c_int64()
+    rc = lib().hdc_validate_axis(L, M, m, p, q, D, dtype, C.byref(po), C.byref(qo), C.byref(Do))
+    return rc, (po.value, qo.value, Do.value)
+
+
+def max_fft_size(dtype=HDC_C128) -> int:
+    return int(lib().hdc_max_fft_size(dtype))
+
+
+def max_padded_size(dtype=HDC_C128) -> int:
+    return int(lib().hdc_max_padded_size(dtype))
+
+
+def _per_axis(v, dims, name):
+    if v is None:
+        return None
+    if isinstance(v, (list, tuple)):
+        if len(v) != dims:
+            raise ValueError(f"{name} needs {dims} entries")
+        return [int(x) for x in v]
+    return [int(v)] * dims
+
+
+def workspace_size(L, M, m, p=0, q=0, D=0, dtype=HDC_C128, batch=1, inplace=False) -> int:
+    dims = len(L)
+    M, m, p, q, D = (_per_axis(v, dims, n) for v, n in ((M, "M"), (m, "m"), (p, "p"), (q, "q"), (D, "D")))
+    nb = C.c_size_t()
+    rc = lib().hdc_workspace_size(dims, _arr(L), _arr(M), _arr(m), _arr(p), _arr(q), _arr(D), dtype,
+                                  int(batch), int(bool(inplace)), C.byref(nb))
+    _check(rc, "workspace_size")
+    return nb.value
+
+
+# ------------------------------------------------------- torch entry points
+
+def _torch():
+    import torch
+    return torch
+
+
+def dtype_code(t) -> int:
+    torch = _torch()
+    if t == torch.complex128:
+        return HDC_C128
+    if t == torch.complex64:
+        return HDC_C64
+    raise TypeError(f"unsupported dtype {t}: use torch.complex64 or torch.complex128")
+
+
+def convnd(f, g, dims: int, m, M=None, p=0, q=0, D=0, out=None, inplace=False, workspace=None,
+           stream=None):
+    """First L outputs per axis of the linear convolution of f and g over
+    their last `dims` axes; leading axes are a batch.  Returns the output
+    tensor (f itself when inplace)."""
+    torch = _torch()
+    if not (f.is_cuda and g.is_cuda):
+        raise ValueError("f and g must be CUDA tensors (there is no CPU path)")
+    if f.shape != g.shape or f.dtype != g.dtype:
+        raise ValueError("f and g must have the same shape and dtype")
+    if f.dim() < dims:
+        raise ValueError(f"need at least {dims} axes")
+    if not (f.is_contiguous() and g.is_contiguous()):
+        raise ValueError("f and g must be contiguous")
+    dt = dtype_code(f.dtype)
+    L = [int(x) for x in f.shape[f.dim() - dims:]]
+    batch = 1
+    for x in f.shape[: f.dim() - dims]:
+        batch *= int(x)
+    Mv = _per_axis(M, dims, "M") or [2 * l - 1 for l in L]
+    mv = _per_axis(m, dims, "m")
+    pv = _per_axis(p, dims, "p")
+    qv = _per_axis(q, dims, "q")
+    Dv = _per_axis(D, dims, "D")
+    if inplace:
+        h = f
+    else:
+        h = out if out is not None else torch.empty_like(f)
+        if h.shape != f.shape or h.dtype != f.dtype or not h.is_contiguous() or not h.is_cuda:
+            raise ValueError("out must match f")
+    nbytes = workspace_size(L, Mv, mv, pv, qv, Dv, dt, batch, inplace)
+    if workspace is None or workspace.numel() * workspace.element_size() < nbytes:
+        workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=f.device)
+    st = stream if stream is not None else torch.cuda.current_stream(f.device)
+    with torch.cuda.device(f.device):
+        rc = lib().hdc_convnd(dims, f.data_ptr(), g.data_ptr(), h.data_ptr(), _arr(L), _arr(Mv), _arr(mv),
+                              _arr(pv), _arr(qv), _arr(Dv), int(bool(inplace)), dt, batch,
+                              workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                              st.cuda_stream)
+    _check(rc, "hdc_convnd")
+    return h
+
+
+def conv1d(f, g, m, M=None, p=0, q=0, D=0, **kw):
+    return convnd(f, g, 1, m, M, p, q, D, **kw)
+
+
+def conv2d(f, g, m, M=None, p=0, q=0, D=0, **kw):
+    return convnd(f, g, 2, m, M, p, q, D, **kw)
+
+
+def conv3d(f, g, m, M=None, p=0, q=0, D=0, **kw):
+    return convnd(f, g, 3, m, M, p, q, D, **kw)
+
+
+def probe_fma_peak(dtype=HDC_C128, iters=1 << 16, blocks=None, threads=256, reps=5, device=None):
+    """Measured vector FMA throughput in TFLOP/s (best of reps launches)."""
+    torch = _torch()
+    dev = torch.device(device or "cuda")
+    props = torch.cuda.get_device_properties(dev)
+    blocks = blocks or props.multi_processor_count * 8
+    out = torch.empty(blocks * threads, dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream(dev)
+    fl = C.c_double()
+    best = 0.0
+    with torch.cuda.device(dev):
+        for i in range(reps + 1):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            _check(lib().hdc_probe_fma(dtype, iters, blocks, threads, out.data_ptr(), st.cuda_stream,
+                                       C.byref(fl)), "probe_fma")
+            e1.record(st)
+            e1.synchronize()
+            if i:
+                best = max(best, fl.value / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    return best
+
+
+def release_caches() -> None:
+    _check(lib().hdc_release_caches(), "release_caches")

@@ -1,0 +1,410 @@
+// hdc_api.cu -- host side of the C ABI declared in include/hdc.h:
+// parameter derivation and validation (Section 2.5), the twiddle-table cache,
+// workspace sizing, and the drivers that sequence the kernels of
+// hdc_kernels.cu for 1-D rows and the N-D recursion over axes (Section 3.6).
+#include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <stdint.h>
+#include <string.h>
+#include <tuple>
+
+#include "hdc.h"
+#include "hdc_internal.h"
+
+#define HDC_EXPORT extern "C" __attribute__((visibility("default")))
+
+namespace hdc {
+
+template <typename T> cudaError_t launch_twiddle(cx<T>* tw, int64_t n, cudaStream_t st);
+
+// ----------------------------------------------------------- FFT plans
+
+FftPlan make_fft_plan(int64_t n)
+{
+    FftPlan fp;
+    memset(&fp, 0, sizeof(fp));
+    fp.n = (int)n;
+    int64_t k = n;
+    int ns = 0;
+    while (k % 8 == 0 && ns < HDC_MAX_STAGES) { fp.rad[ns++] = 8; k /= 8; }
+    while (k % 4 == 0 && ns < HDC_MAX_STAGES) { fp.rad[ns++] = 4; k /= 4; }
+    while (k % 2 == 0 && ns < HDC_MAX_STAGES) { fp.rad[ns++] = 2; k /= 2; }
+    while (k % 7 == 0 && ns < HDC_MAX_STAGES) { fp.rad[ns++] = 7; k /= 7; }
+    while (k % 5 == 0 && ns < HDC_MAX_STAGES) { fp.rad[ns++] = 5; k /= 5; }
+    while (k % 3 == 0 && ns < HDC_MAX_STAGES) { fp.rad[ns++] = 3; k /= 3; }
+    fp.nst = ns;
+    return fp;
+}
+
+// ------------------------------------------------------- twiddle cache
+
+namespace {
+std::mutex g_tw_mu;
+std::map<std::tuple<int, int64_t, int>, void*> g_tw;
+} // namespace
+
+template <typename T> const cx<T>* twiddles(int64_t n, cudaError_t* err)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { *err = e; return nullptr; }
+    const int dt = sizeof(T) == 8 ? 1 : 0;
+    std::lock_guard<std::mutex> lk(g_tw_mu);
+    auto key = std::make_tuple(dev, n, dt);
+    auto it = g_tw.find(key);
+    if (it != g_tw.end()) return reinterpret_cast<const cx<T>*>(it->second);
+    void* p = nullptr;
+    e = cudaMalloc(&p, (size_t)n * sizeof(cx<T>));
+    if (e != cudaSuccess) { *err = e; return nullptr; }
+    // built on a private stream and waited for, so the table is complete
+    // before any stream of the caller can read it
+    cudaStream_t s;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        e = launch_twiddle<T>(reinterpret_cast<cx<T>*>(p), n, s);
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = e2;
+        cudaStreamDestroy(s);
+    }
+    if (e != cudaSuccess) { cudaFree(p); *err = e; return nullptr; }
+    g_tw[key] = p;
+    return reinterpret_cast<const cx<T>*>(p);
+}
+template const cx<double>* twiddles<double>(int64_t, cudaError_t*);
+template const cx<float>* twiddles<float>(int64_t, cudaError_t*);
+
+// ----------------------------------------------------------- axis plan
+
+struct Axis {
+    int64_t L, M, m, p, q, D, N;
+    int64_t m1, m2; // split of m for the strided-axis route (m1 == 0: fused rows)
+};
+
+static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+static bool good_size(int64_t n)
+{
+    if (n < 1) return false;
+    for (int f : { 2, 3, 5, 7 })
+        while (n % f == 0) n /= f;
+    return n == 1;
+}
+
+template <typename T> static void split_m(Axis& a)
+{
+    a.m1 = 0;
+    a.m2 = a.m;
+    if (a.m <= max_row_fft<T>()) return;
+    // largest divisor m2 <= max_row with m1 = m / m2 <= max_col
+    for (int64_t d = max_row_fft<T>(); d >= 2; --d) {
+        if (a.m % d) continue;
+        if (a.m / d <= max_col_fft<T>()) { a.m2 = d; a.m1 = a.m / d; return; }
+    }
+    a.m1 = -1; // unsupported
+}
+
+static int64_t max_fft(int dtype) { return dtype == HDC_C128 ? (int64_t)1 << 24 : (int64_t)1 << 25; }
+static int64_t max_padded(int dtype) { return dtype == HDC_C128 ? (int64_t)1 << 25 : (int64_t)1 << 26; }
+
+static int resolve_axis(int64_t L, int64_t M, int64_t m, int64_t p, int64_t q, int64_t D, int dtype, Axis* out)
+{
+    if (dtype != HDC_C64 && dtype != HDC_C128) return HDC_ERR_DTYPE;
+    if (L < 1 || M < 1 || m < 1 || p < 0 || q < 0 || D < 0) return HDC_ERR_PARAM;
+    if (M < 2 * L - 1) return HDC_ERR_ALIAS;
+    if (p == 0) p = ceil_div(L, m);
+    if (q == 0) q = ceil_div(M, m);
+    if (p * m < L || q * m < M) return HDC_ERR_PARAM;
+    if (D == 0) D = q;
+    if (D > q) return HDC_ERR_PARAM;
+    if (!good_size(m) || m > max_fft(dtype)) return HDC_ERR_UNSUPPORTED_SIZE;
+    if (q > max_padded(dtype) / m) return HDC_ERR_UNSUPPORTED_SIZE;
+    Axis a;
+    a.L = L; a.M = M; a.m = m; a.p = p; a.q = q; a.D = D; a.N = q * m;
+    if (dtype == HDC_C128) split_m<double>(a); else split_m<float>(a);
+    if (a.m1 < 0) return HDC_ERR_UNSUPPORTED_SIZE;
+    if (out) *out = a;
+    return HDC_OK;
+}
+
+// ------------------------------------------------------------ workspace
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Elements (complex) of workspace for the N-D problem over axes[0..dims),
+// batch B, shapes L[0..dims).
+static int64_t ws_elems(int dims, const Axis* ax, int64_t B)
+{
+    if (dims == 1) {
+        const Axis& a = ax[0];
+        if (a.m1 == 0) return a.D * B * a.m;
+        return 2 * a.D * B * a.m;
+    }
+    int64_t Cn = 1;
+    for (int i = 1; i < dims; ++i) Cn *= ax[i].L;
+    const Axis& a = ax[0];
+    const int64_t rows = a.D * B * a.m;
+    return 3 * rows * Cn + ws_elems(dims - 1, ax + 1, rows);
+}
+
+static size_t ws_bytes(int dims, const Axis* ax, int64_t B, size_t esz, int ncopy)
+{
+    int64_t tot = 1;
+    for (int i = 0; i < dims; ++i) tot *= ax[i].L;
+    size_t b = 0;
+    b += (size_t)ncopy * align_up((size_t)(B * tot) * esz);
+    b += align_up((size_t)ws_elems(dims, ax, B) * esz);
+    return b + 256;
+}
+
+// ------------------------------------------------------------- drivers
+
+#define HDC_TRY(x)                                  \
+    do {                                            \
+        cudaError_t _e = (x);                       \
+        if (_e != cudaSuccess) return _e;           \
+    } while (0)
+
+// 1-D convolution of B rows (row stride ld) along a contiguous axis.
+template <typename T>
+static cudaError_t run_rows(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t B, int64_t ld,
+                            const Axis& a, cx<T>* ws, cudaStream_t st)
+{
+    const double scale = 1.0 / (double)a.N;
+    if (a.m1 == 0) {
+        for (int64_t r0 = 0; r0 < a.q; r0 += a.D) {
+            const int first = (r0 == 0), last = (r0 + a.D >= a.q);
+            HDC_TRY(launch_residue_rows<T>(f, g, ws, B, ld, a.L, a.m, a.p, a.q, r0, a.D, st));
+            HDC_TRY(launch_unfold<T>(out, ws, B, ld, 1, a.m, a.p, a.q, a.N, 1, 0, a.L, r0, a.D, first,
+                                     last, scale, st));
+        }
+        return cudaSuccess;
+    }
+    // m = m1 m2: fold + m1-point FFTs along the strided view [p m1][m2] with the
+    // inner twiddle zeta_m^{l1 s2}; m2-point row transforms, product and
+    // inverse; inverse m1-point FFTs; unfold.
+    cx<T>* yf = ws;
+    cx<T>* yg = ws + a.D * B * a.m;
+    for (int64_t r0 = 0; r0 < a.q; r0 += a.D) {
+        const int first = (r0 == 0), last = (r0 + a.D >= a.q);
+        const int64_t Dg = (a.D < a.q - r0) ? a.D : (a.q - r0);
+        HDC_TRY(launch_fold_fft_cols<T>(f, g, yf, yg, B, ld, a.m2, a.m1, a.p, a.q, a.N, a.m2, 1, a.L,
+                                        r0, a.D, 1, st));
+        HDC_TRY(launch_residue_rows<T>(yf, yg, yf, Dg * B * a.m1, a.m2, a.m2, a.m2, 1, 1, 0, 1, st));
+        HDC_TRY(launch_ifft_cols<T>(yf, B, a.m2, a.m1, a.q, a.N, Dg, 1, st));
+        HDC_TRY(launch_unfold<T>(out, yf, B, ld, a.m2, a.m1, a.p, a.q, a.N, a.m2, 1, a.L, r0, a.D, first,
+                                 last, scale, st));
+    }
+    return cudaSuccess;
+}
+
+// N-D: residues of axis 0 (strided, Cn = product of the inner extents), the
+// inner (N-1)-D convolution on every transformed row, inverse and unfold.
+template <typename T>
+static cudaError_t run_nd(int dims, const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t B,
+                          const Axis* ax, cx<T>* ws, cudaStream_t st)
+{
+    if (dims == 1) return run_rows<T>(f, g, out, B, ax[0].L, ax[0], ws, st);
+    int64_t Cn = 1;
+    for (int i = 1; i < dims; ++i) Cn *= ax[i].L;
+    const Axis& a = ax[0];
+    const int64_t rows = a.D * B * a.m;
+    cx<T>* wf = ws;
+    cx<T>* wg = wf + rows * Cn;
+    cx<T>* wh = wg + rows * Cn;
+    cx<T>* inner = wh + rows * Cn;
+    const int64_t bstride = a.L * Cn;
+    const double scale = 1.0 / (double)a.N;
+    for (int64_t r0 = 0; r0 < a.q; r0 += a.D) {
+        const int first = (r0 == 0), last = (r0 + a.D >= a.q);
+        const int64_t Dg = (a.D < a.q - r0) ? a.D : (a.q - r0);
+        HDC_TRY(launch_fold_fft_cols<T>(f, g, wf, wg, B, bstride, Cn, a.m, a.p, a.q, a.N, 1, 0,
+                                        a.L * Cn, r0, a.D, 0, st));
+        HDC_TRY(run_nd<T>(dims - 1, wf, wg, wh, Dg * B * a.m, ax + 1, inner, st));
+        HDC_TRY(launch_ifft_cols<T>(wh, B, Cn, a.m, a.q, a.N, Dg, 0, st));
+        HDC_TRY(launch_unfold<T>(out, wh, B, bstride, Cn, a.m, a.p, a.q, a.N, 1, 0, a.L * Cn, r0, a.D,
+                                 first, last, scale, st));
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+static int conv_nd(int dims, const void* f, const void* g, void* h, const Axis* ax, int inplace,
+                   int64_t B, void* ws, size_t ws_bytes_given, cudaStream_t st)
+{
+    using V = cx<T>;
+    int64_t tot = 1;
+    for (int i = 0; i < dims; ++i) tot *= ax[i].L;
+    const bool af = (h == f), ag = (h == g);
+    if ((af || ag) && !inplace) return HDC_ERR_PARAM;
+    const int ncopy = (int)af + (int)(ag && g != f);
+    const size_t need = ws_bytes(dims, ax, B, sizeof(V), ncopy);
+    if (ws == nullptr || ws_bytes_given < need) return HDC_ERR_WORKSPACE;
+    uintptr_t base = ((uintptr_t)ws + 255) & ~(uintptr_t)255;
+    const V* fin = (const V*)f;
+    const V* gin = (const V*)g;
+    const size_t arr = (size_t)(B * tot) * sizeof(V);
+    if (af) {
+        if (cudaMemcpyAsync((void*)base, f, arr, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return HDC_ERR_CUDA;
+        fin = (const V*)base;
+        if (g == f) gin = fin;
+        base += align_up(arr);
+    }
+    if (ag && g != f) {
+        if (cudaMemcpyAsync((void*)base, g, arr, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return HDC_ERR_CUDA;
+        gin = (const V*)base;
+        base += align_up(arr);
+    }
+    cudaError_t e = run_nd<T>(dims, fin, gin, (V*)h, B, ax, (V*)base, st);
+    return e == cudaSuccess ? HDC_OK : HDC_ERR_CUDA;
+}
+
+static int resolve_all(int dims, const int64_t* L, const int64_t* M, const int64_t* m, const int64_t* p,
+                       const int64_t* q, const int64_t* D, int dtype, Axis* ax)
+{
+    if (dims < 1 || dims > HDC_MAX_DIMS || !L || !M || !m) return HDC_ERR_PARAM;
+    for (int i = 0; i < dims; ++i) {
+        int rc = resolve_axis(L[i], M[i], m[i], p ? p[i] : 0, q ? q[i] : 0, D ? D[i] : 0, dtype, &ax[i]);
+        if (rc != HDC_OK) return rc;
+    }
+    return HDC_OK;
+}
+
+} // namespace hdc
+
+using namespace hdc;
+
+// ------------------------------------------------------------------ ABI
+
+HDC_EXPORT const char* hdc_strerror(int status)
+{
+    switch (status) {
+    case HDC_OK: return "ok";
+    case HDC_ERR_PARAM: return "invalid or inconsistent parameters";
+    case HDC_ERR_ALIAS: return "padding too small: M < 2L-1 would alias";
+    case HDC_ERR_UNSUPPORTED_SIZE: return "unsupported size (m must be 2^a 3^b 5^c 7^d within the limits)";
+    case HDC_ERR_DTYPE: return "unknown dtype";
+    case HDC_ERR_ALLOC: return "device allocation failed";
+    case HDC_ERR_CUDA: return "CUDA runtime error";
+    case HDC_ERR_TIMEOUT: return "device wait timed out";
+    case HDC_ERR_NOT_TUNED: return "no tuning record or predictor for this request";
+    case HDC_ERR_WORKSPACE: return "workspace missing or too small";
+    default: return "unknown status";
+    }
+}
+
+HDC_EXPORT int hdc_version(void) { return 100; }
+
+HDC_EXPORT int hdc_is_good_size(int64_t n) { return good_size(n) ? 1 : 0; }
+
+HDC_EXPORT int64_t hdc_next_good_size(int64_t n)
+{
+    if (n < 1) return -1;
+    for (int64_t k = n; k < ((int64_t)1 << 62); ++k)
+        if (good_size(k)) return k;
+    return -1;
+}
+
+HDC_EXPORT int hdc_derive_params(int64_t L, int64_t M, int64_t m, int64_t* p, int64_t* q)
+{
+    if (L < 1 || M < 1 || m < 1 || !p || !q) return HDC_ERR_PARAM;
+    *p = ceil_div(L, m);
+    *q = ceil_div(M, m);
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_explicit_params(int64_t L, int64_t M, int64_t* m, int64_t* p, int64_t* q)
+{
+    if (L < 1 || M < 1 || !m || !p || !q) return HDC_ERR_PARAM;
+    *m = hdc_next_good_size(M);
+    if (*m < 0) return HDC_ERR_UNSUPPORTED_SIZE;
+    *p = 1;
+    *q = 1;
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_validate_axis(int64_t L, int64_t M, int64_t m, int64_t p, int64_t q, int64_t D, int dtype,
+                                 int64_t* p_out, int64_t* q_out, int64_t* D_out)
+{
+    Axis a;
+    int rc = resolve_axis(L, M, m, p, q, D, dtype, &a);
+    if (rc != HDC_OK) return rc;
+    if (p_out) *p_out = a.p;
+    if (q_out) *q_out = a.q;
+    if (D_out) *D_out = a.D;
+    return HDC_OK;
+}
+
+HDC_EXPORT int64_t hdc_max_fft_size(int dtype) { return max_fft(dtype); }
+HDC_EXPORT int64_t hdc_max_padded_size(int dtype) { return max_padded(dtype); }
+
+HDC_EXPORT int hdc_workspace_size(int dims, const int64_t* L, const int64_t* M, const int64_t* m,
+                                  const int64_t* p, const int64_t* q, const int64_t* D, int dtype,
+                                  int64_t batch, int inplace, size_t* bytes)
+{
+    if (!bytes || batch < 0) return HDC_ERR_PARAM;
+    Axis ax[HDC_MAX_DIMS];
+    int rc = resolve_all(dims, L, M, m, p, q, D, dtype, ax);
+    if (rc != HDC_OK) return rc;
+    const size_t esz = dtype == HDC_C128 ? 16 : 8;
+    *bytes = ws_bytes(dims, ax, batch, esz, inplace ? 2 : 0);
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_convnd(int dims, const void* f, const void* g, void* h, const int64_t* L, const int64_t* M,
+                          const int64_t* m, const int64_t* p, const int64_t* q, const int64_t* D, int inplace,
+                          int dtype, int64_t batch, void* workspace, size_t ws_bytes_given, void* stream)
+{
+    Axis ax[HDC_MAX_DIMS];
+    int rc = resolve_all(dims, L, M, m, p, q, D, dtype, ax);
+    if (rc != HDC_OK) return rc;
+    if (batch < 0) return HDC_ERR_PARAM;
+    if (batch == 0) return HDC_OK;
+    if (!f || !g || !h) return HDC_ERR_PARAM;
+    const uintptr_t al = dtype == HDC_C128 ? 15 : 7;
+    if (((uintptr_t)f & al) || ((uintptr_t)g & al) || ((uintptr_t)h & al)) return HDC_ERR_PARAM;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == HDC_C128) return conv_nd<double>(dims, f, g, h, ax, inplace, batch, workspace, ws_bytes_given, st);
+    return conv_nd<float>(dims, f, g, h, ax, inplace, batch, workspace, ws_bytes_given, st);
+}
+
+HDC_EXPORT int hdc_conv1d(const void* f, const void* g, void* h, int64_t L, int64_t M, int64_t m, int64_t p,
+                          int64_t q, int64_t D, int inplace, int dtype, int64_t batch, void* workspace,
+                          size_t ws_bytes_given, void* stream)
+{
+    return hdc_convnd(1, f, g, h, &L, &M, &m, &p, &q, &D, inplace, dtype, batch, workspace, ws_bytes_given,
+                      stream);
+}
+
+HDC_EXPORT int hdc_conv2d(const void* f, const void* g, void* h, const int64_t L[2], const int64_t M[2],
+                          const int64_t m[2], const int64_t p[2], const int64_t q[2], const int64_t D[2],
+                          int inplace, int dtype, int64_t batch, void* workspace, size_t ws_bytes_given,
+                          void* stream)
+{
+    return hdc_convnd(2, f, g, h, L, M, m, p, q, D, inplace, dtype, batch, workspace, ws_bytes_given, stream);
+}
+
+HDC_EXPORT int hdc_conv3d(const void* f, const void* g, void* h, const int64_t L[3], const int64_t M[3],
+                          const int64_t m[3], const int64_t p[3], const int64_t q[3], const int64_t D[3],
+                          int inplace, int dtype, int64_t batch, void* workspace, size_t ws_bytes_given,
+                          void* stream)
+{
+    return hdc_convnd(3, f, g, h, L, M, m, p, q, D, inplace, dtype, batch, workspace, ws_bytes_given, stream);
+}
+
+HDC_EXPORT int hdc_release_caches(void)
+{
+    std::lock_guard<std::mutex> lk(g_tw_mu);
+    int rc = HDC_OK;
+    for (auto& kv : g_tw) {
+        int dev = std::get<0>(kv.first);
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(dev);
+        if (cudaFree(kv.second) != cudaSuccess) rc = HDC_ERR_CUDA;
+        cudaSetDevice(cur);
+    }
+    g_tw.clear();
+    return rc;
+}

@@ -1,0 +1,69 @@
+// hdc_internal.h -- host-side declarations shared by the translation units of
+// the library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "hdc_fft.cuh"
+
+namespace hdc {
+
+// Block size cap of the transform kernels (every stage loops over its
+// butterflies, so any count works; 512 leaves 128 registers per thread).
+constexpr int kMaxThreads = 512;
+// Shared-memory budget: the fused residue kernel holds f, g and one
+// ping-pong buffer of m elements (3 m), the strided-axis kernels a tile of
+// ma x C elements and its ping-pong twin (2 ma C).
+constexpr int64_t kRowBytes = 192 * 1024;
+constexpr int64_t kColBytes = 128 * 1024;
+
+template <typename T> constexpr int64_t max_row_fft() { return kRowBytes / (3 * (int64_t)sizeof(cx<T>)); }
+template <typename T> constexpr int64_t col_tile_elems() { return kColBytes / (2 * (int64_t)sizeof(cx<T>)); }
+template <typename T> constexpr int64_t max_col_fft() { return col_tile_elems<T>(); }
+
+FftPlan make_fft_plan(int64_t n);
+
+// Twiddle table zeta_n^k, k < n, of dtype T on the current device (cached).
+template <typename T> const cx<T>* twiddles(int64_t n, cudaError_t* err);
+
+// ------------------------------------------------------------ launchers
+
+// Fused residue kernel over rows: for every row b < B and residue
+// r = r0 + rr (rr < D, r < q): fold the row of f and g (period m, p blocks,
+// valid elements j < L), m-point FFTs, product, inverse FFT, and write the
+// unscaled result to h + ((rr * B + b) * m).
+template <typename T>
+cudaError_t launch_residue_rows(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_t B,
+                                int64_t ld_in, int64_t L, int64_t m, int64_t p, int64_t q,
+                                int64_t r0, int64_t D, cudaStream_t st);
+
+// Fold along a strided axis + FFT of size ma over that axis, for f (which 0)
+// and g (which 1), column tile of width C.  Array view x[b][a][c] with
+// a < A (axis), c < Cn; element valid iff a * Cn + c < Lvalid.  Output
+// y[which][rr][b][l][c] for rr < D.  Fold twiddle zeta_Nf^{r (i cs + c cc)};
+// if post != 0 the transformed value is multiplied by zeta_{Nf/q}^{l c}
+// (the inner twiddle of a split m = ma * Cn transform).
+template <typename T>
+cudaError_t launch_fold_fft_cols(const cx<T>* f, const cx<T>* g, cx<T>* yf, cx<T>* yg,
+                                 int64_t B, int64_t bstride, int64_t Cn, int64_t ma, int64_t p,
+                                 int64_t q, int64_t Nf, int64_t cs, int64_t cc, int64_t Lvalid,
+                                 int64_t r0, int64_t D, int post, cudaStream_t st);
+
+// In-place inverse FFT of size ma along the strided axis of y[rr][b][l][c],
+// preceded by multiplication with conj(zeta_{Nf/q}^{l c}) if pre != 0.
+template <typename T>
+cudaError_t launch_ifft_cols(cx<T>* y, int64_t B, int64_t Cn, int64_t ma, int64_t q, int64_t Nf,
+                             int64_t D, int pre, cudaStream_t st);
+
+// Unfold-accumulate: out[b][(t ma + i) Cn + c] (valid iff < Lvalid) gets
+// sum_{rr} conj(zeta_Nf^{r (i cs + c cc)}) conj(zeta_q^{r t}) h[rr][b][i][c];
+// added to the previous contents unless first, scaled by `scale` if last.
+template <typename T>
+cudaError_t launch_unfold(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstride, int64_t Cn,
+                          int64_t ma, int64_t p, int64_t q, int64_t Nf, int64_t cs, int64_t cc,
+                          int64_t Lvalid, int64_t r0, int64_t D, int first, int last, double scale,
+                          cudaStream_t st);
+
+} // namespace hdc

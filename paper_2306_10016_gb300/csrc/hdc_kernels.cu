@@ -1,0 +1,379 @@
+// hdc_kernels.cu -- the CUDA kernels of the hot path and their launchers.
+//
+//  k_twiddle        zeta_n^k table in FP64 (exact integer angle, sincospi)
+//  k_residue_rows   fused per (row, residue): fold (Eq. 1 inner sums) of f and
+//                   g -> m-point FFTs -> pointwise product (Section 2.4) ->
+//                   m-point inverse FFT (Eq. 2 inner sum); unscaled result
+//  k_fold_fft_cols  fold along a strided axis + FFT over that axis, a tile of
+//                   C neighbouring columns per block (N-D outer axes, and the
+//                   first half of a split m = m1 m2 transform)
+//  k_ifft_cols      inverse FFT over a strided axis, in place
+//  k_unfold         twiddled unfold-accumulate of the first L outputs (Eq. 2
+//                   outer sums), residues summed in increasing r, one scale
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hdc_internal.h"
+
+namespace hdc {
+
+// ------------------------------------------------------------- twiddles
+
+template <class V>
+__global__ void k_twiddle(V* tw, int64_t n)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    // angle 2 pi k / n folded into (-pi, pi] in integers, then one FP64
+    // sincospi: the table entry is rounded once, never built by recurrence.
+    const int64_t kk = (2 * k > n) ? k - n : k;
+    double s, c;
+    sincospi(2.0 * (double)kk / (double)n, &s, &c);
+    using T = typename real_of<V>::type;
+    tw[k] = mkc<V>((T)c, (T)s);
+}
+
+template <typename T>
+cudaError_t launch_twiddle(cx<T>* tw, int64_t n, cudaStream_t st)
+{
+    const int thr = 256;
+    const int64_t blocks = (n + thr - 1) / thr;
+    k_twiddle<cx<T>><<<(unsigned)blocks, thr, 0, st>>>(tw, n);
+    return cudaGetLastError();
+}
+template cudaError_t launch_twiddle<double>(cx<double>*, int64_t, cudaStream_t);
+template cudaError_t launch_twiddle<float>(cx<float>*, int64_t, cudaStream_t);
+
+// ------------------------------------------------------- helpers (host)
+
+// One thread per radix-8 butterfly of the transform, within [64, kMaxThreads].
+static int threads_for(int64_t elems)
+{
+    int64_t t = (elems + 7) / 8;
+    t = ((t + 31) / 32) * 32;
+    if (t < 64) t = 64;
+    if (t > kMaxThreads) t = kMaxThreads;
+    return (int)t;
+}
+
+template <typename K>
+static cudaError_t allow_smem(K kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// ------------------------------------------------------- residue rows
+
+template <class V>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+k_residue_rows(const V* f, const V* g, V* h, int64_t B, int64_t ld_in, int64_t L, int m, int p,
+               int q, int r0, int Dg, const V* __restrict__ twN, const V* __restrict__ twm,
+               FftPlan fp)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* sa = reinterpret_cast<V*>(smraw);
+    V* sb = sa + m;
+    V* sc = sb + m;
+    const int64_t b = blockIdx.x % B;
+    const int rr = (int)(blockIdx.x / B);
+    const int r = r0 + rr;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const V* fr = f + b * ld_in;
+    const V* gr = g + b * ld_in;
+    // fold: w_r[s] = zeta_N^{r s} sum_t zeta_q^{r t} x[t m + s]   (Eq. 1)
+    for (int s = tid; s < m; s += nthr) {
+        V af = czero<V>(), ag = czero<V>();
+        for (int t = 0; t < p; ++t) {
+            const int64_t j = (int64_t)t * m + s;
+            if (j >= L) break;
+            const V fv = fr[j], gv = gr[j];
+            if (r == 0) {
+                af = cadd(af, fv);
+                ag = cadd(ag, gv);
+            } else {
+                const V w = __ldg(twN + (((int64_t)r * t) % q) * m);
+                af = cfma(fv, w, af);
+                ag = cfma(gv, w, ag);
+            }
+        }
+        if (r != 0) {
+            const V w = __ldg(twN + (int64_t)r * s);
+            af = cmul(af, w);
+            ag = cmul(ag, w);
+        }
+        sa[s] = af;
+        sb[s] = ag;
+    }
+    __syncthreads();
+    fft_smem<V, false>(sa, sc, fp, 1, 1, m, twm, tid, nthr);
+    fft_smem<V, false>(sb, sc, fp, 1, 1, m, twm, tid, nthr);
+    for (int s = tid; s < m; s += nthr) sa[s] = cmul(sa[s], sb[s]);
+    __syncthreads();
+    fft_smem<V, true>(sa, sc, fp, 1, 1, m, twm, tid, nthr);
+    V* hr = h + ((int64_t)rr * B + b) * m;
+    for (int s = tid; s < m; s += nthr) hr[s] = sa[s];
+}
+
+template <typename T>
+cudaError_t launch_residue_rows(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_t B, int64_t ld_in,
+                                int64_t L, int64_t m, int64_t p, int64_t q, int64_t r0, int64_t D,
+                                cudaStream_t st)
+{
+    using V = cx<T>;
+    const int64_t Dg = (D < q - r0) ? D : (q - r0);
+    if (B <= 0 || Dg <= 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    const V* twN = twiddles<T>(q * m, &e);
+    if (e != cudaSuccess) return e;
+    const V* twm = twiddles<T>(m, &e);
+    if (e != cudaSuccess) return e;
+    const FftPlan fp = make_fft_plan(m);
+    const int thr = threads_for(m);
+    const size_t smem = (size_t)(3 * m) * sizeof(V);
+    auto kern = k_residue_rows<V>;
+    if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
+    const int64_t blocks = B * Dg;
+    kern<<<(unsigned)blocks, thr, smem, st>>>(f, g, h, B, ld_in, L, (int)m, (int)p, (int)q, (int)r0,
+                                              (int)Dg, twN, twm, fp);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------ strided-axis passes
+
+static int col_tile(int64_t Cn, int64_t ma, int64_t elems_max)
+{
+    int64_t C = 16;
+    while (C > 1 && ma * C > elems_max) C >>= 1;
+    while (C > 1 && C / 2 >= Cn) C >>= 1;
+    return (int)C;
+}
+
+template <class V>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+k_fold_fft_cols(const V* __restrict__ f, const V* __restrict__ g, V* yf, V* yg, int64_t B,
+                int64_t bstride, int64_t Cn, int ma, int p, int q, int64_t Nf, int64_t cs,
+                int64_t cc, int64_t Lvalid, int r0, int Dg, int C, int nct, int post,
+                const V* __restrict__ twNf, const V* __restrict__ twma, FftPlan fp)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* buf = reinterpret_cast<V*>(smraw);
+    V* tmp = buf + ma * C;
+    int64_t blk = blockIdx.x;
+    const int ct = (int)(blk % nct);
+    blk /= nct;
+    const int rr = (int)(blk % Dg);
+    blk /= Dg;
+    const int which = (int)(blk & 1);
+    const int64_t b = blk >> 1;
+    const int r = r0 + rr;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int64_t c0 = (int64_t)ct * C;
+    const V* x = (which ? g : f) + b * bstride;
+    V* y = which ? yg : yf;
+    const int64_t mq = Nf / q;
+    for (int e = tid; e < ma * C; e += nthr) {
+        const int i = e / C, cl = e - i * C;
+        const int64_t c = c0 + cl;
+        V acc = czero<V>();
+        if (c < Cn) {
+            for (int t = 0; t < p; ++t) {
+                const int64_t lin = ((int64_t)t * ma + i) * Cn + c;
+                if (lin >= Lvalid) break;
+                const V xv = x[lin];
+                if (r == 0) acc = cadd(acc, xv);
+                else acc = cfma(xv, __ldg(twNf + (((int64_t)r * t) % q) * mq), acc);
+            }
+            if (r != 0) acc = cmul(acc, __ldg(twNf + (int64_t)r * (i * cs + c * cc)));
+        }
+        buf[e] = acc;
+    }
+    __syncthreads();
+    if (ma > 1) fft_smem<V, false>(buf, tmp, fp, C, C, 1, twma, tid, nthr);
+    V* yb = y + ((int64_t)rr * B + b) * ma * Cn;
+    for (int e = tid; e < ma * C; e += nthr) {
+        const int l = e / C, cl = e - l * C;
+        const int64_t c = c0 + cl;
+        if (c >= Cn) continue;
+        V v = buf[e];
+        if (post && l != 0 && c != 0) v = cmul(v, __ldg(twNf + (int64_t)l * c * q));
+        yb[(int64_t)l * Cn + c] = v;
+    }
+}
+
+template <typename T>
+cudaError_t launch_fold_fft_cols(const cx<T>* f, const cx<T>* g, cx<T>* yf, cx<T>* yg, int64_t B,
+                                 int64_t bstride, int64_t Cn, int64_t ma, int64_t p, int64_t q,
+                                 int64_t Nf, int64_t cs, int64_t cc, int64_t Lvalid, int64_t r0,
+                                 int64_t D, int post, cudaStream_t st)
+{
+    using V = cx<T>;
+    const int64_t Dg = (D < q - r0) ? D : (q - r0);
+    if (B <= 0 || Dg <= 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    const V* twNf = twiddles<T>(Nf, &e);
+    if (e != cudaSuccess) return e;
+    const V* twma = twiddles<T>(ma, &e);
+    if (e != cudaSuccess) return e;
+    const FftPlan fp = make_fft_plan(ma);
+    const int C = col_tile(Cn, ma, col_tile_elems<T>());
+    const int nct = (int)((Cn + C - 1) / C);
+    const int thr = threads_for(ma * C);
+    const size_t smem = (size_t)(2 * ma * C) * sizeof(V);
+    auto kern = k_fold_fft_cols<V>;
+    if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
+    const int64_t blocks = (int64_t)nct * Dg * 2 * B;
+    kern<<<(unsigned)blocks, thr, smem, st>>>(f, g, yf, yg, B, bstride, Cn, (int)ma, (int)p, (int)q,
+                                              Nf, cs, cc, Lvalid, (int)r0, (int)Dg, C, nct, post,
+                                              twNf, twma, fp);
+    return cudaGetLastError();
+}
+
+template <class V>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+k_ifft_cols(V* y, int64_t B, int64_t Cn, int ma, int q, int64_t Nf, int Dg, int C, int nct, int pre,
+            const V* __restrict__ twNf, const V* __restrict__ twma, FftPlan fp)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* buf = reinterpret_cast<V*>(smraw);
+    V* tmp = buf + ma * C;
+    int64_t blk = blockIdx.x;
+    const int ct = (int)(blk % nct);
+    blk /= nct;
+    const int rr = (int)(blk % Dg);
+    const int64_t b = blk / Dg;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int64_t c0 = (int64_t)ct * C;
+    V* yb = y + ((int64_t)rr * B + b) * ma * Cn;
+    for (int e = tid; e < ma * C; e += nthr) {
+        const int l = e / C, cl = e - l * C;
+        const int64_t c = c0 + cl;
+        V v = czero<V>();
+        if (c < Cn) {
+            v = yb[(int64_t)l * Cn + c];
+            if (pre && l != 0 && c != 0) v = cmulc(v, __ldg(twNf + (int64_t)l * c * q));
+        }
+        buf[e] = v;
+    }
+    __syncthreads();
+    if (ma > 1) fft_smem<V, true>(buf, tmp, fp, C, C, 1, twma, tid, nthr);
+    for (int e = tid; e < ma * C; e += nthr) {
+        const int s = e / C, cl = e - s * C;
+        const int64_t c = c0 + cl;
+        if (c < Cn) yb[(int64_t)s * Cn + c] = buf[e];
+    }
+}
+
+template <typename T>
+cudaError_t launch_ifft_cols(cx<T>* y, int64_t B, int64_t Cn, int64_t ma, int64_t q, int64_t Nf,
+                             int64_t D, int pre, cudaStream_t st)
+{
+    using V = cx<T>;
+    if (B <= 0 || D <= 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    const V* twNf = twiddles<T>(Nf, &e);
+    if (e != cudaSuccess) return e;
+    const V* twma = twiddles<T>(ma, &e);
+    if (e != cudaSuccess) return e;
+    const FftPlan fp = make_fft_plan(ma);
+    const int C = col_tile(Cn, ma, col_tile_elems<T>());
+    const int nct = (int)((Cn + C - 1) / C);
+    const int thr = threads_for(ma * C);
+    const size_t smem = (size_t)(2 * ma * C) * sizeof(V);
+    auto kern = k_ifft_cols<V>;
+    if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
+    const int64_t blocks = (int64_t)nct * D * B;
+    kern<<<(unsigned)blocks, thr, smem, st>>>(y, B, Cn, (int)ma, (int)q, Nf, (int)D, C, nct, pre, twNf,
+                                              twma, fp);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- unfold
+
+template <class V, int PT>
+__global__ void __launch_bounds__(256)
+k_unfold(V* out, const V* __restrict__ h, int64_t B, int64_t bstride, int64_t Cn, int64_t ma,
+         int p, int q, int64_t Nf, int64_t cs, int64_t cc, int64_t Lvalid, int r0, int Dg,
+         int first, int last, typename real_of<V>::type scale, const V* __restrict__ twNf)
+{
+    const int64_t per = ma * Cn;
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gid >= per * B) return;
+    const int64_t b = gid / per;
+    const int64_t e = gid - b * per;
+    const int64_t i = e / Cn, c = e - i * Cn;
+    const int64_t mq = Nf / q;
+    V* ob = out + b * bstride;
+    for (int t0 = 0; t0 < p; t0 += PT) {
+        if ((((int64_t)t0 * ma + i) * Cn + c) >= Lvalid) break;
+        V acc[PT];
+#pragma unroll
+        for (int tt = 0; tt < PT; ++tt) acc[tt] = czero<V>();
+        for (int rr = 0; rr < Dg; ++rr) {
+            const int r = r0 + rr;
+            V hv = h[(((int64_t)rr * B + b) * ma + i) * Cn + c];
+            if (r != 0) hv = cmulc(hv, __ldg(twNf + (int64_t)r * (i * cs + c * cc)));
+#pragma unroll
+            for (int tt = 0; tt < PT; ++tt) {
+                const int t = t0 + tt;
+                if (t < p) {
+                    if (r == 0 || t == 0) acc[tt] = cadd(acc[tt], hv);
+                    else acc[tt] = cfmac(hv, __ldg(twNf + (((int64_t)r * t) % q) * mq), acc[tt]);
+                }
+            }
+        }
+#pragma unroll
+        for (int tt = 0; tt < PT; ++tt) {
+            const int t = t0 + tt;
+            if (t >= p) break;
+            const int64_t lin = ((int64_t)t * ma + i) * Cn + c;
+            if (lin >= Lvalid) break;
+            V v = acc[tt];
+            if (!first) v = cadd(v, ob[lin]);
+            if (last) v = cscale(v, scale);
+            ob[lin] = v;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_unfold(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstride, int64_t Cn,
+                          int64_t ma, int64_t p, int64_t q, int64_t Nf, int64_t cs, int64_t cc,
+                          int64_t Lvalid, int64_t r0, int64_t D, int first, int last, double scale,
+                          cudaStream_t st)
+{
+    using V = cx<T>;
+    const int64_t Dg = (D < q - r0) ? D : (q - r0);
+    if (B <= 0 || Dg <= 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    const V* twNf = twiddles<T>(Nf, &e);
+    if (e != cudaSuccess) return e;
+    const int thr = 256;
+    const int64_t total = ma * Cn * B;
+    const int64_t blocks = (total + thr - 1) / thr;
+    k_unfold<V, 4><<<(unsigned)blocks, thr, 0, st>>>(out, h, B, bstride, Cn, ma, (int)p, (int)q, Nf,
+                                                     cs, cc, Lvalid, (int)r0, (int)Dg, first, last,
+                                                     (T)scale, twNf);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------ instantiations
+
+#define HDC_INST(T)                                                                                       \
+    template cudaError_t launch_residue_rows<T>(const cx<T>*, const cx<T>*, cx<T>*, int64_t, int64_t,   \
+                                                int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,   \
+                                                cudaStream_t);                                          \
+    template cudaError_t launch_fold_fft_cols<T>(const cx<T>*, const cx<T>*, cx<T>*, cx<T>*, int64_t,   \
+                                                 int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,  \
+                                                 int64_t, int64_t, int64_t, int64_t, int64_t, int,      \
+                                                 cudaStream_t);                                         \
+    template cudaError_t launch_ifft_cols<T>(cx<T>*, int64_t, int64_t, int64_t, int64_t, int64_t,      \
+                                             int64_t, int, cudaStream_t);                               \
+    template cudaError_t launch_unfold<T>(cx<T>*, const cx<T>*, int64_t, int64_t, int64_t, int64_t,     \
+                                          int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,         \
+                                          int64_t, int64_t, int, int, double, cudaStream_t);
+
+HDC_INST(double)
+HDC_INST(float)
+
+} // namespace hdc
