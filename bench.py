@@ -1,0 +1,396 @@
+"""Throughput of hybrid dealiased convolution on GB300.
+
+Workload (one step): the 1-D complex FP64 sweep L in {2^10 .. 2^22} and
+{3 * 2^9 .. 3 * 2^20} (25 sizes), M = 2L - 1, inputs uniform in the unit
+disk (seeded), each size convolved once with its tuned hybrid parameters
+(grid search of Section 4.2 run before the timed region).  The metric is
+conv outputs per second over the whole sweep; the explicit-padding path
+(m = nextgood(M), p = q = 1) and the FP32 path are timed the same way and
+reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank runs the same
+independent sweep (the convolutions shard with no exchange: weak scaling),
+the time is the max over ranks and value counts every rank's outputs.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "conv outputs/s & %roofline, tuned hybrid vs explicit, FP64 err≤1e-12"
+UNIT = "outputs/s"
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+# FP64 / FP32 vector FMA units per SM of GB300 (2 DFMA and 128 FFMA per clock),
+# 2 flops per FMA: peak = SMs x units x 2 x max SM clock.
+FP64_FMA_PER_CLK = 2
+FP32_FMA_PER_CLK = 128
+
+
+def sweep_sizes():
+    s = [1 << k for k in range(10, 23)] + [3 << k for k in range(9, 21)]
+    return sorted(s)
+
+
+def workload_name(dtype):
+    return (f"1-D complex {dtype} sweep L=2^10..2^22 and 3*2^9..3*2^20 (25 sizes), M=2L-1, "
+            "unit-disk inputs, tuned hybrid (m,p,q,D) per size")
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, throttle reasons) during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.th:
+            self.th.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ oracle (CPU)
+
+def cpu_baseline(sizes, budget_s=20.0, seed_base=0):
+    """The oracle's explicitly padded FFT convolution (O2) on the host cores,
+    over the sweep's sizes in increasing order until the time budget is used."""
+    import oracle
+    from paper_2306_10016_gb300 import synth
+    oracle.lib()
+    done, outs, t_tot = [], 0, 0.0
+    for i, L in enumerate(sizes):
+        f = synth.unit_disk(seed_base + 1 + i, (L,))
+        g = synth.unit_disk(seed_base + 1001 + i, (L,))
+        t0 = time.perf_counter()
+        oracle.conv_fft(f, g)
+        dt = time.perf_counter() - t0
+        t_tot += dt
+        outs += L
+        done.append(L)
+        if t_tot > budget_s:
+            break
+    return {"value": outs / t_tot, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"explicit zero-padded radix-2 FFT convolution (FP64, OpenMP) of the sweep sizes "
+                      f"{done[0]}..{done[-1]} ({len(done)} of {len(sizes)} sizes, each once), {t_tot:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle timed on the host cores, bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2306_10016_gb300 import synth
+    oracle.lib()
+    sizes = [L for L in sweep_sizes() if L <= (1 << 16)]
+    inputs = [(synth.unit_disk(1 + i, (L,)), synth.unit_disk(1001 + i, (L,))) for i, L in enumerate(sizes)]
+    for _ in range(max(0, args.warmup)):
+        for f, g in inputs[:3]:
+            oracle.conv_fft(f, g)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for f, g in inputs:
+            oracle.conv_fft(f, g)
+        ts.append(time.perf_counter() - t0)
+    outs = sum(sizes)
+    value = outs / (sum(ts) / len(ts))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(ts) / len(ts),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name("FP64"), "reference_sample": f"sizes {sizes[0]}..{sizes[-1]} "
+                   f"({len(sizes)} of 25) per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"explicit zero-padded radix-2 FFT convolution (FP64) of the sweep sizes "
+                                   f"{sizes[0]}..{sizes[-1]} per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hdc", choices=["hdc", "reference"])
+    ap.add_argument("--tuning-db", default=os.path.join(ROOT, "gpurun_out", "hdc_tuning.txt"))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sizes", default="", help="comma-separated L list (default: the full sweep)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import paper_2306_10016_gb300 as hdc
+    from paper_2306_10016_gb300 import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    hdc.build()
+    hdc.lib()
+
+    sizes = [int(x) for x in args.sizes.split(",")] if args.sizes else sweep_sizes()
+    os.makedirs(os.path.dirname(args.tuning_db), exist_ok=True)
+
+    def make_inputs(tdt):
+        ins = []
+        for i, L in enumerate(sizes):
+            f = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 10 + i, (L,))).to(dev, tdt)
+            g = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 1010 + i, (L,))).to(dev, tdt)
+            ins.append((f, g, torch.empty_like(f)))
+        return ins
+
+    def make_plans(dtype, mode):
+        plans = []
+        for L in sizes:
+            db = args.tuning_db if mode == hdc.HDC_TUNE_EXHAUSTIVE else None
+            plans.append(hdc.Plan([L], dtype=dtype, mode=mode, tuning_db=db))
+        return plans
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+
+    def time_sweep(plans, ins, steps, warmup, stats=False, nvtx=None):
+        wsb = max(p.workspace_bytes for p in plans)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        st = torch.cuda.current_stream(dev)
+        for _ in range(warmup):
+            for p, (f, g, h) in zip(plans, ins):
+                p.execute(f, g, out=h, workspace=ws, stream=st)
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        if stats:
+            hdc.stats_reset()
+            hdc.stats_timing(True)
+        n0 = hdc.total_launches()
+        if nvtx:
+            torch.cuda.nvtx.range_push(nvtx)
+        ev = []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for p, (f, g, h) in zip(plans, ins):
+                p.execute(f, g, out=h, workspace=ws, stream=st)
+            e1.record(st)
+            ev.append((e0, e1))
+        torch.cuda.synchronize(dev)
+        if nvtx:
+            torch.cuda.nvtx.range_pop()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        launches = hdc.total_launches() - n0
+        if stats:
+            hdc.stats_timing(False)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return sum(ms) / len(ms), launches, ms
+
+    # --- measured FMA peaks (context beside the unit-count peak)
+    fp64_probe = hdc.probe_fma_peak(hdc.HDC_C128, iters=1 << 14, device=dev)
+
+    # --- FP64 tuned hybrid (headline)
+    t_tune0 = time.perf_counter()
+    ins64 = make_inputs(torch.complex128)
+    plans64 = make_plans(hdc.HDC_C128, hdc.HDC_TUNE_EXHAUSTIVE)
+    tune_s = time.perf_counter() - t_tune0
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms64, launches, ms_list = time_sweep(plans64, ins64, args.steps, args.warmup, stats=True,
+                                         nvtx="hdc_fp64_timed")
+    clocks = sampler.stop()
+    kstats = hdc.stats()
+
+    # max over ranks
+    def rank_max(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms64 = rank_max(ms64)
+    outs = sum(sizes)
+    value = world * outs / (ms64 * 1e-3)
+
+    # --- explicit padding, FP64
+    plans_ex = make_plans(hdc.HDC_C128, hdc.HDC_EXPLICIT)
+    ms_ex, _, _ = time_sweep(plans_ex, ins64, args.steps, args.warmup)
+    ms_ex = rank_max(ms_ex)
+
+    # --- per-size hybrid vs explicit (device time, FP64)
+    per_size = []
+    for L, pt, pe, (f, g, h) in zip(sizes, plans64, plans_ex, ins64):
+        t_h, _, _ = time_sweep([pt], [(f, g, h)], 3, 1)
+        t_e, _, _ = time_sweep([pe], [(f, g, h)], 3, 1)
+        prm = pt.params[0]
+        per_size.append({"L": L, "m": prm["m"], "p": prm["p"], "q": prm["q"], "D": prm["D"],
+                         "hybrid_ms": round(t_h, 5), "explicit_ms": round(t_e, 5)})
+    del ins64
+
+    # --- FP32 tuned hybrid
+    ins32 = make_inputs(torch.complex64)
+    plans32 = make_plans(hdc.HDC_C64, hdc.HDC_TUNE_EXHAUSTIVE)
+    ms32, _, _ = time_sweep(plans32, ins32, args.steps, args.warmup)
+    ms32 = rank_max(ms32)
+    del ins32
+
+    # --- end to end through the host-buffer C call (FP64)
+    pinned = []
+    for i, L in enumerate(sizes):
+        f = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 10 + i, (L,))).pin_memory()
+        g = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 1010 + i, (L,))).pin_memory()
+        pinned.append((f, g, torch.empty_like(f).pin_memory()))
+    wsh = max(hdc.workspace_size_host([L], [2 * L - 1], [p.params[0]["m"]], D=[p.params[0]["D"]])
+              for L, p in zip(sizes, plans64))
+    wsh_t = torch.empty(wsh, dtype=torch.uint8, device=dev)
+
+    def e2e_step():
+        for L, p, (f, g, h) in zip(sizes, plans64, pinned):
+            prm = p.params[0]
+            hdc.convnd_host(f, g, h, 1, prm["m"], p=prm["p"], q=prm["q"], D=prm["D"], workspace=wsh_t)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e2e_s = rank_max((time.perf_counter() - t0) / args.steps)
+    h2d = sum(2 * L * 16 for L in sizes)
+    d2h = sum(L * 16 for L in sizes)
+
+    # --- roofline of the dominant kernel (FP64 ALU bound)
+    dom = max((k for k in kstats if kstats[k]["ms"] > 0), key=lambda k: kstats[k]["ms"])
+    d = kstats[dom]
+    per_launch_flops = d["flops"] / max(1, d["launches"])
+    avg_ms = d["ms"] / max(1, d["launches"])
+    achieved = per_launch_flops / (avg_ms * 1e-3) / 1e12
+    peak = SM_COUNT * FP64_FMA_PER_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    total_ms = sum(v["ms"] for v in kstats.values())
+    roofline = {
+        "bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+        "frac": round(achieved / peak, 4), "traffic": None, "kernel": dom,
+        "peak_basis": "152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz (unit counts and max clock)",
+        "peak_measured_fma_probe": round(fp64_probe, 4),
+        "share_of_step": round(d["ms"] / total_ms, 4) if total_ms > 0 else None,
+        "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                        "model_tflops": round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 4) if v["ms"] > 0 else None}
+                    for k, v in kstats.items() if v["launches"]},
+        "whole_step_frac": None,
+    }
+    # whole-step roofline: model flops of the sweep at its tuned tuples / time
+    step_flops = sum(pt.params[0]["q"] * (15 * pt.params[0]["m"] * math.log2(pt.params[0]["m"])
+                                         + 6 * pt.params[0]["m"] + 24 * L) + 2 * L
+                     for L, pt in zip(sizes, plans64))
+    roofline["whole_step_frac"] = round(step_flops / (ms64 * 1e-3) / (peak * 1e12), 4)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(sizes)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name("FP64"), "sizes": len(sizes), "outputs_per_step": outs,
+                   "l2": "flushed between timed steps (256 MiB write)", "tuning": "grid search (Section 4.2), "
+                   "candidates within 1.5x of the least model flops, m >= 16", "tuning_s": round(tune_s, 1),
+                   "parallelism": f"replicas x{world}"},
+        "explicit": {"value": world * outs / (ms_ex * 1e-3), "ms_per_step": ms_ex,
+                     "hybrid_speedup": round(ms_ex / ms64, 4)},
+        "fp32": {"value": world * outs / (ms32 * 1e-3), "ms_per_step": ms32},
+        "per_size_fp64": per_size,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * outs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "step_ms": [round(x, 4) for x in ms_list],
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -73,6 +73,25 @@ typedef enum hdc_dtype {
     HDC_C128 = 1   /* complex<double> */
 } hdc_dtype;
 
+/* How a plan chooses (m, p, q, D) per axis. */
+typedef enum hdc_mode {
+    HDC_FIXED = 0,            /* the caller's m (and D) per axis                    */
+    HDC_TUNE_EXHAUSTIVE = 1,  /* grid search on the device (Section 4.2), cached     */
+    HDC_PREDICT_MLP = 2,      /* learned predictor of the parameters                 */
+    HDC_EXPLICIT = 3,         /* explicit padding m = nextgood(M), p = q = 1 (3.1)   */
+    HDC_TUNE_CACHED_ONLY = 4  /* tuning database only; HDC_ERR_NOT_TUNED if absent   */
+} hdc_mode;
+
+/* One parameter choice of one axis and its measured time. */
+typedef struct hdc_tuple {
+    int64_t m, p, q, D;
+    double model_flops;  /* F1 = q (15 m log2 m + 6 m + 24 L) + 2 L of the axis   */
+    double ms;           /* median device time of the whole convolution, or -1    */
+} hdc_tuple;
+
+/* Opaque, library-owned plan (host memory only). */
+typedef struct hdc_plan hdc_plan;
+
 /* ------------------------------------------------------------ host helpers
  * No GPU needed. */
 
@@ -147,9 +166,93 @@ int hdc_convnd(int dims, const void* f, const void* g, void* h,
                int inplace, int dtype, int64_t batch, void* workspace,
                size_t ws_bytes, void* stream);
 
+/* The same convolution on HOST buffers f, g, h (pinned for asynchronous
+ * copies; pageable works but serialises): copies f and g into the device
+ * workspace, convolves there and copies the result back into h, all on
+ * `stream`; synchronise the stream before reading h.  The device workspace
+ * holds both device copies, the result and the convolution workspace: size
+ * it with hdc_workspace_size_host().  inplace is not accepted here. */
+int hdc_workspace_size_host(int dims, const int64_t* L, const int64_t* M,
+                            const int64_t* m, const int64_t* p, const int64_t* q,
+                            const int64_t* D, int dtype, int64_t batch,
+                            size_t* bytes);
+int hdc_convnd_host(int dims, const void* f_host, const void* g_host,
+                    void* h_host, const int64_t* L, const int64_t* M,
+                    const int64_t* m, const int64_t* p, const int64_t* q,
+                    const int64_t* D, int dtype, int64_t batch,
+                    void* dev_workspace, size_t ws_bytes, void* stream);
+
 /* Free the cached twiddle tables on every device (call with no work in
  * flight that uses them). */
 int hdc_release_caches(void);
+
+/* ----------------------------------------------------- parameter search
+ * Section 4.2 (A0 grid search, separable per axis).  Candidates of an axis:
+ * for every q, the m = 2^a 3^b 5^c 7^d >= m_min that pad M least (the three
+ * smallest >= ceil(M/q), the next power of two, the next 3 * 2^k), p and q
+ * derived, D = q; kept when the model flops F1 are within max_ratio (>= 1)
+ * of the axis minimum; sorted by F1.  Writes up to `cap` entries, the full
+ * count to *n. */
+int hdc_tune_candidates(int64_t L, int64_t M, int dtype, double max_ratio,
+                        int64_t m_min, hdc_tuple* out, int64_t cap, int64_t* n);
+
+/* Largest workspace any candidate combination of the search needs. */
+int hdc_tune_workspace_size(int dims, const int64_t* L, const int64_t* M,
+                            int dtype, int64_t batch, double max_ratio,
+                            int64_t m_min, size_t* bytes);
+
+/* Time candidates on the caller's device buffers (f, g, h: batch x L;
+ * workspace of hdc_tune_workspace_size) with `warmup` untimed and `reps`
+ * timed runs each (median, CUDA events on `stream`; synchronises).  Axes are
+ * searched one at a time, last axis first, the others held at their best so
+ * far; the three fastest m of each axis are re-timed with D = 1, 2, 4, ... < q.
+ * best[dims] receives the choice; trials (optional, cap records of dims
+ * tuples each) every timed configuration, *ntrials their count. */
+int hdc_tune_convnd(int dims, const int64_t* L, const int64_t* M, int dtype,
+                    int64_t batch, const void* f, const void* g, void* h,
+                    void* workspace, size_t ws_bytes, int warmup, int reps,
+                    double max_ratio, int64_t m_min, void* stream,
+                    hdc_tuple* best, hdc_tuple* trials, int64_t cap,
+                    int64_t* ntrials);
+int hdc_tune_conv1d(int64_t L, int64_t M, int dtype, int64_t batch,
+                    const void* f, const void* g, void* h, void* workspace,
+                    size_t ws_bytes, int warmup, int reps, double max_ratio,
+                    int64_t m_min, void* stream, hdc_tuple* best,
+                    hdc_tuple* trials, int64_t cap, int64_t* ntrials);
+
+/* ---------------------------------------------------------------- plans
+ * A plan fixes (m, p, q, D) per axis for one (dims, L, M, dtype, batch).
+ * HDC_TUNE_EXHAUSTIVE looks the problem up in the text database at
+ * `tuning_db` (may be NULL) and otherwise runs hdc_tune_convnd on scratch
+ * buffers it allocates and frees itself (the one place besides twiddle
+ * tables where the library allocates), then appends the result to the
+ * database.  HDC_FIXED takes m (and D, may be NULL) from the caller. */
+int hdc_plan_create(hdc_plan** plan, int dims, const int64_t* L,
+                    const int64_t* M, const int64_t* m, const int64_t* D,
+                    int dtype, int64_t batch, int mode, const char* tuning_db,
+                    void* stream);
+/* Per-axis parameters of the plan (arrays of length dims; NULL skips). */
+int hdc_plan_params(const hdc_plan* plan, int64_t* m, int64_t* p, int64_t* q,
+                    int64_t* D);
+/* Device workspace bytes hdc_plan_execute needs (in-place included). */
+size_t hdc_plan_workspace(const hdc_plan* plan);
+int hdc_plan_execute(const hdc_plan* plan, const void* f, const void* g,
+                     void* h, void* workspace, size_t ws_bytes, void* stream);
+int hdc_plan_destroy(hdc_plan* plan);
+
+/* ------------------------------------------------------ launch statistics
+ * Counting of every kernel launch (always on) and, when enabled, CUDA events
+ * recorded on the launch stream around each launch.  Read after the work
+ * has completed (synchronise first). */
+int hdc_stats_reset(void);
+int hdc_stats_timing(int on);
+int hdc_stats_kernel_count(void);
+const char* hdc_stats_kernel_name(int id);
+int64_t hdc_stats_total_launches(void);
+/* launches, summed event time (ms), model flops and algorithmic bytes of
+ * kernel `id` since the last reset. */
+int hdc_stats_get(int id, int64_t* launches, double* ms, double* flops,
+                  double* bytes);
 
 /* ------------------------------------------------------------ measurement
  * Vector FMA throughput probe: the arithmetic roofline of this path (it runs

@@ -23,6 +23,12 @@ from . import build_ext as _build_ext
 HDC_C64 = 0
 HDC_C128 = 1
 
+HDC_FIXED = 0
+HDC_TUNE_EXHAUSTIVE = 1
+HDC_PREDICT_MLP = 2
+HDC_EXPLICIT = 3
+HDC_TUNE_CACHED_ONLY = 4
+
 HDC_OK = 0
 HDC_ERR_PARAM = -1
 HDC_ERR_ALIAS = -2
@@ -64,6 +70,45 @@ _SIGS = [
                              C.c_int, _i64, _vp, _sz, _vp]),
     ("hdc_release_caches", C.c_int, []),
     ("hdc_probe_fma", C.c_int, [C.c_int, _i64, C.c_int, C.c_int, _vp, _vp, C.POINTER(C.c_double)]),
+]
+
+
+
+class Tuple(C.Structure):
+    """hdc_tuple: one axis' (m, p, q, D), its model flops and measured ms."""
+    _fields_ = [("m", C.c_int64), ("p", C.c_int64), ("q", C.c_int64), ("D", C.c_int64),
+                ("model_flops", C.c_double), ("ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_tp = C.POINTER(Tuple)
+_SIGS += [
+    ("hdc_workspace_size_host", C.c_int, [C.c_int, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, C.c_int, _i64,
+                                          C.POINTER(_sz)]),
+    ("hdc_convnd_host", C.c_int, [C.c_int, _vp, _vp, _vp, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, C.c_int,
+                                  _i64, _vp, _sz, _vp]),
+    ("hdc_tune_candidates", C.c_int, [_i64, _i64, C.c_int, C.c_double, _i64, _tp, _i64, _i64p]),
+    ("hdc_tune_workspace_size", C.c_int, [C.c_int, _i64p, _i64p, C.c_int, _i64, C.c_double, _i64,
+                                          C.POINTER(_sz)]),
+    ("hdc_tune_convnd", C.c_int, [C.c_int, _i64p, _i64p, C.c_int, _i64, _vp, _vp, _vp, _vp, _sz, C.c_int, C.c_int,
+                                  C.c_double, _i64, _vp, _tp, _tp, _i64, _i64p]),
+    ("hdc_tune_conv1d", C.c_int, [_i64, _i64, C.c_int, _i64, _vp, _vp, _vp, _vp, _sz, C.c_int, C.c_int, C.c_double,
+                                  _i64, _vp, _tp, _tp, _i64, _i64p]),
+    ("hdc_plan_create", C.c_int, [C.POINTER(_vp), C.c_int, _i64p, _i64p, _i64p, _i64p, C.c_int, _i64, C.c_int,
+                                  C.c_char_p, _vp]),
+    ("hdc_plan_params", C.c_int, [_vp, _i64p, _i64p, _i64p, _i64p]),
+    ("hdc_plan_workspace", _sz, [_vp]),
+    ("hdc_plan_execute", C.c_int, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    ("hdc_plan_destroy", C.c_int, [_vp]),
+    ("hdc_stats_reset", C.c_int, []),
+    ("hdc_stats_timing", C.c_int, [C.c_int]),
+    ("hdc_stats_kernel_count", C.c_int, []),
+    ("hdc_stats_kernel_name", C.c_char_p, [C.c_int]),
+    ("hdc_stats_total_launches", _i64, []),
+    ("hdc_stats_get", C.c_int, [C.c_int, _i64p, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                C.POINTER(C.c_double)]),
 ]
 
 _lib = None
@@ -261,6 +306,155 @@ def probe_fma_peak(dtype=HDC_C128, iters=1 << 16, blocks=None, threads=256, reps
             if i:
                 best = max(best, fl.value / (e0.elapsed_time(e1) * 1e-3) / 1e12)
     return best
+
+
+# ------------------------------------------------------------- host buffers
+
+def workspace_size_host(L, M, m, p=0, q=0, D=0, dtype=HDC_C128, batch=1) -> int:
+    dims = len(L)
+    M, m, p, q, D = (_per_axis(v, dims, n) for v, n in ((M, "M"), (m, "m"), (p, "p"), (q, "q"), (D, "D")))
+    nb = C.c_size_t()
+    _check(lib().hdc_workspace_size_host(dims, _arr(L), _arr(M), _arr(m), _arr(p), _arr(q), _arr(D), dtype,
+                                         int(batch), C.byref(nb)), "workspace_size_host")
+    return nb.value
+
+
+def convnd_host(f, g, h, dims, m, M=None, p=0, q=0, D=0, workspace=None, stream=None):
+    """The convolution on host tensors f, g -> h (CPU torch tensors, pinned
+    for overlap); copies in, convolution and copy out all run through one C
+    call on the device.  Synchronises the stream before returning."""
+    torch = _torch()
+    for t in (f, g, h):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("convnd_host takes contiguous host tensors")
+    dt = dtype_code(f.dtype)
+    L = [int(x) for x in f.shape[f.dim() - dims:]]
+    batch = 1
+    for x in f.shape[: f.dim() - dims]:
+        batch *= int(x)
+    Mv = _per_axis(M, dims, "M") or [2 * l - 1 for l in L]
+    args = [_per_axis(v, dims, n) for v, n in ((m, "m"), (p, "p"), (q, "q"), (D, "D"))]
+    nbytes = workspace_size_host(L, Mv, *args, dtype=dt, batch=batch)
+    if workspace is None or workspace.numel() * workspace.element_size() < nbytes:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    st = stream if stream is not None else torch.cuda.current_stream(workspace.device)
+    _check(lib().hdc_convnd_host(dims, f.data_ptr(), g.data_ptr(), h.data_ptr(), _arr(L), _arr(Mv),
+                                 *[_arr(a) for a in args], dt, batch, workspace.data_ptr(),
+                                 workspace.numel() * workspace.element_size(), st.cuda_stream), "convnd_host")
+    st.synchronize()
+    return h
+
+
+# -------------------------------------------------------- parameter search
+
+def tune_candidates(L: int, M: int, dtype=HDC_C128, max_ratio=2.0, m_min=16):
+    n = C.c_int64()
+    _check(lib().hdc_tune_candidates(L, M, dtype, max_ratio, m_min, None, 0, C.byref(n)), "tune_candidates")
+    buf = (Tuple * max(1, n.value))()
+    _check(lib().hdc_tune_candidates(L, M, dtype, max_ratio, m_min, buf, n.value, C.byref(n)), "tune_candidates")
+    return [buf[i].as_dict() for i in range(n.value)]
+
+
+def tune(f, g, dims, M=None, max_ratio=2.0, m_min=16, warmup=1, reps=3, out=None, stream=None):
+    """Grid search (Section 4.2) on the given device tensors; returns
+    (best per axis, trials) where trials is a list of per-axis dict lists."""
+    torch = _torch()
+    dt = dtype_code(f.dtype)
+    L = [int(x) for x in f.shape[f.dim() - dims:]]
+    batch = 1
+    for x in f.shape[: f.dim() - dims]:
+        batch *= int(x)
+    Mv = _per_axis(M, dims, "M") or [2 * l - 1 for l in L]
+    nb = C.c_size_t()
+    _check(lib().hdc_tune_workspace_size(dims, _arr(L), _arr(Mv), dt, batch, max_ratio, m_min, C.byref(nb)),
+           "tune_workspace_size")
+    ws = torch.empty(max(1, nb.value), dtype=torch.uint8, device=f.device)
+    h = out if out is not None else torch.empty_like(f)
+    cap = 4096
+    best = (Tuple * dims)()
+    trials = (Tuple * (cap * dims))()
+    nt = C.c_int64()
+    st = stream if stream is not None else torch.cuda.current_stream(f.device)
+    with torch.cuda.device(f.device):
+        _check(lib().hdc_tune_convnd(dims, _arr(L), _arr(Mv), dt, batch, f.data_ptr(), g.data_ptr(), h.data_ptr(),
+                                     ws.data_ptr(), nb.value, warmup, reps, max_ratio, m_min, st.cuda_stream, best,
+                                     trials, cap, C.byref(nt)), "tune_convnd")
+    tr = [[trials[i * dims + a].as_dict() for a in range(dims)] for i in range(min(nt.value, cap))]
+    return [best[a].as_dict() for a in range(dims)], tr
+
+
+class Plan:
+    """(m, p, q, D) per axis fixed for one problem shape (hdc_plan_*)."""
+
+    def __init__(self, L, M=None, dtype=HDC_C128, batch=1, mode=HDC_TUNE_EXHAUSTIVE, m=None, D=None,
+                 tuning_db=None, stream=None):
+        torch = _torch()
+        self.L = [int(x) for x in L]
+        self.dims = len(self.L)
+        self.M = _per_axis(M, self.dims, "M") or [2 * l - 1 for l in self.L]
+        self.dtype = dtype
+        self.batch = int(batch)
+        h = C.c_void_p()
+        st = stream if stream is not None else torch.cuda.current_stream()
+        mm = _arr(_per_axis(m, self.dims, "m")) if m is not None else None
+        DD = _arr(_per_axis(D, self.dims, "D")) if D is not None else None
+        db = tuning_db.encode() if tuning_db else None
+        _check(lib().hdc_plan_create(C.byref(h), self.dims, _arr(self.L), _arr(self.M), mm, DD, dtype, self.batch,
+                                     mode, db, st.cuda_stream), "plan_create")
+        self._h = h
+
+    @property
+    def params(self):
+        arrs = [(C.c_int64 * self.dims)() for _ in range(4)]
+        _check(lib().hdc_plan_params(self._h, *arrs), "plan_params")
+        return [dict(m=arrs[0][i], p=arrs[1][i], q=arrs[2][i], D=arrs[3][i]) for i in range(self.dims)]
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(lib().hdc_plan_workspace(self._h))
+
+    def execute(self, f, g, out=None, workspace=None, stream=None):
+        torch = _torch()
+        h = out if out is not None else torch.empty_like(f)
+        nbytes = self.workspace_bytes
+        if workspace is None or workspace.numel() * workspace.element_size() < nbytes:
+            workspace = torch.empty(nbytes, dtype=torch.uint8, device=f.device)
+        st = stream if stream is not None else torch.cuda.current_stream(f.device)
+        _check(lib().hdc_plan_execute(self._h, f.data_ptr(), g.data_ptr(), h.data_ptr(), workspace.data_ptr(),
+                                      workspace.numel() * workspace.element_size(), st.cuda_stream), "plan_execute")
+        return h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.hdc_plan_destroy(self._h)
+            self._h = None
+
+
+# ------------------------------------------------------- launch statistics
+
+def stats_reset() -> None:
+    lib().hdc_stats_reset()
+
+
+def stats_timing(on: bool) -> None:
+    lib().hdc_stats_timing(int(bool(on)))
+
+
+def total_launches() -> int:
+    return int(lib().hdc_stats_total_launches())
+
+
+def stats() -> dict:
+    """{kernel: {launches, ms, flops, bytes}} since the last reset (read
+    after synchronising)."""
+    out = {}
+    for k in range(lib().hdc_stats_kernel_count()):
+        n = C.c_int64()
+        ms, fl, by = C.c_double(), C.c_double(), C.c_double()
+        _check(lib().hdc_stats_get(k, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by)), "stats_get")
+        out[lib().hdc_stats_kernel_name(k).decode()] = dict(launches=n.value, ms=ms.value, flops=fl.value,
+                                                             bytes=by.value)
+    return out
 
 
 def release_caches() -> None:

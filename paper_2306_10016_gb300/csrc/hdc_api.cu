@@ -393,6 +393,56 @@ HDC_EXPORT int hdc_conv3d(const void* f, const void* g, void* h, const int64_t L
     return hdc_convnd(3, f, g, h, L, M, m, p, q, D, inplace, dtype, batch, workspace, ws_bytes_given, stream);
 }
 
+HDC_EXPORT int hdc_workspace_size_host(int dims, const int64_t* L, const int64_t* M, const int64_t* m,
+                                       const int64_t* p, const int64_t* q, const int64_t* D, int dtype,
+                                       int64_t batch, size_t* bytes)
+{
+    if (!bytes || batch < 0) return HDC_ERR_PARAM;
+    Axis ax[HDC_MAX_DIMS];
+    int rc = resolve_all(dims, L, M, m, p, q, D, dtype, ax);
+    if (rc != HDC_OK) return rc;
+    const size_t esz = dtype == HDC_C128 ? 16 : 8;
+    int64_t tot = batch;
+    for (int i = 0; i < dims; ++i) tot *= ax[i].L;
+    *bytes = 3 * align_up((size_t)tot * esz) + ws_bytes(dims, ax, batch, esz, 0) + 256;
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_convnd_host(int dims, const void* f_host, const void* g_host, void* h_host, const int64_t* L,
+                               const int64_t* M, const int64_t* m, const int64_t* p, const int64_t* q,
+                               const int64_t* D, int dtype, int64_t batch, void* dev_ws, size_t ws_bytes_given,
+                               void* stream)
+{
+    Axis ax[HDC_MAX_DIMS];
+    int rc = resolve_all(dims, L, M, m, p, q, D, dtype, ax);
+    if (rc != HDC_OK) return rc;
+    if (batch < 0) return HDC_ERR_PARAM;
+    if (batch == 0) return HDC_OK;
+    if (!f_host || !g_host || !h_host) return HDC_ERR_PARAM;
+    size_t need = 0;
+    rc = hdc_workspace_size_host(dims, L, M, m, p, q, D, dtype, batch, &need);
+    if (rc != HDC_OK) return rc;
+    if (!dev_ws || ws_bytes_given < need) return HDC_ERR_WORKSPACE;
+    const size_t esz = dtype == HDC_C128 ? 16 : 8;
+    int64_t tot = batch;
+    for (int i = 0; i < dims; ++i) tot *= ax[i].L;
+    const size_t arr = (size_t)tot * esz;
+    uintptr_t base = ((uintptr_t)dev_ws + 255) & ~(uintptr_t)255;
+    void* df = (void*)base;
+    void* dg = (void*)(base + align_up(arr));
+    void* dh = (void*)(base + 2 * align_up(arr));
+    void* w = (void*)(base + 3 * align_up(arr));
+    const size_t wbytes = ws_bytes_given - (size_t)((uintptr_t)w - (uintptr_t)dev_ws);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(df, f_host, arr, cudaMemcpyHostToDevice, st) != cudaSuccess) return HDC_ERR_CUDA;
+    if (cudaMemcpyAsync(dg, g_host, arr, cudaMemcpyHostToDevice, st) != cudaSuccess) return HDC_ERR_CUDA;
+    rc = dtype == HDC_C128 ? conv_nd<double>(dims, df, dg, dh, ax, 0, batch, w, wbytes, st)
+                           : conv_nd<float>(dims, df, dg, dh, ax, 0, batch, w, wbytes, st);
+    if (rc != HDC_OK) return rc;
+    if (cudaMemcpyAsync(h_host, dh, arr, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HDC_ERR_CUDA;
+    return HDC_OK;
+}
+
 HDC_EXPORT int hdc_release_caches(void)
 {
     std::lock_guard<std::mutex> lk(g_tw_mu);

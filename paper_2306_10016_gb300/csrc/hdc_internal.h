@@ -25,6 +25,24 @@ template <typename T> constexpr int64_t max_col_fft() { return col_tile_elems<T>
 
 FftPlan make_fft_plan(int64_t n);
 
+// ------------------------------------------------------ launch statistics
+// Every launcher counts its launches and the model flops / algorithmic
+// bytes of the launch; when timing is on it also brackets the launch with
+// CUDA events on its stream.
+
+enum KernelId { K_TWIDDLE = 0, K_RESIDUE_ROWS, K_FOLD_FFT_COLS, K_IFFT_COLS, K_UNFOLD, K_BATCHED, K_COUNT };
+
+struct LaunchScope {
+    int kid;
+    cudaStream_t st;
+    cudaEvent_t e0;
+    LaunchScope(int kid, cudaStream_t st, double flops, double bytes);
+    ~LaunchScope();
+};
+
+// 5 n log2(n): the flop count convention of one n-point complex FFT.
+double fft_flops(double n);
+
 // Twiddle table zeta_n^k, k < n, of dtype T on the current device (cached).
 template <typename T> const cx<T>* twiddles(int64_t n, cudaError_t* err);
 

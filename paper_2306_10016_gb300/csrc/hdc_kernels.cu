@@ -38,6 +38,7 @@ cudaError_t launch_twiddle(cx<T>* tw, int64_t n, cudaStream_t st)
 {
     const int thr = 256;
     const int64_t blocks = (n + thr - 1) / thr;
+    LaunchScope ls(K_TWIDDLE, st, 0.0, (double)n * sizeof(cx<T>));
     k_twiddle<cx<T>><<<(unsigned)blocks, thr, 0, st>>>(tw, n);
     return cudaGetLastError();
 }
@@ -134,6 +135,12 @@ cudaError_t launch_residue_rows(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_
     auto kern = k_residue_rows<V>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     const int64_t blocks = B * Dg;
+    // model: 3 FFTs + product per residue, and the fold of f and g (8 flops
+    // per element each) unless the fold is a plain copy (p = q = 1)
+    const double Lrow = (double)((L < p * m) ? L : p * m);
+    const double fold = (p == 1 && q == 1) ? 0.0 : 16.0 * Lrow;
+    LaunchScope ls(K_RESIDUE_ROWS, st, (double)(B * Dg) * (3.0 * fft_flops((double)m) + 6.0 * m + fold),
+                   (2.0 * B * Lrow + (double)(Dg * B * m)) * sizeof(V));
     kern<<<(unsigned)blocks, thr, smem, st>>>(f, g, h, B, ld_in, L, (int)m, (int)p, (int)q, (int)r0,
                                               (int)Dg, twN, twm, fp);
     return cudaGetLastError();
@@ -223,6 +230,9 @@ cudaError_t launch_fold_fft_cols(const cx<T>* f, const cx<T>* g, cx<T>* yf, cx<T
     auto kern = k_fold_fft_cols<V>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     const int64_t blocks = (int64_t)nct * Dg * 2 * B;
+    LaunchScope ls(K_FOLD_FFT_COLS, st,
+                   2.0 * Dg * B * (8.0 * Lvalid + (double)Cn * fft_flops((double)ma)),
+                   (2.0 * B * Lvalid + 2.0 * Dg * B * ma * Cn) * sizeof(V));
     kern<<<(unsigned)blocks, thr, smem, st>>>(f, g, yf, yg, B, bstride, Cn, (int)ma, (int)p, (int)q,
                                               Nf, cs, cc, Lvalid, (int)r0, (int)Dg, C, nct, post,
                                               twNf, twma, fp);
@@ -283,6 +293,8 @@ cudaError_t launch_ifft_cols(cx<T>* y, int64_t B, int64_t Cn, int64_t ma, int64_
     auto kern = k_ifft_cols<V>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     const int64_t blocks = (int64_t)nct * D * B;
+    LaunchScope ls(K_IFFT_COLS, st, (double)(D * B) * (double)Cn * fft_flops((double)ma),
+                   2.0 * D * B * ma * Cn * sizeof(V));
     kern<<<(unsigned)blocks, thr, smem, st>>>(y, B, Cn, (int)ma, (int)q, Nf, (int)D, C, nct, pre, twNf,
                                               twma, fp);
     return cudaGetLastError();
@@ -351,6 +363,8 @@ cudaError_t launch_unfold(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstride
     const int thr = 256;
     const int64_t total = ma * Cn * B;
     const int64_t blocks = (total + thr - 1) / thr;
+    LaunchScope ls(K_UNFOLD, st, (double)(Dg * B) * 8.0 * Lvalid + (last ? 2.0 * B * Lvalid : 0.0),
+                   ((double)(Dg * B * ma * Cn) + (first ? 1.0 : 2.0) * B * Lvalid) * sizeof(V));
     k_unfold<V, 4><<<(unsigned)blocks, thr, 0, st>>>(out, h, B, bstride, Cn, ma, (int)p, (int)q, Nf,
                                                      cs, cc, Lvalid, (int)r0, (int)Dg, first, last,
                                                      (T)scale, twNf);

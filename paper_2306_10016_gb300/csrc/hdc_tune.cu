@@ -1,0 +1,444 @@
+// hdc_tune.cu -- parameter search and plans.
+//
+// The exhaustive tuner is the grid search of Section 4.2 (A0): enumerate the
+// valid (m, p, q, D) of an axis, time each candidate on the device, keep the
+// fastest.  For N dimensions it uses the separability argument of the same
+// section: each axis is searched with the other axes held at their current
+// best, one axis after the other, so the cost is the sum and not the product
+// of the per-axis candidate counts.  The timing score is the whole
+// convolution (Section 4.3 times only the forward routine; a GPU launch
+// sequence has no separable forward cost worth scoring on its own).
+//
+// Candidates of an axis: for each q, the m of the form 2^a 3^b 5^c 7^d that
+// pad M least (the three smallest >= ceil(M/q), the next power of two and the
+// next 3 * 2^k), with p = ceil(L/m), q = ceil(M/m), D = q; kept when their
+// model flops F1 = q (15 m log2 m + 6 m + 24 L) + 2 L are within max_ratio of
+// the smallest F1 of the axis (m >= m_min).  The fastest few m are then
+// re-timed with D in {1, 2, 4, ...} below q.
+//
+// Plans remember the chosen parameters; a text tuning database keyed by
+// (device, dtype, batch, dims, L, M) caches search results across runs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "hdc.h"
+#include "hdc_internal.h"
+
+#define HDC_EXPORT extern "C" __attribute__((visibility("default")))
+
+namespace {
+
+double model_flops_axis(int64_t L, int64_t m, int64_t q)
+{
+    const double md = (double)m;
+    const double lg = m > 1 ? std::log2(md) : 0.0;
+    return (double)q * (15.0 * md * lg + 6.0 * md + 24.0 * (double)L) + 2.0 * (double)L;
+}
+
+int64_t next_pow2_times(int64_t n, int64_t base)
+{
+    int64_t v = base;
+    while (v < n) v *= 2;
+    return v;
+}
+
+// For every q, the m that pad M least: the three smallest good sizes
+// >= ceil(M/q), the next power of two and the next 3 * 2^k (sizes whose FFTs
+// use the largest radices).  q grows until even the fold/unfold term
+// 24 q L alone exceeds max_ratio times the best model flops seen.
+std::vector<hdc_tuple> candidates(int64_t L, int64_t M, int dtype, double max_ratio, int64_t m_min)
+{
+    std::vector<hdc_tuple> out;
+    if (m_min < 1) m_min = 1;
+    double best = 1e300;
+    std::vector<int64_t> ms;
+    for (int64_t q = 1;; ++q) {
+        const int64_t lo = (M + q - 1) / q;
+        if (lo < m_min && q > 1) break;
+        if (24.0 * (double)q * (double)L > max_ratio * best) break;
+        int64_t m = lo;
+        for (int k = 0; k < 3; ++k) {
+            m = hdc_next_good_size(m);
+            if (m < 1) break;
+            ms.push_back(m);
+            best = std::min(best, model_flops_axis(L, m, (M + m - 1) / m));
+            ++m;
+        }
+        ms.push_back(next_pow2_times(lo, 1));
+        ms.push_back(next_pow2_times(lo, 3));
+    }
+    std::sort(ms.begin(), ms.end());
+    ms.erase(std::unique(ms.begin(), ms.end()), ms.end());
+    for (int64_t m : ms) {
+        if (m < m_min) continue;
+        int64_t p = 0, q = 0, D = 0;
+        if (hdc_validate_axis(L, M, m, 0, 0, 0, dtype, &p, &q, &D) != HDC_OK) continue;
+        hdc_tuple t;
+        t.m = m; t.p = p; t.q = q; t.D = q;
+        t.model_flops = model_flops_axis(L, m, q);
+        t.ms = -1.0;
+        out.push_back(t);
+    }
+    if (out.empty()) return out;
+    best = out[0].model_flops;
+    for (auto& t : out) best = std::min(best, t.model_flops);
+    std::vector<hdc_tuple> kept;
+    for (auto& t : out)
+        if (t.model_flops <= max_ratio * best) kept.push_back(t);
+    std::sort(kept.begin(), kept.end(),
+              [](const hdc_tuple& a, const hdc_tuple& b) { return a.model_flops < b.model_flops; });
+    return kept;
+}
+
+std::string device_key()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp pr;
+    if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) return "unknown";
+    std::string s = pr.name;
+    for (auto& c : s)
+        if (c == ' ') c = '_';
+    return s;
+}
+
+std::mutex g_db_mu;
+
+std::string db_key(int dims, const int64_t* L, const int64_t* M, int dtype, int64_t batch)
+{
+    std::string k = "v1 " + device_key() + " " + std::to_string(dtype) + " " + std::to_string(batch) + " " +
+                    std::to_string(dims);
+    for (int i = 0; i < dims; ++i) k += " " + std::to_string(L[i]);
+    for (int i = 0; i < dims; ++i) k += " " + std::to_string(M[i]);
+    return k;
+}
+
+bool db_lookup(const char* path, const std::string& key, int dims, hdc_tuple* best)
+{
+    if (!path || !*path) return false;
+    std::lock_guard<std::mutex> lk(g_db_mu);
+    FILE* fp = fopen(path, "r");
+    if (!fp) return false;
+    char line[4096];
+    bool found = false;
+    while (fgets(line, sizeof line, fp)) {
+        char* bar = strchr(line, '|');
+        if (!bar) continue;
+        std::string k(line, bar - line);
+        while (!k.empty() && k.back() == ' ') k.pop_back();
+        if (k != key) continue;
+        // record: per axis "m p q D", then the time
+        const char* s = bar + 1;
+        hdc_tuple t[HDC_MAX_DIMS];
+        bool ok = true;
+        int used = 0;
+        for (int i = 0; i < dims && ok; ++i) {
+            long long m, p, q, D;
+            if (sscanf(s, " %lld %lld %lld %lld%n", &m, &p, &q, &D, &used) != 4) ok = false;
+            s += used;
+            t[i].m = m; t[i].p = p; t[i].q = q; t[i].D = D;
+            t[i].model_flops = 0.0;
+        }
+        double ms = -1.0;
+        if (ok && sscanf(s, " %lf", &ms) != 1) ok = false;
+        if (!ok) continue; // a corrupt line is skipped, never trusted
+        for (int i = 0; i < dims; ++i) {
+            t[i].ms = ms;
+            best[i] = t[i];
+        }
+        found = true; // the last matching record wins
+    }
+    fclose(fp);
+    return found;
+}
+
+void db_store(const char* path, const std::string& key, int dims, const hdc_tuple* best)
+{
+    if (!path || !*path) return;
+    std::lock_guard<std::mutex> lk(g_db_mu);
+    FILE* fp = fopen(path, "a");
+    if (!fp) return;
+    fprintf(fp, "%s |", key.c_str());
+    for (int i = 0; i < dims; ++i)
+        fprintf(fp, " %lld %lld %lld %lld", (long long)best[i].m, (long long)best[i].p, (long long)best[i].q,
+                (long long)best[i].D);
+    fprintf(fp, " %.6f\n", best[0].ms);
+    fclose(fp);
+}
+
+// Median device time of one configuration (ms), or < 0 on error.
+double time_config(int dims, const void* f, const void* g, void* h, const int64_t* L, const int64_t* M,
+                   const hdc_tuple* t, int dtype, int64_t batch, void* ws, size_t ws_bytes, int warmup, int reps,
+                   cudaStream_t st)
+{
+    int64_t m[HDC_MAX_DIMS], p[HDC_MAX_DIMS], q[HDC_MAX_DIMS], D[HDC_MAX_DIMS];
+    for (int i = 0; i < dims; ++i) { m[i] = t[i].m; p[i] = t[i].p; q[i] = t[i].q; D[i] = t[i].D; }
+    size_t need = 0;
+    if (hdc_workspace_size(dims, L, M, m, p, q, D, dtype, batch, 0, &need) != HDC_OK || need > ws_bytes) return -1.0;
+    for (int w = 0; w < warmup; ++w)
+        if (hdc_convnd(dims, f, g, h, L, M, m, p, q, D, 0, dtype, batch, ws, ws_bytes, st) != HDC_OK) return -1.0;
+    std::vector<float> ts;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return -1.0;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return -1.0; }
+    double res = -1.0;
+    for (int r = 0; r < reps; ++r) {
+        cudaEventRecord(e0, st);
+        if (hdc_convnd(dims, f, g, h, L, M, m, p, q, D, 0, dtype, batch, ws, ws_bytes, st) != HDC_OK) break;
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ts.push_back(ms);
+    }
+    if ((int)ts.size() == reps && reps > 0) {
+        std::sort(ts.begin(), ts.end());
+        res = ts[ts.size() / 2];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return res;
+}
+
+} // namespace
+
+// ------------------------------------------------------------------ ABI
+
+HDC_EXPORT int hdc_tune_candidates(int64_t L, int64_t M, int dtype, double max_ratio, int64_t m_min,
+                                   hdc_tuple* out, int64_t cap, int64_t* n)
+{
+    if (!n || L < 1 || M < 2 * L - 1 || max_ratio < 1.0) return L >= 1 && M < 2 * L - 1 ? HDC_ERR_ALIAS : HDC_ERR_PARAM;
+    if (dtype != HDC_C64 && dtype != HDC_C128) return HDC_ERR_DTYPE;
+    auto c = candidates(L, M, dtype, max_ratio, m_min);
+    *n = (int64_t)c.size();
+    for (int64_t i = 0; i < cap && i < (int64_t)c.size(); ++i) out[i] = c[i];
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_tune_workspace_size(int dims, const int64_t* L, const int64_t* M, int dtype, int64_t batch,
+                                       double max_ratio, int64_t m_min, size_t* bytes)
+{
+    if (!bytes || dims < 1 || dims > HDC_MAX_DIMS || !L || !M) return HDC_ERR_PARAM;
+    // per-axis worst case: the largest workspace any single-axis candidate
+    // (with every D) needs while the other axes take their worst candidate
+    std::vector<hdc_tuple> c[HDC_MAX_DIMS];
+    for (int i = 0; i < dims; ++i) {
+        c[i] = candidates(L[i], M[i], dtype, max_ratio, m_min);
+        if (c[i].empty()) return HDC_ERR_UNSUPPORTED_SIZE;
+    }
+    size_t worst = 0;
+    int64_t m[HDC_MAX_DIMS], p[HDC_MAX_DIMS], q[HDC_MAX_DIMS], D[HDC_MAX_DIMS];
+    // enumerate the product (small: a few dozen per axis)
+    int64_t idx[HDC_MAX_DIMS] = { 0, 0, 0 };
+    while (true) {
+        for (int i = 0; i < dims; ++i) {
+            const hdc_tuple& t = c[i][idx[i]];
+            m[i] = t.m; p[i] = t.p; q[i] = t.q; D[i] = t.q;
+        }
+        size_t b = 0;
+        if (hdc_workspace_size(dims, L, M, m, p, q, D, dtype, batch, 0, &b) == HDC_OK) worst = std::max(worst, b);
+        int k = dims - 1;
+        while (k >= 0 && ++idx[k] == (int64_t)c[k].size()) idx[k--] = 0;
+        if (k < 0) break;
+    }
+    *bytes = worst;
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_tune_convnd(int dims, const int64_t* L, const int64_t* M, int dtype, int64_t batch,
+                               const void* f, const void* g, void* h, void* ws, size_t ws_bytes, int warmup,
+                               int reps, double max_ratio, int64_t m_min, void* stream, hdc_tuple* best,
+                               hdc_tuple* trials, int64_t cap, int64_t* ntrials)
+{
+    if (dims < 1 || dims > HDC_MAX_DIMS || !L || !M || !best || !f || !g || !h || reps < 1) return HDC_ERR_PARAM;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<hdc_tuple> c[HDC_MAX_DIMS];
+    hdc_tuple cur[HDC_MAX_DIMS];
+    for (int i = 0; i < dims; ++i) {
+        if (M[i] < 2 * L[i] - 1) return HDC_ERR_ALIAS;
+        c[i] = candidates(L[i], M[i], dtype, max_ratio, m_min);
+        if (c[i].empty()) return HDC_ERR_UNSUPPORTED_SIZE;
+        cur[i] = c[i][0]; // the smallest model flops as the starting point
+    }
+    int64_t nt = 0;
+    auto record = [&](const hdc_tuple* t, double ms) {
+        if (trials && nt < cap * dims) {
+            for (int i = 0; i < dims; ++i) {
+                trials[nt * dims + i] = t[i];
+                trials[nt * dims + i].ms = ms;
+            }
+        }
+        ++nt;
+    };
+    double best_ms = -1.0;
+    for (int ax = dims - 1; ax >= 0; --ax) {
+        // sweep m for this axis with D = q
+        std::vector<std::pair<double, hdc_tuple>> timed;
+        for (const auto& cand : c[ax]) {
+            hdc_tuple t[HDC_MAX_DIMS];
+            for (int i = 0; i < dims; ++i) t[i] = cur[i];
+            t[ax] = cand;
+            const double ms = time_config(dims, f, g, h, L, M, t, dtype, batch, ws, ws_bytes, warmup, reps, st);
+            if (ms < 0) continue;
+            record(t, ms);
+            timed.emplace_back(ms, cand);
+        }
+        if (timed.empty()) return HDC_ERR_CUDA;
+        std::sort(timed.begin(), timed.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+        hdc_tuple bax = timed[0].second;
+        double bms = timed[0].first;
+        // D below q for the three fastest m
+        for (size_t k = 0; k < timed.size() && k < 3; ++k) {
+            hdc_tuple base = timed[k].second;
+            for (int64_t Dv = 1; Dv < base.q; Dv *= 2) {
+                hdc_tuple t[HDC_MAX_DIMS];
+                for (int i = 0; i < dims; ++i) t[i] = cur[i];
+                t[ax] = base;
+                t[ax].D = Dv;
+                const double ms = time_config(dims, f, g, h, L, M, t, dtype, batch, ws, ws_bytes, warmup, reps, st);
+                if (ms < 0) continue;
+                record(t, ms);
+                if (ms < bms) { bms = ms; bax = t[ax]; }
+            }
+        }
+        cur[ax] = bax;
+        best_ms = bms;
+    }
+    for (int i = 0; i < dims; ++i) {
+        best[i] = cur[i];
+        best[i].ms = best_ms;
+    }
+    if (ntrials) *ntrials = nt;
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_tune_conv1d(int64_t L, int64_t M, int dtype, int64_t batch, const void* f, const void* g,
+                               void* h, void* ws, size_t ws_bytes, int warmup, int reps, double max_ratio,
+                               int64_t m_min, void* stream, hdc_tuple* best, hdc_tuple* trials, int64_t cap,
+                               int64_t* ntrials)
+{
+    return hdc_tune_convnd(1, &L, &M, dtype, batch, f, g, h, ws, ws_bytes, warmup, reps, max_ratio, m_min, stream,
+                           best, trials, cap, ntrials);
+}
+
+// ---------------------------------------------------------------- plans
+
+// Search bounds of plans made with HDC_TUNE_EXHAUSTIVE: candidates within
+// 1.5x of the smallest model flops, m >= 16.
+constexpr double kPlanRatio = 1.5;
+constexpr int64_t kPlanMmin = 16;
+
+struct hdc_plan {
+    int dims;
+    int dtype;
+    int64_t batch;
+    int64_t L[HDC_MAX_DIMS], M[HDC_MAX_DIMS];
+    hdc_tuple t[HDC_MAX_DIMS];
+    size_t ws;
+};
+
+HDC_EXPORT int hdc_plan_create(hdc_plan** out, int dims, const int64_t* L, const int64_t* M, const int64_t* m,
+                               const int64_t* D, int dtype, int64_t batch, int mode, const char* tuning_db,
+                               void* stream)
+{
+    if (!out || dims < 1 || dims > HDC_MAX_DIMS || !L || !M || batch < 1) return HDC_ERR_PARAM;
+    if (dtype != HDC_C64 && dtype != HDC_C128) return HDC_ERR_DTYPE;
+    hdc_plan pl;
+    memset(&pl, 0, sizeof pl);
+    pl.dims = dims;
+    pl.dtype = dtype;
+    pl.batch = batch;
+    for (int i = 0; i < dims; ++i) { pl.L[i] = L[i]; pl.M[i] = M[i]; }
+    const std::string key = db_key(dims, L, M, dtype, batch);
+    if (mode == HDC_FIXED || mode == HDC_EXPLICIT) {
+        for (int i = 0; i < dims; ++i) {
+            int64_t mi = 0, p = 0, q = 0, Dv = 0;
+            if (mode == HDC_EXPLICIT) {
+                int rc = hdc_explicit_params(L[i], M[i], &mi, &p, &q);
+                if (rc != HDC_OK) return rc;
+            } else {
+                if (!m) return HDC_ERR_PARAM;
+                mi = m[i];
+            }
+            int rc = hdc_validate_axis(L[i], M[i], mi, 0, 0, D ? D[i] : 0, dtype, &p, &q, &Dv);
+            if (rc != HDC_OK) return rc;
+            pl.t[i].m = mi; pl.t[i].p = p; pl.t[i].q = q; pl.t[i].D = Dv;
+            pl.t[i].model_flops = model_flops_axis(L[i], mi, q);
+            pl.t[i].ms = -1.0;
+        }
+    } else if (mode == HDC_TUNE_EXHAUSTIVE || mode == HDC_TUNE_CACHED_ONLY) {
+        if (!db_lookup(tuning_db, key, dims, pl.t)) {
+            if (mode == HDC_TUNE_CACHED_ONLY) return HDC_ERR_NOT_TUNED;
+            // tune on scratch buffers of the problem's shape (zeros suffice:
+            // the kernels' work does not depend on the values)
+            int64_t tot = batch;
+            for (int i = 0; i < dims; ++i) tot *= L[i];
+            const size_t esz = dtype == HDC_C128 ? 16 : 8;
+            size_t wsb = 0;
+            int rc = hdc_tune_workspace_size(dims, L, M, dtype, batch, kPlanRatio, kPlanMmin, &wsb);
+            if (rc != HDC_OK) return rc;
+            void *bf = nullptr, *bg = nullptr, *bh = nullptr, *bw = nullptr;
+            cudaStream_t st = (cudaStream_t)stream;
+            if (cudaMalloc(&bf, tot * esz) != cudaSuccess || cudaMalloc(&bg, tot * esz) != cudaSuccess ||
+                cudaMalloc(&bh, tot * esz) != cudaSuccess || cudaMalloc(&bw, wsb) != cudaSuccess) {
+                cudaFree(bf); cudaFree(bg); cudaFree(bh); cudaFree(bw);
+                return HDC_ERR_ALLOC;
+            }
+            cudaMemsetAsync(bf, 0, tot * esz, st);
+            cudaMemsetAsync(bg, 0, tot * esz, st);
+            rc = hdc_tune_convnd(dims, L, M, dtype, batch, bf, bg, bh, bw, wsb, 1, 3, kPlanRatio, kPlanMmin, stream, pl.t, nullptr,
+                                 0, nullptr);
+            cudaStreamSynchronize(st);
+            cudaFree(bf); cudaFree(bg); cudaFree(bh); cudaFree(bw);
+            if (rc != HDC_OK) return rc;
+            db_store(tuning_db, key, dims, pl.t);
+        }
+    } else {
+        return HDC_ERR_PARAM;
+    }
+    int64_t mm[HDC_MAX_DIMS], pp[HDC_MAX_DIMS], qq[HDC_MAX_DIMS], DD[HDC_MAX_DIMS];
+    for (int i = 0; i < dims; ++i) { mm[i] = pl.t[i].m; pp[i] = pl.t[i].p; qq[i] = pl.t[i].q; DD[i] = pl.t[i].D; }
+    int rc = hdc_workspace_size(dims, L, M, mm, pp, qq, DD, dtype, batch, 1, &pl.ws);
+    if (rc != HDC_OK) return rc;
+    hdc_plan* p = new (std::nothrow) hdc_plan(pl);
+    if (!p) return HDC_ERR_ALLOC;
+    *out = p;
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_plan_params(const hdc_plan* pl, int64_t* m, int64_t* p, int64_t* q, int64_t* D)
+{
+    if (!pl) return HDC_ERR_PARAM;
+    for (int i = 0; i < pl->dims; ++i) {
+        if (m) m[i] = pl->t[i].m;
+        if (p) p[i] = pl->t[i].p;
+        if (q) q[i] = pl->t[i].q;
+        if (D) D[i] = pl->t[i].D;
+    }
+    return HDC_OK;
+}
+
+HDC_EXPORT size_t hdc_plan_workspace(const hdc_plan* pl) { return pl ? pl->ws : 0; }
+
+HDC_EXPORT int hdc_plan_execute(const hdc_plan* pl, const void* f, const void* g, void* h, void* ws,
+                                size_t ws_bytes, void* stream)
+{
+    if (!pl) return HDC_ERR_PARAM;
+    int64_t m[HDC_MAX_DIMS], p[HDC_MAX_DIMS], q[HDC_MAX_DIMS], D[HDC_MAX_DIMS];
+    for (int i = 0; i < pl->dims; ++i) { m[i] = pl->t[i].m; p[i] = pl->t[i].p; q[i] = pl->t[i].q; D[i] = pl->t[i].D; }
+    return hdc_convnd(pl->dims, f, g, h, pl->L, pl->M, m, p, q, D, (h == f || h == g) ? 1 : 0, pl->dtype, pl->batch,
+                      ws, ws_bytes, stream);
+}
+
+HDC_EXPORT int hdc_plan_destroy(hdc_plan* pl)
+{
+    delete pl;
+    return HDC_OK;
+}
