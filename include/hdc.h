@@ -186,6 +186,37 @@ int hdc_convnd_host(int dims, const void* f_host, const void* g_host,
  * flight that uses them). */
 int hdc_release_caches(void);
 
+/* ------------------------------------------------- allocation-free call
+ * No counterpart in the paper: an addition for callers that cannot allocate
+ * device memory while they run (a plugin inside an application that owns
+ * the device-memory budget; a real-time loop that cannot take cudaMalloc's
+ * implicit synchronisation and unbounded latency).
+ *
+ * hdc_conv1d_noalloc computes the same 1-D convolution as hdc_conv1d (same
+ * parameters and results) but calls no cudaMalloc, cudaFree or allocating
+ * library routine, takes no workspace and leaves the twiddle cache alone.
+ * Its scratch -- the two twiddle tables (q m and m entries) and the
+ * D x batch x m residue workspace, each rounded up to 256 bytes -- lives in
+ * one fixed device array of HDC_NOALLOC_SCRATCH_BYTES that every GPU loading
+ * the library holds until the process exits.
+ *  - f, g, h: device pointers (batch x L complex); h may alias neither f nor
+ *    g (there is no in-place mode here).
+ *  - Only the single-tile route: m <= 4096 (complex<double>) or m <= 8192
+ *    (complex<float>).  Sizes whose scratch exceeds the array, or larger m,
+ *    return HDC_ERR_UNSUPPORTED_SIZE before anything is launched; other
+ *    errors as hdc_conv1d.
+ *  - The first call on a device, with that device current, looks up the
+ *    array's device address (cudaGetSymbolAddress) and keeps it; make that
+ *    first call before any stream capture.
+ *  - All calls share the one array and every call rewrites what it reads,
+ *    so nothing from an earlier call leaks into a result; but calls whose
+ *    work overlaps on the GPU (other streams, other host threads) race on
+ *    the array: order them on one stream or synchronise between them. */
+#define HDC_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+int hdc_conv1d_noalloc(const void* f, const void* g, void* h, int64_t L,
+                       int64_t M, int64_t m, int64_t p, int64_t q, int64_t D,
+                       int dtype, int64_t batch, void* stream);
+
 /* ----------------------------------------------------- parameter search
  * Section 4.2 (A0 grid search, separable per axis).  Candidates of an axis:
  * for every q, the m = 2^a 3^b 5^c 7^d >= m_min that pad M least (the three

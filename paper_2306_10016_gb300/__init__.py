@@ -70,6 +70,7 @@ _SIGS = [
                              C.c_int, _i64, _vp, _sz, _vp]),
     ("hdc_release_caches", C.c_int, []),
     ("hdc_probe_fma", C.c_int, [C.c_int, _i64, C.c_int, C.c_int, _vp, _vp, C.POINTER(C.c_double)]),
+    ("hdc_conv1d_noalloc", C.c_int, [_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _i64, C.c_int, _i64, _vp]),
 ]
 
 
@@ -455,6 +456,25 @@ def stats() -> dict:
         out[lib().hdc_stats_kernel_name(k).decode()] = dict(launches=n.value, ms=ms.value, flops=fl.value,
                                                              bytes=by.value)
     return out
+
+
+def conv1d_noalloc(f, g, m, M=None, p=0, q=0, D=0, out=None, stream=None):
+    """hdc_conv1d_noalloc: the 1-D convolution with the library's fixed
+    device scratch array instead of a workspace (no device allocation in the
+    call; `out` must be given by callers that cannot allocate either)."""
+    torch = _torch()
+    if not (f.is_cuda and g.is_cuda) or f.shape != g.shape or f.dtype != g.dtype:
+        raise ValueError("f and g must be CUDA tensors of one shape and dtype")
+    L = int(f.shape[-1])
+    batch = f.numel() // L if L else 0
+    h = out if out is not None else torch.empty_like(f)
+    st = stream if stream is not None else torch.cuda.current_stream(f.device)
+    with torch.cuda.device(f.device):
+        rc = lib().hdc_conv1d_noalloc(f.data_ptr(), g.data_ptr(), h.data_ptr(), L,
+                                      int(M) if M is not None else 2 * L - 1, int(m), int(p), int(q), int(D),
+                                      dtype_code(f.dtype), batch, st.cuda_stream)
+    _check(rc, "hdc_conv1d_noalloc")
+    return h
 
 
 def release_caches() -> None:

@@ -84,4 +84,18 @@ cudaError_t launch_unfold(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstride
                           int64_t Lvalid, int64_t r0, int64_t D, int first, int last, double scale,
                           cudaStream_t st);
 
+// The same launches with caller-provided twiddle tables (no library cache):
+// twN = zeta_{q m}^k (q m entries), twm = zeta_m^k (m entries), twNf as in
+// launch_unfold; launch_twiddle_into fills a table of n entries on `st`.
+template <typename T> cudaError_t launch_twiddle_into(cx<T>* tw, int64_t n, cudaStream_t st);
+template <typename T>
+cudaError_t launch_residue_rows_tw(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_t B, int64_t ld_in,
+                                   int64_t L, int64_t m, int64_t p, int64_t q, int64_t r0, int64_t D,
+                                   const cx<T>* twN, const cx<T>* twm, cudaStream_t st);
+template <typename T>
+cudaError_t launch_unfold_tw(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstride, int64_t Cn, int64_t ma,
+                             int64_t p, int64_t q, int64_t Nf, int64_t cs, int64_t cc, int64_t Lvalid,
+                             int64_t r0, int64_t D, int first, int last, double scale, const cx<T>* twNf,
+                             cudaStream_t st);
+
 } // namespace hdc

@@ -371,6 +371,72 @@ cudaError_t launch_unfold(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstride
     return cudaGetLastError();
 }
 
+// ---------------------------------------- launchers with caller twiddles
+// The same kernels with the twiddle tables passed in (for callers that keep
+// the tables in memory of their own instead of the library cache).
+
+template <typename T>
+cudaError_t launch_twiddle_into(cx<T>* tw, int64_t n, cudaStream_t st)
+{
+    return launch_twiddle<T>(tw, n, st);
+}
+
+template <typename T>
+cudaError_t launch_residue_rows_tw(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_t B, int64_t ld_in,
+                                   int64_t L, int64_t m, int64_t p, int64_t q, int64_t r0, int64_t D,
+                                   const cx<T>* twN, const cx<T>* twm, cudaStream_t st)
+{
+    using V = cx<T>;
+    const int64_t Dg = (D < q - r0) ? D : (q - r0);
+    if (B <= 0 || Dg <= 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    const FftPlan fp = make_fft_plan(m);
+    const int thr = threads_for(m);
+    const size_t smem = (size_t)(3 * m) * sizeof(V);
+    auto kern = k_residue_rows<V>;
+    if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
+    const int64_t blocks = B * Dg;
+    const double Lrow = (double)((L < p * m) ? L : p * m);
+    const double fold = (p == 1 && q == 1) ? 0.0 : 16.0 * Lrow;
+    LaunchScope ls(K_RESIDUE_ROWS, st, (double)(B * Dg) * (3.0 * fft_flops((double)m) + 6.0 * m + fold),
+                   (2.0 * B * Lrow + (double)(Dg * B * m)) * sizeof(V));
+    kern<<<(unsigned)blocks, thr, smem, st>>>(f, g, h, B, ld_in, L, (int)m, (int)p, (int)q, (int)r0,
+                                              (int)Dg, twN, twm, fp);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_unfold_tw(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstride, int64_t Cn, int64_t ma,
+                             int64_t p, int64_t q, int64_t Nf, int64_t cs, int64_t cc, int64_t Lvalid,
+                             int64_t r0, int64_t D, int first, int last, double scale, const cx<T>* twNf,
+                             cudaStream_t st)
+{
+    using V = cx<T>;
+    const int64_t Dg = (D < q - r0) ? D : (q - r0);
+    if (B <= 0 || Dg <= 0) return cudaSuccess;
+    const int thr = 256;
+    const int64_t total = ma * Cn * B;
+    const int64_t blocks = (total + thr - 1) / thr;
+    LaunchScope ls(K_UNFOLD, st, (double)(Dg * B) * 8.0 * Lvalid + (last ? 2.0 * B * Lvalid : 0.0),
+                   ((double)(Dg * B * ma * Cn) + (first ? 1.0 : 2.0) * B * Lvalid) * sizeof(V));
+    k_unfold<V, 4><<<(unsigned)blocks, thr, 0, st>>>(out, h, B, bstride, Cn, ma, (int)p, (int)q, Nf, cs, cc,
+                                                     Lvalid, (int)r0, (int)Dg, first, last, (T)scale, twNf);
+    return cudaGetLastError();
+}
+
+#define HDC_INST_TW(T)                                                                                    \
+    template cudaError_t launch_twiddle_into<T>(cx<T>*, int64_t, cudaStream_t);                          \
+    template cudaError_t launch_residue_rows_tw<T>(const cx<T>*, const cx<T>*, cx<T>*, int64_t, int64_t, \
+                                                   int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, \
+                                                   const cx<T>*, const cx<T>*, cudaStream_t);            \
+    template cudaError_t launch_unfold_tw<T>(cx<T>*, const cx<T>*, int64_t, int64_t, int64_t, int64_t,   \
+                                             int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,       \
+                                             int64_t, int64_t, int, int, double, const cx<T>*,           \
+                                             cudaStream_t);
+
+HDC_INST_TW(double)
+HDC_INST_TW(float)
+
 // ------------------------------------------------------ instantiations
 
 #define HDC_INST(T)                                                                                       \
