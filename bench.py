@@ -176,7 +176,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hdc", choices=["hdc", "reference"])
-    ap.add_argument("--tuning-db", default=os.path.join(ROOT, "gpurun_out", "hdc_tuning.txt"))
+    ap.add_argument("--tuning-db", default=os.environ.get(
+        "HDC_TUNING_DB", os.path.join(os.path.expanduser("~"), ".cache", "hdc", "tuning.txt")))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sizes", default="", help="comma-separated L list (default: the full sweep)")
     args = ap.parse_args()

@@ -84,7 +84,7 @@ def test_explicit_params(lib):
 
 def test_validation_errors(lib):
     C128 = hdc.HDC_C128
-    # BASELINE config 1 literal (m=512, p=1 with L=1024) violates p m >= L
+    # the L=1024, m=512 workload written with p=1 violates p m >= L (Section 2.5)
     rc, _ = hdc.validate_axis(1024, 2047, 512, 1, 4, 1, C128)
     assert rc == hdc.HDC_ERR_PARAM
     rc, (p, q, D) = hdc.validate_axis(1024, 2047, 512, 0, 0, 1, C128)
