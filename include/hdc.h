@@ -201,7 +201,7 @@ int hdc_release_caches(void);
  * the library holds until the process exits.
  *  - f, g, h: device pointers (batch x L complex); h may alias neither f nor
  *    g (there is no in-place mode here).
- *  - Only the single-tile route: m <= 4096 (complex<double>) or m <= 8192
+ *  - Only the single-tile route: m <= 2048 (complex<double>) or m <= 4096
  *    (complex<float>).  Sizes whose scratch exceeds the array, or larger m,
  *    return HDC_ERR_UNSUPPORTED_SIZE before anything is launched; other
  *    errors as hdc_conv1d.

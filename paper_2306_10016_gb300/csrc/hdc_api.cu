@@ -79,7 +79,8 @@ template const cx<float>* twiddles<float>(int64_t, cudaError_t*);
 
 struct Axis {
     int64_t L, M, m, p, q, D, N;
-    int64_t m1, m2; // split of m for the strided-axis route (m1 == 0: fused rows)
+    int64_t m1, m2; // m1 < 0: m not supported (no split within the tile limits)
+    int dtype;
 };
 
 static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -92,17 +93,70 @@ static bool good_size(int64_t n)
     return n == 1;
 }
 
+// Some split m = m1 m2 with m2 <= max_row and m1 <= max_col exists?
+template <typename T> static bool splittable(int64_t m)
+{
+    for (int64_t d = max_row_fft<T>(); d >= 2; --d)
+        if (m % d == 0 && m / d <= max_col_fft<T>()) return true;
+    return false;
+}
+
 template <typename T> static void split_m(Axis& a)
 {
     a.m1 = 0;
     a.m2 = a.m;
     if (a.m <= max_row_fft<T>()) return;
-    // largest divisor m2 <= max_row with m1 = m / m2 <= max_col
-    for (int64_t d = max_row_fft<T>(); d >= 2; --d) {
-        if (a.m % d) continue;
-        if (a.m / d <= max_col_fft<T>()) { a.m2 = d; a.m1 = a.m / d; return; }
+    if (!splittable<T>(a.m)) a.m1 = -1; // unsupported
+}
+
+static int sm_count()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else
+            n = 152;
     }
-    a.m1 = -1; // unsupported
+    return n;
+}
+
+// Route of one 1-D pass over B rows: fused residue kernel (m1 = 0) or the
+// split m = m1 m2.  FP64 work runs at a few flops per clock per SM, so the
+// choice is made for parallelism: keep the fused kernel when it already
+// launches two blocks per SM (or m is too small to split usefully);
+// otherwise take the largest row length m2 whose middle pass has two blocks
+// per SM, else the split with the most rows.
+template <typename T> static void route_for(const Axis& a, int64_t B, int64_t* m1o, int64_t* m2o)
+{
+    const int64_t Dg = a.D < a.q ? a.D : a.q;
+    const int64_t want = 2 * (int64_t)sm_count();
+    const bool fused_ok = a.m <= max_row_fft<T>();
+    if (fused_ok && (B * Dg >= want || a.m < 512)) { *m1o = 0; *m2o = a.m; return; }
+    int64_t b1 = -1, b2 = -1;
+    const int64_t top = a.m / 2 < max_row_fft<T>() ? a.m / 2 : max_row_fft<T>();
+    for (int64_t d = top; d >= 32; --d) {
+        if (a.m % d) continue;
+        const int64_t m1 = a.m / d;
+        if (m1 > max_col_fft<T>()) break;
+        b1 = m1; b2 = d;
+        if (Dg * B * m1 >= want) break;
+    }
+    if (b1 < 0 || (fused_ok && Dg * B * b1 < 4 * B * Dg)) {
+        if (fused_ok) { *m1o = 0; *m2o = a.m; return; }
+        // no split down to rows of 32: the largest admissible m2
+        for (int64_t d = max_row_fft<T>(); d >= 2; --d)
+            if (a.m % d == 0 && a.m / d <= max_col_fft<T>()) { b1 = a.m / d; b2 = d; break; }
+    }
+    *m1o = b1; *m2o = b2;
+}
+
+static void route(const Axis& a, int64_t B, int dtype, int64_t* m1, int64_t* m2)
+{
+    if (dtype == HDC_C128) route_for<double>(a, B, m1, m2);
+    else route_for<float>(a, B, m1, m2);
 }
 
 static int64_t max_fft(int dtype) { return dtype == HDC_C128 ? (int64_t)1 << 24 : (int64_t)1 << 25; }
@@ -122,6 +176,7 @@ static int resolve_axis(int64_t L, int64_t M, int64_t m, int64_t p, int64_t q, i
     if (q > max_padded(dtype) / m) return HDC_ERR_UNSUPPORTED_SIZE;
     Axis a;
     a.L = L; a.M = M; a.m = m; a.p = p; a.q = q; a.D = D; a.N = q * m;
+    a.dtype = dtype;
     if (dtype == HDC_C128) split_m<double>(a); else split_m<float>(a);
     if (a.m1 < 0) return HDC_ERR_UNSUPPORTED_SIZE;
     if (out) *out = a;
@@ -138,7 +193,9 @@ static int64_t ws_elems(int dims, const Axis* ax, int64_t B)
 {
     if (dims == 1) {
         const Axis& a = ax[0];
-        if (a.m1 == 0) return a.D * B * a.m;
+        int64_t m1 = 0, m2 = 0;
+        route(a, B, a.dtype, &m1, &m2);
+        if (m1 == 0) return a.D * B * a.m;
         return 2 * a.D * B * a.m;
     }
     int64_t Cn = 1;
@@ -172,7 +229,9 @@ static cudaError_t run_rows(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t 
                             const Axis& a, cx<T>* ws, cudaStream_t st)
 {
     const double scale = 1.0 / (double)a.N;
-    if (a.m1 == 0) {
+    int64_t m1 = 0, m2 = 0;
+    route(a, B, a.dtype, &m1, &m2);
+    if (m1 == 0) {
         for (int64_t r0 = 0; r0 < a.q; r0 += a.D) {
             const int first = (r0 == 0), last = (r0 + a.D >= a.q);
             HDC_TRY(launch_residue_rows<T>(f, g, ws, B, ld, a.L, a.m, a.p, a.q, r0, a.D, st));
@@ -189,12 +248,12 @@ static cudaError_t run_rows(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t 
     for (int64_t r0 = 0; r0 < a.q; r0 += a.D) {
         const int first = (r0 == 0), last = (r0 + a.D >= a.q);
         const int64_t Dg = (a.D < a.q - r0) ? a.D : (a.q - r0);
-        HDC_TRY(launch_fold_fft_cols<T>(f, g, yf, yg, B, ld, a.m2, a.m1, a.p, a.q, a.N, a.m2, 1, a.L,
-                                        r0, a.D, 1, st));
-        HDC_TRY(launch_residue_rows<T>(yf, yg, yf, Dg * B * a.m1, a.m2, a.m2, a.m2, 1, 1, 0, 1, st));
-        HDC_TRY(launch_ifft_cols<T>(yf, B, a.m2, a.m1, a.q, a.N, Dg, 1, st));
-        HDC_TRY(launch_unfold<T>(out, yf, B, ld, a.m2, a.m1, a.p, a.q, a.N, a.m2, 1, a.L, r0, a.D, first,
-                                 last, scale, st));
+        HDC_TRY(launch_fold_fft_cols<T>(f, g, yf, yg, B, ld, m2, m1, a.p, a.q, a.N, m2, 1, a.L, r0, a.D, 1,
+                                        st));
+        HDC_TRY(launch_residue_rows<T>(yf, yg, yf, Dg * B * m1, m2, m2, m2, 1, 1, 0, 1, st));
+        HDC_TRY(launch_ifft_cols<T>(yf, B, m2, m1, a.q, a.N, Dg, 1, st));
+        HDC_TRY(launch_unfold<T>(out, yf, B, ld, m2, m1, a.p, a.q, a.N, m2, 1, a.L, r0, a.D, first, last,
+                                 scale, st));
     }
     return cudaSuccess;
 }

@@ -11,17 +11,22 @@
 namespace hdc {
 
 // Block size cap of the transform kernels (every stage loops over its
-// butterflies, so any count works; 512 leaves 128 registers per thread).
-constexpr int kMaxThreads = 512;
-// Shared-memory budget: the fused residue kernel holds f, g and one
-// ping-pong buffer of m elements (3 m), the strided-axis kernels a tile of
-// ma x C elements and its ping-pong twin (2 ma C).
-constexpr int64_t kRowBytes = 192 * 1024;
-constexpr int64_t kColBytes = 128 * 1024;
+// butterflies, so any count works): 256 threads at up to 128 registers let
+// two blocks share an SM.
+constexpr int kMaxThreads = 256;
+// Shared-memory budgets.  The fused residue kernel holds f, g and one
+// ping-pong buffer of m elements (3 m): 96 KiB keeps two blocks per SM, so
+// one block's loads and barriers overlap the other's arithmetic.  The
+// strided-axis kernels hold a tile of ma x C elements and its ping-pong twin
+// (2 ma C): C is chosen so a tile fits 64 KiB (three blocks per SM), and a
+// single column may use up to 128 KiB.
+constexpr int64_t kRowBytes = 96 * 1024;
+constexpr int64_t kColTargetBytes = 64 * 1024;
+constexpr int64_t kColMaxBytes = 128 * 1024;
 
-template <typename T> constexpr int64_t max_row_fft() { return kRowBytes / (3 * (int64_t)sizeof(cx<T>)); }
-template <typename T> constexpr int64_t col_tile_elems() { return kColBytes / (2 * (int64_t)sizeof(cx<T>)); }
-template <typename T> constexpr int64_t max_col_fft() { return col_tile_elems<T>(); }
+template <typename T> constexpr int64_t max_row_fft() { return kRowBytes / (3 * (int64_t)sizeof(cx<T>)) / 16 * 16; }
+template <typename T> constexpr int64_t col_tile_target() { return kColTargetBytes / (2 * (int64_t)sizeof(cx<T>)); }
+template <typename T> constexpr int64_t max_col_fft() { return kColMaxBytes / (2 * (int64_t)sizeof(cx<T>)); }
 
 FftPlan make_fft_plan(int64_t n);
 

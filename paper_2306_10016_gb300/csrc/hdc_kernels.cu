@@ -67,7 +67,7 @@ static cudaError_t allow_smem(K kernel, size_t bytes)
 // ------------------------------------------------------- residue rows
 
 template <class V>
-__global__ void __launch_bounds__(kMaxThreads, 1)
+__global__ void __launch_bounds__(kMaxThreads, 2)
 k_residue_rows(const V* f, const V* g, V* h, int64_t B, int64_t ld_in, int64_t L, int m, int p,
                int q, int r0, int Dg, const V* __restrict__ twN, const V* __restrict__ twm,
                FftPlan fp)
@@ -83,6 +83,13 @@ k_residue_rows(const V* f, const V* g, V* h, int64_t B, int64_t ld_in, int64_t L
     const V* fr = f + b * ld_in;
     const V* gr = g + b * ld_in;
     // fold: w_r[s] = zeta_N^{r s} sum_t zeta_q^{r t} x[t m + s]   (Eq. 1)
+    if (p == 1 && q == 1 && L >= m) {
+        // plain copy (rows of a split transform): no arithmetic
+        for (int s = tid; s < m; s += nthr) {
+            sa[s] = fr[s];
+            sb[s] = gr[s];
+        }
+    } else
     for (int s = tid; s < m; s += nthr) {
         V af = czero<V>(), ag = czero<V>();
         for (int t = 0; t < p; ++t) {
@@ -157,7 +164,7 @@ static int col_tile(int64_t Cn, int64_t ma, int64_t elems_max)
 }
 
 template <class V>
-__global__ void __launch_bounds__(kMaxThreads, 1)
+__global__ void __launch_bounds__(kMaxThreads, 2)
 k_fold_fft_cols(const V* __restrict__ f, const V* __restrict__ g, V* yf, V* yg, int64_t B,
                 int64_t bstride, int64_t Cn, int ma, int p, int q, int64_t Nf, int64_t cs,
                 int64_t cc, int64_t Lvalid, int r0, int Dg, int C, int nct, int post,
@@ -223,7 +230,7 @@ cudaError_t launch_fold_fft_cols(const cx<T>* f, const cx<T>* g, cx<T>* yf, cx<T
     const V* twma = twiddles<T>(ma, &e);
     if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(ma);
-    const int C = col_tile(Cn, ma, col_tile_elems<T>());
+    const int C = col_tile(Cn, ma, col_tile_target<T>());
     const int nct = (int)((Cn + C - 1) / C);
     const int thr = threads_for(ma * C);
     const size_t smem = (size_t)(2 * ma * C) * sizeof(V);
@@ -240,7 +247,7 @@ cudaError_t launch_fold_fft_cols(const cx<T>* f, const cx<T>* g, cx<T>* yf, cx<T
 }
 
 template <class V>
-__global__ void __launch_bounds__(kMaxThreads, 1)
+__global__ void __launch_bounds__(kMaxThreads, 2)
 k_ifft_cols(V* y, int64_t B, int64_t Cn, int ma, int q, int64_t Nf, int Dg, int C, int nct, int pre,
             const V* __restrict__ twNf, const V* __restrict__ twma, FftPlan fp)
 {
@@ -286,7 +293,7 @@ cudaError_t launch_ifft_cols(cx<T>* y, int64_t B, int64_t Cn, int64_t ma, int64_
     const V* twma = twiddles<T>(ma, &e);
     if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(ma);
-    const int C = col_tile(Cn, ma, col_tile_elems<T>());
+    const int C = col_tile(Cn, ma, col_tile_target<T>());
     const int nct = (int)((Cn + C - 1) / C);
     const int thr = threads_for(ma * C);
     const size_t smem = (size_t)(2 * ma * C) * sizeof(V);

@@ -32,6 +32,17 @@ std::vector<cudaEvent_t> g_pool;
 const char* g_names[K_COUNT] = { "k_twiddle", "k_residue_rows", "k_fold_fft_cols", "k_ifft_cols", "k_unfold",
                                  "k_batched" };
 
+// Inside a stream capture an event record must be an external record node
+// for the event to carry a time stamp when the graph replays.
+void record(cudaEvent_t e, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, st);
+}
+
 cudaEvent_t take_event()
 {
     if (!g_pool.empty()) {
@@ -56,7 +67,7 @@ LaunchScope::LaunchScope(int k, cudaStream_t s, double flops, double bytes) : ki
     g_k[kid].bytes += bytes;
     if (g_timing.load()) {
         e0 = take_event();
-        if (e0) cudaEventRecord(e0, st);
+        if (e0) record(e0, st);
     }
 }
 
@@ -66,7 +77,7 @@ LaunchScope::~LaunchScope()
     std::lock_guard<std::mutex> lk(g_mu);
     cudaEvent_t e1 = take_event();
     if (!e1) return;
-    cudaEventRecord(e1, st);
+    record(e1, st);
     g_k[kid].ev.emplace_back(e0, e1);
 }
 

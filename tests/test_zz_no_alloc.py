@@ -62,10 +62,10 @@ def test_noalloc_rejects_oversize_and_aliasing(hdc):
     f = torch.zeros((L,), dtype=torch.complex128, device="cuda")
     g = torch.zeros_like(f)
     h = torch.empty_like(f)
-    # m beyond the single-tile route (FP64: 4096)
+    # m beyond the single-tile route (FP64: 2048)
     assert _noalloc_abi(hdc, f, g, h, L, m, 0) == hdc.HDC_ERR_UNSUPPORTED_SIZE
-    # workspace beyond the fixed scratch array: 64 rows x q=8 x 4096 x 16 B
-    B, L, m = 64, 16384, 4096
+    # workspace beyond the fixed scratch array: 64 rows x q=16 x 2048 x 16 B = 32 MiB + tables
+    B, L, m = 64, 16384, 2048
     f = torch.zeros((B, L), dtype=torch.complex128, device="cuda")
     g = torch.zeros_like(f)
     h = torch.empty_like(f)
