@@ -337,6 +337,64 @@ def main():
     ms32 = rank_max(ms32)
     del ins32
 
+    # --- batched: 4096 convolutions, L log-uniform in [64, 65536], one
+    # persistent launch per step, replayed from a CUDA graph
+    def batched_run(tdt, dcode, nconv=4096):
+        Ls = [int(x) for x in synth.log_uniform_lengths(synth.BASE_SEED + 4, nconv, 64, 65536)]
+        tot = sum(Ls)
+        fa = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 40, (tot,))).to(dev, tdt)
+        ga = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 41, (tot,))).to(dev, tdt)
+        ha = torch.empty_like(fa)
+        offs = np.concatenate([[0], np.cumsum(Ls)])
+        fs = [fa[offs[i]:offs[i + 1]] for i in range(nconv)]
+        gs = [ga[offs[i]:offs[i + 1]] for i in range(nconv)]
+        hs = [ha[offs[i]:offs[i + 1]] for i in range(nconv)]
+        t0 = time.perf_counter()
+        ms_t, _ = hdc.batched_tune(fs, gs, hs, reps=2, max_cands=6)
+        tune_b = time.perf_counter() - t0
+        res = {}
+        for name, mlist in (("tuned", ms_t), ("explicit", [hdc.next_good_size(2 * L - 1) for L in Ls])):
+            plan = hdc.BatchedPlan(Ls, mlist, dcode)
+            wsb = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=dev)
+            plan.bind(fs, gs, hs)
+            side = torch.cuda.Stream(dev)
+            with torch.cuda.stream(side):
+                for _ in range(max(1, args.warmup)):
+                    plan.execute(wsb, stream=side)
+            torch.cuda.synchronize(dev)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=side):
+                plan.execute(wsb, stream=side)
+            st = torch.cuda.current_stream(dev)
+            ev = []
+            for _ in range(args.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                graph.replay()
+                e1.record(st)
+                ev.append((e0, e1))
+            torch.cuda.synchronize(dev)
+            ok = hdc.BatchedPlan.status(wsb) == 0
+            msb = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+            fl = sum(pp["q"] * (15 * pp["m"] * math.log2(pp["m"]) + 6 * pp["m"] + 24 * pp["L"]) + 2 * pp["L"]
+                     for pp in plan.params)
+            res[name] = {"value": world * tot / (msb * 1e-3), "ms": round(msb, 4), "status_ok": ok,
+                         "model_tflops": round(fl / (msb * 1e-3) / 1e12, 4)}
+            del graph, plan, wsb
+        res["convolutions"] = nconv
+        res["outputs"] = tot
+        res["tuning_s"] = round(tune_b, 1)
+        return res
+
+    batched64 = batched_run(torch.complex128, hdc.HDC_C128)
+    batched64["roofline_frac"] = round(batched64["tuned"]["model_tflops"] / (
+        SM_COUNT * FP64_FMA_PER_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12), 4)
+    batched32 = batched_run(torch.complex64, hdc.HDC_C64)
+    batched32["roofline_frac"] = round(batched32["tuned"]["model_tflops"] / (
+        SM_COUNT * FP32_FMA_PER_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12), 4)
+
     # --- end to end through the host-buffer C call (FP64)
     pinned = []
     for i, L in enumerate(sizes):
@@ -406,6 +464,8 @@ def main():
         "explicit": {"value": world * outs / (ms_ex * 1e-3), "ms_per_step": ms_ex,
                      "hybrid_speedup": round(ms_ex / ms64, 4)},
         "fp32": {"value": world * outs / (ms32 * 1e-3), "ms_per_step": ms32},
+        "batched_fp64": batched64,
+        "batched_fp32": batched32,
         "per_size_fp64": per_size,
         "roofline": roofline,
         "cpu_baseline": cpu,

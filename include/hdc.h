@@ -271,6 +271,56 @@ int hdc_plan_execute(const hdc_plan* plan, const void* f, const void* g,
                      void* h, void* workspace, size_t ws_bytes, void* stream);
 int hdc_plan_destroy(hdc_plan* plan);
 
+/* ---------------------------------------------------- batched execution
+ * n independent 1-D convolutions of uneven lengths L_i (M_i = 2 L_i - 1,
+ * FFT size m_i per convolution, p_i and q_i derived, all residues in one
+ * pass) in ONE cooperative persistent launch: blocks claim work items of
+ * four phases (column fold+FFT, row transforms, column inverse FFT, unfold)
+ * from atomic counters and meet at a grid barrier between phases.  The
+ * barrier's spin is bounded; if it runs out, the status word in the
+ * workspace becomes HDC_ERR_TIMEOUT and the blocks return.  The launch and
+ * the memset that clears its counters may be captured in a CUDA graph.
+ * No counterpart in the paper (its method convolves one problem at a time).
+ *
+ * create: validates every (L_i, 2 L_i - 1, m_i), builds the work lists and
+ *   uploads them (library-owned device memory, freed by destroy).
+ * execute: f, g, h are DEVICE arrays of n device pointers (each to L_i
+ *   complex values); workspace of hdc_batched_workspace() bytes. */
+typedef struct hdc_batched hdc_batched;
+int hdc_batched_create(hdc_batched** plan, int64_t n, const int64_t* L,
+                       const int64_t* m, int dtype);
+size_t hdc_batched_workspace(const hdc_batched* plan);
+/* per-convolution m, p, q and the split m = m1 m2 (m1 = 0: one row tile) */
+int hdc_batched_params(const hdc_batched* plan, int64_t* m, int64_t* p,
+                       int64_t* q, int64_t* m1, int64_t* m2);
+int hdc_batched_execute(hdc_batched* plan, const void* const* f,
+                        const void* const* g, void* const* h, void* workspace,
+                        size_t ws_bytes, void* stream);
+/* Status word of the last execute in `workspace` (synchronous copy; call
+ * after the stream has finished): 0 or HDC_ERR_TIMEOUT. */
+int hdc_batched_status(const void* workspace, int* status);
+/* Barrier limits: spin iterations (about 64 ns each) before giving up, and
+ * arrivals the barrier waits for beyond the grid (0 in normal use; a
+ * positive value makes every barrier wait for blocks that do not exist,
+ * which exercises the timeout path without a fault). */
+int hdc_batched_set_barrier(hdc_batched* plan, long long spin_limit,
+                            int extra_arrivals);
+int hdc_batched_destroy(hdc_batched* plan);
+/* Per-size schedules (the grid search of Section 4.2 applied to the batched
+ * kernel, with size classes as the separable axes): lengths are grouped by
+ * floor(log2 L); every group starts at the candidate m of least model flops
+ * among the first `max_cands` candidates of its longest member
+ * (hdc_tune_candidates, ratio 1.5, m >= 16); then, group by group (largest
+ * total length first, the others held), each candidate is timed on the
+ * WHOLE batch with this kernel (`reps` timed runs, median) and the fastest
+ * kept.  m_out receives every convolution's m.  f_host, g_host, h_host: HOST
+ * arrays of the n device pointers.  Allocates and frees its own scratch;
+ * synchronises `stream`.  *ms_out: the time of the final assignment. */
+int hdc_batched_tune(int64_t n, const int64_t* L, int dtype,
+                     const void* const* f_host, const void* const* g_host,
+                     void* const* h_host, int reps, int max_cands,
+                     void* stream, int64_t* m_out, double* ms_out);
+
 /* ------------------------------------------------------ launch statistics
  * Counting of every kernel launch (always on) and, when enabled, CUDA events
  * recorded on the launch stream around each launch.  Read after the work

@@ -103,6 +103,15 @@ _SIGS += [
     ("hdc_plan_workspace", _sz, [_vp]),
     ("hdc_plan_execute", C.c_int, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     ("hdc_plan_destroy", C.c_int, [_vp]),
+    ("hdc_batched_create", C.c_int, [C.POINTER(_vp), _i64, _i64p, _i64p, C.c_int]),
+    ("hdc_batched_workspace", _sz, [_vp]),
+    ("hdc_batched_params", C.c_int, [_vp, _i64p, _i64p, _i64p, _i64p, _i64p]),
+    ("hdc_batched_execute", C.c_int, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    ("hdc_batched_status", C.c_int, [_vp, C.POINTER(C.c_int)]),
+    ("hdc_batched_set_barrier", C.c_int, [_vp, C.c_longlong, C.c_int]),
+    ("hdc_batched_destroy", C.c_int, [_vp]),
+    ("hdc_batched_tune", C.c_int, [_i64, _i64p, C.c_int, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.c_int,
+                                   C.c_int, _vp, _i64p, C.POINTER(C.c_double)]),
     ("hdc_stats_reset", C.c_int, []),
     ("hdc_stats_timing", C.c_int, [C.c_int]),
     ("hdc_stats_kernel_count", C.c_int, []),
@@ -428,6 +437,83 @@ class Plan:
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
             _lib.hdc_plan_destroy(self._h)
+            self._h = None
+
+
+# --------------------------------------------------------- batched plans
+
+def _ptr_arrays(ts):
+    return (C.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+
+def batched_tune(fs, gs, hs, reps=3, max_cands=12, stream=None):
+    """Per-size-class m for the batched kernel (hdc_batched_tune) on the
+    given lists of device tensors; returns (m list, summed best ms)."""
+    torch = _torch()
+    n = len(fs)
+    L = _arr([int(t.shape[-1]) for t in fs])
+    m = (C.c_int64 * n)()
+    ms = C.c_double()
+    st = stream if stream is not None else torch.cuda.current_stream(fs[0].device)
+    _check(lib().hdc_batched_tune(n, L, dtype_code(fs[0].dtype), _ptr_arrays(fs), _ptr_arrays(gs), _ptr_arrays(hs),
+                                  reps, max_cands, st.cuda_stream, m, C.byref(ms)), "batched_tune")
+    return list(m), ms.value
+
+
+class BatchedPlan:
+    """n 1-D convolutions of lengths L (M = 2L-1) and FFT sizes m in one
+    persistent launch (hdc_batched_*)."""
+
+    def __init__(self, L, m, dtype=HDC_C128):
+        self.L = [int(x) for x in L]
+        self.n = len(self.L)
+        h = C.c_void_p()
+        _check(lib().hdc_batched_create(C.byref(h), self.n, _arr(self.L), _arr(m), dtype), "batched_create")
+        self._h = h
+        self.dtype = dtype
+        self._ptrs = None
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(lib().hdc_batched_workspace(self._h))
+
+    @property
+    def params(self):
+        arrs = [(C.c_int64 * self.n)() for _ in range(5)]
+        _check(lib().hdc_batched_params(self._h, *arrs), "batched_params")
+        return [dict(L=self.L[i], m=arrs[0][i], p=arrs[1][i], q=arrs[2][i], m1=arrs[3][i], m2=arrs[4][i])
+                for i in range(self.n)]
+
+    def bind(self, fs, gs, hs):
+        """Device arrays of the n input/output pointers (kept by the plan, so a
+        captured launch keeps reading valid arrays)."""
+        torch = _torch()
+        dev = fs[0].device
+        self._ptrs = [torch.tensor([t.data_ptr() for t in ts], dtype=torch.int64, device=dev) for ts in (fs, gs, hs)]
+        return self._ptrs
+
+    def execute(self, workspace, stream=None):
+        torch = _torch()
+        if self._ptrs is None:
+            raise RuntimeError("bind() the input and output tensors first")
+        st = stream if stream is not None else torch.cuda.current_stream(workspace.device)
+        pf, pg, ph = self._ptrs
+        _check(lib().hdc_batched_execute(self._h, pf.data_ptr(), pg.data_ptr(), ph.data_ptr(), workspace.data_ptr(),
+                                         workspace.numel() * workspace.element_size(), st.cuda_stream),
+               "batched_execute")
+
+    @staticmethod
+    def status(workspace) -> int:
+        v = C.c_int()
+        _check(lib().hdc_batched_status(workspace.data_ptr(), C.byref(v)), "batched_status")
+        return v.value
+
+    def set_barrier(self, spin_limit: int, extra_arrivals: int = 0):
+        _check(lib().hdc_batched_set_barrier(self._h, int(spin_limit), int(extra_arrivals)), "batched_set_barrier")
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.hdc_batched_destroy(self._h)
             self._h = None
 
 

@@ -1,0 +1,527 @@
+// hdc_batched.cu -- many independent 1-D convolutions of uneven length in one
+// persistent launch.
+//
+// A batched plan turns n convolutions (lengths L_i, M_i = 2 L_i - 1, FFT
+// sizes m_i chosen per size class) into four lists of work items, one per
+// phase of the residue method:
+//   phase 0  fold + m1-point FFTs of column tiles       (split convolutions)
+//   phase 1  one residue of a whole row: fold, FFTs, product, inverse FFT
+//            (fused convolutions), or one m2-point row of the split ones
+//   phase 2  inverse m1-point FFTs of column tiles       (split convolutions)
+//   phase 3  unfold of a chunk of one convolution's outputs (all)
+// Every convolution's work lives in the same four phases, so one cooperative
+// launch of as many blocks as fit on the GPU runs them all: blocks claim
+// items of the current phase with an atomic counter, then meet at a grid
+// barrier before the next phase.  The barrier's spin is bounded: when it
+// runs out the block writes HDC_ERR_TIMEOUT into the status word of the
+// workspace and returns (no trap, no hang); hdc_batched_status reads it.
+// The launch (with the memset that clears the counters) can be captured in a
+// CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hdc.h"
+#include "hdc_bodies.cuh"
+#include "hdc_internal.h"
+
+#define HDC_EXPORT extern "C" __attribute__((visibility("default")))
+
+namespace hdc {
+
+template <class V> struct BConv {
+    const V* twN;
+    const V* twm;  // m-point table (fused) or m2-point table (split rows)
+    const V* twm1; // m1-point table (split columns)
+    int64_t L, N, ws_off;
+    int m, p, q, m1, m2, C, nct, per; // m1 == 0: fused; per = outputs per residue block
+    FftPlan fpm;                      // plan of m (fused) or m2 (split rows)
+    FftPlan fpm1;                     // plan of m1
+};
+
+struct BItem {
+    int conv, a, b, c;
+};
+
+// Workspace header (the first 256 bytes): phase counters, barrier, status.
+struct BHeader {
+    unsigned int ctr[4];
+    unsigned int arrive;
+    int status;
+    unsigned int pad[58];
+};
+static_assert(sizeof(BHeader) == 256, "header must stay 256 bytes");
+
+constexpr int kUnfoldChunk = 1024; // outputs per unfold item
+
+__device__ __forceinline__ bool grid_barrier(BHeader* hd, unsigned int target, long long spin_limit)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(&hd->arrive, 1u);
+        long long it = 0;
+        int ok = 1;
+        while (*(volatile unsigned int*)&hd->arrive < target) {
+            if (*(volatile int*)&hd->status != 0 || ++it > spin_limit) {
+                atomicCAS(&hd->status, 0, (int)HDC_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <class V>
+__global__ void __launch_bounds__(kMaxThreads)
+k_batched(const BConv<V>* __restrict__ convs, const BItem* __restrict__ it0, const BItem* __restrict__ it1,
+          const BItem* __restrict__ it2, const BItem* __restrict__ it3, int n0, int n1, int n2, int n3,
+          const V* const* __restrict__ fp_, const V* const* __restrict__ gp_, V* const* __restrict__ hp_, V* ws,
+          BHeader* hd, long long spin_limit, int extra_arrivals)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* smem = reinterpret_cast<V*>(smraw);
+    __shared__ int s_idx;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const BItem* lists[4] = { it0, it1, it2, it3 };
+    const int counts[4] = { n0, n1, n2, n3 };
+    for (int ph = 0; ph < 4; ++ph) {
+        const BItem* items = lists[ph];
+        const int n = counts[ph];
+        while (true) {
+            if (tid == 0) s_idx = (int)atomicAdd(&hd->ctr[ph], 1u);
+            __syncthreads();
+            const int idx = s_idx;
+            __syncthreads();
+            if (idx >= n) break;
+            const BItem itm = items[idx];
+            const BConv<V>& cv = convs[itm.conv];
+            V* cws = ws + cv.ws_off;
+            if (ph == 0) {
+                // (conv, r, which, column tile): yf/yg [r][l1][c]
+                const int r = itm.a, which = itm.b, ct = itm.c;
+                const V* x = which ? gp_[itm.conv] : fp_[itm.conv];
+                V* yb = cws + (int64_t)which * cv.q * cv.m + (int64_t)r * cv.m;
+                fold_fft_cols_body<V>(x, yb, cv.m2, cv.m1, cv.p, cv.q, cv.N, cv.m2, 1, cv.L, r, (int64_t)ct * cv.C,
+                                      cv.C, 1, cv.twN, cv.twm1, cv.fpm1, smem, tid, nthr);
+            } else if (ph == 1) {
+                if (cv.m1 == 0) {
+                    const int r = itm.a;
+                    residue_row_body<V>(fp_[itm.conv], gp_[itm.conv], cws + (int64_t)r * cv.m, cv.L, cv.m, cv.p,
+                                        cv.q, r, cv.twN, cv.twm, cv.fpm, smem, tid, nthr);
+                } else {
+                    const int64_t row = itm.a;
+                    V* yf = cws + row * cv.m2;
+                    const V* yg = cws + (int64_t)cv.q * cv.m + row * cv.m2;
+                    residue_row_body<V>(yf, yg, yf, cv.m2, cv.m2, 1, 1, 0, cv.twm, cv.twm, cv.fpm, smem, tid, nthr);
+                }
+            } else if (ph == 2) {
+                const int r = itm.a, ct = itm.c;
+                ifft_cols_body<V>(cws + (int64_t)r * cv.m, cv.m2, cv.m1, cv.q, cv.N, (int64_t)ct * cv.C, cv.C, 1,
+                                  cv.twN, cv.twm1, cv.fpm1, smem, tid, nthr);
+            } else {
+                const int64_t e0 = (int64_t)itm.a * kUnfoldChunk;
+                const int64_t e1 = min((int64_t)cv.per, e0 + kUnfoldChunk);
+                const int64_t Cn = cv.m1 ? cv.m2 : 1;
+                const int64_t ma = cv.m1 ? cv.m1 : cv.m;
+                const int64_t cs = cv.m1 ? cv.m2 : 1;
+                const int64_t cc = cv.m1 ? 1 : 0;
+                using T = typename real_of<V>::type;
+                for (int64_t e = e0 + tid; e < e1; e += nthr) {
+                    const int64_t i = e / Cn, c = e - i * Cn;
+                    unfold_elem<V, 4>(hp_[itm.conv], cws, cv.m, Cn, ma, i, c, cv.p, cv.q, cv.N, cs, cc, cv.L, 0,
+                                      cv.q, 1, 1, (T)(1.0 / (double)cv.N), cv.twN);
+                }
+            }
+        }
+        if (ph < 3) {
+            const unsigned int target = (unsigned int)(gridDim.x * (ph + 1)) + (unsigned int)extra_arrivals;
+            if (!grid_barrier(hd, target, spin_limit)) return;
+        }
+    }
+}
+
+} // namespace hdc
+
+using namespace hdc;
+
+struct hdc_batched {
+    int dtype;
+    int64_t n;
+    std::vector<int64_t> L, m, p, q, m1, m2;
+    void* d_conv = nullptr;
+    void* d_items[4] = { nullptr, nullptr, nullptr, nullptr };
+    int nitems[4] = { 0, 0, 0, 0 };
+    size_t ws = 0;     // bytes, header included
+    size_t smem = 0;   // dynamic shared memory of the launch
+    int grid = 0;
+    long long spin_limit = 1LL << 26;
+    int extra_arrivals = 0;
+};
+
+namespace {
+
+constexpr int64_t kBatchedSmem = 96 * 1024;
+
+template <typename T> int64_t batched_col_elems() { return kBatchedSmem / (2 * (int64_t)sizeof(cx<T>)); }
+
+// Route of one convolution in the batched kernel: fused when m fits one
+// row tile; otherwise m = m1 m2 with the largest m2 <= max_row and
+// m1 <= the column budget.  Returns false if neither fits.
+template <typename T> bool batched_route(int64_t m, int64_t* m1, int64_t* m2)
+{
+    if (m <= max_row_fft<T>()) { *m1 = 0; *m2 = m; return true; }
+    for (int64_t d = max_row_fft<T>(); d >= 2; --d)
+        if (m % d == 0 && m / d <= batched_col_elems<T>()) { *m1 = m / d; *m2 = d; return true; }
+    return false;
+}
+
+template <typename T> int col_tile_b(int64_t Cn, int64_t ma)
+{
+    int64_t C = 16;
+    while (C > 1 && ma * C > batched_col_elems<T>()) C >>= 1;
+    while (C > 1 && C / 2 >= Cn) C >>= 1;
+    return (int)C;
+}
+
+void free_plan(hdc_batched* b)
+{
+    if (!b) return;
+    cudaFree(b->d_conv);
+    for (auto& p : b->d_items) cudaFree(p);
+    delete b;
+}
+
+template <typename T> int build(hdc_batched* b)
+{
+    using V = cx<T>;
+    std::vector<BConv<V>> convs((size_t)b->n);
+    std::vector<BItem> items[4];
+    std::vector<std::pair<double, int64_t>> cost;
+    int64_t off = 0;
+    size_t smem = 0;
+    b->m1.assign(b->n, 0);
+    b->m2.assign(b->n, 0);
+    for (int64_t i = 0; i < b->n; ++i) {
+        BConv<V> cv;
+        memset(&cv, 0, sizeof cv);
+        int64_t m1 = 0, m2 = 0;
+        if (!batched_route<T>(b->m[i], &m1, &m2)) return HDC_ERR_UNSUPPORTED_SIZE;
+        cudaError_t e = cudaSuccess;
+        cv.L = b->L[i];
+        cv.m = (int)b->m[i];
+        cv.p = (int)b->p[i];
+        cv.q = (int)b->q[i];
+        cv.N = b->q[i] * b->m[i];
+        cv.m1 = (int)m1;
+        cv.m2 = (int)m2;
+        cv.twN = twiddles<T>(cv.N, &e);
+        if (e != cudaSuccess) return HDC_ERR_CUDA;
+        cv.twm = twiddles<T>(m1 ? m2 : b->m[i], &e);
+        if (e != cudaSuccess) return HDC_ERR_CUDA;
+        cv.fpm = make_fft_plan(m1 ? m2 : b->m[i]);
+        if (m1) {
+            cv.twm1 = twiddles<T>(m1, &e);
+            if (e != cudaSuccess) return HDC_ERR_CUDA;
+            cv.fpm1 = make_fft_plan(m1);
+            cv.C = col_tile_b<T>(m2, m1);
+            cv.nct = (int)((m2 + cv.C - 1) / cv.C);
+        }
+        cv.per = cv.m;
+        cv.ws_off = off;
+        off += ((m1 ? 2 : 1) * b->q[i] * b->m[i] + 31) / 32 * 32;
+        b->m1[i] = m1;
+        b->m2[i] = m2;
+        convs[(size_t)i] = cv;
+        smem = std::max(smem, (size_t)(3 * (m1 ? m2 : b->m[i])) * sizeof(V));
+        if (m1) smem = std::max(smem, (size_t)(2 * m1 * cv.C) * sizeof(V));
+        cost.emplace_back((double)cv.q * cv.m * std::log2((double)cv.m + 1.0) + (double)cv.q * cv.L, i);
+    }
+    // largest convolutions first in every phase: the tail of each phase is
+    // made of small items
+    std::sort(cost.begin(), cost.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    for (auto& ce : cost) {
+        const int64_t i = ce.second;
+        const BConv<V>& cv = convs[(size_t)i];
+        const int ci = (int)i;
+        if (cv.m1) {
+            for (int r = 0; r < cv.q; ++r)
+                for (int w = 0; w < 2; ++w)
+                    for (int ct = 0; ct < cv.nct; ++ct) items[0].push_back({ ci, r, w, ct });
+            for (int row = 0; row < cv.q * cv.m1; ++row) items[1].push_back({ ci, row, 0, 0 });
+            for (int r = 0; r < cv.q; ++r)
+                for (int ct = 0; ct < cv.nct; ++ct) items[2].push_back({ ci, r, 0, ct });
+        } else {
+            for (int r = 0; r < cv.q; ++r) items[1].push_back({ ci, r, 0, 0 });
+        }
+        const int nch = (cv.per + kUnfoldChunk - 1) / kUnfoldChunk;
+        for (int k = 0; k < nch; ++k) items[3].push_back({ ci, k, 0, 0 });
+    }
+    if (cudaMalloc(&b->d_conv, convs.size() * sizeof(BConv<V>)) != cudaSuccess) return HDC_ERR_ALLOC;
+    if (cudaMemcpy(b->d_conv, convs.data(), convs.size() * sizeof(BConv<V>), cudaMemcpyHostToDevice) != cudaSuccess)
+        return HDC_ERR_CUDA;
+    for (int ph = 0; ph < 4; ++ph) {
+        b->nitems[ph] = (int)items[ph].size();
+        if (items[ph].empty()) continue;
+        if (cudaMalloc(&b->d_items[ph], items[ph].size() * sizeof(BItem)) != cudaSuccess) return HDC_ERR_ALLOC;
+        if (cudaMemcpy(b->d_items[ph], items[ph].data(), items[ph].size() * sizeof(BItem), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return HDC_ERR_CUDA;
+    }
+    b->ws = sizeof(BHeader) + (size_t)off * sizeof(V) + 256;
+    b->smem = std::max(smem, (size_t)1024);
+    auto kern = k_batched<V>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem) != cudaSuccess)
+        return HDC_ERR_CUDA;
+    int per_sm = 0, dev = 0, nsm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMaxThreads, b->smem) != cudaSuccess)
+        return HDC_ERR_CUDA;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (per_sm < 1 || nsm < 1) return HDC_ERR_UNSUPPORTED_SIZE;
+    b->grid = per_sm * nsm;
+    return HDC_OK;
+}
+
+template <typename T>
+int launch(hdc_batched* b, const void* const* f, const void* const* g, void* const* h, void* ws, cudaStream_t st)
+{
+    using V = cx<T>;
+    uintptr_t base = ((uintptr_t)ws + 255) & ~(uintptr_t)255;
+    BHeader* hd = (BHeader*)base;
+    V* data = (V*)(base + sizeof(BHeader));
+    if (cudaMemsetAsync(hd, 0, sizeof(BHeader), st) != cudaSuccess) return HDC_ERR_CUDA;
+    double flops = 0.0;
+    for (int64_t i = 0; i < b->n; ++i) {
+        const double md = (double)b->m[i];
+        flops += (double)b->q[i] * (15.0 * md * std::log2(md > 1 ? md : 2) + 6.0 * md + 24.0 * b->L[i]) +
+                 2.0 * b->L[i];
+    }
+    LaunchScope ls(K_BATCHED, st, flops, 0.0);
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3((unsigned)b->grid);
+    cfg.blockDim = dim3(kMaxThreads);
+    cfg.dynamicSmemBytes = b->smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const BConv<V>* cv = (const BConv<V>*)b->d_conv;
+    const BItem* i0 = (const BItem*)b->d_items[0];
+    const BItem* i1 = (const BItem*)b->d_items[1];
+    const BItem* i2 = (const BItem*)b->d_items[2];
+    const BItem* i3 = (const BItem*)b->d_items[3];
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_batched<V>, cv, i0, i1, i2, i3, b->nitems[0], b->nitems[1],
+                                       b->nitems[2], b->nitems[3], (const V* const*)f, (const V* const*)g,
+                                       (V* const*)h, data, hd, b->spin_limit, b->extra_arrivals);
+    return e == cudaSuccess ? HDC_OK : HDC_ERR_CUDA;
+}
+
+} // namespace
+
+HDC_EXPORT int hdc_batched_create(hdc_batched** out, int64_t n, const int64_t* L, const int64_t* m, int dtype)
+{
+    if (!out || n < 1 || !L || !m) return HDC_ERR_PARAM;
+    if (dtype != HDC_C64 && dtype != HDC_C128) return HDC_ERR_DTYPE;
+    hdc_batched* b = new (std::nothrow) hdc_batched;
+    if (!b) return HDC_ERR_ALLOC;
+    b->dtype = dtype;
+    b->n = n;
+    b->L.assign(L, L + n);
+    b->m.assign(m, m + n);
+    b->p.resize(n);
+    b->q.resize(n);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t Dv = 0;
+        int rc = hdc_validate_axis(L[i], 2 * L[i] - 1, m[i], 0, 0, 0, dtype, &b->p[i], &b->q[i], &Dv);
+        if (rc != HDC_OK) { free_plan(b); return rc; }
+    }
+    int rc = dtype == HDC_C128 ? build<double>(b) : build<float>(b);
+    if (rc != HDC_OK) { free_plan(b); return rc; }
+    *out = b;
+    return HDC_OK;
+}
+
+HDC_EXPORT size_t hdc_batched_workspace(const hdc_batched* b) { return b ? b->ws : 0; }
+
+HDC_EXPORT int hdc_batched_params(const hdc_batched* b, int64_t* m, int64_t* p, int64_t* q, int64_t* m1, int64_t* m2)
+{
+    if (!b) return HDC_ERR_PARAM;
+    for (int64_t i = 0; i < b->n; ++i) {
+        if (m) m[i] = b->m[i];
+        if (p) p[i] = b->p[i];
+        if (q) q[i] = b->q[i];
+        if (m1) m1[i] = b->m1[i];
+        if (m2) m2[i] = b->m2[i];
+    }
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_batched_execute(hdc_batched* b, const void* const* f, const void* const* g, void* const* h,
+                                   void* workspace, size_t ws_bytes, void* stream)
+{
+    if (!b || !f || !g || !h) return HDC_ERR_PARAM;
+    if (!workspace || ws_bytes < b->ws) return HDC_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    return b->dtype == HDC_C128 ? launch<double>(b, f, g, h, workspace, st) : launch<float>(b, f, g, h, workspace, st);
+}
+
+HDC_EXPORT int hdc_batched_status(const void* workspace, int* status)
+{
+    if (!workspace || !status) return HDC_ERR_PARAM;
+    uintptr_t base = ((uintptr_t)workspace + 255) & ~(uintptr_t)255;
+    int v = 0;
+    if (cudaMemcpy(&v, (const void*)(base + offsetof(BHeader, status)), sizeof v, cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+        return HDC_ERR_CUDA;
+    *status = v;
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_batched_set_barrier(hdc_batched* b, long long spin_limit, int extra_arrivals)
+{
+    if (!b || spin_limit < 1 || extra_arrivals < 0) return HDC_ERR_PARAM;
+    b->spin_limit = spin_limit;
+    b->extra_arrivals = extra_arrivals;
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_batched_destroy(hdc_batched* b)
+{
+    free_plan(b);
+    return HDC_OK;
+}
+
+// ------------------------------------------------------------- tuning
+
+namespace {
+
+// Size class of a length: floor(log2 L).
+int size_class(int64_t L)
+{
+    int k = 0;
+    while ((L >> (k + 1)) > 0) ++k;
+    return k;
+}
+
+template <typename T> bool batched_ok(int64_t m)
+{
+    int64_t a = 0, b = 0;
+    return batched_route<T>(m, &a, &b);
+}
+
+} // namespace
+
+HDC_EXPORT int hdc_batched_tune(int64_t n, const int64_t* L, int dtype, const void* const* f_host,
+                                const void* const* g_host, void* const* h_host, int reps, int max_cands,
+                                void* stream, int64_t* m_out, double* ms_out)
+{
+    if (n < 1 || !L || !f_host || !g_host || !h_host || !m_out || reps < 1 || max_cands < 1) return HDC_ERR_PARAM;
+    if (dtype != HDC_C64 && dtype != HDC_C128) return HDC_ERR_DTYPE;
+    cudaStream_t st = (cudaStream_t)stream;
+    // classes, their members and candidate m (of the longest member)
+    std::vector<std::vector<int64_t>> members(64);
+    for (int64_t i = 0; i < n; ++i) {
+        if (L[i] < 1) return HDC_ERR_PARAM;
+        members[size_class(L[i])].push_back(i);
+    }
+    std::vector<int> order;
+    std::vector<std::vector<int64_t>> cands(64);
+    std::vector<double> work(64, 0.0);
+    for (int k = 0; k < 64; ++k) {
+        if (members[k].empty()) continue;
+        int64_t Lmax = 0;
+        for (int64_t i : members[k]) { Lmax = std::max(Lmax, L[i]); work[k] += (double)L[i]; }
+        int64_t nc = 0;
+        hdc_tune_candidates(Lmax, 2 * Lmax - 1, dtype, 1.5, 16, nullptr, 0, &nc);
+        std::vector<hdc_tuple> cand((size_t)std::max<int64_t>(nc, 1));
+        hdc_tune_candidates(Lmax, 2 * Lmax - 1, dtype, 1.5, 16, cand.data(), nc, &nc);
+        for (int64_t c = 0; c < nc && (int64_t)cands[k].size() < max_cands; ++c) {
+            const int64_t m = cand[(size_t)c].m;
+            if (dtype == HDC_C128 ? batched_ok<double>(m) : batched_ok<float>(m)) cands[k].push_back(m);
+        }
+        if (cands[k].empty()) return HDC_ERR_UNSUPPORTED_SIZE;
+        for (int64_t i : members[k]) m_out[i] = cands[k][0]; // least model flops to start
+        order.push_back(k);
+    }
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+    void* dptr = nullptr;
+    if (cudaMalloc(&dptr, 3 * (size_t)n * sizeof(void*)) != cudaSuccess) return HDC_ERR_ALLOC;
+    const void** pf = (const void**)dptr;
+    const void** pg = pf + n;
+    void** ph = (void**)(pg + n);
+    cudaMemcpy(pf, f_host, n * sizeof(void*), cudaMemcpyHostToDevice);
+    cudaMemcpy(pg, g_host, n * sizeof(void*), cudaMemcpyHostToDevice);
+    cudaMemcpy(ph, h_host, n * sizeof(void*), cudaMemcpyHostToDevice);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    void* ws = nullptr;
+    size_t ws_cap = 0;
+    int rc = HDC_OK;
+    // time the whole batch with the current assignment (median of reps)
+    auto time_all = [&](double* out) -> int {
+        hdc_batched* b = nullptr;
+        int r = hdc_batched_create(&b, n, L, m_out, dtype);
+        if (r != HDC_OK) return r;
+        if (b->ws > ws_cap) {
+            cudaFree(ws);
+            ws = nullptr;
+            ws_cap = 0;
+            if (cudaMalloc(&ws, b->ws) != cudaSuccess) { hdc_batched_destroy(b); return HDC_ERR_ALLOC; }
+            ws_cap = b->ws;
+        }
+        hdc_batched_execute(b, pf, pg, ph, ws, ws_cap, st);
+        std::vector<float> ts;
+        for (int k = 0; k < reps; ++k) {
+            cudaEventRecord(e0, st);
+            hdc_batched_execute(b, pf, pg, ph, ws, ws_cap, st);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            ts.push_back(t);
+        }
+        int stt = 0;
+        hdc_batched_status(ws, &stt);
+        hdc_batched_destroy(b);
+        if (stt != 0) return stt;
+        std::sort(ts.begin(), ts.end());
+        *out = ts[ts.size() / 2];
+        return HDC_OK;
+    };
+    double best = 0.0;
+    rc = time_all(&best);
+    // one class at a time, largest work first, the others held (Section 4.2)
+    for (int k : order) {
+        if (rc != HDC_OK) break;
+        int64_t bestm = cands[k][0];
+        for (size_t c = 1; c < cands[k].size(); ++c) {
+            for (int64_t i : members[k]) m_out[i] = cands[k][c];
+            double t = 0.0;
+            const int r = time_all(&t);
+            if (r == HDC_OK && t < best) { best = t; bestm = cands[k][c]; }
+        }
+        for (int64_t i : members[k]) m_out[i] = bestm;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(ws);
+    cudaFree(dptr);
+    if (ms_out) *ms_out = best;
+    return rc;
+}

@@ -1,0 +1,181 @@
+// hdc_bodies.cuh -- block-level bodies of the residue kernels, shared by the
+// one-pass kernels (hdc_kernels.cu) and the persistent batched kernel
+// (hdc_batched.cu).  Every body is executed by all threads of a block,
+// works in the shared memory it is given, and ends with a barrier so the
+// block may run the next body on the same shared memory.
+#pragma once
+
+#include "hdc_fft.cuh"
+
+namespace hdc {
+
+// One residue r of one row: fold (Eq. 1 inner sum, then zeta_N^{r s}) of f
+// and g, m-point forward FFTs, pointwise product (Section 2.4), inverse FFT
+// (Eq. 2 inner sum); the unscaled result goes to hr[0..m).  smem: 3 m.
+// With p = q = 1 and L >= m the fold is a plain copy of the rows.
+template <class V>
+__device__ __forceinline__ void residue_row_body(const V* fr, const V* gr, V* hr, int64_t L, int m, int p, int q,
+                                                 int r, const V* __restrict__ twN, const V* __restrict__ twm,
+                                                 const FftPlan& fp, V* smem, int tid, int nthr)
+{
+    V* sa = smem;
+    V* sb = sa + m;
+    V* sc = sb + m;
+    if (p == 1 && q == 1 && L >= m) {
+        for (int s = tid; s < m; s += nthr) {
+            sa[s] = fr[s];
+            sb[s] = gr[s];
+        }
+    } else {
+        for (int s = tid; s < m; s += nthr) {
+            V af = czero<V>(), ag = czero<V>();
+            for (int t = 0; t < p; ++t) {
+                const int64_t j = (int64_t)t * m + s;
+                if (j >= L) break;
+                const V fv = fr[j], gv = gr[j];
+                if (r == 0) {
+                    af = cadd(af, fv);
+                    ag = cadd(ag, gv);
+                } else {
+                    const V w = __ldg(twN + (((int64_t)r * t) % q) * m);
+                    af = cfma(fv, w, af);
+                    ag = cfma(gv, w, ag);
+                }
+            }
+            if (r != 0) {
+                const V w = __ldg(twN + (int64_t)r * s);
+                af = cmul(af, w);
+                ag = cmul(ag, w);
+            }
+            sa[s] = af;
+            sb[s] = ag;
+        }
+    }
+    __syncthreads();
+    fft_smem<V, false>(sa, sc, fp, 1, 1, m, twm, tid, nthr);
+    fft_smem<V, false>(sb, sc, fp, 1, 1, m, twm, tid, nthr);
+    for (int s = tid; s < m; s += nthr) sa[s] = cmul(sa[s], sb[s]);
+    __syncthreads();
+    fft_smem<V, true>(sa, sc, fp, 1, 1, m, twm, tid, nthr);
+    for (int s = tid; s < m; s += nthr) hr[s] = sa[s];
+    __syncthreads();
+}
+
+// Fold along a strided axis and FFT of size ma over it, for the columns
+// c0 .. c0+C-1 (< Cn) of one input x (view x[a][c], a = t ma + i, element
+// valid iff a Cn + c < Lvalid); residue r; result to yb[l][c] (row length
+// Cn), times zeta_{Nf/q}^{l c} if post.  smem: 2 ma C.
+template <class V>
+__device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn, int ma, int p, int q, int64_t Nf,
+                                                   int64_t cs, int64_t cc, int64_t Lvalid, int r, int64_t c0, int C,
+                                                   int post, const V* __restrict__ twNf,
+                                                   const V* __restrict__ twma, const FftPlan& fp, V* smem, int tid,
+                                                   int nthr)
+{
+    V* buf = smem;
+    V* tmp = buf + ma * C;
+    const int64_t mq = Nf / q;
+    for (int e = tid; e < ma * C; e += nthr) {
+        const int i = e / C, cl = e - i * C;
+        const int64_t c = c0 + cl;
+        V acc = czero<V>();
+        if (c < Cn) {
+            for (int t = 0; t < p; ++t) {
+                const int64_t lin = ((int64_t)t * ma + i) * Cn + c;
+                if (lin >= Lvalid) break;
+                const V xv = x[lin];
+                if (r == 0) acc = cadd(acc, xv);
+                else acc = cfma(xv, __ldg(twNf + (((int64_t)r * t) % q) * mq), acc);
+            }
+            if (r != 0) acc = cmul(acc, __ldg(twNf + (int64_t)r * (i * cs + c * cc)));
+        }
+        buf[e] = acc;
+    }
+    __syncthreads();
+    if (ma > 1) fft_smem<V, false>(buf, tmp, fp, C, C, 1, twma, tid, nthr);
+    for (int e = tid; e < ma * C; e += nthr) {
+        const int l = e / C, cl = e - l * C;
+        const int64_t c = c0 + cl;
+        if (c >= Cn) continue;
+        V v = buf[e];
+        if (post && l != 0 && c != 0) v = cmul(v, __ldg(twNf + (int64_t)l * c * q));
+        yb[(int64_t)l * Cn + c] = v;
+    }
+    __syncthreads();
+}
+
+// Inverse FFT of size ma along the strided axis of yb[l][c] (row length Cn)
+// for columns c0 .. c0+C-1, in place, after multiplying by
+// conj(zeta_{Nf/q}^{l c}) if pre.  smem: 2 ma C.
+template <class V>
+__device__ __forceinline__ void ifft_cols_body(V* yb, int64_t Cn, int ma, int q, int64_t Nf, int64_t c0, int C,
+                                               int pre, const V* __restrict__ twNf, const V* __restrict__ twma,
+                                               const FftPlan& fp, V* smem, int tid, int nthr)
+{
+    V* buf = smem;
+    V* tmp = buf + ma * C;
+    for (int e = tid; e < ma * C; e += nthr) {
+        const int l = e / C, cl = e - l * C;
+        const int64_t c = c0 + cl;
+        V v = czero<V>();
+        if (c < Cn) {
+            v = yb[(int64_t)l * Cn + c];
+            if (pre && l != 0 && c != 0) v = cmulc(v, __ldg(twNf + (int64_t)l * c * q));
+        }
+        buf[e] = v;
+    }
+    __syncthreads();
+    if (ma > 1) fft_smem<V, true>(buf, tmp, fp, C, C, 1, twma, tid, nthr);
+    for (int e = tid; e < ma * C; e += nthr) {
+        const int s = e / C, cl = e - s * C;
+        const int64_t c = c0 + cl;
+        if (c < Cn) yb[(int64_t)s * Cn + c] = buf[e];
+    }
+    __syncthreads();
+}
+
+// Unfold of one element (i, c) of one row: out[(t ma + i) Cn + c] for every
+// t < p with index < Lvalid gets sum_{rr < Dg} conj(zeta_Nf^{r (i cs + c cc)})
+// conj(zeta_q^{r t}) h_rr[i][c] (h_rr = h + rr * hstride), residues r = r0 + rr
+// in increasing order; added to the previous contents unless first, scaled if
+// last.  PT outputs are accumulated per sweep over the residues.
+template <class V, int PT>
+__device__ __forceinline__ void unfold_elem(V* ob, const V* __restrict__ h, int64_t hstride, int64_t Cn,
+                                            int64_t ma, int64_t i, int64_t c, int p, int q, int64_t Nf, int64_t cs,
+                                            int64_t cc, int64_t Lvalid, int r0, int Dg, int first, int last,
+                                            typename real_of<V>::type scale, const V* __restrict__ twNf)
+{
+    const int64_t mq = Nf / q;
+    for (int t0 = 0; t0 < p; t0 += PT) {
+        if ((((int64_t)t0 * ma + i) * Cn + c) >= Lvalid) break;
+        V acc[PT];
+#pragma unroll
+        for (int tt = 0; tt < PT; ++tt) acc[tt] = czero<V>();
+        for (int rr = 0; rr < Dg; ++rr) {
+            const int r = r0 + rr;
+            V hv = h[(int64_t)rr * hstride + i * Cn + c];
+            if (r != 0) hv = cmulc(hv, __ldg(twNf + (int64_t)r * (i * cs + c * cc)));
+#pragma unroll
+            for (int tt = 0; tt < PT; ++tt) {
+                const int t = t0 + tt;
+                if (t < p) {
+                    if (r == 0 || t == 0) acc[tt] = cadd(acc[tt], hv);
+                    else acc[tt] = cfmac(hv, __ldg(twNf + (((int64_t)r * t) % q) * mq), acc[tt]);
+                }
+            }
+        }
+#pragma unroll
+        for (int tt = 0; tt < PT; ++tt) {
+            const int t = t0 + tt;
+            if (t >= p) break;
+            const int64_t lin = ((int64_t)t * ma + i) * Cn + c;
+            if (lin >= Lvalid) break;
+            V v = acc[tt];
+            if (!first) v = cadd(v, ob[lin]);
+            if (last) v = cscale(v, scale);
+            ob[lin] = v;
+        }
+    }
+}
+
+} // namespace hdc

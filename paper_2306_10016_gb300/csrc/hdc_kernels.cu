@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "hdc_bodies.cuh"
 #include "hdc_internal.h"
 
 namespace hdc {
@@ -73,54 +74,10 @@ k_residue_rows(const V* f, const V* g, V* h, int64_t B, int64_t ld_in, int64_t L
                FftPlan fp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    V* sa = reinterpret_cast<V*>(smraw);
-    V* sb = sa + m;
-    V* sc = sb + m;
     const int64_t b = blockIdx.x % B;
     const int rr = (int)(blockIdx.x / B);
-    const int r = r0 + rr;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const V* fr = f + b * ld_in;
-    const V* gr = g + b * ld_in;
-    // fold: w_r[s] = zeta_N^{r s} sum_t zeta_q^{r t} x[t m + s]   (Eq. 1)
-    if (p == 1 && q == 1 && L >= m) {
-        // plain copy (rows of a split transform): no arithmetic
-        for (int s = tid; s < m; s += nthr) {
-            sa[s] = fr[s];
-            sb[s] = gr[s];
-        }
-    } else
-    for (int s = tid; s < m; s += nthr) {
-        V af = czero<V>(), ag = czero<V>();
-        for (int t = 0; t < p; ++t) {
-            const int64_t j = (int64_t)t * m + s;
-            if (j >= L) break;
-            const V fv = fr[j], gv = gr[j];
-            if (r == 0) {
-                af = cadd(af, fv);
-                ag = cadd(ag, gv);
-            } else {
-                const V w = __ldg(twN + (((int64_t)r * t) % q) * m);
-                af = cfma(fv, w, af);
-                ag = cfma(gv, w, ag);
-            }
-        }
-        if (r != 0) {
-            const V w = __ldg(twN + (int64_t)r * s);
-            af = cmul(af, w);
-            ag = cmul(ag, w);
-        }
-        sa[s] = af;
-        sb[s] = ag;
-    }
-    __syncthreads();
-    fft_smem<V, false>(sa, sc, fp, 1, 1, m, twm, tid, nthr);
-    fft_smem<V, false>(sb, sc, fp, 1, 1, m, twm, tid, nthr);
-    for (int s = tid; s < m; s += nthr) sa[s] = cmul(sa[s], sb[s]);
-    __syncthreads();
-    fft_smem<V, true>(sa, sc, fp, 1, 1, m, twm, tid, nthr);
-    V* hr = h + ((int64_t)rr * B + b) * m;
-    for (int s = tid; s < m; s += nthr) hr[s] = sa[s];
+    residue_row_body<V>(f + b * ld_in, g + b * ld_in, h + ((int64_t)rr * B + b) * m, L, m, p, q, r0 + rr, twN, twm,
+                        fp, reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
 }
 
 template <typename T>
@@ -171,8 +128,6 @@ k_fold_fft_cols(const V* __restrict__ f, const V* __restrict__ g, V* yf, V* yg, 
                 const V* __restrict__ twNf, const V* __restrict__ twma, FftPlan fp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    V* buf = reinterpret_cast<V*>(smraw);
-    V* tmp = buf + ma * C;
     int64_t blk = blockIdx.x;
     const int ct = (int)(blk % nct);
     blk /= nct;
@@ -180,39 +135,10 @@ k_fold_fft_cols(const V* __restrict__ f, const V* __restrict__ g, V* yf, V* yg, 
     blk /= Dg;
     const int which = (int)(blk & 1);
     const int64_t b = blk >> 1;
-    const int r = r0 + rr;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int64_t c0 = (int64_t)ct * C;
     const V* x = (which ? g : f) + b * bstride;
-    V* y = which ? yg : yf;
-    const int64_t mq = Nf / q;
-    for (int e = tid; e < ma * C; e += nthr) {
-        const int i = e / C, cl = e - i * C;
-        const int64_t c = c0 + cl;
-        V acc = czero<V>();
-        if (c < Cn) {
-            for (int t = 0; t < p; ++t) {
-                const int64_t lin = ((int64_t)t * ma + i) * Cn + c;
-                if (lin >= Lvalid) break;
-                const V xv = x[lin];
-                if (r == 0) acc = cadd(acc, xv);
-                else acc = cfma(xv, __ldg(twNf + (((int64_t)r * t) % q) * mq), acc);
-            }
-            if (r != 0) acc = cmul(acc, __ldg(twNf + (int64_t)r * (i * cs + c * cc)));
-        }
-        buf[e] = acc;
-    }
-    __syncthreads();
-    if (ma > 1) fft_smem<V, false>(buf, tmp, fp, C, C, 1, twma, tid, nthr);
-    V* yb = y + ((int64_t)rr * B + b) * ma * Cn;
-    for (int e = tid; e < ma * C; e += nthr) {
-        const int l = e / C, cl = e - l * C;
-        const int64_t c = c0 + cl;
-        if (c >= Cn) continue;
-        V v = buf[e];
-        if (post && l != 0 && c != 0) v = cmul(v, __ldg(twNf + (int64_t)l * c * q));
-        yb[(int64_t)l * Cn + c] = v;
-    }
+    V* yb = (which ? yg : yf) + ((int64_t)rr * B + b) * ma * Cn;
+    fold_fft_cols_body<V>(x, yb, Cn, ma, p, q, Nf, cs, cc, Lvalid, r0 + rr, (int64_t)ct * C, C, post, twNf, twma, fp,
+                          reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
 }
 
 template <typename T>
@@ -252,33 +178,13 @@ k_ifft_cols(V* y, int64_t B, int64_t Cn, int ma, int q, int64_t Nf, int Dg, int 
             const V* __restrict__ twNf, const V* __restrict__ twma, FftPlan fp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    V* buf = reinterpret_cast<V*>(smraw);
-    V* tmp = buf + ma * C;
     int64_t blk = blockIdx.x;
     const int ct = (int)(blk % nct);
     blk /= nct;
     const int rr = (int)(blk % Dg);
     const int64_t b = blk / Dg;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int64_t c0 = (int64_t)ct * C;
-    V* yb = y + ((int64_t)rr * B + b) * ma * Cn;
-    for (int e = tid; e < ma * C; e += nthr) {
-        const int l = e / C, cl = e - l * C;
-        const int64_t c = c0 + cl;
-        V v = czero<V>();
-        if (c < Cn) {
-            v = yb[(int64_t)l * Cn + c];
-            if (pre && l != 0 && c != 0) v = cmulc(v, __ldg(twNf + (int64_t)l * c * q));
-        }
-        buf[e] = v;
-    }
-    __syncthreads();
-    if (ma > 1) fft_smem<V, true>(buf, tmp, fp, C, C, 1, twma, tid, nthr);
-    for (int e = tid; e < ma * C; e += nthr) {
-        const int s = e / C, cl = e - s * C;
-        const int64_t c = c0 + cl;
-        if (c < Cn) yb[(int64_t)s * Cn + c] = buf[e];
-    }
+    ifft_cols_body<V>(y + ((int64_t)rr * B + b) * ma * Cn, Cn, ma, q, Nf, (int64_t)ct * C, C, pre, twNf, twma, fp,
+                      reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
 }
 
 template <typename T>
@@ -321,38 +227,8 @@ k_unfold(V* out, const V* __restrict__ h, int64_t B, int64_t bstride, int64_t Cn
     const int64_t b = gid / per;
     const int64_t e = gid - b * per;
     const int64_t i = e / Cn, c = e - i * Cn;
-    const int64_t mq = Nf / q;
-    V* ob = out + b * bstride;
-    for (int t0 = 0; t0 < p; t0 += PT) {
-        if ((((int64_t)t0 * ma + i) * Cn + c) >= Lvalid) break;
-        V acc[PT];
-#pragma unroll
-        for (int tt = 0; tt < PT; ++tt) acc[tt] = czero<V>();
-        for (int rr = 0; rr < Dg; ++rr) {
-            const int r = r0 + rr;
-            V hv = h[(((int64_t)rr * B + b) * ma + i) * Cn + c];
-            if (r != 0) hv = cmulc(hv, __ldg(twNf + (int64_t)r * (i * cs + c * cc)));
-#pragma unroll
-            for (int tt = 0; tt < PT; ++tt) {
-                const int t = t0 + tt;
-                if (t < p) {
-                    if (r == 0 || t == 0) acc[tt] = cadd(acc[tt], hv);
-                    else acc[tt] = cfmac(hv, __ldg(twNf + (((int64_t)r * t) % q) * mq), acc[tt]);
-                }
-            }
-        }
-#pragma unroll
-        for (int tt = 0; tt < PT; ++tt) {
-            const int t = t0 + tt;
-            if (t >= p) break;
-            const int64_t lin = ((int64_t)t * ma + i) * Cn + c;
-            if (lin >= Lvalid) break;
-            V v = acc[tt];
-            if (!first) v = cadd(v, ob[lin]);
-            if (last) v = cscale(v, scale);
-            ob[lin] = v;
-        }
-    }
+    unfold_elem<V, PT>(out + b * bstride, h + b * per, B * per, Cn, ma, i, c, p, q, Nf, cs, cc, Lvalid, r0, Dg, first,
+                       last, scale, twNf);
 }
 
 template <typename T>
