@@ -350,7 +350,7 @@ def main():
         gs = [ga[offs[i]:offs[i + 1]] for i in range(nconv)]
         hs = [ha[offs[i]:offs[i + 1]] for i in range(nconv)]
         t0 = time.perf_counter()
-        ms_t, _ = hdc.batched_tune(fs, gs, hs, reps=2, max_cands=6)
+        ms_t, _ = hdc.batched_tune(fs, gs, hs, reps=3, max_cands=8)
         tune_b = time.perf_counter() - t0
         res = {}
         for name, mlist in (("tuned", ms_t), ("explicit", [hdc.next_good_size(2 * L - 1) for L in Ls])):
@@ -394,6 +394,73 @@ def main():
     batched32 = batched_run(torch.complex64, hdc.HDC_C64)
     batched32["roofline_frac"] = round(batched32["tuned"]["model_tflops"] / (
         SM_COUNT * FP32_FMA_PER_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12), 4)
+
+    # --- N-D and Hermitian configurations (FP64): tuned 2-D 1024^2 and 3-D
+    # 128^3, and the centered Hermitian 2-D convolution of 1024^2 real fields
+    # (K = 512 modes per axis, padding 3/2); each timed as graph replays
+    peak64 = SM_COUNT * FP64_FMA_PER_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+    def graph_time(run, steps):
+        side = torch.cuda.Stream(dev)
+        with torch.cuda.stream(side):
+            for _ in range(max(1, args.warmup)):
+                run(side)
+        torch.cuda.synchronize(dev)
+        hdc.stats_reset()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side):
+            run(side)
+        fl = sum(v["flops"] for v in hdc.stats().values())
+        st = torch.cuda.current_stream(dev)
+        ev = []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            graph.replay()
+            e1.record(st)
+            ev.append((e0, e1))
+        torch.cuda.synchronize(dev)
+        del graph
+        return sum(a.elapsed_time(b) for a, b in ev) / len(ev), fl
+
+    nd = {}
+    for name, shape in (("2d_1024x1024", (1024, 1024)), ("3d_128x128x128", (128, 128, 128))):
+        f = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 30, shape)).to(dev)
+        g = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 31, shape)).to(dev)
+        h = torch.empty_like(f)
+        t0 = time.perf_counter()
+        best, _ = hdc.tune(f, g, len(shape), max_ratio=1.3, reps=2)
+        tt = time.perf_counter() - t0
+        mv = [b["m"] for b in best]
+        Dv = [b["D"] for b in best]
+        nbytes = hdc.workspace_size(list(shape), [2 * x - 1 for x in shape], mv, D=Dv)
+        wsn = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        msn, fl = graph_time(lambda s_: hdc.convnd(f, g, len(shape), mv, D=Dv, out=h, workspace=wsn, stream=s_),
+                             args.steps)
+        outs_n = int(np.prod(shape))
+        nd[name] = {"value": world * outs_n / (msn * 1e-3), "ms": round(msn, 4), "m": mv, "D": Dv,
+                    "model_tflops": round(fl / (msn * 1e-3) / 1e12, 4),
+                    "roofline_frac": round(fl / (msn * 1e-3) / 1e12 / peak64, 4), "tuning_s": round(tt, 1)}
+        del f, g, h, wsn
+    K = 512
+    fh = torch.from_numpy(synth.hermitian_normal(synth.BASE_SEED + 32, K)).to(dev)
+    gh = torch.from_numpy(synth.hermitian_normal(synth.BASE_SEED + 33, K)).to(dev)
+    hh = torch.empty_like(fh)
+    herm = {}
+    for mh in (K, 3 * K // 2, 3 * K):      # q = 3, 2, 1 for M = 3K - 2
+        try:
+            msh, fl = graph_time(lambda s_: hdc.conv2d_hermitian(fh, gh, m=mh, out=hh, stream=s_), args.steps)
+        except hdc.HDCError:
+            continue
+        herm[str(mh)] = {"ms": round(msh, 4), "model_tflops": round(fl / (msh * 1e-3) / 1e12, 4)}
+    bm = min(herm, key=lambda k: herm[k]["ms"])
+    nd["hermitian_2d_K512"] = {"value": world * (2 * K - 1) * K / (herm[bm]["ms"] * 1e-3), "ms": herm[bm]["ms"],
+                               "m": int(bm), "model_tflops": herm[bm]["model_tflops"],
+                               "roofline_frac": round(herm[bm]["model_tflops"] / peak64, 4),
+                               "outputs": (2 * K - 1) * K, "by_m": herm}
+    del fh, gh, hh
 
     # --- end to end through the host-buffer C call (FP64)
     pinned = []
@@ -464,6 +531,7 @@ def main():
         "explicit": {"value": world * outs / (ms_ex * 1e-3), "ms_per_step": ms_ex,
                      "hybrid_speedup": round(ms_ex / ms64, 4)},
         "fp32": {"value": world * outs / (ms32 * 1e-3), "ms_per_step": ms32},
+        "nd_fp64": nd,
         "batched_fp64": batched64,
         "batched_fp32": batched32,
         "per_size_fp64": per_size,

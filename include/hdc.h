@@ -182,6 +182,43 @@ int hdc_convnd_host(int dims, const void* f_host, const void* g_host,
                     const int64_t* D, int dtype, int64_t batch,
                     void* dev_workspace, size_t ws_bytes, void* stream);
 
+/* Output windows (Section 3.1 read for any slice of the linear
+ * convolution): per axis, the outputs [o, o + Lw) of the full linear
+ * convolution (length 2L - 1) instead of the first L.  The window is
+ * alias-free when M >= 2L - 1 - o and o + Lw <= q m (else HDC_ERR_ALIAS);
+ * o = 0, Lw = 2L - 1 with M >= 2L - 1 gives the whole linear convolution.
+ * h: batch x prod(Lw) complex.  Same conventions as hdc_convnd (no
+ * in-place mode). */
+int hdc_workspace_size_window(int dims, const int64_t* L, const int64_t* M,
+                              const int64_t* m, const int64_t* p,
+                              const int64_t* q, const int64_t* D,
+                              const int64_t* o, const int64_t* Lw, int dtype,
+                              int64_t batch, size_t* bytes);
+int hdc_convnd_window(int dims, const void* f, const void* g, void* h,
+                      const int64_t* L, const int64_t* M, const int64_t* m,
+                      const int64_t* p, const int64_t* q, const int64_t* D,
+                      const int64_t* o, const int64_t* Lw, int dtype,
+                      int64_t batch, void* workspace, size_t ws_bytes,
+                      void* stream);
+
+/* Centered Hermitian 2-D convolution (the paper names the Hermitian case as
+ * prior work, Section 1, and future work, Section 7; this is the reading
+ * used here): f and g are the non-redundant halves of two Hermitian-
+ * symmetric spectra on |kx|, |ky| <= K-1 -- arrays (2K-1) x K, row
+ * kx + K - 1, column ky >= 0, the other half being f(-k) = conj(f(k)) --
+ * and h (same layout) gets h_k = sum_{p, k-p in the box} f_p g_{k-p} for
+ * |kx| <= K-1, 0 <= ky <= K-1: the dealiased product of two real fields.
+ * Computed as the linear convolution of the index-shifted full spectra
+ * with padding M = 3K - 2 per axis (the 3/2 ratio; m per axis, e.g. m = K
+ * gives q = 3), keeping the windows [K-1, 3K-3] and [2K-2, 3K-3].
+ * h may alias neither input. */
+int hdc_workspace_size_hermitian(int64_t K, const int64_t* m, const int64_t* D,
+                                 int dtype, int64_t batch, size_t* bytes);
+int hdc_conv2d_hermitian(const void* f, const void* g, void* h, int64_t K,
+                         const int64_t* m, const int64_t* D, int dtype,
+                         int64_t batch, void* workspace, size_t ws_bytes,
+                         void* stream);
+
 /* Free the cached twiddle tables on every device (call with no work in
  * flight that uses them). */
 int hdc_release_caches(void);
@@ -308,14 +345,15 @@ int hdc_batched_set_barrier(hdc_batched* plan, long long spin_limit,
 int hdc_batched_destroy(hdc_batched* plan);
 /* Per-size schedules (the grid search of Section 4.2 applied to the batched
  * kernel, with size classes as the separable axes): lengths are grouped by
- * floor(log2 L); every group starts at the candidate m of least model flops
- * among the first `max_cands` candidates of its longest member
- * (hdc_tune_candidates, ratio 1.5, m >= 16); then, group by group (largest
- * total length first, the others held), each candidate is timed on the
- * WHOLE batch with this kernel (`reps` timed runs, median) and the fastest
- * kept.  m_out receives every convolution's m.  f_host, g_host, h_host: HOST
- * arrays of the n device pointers.  Allocates and frees its own scratch;
- * synchronises `stream`.  *ms_out: the time of the final assignment. */
+ * floor(log2 L); a group's schedule is its residue count q (from 1, 2, 3,
+ * 4, 5, 6, 8, 10, 12, 16, the first `max_cands` usable ones) and every
+ * member gets its own m = nextgood(ceil((2 L_i - 1) / q)).  All groups start
+ * at q = 1 (explicit padding); then group by group (largest total length
+ * first, the others held) each q is timed on the WHOLE batch with this
+ * kernel (`reps` timed runs, median) and the fastest kept.  m_out receives
+ * every convolution's m.  f_host, g_host, h_host: HOST arrays of the n
+ * device pointers.  Allocates and frees its own scratch; synchronises
+ * `stream`.  *ms_out: the time of the final assignment. */
 int hdc_batched_tune(int64_t n, const int64_t* L, int dtype,
                      const void* const* f_host, const void* const* g_host,
                      void* const* h_host, int reps, int max_cands,

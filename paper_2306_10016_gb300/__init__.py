@@ -112,6 +112,12 @@ _SIGS += [
     ("hdc_batched_destroy", C.c_int, [_vp]),
     ("hdc_batched_tune", C.c_int, [_i64, _i64p, C.c_int, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.c_int,
                                    C.c_int, _vp, _i64p, C.POINTER(C.c_double)]),
+    ("hdc_workspace_size_window", C.c_int, [C.c_int, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p,
+                                            C.c_int, _i64, C.POINTER(_sz)]),
+    ("hdc_convnd_window", C.c_int, [C.c_int, _vp, _vp, _vp, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p,
+                                    C.c_int, _i64, _vp, _sz, _vp]),
+    ("hdc_workspace_size_hermitian", C.c_int, [_i64, _i64p, _i64p, C.c_int, _i64, C.POINTER(_sz)]),
+    ("hdc_conv2d_hermitian", C.c_int, [_vp, _vp, _vp, _i64, _i64p, _i64p, C.c_int, _i64, _vp, _sz, _vp]),
     ("hdc_stats_reset", C.c_int, []),
     ("hdc_stats_timing", C.c_int, [C.c_int]),
     ("hdc_stats_kernel_count", C.c_int, []),
@@ -279,6 +285,62 @@ def convnd(f, g, dims: int, m, M=None, p=0, q=0, D=0, out=None, inplace=False, w
                               workspace.data_ptr(), workspace.numel() * workspace.element_size(),
                               st.cuda_stream)
     _check(rc, "hdc_convnd")
+    return h
+
+
+def convnd_window(f, g, dims, m, o, Lw, M=None, p=0, q=0, D=0, out=None, workspace=None, stream=None):
+    """Outputs [o, o + Lw) per axis of the linear convolution of f and g
+    over their last `dims` axes (hdc_convnd_window); M defaults to 2L - 1."""
+    torch = _torch()
+    if not (f.is_cuda and g.is_cuda) or f.shape != g.shape or f.dtype != g.dtype:
+        raise ValueError("f and g must be CUDA tensors of one shape and dtype")
+    dt = dtype_code(f.dtype)
+    L = [int(x) for x in f.shape[f.dim() - dims:]]
+    lead = list(f.shape[: f.dim() - dims])
+    batch = 1
+    for x in lead:
+        batch *= int(x)
+    Mv = _per_axis(M, dims, "M") or [2 * l - 1 for l in L]
+    mv, pv, qv, Dv, ov, Lwv = (_per_axis(v, dims, n) for v, n in ((m, "m"), (p, "p"), (q, "q"), (D, "D"),
+                                                                  (o, "o"), (Lw, "Lw")))
+    h = out if out is not None else torch.empty(lead + Lwv, dtype=f.dtype, device=f.device)
+    nb = C.c_size_t()
+    _check(lib().hdc_workspace_size_window(dims, _arr(L), _arr(Mv), _arr(mv), _arr(pv), _arr(qv), _arr(Dv), _arr(ov),
+                                           _arr(Lwv), dt, batch, C.byref(nb)), "workspace_size_window")
+    if workspace is None or workspace.numel() * workspace.element_size() < nb.value:
+        workspace = torch.empty(max(1, nb.value), dtype=torch.uint8, device=f.device)
+    st = stream if stream is not None else torch.cuda.current_stream(f.device)
+    with torch.cuda.device(f.device):
+        _check(lib().hdc_convnd_window(dims, f.data_ptr(), g.data_ptr(), h.data_ptr(), _arr(L), _arr(Mv), _arr(mv),
+                                       _arr(pv), _arr(qv), _arr(Dv), _arr(ov), _arr(Lwv), dt, batch,
+                                       workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                       st.cuda_stream), "hdc_convnd_window")
+    return h
+
+
+def conv2d_hermitian(f, g, m=None, D=0, out=None, workspace=None, stream=None):
+    """Centered Hermitian 2-D convolution of half-plane spectra (2K-1, K)
+    (leading axes: batch), padding 3/2; m per axis defaults to K."""
+    torch = _torch()
+    if not (f.is_cuda and g.is_cuda) or f.shape != g.shape or f.dtype != g.dtype:
+        raise ValueError("f and g must be CUDA tensors of one shape and dtype")
+    K = int(f.shape[-1])
+    if int(f.shape[-2]) != 2 * K - 1:
+        raise ValueError("half-plane spectra have shape (2K-1, K)")
+    batch = f.numel() // ((2 * K - 1) * K)
+    dt = dtype_code(f.dtype)
+    mv = _arr(_per_axis(m if m is not None else K, 2, "m"))
+    Dv = _arr(_per_axis(D, 2, "D"))
+    h = out if out is not None else torch.empty_like(f)
+    nb = C.c_size_t()
+    _check(lib().hdc_workspace_size_hermitian(K, mv, Dv, dt, batch, C.byref(nb)), "workspace_size_hermitian")
+    if workspace is None or workspace.numel() * workspace.element_size() < nb.value:
+        workspace = torch.empty(max(1, nb.value), dtype=torch.uint8, device=f.device)
+    st = stream if stream is not None else torch.cuda.current_stream(f.device)
+    with torch.cuda.device(f.device):
+        _check(lib().hdc_conv2d_hermitian(f.data_ptr(), g.data_ptr(), h.data_ptr(), K, mv, Dv, dt, batch,
+                                          workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                          st.cuda_stream), "hdc_conv2d_hermitian")
     return h
 
 

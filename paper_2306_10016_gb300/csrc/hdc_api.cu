@@ -81,6 +81,7 @@ struct Axis {
     int64_t L, M, m, p, q, D, N;
     int64_t m1, m2; // m1 < 0: m not supported (no split within the tile limits)
     int dtype;
+    int64_t o, Lw, pout; // output window [o, o + Lw) of the linear convolution; pout = ceil((o + Lw) / m)
 };
 
 static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -162,14 +163,22 @@ static void route(const Axis& a, int64_t B, int dtype, int64_t* m1, int64_t* m2)
 static int64_t max_fft(int dtype) { return dtype == HDC_C128 ? (int64_t)1 << 24 : (int64_t)1 << 25; }
 static int64_t max_padded(int dtype) { return dtype == HDC_C128 ? (int64_t)1 << 25 : (int64_t)1 << 26; }
 
-static int resolve_axis(int64_t L, int64_t M, int64_t m, int64_t p, int64_t q, int64_t D, int dtype, Axis* out)
+// One axis.  The output window [o, o + Lw) of the full linear convolution
+// (length 2L - 1) is alias-free when the padded length reaches past every
+// output that could wrap onto the window: M >= 2L - 1 - o (o = 0, Lw = L is
+// the first-L convolution of Eq. 4 and needs M >= 2L - 1, Section 3.1).
+static int resolve_axis(int64_t L, int64_t M, int64_t m, int64_t p, int64_t q, int64_t D, int dtype, Axis* out,
+                        int64_t o = 0, int64_t Lw = -1)
 {
     if (dtype != HDC_C64 && dtype != HDC_C128) return HDC_ERR_DTYPE;
-    if (L < 1 || M < 1 || m < 1 || p < 0 || q < 0 || D < 0) return HDC_ERR_PARAM;
-    if (M < 2 * L - 1) return HDC_ERR_ALIAS;
+    if (Lw < 0) Lw = L;
+    if (L < 1 || M < 1 || m < 1 || p < 0 || q < 0 || D < 0 || o < 0 || Lw < 1) return HDC_ERR_PARAM;
+    if (o + Lw > 2 * L - 1) return HDC_ERR_PARAM;
+    if (M < 2 * L - 1 - o) return HDC_ERR_ALIAS;
     if (p == 0) p = ceil_div(L, m);
     if (q == 0) q = ceil_div(M, m);
     if (p * m < L || q * m < M) return HDC_ERR_PARAM;
+    if (o + Lw > q * m) return HDC_ERR_ALIAS;
     if (D == 0) D = q;
     if (D > q) return HDC_ERR_PARAM;
     if (!good_size(m) || m > max_fft(dtype)) return HDC_ERR_UNSUPPORTED_SIZE;
@@ -177,6 +186,7 @@ static int resolve_axis(int64_t L, int64_t M, int64_t m, int64_t p, int64_t q, i
     Axis a;
     a.L = L; a.M = M; a.m = m; a.p = p; a.q = q; a.D = D; a.N = q * m;
     a.dtype = dtype;
+    a.o = o; a.Lw = Lw; a.pout = ceil_div(o + Lw, m);
     if (dtype == HDC_C128) split_m<double>(a); else split_m<float>(a);
     if (a.m1 < 0) return HDC_ERR_UNSUPPORTED_SIZE;
     if (out) *out = a;
@@ -198,11 +208,11 @@ static int64_t ws_elems(int dims, const Axis* ax, int64_t B)
         if (m1 == 0) return a.D * B * a.m;
         return 2 * a.D * B * a.m;
     }
-    int64_t Cn = 1;
-    for (int i = 1; i < dims; ++i) Cn *= ax[i].L;
+    int64_t Cn = 1, Cw = 1;
+    for (int i = 1; i < dims; ++i) { Cn *= ax[i].L; Cw *= ax[i].Lw; }
     const Axis& a = ax[0];
     const int64_t rows = a.D * B * a.m;
-    return 3 * rows * Cn + ws_elems(dims - 1, ax + 1, rows);
+    return rows * (2 * Cn + Cw) + ws_elems(dims - 1, ax + 1, rows);
 }
 
 static size_t ws_bytes(int dims, const Axis* ax, int64_t B, size_t esz, int ncopy)
@@ -223,9 +233,10 @@ static size_t ws_bytes(int dims, const Axis* ax, int64_t B, size_t esz, int ncop
         if (_e != cudaSuccess) return _e;           \
     } while (0)
 
-// 1-D convolution of B rows (row stride ld) along a contiguous axis.
+// 1-D convolution of B rows (input row stride ld, output row stride ldo)
+// along a contiguous axis; outputs [a.o, a.o + a.Lw) of every row.
 template <typename T>
-static cudaError_t run_rows(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t B, int64_t ld,
+static cudaError_t run_rows(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t B, int64_t ld, int64_t ldo,
                             const Axis& a, cx<T>* ws, cudaStream_t st)
 {
     const double scale = 1.0 / (double)a.N;
@@ -235,8 +246,8 @@ static cudaError_t run_rows(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t 
         for (int64_t r0 = 0; r0 < a.q; r0 += a.D) {
             const int first = (r0 == 0), last = (r0 + a.D >= a.q);
             HDC_TRY(launch_residue_rows<T>(f, g, ws, B, ld, a.L, a.m, a.p, a.q, r0, a.D, st));
-            HDC_TRY(launch_unfold<T>(out, ws, B, ld, 1, a.m, a.p, a.q, a.N, 1, 0, a.L, r0, a.D, first,
-                                     last, scale, st));
+            HDC_TRY(launch_unfold<T>(out, ws, B, ldo, 1, a.m, a.pout, a.q, a.N, 1, 0, a.o, a.o + a.Lw, r0,
+                                     a.D, first, last, scale, st));
         }
         return cudaSuccess;
     }
@@ -252,28 +263,30 @@ static cudaError_t run_rows(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t 
                                         st));
         HDC_TRY(launch_residue_rows<T>(yf, yg, yf, Dg * B * m1, m2, m2, m2, 1, 1, 0, 1, st));
         HDC_TRY(launch_ifft_cols<T>(yf, B, m2, m1, a.q, a.N, Dg, 1, st));
-        HDC_TRY(launch_unfold<T>(out, yf, B, ld, m2, m1, a.p, a.q, a.N, m2, 1, a.L, r0, a.D, first, last,
-                                 scale, st));
+        HDC_TRY(launch_unfold<T>(out, yf, B, ldo, m2, m1, a.pout, a.q, a.N, m2, 1, a.o, a.o + a.Lw, r0,
+                                 a.D, first, last, scale, st));
     }
     return cudaSuccess;
 }
 
-// N-D: residues of axis 0 (strided, Cn = product of the inner extents), the
-// inner (N-1)-D convolution on every transformed row, inverse and unfold.
+// N-D: residues of axis 0 (strided, Cn = product of the inner input
+// extents, Cw of the inner output extents), the inner (N-1)-D convolution on
+// every transformed row, inverse and unfold of the window of axis 0.
 template <typename T>
 static cudaError_t run_nd(int dims, const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t B,
                           const Axis* ax, cx<T>* ws, cudaStream_t st)
 {
-    if (dims == 1) return run_rows<T>(f, g, out, B, ax[0].L, ax[0], ws, st);
-    int64_t Cn = 1;
-    for (int i = 1; i < dims; ++i) Cn *= ax[i].L;
+    if (dims == 1) return run_rows<T>(f, g, out, B, ax[0].L, ax[0].Lw, ax[0], ws, st);
+    int64_t Cn = 1, Cw = 1;
+    for (int i = 1; i < dims; ++i) { Cn *= ax[i].L; Cw *= ax[i].Lw; }
     const Axis& a = ax[0];
     const int64_t rows = a.D * B * a.m;
     cx<T>* wf = ws;
     cx<T>* wg = wf + rows * Cn;
     cx<T>* wh = wg + rows * Cn;
-    cx<T>* inner = wh + rows * Cn;
+    cx<T>* inner = wh + rows * Cw;
     const int64_t bstride = a.L * Cn;
+    const int64_t ostride = a.Lw * Cw;
     const double scale = 1.0 / (double)a.N;
     for (int64_t r0 = 0; r0 < a.q; r0 += a.D) {
         const int first = (r0 == 0), last = (r0 + a.D >= a.q);
@@ -281,9 +294,9 @@ static cudaError_t run_nd(int dims, const cx<T>* f, const cx<T>* g, cx<T>* out, 
         HDC_TRY(launch_fold_fft_cols<T>(f, g, wf, wg, B, bstride, Cn, a.m, a.p, a.q, a.N, 1, 0,
                                         a.L * Cn, r0, a.D, 0, st));
         HDC_TRY(run_nd<T>(dims - 1, wf, wg, wh, Dg * B * a.m, ax + 1, inner, st));
-        HDC_TRY(launch_ifft_cols<T>(wh, B, Cn, a.m, a.q, a.N, Dg, 0, st));
-        HDC_TRY(launch_unfold<T>(out, wh, B, bstride, Cn, a.m, a.p, a.q, a.N, 1, 0, a.L * Cn, r0, a.D,
-                                 first, last, scale, st));
+        HDC_TRY(launch_ifft_cols<T>(wh, B, Cw, a.m, a.q, a.N, Dg, 0, st));
+        HDC_TRY(launch_unfold<T>(out, wh, B, ostride, Cw, a.m, a.pout, a.q, a.N, 1, 0, a.o * Cw,
+                                 (a.o + a.Lw) * Cw, r0, a.D, first, last, scale, st));
     }
     return cudaSuccess;
 }
@@ -294,9 +307,13 @@ static int conv_nd(int dims, const void* f, const void* g, void* h, const Axis* 
 {
     using V = cx<T>;
     int64_t tot = 1;
-    for (int i = 0; i < dims; ++i) tot *= ax[i].L;
+    bool same_shape = true;
+    for (int i = 0; i < dims; ++i) {
+        tot *= ax[i].L;
+        same_shape = same_shape && ax[i].o == 0 && ax[i].Lw == ax[i].L;
+    }
     const bool af = (h == f), ag = (h == g);
-    if ((af || ag) && !inplace) return HDC_ERR_PARAM;
+    if ((af || ag) && (!inplace || !same_shape)) return HDC_ERR_PARAM;
     const int ncopy = (int)af + (int)(ag && g != f);
     const size_t need = ws_bytes(dims, ax, B, sizeof(V), ncopy);
     if (ws == nullptr || ws_bytes_given < need) return HDC_ERR_WORKSPACE;
@@ -320,11 +337,13 @@ static int conv_nd(int dims, const void* f, const void* g, void* h, const Axis* 
 }
 
 static int resolve_all(int dims, const int64_t* L, const int64_t* M, const int64_t* m, const int64_t* p,
-                       const int64_t* q, const int64_t* D, int dtype, Axis* ax)
+                       const int64_t* q, const int64_t* D, int dtype, Axis* ax, const int64_t* o = nullptr,
+                       const int64_t* Lw = nullptr)
 {
     if (dims < 1 || dims > HDC_MAX_DIMS || !L || !M || !m) return HDC_ERR_PARAM;
     for (int i = 0; i < dims; ++i) {
-        int rc = resolve_axis(L[i], M[i], m[i], p ? p[i] : 0, q ? q[i] : 0, D ? D[i] : 0, dtype, &ax[i]);
+        int rc = resolve_axis(L[i], M[i], m[i], p ? p[i] : 0, q ? q[i] : 0, D ? D[i] : 0, dtype, &ax[i],
+                              o ? o[i] : 0, Lw ? Lw[i] : -1);
         if (rc != HDC_OK) return rc;
     }
     return HDC_OK;
@@ -500,6 +519,103 @@ HDC_EXPORT int hdc_convnd_host(int dims, const void* f_host, const void* g_host,
     if (rc != HDC_OK) return rc;
     if (cudaMemcpyAsync(h_host, dh, arr, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HDC_ERR_CUDA;
     return HDC_OK;
+}
+
+HDC_EXPORT int hdc_workspace_size_window(int dims, const int64_t* L, const int64_t* M, const int64_t* m,
+                                         const int64_t* p, const int64_t* q, const int64_t* D, const int64_t* o,
+                                         const int64_t* Lw, int dtype, int64_t batch, size_t* bytes)
+{
+    if (!bytes || batch < 0 || !o || !Lw) return HDC_ERR_PARAM;
+    Axis ax[HDC_MAX_DIMS];
+    int rc = resolve_all(dims, L, M, m, p, q, D, dtype, ax, o, Lw);
+    if (rc != HDC_OK) return rc;
+    *bytes = ws_bytes(dims, ax, batch, dtype == HDC_C128 ? 16 : 8, 0);
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_convnd_window(int dims, const void* f, const void* g, void* h, const int64_t* L, const int64_t* M,
+                                 const int64_t* m, const int64_t* p, const int64_t* q, const int64_t* D,
+                                 const int64_t* o, const int64_t* Lw, int dtype, int64_t batch, void* workspace,
+                                 size_t ws_bytes_given, void* stream)
+{
+    if (!o || !Lw) return HDC_ERR_PARAM;
+    Axis ax[HDC_MAX_DIMS];
+    int rc = resolve_all(dims, L, M, m, p, q, D, dtype, ax, o, Lw);
+    if (rc != HDC_OK) return rc;
+    if (batch < 0) return HDC_ERR_PARAM;
+    if (batch == 0) return HDC_OK;
+    if (!f || !g || !h) return HDC_ERR_PARAM;
+    const uintptr_t al = dtype == HDC_C128 ? 15 : 7;
+    if (((uintptr_t)f & al) || ((uintptr_t)g & al) || ((uintptr_t)h & al)) return HDC_ERR_PARAM;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == HDC_C128) return conv_nd<double>(dims, f, g, h, ax, 0, batch, workspace, ws_bytes_given, st);
+    return conv_nd<float>(dims, f, g, h, ax, 0, batch, workspace, ws_bytes_given, st);
+}
+
+// Centered Hermitian 2-D convolution as a windowed linear convolution of the
+// index-shifted full spectra (shift c = K - 1 per axis): outputs kx in
+// [-c, c] are the window [c, 3c] of axis 0, ky in [0, c] the window [2c, 3c]
+// of axis 1; both alias-free with M = 3K - 2 (the 3/2 padding ratio).
+static void hermitian_axes(int64_t K, int64_t L[2], int64_t M[2], int64_t o[2], int64_t Lw[2])
+{
+    const int64_t c = K - 1;
+    L[0] = L[1] = 2 * K - 1;
+    M[0] = M[1] = 3 * K - 2;
+    o[0] = c;
+    o[1] = 2 * c;
+    Lw[0] = 2 * K - 1;
+    Lw[1] = K;
+}
+
+HDC_EXPORT int hdc_workspace_size_hermitian(int64_t K, const int64_t* m, const int64_t* D, int dtype, int64_t batch,
+                                            size_t* bytes)
+{
+    if (K < 1 || !m || !bytes || batch < 0) return HDC_ERR_PARAM;
+    int64_t L[2], M[2], o[2], Lw[2];
+    hermitian_axes(K, L, M, o, Lw);
+    size_t conv = 0;
+    int rc = hdc_workspace_size_window(2, L, M, m, nullptr, nullptr, D, o, Lw, dtype, batch, &conv);
+    if (rc != HDC_OK) return rc;
+    const size_t esz = dtype == HDC_C128 ? 16 : 8;
+    *bytes = 2 * align_up((size_t)(batch * L[0] * L[1]) * esz) + conv + 256;
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_conv2d_hermitian(const void* f, const void* g, void* h, int64_t K, const int64_t* m,
+                                    const int64_t* D, int dtype, int64_t batch, void* workspace,
+                                    size_t ws_bytes_given, void* stream)
+{
+    if (K < 1 || !m) return HDC_ERR_PARAM;
+    int64_t L[2], M[2], o[2], Lw[2];
+    hermitian_axes(K, L, M, o, Lw);
+    Axis ax[2];
+    int rc = resolve_all(2, L, M, m, nullptr, nullptr, D, dtype, ax, o, Lw);
+    if (rc != HDC_OK) return rc;
+    if (batch < 0) return HDC_ERR_PARAM;
+    if (batch == 0) return HDC_OK;
+    if (!f || !g || !h || h == f || h == g) return HDC_ERR_PARAM;
+    size_t need = 0;
+    rc = hdc_workspace_size_hermitian(K, m, D, dtype, batch, &need);
+    if (rc != HDC_OK) return rc;
+    if (!workspace || ws_bytes_given < need) return HDC_ERR_WORKSPACE;
+    const size_t esz = dtype == HDC_C128 ? 16 : 8;
+    const size_t arr = align_up((size_t)(batch * L[0] * L[1]) * esz);
+    uintptr_t base = ((uintptr_t)workspace + 255) & ~(uintptr_t)255;
+    void* ff = (void*)base;
+    void* gg = (void*)(base + arr);
+    void* w = (void*)(base + 2 * arr);
+    const size_t wbytes = ws_bytes_given - (size_t)((uintptr_t)w - (uintptr_t)workspace);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == HDC_C128) {
+        if (launch_hermitian_expand<double>((const cx<double>*)f, (cx<double>*)ff, K, batch, st) != cudaSuccess ||
+            launch_hermitian_expand<double>((const cx<double>*)g, (cx<double>*)gg, K, batch, st) != cudaSuccess)
+            return HDC_ERR_CUDA;
+        return conv_nd<double>(2, ff, gg, h, ax, 0, batch, w, wbytes, st);
+    }
+    if (launch_hermitian_expand<float>((const cx<float>*)f, (cx<float>*)ff, K, batch, st) != cudaSuccess ||
+        launch_hermitian_expand<float>((const cx<float>*)g, (cx<float>*)gg, K, batch, st) != cudaSuccess)
+        return HDC_ERR_CUDA;
+    return conv_nd<float>(2, ff, gg, h, ax, 0, batch, w, wbytes, st);
 }
 
 HDC_EXPORT int hdc_release_caches(void)

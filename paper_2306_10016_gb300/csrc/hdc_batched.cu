@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -140,8 +141,8 @@ k_batched(const BConv<V>* __restrict__ convs, const BItem* __restrict__ it0, con
                 using T = typename real_of<V>::type;
                 for (int64_t e = e0 + tid; e < e1; e += nthr) {
                     const int64_t i = e / Cn, c = e - i * Cn;
-                    unfold_elem<V, 4>(hp_[itm.conv], cws, cv.m, Cn, ma, i, c, cv.p, cv.q, cv.N, cs, cc, cv.L, 0,
-                                      cv.q, 1, 1, (T)(1.0 / (double)cv.N), cv.twN);
+                    unfold_elem<V, 4>(hp_[itm.conv], cws, cv.m, Cn, ma, i, c, cv.p, cv.q, cv.N, cs, cc, (int64_t)0,
+                                      cv.L, 0, cv.q, 1, 1, (T)(1.0 / (double)cv.N), cv.twN);
                 }
             }
         }
@@ -433,7 +434,16 @@ HDC_EXPORT int hdc_batched_tune(int64_t n, const int64_t* L, int dtype, const vo
     if (n < 1 || !L || !f_host || !g_host || !h_host || !m_out || reps < 1 || max_cands < 1) return HDC_ERR_PARAM;
     if (dtype != HDC_C64 && dtype != HDC_C128) return HDC_ERR_DTYPE;
     cudaStream_t st = (cudaStream_t)stream;
-    // classes, their members and candidate m (of the longest member)
+    // A class's schedule is its residue count q: every member gets its own
+    // m = nextgood(ceil(M_i / q)), so the FFT size follows each length.
+    static const int64_t qs[] = { 1, 2, 3, 4, 5, 6, 8, 10, 12, 16 };
+    auto m_for = [&](int64_t Li, int64_t q) -> int64_t {
+        const int64_t M = 2 * Li - 1;
+        const int64_t m = hdc_next_good_size((M + q - 1) / q);
+        if (m < 1) return -1;
+        const bool ok = dtype == HDC_C128 ? batched_ok<double>(m) : batched_ok<float>(m);
+        return ok ? m : -1;
+    };
     std::vector<std::vector<int64_t>> members(64);
     for (int64_t i = 0; i < n; ++i) {
         if (L[i] < 1) return HDC_ERR_PARAM;
@@ -444,18 +454,17 @@ HDC_EXPORT int hdc_batched_tune(int64_t n, const int64_t* L, int dtype, const vo
     std::vector<double> work(64, 0.0);
     for (int k = 0; k < 64; ++k) {
         if (members[k].empty()) continue;
-        int64_t Lmax = 0;
-        for (int64_t i : members[k]) { Lmax = std::max(Lmax, L[i]); work[k] += (double)L[i]; }
-        int64_t nc = 0;
-        hdc_tune_candidates(Lmax, 2 * Lmax - 1, dtype, 1.5, 16, nullptr, 0, &nc);
-        std::vector<hdc_tuple> cand((size_t)std::max<int64_t>(nc, 1));
-        hdc_tune_candidates(Lmax, 2 * Lmax - 1, dtype, 1.5, 16, cand.data(), nc, &nc);
-        for (int64_t c = 0; c < nc && (int64_t)cands[k].size() < max_cands; ++c) {
-            const int64_t m = cand[(size_t)c].m;
-            if (dtype == HDC_C128 ? batched_ok<double>(m) : batched_ok<float>(m)) cands[k].push_back(m);
+        int64_t Lmin = INT64_MAX;
+        for (int64_t i : members[k]) { Lmin = std::min(Lmin, L[i]); work[k] += (double)L[i]; }
+        for (int64_t q : qs) {
+            if ((int64_t)cands[k].size() >= max_cands) break;
+            // q is usable when every member has an m >= 16 that the kernel supports
+            bool ok = (2 * Lmin - 1 + q - 1) / q >= 16 || q == 1;
+            for (int64_t i : members[k]) ok = ok && m_for(L[i], q) > 0;
+            if (ok) cands[k].push_back(q);
         }
         if (cands[k].empty()) return HDC_ERR_UNSUPPORTED_SIZE;
-        for (int64_t i : members[k]) m_out[i] = cands[k][0]; // least model flops to start
+        for (int64_t i : members[k]) m_out[i] = m_for(L[i], cands[k][0]);
         order.push_back(k);
     }
     std::sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
@@ -509,14 +518,14 @@ HDC_EXPORT int hdc_batched_tune(int64_t n, const int64_t* L, int dtype, const vo
     // one class at a time, largest work first, the others held (Section 4.2)
     for (int k : order) {
         if (rc != HDC_OK) break;
-        int64_t bestm = cands[k][0];
+        int64_t bestq = cands[k][0];
         for (size_t c = 1; c < cands[k].size(); ++c) {
-            for (int64_t i : members[k]) m_out[i] = cands[k][c];
+            for (int64_t i : members[k]) m_out[i] = m_for(L[i], cands[k][c]);
             double t = 0.0;
             const int r = time_all(&t);
-            if (r == HDC_OK && t < best) { best = t; bestm = cands[k][c]; }
+            if (r == HDC_OK && t < best) { best = t; bestq = cands[k][c]; }
         }
-        for (int64_t i : members[k]) m_out[i] = bestm;
+        for (int64_t i : members[k]) m_out[i] = m_for(L[i], bestq);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -134,20 +134,23 @@ __device__ __forceinline__ void ifft_cols_body(V* yb, int64_t Cn, int ma, int q,
     __syncthreads();
 }
 
-// Unfold of one element (i, c) of one row: out[(t ma + i) Cn + c] for every
-// t < p with index < Lvalid gets sum_{rr < Dg} conj(zeta_Nf^{r (i cs + c cc)})
-// conj(zeta_q^{r t}) h_rr[i][c] (h_rr = h + rr * hstride), residues r = r0 + rr
-// in increasing order; added to the previous contents unless first, scaled if
-// last.  PT outputs are accumulated per sweep over the residues.
+// Unfold of one element (i, c) of one row: the output at linear index
+// lin = (t ma + i) Cn + c, for every t < p with lo <= lin < hi, is
+// sum_{rr < Dg} conj(zeta_Nf^{r (i cs + c cc)}) conj(zeta_q^{r t}) h_rr[i][c]
+// (h_rr = h + rr * hstride, residues r = r0 + rr in increasing order),
+// written to ob[lin - lo]; added to the previous contents unless first,
+// scaled if last.  PT outputs are accumulated per sweep over the residues.
 template <class V, int PT>
 __device__ __forceinline__ void unfold_elem(V* ob, const V* __restrict__ h, int64_t hstride, int64_t Cn,
                                             int64_t ma, int64_t i, int64_t c, int p, int q, int64_t Nf, int64_t cs,
-                                            int64_t cc, int64_t Lvalid, int r0, int Dg, int first, int last,
+                                            int64_t cc, int64_t lo, int64_t hi, int r0, int Dg, int first, int last,
                                             typename real_of<V>::type scale, const V* __restrict__ twNf)
 {
     const int64_t mq = Nf / q;
     for (int t0 = 0; t0 < p; t0 += PT) {
-        if ((((int64_t)t0 * ma + i) * Cn + c) >= Lvalid) break;
+        if ((((int64_t)t0 * ma + i) * Cn + c) >= hi) break;
+        const int tl = (t0 + PT - 1 < p) ? t0 + PT - 1 : p - 1;
+        if ((((int64_t)tl * ma + i) * Cn + c) < lo) continue;
         V acc[PT];
 #pragma unroll
         for (int tt = 0; tt < PT; ++tt) acc[tt] = czero<V>();
@@ -169,11 +172,12 @@ __device__ __forceinline__ void unfold_elem(V* ob, const V* __restrict__ h, int6
             const int t = t0 + tt;
             if (t >= p) break;
             const int64_t lin = ((int64_t)t * ma + i) * Cn + c;
-            if (lin >= Lvalid) break;
+            if (lin >= hi) break;
+            if (lin < lo) continue;
             V v = acc[tt];
-            if (!first) v = cadd(v, ob[lin]);
+            if (!first) v = cadd(v, ob[lin - lo]);
             if (last) v = cscale(v, scale);
-            ob[lin] = v;
+            ob[lin - lo] = v;
         }
     }
 }

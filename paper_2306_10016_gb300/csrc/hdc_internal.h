@@ -80,14 +80,19 @@ template <typename T>
 cudaError_t launch_ifft_cols(cx<T>* y, int64_t B, int64_t Cn, int64_t ma, int64_t q, int64_t Nf,
                              int64_t D, int pre, cudaStream_t st);
 
-// Unfold-accumulate: out[b][(t ma + i) Cn + c] (valid iff < Lvalid) gets
+// Unfold-accumulate: the output at lin = (t ma + i) Cn + c, t < p, kept iff
+// lo <= lin < hi and stored at out[b * bstride + lin - lo], gets
 // sum_{rr} conj(zeta_Nf^{r (i cs + c cc)}) conj(zeta_q^{r t}) h[rr][b][i][c];
 // added to the previous contents unless first, scaled by `scale` if last.
 template <typename T>
 cudaError_t launch_unfold(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstride, int64_t Cn,
                           int64_t ma, int64_t p, int64_t q, int64_t Nf, int64_t cs, int64_t cc,
-                          int64_t Lvalid, int64_t r0, int64_t D, int first, int last, double scale,
+                          int64_t lo, int64_t hi, int64_t r0, int64_t D, int first, int last, double scale,
                           cudaStream_t st);
+
+// Full (2K-1) x (2K-1) centered spectrum from its ky >= 0 half, B arrays.
+template <typename T>
+cudaError_t launch_hermitian_expand(const cx<T>* half, cx<T>* full, int64_t K, int64_t B, cudaStream_t st);
 
 // The same launches with caller-provided twiddle tables (no library cache):
 // twN = zeta_{q m}^k (q m entries), twm = zeta_m^k (m entries), twNf as in

@@ -218,7 +218,7 @@ cudaError_t launch_ifft_cols(cx<T>* y, int64_t B, int64_t Cn, int64_t ma, int64_
 template <class V, int PT>
 __global__ void __launch_bounds__(256)
 k_unfold(V* out, const V* __restrict__ h, int64_t B, int64_t bstride, int64_t Cn, int64_t ma,
-         int p, int q, int64_t Nf, int64_t cs, int64_t cc, int64_t Lvalid, int r0, int Dg,
+         int p, int q, int64_t Nf, int64_t cs, int64_t cc, int64_t lo, int64_t hi, int r0, int Dg,
          int first, int last, typename real_of<V>::type scale, const V* __restrict__ twNf)
 {
     const int64_t per = ma * Cn;
@@ -227,14 +227,14 @@ k_unfold(V* out, const V* __restrict__ h, int64_t B, int64_t bstride, int64_t Cn
     const int64_t b = gid / per;
     const int64_t e = gid - b * per;
     const int64_t i = e / Cn, c = e - i * Cn;
-    unfold_elem<V, PT>(out + b * bstride, h + b * per, B * per, Cn, ma, i, c, p, q, Nf, cs, cc, Lvalid, r0, Dg, first,
-                       last, scale, twNf);
+    unfold_elem<V, PT>(out + b * bstride, h + b * per, B * per, Cn, ma, i, c, p, q, Nf, cs, cc, lo, hi, r0, Dg,
+                       first, last, scale, twNf);
 }
 
 template <typename T>
 cudaError_t launch_unfold(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstride, int64_t Cn,
                           int64_t ma, int64_t p, int64_t q, int64_t Nf, int64_t cs, int64_t cc,
-                          int64_t Lvalid, int64_t r0, int64_t D, int first, int last, double scale,
+                          int64_t lo, int64_t hi, int64_t r0, int64_t D, int first, int last, double scale,
                           cudaStream_t st)
 {
     using V = cx<T>;
@@ -246,13 +246,51 @@ cudaError_t launch_unfold(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstride
     const int thr = 256;
     const int64_t total = ma * Cn * B;
     const int64_t blocks = (total + thr - 1) / thr;
-    LaunchScope ls(K_UNFOLD, st, (double)(Dg * B) * 8.0 * Lvalid + (last ? 2.0 * B * Lvalid : 0.0),
-                   ((double)(Dg * B * ma * Cn) + (first ? 1.0 : 2.0) * B * Lvalid) * sizeof(V));
+    const double nout = (double)(hi - lo);
+    LaunchScope ls(K_UNFOLD, st, (double)(Dg * B) * 8.0 * nout + (last ? 2.0 * B * nout : 0.0),
+                   ((double)(Dg * B * ma * Cn) + (first ? 1.0 : 2.0) * B * nout) * sizeof(V));
     k_unfold<V, 4><<<(unsigned)blocks, thr, 0, st>>>(out, h, B, bstride, Cn, ma, (int)p, (int)q, Nf,
-                                                     cs, cc, Lvalid, (int)r0, (int)Dg, first, last,
+                                                     cs, cc, lo, hi, (int)r0, (int)Dg, first, last,
                                                      (T)scale, twNf);
     return cudaGetLastError();
 }
+
+// ------------------------------------------------ Hermitian expansion
+// full[b][x][y] (x, y in [0, 2c], c = K - 1) of the centered spectrum from
+// its half half[b][x][ky] (ky in [0, c]): f(kx, ky) for ky >= 0, and
+// conj(f(-kx, -ky)) for ky < 0 (the spectrum of a real field).
+
+template <class V>
+__global__ void k_hermitian_expand(const V* __restrict__ half, V* __restrict__ full, int64_t K, int64_t B)
+{
+    const int64_t n = 2 * K - 1, c = K - 1;
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gid >= B * n * n) return;
+    const int64_t b = gid / (n * n);
+    const int64_t e = gid - b * n * n;
+    const int64_t x = e / n, y = e - x * n;
+    const V* hb = half + b * n * K;
+    V v;
+    if (y >= c) {
+        v = hb[x * K + (y - c)];
+    } else {
+        const V w = hb[(2 * c - x) * K + (c - y)];
+        v = mkc<V>(w.x, -w.y);
+    }
+    full[gid] = v;
+}
+
+template <typename T>
+cudaError_t launch_hermitian_expand(const cx<T>* half, cx<T>* full, int64_t K, int64_t B, cudaStream_t st)
+{
+    const int thr = 256;
+    const int64_t tot = B * (2 * K - 1) * (2 * K - 1);
+    if (tot <= 0) return cudaSuccess;
+    k_hermitian_expand<cx<T>><<<(unsigned)((tot + thr - 1) / thr), thr, 0, st>>>(half, full, K, B);
+    return cudaGetLastError();
+}
+template cudaError_t launch_hermitian_expand<double>(const cx<double>*, cx<double>*, int64_t, int64_t, cudaStream_t);
+template cudaError_t launch_hermitian_expand<float>(const cx<float>*, cx<float>*, int64_t, int64_t, cudaStream_t);
 
 // ---------------------------------------- launchers with caller twiddles
 // The same kernels with the twiddle tables passed in (for callers that keep
@@ -303,7 +341,8 @@ cudaError_t launch_unfold_tw(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstr
     LaunchScope ls(K_UNFOLD, st, (double)(Dg * B) * 8.0 * Lvalid + (last ? 2.0 * B * Lvalid : 0.0),
                    ((double)(Dg * B * ma * Cn) + (first ? 1.0 : 2.0) * B * Lvalid) * sizeof(V));
     k_unfold<V, 4><<<(unsigned)blocks, thr, 0, st>>>(out, h, B, bstride, Cn, ma, (int)p, (int)q, Nf, cs, cc,
-                                                     Lvalid, (int)r0, (int)Dg, first, last, (T)scale, twNf);
+                                                     (int64_t)0, Lvalid, (int)r0, (int)Dg, first, last, (T)scale,
+                                                     twNf);
     return cudaGetLastError();
 }
 
@@ -334,7 +373,7 @@ HDC_INST_TW(float)
                                              int64_t, int, cudaStream_t);                               \
     template cudaError_t launch_unfold<T>(cx<T>*, const cx<T>*, int64_t, int64_t, int64_t, int64_t,     \
                                           int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,         \
-                                          int64_t, int64_t, int, int, double, cudaStream_t);
+                                          int64_t, int64_t, int64_t, int, int, double, cudaStream_t);
 
 HDC_INST(double)
 HDC_INST(float)
