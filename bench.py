@@ -37,6 +37,11 @@ SM_MAX_MHZ = 2070.0
 # 2 flops per FMA: peak = SMs x units x 2 x max SM clock.
 FP64_FMA_PER_CLK = 2
 FP32_FMA_PER_CLK = 128
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# dominant kernel, averaged over its launches in one ncu capture of this
+# sweep's timed steps (eager launches); to be re-taken whenever that kernel
+# changes (and None until then).
+NCU_TRAFFIC_PER_LAUNCH = {"k_residue_rows": 4.459e7}
 
 
 def sweep_sizes():
@@ -180,6 +185,9 @@ def main():
         "HDC_TUNING_DB", os.path.join(os.path.expanduser("~"), ".cache", "hdc", "tuning.txt")))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sizes", default="", help="comma-separated L list (default: the full sweep)")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch every timed step directly instead of replaying a captured CUDA graph "
+                         "(same work; for profilers that do not follow graph replays)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -247,31 +255,46 @@ def main():
             torch.cuda.synchronize(dev)
             hdc.stats_reset()
         n0 = hdc.total_launches()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=side):
-            for _ in range(reps):
-                step(side)
-        per_step = hdc.total_launches() - n0
-        if stats:
-            hdc.stats_timing(False)
         st = torch.cuda.current_stream(dev)
-        graph.replay()
+        if args.eager:
+            graph = None
+
+            def replay():
+                for _ in range(reps):
+                    step(st)
+        else:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=side):
+                for _ in range(reps):
+                    step(side)
+            replay = graph.replay
+        per_step = hdc.total_launches() - n0
+        if stats and not args.eager:
+            hdc.stats_timing(False)
+        replay()
         torch.cuda.synchronize(dev)
+        if stats and args.eager:
+            hdc.stats_reset()
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize(dev)
         if nvtx:
             torch.cuda.nvtx.range_push(nvtx)
+        n1 = hdc.total_launches()
         ev = []
         for _ in range(steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(st)
-            graph.replay()
+            replay()
             e1.record(st)
             ev.append((e0, e1))
         torch.cuda.synchronize(dev)
+        if args.eager:
+            per_step = (hdc.total_launches() - n1) // steps
+        if stats and args.eager:
+            hdc.stats_timing(False)
         if nvtx:
             torch.cuda.nvtx.range_pop()
         if dist is not None:
@@ -281,9 +304,14 @@ def main():
         kst = None
         if stats:
             try:
-                kst = hdc.stats()     # event pairs of the last replay
+                kst = hdc.stats()     # event pairs of the last replay (graph) or of every step (eager)
             except Exception:
                 kst = None
+            if kst is not None and args.eager:
+                for v in kst.values():   # per step, as after a replay
+                    v["ms"] /= steps
+                    v["flops"] /= steps
+                    v["launches"] //= steps
         del graph
         return sum(ms) / len(ms), per_step * steps, ms, kst
 
@@ -362,17 +390,22 @@ def main():
                 for _ in range(max(1, args.warmup)):
                     plan.execute(wsb, stream=side)
             torch.cuda.synchronize(dev)
-            graph = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(graph, stream=side):
-                plan.execute(wsb, stream=side)
             st = torch.cuda.current_stream(dev)
+            if args.eager:
+                graph = None
+                replay = lambda: plan.execute(wsb, stream=st)   # noqa: E731
+            else:
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph, stream=side):
+                    plan.execute(wsb, stream=side)
+                replay = graph.replay
             ev = []
             for _ in range(args.steps):
                 flush.zero_()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(st)
-                graph.replay()
+                replay()
                 e1.record(st)
                 ev.append((e0, e1))
             torch.cuda.synchronize(dev)
@@ -407,18 +440,24 @@ def main():
                 run(side)
         torch.cuda.synchronize(dev)
         hdc.stats_reset()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=side):
-            run(side)
-        fl = sum(v["flops"] for v in hdc.stats().values())
         st = torch.cuda.current_stream(dev)
+        if args.eager:
+            graph = None
+            run(st)
+            replay = lambda: run(st)   # noqa: E731
+        else:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=side):
+                run(side)
+            replay = graph.replay
+        fl = sum(v["flops"] for v in hdc.stats().values())
         ev = []
         for _ in range(steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(st)
-            graph.replay()
+            replay()
             e1.record(st)
             ev.append((e0, e1))
         torch.cuda.synchronize(dev)
@@ -500,7 +539,8 @@ def main():
     total_ms = sum(v["ms"] for v in kstats.values())
     roofline = {
         "bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
-        "frac": round(achieved / peak, 4), "traffic": None, "kernel": dom,
+        "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC_PER_LAUNCH.get(dom), "kernel": dom,
+        "algorithmic_bytes_per_launch": d["bytes"] / max(1, d["launches"]),
         "peak_basis": "152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz (unit counts and max clock)",
         "peak_measured_fma_probe": round(fp64_probe, 4),
         "share_of_step": round(d["ms"] / total_ms, 4) if total_ms > 0 else None,
@@ -524,7 +564,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name("FP64"), "sizes": len(sizes), "outputs_per_step": outs,
-                   "launch": "one step captured in a CUDA graph, replayed per timed step",
+                   "launch": ("eager launches per timed step" if args.eager else
+                              "one step captured in a CUDA graph, replayed per timed step"),
                    "l2": "flushed between timed steps (256 MiB write)", "tuning": "grid search (Section 4.2), "
                    "candidates within 1.5x of the least model flops, m >= 16", "tuning_s": round(tune_s, 1),
                    "parallelism": f"replicas x{world}"},

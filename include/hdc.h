@@ -259,8 +259,8 @@ int hdc_conv1d_noalloc(const void* f, const void* g, void* h, int64_t L,
  * for every q, the m = 2^a 3^b 5^c 7^d >= m_min that pad M least (the three
  * smallest >= ceil(M/q), the next power of two, the next 3 * 2^k), p and q
  * derived, D = q; kept when the model flops F1 are within max_ratio (>= 1)
- * of the axis minimum; sorted by F1.  Writes up to `cap` entries, the full
- * count to *n. */
+ * of the axis minimum; sorted by F1 (an axis with nextgood(M) < m_min uses
+ * m_min = nextgood(M)).  Writes up to `cap` entries, the full count to *n. */
 int hdc_tune_candidates(int64_t L, int64_t M, int dtype, double max_ratio,
                         int64_t m_min, hdc_tuple* out, int64_t cap, int64_t* n);
 
@@ -294,7 +294,10 @@ int hdc_tune_conv1d(int64_t L, int64_t M, int dtype, int64_t batch,
  * `tuning_db` (may be NULL) and otherwise runs hdc_tune_convnd on scratch
  * buffers it allocates and frees itself (the one place besides twiddle
  * tables where the library allocates), then appends the result to the
- * database.  HDC_FIXED takes m (and D, may be NULL) from the caller. */
+ * database.  HDC_FIXED takes m (and D, may be NULL) from the caller.
+ * HDC_PREDICT_MLP reads the network checkpoint at `tuning_db` (written by
+ * hdc_mlp_save with HDC_MLP_FEATURES inputs, HDC_MLP_HIDDEN hidden units and
+ * hdc_mlp_num_q_classes() + 2 outputs) and runs its inference kernels. */
 int hdc_plan_create(hdc_plan** plan, int dims, const int64_t* L,
                     const int64_t* M, const int64_t* m, const int64_t* D,
                     int dtype, int64_t batch, int mode, const char* tuning_db,
@@ -358,6 +361,53 @@ int hdc_batched_tune(int64_t n, const int64_t* L, int dtype,
                      const void* const* f_host, const void* const* g_host,
                      void* const* h_host, int reps, int max_cands,
                      void* stream, int64_t* m_out, double* ms_out);
+
+/* ------------------------------------------------- learned predictor (MLP)
+ * A per-axis classifier of the parameters (the paper's Section 5.3 finds
+ * classification better than regression; Section 4.2's separability lets
+ * each axis be predicted on its own): FP32 MLP n_in -> H -> H -> H -> n_out
+ * with ReLU, hand-written forward / backward / Adam kernels, deterministic
+ * sums.  Heads: outputs [0, n_q) score the residue-count classes
+ * hdc_mlp_q_class(k), outputs [n_q, n_q + 2) score D = q versus D = 1.
+ * Parameters: one float vector, per layer W[i][o] (row-major) then b[o].
+ * Device memory of the network is library-owned (create/destroy). */
+#define HDC_MLP_FEATURES 8
+#define HDC_MLP_HIDDEN 64
+typedef struct hdc_mlp hdc_mlp;
+int hdc_mlp_create(hdc_mlp** net, int n_in, int n_hidden, int n_out);
+int hdc_mlp_num_params(const hdc_mlp* net);
+/* host <-> device parameter copies (set also clears the Adam state) */
+int hdc_mlp_set_params(hdc_mlp* net, const float* host);
+int hdc_mlp_get_params(const hdc_mlp* net, float* host);
+int hdc_mlp_get_grads(const hdc_mlp* net, float* host);
+/* X: device n x n_in; logits: device n x n_out */
+int hdc_mlp_forward(hdc_mlp* net, const float* X, int64_t n, float* logits,
+                    void* stream);
+/* Forward, mean softmax cross-entropy of both heads (labels yq in [0, n_q),
+ * yd in {0, 1}; -1 skips a head) into *loss (device float), gradients kept
+ * in the network.  X, yq, yd, loss: device pointers. */
+int hdc_mlp_loss_grad(hdc_mlp* net, const float* X, const int* yq,
+                      const int* yd, int64_t n, int n_q, float* loss,
+                      void* stream);
+/* One Adam step (bias-corrected) with the stored gradients. */
+int hdc_mlp_adam(hdc_mlp* net, float lr, float beta1, float beta2, float eps,
+                 void* stream);
+/* Checkpoint (parameters, Adam moments, step count) to / from a file. */
+int hdc_mlp_save(const hdc_mlp* net, const char* path);
+int hdc_mlp_load(hdc_mlp* net, const char* path);
+int hdc_mlp_destroy(hdc_mlp* net);
+/* Residue-count classes: count, value of class k, nearest class of q. */
+int hdc_mlp_num_q_classes(void);
+int64_t hdc_mlp_q_class(int k);
+int hdc_mlp_q_to_class(int64_t q);
+/* HDC_MLP_FEATURES features per axis of a problem (dims x 8 floats). */
+int hdc_mlp_axis_features(int dims, const int64_t* L, const int64_t* M,
+                          int dtype, int64_t batch, float* out);
+/* (m, p, q, D) of one axis from its logits: the most likely residue class
+ * whose tuple is valid, m = nextgood(ceil(M / q)), D from the D head. */
+int hdc_mlp_decode_axis(const float* logits, int n_q, int64_t L, int64_t M,
+                        int dtype, int64_t* m, int64_t* p, int64_t* q,
+                        int64_t* D);
 
 /* ------------------------------------------------------ launch statistics
  * Counting of every kernel launch (always on) and, when enabled, CUDA events

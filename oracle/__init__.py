@@ -15,6 +15,8 @@ formula each one writes out):
 * ``residue_forward / residue_backward / conv_hybrid`` -- Eq. 1, Eq. 2 (O5)
 * ``conv_hermitian_direct / conv_hermitian_fft`` -- centered Hermitian (O6)
 * ``dft(x, sign)``                -- the DFT by its definition
+* ``mlp_loss_grad(params, sizes, X, yq, yd, n_q)`` / ``adam_step`` -- the
+  parameter predictor's network in FP64 (O7)
 """
 from __future__ import annotations
 
@@ -51,6 +53,12 @@ def lib():
         L.hdco_conv_hybrid_1d.argtypes = [_dp, _dp, _i64, _i64, _i64, _i64, _dp]
         L.hdco_conv_hermitian_2d_direct.argtypes = [_dp, _dp, _i64, _dp]
         L.hdco_conv_hermitian_2d_fft.argtypes = [_dp, _dp, _i64, _dp]
+        _ip32 = C.POINTER(C.c_int)
+        L.hdco_mlp_loss_grad.argtypes = [_dp, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _ip32, _ip32, C.c_int,
+                                         _dp, _dp, _dp]
+        L.hdco_adam_step.argtypes = [_dp, _dp, _dp, _dp, C.c_long, C.c_double, C.c_double, C.c_double,
+                                     C.c_double, C.c_long]
+        L.hdco_adam_step.restype = None
         L.hdco_root_of_unity.argtypes = [_i64, _i64, _dp]
         L.hdco_root_of_unity.restype = None
         L.hdco_num_threads.restype = C.c_int
@@ -196,3 +204,31 @@ def conv_hermitian_fft(f, g):
     h = np.empty_like(f)
     _check(lib().hdco_conv_hermitian_2d_fft(_dptr(f), _dptr(g), K, _dptr(h)), "herm_fft")
     return h
+
+
+def mlp_num_params(n_in, H, n_out):
+    dims = [n_in, H, H, H, n_out]
+    return sum(dims[l] * dims[l + 1] + dims[l + 1] for l in range(4))
+
+
+def mlp_loss_grad(params, n_in, H, n_out, X, yq, yd, n_q):
+    """FP64 loss, gradient and logits of the predictor network (O7)."""
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    n = X.shape[0]
+    yq = np.ascontiguousarray(yq, dtype=np.int32)
+    yd = np.ascontiguousarray(yd, dtype=np.int32)
+    grad = np.zeros_like(P)
+    logits = np.zeros((n, n_out))
+    loss = C.c_double()
+    ip = C.POINTER(C.c_int)
+    _check(lib().hdco_mlp_loss_grad(_dptr(P), n_in, H, n_out, n_q, _dptr(X), yq.ctypes.data_as(ip),
+                                    yd.ctypes.data_as(ip), n, C.byref(loss), _dptr(grad), _dptr(logits)),
+           "mlp_loss_grad")
+    return loss.value, grad, logits
+
+
+def adam_step(p, g, m, v, lr, b1, b2, eps, t):
+    """In place on float64 arrays p, m, v."""
+    lib().hdco_adam_step(_dptr(p), _dptr(np.ascontiguousarray(g, dtype=np.float64)), _dptr(m), _dptr(v), p.size,
+                         lr, b1, b2, eps, t)

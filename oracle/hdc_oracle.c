@@ -17,6 +17,7 @@
  *   O5  residue forward/backward transforms written out as Eq. 1 and Eq. 2,
  *       and the hybrid convolution built from them (Section 2.2, 3.3, 3.5)
  *   O6  centered Hermitian (2-D) convolution by its definition
+ *   O7  the parameter predictor's MLP: loss and gradients in FP64, Adam
  *
  * Sign convention (the paper's Eq. 1 and Eq. 2): zeta_n = exp(2 pi i / n),
  * forward transforms use zeta^{+kj} unscaled, backward use zeta^{-kj}/n.
@@ -676,6 +677,96 @@ HDCO_API int hdco_conv_hermitian_2d_fft(const double* f, const double* g,
     free(A);
     free(B);
     return 0;
+}
+
+/* ------------------------------------------------ O7 MLP predictor (FP64) */
+
+/* Network n_in -> H -> H -> H -> n_out with ReLU after the hidden layers;
+ * parameters per layer W[i][o] (row-major) then b[o].  Loss: mean over the
+ * n samples of softmax cross-entropy on outputs [0, n_q) with label yq and
+ * on outputs [n_q, n_q + 2) with label yd (a label < 0 skips that term).
+ * Writes the loss, the gradient of every parameter and the logits. */
+HDCO_API int hdco_mlp_loss_grad(const double* P, int n_in, int H, int n_out, int n_q, const double* X,
+                                const int* yq, const int* yd, int n, double* loss, double* grad,
+                                double* logits)
+{
+    int dims[5] = { n_in, H, H, H, n_out };
+    long off_w[4], off_b[4], np = 0;
+    for (int l = 0; l < 4; ++l) {
+        off_w[l] = np;
+        np += (long)dims[l] * dims[l + 1];
+        off_b[l] = np;
+        np += dims[l + 1];
+    }
+    for (long k = 0; k < np; ++k) grad[k] = 0.0;
+    double* z[5];
+    double* a[5];
+    double* dz[5];
+    for (int l = 1; l <= 4; ++l) {
+        z[l] = (double*)calloc((size_t)dims[l], sizeof(double));
+        a[l] = (double*)calloc((size_t)dims[l], sizeof(double));
+        dz[l] = (double*)calloc((size_t)dims[l], sizeof(double));
+    }
+    double total = 0.0;
+    for (int s = 0; s < n; ++s) {
+        /* forward */
+        const double* in = X + (long)s * n_in;
+        for (int l = 1; l <= 4; ++l) {
+            const double* prev = (l == 1) ? in : a[l - 1];
+            for (int o = 0; o < dims[l]; ++o) {
+                double acc = P[off_b[l - 1] + o];
+                for (int i = 0; i < dims[l - 1]; ++i) acc += prev[i] * P[off_w[l - 1] + (long)i * dims[l] + o];
+                z[l][o] = acc;
+                a[l][o] = (l < 4 && acc < 0.0) ? 0.0 : acc;
+            }
+        }
+        for (int o = 0; o < n_out; ++o) {
+            logits[(long)s * n_out + o] = z[4][o];
+            dz[4][o] = 0.0;
+        }
+        /* two softmax cross-entropy heads */
+        int lo[2] = { 0, n_q }, hi[2] = { n_q, n_q + 2 }, y[2] = { yq[s], yd[s] };
+        for (int h = 0; h < 2; ++h) {
+            if (y[h] < 0) continue;
+            double mx = z[4][lo[h]];
+            for (int k = lo[h]; k < hi[h]; ++k) mx = z[4][k] > mx ? z[4][k] : mx;
+            double se = 0.0;
+            for (int k = lo[h]; k < hi[h]; ++k) se += exp(z[4][k] - mx);
+            double lse = mx + log(se);
+            total += lse - z[4][lo[h] + y[h]];
+            for (int k = lo[h]; k < hi[h]; ++k)
+                dz[4][k] = (exp(z[4][k] - lse) - ((k - lo[h]) == y[h] ? 1.0 : 0.0)) / (double)n;
+        }
+        /* backward */
+        for (int l = 4; l >= 1; --l) {
+            const double* prev = (l == 1) ? in : a[l - 1];
+            for (int o = 0; o < dims[l]; ++o) {
+                grad[off_b[l - 1] + o] += dz[l][o];
+                for (int i = 0; i < dims[l - 1]; ++i) grad[off_w[l - 1] + (long)i * dims[l] + o] += prev[i] * dz[l][o];
+            }
+            if (l > 1)
+                for (int i = 0; i < dims[l - 1]; ++i) {
+                    double acc = 0.0;
+                    for (int o = 0; o < dims[l]; ++o) acc += dz[l][o] * P[off_w[l - 1] + (long)i * dims[l] + o];
+                    dz[l - 1][i] = z[l - 1][i] > 0.0 ? acc : 0.0;
+                }
+        }
+    }
+    *loss = total / (double)n;
+    for (int l = 1; l <= 4; ++l) { free(z[l]); free(a[l]); free(dz[l]); }
+    return 0;
+}
+
+/* One Adam step (Kingma and Ba, 2015) with bias correction at step t >= 1. */
+HDCO_API void hdco_adam_step(double* p, const double* g, double* m, double* v, long n, double lr, double b1,
+                             double b2, double eps, long t)
+{
+    double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);
+    for (long k = 0; k < n; ++k) {
+        m[k] = b1 * m[k] + (1.0 - b1) * g[k];
+        v[k] = b2 * v[k] + (1.0 - b2) * g[k] * g[k];
+        p[k] -= lr * (m[k] / c1) / (sqrt(v[k] / c2) + eps);
+    }
 }
 
 HDCO_API int hdco_num_threads(void)

@@ -118,6 +118,23 @@ _SIGS += [
                                     C.c_int, _i64, _vp, _sz, _vp]),
     ("hdc_workspace_size_hermitian", C.c_int, [_i64, _i64p, _i64p, C.c_int, _i64, C.POINTER(_sz)]),
     ("hdc_conv2d_hermitian", C.c_int, [_vp, _vp, _vp, _i64, _i64p, _i64p, C.c_int, _i64, _vp, _sz, _vp]),
+    ("hdc_mlp_create", C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, C.c_int]),
+    ("hdc_mlp_num_params", C.c_int, [_vp]),
+    ("hdc_mlp_set_params", C.c_int, [_vp, C.POINTER(C.c_float)]),
+    ("hdc_mlp_get_params", C.c_int, [_vp, C.POINTER(C.c_float)]),
+    ("hdc_mlp_get_grads", C.c_int, [_vp, C.POINTER(C.c_float)]),
+    ("hdc_mlp_forward", C.c_int, [_vp, _vp, _i64, _vp, _vp]),
+    ("hdc_mlp_loss_grad", C.c_int, [_vp, _vp, _vp, _vp, _i64, C.c_int, _vp, _vp]),
+    ("hdc_mlp_adam", C.c_int, [_vp, C.c_float, C.c_float, C.c_float, C.c_float, _vp]),
+    ("hdc_mlp_save", C.c_int, [_vp, C.c_char_p]),
+    ("hdc_mlp_load", C.c_int, [_vp, C.c_char_p]),
+    ("hdc_mlp_destroy", C.c_int, [_vp]),
+    ("hdc_mlp_num_q_classes", C.c_int, []),
+    ("hdc_mlp_q_class", _i64, [C.c_int]),
+    ("hdc_mlp_q_to_class", C.c_int, [_i64]),
+    ("hdc_mlp_axis_features", C.c_int, [C.c_int, _i64p, _i64p, C.c_int, _i64, C.POINTER(C.c_float)]),
+    ("hdc_mlp_decode_axis", C.c_int, [C.POINTER(C.c_float), C.c_int, _i64, _i64, C.c_int, _i64p, _i64p, _i64p,
+                                      _i64p]),
     ("hdc_stats_reset", C.c_int, []),
     ("hdc_stats_timing", C.c_int, [C.c_int]),
     ("hdc_stats_kernel_count", C.c_int, []),
@@ -576,6 +593,99 @@ class BatchedPlan:
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
             _lib.hdc_batched_destroy(self._h)
+            self._h = None
+
+
+# ------------------------------------------------------ learned predictor
+
+MLP_FEATURES = 8
+MLP_HIDDEN = 64
+
+
+def mlp_q_classes():
+    return [int(lib().hdc_mlp_q_class(k)) for k in range(lib().hdc_mlp_num_q_classes())]
+
+
+def mlp_q_to_class(q: int) -> int:
+    return int(lib().hdc_mlp_q_to_class(int(q)))
+
+
+def mlp_axis_features(L, M=None, dtype=HDC_C128, batch=1):
+    import numpy as np
+    dims = len(L)
+    Mv = M if M is not None else [2 * l - 1 for l in L]
+    out = (C.c_float * (dims * MLP_FEATURES))()
+    _check(lib().hdc_mlp_axis_features(dims, _arr(L), _arr(Mv), dtype, int(batch), out), "mlp_axis_features")
+    return np.array(out, dtype=np.float32).reshape(dims, MLP_FEATURES)
+
+
+def mlp_decode_axis(logits, L: int, M: int, dtype=HDC_C128):
+    import numpy as np
+    lg = np.ascontiguousarray(logits, dtype=np.float32)
+    m, p, q, D = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+    _check(lib().hdc_mlp_decode_axis(lg.ctypes.data_as(C.POINTER(C.c_float)), lg.size - 2, L, M, dtype, C.byref(m),
+                                     C.byref(p), C.byref(q), C.byref(D)), "mlp_decode_axis")
+    return dict(m=m.value, p=p.value, q=q.value, D=D.value)
+
+
+class MLP:
+    """The parameter predictor network on the GPU (hdc_mlp_*)."""
+
+    def __init__(self, n_in=MLP_FEATURES, hidden=MLP_HIDDEN, n_out=None):
+        if n_out is None:
+            n_out = lib().hdc_mlp_num_q_classes() + 2
+        self.n_in, self.hidden, self.n_out = n_in, hidden, n_out
+        h = C.c_void_p()
+        _check(lib().hdc_mlp_create(C.byref(h), n_in, hidden, n_out), "mlp_create")
+        self._h = h
+        self.n_params = int(lib().hdc_mlp_num_params(h))
+
+    def set_params(self, params):
+        import numpy as np
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        assert a.size == self.n_params
+        _check(lib().hdc_mlp_set_params(self._h, a.ctypes.data_as(C.POINTER(C.c_float))), "mlp_set_params")
+
+    def params(self):
+        import numpy as np
+        a = np.empty(self.n_params, dtype=np.float32)
+        _check(lib().hdc_mlp_get_params(self._h, a.ctypes.data_as(C.POINTER(C.c_float))), "mlp_get_params")
+        return a
+
+    def grads(self):
+        import numpy as np
+        a = np.empty(self.n_params, dtype=np.float32)
+        _check(lib().hdc_mlp_get_grads(self._h, a.ctypes.data_as(C.POINTER(C.c_float))), "mlp_get_grads")
+        return a
+
+    def forward(self, X, stream=None):
+        torch = _torch()
+        out = torch.empty((X.shape[0], self.n_out), dtype=torch.float32, device=X.device)
+        st = stream if stream is not None else torch.cuda.current_stream(X.device)
+        _check(lib().hdc_mlp_forward(self._h, X.data_ptr(), X.shape[0], out.data_ptr(), st.cuda_stream), "mlp_forward")
+        return out
+
+    def loss_grad(self, X, yq, yd, loss_out, stream=None):
+        """Device tensors: X float32 (n, n_in), yq / yd int32 (n,), loss_out float32 (1,)."""
+        torch = _torch()
+        st = stream if stream is not None else torch.cuda.current_stream(X.device)
+        _check(lib().hdc_mlp_loss_grad(self._h, X.data_ptr(), yq.data_ptr(), yd.data_ptr(), X.shape[0],
+                                       self.n_out - 2, loss_out.data_ptr(), st.cuda_stream), "mlp_loss_grad")
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        torch = _torch()
+        st = stream if stream is not None else torch.cuda.current_stream()
+        _check(lib().hdc_mlp_adam(self._h, lr, beta1, beta2, eps, st.cuda_stream), "mlp_adam")
+
+    def save(self, path):
+        _check(lib().hdc_mlp_save(self._h, str(path).encode()), "mlp_save")
+
+    def load(self, path):
+        _check(lib().hdc_mlp_load(self._h, str(path).encode()), "mlp_load")
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.hdc_mlp_destroy(self._h)
             self._h = None
 
 

@@ -57,6 +57,9 @@ std::vector<hdc_tuple> candidates(int64_t L, int64_t M, int dtype, double max_ra
 {
     std::vector<hdc_tuple> out;
     if (m_min < 1) m_min = 1;
+    // an axis too short for any m >= m_min keeps its explicit size
+    const int64_t top = hdc_next_good_size(M);
+    if (top > 0 && top < m_min) m_min = top;
     double best = 1e300;
     std::vector<int64_t> ms;
     for (int64_t q = 1;; ++q) {
@@ -344,6 +347,47 @@ struct hdc_plan {
     size_t ws;
 };
 
+// Parameters from the learned predictor: features of every axis, one
+// forward pass of the network on the device, decode per axis.
+static int predict_mlp(int dims, const int64_t* L, const int64_t* M, int dtype, int64_t batch, const char* path,
+                       cudaStream_t st, hdc_tuple* t)
+{
+    if (!path || !*path) return HDC_ERR_NOT_TUNED;
+    const int nq = hdc_mlp_num_q_classes();
+    hdc_mlp* net = nullptr;
+    int rc = hdc_mlp_create(&net, HDC_MLP_FEATURES, HDC_MLP_HIDDEN, nq + 2);
+    if (rc != HDC_OK) return rc;
+    if (hdc_mlp_load(net, path) != HDC_OK) { hdc_mlp_destroy(net); return HDC_ERR_NOT_TUNED; }
+    float feat[HDC_MAX_DIMS * HDC_MLP_FEATURES];
+    rc = hdc_mlp_axis_features(dims, L, M, dtype, batch, feat);
+    std::vector<float> logits((size_t)dims * (nq + 2));
+    float* dbuf = nullptr;
+    if (rc == HDC_OK && cudaMalloc(&dbuf, sizeof(float) * (size_t)dims * (HDC_MLP_FEATURES + nq + 2)) != cudaSuccess)
+        rc = HDC_ERR_ALLOC;
+    if (rc == HDC_OK) {
+        float* dx = dbuf;
+        float* dl = dbuf + (size_t)dims * HDC_MLP_FEATURES;
+        if (cudaMemcpyAsync(dx, feat, sizeof(float) * dims * HDC_MLP_FEATURES, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess)
+            rc = HDC_ERR_CUDA;
+        if (rc == HDC_OK) rc = hdc_mlp_forward(net, dx, dims, dl, st);
+        if (rc == HDC_OK &&
+            (cudaMemcpyAsync(logits.data(), dl, sizeof(float) * logits.size(), cudaMemcpyDeviceToHost, st) !=
+                 cudaSuccess ||
+             cudaStreamSynchronize(st) != cudaSuccess))
+            rc = HDC_ERR_CUDA;
+    }
+    cudaFree(dbuf);
+    hdc_mlp_destroy(net);
+    for (int i = 0; i < dims && rc == HDC_OK; ++i) {
+        rc = hdc_mlp_decode_axis(logits.data() + (size_t)i * (nq + 2), nq, L[i], M[i], dtype, &t[i].m, &t[i].p,
+                                 &t[i].q, &t[i].D);
+        t[i].model_flops = model_flops_axis(L[i], t[i].m, t[i].q);
+        t[i].ms = -1.0;
+    }
+    return rc;
+}
+
 HDC_EXPORT int hdc_plan_create(hdc_plan** out, int dims, const int64_t* L, const int64_t* M, const int64_t* m,
                                const int64_t* D, int dtype, int64_t batch, int mode, const char* tuning_db,
                                void* stream)
@@ -400,6 +444,9 @@ HDC_EXPORT int hdc_plan_create(hdc_plan** out, int dims, const int64_t* L, const
             if (rc != HDC_OK) return rc;
             db_store(tuning_db, key, dims, pl.t);
         }
+    } else if (mode == HDC_PREDICT_MLP) {
+        int rc = predict_mlp(dims, L, M, dtype, batch, tuning_db, (cudaStream_t)stream, pl.t);
+        if (rc != HDC_OK) return rc;
     } else {
         return HDC_ERR_PARAM;
     }

@@ -1,0 +1,273 @@
+"""Learned parameter predictor: data from the grid search, training on the
+GPU, regret against the grid search.
+
+Section 5 of the paper caches optimizer timings of small squares and
+rectangles of sizes 2^a 3^b 5^c 7^d and fits classifiers to them (Section
+5.3: classification beats regression); Section 4.2 searches each axis on its
+own.  Here:
+
+* ``collect``: 2-D squares and rectangles with sides in the 2^a 3^b 5^c 7^d
+  sizes of [16, 512] (plus skinny rectangles of height 4 to 32), each
+  searched by the exhaustive tuner (``hdc_tune_convnd``) on the GPU; the
+  record keeps the best (m, p, q, D) per axis and its time.
+* ``samples``: one sample per axis: the HDC_MLP_FEATURES features of the
+  axis in its problem, the class of its best residue count q and whether
+  its best D was q (all residues in one pass) or less.
+* ``train``: full-batch Adam on the GPU with the library's forward,
+  backward and Adam kernels; the initial weights are drawn on the host.
+* ``evaluate``: for larger problems (2-D rectangles up to 4096 x 2048, 3-D
+  cubes up to 256^3) the regret T(predicted) / T(grid-search best) - 1,
+  beside two predictors-free rules: explicit padding (q = 1 per axis) and a
+  fixed q = 2 per axis.
+
+    python -m paper_2306_10016_gb300.predictor --out DIR [--collect N]
+           [--train STEPS] [--eval] [--dataset FILE] [--weights FILE]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import time
+
+import numpy as np
+
+from . import synth
+
+
+def good_sizes(lo: int, hi: int):
+    out = []
+    for n in range(lo, hi + 1):
+        k = n
+        for f in (2, 3, 5, 7):
+            while k % f == 0:
+                k //= f
+        if k == 1:
+            out.append(n)
+    return out
+
+
+def training_problems(seed: int, n_rect: int):
+    """All squares with sides in the 7-smooth sizes of [16, 512], skinny
+    rectangles of heights 4..32, and n_rect seeded rectangles."""
+    sides = good_sizes(16, 512)
+    probs = [(s, s) for s in sides]
+    for s in sides[::3]:
+        for h in (4, 8, 16, 32):
+            probs.append((s, h))
+            probs.append((h, s))
+    u = synth.uniform01(seed, 2 * n_rect)
+    for k in range(n_rect):
+        a = sides[int(u[2 * k] * len(sides))]
+        b = sides[int(u[2 * k + 1] * len(sides))]
+        probs.append((a, b))
+    seen, out = set(), []
+    for p in probs:
+        if p not in seen:
+            seen.add(p)
+            out.append(p)
+    return out
+
+
+def collect(problems, dtype=None, max_ratio=1.5, reps=3, log=None):
+    import torch
+
+    import paper_2306_10016_gb300 as hdc
+    dtype = hdc.HDC_C128 if dtype is None else dtype
+    tdt = torch.complex128 if dtype == hdc.HDC_C128 else torch.complex64
+    recs = []
+    for k, shape in enumerate(problems):
+        f = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 50 + k, shape)).to("cuda", tdt)
+        g = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 5050 + k, shape)).to("cuda", tdt)
+        best, trials = hdc.tune(f, g, len(shape), max_ratio=max_ratio, reps=reps)
+        recs.append({"L": list(shape), "M": [2 * x - 1 for x in shape], "dtype": int(dtype), "batch": 1,
+                     "best": [{k2: b[k2] for k2 in ("m", "p", "q", "D")} for b in best],
+                     "ms": best[0]["ms"], "trials": len(trials)})
+        if log and k % 20 == 0:
+            log(f"collect {k}/{len(problems)} {shape} -> {recs[-1]['best']}")
+    return recs
+
+
+def samples(records):
+    import paper_2306_10016_gb300 as hdc
+    X, yq, yd = [], [], []
+    for r in records:
+        feats = hdc.mlp_axis_features(r["L"], r["M"], r["dtype"], r.get("batch", 1))
+        for a, b in enumerate(r["best"]):
+            X.append(feats[a])
+            yq.append(hdc.mlp_q_to_class(b["q"]))
+            yd.append(0 if b["D"] >= b["q"] else 1)
+    return (np.array(X, dtype=np.float32), np.array(yq, dtype=np.int32), np.array(yd, dtype=np.int32))
+
+
+def init_params(n_in, hidden, n_out, seed):
+    """Uniform weights in +-sqrt(6 / fan_in) (He et al., 2015), zero biases."""
+    dims = [n_in, hidden, hidden, hidden, n_out]
+    parts = []
+    for l in range(4):
+        nw = dims[l] * dims[l + 1]
+        bound = math.sqrt(6.0 / dims[l])
+        parts.append((2.0 * synth.uniform01(seed + l, nw) - 1.0) * bound)
+        parts.append(np.zeros(dims[l + 1]))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def train(X, yq, yd, steps=3000, lr=3e-3, seed=230610016, log=None, checkpoint=None, resume=None):
+    """Full-batch Adam on the GPU; returns (network, loss history)."""
+    import torch
+
+    import paper_2306_10016_gb300 as hdc
+    net = hdc.MLP()
+    if resume and os.path.exists(resume):
+        net.load(resume)
+    else:
+        net.set_params(init_params(net.n_in, net.hidden, net.n_out, seed))
+    Xd = torch.from_numpy(X).cuda()
+    yqd = torch.from_numpy(yq).cuda()
+    ydd = torch.from_numpy(yd).cuda()
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    hist = []
+    for it in range(steps):
+        net.loss_grad(Xd, yqd, ydd, loss)
+        net.adam(lr)
+        if it % 100 == 0 or it == steps - 1:
+            hist.append((it, float(loss.item())))
+            if log:
+                log(f"train step {it} loss {hist[-1][1]:.4f}")
+    if checkpoint:
+        net.save(checkpoint)
+    return net, hist
+
+
+def accuracy(net_or_params, X, yq, yd):
+    """Classification accuracy of both heads (q class, D class)."""
+    import torch
+    logits = net_or_params.forward(torch.from_numpy(X).cuda()).cpu().numpy()
+    nq = logits.shape[1] - 2
+    aq = float(np.mean(np.argmax(logits[:, :nq], axis=1) == yq))
+    ad = float(np.mean(np.argmax(logits[:, nq:], axis=1) == yd))
+    return aq, ad
+
+
+def _time_params(f, g, dims, prm, reps=5):
+    import torch
+
+    import paper_2306_10016_gb300 as hdc
+    m = [p["m"] for p in prm]
+    D = [p["D"] for p in prm]
+    L = list(f.shape[-dims:])
+    ws = torch.empty(hdc.workspace_size(L, [2 * x - 1 for x in L], m, D=D), dtype=torch.uint8, device=f.device)
+    h = torch.empty_like(f)
+    for _ in range(2):
+        hdc.convnd(f, g, dims, m, D=D, out=h, workspace=ws)
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        hdc.convnd(f, g, dims, m, D=D, out=h, workspace=ws)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def _rule_params(L, q):
+    import paper_2306_10016_gb300 as hdc
+    out = []
+    for l in L:
+        M = 2 * l - 1
+        m = hdc.next_good_size(-(-M // q))
+        rc, (p, qq, D) = hdc.validate_axis(l, M, m)
+        out.append(dict(m=m, p=p, q=qq, D=D))
+    return out
+
+
+EVAL_PROBLEMS = [(768, 768), (1024, 1024), (2048, 512), (2048, 1024), (3072, 1536), (4096, 2048),
+                 (32, 32, 32), (64, 64, 64), (128, 128, 128), (256, 256, 256)]
+
+
+def evaluate(weights, problems=None, dtype=None, reps=5, log=None):
+    import torch
+
+    import paper_2306_10016_gb300 as hdc
+    dtype = hdc.HDC_C128 if dtype is None else dtype
+    tdt = torch.complex128 if dtype == hdc.HDC_C128 else torch.complex64
+    rows = []
+    for k, shape in enumerate(problems or EVAL_PROBLEMS):
+        dims = len(shape)
+        f = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 90 + k, shape)).to("cuda", tdt)
+        g = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 9090 + k, shape)).to("cuda", tdt)
+        t0 = time.perf_counter()
+        best, _ = hdc.tune(f, g, dims, max_ratio=1.5, reps=3)
+        t_search = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        pred = hdc.Plan(list(shape), dtype=dtype, mode=hdc.HDC_PREDICT_MLP, tuning_db=str(weights)).params
+        t_pred = time.perf_counter() - t0
+        cand = {"search": [dict(m=b["m"], p=b["p"], q=b["q"], D=b["D"]) for b in best], "mlp": pred,
+                "explicit": _rule_params(shape, 1), "q2": _rule_params(shape, 2)}
+        t = {k2: _time_params(f, g, dims, v, reps) for k2, v in cand.items()}
+        row = {"shape": list(shape), "ms": {k2: round(v, 4) for k2, v in t.items()},
+               "regret": {k2: round(t[k2] / t["search"] - 1.0, 4) for k2 in ("mlp", "explicit", "q2")},
+               "params": cand, "search_s": round(t_search, 2), "predict_s": round(t_pred, 4)}
+        rows.append(row)
+        if log:
+            log(f"eval {shape}: {row['ms']} regret {row['regret']}")
+        del f, g
+        torch.cuda.empty_cache()
+
+    def stats(key):
+        r = np.array([max(0.0, x["regret"][key]) for x in rows])
+        return {"geomean": float(np.exp(np.mean(np.log1p(r))) - 1.0), "p90": float(np.quantile(r, 0.9)),
+                "max": float(r.max())}
+
+    return {"rows": rows, "summary": {k2: stats(k2) for k2 in ("mlp", "explicit", "q2")}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--collect", type=int, default=0, help="seeded rectangles beyond the squares (0: skip)")
+    ap.add_argument("--dataset", default=None)
+    ap.add_argument("--train", type=int, default=0)
+    ap.add_argument("--lr", type=float, default=3e-3)
+    ap.add_argument("--weights", default=None)
+    ap.add_argument("--eval", action="store_true")
+    a = ap.parse_args(argv)
+    os.makedirs(a.out, exist_ok=True)
+
+    def log(msg):
+        print(msg, flush=True)
+
+    ds_path = a.dataset or os.path.join(a.out, "mlp_dataset.json")
+    w_path = a.weights or os.path.join(a.out, "mlp_weights.bin")
+    report = {}
+    if a.collect:
+        t0 = time.perf_counter()
+        recs = collect(training_problems(synth.BASE_SEED + 5, a.collect), log=log)
+        report["collect_s"] = round(time.perf_counter() - t0, 1)
+        with open(ds_path, "w") as fh:
+            json.dump(recs, fh)
+    if a.train:
+        with open(ds_path) as fh:
+            recs = json.load(fh)
+        X, yq, yd = samples(recs)
+        t0 = time.perf_counter()
+        net, hist = train(X, yq, yd, steps=a.train, lr=a.lr, log=log, checkpoint=w_path)
+        report["train_s"] = round(time.perf_counter() - t0, 2)
+        report["train_samples"] = int(X.shape[0])
+        report["loss"] = hist
+        aq, ad = accuracy(net, X, yq, yd)
+        counts = np.bincount(yq, minlength=net.n_out - 2)
+        report["train_accuracy"] = {"q": aq, "D": ad, "q_majority_rule": float(counts.max() / counts.sum())}
+        log(f"train accuracy q {aq:.3f} D {ad:.3f} (majority {report['train_accuracy']['q_majority_rule']:.3f})")
+    if a.eval:
+        report["eval"] = evaluate(w_path, log=log)
+        log(json.dumps(report["eval"]["summary"]))
+    with open(os.path.join(a.out, "mlp_report.json"), "w") as fh:
+        json.dump(report, fh, indent=1)
+
+
+if __name__ == "__main__":
+    main()

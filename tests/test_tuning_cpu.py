@@ -38,6 +38,12 @@ def test_candidates_valid_and_within_ratio(lib, L):
         assert 2 * L in ms and L in ms
 
 
+def test_candidates_short_axis_keeps_explicit(lib):
+    # M = 7 < m_min = 16: the explicit size still qualifies
+    c = hdc.tune_candidates(4, 7, hdc.HDC_C128, 1.5, 16)
+    assert c and c[0]["m"] == 7 or any(t["m"] == 7 for t in c)
+
+
 def _db_plan(path, L, mode=hdc.HDC_TUNE_CACHED_ONLY):
     h = C.c_void_p()
     arr = lambda v: (C.c_int64 * 1)(v)
