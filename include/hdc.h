@@ -125,9 +125,13 @@ int hdc_validate_axis(int64_t L, int64_t M, int64_t m, int64_t p, int64_t q,
                       int64_t D, int dtype, int64_t* p_out, int64_t* q_out,
                       int64_t* D_out);
 
-/* Largest FFT size m and padded size q m accepted for a dtype. */
+/* Largest FFT size m and padded size q m accepted for a dtype.  An axis that
+ * has inner axes (all but the last of a 2-D / 3-D call) runs its m-point
+ * FFT in one column tile: m <= hdc_max_outer_fft_size (4096 for
+ * complex<double>, 8192 for complex<float>), else HDC_ERR_UNSUPPORTED_SIZE. */
 int64_t hdc_max_fft_size(int dtype);
 int64_t hdc_max_padded_size(int dtype);
+int64_t hdc_max_outer_fft_size(int dtype);
 
 /* Bytes of device workspace an N-D call needs (dims in 1..3; arrays of
  * length dims; p/q/D entries may be 0 = derive).  Writes *bytes. */
@@ -200,6 +204,19 @@ int hdc_convnd_window(int dims, const void* f, const void* g, void* h,
                       const int64_t* o, const int64_t* Lw, int dtype,
                       int64_t batch, void* workspace, size_t ws_bytes,
                       void* stream);
+
+/* The share of residues [r_lo, r_hi) of axis 0 (0 <= r_lo < r_hi <= q[0]):
+ * the outer sum of Eq. 2 restricted to that range, scaled by 1/N, so the
+ * shares of disjoint ranges add up to the convolution.  Residues are
+ * independent until that sum (Section 2.2), which is how a convolution is
+ * split over several GPUs: each computes one range, then one sum-reduction
+ * of the outputs.  Same arguments as hdc_convnd (no in-place mode; the
+ * workspace of hdc_workspace_size is enough). */
+int hdc_convnd_residues(int dims, const void* f, const void* g, void* h,
+                        const int64_t* L, const int64_t* M, const int64_t* m,
+                        const int64_t* p, const int64_t* q, const int64_t* D,
+                        int64_t r_lo, int64_t r_hi, int dtype, int64_t batch,
+                        void* workspace, size_t ws_bytes, void* stream);
 
 /* Centered Hermitian 2-D convolution (the paper names the Hermitian case as
  * prior work, Section 1, and future work, Section 7; this is the reading
@@ -404,10 +421,12 @@ int hdc_mlp_q_to_class(int64_t q);
 int hdc_mlp_axis_features(int dims, const int64_t* L, const int64_t* M,
                           int dtype, int64_t batch, float* out);
 /* (m, p, q, D) of one axis from its logits: the most likely residue class
- * whose tuple is valid, m = nextgood(ceil(M / q)), D from the D head. */
+ * whose tuple is valid with m <= max_m (0: no bound), m = nextgood(ceil(M /
+ * q)), D from the D head.  rank > 0 skips the `rank` most likely valid
+ * classes (the k-th best guess, for searches over the top classes). */
 int hdc_mlp_decode_axis(const float* logits, int n_q, int64_t L, int64_t M,
-                        int dtype, int64_t* m, int64_t* p, int64_t* q,
-                        int64_t* D);
+                        int dtype, int64_t max_m, int rank, int64_t* m,
+                        int64_t* p, int64_t* q, int64_t* D);
 
 /* ------------------------------------------------------ launch statistics
  * Counting of every kernel launch (always on) and, when enabled, CUDA events

@@ -58,6 +58,7 @@ _SIGS = [
     ("hdc_validate_axis", C.c_int, [_i64, _i64, _i64, _i64, _i64, _i64, C.c_int, _i64p, _i64p, _i64p]),
     ("hdc_max_fft_size", _i64, [C.c_int]),
     ("hdc_max_padded_size", _i64, [C.c_int]),
+    ("hdc_max_outer_fft_size", _i64, [C.c_int]),
     ("hdc_workspace_size", C.c_int, [C.c_int, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, C.c_int, _i64,
                                      C.c_int, C.POINTER(_sz)]),
     ("hdc_conv1d", C.c_int, [_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _i64, C.c_int, C.c_int, _i64,
@@ -133,8 +134,10 @@ _SIGS += [
     ("hdc_mlp_q_class", _i64, [C.c_int]),
     ("hdc_mlp_q_to_class", C.c_int, [_i64]),
     ("hdc_mlp_axis_features", C.c_int, [C.c_int, _i64p, _i64p, C.c_int, _i64, C.POINTER(C.c_float)]),
-    ("hdc_mlp_decode_axis", C.c_int, [C.POINTER(C.c_float), C.c_int, _i64, _i64, C.c_int, _i64p, _i64p, _i64p,
-                                      _i64p]),
+    ("hdc_mlp_decode_axis", C.c_int, [C.POINTER(C.c_float), C.c_int, _i64, _i64, C.c_int, _i64, C.c_int, _i64p,
+                                      _i64p, _i64p, _i64p]),
+    ("hdc_convnd_residues", C.c_int, [C.c_int, _vp, _vp, _vp, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, _i64, _i64,
+                                      C.c_int, _i64, _vp, _sz, _vp]),
     ("hdc_stats_reset", C.c_int, []),
     ("hdc_stats_timing", C.c_int, [C.c_int]),
     ("hdc_stats_kernel_count", C.c_int, []),
@@ -358,6 +361,32 @@ def conv2d_hermitian(f, g, m=None, D=0, out=None, workspace=None, stream=None):
         _check(lib().hdc_conv2d_hermitian(f.data_ptr(), g.data_ptr(), h.data_ptr(), K, mv, Dv, dt, batch,
                                           workspace.data_ptr(), workspace.numel() * workspace.element_size(),
                                           st.cuda_stream), "hdc_conv2d_hermitian")
+    return h
+
+
+def convnd_residues(f, g, dims, m, r_lo, r_hi, M=None, p=0, q=0, D=0, out=None, workspace=None, stream=None):
+    """The share of residues [r_lo, r_hi) of axis 0 (hdc_convnd_residues);
+    the shares of disjoint ranges add up to the convolution."""
+    torch = _torch()
+    if not (f.is_cuda and g.is_cuda) or f.shape != g.shape or f.dtype != g.dtype:
+        raise ValueError("f and g must be CUDA tensors of one shape and dtype")
+    dt = dtype_code(f.dtype)
+    L = [int(x) for x in f.shape[f.dim() - dims:]]
+    batch = 1
+    for x in f.shape[: f.dim() - dims]:
+        batch *= int(x)
+    Mv = _per_axis(M, dims, "M") or [2 * l - 1 for l in L]
+    mv, pv, qv, Dv = (_per_axis(v, dims, n) for v, n in ((m, "m"), (p, "p"), (q, "q"), (D, "D")))
+    h = out if out is not None else torch.empty_like(f)
+    nbytes = workspace_size(L, Mv, mv, pv, qv, Dv, dt, batch)
+    if workspace is None or workspace.numel() * workspace.element_size() < nbytes:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=f.device)
+    st = stream if stream is not None else torch.cuda.current_stream(f.device)
+    with torch.cuda.device(f.device):
+        _check(lib().hdc_convnd_residues(dims, f.data_ptr(), g.data_ptr(), h.data_ptr(), _arr(L), _arr(Mv), _arr(mv),
+                                         _arr(pv), _arr(qv), _arr(Dv), int(r_lo), int(r_hi), dt, batch,
+                                         workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                         st.cuda_stream), "hdc_convnd_residues")
     return h
 
 
@@ -619,12 +648,16 @@ def mlp_axis_features(L, M=None, dtype=HDC_C128, batch=1):
     return np.array(out, dtype=np.float32).reshape(dims, MLP_FEATURES)
 
 
-def mlp_decode_axis(logits, L: int, M: int, dtype=HDC_C128):
+def max_outer_fft_size(dtype=HDC_C128) -> int:
+    return int(lib().hdc_max_outer_fft_size(dtype))
+
+
+def mlp_decode_axis(logits, L: int, M: int, dtype=HDC_C128, max_m: int = 0, rank: int = 0):
     import numpy as np
     lg = np.ascontiguousarray(logits, dtype=np.float32)
     m, p, q, D = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
-    _check(lib().hdc_mlp_decode_axis(lg.ctypes.data_as(C.POINTER(C.c_float)), lg.size - 2, L, M, dtype, C.byref(m),
-                                     C.byref(p), C.byref(q), C.byref(D)), "mlp_decode_axis")
+    _check(lib().hdc_mlp_decode_axis(lg.ctypes.data_as(C.POINTER(C.c_float)), lg.size - 2, L, M, dtype, int(max_m),
+                                     int(rank), C.byref(m), C.byref(p), C.byref(q), C.byref(D)), "mlp_decode_axis")
     return dict(m=m.value, p=p.value, q=q.value, D=D.value)
 
 

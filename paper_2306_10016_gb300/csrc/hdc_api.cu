@@ -235,19 +235,24 @@ static size_t ws_bytes(int dims, const Axis* ax, int64_t B, size_t esz, int ncop
 
 // 1-D convolution of B rows (input row stride ld, output row stride ldo)
 // along a contiguous axis; outputs [a.o, a.o + a.Lw) of every row.
+// Residues [r_lo, r_hi) only (all: 0, q): the result is that range's share
+// of the sum over residues, already scaled by 1/N, so the shares of disjoint
+// ranges add up to the convolution.
 template <typename T>
 static cudaError_t run_rows(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t B, int64_t ld, int64_t ldo,
-                            const Axis& a, cx<T>* ws, cudaStream_t st)
+                            const Axis& a, cx<T>* ws, cudaStream_t st, int64_t r_lo = 0, int64_t r_hi = -1)
 {
     const double scale = 1.0 / (double)a.N;
+    if (r_hi < 0) r_hi = a.q;
     int64_t m1 = 0, m2 = 0;
     route(a, B, a.dtype, &m1, &m2);
     if (m1 == 0) {
-        for (int64_t r0 = 0; r0 < a.q; r0 += a.D) {
-            const int first = (r0 == 0), last = (r0 + a.D >= a.q);
-            HDC_TRY(launch_residue_rows<T>(f, g, ws, B, ld, a.L, a.m, a.p, a.q, r0, a.D, st));
+        for (int64_t r0 = r_lo; r0 < r_hi; r0 += a.D) {
+            const int64_t Dp = (a.D < r_hi - r0) ? a.D : (r_hi - r0);
+            const int first = (r0 == r_lo), last = (r0 + Dp >= r_hi);
+            HDC_TRY(launch_residue_rows<T>(f, g, ws, B, ld, a.L, a.m, a.p, a.q, r0, Dp, st));
             HDC_TRY(launch_unfold<T>(out, ws, B, ldo, 1, a.m, a.pout, a.q, a.N, 1, 0, a.o, a.o + a.Lw, r0,
-                                     a.D, first, last, scale, st));
+                                     Dp, first, last, scale, st));
         }
         return cudaSuccess;
     }
@@ -256,15 +261,15 @@ static cudaError_t run_rows(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t 
     // inverse; inverse m1-point FFTs; unfold.
     cx<T>* yf = ws;
     cx<T>* yg = ws + a.D * B * a.m;
-    for (int64_t r0 = 0; r0 < a.q; r0 += a.D) {
-        const int first = (r0 == 0), last = (r0 + a.D >= a.q);
-        const int64_t Dg = (a.D < a.q - r0) ? a.D : (a.q - r0);
-        HDC_TRY(launch_fold_fft_cols<T>(f, g, yf, yg, B, ld, m2, m1, a.p, a.q, a.N, m2, 1, a.L, r0, a.D, 1,
+    for (int64_t r0 = r_lo; r0 < r_hi; r0 += a.D) {
+        const int64_t Dg = (a.D < r_hi - r0) ? a.D : (r_hi - r0);
+        const int first = (r0 == r_lo), last = (r0 + Dg >= r_hi);
+        HDC_TRY(launch_fold_fft_cols<T>(f, g, yf, yg, B, ld, m2, m1, a.p, a.q, a.N, m2, 1, a.L, r0, Dg, 1,
                                         st));
         HDC_TRY(launch_residue_rows<T>(yf, yg, yf, Dg * B * m1, m2, m2, m2, 1, 1, 0, 1, st));
         HDC_TRY(launch_ifft_cols<T>(yf, B, m2, m1, a.q, a.N, Dg, 1, st));
         HDC_TRY(launch_unfold<T>(out, yf, B, ldo, m2, m1, a.pout, a.q, a.N, m2, 1, a.o, a.o + a.Lw, r0,
-                                 a.D, first, last, scale, st));
+                                 Dg, first, last, scale, st));
     }
     return cudaSuccess;
 }
@@ -274,9 +279,10 @@ static cudaError_t run_rows(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t 
 // every transformed row, inverse and unfold of the window of axis 0.
 template <typename T>
 static cudaError_t run_nd(int dims, const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t B,
-                          const Axis* ax, cx<T>* ws, cudaStream_t st)
+                          const Axis* ax, cx<T>* ws, cudaStream_t st, int64_t r_lo = 0, int64_t r_hi = -1)
 {
-    if (dims == 1) return run_rows<T>(f, g, out, B, ax[0].L, ax[0].Lw, ax[0], ws, st);
+    if (dims == 1) return run_rows<T>(f, g, out, B, ax[0].L, ax[0].Lw, ax[0], ws, st, r_lo, r_hi);
+    if (r_hi < 0) r_hi = ax[0].q;
     int64_t Cn = 1, Cw = 1;
     for (int i = 1; i < dims; ++i) { Cn *= ax[i].L; Cw *= ax[i].Lw; }
     const Axis& a = ax[0];
@@ -288,22 +294,23 @@ static cudaError_t run_nd(int dims, const cx<T>* f, const cx<T>* g, cx<T>* out, 
     const int64_t bstride = a.L * Cn;
     const int64_t ostride = a.Lw * Cw;
     const double scale = 1.0 / (double)a.N;
-    for (int64_t r0 = 0; r0 < a.q; r0 += a.D) {
-        const int first = (r0 == 0), last = (r0 + a.D >= a.q);
-        const int64_t Dg = (a.D < a.q - r0) ? a.D : (a.q - r0);
+    for (int64_t r0 = r_lo; r0 < r_hi; r0 += a.D) {
+        const int64_t Dg = (a.D < r_hi - r0) ? a.D : (r_hi - r0);
+        const int first = (r0 == r_lo), last = (r0 + Dg >= r_hi);
         HDC_TRY(launch_fold_fft_cols<T>(f, g, wf, wg, B, bstride, Cn, a.m, a.p, a.q, a.N, 1, 0,
-                                        a.L * Cn, r0, a.D, 0, st));
+                                        a.L * Cn, r0, Dg, 0, st));
         HDC_TRY(run_nd<T>(dims - 1, wf, wg, wh, Dg * B * a.m, ax + 1, inner, st));
         HDC_TRY(launch_ifft_cols<T>(wh, B, Cw, a.m, a.q, a.N, Dg, 0, st));
         HDC_TRY(launch_unfold<T>(out, wh, B, ostride, Cw, a.m, a.pout, a.q, a.N, 1, 0, a.o * Cw,
-                                 (a.o + a.Lw) * Cw, r0, a.D, first, last, scale, st));
+                                 (a.o + a.Lw) * Cw, r0, Dg, first, last, scale, st));
     }
     return cudaSuccess;
 }
 
 template <typename T>
 static int conv_nd(int dims, const void* f, const void* g, void* h, const Axis* ax, int inplace,
-                   int64_t B, void* ws, size_t ws_bytes_given, cudaStream_t st)
+                   int64_t B, void* ws, size_t ws_bytes_given, cudaStream_t st, int64_t r_lo = 0,
+                   int64_t r_hi = -1)
 {
     using V = cx<T>;
     int64_t tot = 1;
@@ -332,7 +339,7 @@ static int conv_nd(int dims, const void* f, const void* g, void* h, const Axis* 
         gin = (const V*)base;
         base += align_up(arr);
     }
-    cudaError_t e = run_nd<T>(dims, fin, gin, (V*)h, B, ax, (V*)base, st);
+    cudaError_t e = run_nd<T>(dims, fin, gin, (V*)h, B, ax, (V*)base, st, r_lo, r_hi);
     return e == cudaSuccess ? HDC_OK : HDC_ERR_CUDA;
 }
 
@@ -345,6 +352,9 @@ static int resolve_all(int dims, const int64_t* L, const int64_t* M, const int64
         int rc = resolve_axis(L[i], M[i], m[i], p ? p[i] : 0, q ? q[i] : 0, D ? D[i] : 0, dtype, &ax[i],
                               o ? o[i] : 0, Lw ? Lw[i] : -1);
         if (rc != HDC_OK) return rc;
+        // an axis with inner axes runs its whole m-point FFT in one column tile
+        if (i < dims - 1 && m[i] > (dtype == HDC_C128 ? max_col_fft<double>() : max_col_fft<float>()))
+            return HDC_ERR_UNSUPPORTED_SIZE;
     }
     return HDC_OK;
 }
@@ -415,6 +425,10 @@ HDC_EXPORT int hdc_validate_axis(int64_t L, int64_t M, int64_t m, int64_t p, int
 }
 
 HDC_EXPORT int64_t hdc_max_fft_size(int dtype) { return max_fft(dtype); }
+HDC_EXPORT int64_t hdc_max_outer_fft_size(int dtype)
+{
+    return dtype == HDC_C128 ? max_col_fft<double>() : max_col_fft<float>();
+}
 HDC_EXPORT int64_t hdc_max_padded_size(int dtype) { return max_padded(dtype); }
 
 HDC_EXPORT int hdc_workspace_size(int dims, const int64_t* L, const int64_t* M, const int64_t* m,
@@ -616,6 +630,25 @@ HDC_EXPORT int hdc_conv2d_hermitian(const void* f, const void* g, void* h, int64
         launch_hermitian_expand<float>((const cx<float>*)g, (cx<float>*)gg, K, batch, st) != cudaSuccess)
         return HDC_ERR_CUDA;
     return conv_nd<float>(2, ff, gg, h, ax, 0, batch, w, wbytes, st);
+}
+
+HDC_EXPORT int hdc_convnd_residues(int dims, const void* f, const void* g, void* h, const int64_t* L,
+                                   const int64_t* M, const int64_t* m, const int64_t* p, const int64_t* q,
+                                   const int64_t* D, int64_t r_lo, int64_t r_hi, int dtype, int64_t batch,
+                                   void* workspace, size_t ws_bytes_given, void* stream)
+{
+    Axis ax[HDC_MAX_DIMS];
+    int rc = resolve_all(dims, L, M, m, p, q, D, dtype, ax);
+    if (rc != HDC_OK) return rc;
+    if (batch < 0 || r_lo < 0 || r_hi > ax[0].q || r_lo >= r_hi) return HDC_ERR_PARAM;
+    if (batch == 0) return HDC_OK;
+    if (!f || !g || !h || h == f || h == g) return HDC_ERR_PARAM;
+    const uintptr_t al = dtype == HDC_C128 ? 15 : 7;
+    if (((uintptr_t)f & al) || ((uintptr_t)g & al) || ((uintptr_t)h & al)) return HDC_ERR_PARAM;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == HDC_C128)
+        return conv_nd<double>(dims, f, g, h, ax, 0, batch, workspace, ws_bytes_given, st, r_lo, r_hi);
+    return conv_nd<float>(dims, f, g, h, ax, 0, batch, workspace, ws_bytes_given, st, r_lo, r_hi);
 }
 
 HDC_EXPORT int hdc_release_caches(void)

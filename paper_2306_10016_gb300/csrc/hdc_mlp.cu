@@ -418,23 +418,25 @@ HDC_EXPORT int hdc_mlp_axis_features(int dims, const int64_t* L, const int64_t* 
 }
 
 // Parameters of one axis from its n_q + 2 logits.
-HDC_EXPORT int hdc_mlp_decode_axis(const float* logits, int n_q, int64_t L, int64_t M, int dtype, int64_t* m,
-                                   int64_t* p, int64_t* q, int64_t* D)
+HDC_EXPORT int hdc_mlp_decode_axis(const float* logits, int n_q, int64_t L, int64_t M, int dtype, int64_t max_m,
+                                   int rank, int64_t* m, int64_t* p, int64_t* q, int64_t* D)
 {
-    if (!logits || n_q != kNQ || !m || !p || !q || !D) return HDC_ERR_PARAM;
-    // the most likely class whose tuple is valid
+    if (!logits || n_q != kNQ || !m || !p || !q || !D || rank < 0) return HDC_ERR_PARAM;
+    // classes in decreasing score; the rank-th one whose tuple is valid
     std::vector<int> order(kNQ);
     for (int k = 0; k < kNQ; ++k) order[k] = k;
     for (int a = 0; a < kNQ; ++a)
         for (int b = a + 1; b < kNQ; ++b)
             if (logits[order[b]] > logits[order[a]]) std::swap(order[a], order[b]);
     const bool one = logits[kNQ + 1] > logits[kNQ];
+    int seen = 0;
     for (int k : order) {
         const int64_t qc = kQClasses[k];
         const int64_t mm = hdc_next_good_size((M + qc - 1) / qc);
-        if (mm < 1) continue;
+        if (mm < 1 || (max_m > 0 && mm > max_m)) continue;
         int64_t pp = 0, qq = 0, DD = 0;
         if (hdc_validate_axis(L, M, mm, 0, 0, one ? 1 : 0, dtype, &pp, &qq, &DD) != HDC_OK) continue;
+        if (seen++ < rank) continue;
         *m = mm;
         *p = pp;
         *q = qq;

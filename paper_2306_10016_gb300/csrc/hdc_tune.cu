@@ -380,8 +380,9 @@ static int predict_mlp(int dims, const int64_t* L, const int64_t* M, int dtype, 
     cudaFree(dbuf);
     hdc_mlp_destroy(net);
     for (int i = 0; i < dims && rc == HDC_OK; ++i) {
-        rc = hdc_mlp_decode_axis(logits.data() + (size_t)i * (nq + 2), nq, L[i], M[i], dtype, &t[i].m, &t[i].p,
-                                 &t[i].q, &t[i].D);
+        const int64_t max_m = i < dims - 1 ? hdc_max_outer_fft_size(dtype) : 0;
+        rc = hdc_mlp_decode_axis(logits.data() + (size_t)i * (nq + 2), nq, L[i], M[i], dtype, max_m, 0, &t[i].m,
+                                 &t[i].p, &t[i].q, &t[i].D);
         t[i].model_flops = model_flops_axis(L[i], t[i].m, t[i].q);
         t[i].ms = -1.0;
     }
