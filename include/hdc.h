@@ -79,7 +79,8 @@ typedef enum hdc_mode {
     HDC_TUNE_EXHAUSTIVE = 1,  /* grid search on the device (Section 4.2), cached     */
     HDC_PREDICT_MLP = 2,      /* learned predictor of the parameters                 */
     HDC_EXPLICIT = 3,         /* explicit padding m = nextgood(M), p = q = 1 (3.1)   */
-    HDC_TUNE_CACHED_ONLY = 4  /* tuning database only; HDC_ERR_NOT_TUNED if absent   */
+    HDC_TUNE_CACHED_ONLY = 4, /* tuning database only; HDC_ERR_NOT_TUNED if absent   */
+    HDC_PREDICT_MLP_SEARCH = 5 /* time the predictor's 3 best classes per axis        */
 } hdc_mode;
 
 /* One parameter choice of one axis and its measured time. */
@@ -314,7 +315,10 @@ int hdc_tune_conv1d(int64_t L, int64_t M, int dtype, int64_t batch,
  * database.  HDC_FIXED takes m (and D, may be NULL) from the caller.
  * HDC_PREDICT_MLP reads the network checkpoint at `tuning_db` (written by
  * hdc_mlp_save with HDC_MLP_FEATURES inputs, HDC_MLP_HIDDEN hidden units and
- * hdc_mlp_num_q_classes() + 2 outputs) and runs its inference kernels. */
+ * hdc_mlp_num_q_classes() + 2 outputs) and runs its inference kernels;
+ * HDC_PREDICT_MLP_SEARCH then times the network's three most likely classes
+ * of every axis (one axis at a time, last first, the others held) on
+ * scratch buffers it allocates and frees, and keeps the fastest. */
 int hdc_plan_create(hdc_plan** plan, int dims, const int64_t* L,
                     const int64_t* M, const int64_t* m, const int64_t* D,
                     int dtype, int64_t batch, int mode, const char* tuning_db,

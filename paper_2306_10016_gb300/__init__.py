@@ -28,6 +28,7 @@ HDC_TUNE_EXHAUSTIVE = 1
 HDC_PREDICT_MLP = 2
 HDC_EXPLICIT = 3
 HDC_TUNE_CACHED_ONLY = 4
+HDC_PREDICT_MLP_SEARCH = 5
 
 HDC_OK = 0
 HDC_ERR_PARAM = -1
@@ -41,6 +42,10 @@ HDC_ERR_NOT_TUNED = -8
 HDC_ERR_WORKSPACE = -9
 
 LIB_PATH = _build_ext.LIB
+# the predictor network trained on this GPU's grid-search timings (a
+# checkpoint of hdc_mlp_save) and the dataset it was trained on
+MLP_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "mlp_gb300.bin")
+MLP_DATASET = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "mlp_dataset_gb300.json.gz")
 
 _i64 = C.c_int64
 _i64p = C.POINTER(C.c_int64)
@@ -516,6 +521,8 @@ class Plan:
         st = stream if stream is not None else torch.cuda.current_stream()
         mm = _arr(_per_axis(m, self.dims, "m")) if m is not None else None
         DD = _arr(_per_axis(D, self.dims, "D")) if D is not None else None
+        if tuning_db is None and mode in (HDC_PREDICT_MLP, HDC_PREDICT_MLP_SEARCH):
+            tuning_db = MLP_WEIGHTS
         db = tuning_db.encode() if tuning_db else None
         _check(lib().hdc_plan_create(C.byref(h), self.dims, _arr(self.L), _arr(self.M), mm, DD, dtype, self.batch,
                                      mode, db, st.cuda_stream), "plan_create")

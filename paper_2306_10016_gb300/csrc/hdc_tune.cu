@@ -347,10 +347,10 @@ struct hdc_plan {
     size_t ws;
 };
 
-// Parameters from the learned predictor: features of every axis, one
-// forward pass of the network on the device, decode per axis.
-static int predict_mlp(int dims, const int64_t* L, const int64_t* M, int dtype, int64_t batch, const char* path,
-                       cudaStream_t st, hdc_tuple* t)
+// Logits of the learned predictor for every axis: features, one forward
+// pass of the network on the device.
+static int mlp_logits(int dims, const int64_t* L, const int64_t* M, int dtype, int64_t batch, const char* path,
+                      cudaStream_t st, std::vector<float>& logits)
 {
     if (!path || !*path) return HDC_ERR_NOT_TUNED;
     const int nq = hdc_mlp_num_q_classes();
@@ -360,7 +360,7 @@ static int predict_mlp(int dims, const int64_t* L, const int64_t* M, int dtype, 
     if (hdc_mlp_load(net, path) != HDC_OK) { hdc_mlp_destroy(net); return HDC_ERR_NOT_TUNED; }
     float feat[HDC_MAX_DIMS * HDC_MLP_FEATURES];
     rc = hdc_mlp_axis_features(dims, L, M, dtype, batch, feat);
-    std::vector<float> logits((size_t)dims * (nq + 2));
+    logits.assign((size_t)dims * (nq + 2), 0.f);
     float* dbuf = nullptr;
     if (rc == HDC_OK && cudaMalloc(&dbuf, sizeof(float) * (size_t)dims * (HDC_MLP_FEATURES + nq + 2)) != cudaSuccess)
         rc = HDC_ERR_ALLOC;
@@ -379,14 +379,82 @@ static int predict_mlp(int dims, const int64_t* L, const int64_t* M, int dtype, 
     }
     cudaFree(dbuf);
     hdc_mlp_destroy(net);
-    for (int i = 0; i < dims && rc == HDC_OK; ++i) {
-        const int64_t max_m = i < dims - 1 ? hdc_max_outer_fft_size(dtype) : 0;
-        rc = hdc_mlp_decode_axis(logits.data() + (size_t)i * (nq + 2), nq, L[i], M[i], dtype, max_m, 0, &t[i].m,
-                                 &t[i].p, &t[i].q, &t[i].D);
-        t[i].model_flops = model_flops_axis(L[i], t[i].m, t[i].q);
-        t[i].ms = -1.0;
-    }
     return rc;
+}
+
+// k-th most likely valid tuple of axis i (outer axes within one column tile)
+static int mlp_axis_choice(const std::vector<float>& logits, int dims, int i, const int64_t* L, const int64_t* M,
+                           int dtype, int rank, hdc_tuple* t)
+{
+    const int nq = hdc_mlp_num_q_classes();
+    const int64_t max_m = i < dims - 1 ? hdc_max_outer_fft_size(dtype) : 0;
+    int rc = hdc_mlp_decode_axis(logits.data() + (size_t)i * (nq + 2), nq, L[i], M[i], dtype, max_m, rank, &t->m,
+                                 &t->p, &t->q, &t->D);
+    t->model_flops = model_flops_axis(L[i], t->m, t->q);
+    t->ms = -1.0;
+    return rc;
+}
+
+// Parameters from the learned predictor: its most likely class per axis, or
+// (search) the fastest of its `topk` most likely classes per axis, timed
+// one axis at a time with the others held (last axis first) on scratch
+// buffers allocated here.
+static int predict_mlp(int dims, const int64_t* L, const int64_t* M, int dtype, int64_t batch, const char* path,
+                       cudaStream_t st, hdc_tuple* t, int topk)
+{
+    std::vector<float> logits;
+    int rc = mlp_logits(dims, L, M, dtype, batch, path, st, logits);
+    if (rc != HDC_OK) return rc;
+    for (int i = 0; i < dims; ++i) {
+        rc = mlp_axis_choice(logits, dims, i, L, M, dtype, 0, &t[i]);
+        if (rc != HDC_OK) return rc;
+    }
+    if (topk <= 1) return HDC_OK;
+    int64_t tot = batch;
+    for (int i = 0; i < dims; ++i) tot *= L[i];
+    const size_t esz = dtype == HDC_C128 ? 16 : 8;
+    // the largest workspace of the candidates
+    size_t wsb = 0;
+    std::vector<hdc_tuple> cand[HDC_MAX_DIMS];
+    for (int i = 0; i < dims; ++i)
+        for (int r = 0; r < topk; ++r) {
+            hdc_tuple c;
+            if (mlp_axis_choice(logits, dims, i, L, M, dtype, r, &c) == HDC_OK) cand[i].push_back(c);
+        }
+    for (int i = 0; i < dims; ++i)
+        for (const auto& c : cand[i]) {
+            int64_t mm[HDC_MAX_DIMS], DD[HDC_MAX_DIMS];
+            for (int j = 0; j < dims; ++j) { mm[j] = t[j].m; DD[j] = t[j].D; }
+            mm[i] = c.m;
+            DD[i] = c.D;
+            size_t b = 0;
+            if (hdc_workspace_size(dims, L, M, mm, nullptr, nullptr, DD, dtype, batch, 0, &b) == HDC_OK)
+                wsb = std::max(wsb, b);
+        }
+    void *bf = nullptr, *bg = nullptr, *bh = nullptr, *bw = nullptr;
+    if (cudaMalloc(&bf, tot * esz) != cudaSuccess || cudaMalloc(&bg, tot * esz) != cudaSuccess ||
+        cudaMalloc(&bh, tot * esz) != cudaSuccess || cudaMalloc(&bw, wsb) != cudaSuccess) {
+        cudaFree(bf); cudaFree(bg); cudaFree(bh); cudaFree(bw);
+        return HDC_ERR_ALLOC;
+    }
+    cudaMemsetAsync(bf, 0, tot * esz, st);
+    cudaMemsetAsync(bg, 0, tot * esz, st);
+    for (int i = dims - 1; i >= 0; --i) {
+        double best = -1.0;
+        hdc_tuple pick = t[i];
+        for (const auto& c : cand[i]) {
+            hdc_tuple trial[HDC_MAX_DIMS];
+            for (int j = 0; j < dims; ++j) trial[j] = t[j];
+            trial[i] = c;
+            const double ms = time_config(dims, bf, bg, bh, L, M, trial, dtype, batch, bw, wsb, 1, 3, st);
+            if (ms >= 0 && (best < 0 || ms < best)) { best = ms; pick = c; }
+        }
+        t[i] = pick;
+        t[i].ms = best;
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(bf); cudaFree(bg); cudaFree(bh); cudaFree(bw);
+    return HDC_OK;
 }
 
 HDC_EXPORT int hdc_plan_create(hdc_plan** out, int dims, const int64_t* L, const int64_t* M, const int64_t* m,
@@ -445,8 +513,9 @@ HDC_EXPORT int hdc_plan_create(hdc_plan** out, int dims, const int64_t* L, const
             if (rc != HDC_OK) return rc;
             db_store(tuning_db, key, dims, pl.t);
         }
-    } else if (mode == HDC_PREDICT_MLP) {
-        int rc = predict_mlp(dims, L, M, dtype, batch, tuning_db, (cudaStream_t)stream, pl.t);
+    } else if (mode == HDC_PREDICT_MLP || mode == HDC_PREDICT_MLP_SEARCH) {
+        int rc = predict_mlp(dims, L, M, dtype, batch, tuning_db, (cudaStream_t)stream, pl.t,
+                             mode == HDC_PREDICT_MLP_SEARCH ? 3 : 1);
         if (rc != HDC_OK) return rc;
     } else {
         return HDC_ERR_PARAM;

@@ -131,3 +131,20 @@ def test_plan_predict_mlp(hdc, tmp_path):
     with pytest.raises(hdc.HDCError) as ei:
         hdc.Plan(list(shape), mode=hdc.HDC_PREDICT_MLP, tuning_db=str(tmp_path / "none.bin"))
     assert ei.value.code == hdc.HDC_ERR_NOT_TUNED
+
+
+def test_plan_predict_mlp_search_packaged(hdc):
+    """The packaged predictor with the guided search of its three best
+    classes per axis gives a valid, correct plan."""
+    import os
+    if not os.path.exists(hdc.MLP_WEIGHTS):
+        pytest.skip("no trained predictor in the package")
+    shape = (96, 320)
+    pl = hdc.Plan(list(shape), mode=hdc.HDC_PREDICT_MLP_SEARCH)
+    prm = pl.params
+    assert all(p["q"] * p["m"] >= 2 * L - 1 for p, L in zip(prm, shape))
+    f = synth.unit_disk(41, shape)
+    g = synth.unit_disk(42, shape)
+    h = pl.execute(torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    assert rel_max_err(h.cpu().numpy(), oracle.conv_fft(f, g)) < 1e-12
