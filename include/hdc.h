@@ -250,8 +250,9 @@ int hdc_release_caches(void);
  * hdc_conv1d_noalloc computes the same 1-D convolution as hdc_conv1d (same
  * parameters and results) but calls no cudaMalloc, cudaFree or allocating
  * library routine, takes no workspace and leaves the twiddle cache alone.
- * Its scratch -- the two twiddle tables (q m and m entries) and the
- * D x batch x m residue workspace, each rounded up to 256 bytes -- lives in
+ * Its scratch -- the twiddle tables (q m entries, and m entries in two
+ * forms) and the D x batch x m residue workspace, each rounded up to 256
+ * bytes -- lives in
  * one fixed device array of HDC_NOALLOC_SCRATCH_BYTES that every GPU loading
  * the library holds until the process exits.
  *  - f, g, h: device pointers (batch x L complex); h may alias neither f nor

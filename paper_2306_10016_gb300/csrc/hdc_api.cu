@@ -18,6 +18,7 @@
 namespace hdc {
 
 template <typename T> cudaError_t launch_twiddle(cx<T>* tw, int64_t n, cudaStream_t st);
+template <typename T> cudaError_t launch_twiddle_lf(cx<T>* tw, int64_t n, cudaStream_t st);
 
 // ----------------------------------------------------------- FFT plans
 
@@ -45,12 +46,12 @@ std::mutex g_tw_mu;
 std::map<std::tuple<int, int64_t, int>, void*> g_tw;
 } // namespace
 
-template <typename T> const cx<T>* twiddles(int64_t n, cudaError_t* err)
+template <typename T> static const cx<T>* twiddle_table(int64_t n, bool lf, cudaError_t* err)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) { *err = e; return nullptr; }
-    const int dt = sizeof(T) == 8 ? 1 : 0;
+    const int dt = (sizeof(T) == 8 ? 1 : 0) + (lf ? 2 : 0);
     std::lock_guard<std::mutex> lk(g_tw_mu);
     auto key = std::make_tuple(dev, n, dt);
     auto it = g_tw.find(key);
@@ -63,7 +64,8 @@ template <typename T> const cx<T>* twiddles(int64_t n, cudaError_t* err)
     cudaStream_t s;
     e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e == cudaSuccess) {
-        e = launch_twiddle<T>(reinterpret_cast<cx<T>*>(p), n, s);
+        e = lf ? launch_twiddle_lf<T>(reinterpret_cast<cx<T>*>(p), n, s)
+               : launch_twiddle<T>(reinterpret_cast<cx<T>*>(p), n, s);
         cudaError_t e2 = cudaStreamSynchronize(s);
         if (e == cudaSuccess) e = e2;
         cudaStreamDestroy(s);
@@ -72,6 +74,11 @@ template <typename T> const cx<T>* twiddles(int64_t n, cudaError_t* err)
     g_tw[key] = p;
     return reinterpret_cast<const cx<T>*>(p);
 }
+
+template <typename T> const cx<T>* twiddles(int64_t n, cudaError_t* err) { return twiddle_table<T>(n, false, err); }
+template <typename T> const cx<T>* twiddles_lf(int64_t n, cudaError_t* err) { return twiddle_table<T>(n, true, err); }
+template const cx<double>* twiddles_lf<double>(int64_t, cudaError_t*);
+template const cx<float>* twiddles_lf<float>(int64_t, cudaError_t*);
 template const cx<double>* twiddles<double>(int64_t, cudaError_t*);
 template const cx<float>* twiddles<float>(int64_t, cudaError_t*);
 

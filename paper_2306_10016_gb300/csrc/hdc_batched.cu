@@ -39,6 +39,8 @@ template <class V> struct BConv {
     const V* twN;
     const V* twm;  // m-point table (fused) or m2-point table (split rows)
     const V* twm1; // m1-point table (split columns)
+    const V* twml;  // the same two tables in scale-tangent form
+    const V* twm1l;
     int64_t L, N, ws_off;
     int m, p, q, m1, m2, C, nct, per; // m1 == 0: fused; per = outputs per residue block
     FftPlan fpm;                      // plan of m (fused) or m2 (split rows)
@@ -115,22 +117,23 @@ k_batched(const BConv<V>* __restrict__ convs, const BItem* __restrict__ it0, con
                 const V* x = which ? gp_[itm.conv] : fp_[itm.conv];
                 V* yb = cws + (int64_t)which * cv.q * cv.m + (int64_t)r * cv.m;
                 fold_fft_cols_body<V>(x, yb, cv.m2, cv.m1, cv.p, cv.q, cv.N, cv.m2, 1, cv.L, r, (int64_t)ct * cv.C,
-                                      cv.C, 1, cv.twN, cv.twm1, cv.fpm1, smem, tid, nthr);
+                                      cv.C, 1, cv.twN, cv.twm1, cv.twm1l, cv.fpm1, smem, tid, nthr);
             } else if (ph == 1) {
                 if (cv.m1 == 0) {
                     const int r = itm.a;
                     residue_row_body<V>(fp_[itm.conv], gp_[itm.conv], cws + (int64_t)r * cv.m, cv.L, cv.m, cv.p,
-                                        cv.q, r, cv.twN, cv.twm, cv.fpm, smem, tid, nthr);
+                                        cv.q, r, cv.twN, cv.twm, cv.twml, cv.fpm, smem, tid, nthr);
                 } else {
                     const int64_t row = itm.a;
                     V* yf = cws + row * cv.m2;
                     const V* yg = cws + (int64_t)cv.q * cv.m + row * cv.m2;
-                    residue_row_body<V>(yf, yg, yf, cv.m2, cv.m2, 1, 1, 0, cv.twm, cv.twm, cv.fpm, smem, tid, nthr);
+                    residue_row_body<V>(yf, yg, yf, cv.m2, cv.m2, 1, 1, 0, cv.twm, cv.twm, cv.twml, cv.fpm, smem, tid,
+                                        nthr);
                 }
             } else if (ph == 2) {
                 const int r = itm.a, ct = itm.c;
                 ifft_cols_body<V>(cws + (int64_t)r * cv.m, cv.m2, cv.m1, cv.q, cv.N, (int64_t)ct * cv.C, cv.C, 1,
-                                  cv.twN, cv.twm1, cv.fpm1, smem, tid, nthr);
+                                  cv.twN, cv.twm1, cv.twm1l, cv.fpm1, smem, tid, nthr);
             } else {
                 const int64_t e0 = (int64_t)itm.a * kUnfoldChunk;
                 const int64_t e1 = min((int64_t)cv.per, e0 + kUnfoldChunk);
@@ -231,9 +234,13 @@ template <typename T> int build(hdc_batched* b)
         if (e != cudaSuccess) return HDC_ERR_CUDA;
         cv.twm = twiddles<T>(m1 ? m2 : b->m[i], &e);
         if (e != cudaSuccess) return HDC_ERR_CUDA;
+        cv.twml = twiddles_lf<T>(m1 ? m2 : b->m[i], &e);
+        if (e != cudaSuccess) return HDC_ERR_CUDA;
         cv.fpm = make_fft_plan(m1 ? m2 : b->m[i]);
         if (m1) {
             cv.twm1 = twiddles<T>(m1, &e);
+            if (e != cudaSuccess) return HDC_ERR_CUDA;
+            cv.twm1l = twiddles_lf<T>(m1, &e);
             if (e != cudaSuccess) return HDC_ERR_CUDA;
             cv.fpm1 = make_fft_plan(m1);
             cv.C = col_tile_b<T>(m2, m1);
@@ -245,7 +252,7 @@ template <typename T> int build(hdc_batched* b)
         b->m1[i] = m1;
         b->m2[i] = m2;
         convs[(size_t)i] = cv;
-        smem = std::max(smem, (size_t)(3 * (m1 ? m2 : b->m[i])) * sizeof(V));
+        smem = std::max(smem, (size_t)(3 * padded_len(m1 ? m2 : b->m[i])) * sizeof(V));
         if (m1) smem = std::max(smem, (size_t)(2 * m1 * cv.C) * sizeof(V));
         cost.emplace_back((double)cv.q * cv.m * std::log2((double)cv.m + 1.0) + (double)cv.q * cv.L, i);
     }

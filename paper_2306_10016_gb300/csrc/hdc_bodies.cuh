@@ -11,20 +11,23 @@ namespace hdc {
 
 // One residue r of one row: fold (Eq. 1 inner sum, then zeta_N^{r s}) of f
 // and g, m-point forward FFTs, pointwise product (Section 2.4), inverse FFT
-// (Eq. 2 inner sum); the unscaled result goes to hr[0..m).  smem: 3 m.
-// With p = q = 1 and L >= m the fold is a plain copy of the rows.
+// (Eq. 2 inner sum); the unscaled result goes to hr[0..m).  smem: three
+// padded buffers of m (3 padded_len(m) elements).  With p = q = 1 and
+// L >= m the fold is a plain copy of the rows.
 template <class V>
 __device__ __forceinline__ void residue_row_body(const V* fr, const V* gr, V* hr, int64_t L, int m, int p, int q,
                                                  int r, const V* __restrict__ twN, const V* __restrict__ twm,
-                                                 const FftPlan& fp, V* smem, int tid, int nthr)
+                                                 const V* __restrict__ twml, const FftPlan& fp, V* smem, int tid,
+                                                 int nthr)
 {
+    const int plen = (int)padded_len(m);
     V* sa = smem;
-    V* sb = sa + m;
-    V* sc = sb + m;
+    V* sb = sa + plen;
+    V* sc = sb + plen;
     if (p == 1 && q == 1 && L >= m) {
         for (int s = tid; s < m; s += nthr) {
-            sa[s] = fr[s];
-            sb[s] = gr[s];
+            sa[sidx<true>(s)] = fr[s];
+            sb[sidx<true>(s)] = gr[s];
         }
     } else {
         for (int s = tid; s < m; s += nthr) {
@@ -47,17 +50,17 @@ __device__ __forceinline__ void residue_row_body(const V* fr, const V* gr, V* hr
                 af = cmul(af, w);
                 ag = cmul(ag, w);
             }
-            sa[s] = af;
-            sb[s] = ag;
+            sa[sidx<true>(s)] = af;
+            sb[sidx<true>(s)] = ag;
         }
     }
     __syncthreads();
-    fft_smem<V, false>(sa, sc, fp, 1, 1, m, twm, tid, nthr);
-    fft_smem<V, false>(sb, sc, fp, 1, 1, m, twm, tid, nthr);
-    for (int s = tid; s < m; s += nthr) sa[s] = cmul(sa[s], sb[s]);
+    fft_smem<V, false, true>(sa, sc, fp, 1, 1, m, twm, twml, tid, nthr);
+    fft_smem<V, false, true>(sb, sc, fp, 1, 1, m, twm, twml, tid, nthr);
+    for (int s = tid; s < m; s += nthr) sa[sidx<true>(s)] = cmul(sa[sidx<true>(s)], sb[sidx<true>(s)]);
     __syncthreads();
-    fft_smem<V, true>(sa, sc, fp, 1, 1, m, twm, tid, nthr);
-    for (int s = tid; s < m; s += nthr) hr[s] = sa[s];
+    fft_smem<V, true, true>(sa, sc, fp, 1, 1, m, twm, twml, tid, nthr);
+    for (int s = tid; s < m; s += nthr) hr[s] = sa[sidx<true>(s)];
     __syncthreads();
 }
 
@@ -69,8 +72,8 @@ template <class V>
 __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn, int ma, int p, int q, int64_t Nf,
                                                    int64_t cs, int64_t cc, int64_t Lvalid, int r, int64_t c0, int C,
                                                    int post, const V* __restrict__ twNf,
-                                                   const V* __restrict__ twma, const FftPlan& fp, V* smem, int tid,
-                                                   int nthr)
+                                                   const V* __restrict__ twma, const V* __restrict__ twmal,
+                                                   const FftPlan& fp, V* smem, int tid, int nthr)
 {
     V* buf = smem;
     V* tmp = buf + ma * C;
@@ -92,7 +95,7 @@ __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn
         buf[e] = acc;
     }
     __syncthreads();
-    if (ma > 1) fft_smem<V, false>(buf, tmp, fp, C, C, 1, twma, tid, nthr);
+    if (ma > 1) fft_smem<V, false>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);
     for (int e = tid; e < ma * C; e += nthr) {
         const int l = e / C, cl = e - l * C;
         const int64_t c = c0 + cl;
@@ -110,7 +113,8 @@ __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn
 template <class V>
 __device__ __forceinline__ void ifft_cols_body(V* yb, int64_t Cn, int ma, int q, int64_t Nf, int64_t c0, int C,
                                                int pre, const V* __restrict__ twNf, const V* __restrict__ twma,
-                                               const FftPlan& fp, V* smem, int tid, int nthr)
+                                               const V* __restrict__ twmal, const FftPlan& fp, V* smem, int tid,
+                                               int nthr)
 {
     V* buf = smem;
     V* tmp = buf + ma * C;
@@ -125,7 +129,7 @@ __device__ __forceinline__ void ifft_cols_body(V* yb, int64_t Cn, int ma, int q,
         buf[e] = v;
     }
     __syncthreads();
-    if (ma > 1) fft_smem<V, true>(buf, tmp, fp, C, C, 1, twma, tid, nthr);
+    if (ma > 1) fft_smem<V, true>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);
     for (int e = tid; e < ma * C; e += nthr) {
         const int s = e / C, cl = e - s * C;
         const int64_t c = c0 + cl;

@@ -14,7 +14,9 @@
 //   outputs (j div Ns) Ns R + (j mod Ns) + r Ns
 // after which the data of the next stage is in order, so no bit reversal is
 // ever needed.  Twiddles come from a table tw[k] = zeta_n^k, k < n, made in
-// FP64 from exact integer angles.
+// FP64 from exact integer angles; radix-2, 4 and 8 stages after the first
+// merge them into their butterflies from a second table twl of the same
+// values in scale-tangent form (see lf_bfly).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -192,6 +194,127 @@ template <class V, bool INV> struct Dft<V, 3, INV> : DftOdd<V, 3, INV> {};
 template <class V, bool INV> struct Dft<V, 5, INV> : DftOdd<V, 5, INV> {};
 template <class V, bool INV> struct Dft<V, 7, INV> : DftOdd<V, 7, INV> {};
 
+// ------------------------------------------- twiddle-merged butterflies
+// A twiddled butterfly a +- w b in 6 FMAs (the tangent form of Linzer and
+// Feig): the table keeps w as sc (1 + i t) with |t| <= 1 ("form 0",
+// sc = cos) or as i sc (1 + i t) ("form 1", sc = sin); the form is the last
+// mantissa bit of sc.  u = (1 + i t) b takes 2 FMAs; in form 1, i u swaps
+// the parts and negates one, and that sign goes into the per-twiddle scale
+// pair (sx, sy), so a +- w b = (a.x +- sx px, a.y +- sy py) with (px, py) =
+// (u.x, u.y) or (u.y, u.x) picked by register selects: 4 more FMAs.  The
+// inverse transform uses conj(w): t -> -t, and the sign of form 1 moves to
+// sy.  The sign flips are integer XORs on the high word, made once per
+// twiddle, so the FP64 pipe sees the 6 FMAs only.
+
+__device__ __forceinline__ double flip_sign_if(double x, bool c)
+{
+    unsigned hi = (unsigned)__double2hiint(x), out;
+    asm("xor.b32 %0, %1, %2;" : "=r"(out) : "r"(hi), "r"((unsigned)c << 31));
+    return __hiloint2double((int)out, __double2loint(x));
+}
+__device__ __forceinline__ float flip_sign_if(float x, bool c)
+{
+    unsigned out;
+    asm("xor.b32 %0, %1, %2;" : "=r"(out) : "r"(__float_as_uint(x)), "r"((unsigned)c << 31));
+    return __uint_as_float(out);
+}
+
+template <class V> __device__ __forceinline__ bool lf_form(V e);
+template <> __device__ __forceinline__ bool lf_form<double2>(double2 e)
+{
+    return (__double2loint(e.x) & 1) != 0;
+}
+template <> __device__ __forceinline__ bool lf_form<float2>(float2 e) { return (__float_as_int(e.x) & 1) != 0; }
+
+template <class V> struct LfW {
+    using T = typename real_of<V>::type;
+    T sx, sy, tt;
+    bool f1;
+};
+
+template <class V, bool INV> __device__ __forceinline__ LfW<V> lf_prep(V e)
+{
+    LfW<V> w;
+    w.f1 = lf_form(e);
+    w.tt = e.y;
+    w.sx = INV ? e.x : flip_sign_if(e.x, w.f1);
+    w.sy = INV ? flip_sign_if(e.x, w.f1) : e.x;
+    return w;
+}
+
+template <class V, bool INV> __device__ __forceinline__ void lf_bfly(V& a, V& b, const LfW<V>& w)
+{
+    using T = typename real_of<V>::type;
+    const T ux = INV ? fma(w.tt, b.y, b.x) : fma(-w.tt, b.y, b.x);
+    const T uy = INV ? fma(-w.tt, b.x, b.y) : fma(w.tt, b.x, b.y);
+    const T px = w.f1 ? uy : ux;
+    const T py = w.f1 ? ux : uy;
+    const V a0 = a;
+    a = mkc<V>(fma(w.sx, px, a0.x), fma(w.sy, py, a0.y));
+    b = mkc<V>(fma(-w.sx, px, a0.x), fma(-w.sy, py, a0.y));
+}
+
+template <class V, bool INV> __device__ __forceinline__ LfW<V> lf_load(const V* __restrict__ twl, int i)
+{
+    return lf_prep<V, INV>(ldg_c(twl + i));
+}
+
+// DFT_R of (W^r x_r), W = zeta_n^k (k < n/R), as R/2 log2 R twiddle-merged
+// butterflies; twl[e] = zeta_n^e in the form above.  Outputs in natural order.
+template <class V, int R, bool INV> struct DftLF;
+
+template <class V, bool INV> struct DftLF<V, 2, INV> {
+    static __device__ __forceinline__ void run(V* v, const V* __restrict__ twl, int k, int n)
+    {
+        lf_bfly<V, INV>(v[0], v[1], lf_load<V, INV>(twl, k));
+    }
+};
+
+template <class V, bool INV> struct DftLF<V, 4, INV> {
+    // B_r = x_r +- W^2 x_{r+2}; X_0, X_2 = B_0+ +- W B_1+; X_1, X_3 = B_0- +- (i W) B_1-
+    static __device__ __forceinline__ void run(V* v, const V* __restrict__ twl, int k, int n)
+    {
+        const LfW<V> w2 = lf_load<V, INV>(twl, 2 * k), w1 = lf_load<V, INV>(twl, k), wi = lf_load<V, INV>(twl, k + n / 4);
+        lf_bfly<V, INV>(v[0], v[2], w2);
+        lf_bfly<V, INV>(v[1], v[3], w2);
+        lf_bfly<V, INV>(v[0], v[1], w1);  // v0 = X0, v1 = X2
+        lf_bfly<V, INV>(v[2], v[3], wi);  // v2 = X1, v3 = X3
+        const V x1 = v[2], x2 = v[1];
+        v[1] = x1;
+        v[2] = x2;
+    }
+};
+
+template <class V, bool INV> struct DftLF<V, 8, INV> {
+    // B_r = x_r +- W^4 x_{r+4}; evens: E_r = B_r+ +- W^2 B_{r+2}+, X_0/4 = E_0+ +- W E_1+,
+    // X_2/6 = E_0- +- (iW) E_1-; odds (V = zeta_8 W): F_r = B_r- +- (i W^2) B_{r+2}-,
+    // X_1/5 = F_0+ +- (zeta_8 W) F_1+, X_3/7 = F_0- +- (zeta_8^3 W) F_1-
+    static __device__ __forceinline__ void run(V* v, const V* __restrict__ twl, int k, int n)
+    {
+        const int e8 = n / 8;
+        const LfW<V> w4 = lf_load<V, INV>(twl, 4 * k);
+        lf_bfly<V, INV>(v[0], v[4], w4);
+        lf_bfly<V, INV>(v[1], v[5], w4);
+        lf_bfly<V, INV>(v[2], v[6], w4);
+        lf_bfly<V, INV>(v[3], v[7], w4);
+        // v0..3 = B+, v4..7 = B-
+        const LfW<V> w2 = lf_load<V, INV>(twl, 2 * k), w2i = lf_load<V, INV>(twl, 2 * k + 2 * e8);
+        lf_bfly<V, INV>(v[0], v[2], w2);   // E0+, E0-
+        lf_bfly<V, INV>(v[1], v[3], w2);   // E1+, E1-
+        lf_bfly<V, INV>(v[4], v[6], w2i);  // F0+, F0-
+        lf_bfly<V, INV>(v[5], v[7], w2i);  // F1+, F1-
+        const LfW<V> w1 = lf_load<V, INV>(twl, k), wi = lf_load<V, INV>(twl, k + 2 * e8);
+        const LfW<V> z1 = lf_load<V, INV>(twl, k + e8), z3 = lf_load<V, INV>(twl, k + 3 * e8);
+        lf_bfly<V, INV>(v[0], v[1], w1);   // X0, X4
+        lf_bfly<V, INV>(v[2], v[3], wi);   // X2, X6
+        lf_bfly<V, INV>(v[4], v[5], z1);   // X1, X5
+        lf_bfly<V, INV>(v[6], v[7], z3);   // X3, X7
+        const V X0 = v[0], X4 = v[1], X2 = v[2], X6 = v[3], X1 = v[4], X5 = v[5], X3 = v[6], X7 = v[7];
+        v[0] = X0; v[1] = X1; v[2] = X2; v[3] = X3;
+        v[4] = X4; v[5] = X5; v[6] = X6; v[7] = X7;
+    }
+};
+
 // ---------------------------------------------------------- FFT plan
 
 #define HDC_MAX_STAGES 32
@@ -204,11 +327,21 @@ struct FftPlan {
 
 // ---------------------------------------------------------- one stage
 // src -> dst (distinct shared buffers); one barrier at the end.
+//
+// With PAD, logical element x lives at x + x/8: the first stage's outputs go
+// to positions R apart, and without the pad slot every lane of a warp would
+// hit the same banks (R = 8 complex values = 128 bytes in FP64, 64 in FP32).
 
-template <class V, int R, bool INV>
+template <bool PAD> __device__ __forceinline__ int sidx(int x) { return PAD ? x + (x >> 3) : x; }
+
+// shared-memory elements a padded buffer of n logical elements occupies
+__host__ __device__ constexpr int64_t padded_len(int64_t n) { return n + (n >> 3) + 1; }
+
+template <class V, int R, bool INV, bool PAD>
 __device__ __forceinline__ void fft_stage(const V* src, V* dst, int n, int ncol, int ld, int cs, int Ns,
-                                          const V* __restrict__ tw, int tid, int nthr)
+                                          const V* __restrict__ tw, const V* __restrict__ twl, int tid, int nthr)
 {
+    constexpr bool kLF = (R == 2 || R == 4 || R == 8);
     const int nb = n / R;
     const int total = nb * ncol;
     const int tstep = n / (Ns * R);
@@ -218,20 +351,25 @@ __device__ __forceinline__ void fft_stage(const V* src, V* dst, int n, int ncol,
         const int base = c * cs;
         V v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[base + (j + r * nb) * ld];
+        for (int r = 0; r < R; ++r) v[r] = src[sidx<PAD>(base + (j + r * nb) * ld)];
         const int jm = j % Ns;
-        if (jm != 0) {
-            const int k = jm * tstep;
+        if (kLF && Ns > 1) {
+            // every butterfly of the stage carries its twiddles (W = 1 when jm = 0)
+            DftLF<V, kLF ? R : 2, INV>::run(v, twl, jm * tstep, n);
+        } else {
+            if (jm != 0) {
+                const int k = jm * tstep;
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                const V w = ldg_c(tw + r * k);
-                v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+                for (int r = 1; r < R; ++r) {
+                    const V w = ldg_c(tw + r * k);
+                    v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+                }
             }
+            Dft<V, R, INV>::run(v);
         }
-        Dft<V, R, INV>::run(v);
         const int o = base + ((j - jm) * R + jm) * ld;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[o + r * Ns * ld] = v[r];
+        for (int r = 0; r < R; ++r) dst[sidx<PAD>(o + r * Ns * ld)] = v[r];
     }
     __syncthreads();
 }
@@ -240,9 +378,9 @@ __device__ __forceinline__ void fft_stage(const V* src, V* dst, int n, int ncol,
 // addressing) as the other half of the ping-pong.  The caller must have
 // synchronised after filling buf; on return the result is in buf and the
 // block is synchronised.
-template <class V, bool INV>
+template <class V, bool INV, bool PAD = false>
 __device__ __forceinline__ void fft_smem(V* buf, V* tmp, const FftPlan& fp, int ncol, int ld, int cs,
-                                         const V* __restrict__ tw, int tid, int nthr)
+                                         const V* __restrict__ tw, const V* __restrict__ twl, int tid, int nthr)
 {
     int Ns = 1;
     const int n = fp.n;
@@ -251,12 +389,12 @@ __device__ __forceinline__ void fft_smem(V* buf, V* tmp, const FftPlan& fp, int 
     for (int s = 0; s < fp.nst; ++s) {
         const int R = fp.rad[s];
         switch (R) {
-        case 8: fft_stage<V, 8, INV>(a, b, n, ncol, ld, cs, Ns, tw, tid, nthr); break;
-        case 4: fft_stage<V, 4, INV>(a, b, n, ncol, ld, cs, Ns, tw, tid, nthr); break;
-        case 2: fft_stage<V, 2, INV>(a, b, n, ncol, ld, cs, Ns, tw, tid, nthr); break;
-        case 3: fft_stage<V, 3, INV>(a, b, n, ncol, ld, cs, Ns, tw, tid, nthr); break;
-        case 5: fft_stage<V, 5, INV>(a, b, n, ncol, ld, cs, Ns, tw, tid, nthr); break;
-        case 7: fft_stage<V, 7, INV>(a, b, n, ncol, ld, cs, Ns, tw, tid, nthr); break;
+        case 8: fft_stage<V, 8, INV, PAD>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
+        case 4: fft_stage<V, 4, INV, PAD>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
+        case 2: fft_stage<V, 2, INV, PAD>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
+        case 3: fft_stage<V, 3, INV, PAD>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
+        case 5: fft_stage<V, 5, INV, PAD>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
+        case 7: fft_stage<V, 7, INV, PAD>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
         default: break;
         }
         Ns *= R;
@@ -268,7 +406,7 @@ __device__ __forceinline__ void fft_smem(V* buf, V* tmp, const FftPlan& fp, int 
         const int tot = n * ncol;
         for (int e = tid; e < tot; e += nthr) {
             const int i = e / ncol, c = e - i * ncol;
-            buf[c * cs + i * ld] = a[c * cs + i * ld];
+            buf[sidx<PAD>(c * cs + i * ld)] = a[sidx<PAD>(c * cs + i * ld)];
         }
         __syncthreads();
     }

@@ -15,16 +15,20 @@ namespace hdc {
 // two blocks share an SM.
 constexpr int kMaxThreads = 256;
 // Shared-memory budgets.  The fused residue kernel holds f, g and one
-// ping-pong buffer of m elements (3 m): 96 KiB keeps two blocks per SM, so
-// one block's loads and barriers overlap the other's arithmetic.  The
+// ping-pong buffer of m elements, each padded by one slot per 8 (3
+// padded_len(m)): 112 KiB still keeps two blocks per SM, so one block's
+// loads and barriers overlap the other's arithmetic.  The
 // strided-axis kernels hold a tile of ma x C elements and its ping-pong twin
 // (2 ma C): C is chosen so a tile fits 64 KiB (three blocks per SM), and a
 // single column may use up to 128 KiB.
-constexpr int64_t kRowBytes = 96 * 1024;
+constexpr int64_t kRowBytes = 112 * 1024;
 constexpr int64_t kColTargetBytes = 64 * 1024;
 constexpr int64_t kColMaxBytes = 128 * 1024;
 
-template <typename T> constexpr int64_t max_row_fft() { return kRowBytes / (3 * (int64_t)sizeof(cx<T>)) / 16 * 16; }
+// largest power-of-two-rounded m whose three padded buffers fit kRowBytes
+template <typename T> constexpr int64_t max_row_fft() { return (int64_t)1 << (sizeof(cx<T>) == 16 ? 11 : 12); }
+static_assert(3 * padded_len(2048) * 16 <= kRowBytes, "FP64 row tile exceeds its budget");
+static_assert(3 * padded_len(4096) * 8 <= kRowBytes, "FP32 row tile exceeds its budget");
 template <typename T> constexpr int64_t col_tile_target() { return kColTargetBytes / (2 * (int64_t)sizeof(cx<T>)); }
 template <typename T> constexpr int64_t max_col_fft() { return kColMaxBytes / (2 * (int64_t)sizeof(cx<T>)); }
 
@@ -48,8 +52,11 @@ struct LaunchScope {
 // 5 n log2(n): the flop count convention of one n-point complex FFT.
 double fft_flops(double n);
 
-// Twiddle table zeta_n^k, k < n, of dtype T on the current device (cached).
+// Twiddle table zeta_n^k, k < n, of dtype T on the current device (cached),
+// and the same values in the scale-tangent form of the twiddle-merged
+// butterflies (see lf_bfly).
 template <typename T> const cx<T>* twiddles(int64_t n, cudaError_t* err);
+template <typename T> const cx<T>* twiddles_lf(int64_t n, cudaError_t* err);
 
 // ------------------------------------------------------------ launchers
 
@@ -98,10 +105,11 @@ cudaError_t launch_hermitian_expand(const cx<T>* half, cx<T>* full, int64_t K, i
 // twN = zeta_{q m}^k (q m entries), twm = zeta_m^k (m entries), twNf as in
 // launch_unfold; launch_twiddle_into fills a table of n entries on `st`.
 template <typename T> cudaError_t launch_twiddle_into(cx<T>* tw, int64_t n, cudaStream_t st);
+template <typename T> cudaError_t launch_twiddle_lf_into(cx<T>* tw, int64_t n, cudaStream_t st);
 template <typename T>
 cudaError_t launch_residue_rows_tw(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_t B, int64_t ld_in,
                                    int64_t L, int64_t m, int64_t p, int64_t q, int64_t r0, int64_t D,
-                                   const cx<T>* twN, const cx<T>* twm, cudaStream_t st);
+                                   const cx<T>* twN, const cx<T>* twm, const cx<T>* twml, cudaStream_t st);
 template <typename T>
 cudaError_t launch_unfold_tw(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstride, int64_t Cn, int64_t ma,
                              int64_t p, int64_t q, int64_t Nf, int64_t cs, int64_t cc, int64_t Lvalid,

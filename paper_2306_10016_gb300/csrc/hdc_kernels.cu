@@ -34,6 +34,46 @@ __global__ void k_twiddle(V* tw, int64_t n)
     tw[k] = mkc<V>((T)c, (T)s);
 }
 
+// The same values in scale-tangent form for the twiddle-merged butterflies:
+// w = scale (1 + i t) with scale = cos, t = tan when |cos| >= |sin| (form 0),
+// else w = i scale (1 + i t) with scale = sin, t = -cot (form 1); the form is
+// stored in the last mantissa bit of scale (a change of one unit in the last
+// place).
+__device__ __forceinline__ void lf_store(double2* tw, int64_t k, double sc, double tt, int form)
+{
+    long long b = (__double_as_longlong(sc) & ~1LL) | (long long)form;
+    tw[k] = make_double2(__longlong_as_double(b), tt);
+}
+__device__ __forceinline__ void lf_store(float2* tw, int64_t k, double sc, double tt, int form)
+{
+    int b = (__float_as_int((float)sc) & ~1) | form;
+    tw[k] = make_float2(__int_as_float(b), (float)tt);
+}
+
+template <class V>
+__global__ void k_twiddle_lf(V* tw, int64_t n)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t kk = (2 * k > n) ? k - n : k;
+    double s, c;
+    sincospi(2.0 * (double)kk / (double)n, &s, &c);
+    if (fabs(c) >= fabs(s)) lf_store(tw, k, c, s / c, 0);
+    else lf_store(tw, k, s, -c / s, 1);
+}
+
+template <typename T>
+cudaError_t launch_twiddle_lf(cx<T>* tw, int64_t n, cudaStream_t st)
+{
+    const int thr = 256;
+    const int64_t blocks = (n + thr - 1) / thr;
+    LaunchScope ls(K_TWIDDLE, st, 0.0, (double)n * sizeof(cx<T>));
+    k_twiddle_lf<cx<T>><<<(unsigned)blocks, thr, 0, st>>>(tw, n);
+    return cudaGetLastError();
+}
+template cudaError_t launch_twiddle_lf<double>(cx<double>*, int64_t, cudaStream_t);
+template cudaError_t launch_twiddle_lf<float>(cx<float>*, int64_t, cudaStream_t);
+
 template <typename T>
 cudaError_t launch_twiddle(cx<T>* tw, int64_t n, cudaStream_t st)
 {
@@ -71,13 +111,13 @@ template <class V>
 __global__ void __launch_bounds__(kMaxThreads, 2)
 k_residue_rows(const V* f, const V* g, V* h, int64_t B, int64_t ld_in, int64_t L, int m, int p,
                int q, int r0, int Dg, const V* __restrict__ twN, const V* __restrict__ twm,
-               FftPlan fp)
+               const V* __restrict__ twml, FftPlan fp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int64_t b = blockIdx.x % B;
     const int rr = (int)(blockIdx.x / B);
     residue_row_body<V>(f + b * ld_in, g + b * ld_in, h + ((int64_t)rr * B + b) * m, L, m, p, q, r0 + rr, twN, twm,
-                        fp, reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
+                        twml, fp, reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
 }
 
 template <typename T>
@@ -93,9 +133,11 @@ cudaError_t launch_residue_rows(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_
     if (e != cudaSuccess) return e;
     const V* twm = twiddles<T>(m, &e);
     if (e != cudaSuccess) return e;
+    const V* twml = twiddles_lf<T>(m, &e);
+    if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(m);
     const int thr = threads_for(m);
-    const size_t smem = (size_t)(3 * m) * sizeof(V);
+    const size_t smem = (size_t)(3 * padded_len(m)) * sizeof(V);
     auto kern = k_residue_rows<V>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     const int64_t blocks = B * Dg;
@@ -106,7 +148,7 @@ cudaError_t launch_residue_rows(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_
     LaunchScope ls(K_RESIDUE_ROWS, st, (double)(B * Dg) * (3.0 * fft_flops((double)m) + 6.0 * m + fold),
                    (2.0 * B * Lrow + (double)(Dg * B * m)) * sizeof(V));
     kern<<<(unsigned)blocks, thr, smem, st>>>(f, g, h, B, ld_in, L, (int)m, (int)p, (int)q, (int)r0,
-                                              (int)Dg, twN, twm, fp);
+                                              (int)Dg, twN, twm, twml, fp);
     return cudaGetLastError();
 }
 
@@ -125,7 +167,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
 k_fold_fft_cols(const V* __restrict__ f, const V* __restrict__ g, V* yf, V* yg, int64_t B,
                 int64_t bstride, int64_t Cn, int ma, int p, int q, int64_t Nf, int64_t cs,
                 int64_t cc, int64_t Lvalid, int r0, int Dg, int C, int nct, int post,
-                const V* __restrict__ twNf, const V* __restrict__ twma, FftPlan fp)
+                const V* __restrict__ twNf, const V* __restrict__ twma, const V* __restrict__ twmal, FftPlan fp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     int64_t blk = blockIdx.x;
@@ -137,8 +179,8 @@ k_fold_fft_cols(const V* __restrict__ f, const V* __restrict__ g, V* yf, V* yg, 
     const int64_t b = blk >> 1;
     const V* x = (which ? g : f) + b * bstride;
     V* yb = (which ? yg : yf) + ((int64_t)rr * B + b) * ma * Cn;
-    fold_fft_cols_body<V>(x, yb, Cn, ma, p, q, Nf, cs, cc, Lvalid, r0 + rr, (int64_t)ct * C, C, post, twNf, twma, fp,
-                          reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
+    fold_fft_cols_body<V>(x, yb, Cn, ma, p, q, Nf, cs, cc, Lvalid, r0 + rr, (int64_t)ct * C, C, post, twNf, twma,
+                          twmal, fp, reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
 }
 
 template <typename T>
@@ -155,6 +197,8 @@ cudaError_t launch_fold_fft_cols(const cx<T>* f, const cx<T>* g, cx<T>* yf, cx<T
     if (e != cudaSuccess) return e;
     const V* twma = twiddles<T>(ma, &e);
     if (e != cudaSuccess) return e;
+    const V* twmal = twiddles_lf<T>(ma, &e);
+    if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(ma);
     const int C = col_tile(Cn, ma, col_tile_target<T>());
     const int nct = (int)((Cn + C - 1) / C);
@@ -168,14 +212,14 @@ cudaError_t launch_fold_fft_cols(const cx<T>* f, const cx<T>* g, cx<T>* yf, cx<T
                    (2.0 * B * Lvalid + 2.0 * Dg * B * ma * Cn) * sizeof(V));
     kern<<<(unsigned)blocks, thr, smem, st>>>(f, g, yf, yg, B, bstride, Cn, (int)ma, (int)p, (int)q,
                                               Nf, cs, cc, Lvalid, (int)r0, (int)Dg, C, nct, post,
-                                              twNf, twma, fp);
+                                              twNf, twma, twmal, fp);
     return cudaGetLastError();
 }
 
 template <class V>
 __global__ void __launch_bounds__(kMaxThreads, 2)
 k_ifft_cols(V* y, int64_t B, int64_t Cn, int ma, int q, int64_t Nf, int Dg, int C, int nct, int pre,
-            const V* __restrict__ twNf, const V* __restrict__ twma, FftPlan fp)
+            const V* __restrict__ twNf, const V* __restrict__ twma, const V* __restrict__ twmal, FftPlan fp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     int64_t blk = blockIdx.x;
@@ -183,8 +227,8 @@ k_ifft_cols(V* y, int64_t B, int64_t Cn, int ma, int q, int64_t Nf, int Dg, int 
     blk /= nct;
     const int rr = (int)(blk % Dg);
     const int64_t b = blk / Dg;
-    ifft_cols_body<V>(y + ((int64_t)rr * B + b) * ma * Cn, Cn, ma, q, Nf, (int64_t)ct * C, C, pre, twNf, twma, fp,
-                      reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
+    ifft_cols_body<V>(y + ((int64_t)rr * B + b) * ma * Cn, Cn, ma, q, Nf, (int64_t)ct * C, C, pre, twNf, twma, twmal,
+                      fp, reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
 }
 
 template <typename T>
@@ -198,6 +242,8 @@ cudaError_t launch_ifft_cols(cx<T>* y, int64_t B, int64_t Cn, int64_t ma, int64_
     if (e != cudaSuccess) return e;
     const V* twma = twiddles<T>(ma, &e);
     if (e != cudaSuccess) return e;
+    const V* twmal = twiddles_lf<T>(ma, &e);
+    if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(ma);
     const int C = col_tile(Cn, ma, col_tile_target<T>());
     const int nct = (int)((Cn + C - 1) / C);
@@ -209,7 +255,7 @@ cudaError_t launch_ifft_cols(cx<T>* y, int64_t B, int64_t Cn, int64_t ma, int64_
     LaunchScope ls(K_IFFT_COLS, st, (double)(D * B) * (double)Cn * fft_flops((double)ma),
                    2.0 * D * B * ma * Cn * sizeof(V));
     kern<<<(unsigned)blocks, thr, smem, st>>>(y, B, Cn, (int)ma, (int)q, Nf, (int)D, C, nct, pre, twNf,
-                                              twma, fp);
+                                              twma, twmal, fp);
     return cudaGetLastError();
 }
 
@@ -303,9 +349,15 @@ cudaError_t launch_twiddle_into(cx<T>* tw, int64_t n, cudaStream_t st)
 }
 
 template <typename T>
+cudaError_t launch_twiddle_lf_into(cx<T>* tw, int64_t n, cudaStream_t st)
+{
+    return launch_twiddle_lf<T>(tw, n, st);
+}
+
+template <typename T>
 cudaError_t launch_residue_rows_tw(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_t B, int64_t ld_in,
                                    int64_t L, int64_t m, int64_t p, int64_t q, int64_t r0, int64_t D,
-                                   const cx<T>* twN, const cx<T>* twm, cudaStream_t st)
+                                   const cx<T>* twN, const cx<T>* twm, const cx<T>* twml, cudaStream_t st)
 {
     using V = cx<T>;
     const int64_t Dg = (D < q - r0) ? D : (q - r0);
@@ -313,7 +365,7 @@ cudaError_t launch_residue_rows_tw(const cx<T>* f, const cx<T>* g, cx<T>* h, int
     cudaError_t e = cudaSuccess;
     const FftPlan fp = make_fft_plan(m);
     const int thr = threads_for(m);
-    const size_t smem = (size_t)(3 * m) * sizeof(V);
+    const size_t smem = (size_t)(3 * padded_len(m)) * sizeof(V);
     auto kern = k_residue_rows<V>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     const int64_t blocks = B * Dg;
@@ -322,7 +374,7 @@ cudaError_t launch_residue_rows_tw(const cx<T>* f, const cx<T>* g, cx<T>* h, int
     LaunchScope ls(K_RESIDUE_ROWS, st, (double)(B * Dg) * (3.0 * fft_flops((double)m) + 6.0 * m + fold),
                    (2.0 * B * Lrow + (double)(Dg * B * m)) * sizeof(V));
     kern<<<(unsigned)blocks, thr, smem, st>>>(f, g, h, B, ld_in, L, (int)m, (int)p, (int)q, (int)r0,
-                                              (int)Dg, twN, twm, fp);
+                                              (int)Dg, twN, twm, twml, fp);
     return cudaGetLastError();
 }
 
@@ -348,9 +400,10 @@ cudaError_t launch_unfold_tw(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstr
 
 #define HDC_INST_TW(T)                                                                                    \
     template cudaError_t launch_twiddle_into<T>(cx<T>*, int64_t, cudaStream_t);                          \
+    template cudaError_t launch_twiddle_lf_into<T>(cx<T>*, int64_t, cudaStream_t);                       \
     template cudaError_t launch_residue_rows_tw<T>(const cx<T>*, const cx<T>*, cx<T>*, int64_t, int64_t, \
                                                    int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, \
-                                                   const cx<T>*, const cx<T>*, cudaStream_t);            \
+                                                   const cx<T>*, const cx<T>*, const cx<T>*, cudaStream_t); \
     template cudaError_t launch_unfold_tw<T>(cx<T>*, const cx<T>*, int64_t, int64_t, int64_t, int64_t,   \
                                              int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,       \
                                              int64_t, int64_t, int, int, double, const cx<T>*,           \

@@ -63,21 +63,23 @@ int run(const void* f, const void* g, void* h, int64_t L, int64_t m, int64_t p, 
     const size_t b_twN = align256((size_t)N * sizeof(V));
     const size_t b_twm = align256((size_t)m * sizeof(V));
     const size_t b_ws = align256((size_t)(D * batch * m) * sizeof(V));
-    if (b_twN + b_twm + b_ws > kScratchBytes) return HDC_ERR_UNSUPPORTED_SIZE;
+    if (b_twN + 2 * b_twm + b_ws > kScratchBytes) return HDC_ERR_UNSUPPORTED_SIZE;
     void* base = nullptr;
     int rc = scratch_address(&base);
     if (rc != HDC_OK) return rc;
     V* twN = reinterpret_cast<V*>(base);
     V* twm = reinterpret_cast<V*>((unsigned char*)base + b_twN);
-    V* ws = reinterpret_cast<V*>((unsigned char*)base + b_twN + b_twm);
+    V* twml = reinterpret_cast<V*>((unsigned char*)base + b_twN + b_twm);
+    V* ws = reinterpret_cast<V*>((unsigned char*)base + b_twN + 2 * b_twm);
     // every call rewrites the tables and the workspace it reads, so nothing
     // left from an earlier call is used
     if (launch_twiddle_into<T>(twN, N, st) != cudaSuccess) return HDC_ERR_CUDA;
     if (launch_twiddle_into<T>(twm, m, st) != cudaSuccess) return HDC_ERR_CUDA;
+    if (launch_twiddle_lf_into<T>(twml, m, st) != cudaSuccess) return HDC_ERR_CUDA;
     const double scale = 1.0 / (double)N;
     for (int64_t r0 = 0; r0 < q; r0 += D) {
         const int first = (r0 == 0), last = (r0 + D >= q);
-        if (launch_residue_rows_tw<T>((const V*)f, (const V*)g, ws, batch, L, L, m, p, q, r0, D, twN, twm, st) !=
+        if (launch_residue_rows_tw<T>((const V*)f, (const V*)g, ws, batch, L, L, m, p, q, r0, D, twN, twm, twml, st) !=
             cudaSuccess)
             return HDC_ERR_CUDA;
         if (launch_unfold_tw<T>((V*)h, ws, batch, L, 1, m, p, q, N, 1, 0, L, r0, D, first, last, scale, twN, st) !=
