@@ -17,6 +17,8 @@ formula each one writes out):
 * ``dft(x, sign)``                -- the DFT by its definition
 * ``mlp_loss_grad(params, sizes, X, yq, yd, n_q)`` / ``adam_step`` -- the
   parameter predictor's network in FP64 (O7)
+* ``conv_unequal(f, g, m, lam, M, o, Lw)`` -- unequal lengths with residue
+  matching, Section 3.5 (O8)
 """
 from __future__ import annotations
 
@@ -51,6 +53,7 @@ def lib():
         L.hdco_residue_forward_1d.argtypes = [_dp, _i64, _i64, _i64, _i64, _dp]
         L.hdco_residue_backward_1d.argtypes = [_dp, _i64, _i64, _i64, _i64, _dp]
         L.hdco_conv_hybrid_1d.argtypes = [_dp, _dp, _i64, _i64, _i64, _i64, _dp]
+        L.hdco_conv_unequal_1d.argtypes = [_dp, _i64, _dp, _i64, _i64, _i64, _i64, _i64, _i64, _dp]
         L.hdco_conv_hermitian_2d_direct.argtypes = [_dp, _dp, _i64, _dp]
         L.hdco_conv_hermitian_2d_fft.argtypes = [_dp, _dp, _i64, _dp]
         _ip32 = C.POINTER(C.c_int)
@@ -183,6 +186,22 @@ def conv_hybrid(f, g, m: int, p: int, q: int):
     g = _c128(g)
     h = np.empty_like(f)
     _check(lib().hdco_conv_hybrid_1d(_dptr(f), _dptr(g), f.size, m, p, q, _dptr(h)), "conv_hybrid")
+    return h
+
+
+def conv_unequal(f, g, m: int, lam: int = 1, M: int | None = None, o: int = 0, Lw: int | None = None):
+    """Outputs [o, o + Lw) of the linear convolution of 1-D f and g of any
+    lengths, by Section 3.5's residue matching (O8).  Defaults: M = Lf + Lg -
+    1 - o, Lw = len(g)."""
+    f = _c128(f)
+    g = _c128(g)
+    Lf, Lg = f.size, g.size
+    if M is None:
+        M = Lf + Lg - 1 - o
+    if Lw is None:
+        Lw = Lg
+    h = np.empty(Lw, dtype=np.complex128)
+    _check(lib().hdco_conv_unequal_1d(_dptr(f), Lf, _dptr(g), Lg, m, lam, M, o, Lw, _dptr(h)), "conv_unequal")
     return h
 
 

@@ -18,6 +18,8 @@
  *       and the hybrid convolution built from them (Section 2.2, 3.3, 3.5)
  *   O6  centered Hermitian (2-D) convolution by its definition
  *   O7  the parameter predictor's MLP: loss and gradients in FP64, Adam
+ *   O8  unequal lengths with residue matching (Section 3.5, the final
+ *       algorithm for one dimension), built from O5's Eq. 1 and Eq. 2
  *
  * Sign convention (the paper's Eq. 1 and Eq. 2): zeta_n = exp(2 pi i / n),
  * forward transforms use zeta^{+kj} unscaled, backward use zeta^{-kj}/n.
@@ -586,6 +588,58 @@ HDCO_API int hdco_conv_hybrid_1d(const double* f, const double* g, int64_t L,
     free(F);
     free(G);
     return rc;
+}
+
+/* ------------------------------------------ O8 unequal lengths, 1-D */
+
+/* Convolution of f (length Lf) and g (length Lg) by the final algorithm of
+ * Section 3.5: f is transformed at m points, g at Lam m points,
+ *   pf = ceil(Lf / m), pg = ceil(Lg / (Lam m)), qg = ceil(M / (Lam m)),
+ *   qf = Lam qg,  N = qg Lam m = qf m.
+ * The forward transforms are Eq. 1 for each input with its own (m, p, q)
+ * (O5; entry q l + r holds residue r at bin l).  For each residue rg of g
+ * and each Lam index l in [0, Lam), the matching residue of f is
+ * rf = qg l + rg, and bin lg = Lam lf + l of residue rg of g multiplies bin
+ * lf of residue rf of f (qg lg + rg = qf lf + rf).  The backward transform
+ * is Eq. 2 with g's parameters, kept for outputs [o, o + Lw) of the linear
+ * convolution.  Needs M >= Lf + Lg - 1 - o and o + Lw <= N (no aliasing).
+ * Returns 0, or -1 on invalid parameters, -3 on allocation failure. */
+HDCO_API int hdco_conv_unequal_1d(const double* f, int64_t Lf, const double* g, int64_t Lg,
+                                  int64_t m, int64_t Lam, int64_t M, int64_t o, int64_t Lw,
+                                  double* h)
+{
+    if (Lf < 1 || Lg < 1 || m < 1 || Lam < 1 || o < 0 || Lw < 1) return -1;
+    if (M < Lf + Lg - 1 - o || o + Lw > Lf + Lg - 1) return -1;
+    const int64_t mg = Lam * m;
+    const int64_t pf = (Lf + m - 1) / m, pg = (Lg + mg - 1) / mg;
+    const int64_t qg = (M + mg - 1) / mg, qf = Lam * qg;
+    const int64_t N = qg * mg;
+    if (o + Lw > N) return -1;
+    const int64_t Lout = o + Lw, pout = (Lout + mg - 1) / mg;
+    double* F = (double*)malloc(sizeof(double) * 2 * (size_t)N);
+    double* G = (double*)malloc(sizeof(double) * 2 * (size_t)N);
+    double* H = (double*)malloc(sizeof(double) * 2 * (size_t)N);
+    double* x = (double*)malloc(sizeof(double) * 2 * (size_t)Lout);
+    if (!F || !G || !H || !x) { free(F); free(G); free(H); free(x); return -3; }
+    int rc = hdco_residue_forward_1d(f, Lf, m, pf, qf, F);
+    rc |= hdco_residue_forward_1d(g, Lg, mg, pg, qg, G);
+    if (rc) { free(F); free(G); free(H); free(x); return -1; }
+    for (int64_t rg = 0; rg < qg; ++rg)
+        for (int64_t l = 0; l < Lam; ++l) {
+            const int64_t rf = qg * l + rg;
+            for (int64_t lf = 0; lf < m; ++lf) {
+                const int64_t lg = Lam * lf + l;
+                const double* a = G + 2 * (qg * lg + rg);
+                const double* b = F + 2 * (qf * lf + rf);
+                double* c = H + 2 * (qg * lg + rg);
+                c[0] = a[0] * b[0] - a[1] * b[1];
+                c[1] = a[0] * b[1] + a[1] * b[0];
+            }
+        }
+    rc = hdco_residue_backward_1d(H, Lout, mg, pout, qg, x);
+    if (rc == 0) memcpy(h, x + 2 * o, sizeof(double) * 2 * (size_t)Lw);
+    free(F); free(G); free(H); free(x);
+    return rc ? -1 : 0;
 }
 
 /* ------------------------------------------- O6 centered Hermitian 2-D */
