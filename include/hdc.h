@@ -206,6 +206,50 @@ int hdc_convnd_window(int dims, const void* f, const void* g, void* h,
                       int64_t batch, void* workspace, size_t ws_bytes,
                       void* stream);
 
+/* Unequal lengths with residue matching (Section 3.5, the final algorithms
+ * for one and for N dimensions).  Per axis i, f has Lf[i] elements and g
+ * Lg[i]; f is transformed at m[i] points and g at lam[i] m[i] points
+ * (lam[i] >= 1; lam = 1 shares one transform size).  Derived per axis:
+ * pf = ceil(Lf / m), pg = ceil(Lg / (lam m)), qg = ceil(M / (lam m)),
+ * qf = lam qg, N = qg lam m = qf m.  Residue rg of g pairs DFT bin
+ * lam lf + l of its lam m-point transform with bin lf of residue qg l + rg of
+ * f (l < lam), since qg (lam lf + l) + rg = qf lf + (qg l + rg).  D[i] is the
+ * number of g residues per pass (1..qg; 0 or NULL: all).
+ *
+ * Output: per axis the window [o, o + Lw) of the linear convolution (length
+ * Lf + Lg - 1); o = NULL means 0, Lw = NULL means Lg (Eq. 4's first outputs
+ * for the longer input).  Alias-free when M >= Lf + Lg - 1 - o and
+ * o + Lw <= N (else HDC_ERR_ALIAS); M = NULL (or M[i] <= 0) takes the least
+ * such M.  Either input may be the longer one, but the shorter one should be
+ * f so it gets the smaller transform.
+ *
+ * m and lam m must be 2^a 3^b 5^c 7^d; lam m within hdc_max_fft_size, and for
+ * every axis but the last within hdc_max_outer_fft_size; a split transform
+ * (lam m above 2048 points for complex<double>, 4096 for complex<float>)
+ * needs a factor m1 of lam m divisible by lam with lam m / m1 within the
+ * row limit (else HDC_ERR_UNSUPPORTED_SIZE).
+ *
+ * f: batch x prod(Lf), g: batch x prod(Lg), h: batch x prod(Lw), complex,
+ * row-major, device memory, distinct buffers (h may alias neither input:
+ * HDC_ERR_PARAM).  The workspace (device, caller-owned, at least the size
+ * hdc_workspace_size_unequal reports) is only used during the call.  Runs
+ * asynchronously on `stream`. */
+int hdc_validate_unequal_axis(int64_t Lf, int64_t Lg, int64_t M, int64_t m,
+                              int64_t lam, int64_t D, int dtype, int64_t* pf,
+                              int64_t* pg, int64_t* qg, int64_t* D_out);
+int hdc_workspace_size_unequal(int dims, const int64_t* Lf,
+                               const int64_t* Lg, const int64_t* M,
+                               const int64_t* m, const int64_t* lam,
+                               const int64_t* D, const int64_t* o,
+                               const int64_t* Lw, int dtype, int64_t batch,
+                               size_t* bytes);
+int hdc_convnd_unequal(int dims, const void* f, const void* g, void* h,
+                       const int64_t* Lf, const int64_t* Lg, const int64_t* M,
+                       const int64_t* m, const int64_t* lam, const int64_t* D,
+                       const int64_t* o, const int64_t* Lw, int dtype,
+                       int64_t batch, void* workspace, size_t ws_bytes,
+                       void* stream);
+
 /* The share of residues [r_lo, r_hi) of axis 0 (0 <= r_lo < r_hi <= q[0]):
  * the outer sum of Eq. 2 restricted to that range, scaled by 1/N, so the
  * shares of disjoint ranges add up to the convolution.  Residues are

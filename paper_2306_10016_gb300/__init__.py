@@ -122,6 +122,12 @@ _SIGS += [
                                             C.c_int, _i64, C.POINTER(_sz)]),
     ("hdc_convnd_window", C.c_int, [C.c_int, _vp, _vp, _vp, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p,
                                     C.c_int, _i64, _vp, _sz, _vp]),
+    ("hdc_validate_unequal_axis", C.c_int, [_i64, _i64, _i64, _i64, _i64, _i64, C.c_int, _i64p, _i64p, _i64p,
+                                            _i64p]),
+    ("hdc_workspace_size_unequal", C.c_int, [C.c_int, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p,
+                                             C.c_int, _i64, C.POINTER(_sz)]),
+    ("hdc_convnd_unequal", C.c_int, [C.c_int, _vp, _vp, _vp, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p,
+                                     _i64p, C.c_int, _i64, _vp, _sz, _vp]),
     ("hdc_workspace_size_hermitian", C.c_int, [_i64, _i64p, _i64p, C.c_int, _i64, C.POINTER(_sz)]),
     ("hdc_conv2d_hermitian", C.c_int, [_vp, _vp, _vp, _i64, _i64p, _i64p, C.c_int, _i64, _vp, _sz, _vp]),
     ("hdc_mlp_create", C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, C.c_int]),
@@ -189,6 +195,8 @@ def _check(rc: int, what: str) -> None:
 
 
 def _arr(vals):
+    if vals is None:
+        return None  # NULL: the library's default for that argument
     a = (C.c_int64 * len(vals))(*[int(v) for v in vals])
     return a
 
@@ -340,6 +348,65 @@ def convnd_window(f, g, dims, m, o, Lw, M=None, p=0, q=0, D=0, out=None, workspa
                                        _arr(pv), _arr(qv), _arr(Dv), _arr(ov), _arr(Lwv), dt, batch,
                                        workspace.data_ptr(), workspace.numel() * workspace.element_size(),
                                        st.cuda_stream), "hdc_convnd_window")
+    return h
+
+
+def validate_unequal_axis(Lf, Lg, m, lam=1, M=0, D=0, dtype=HDC_C128):
+    """(pf, pg, qg, D) of one unequal-length axis (hdc_validate_unequal_axis);
+    raises HdcError when the tuple is invalid."""
+    pf, pg, qg, Do = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+    _check(lib().hdc_validate_unequal_axis(int(Lf), int(Lg), int(M or 0), int(m), int(lam), int(D), dtype,
+                                           C.byref(pf), C.byref(pg), C.byref(qg), C.byref(Do)),
+           "validate_unequal_axis")
+    return pf.value, pg.value, qg.value, Do.value
+
+
+def workspace_size_unequal(Lf, Lg, m, lam=1, M=None, D=0, o=None, Lw=None, dtype=HDC_C128, batch=1) -> int:
+    dims = len(Lf)
+    mv, lv, Mv, Dv, ov, Lwv = (_per_axis(v, dims, n) for v, n in ((m, "m"), (lam, "lam"), (M, "M"), (D, "D"),
+                                                                  (o, "o"), (Lw, "Lw")))
+    nb = C.c_size_t()
+    _check(lib().hdc_workspace_size_unequal(dims, _arr(Lf), _arr(Lg), _arr(Mv), _arr(mv), _arr(lv), _arr(Dv),
+                                            _arr(ov), _arr(Lwv), dtype, int(batch), C.byref(nb)),
+           "workspace_size_unequal")
+    return nb.value
+
+
+def convnd_unequal(f, g, dims, m, lam=1, M=None, D=0, o=None, Lw=None, out=None, workspace=None, stream=None):
+    """Convolution of f and g of different lengths over their last `dims`
+    axes (hdc_convnd_unequal): f at m points, g at lam * m points per axis,
+    residues matched; leading axes (equal for f and g) are a batch.  Output
+    per axis: the window [o, o + Lw) of the linear convolution (default: the
+    first Lg outputs)."""
+    torch = _torch()
+    if not (f.is_cuda and g.is_cuda) or f.dtype != g.dtype:
+        raise ValueError("f and g must be CUDA tensors of one dtype")
+    if not (f.is_contiguous() and g.is_contiguous()):
+        raise ValueError("f and g must be contiguous")
+    if f.dim() < dims or g.dim() != f.dim() or f.shape[: f.dim() - dims] != g.shape[: g.dim() - dims]:
+        raise ValueError("f and g need the same leading (batch) axes")
+    dt = dtype_code(f.dtype)
+    Lf = [int(x) for x in f.shape[f.dim() - dims:]]
+    Lg = [int(x) for x in g.shape[g.dim() - dims:]]
+    lead = list(f.shape[: f.dim() - dims])
+    batch = 1
+    for x in lead:
+        batch *= int(x)
+    mv, lv, Mv, Dv, ov, Lwv = (_per_axis(v, dims, n) for v, n in ((m, "m"), (lam, "lam"), (M, "M"), (D, "D"),
+                                                                  (o, "o"), (Lw, "Lw")))
+    shape = Lwv if Lwv is not None else Lg
+    h = out if out is not None else torch.empty(lead + shape, dtype=f.dtype, device=f.device)
+    nb = C.c_size_t()
+    _check(lib().hdc_workspace_size_unequal(dims, _arr(Lf), _arr(Lg), _arr(Mv), _arr(mv), _arr(lv), _arr(Dv),
+                                            _arr(ov), _arr(Lwv), dt, batch, C.byref(nb)), "workspace_size_unequal")
+    if workspace is None or workspace.numel() * workspace.element_size() < nb.value:
+        workspace = torch.empty(max(1, nb.value), dtype=torch.uint8, device=f.device)
+    st = stream if stream is not None else torch.cuda.current_stream(f.device)
+    with torch.cuda.device(f.device):
+        _check(lib().hdc_convnd_unequal(dims, f.data_ptr(), g.data_ptr(), h.data_ptr(), _arr(Lf), _arr(Lg),
+                                        _arr(Mv), _arr(mv), _arr(lv), _arr(Dv), _arr(ov), _arr(Lwv), dt, batch,
+                                        workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                        st.cuda_stream), "hdc_convnd_unequal")
     return h
 
 

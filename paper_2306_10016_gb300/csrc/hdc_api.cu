@@ -84,9 +84,14 @@ template const cx<float>* twiddles<float>(int64_t, cudaError_t*);
 
 // ----------------------------------------------------------- axis plan
 
+// One axis.  The loop runs over the q residues of g, transformed at m
+// points; f is transformed at mf = m / lam points with lam q residues
+// (residue matching, Section 3.5).  Equal lengths: Lf = L, mf = m, pf = p,
+// lam = 1.
 struct Axis {
-    int64_t L, M, m, p, q, D, N;
-    int64_t m1, m2; // m1 < 0: m not supported (no split within the tile limits)
+    int64_t L, M, m, p, q, D, N; // g: length, padded length, FFT size, fold blocks, residues, per pass, N = q m
+    int64_t Lf, mf, pf, lam;     // f: length, FFT size, fold blocks; lam = m / mf
+    int64_t m1, m2;              // m1 < 0: m not supported (no split within the tile limits)
     int dtype;
     int64_t o, Lw, pout; // output window [o, o + Lw) of the linear convolution; pout = ceil((o + Lw) / m)
 };
@@ -101,11 +106,17 @@ static bool good_size(int64_t n)
     return n == 1;
 }
 
-// Some split m = m1 m2 with m2 <= max_row and m1 <= max_col exists?
-template <typename T> static bool splittable(int64_t m)
+// Split m = m1 m2 admissible: m2 <= max_row, m1 <= max_col, and lam | m1
+// (f's transform then splits as (m1 / lam) m2 with the same rows).
+template <typename T> static bool split_ok(int64_t m, int64_t d, int64_t lam)
+{
+    return m % d == 0 && m / d <= max_col_fft<T>() && (m / d) % lam == 0;
+}
+
+template <typename T> static bool splittable(int64_t m, int64_t lam)
 {
     for (int64_t d = max_row_fft<T>(); d >= 2; --d)
-        if (m % d == 0 && m / d <= max_col_fft<T>()) return true;
+        if (split_ok<T>(m, d, lam)) return true;
     return false;
 }
 
@@ -114,7 +125,7 @@ template <typename T> static void split_m(Axis& a)
     a.m1 = 0;
     a.m2 = a.m;
     if (a.m <= max_row_fft<T>()) return;
-    if (!splittable<T>(a.m)) a.m1 = -1; // unsupported
+    if (!splittable<T>(a.m, a.lam)) a.m1 = -1; // unsupported
 }
 
 static int sm_count()
@@ -149,6 +160,7 @@ template <typename T> static void route_for(const Axis& a, int64_t B, int64_t* m
         if (a.m % d) continue;
         const int64_t m1 = a.m / d;
         if (m1 > max_col_fft<T>()) break;
+        if (m1 % a.lam) continue;
         b1 = m1; b2 = d;
         if (Dg * B * m1 >= want) break;
     }
@@ -156,7 +168,7 @@ template <typename T> static void route_for(const Axis& a, int64_t B, int64_t* m
         if (fused_ok) { *m1o = 0; *m2o = a.m; return; }
         // no split down to rows of 32: the largest admissible m2
         for (int64_t d = max_row_fft<T>(); d >= 2; --d)
-            if (a.m % d == 0 && a.m / d <= max_col_fft<T>()) { b1 = a.m / d; b2 = d; break; }
+            if (split_ok<T>(a.m, d, a.lam)) { b1 = a.m / d; b2 = d; break; }
     }
     *m1o = b1; *m2o = b2;
 }
@@ -192,8 +204,41 @@ static int resolve_axis(int64_t L, int64_t M, int64_t m, int64_t p, int64_t q, i
     if (q > max_padded(dtype) / m) return HDC_ERR_UNSUPPORTED_SIZE;
     Axis a;
     a.L = L; a.M = M; a.m = m; a.p = p; a.q = q; a.D = D; a.N = q * m;
+    a.Lf = L; a.mf = m; a.pf = p; a.lam = 1;
     a.dtype = dtype;
     a.o = o; a.Lw = Lw; a.pout = ceil_div(o + Lw, m);
+    if (dtype == HDC_C128) split_m<double>(a); else split_m<float>(a);
+    if (a.m1 < 0) return HDC_ERR_UNSUPPORTED_SIZE;
+    if (out) *out = a;
+    return HDC_OK;
+}
+
+// One axis with unequal lengths (Section 3.5): f of length Lf transformed at
+// mf points, g of length Lg at mg = lam mf points; pf = ceil(Lf / mf),
+// pg = ceil(Lg / mg), qg = ceil(M / mg), qf = lam qg, N = qg mg = qf mf.  The
+// window [o, o + Lw) of the linear convolution (length Lf + Lg - 1) is
+// alias-free when M >= Lf + Lg - 1 - o and o + Lw <= N.
+static int resolve_axis_uneq(int64_t Lf, int64_t Lg, int64_t M, int64_t mf, int64_t lam, int64_t D, int dtype,
+                             Axis* out, int64_t o, int64_t Lw)
+{
+    if (dtype != HDC_C64 && dtype != HDC_C128) return HDC_ERR_DTYPE;
+    if (Lw < 0) Lw = Lg;
+    if (Lf < 1 || Lg < 1 || mf < 1 || lam < 1 || D < 0 || o < 0 || Lw < 1) return HDC_ERR_PARAM;
+    if (M <= 0) M = Lf + Lg - 1 - o;
+    if (o + Lw > Lf + Lg - 1) return HDC_ERR_PARAM;
+    if (M < Lf + Lg - 1 - o) return HDC_ERR_ALIAS;
+    const int64_t mg = mf * lam;
+    if (!good_size(mf) || !good_size(mg) || mg > max_fft(dtype)) return HDC_ERR_UNSUPPORTED_SIZE;
+    const int64_t qg = ceil_div(M, mg);
+    if (qg * lam > max_padded(dtype) / mf) return HDC_ERR_UNSUPPORTED_SIZE;
+    if (o + Lw > qg * mg) return HDC_ERR_ALIAS;
+    if (D == 0) D = qg;
+    if (D > qg) return HDC_ERR_PARAM;
+    Axis a;
+    a.L = Lg; a.M = M; a.m = mg; a.p = ceil_div(Lg, mg); a.q = qg; a.D = D; a.N = qg * mg;
+    a.Lf = Lf; a.mf = mf; a.pf = ceil_div(Lf, mf); a.lam = lam;
+    a.dtype = dtype;
+    a.o = o; a.Lw = Lw; a.pout = ceil_div(o + Lw, mg);
     if (dtype == HDC_C128) split_m<double>(a); else split_m<float>(a);
     if (a.m1 < 0) return HDC_ERR_UNSUPPORTED_SIZE;
     if (out) *out = a;
@@ -215,11 +260,11 @@ static int64_t ws_elems(int dims, const Axis* ax, int64_t B)
         if (m1 == 0) return a.D * B * a.m;
         return 2 * a.D * B * a.m;
     }
-    int64_t Cn = 1, Cw = 1;
-    for (int i = 1; i < dims; ++i) { Cn *= ax[i].L; Cw *= ax[i].Lw; }
+    int64_t Cn = 1, Cf = 1, Cw = 1;
+    for (int i = 1; i < dims; ++i) { Cn *= ax[i].L; Cf *= ax[i].Lf; Cw *= ax[i].Lw; }
     const Axis& a = ax[0];
     const int64_t rows = a.D * B * a.m;
-    return rows * (2 * Cn + Cw) + ws_elems(dims - 1, ax + 1, rows);
+    return rows * (Cf + Cn + Cw) + ws_elems(dims - 1, ax + 1, rows);
 }
 
 static size_t ws_bytes(int dims, const Axis* ax, int64_t B, size_t esz, int ncopy)
@@ -240,14 +285,15 @@ static size_t ws_bytes(int dims, const Axis* ax, int64_t B, size_t esz, int ncop
         if (_e != cudaSuccess) return _e;           \
     } while (0)
 
-// 1-D convolution of B rows (input row stride ld, output row stride ldo)
-// along a contiguous axis; outputs [a.o, a.o + a.Lw) of every row.
-// Residues [r_lo, r_hi) only (all: 0, q): the result is that range's share
-// of the sum over residues, already scaled by 1/N, so the shares of disjoint
-// ranges add up to the convolution.
+// 1-D convolution of B rows (input row strides ld_f, ld_g, output row
+// stride ldo) along a contiguous axis; outputs [a.o, a.o + a.Lw) of every row.
+// Residues [r_lo, r_hi) of g only (all: 0, q): the result is that range's
+// share of the sum over residues, already scaled by 1/N, so the shares of
+// disjoint ranges add up to the convolution.
 template <typename T>
-static cudaError_t run_rows(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t B, int64_t ld, int64_t ldo,
-                            const Axis& a, cx<T>* ws, cudaStream_t st, int64_t r_lo = 0, int64_t r_hi = -1)
+static cudaError_t run_rows(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t B, int64_t ld_f, int64_t ld_g,
+                            int64_t ldo, const Axis& a, cx<T>* ws, cudaStream_t st, int64_t r_lo = 0,
+                            int64_t r_hi = -1)
 {
     const double scale = 1.0 / (double)a.N;
     if (r_hi < 0) r_hi = a.q;
@@ -257,7 +303,15 @@ static cudaError_t run_rows(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t 
         for (int64_t r0 = r_lo; r0 < r_hi; r0 += a.D) {
             const int64_t Dp = (a.D < r_hi - r0) ? a.D : (r_hi - r0);
             const int first = (r0 == r_lo), last = (r0 + Dp >= r_hi);
-            HDC_TRY(launch_residue_rows<T>(f, g, ws, B, ld, a.L, a.m, a.p, a.q, r0, Dp, st));
+            // with one transform size the fold runs over the longer input's
+            // blocks; the inputs commute, so the longer one goes second
+            if (a.lam == 1 && a.Lf <= a.L)
+                HDC_TRY(launch_residue_rows<T>(f, g, ws, B, ld_f, ld_g, a.Lf, a.L, a.m, a.p, a.q, r0, Dp, st));
+            else if (a.lam == 1)
+                HDC_TRY(launch_residue_rows<T>(g, f, ws, B, ld_g, ld_f, a.L, a.Lf, a.m, a.pf, a.q, r0, Dp, st));
+            else
+                HDC_TRY(launch_residue_rows_lam<T>(f, g, ws, B, ld_f, ld_g, a.Lf, a.L, a.mf, a.lam, a.pf, a.p, a.q,
+                                                   r0, Dp, st));
             HDC_TRY(launch_unfold<T>(out, ws, B, ldo, 1, a.m, a.pout, a.q, a.N, 1, 0, a.o, a.o + a.Lw, r0,
                                      Dp, first, last, scale, st));
         }
@@ -265,15 +319,24 @@ static cudaError_t run_rows(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t 
     }
     // m = m1 m2: fold + m1-point FFTs along the strided view [p m1][m2] with the
     // inner twiddle zeta_m^{l1 s2}; m2-point row transforms, product and
-    // inverse; inverse m1-point FFTs; unfold.
+    // inverse; inverse m1-point FFTs; unfold.  With lam > 1, f's transform
+    // splits as (m1 / lam) m2 and its row l1' of residue q l + r lands on row
+    // lam l1' + l, next to the row of g it multiplies.
     cx<T>* yf = ws;
     cx<T>* yg = ws + a.D * B * a.m;
     for (int64_t r0 = r_lo; r0 < r_hi; r0 += a.D) {
         const int64_t Dg = (a.D < r_hi - r0) ? a.D : (r_hi - r0);
         const int first = (r0 == r_lo), last = (r0 + Dg >= r_hi);
-        HDC_TRY(launch_fold_fft_cols<T>(f, g, yf, yg, B, ld, m2, m1, a.p, a.q, a.N, m2, 1, a.L, r0, Dg, 1,
-                                        st));
-        HDC_TRY(launch_residue_rows<T>(yf, yg, yf, Dg * B * m1, m2, m2, m2, 1, 1, 0, 1, st));
+        const ColSide<T> sf{ f, yf, ld_f, a.Lf, (int)a.pf, (int)(a.q * a.lam), (int)a.q, (int)a.lam };
+        const ColSide<T> sg{ g, yg, ld_g, a.L, (int)a.p, (int)a.q, 0, 1 };
+        if (a.lam == 1) {
+            const ColSide<T> both[2] = { sf, sg };
+            HDC_TRY(launch_fold_fft_cols<T>(both, 2, B, m2, m1, a.N, m2, 1, r0, Dg, 1, st));
+        } else {
+            HDC_TRY(launch_fold_fft_cols<T>(&sg, 1, B, m2, m1, a.N, m2, 1, r0, Dg, 1, st));
+            HDC_TRY(launch_fold_fft_cols<T>(&sf, 1, B, m2, m1 / a.lam, a.N, m2, 1, r0, Dg, 1, st));
+        }
+        HDC_TRY(launch_residue_rows<T>(yf, yg, yf, Dg * B * m1, m2, m2, m2, m2, m2, 1, 1, 0, 1, st));
         HDC_TRY(launch_ifft_cols<T>(yf, B, m2, m1, a.q, a.N, Dg, 1, st));
         HDC_TRY(launch_unfold<T>(out, yf, B, ldo, m2, m1, a.pout, a.q, a.N, m2, 1, a.o, a.o + a.Lw, r0,
                                  Dg, first, last, scale, st));
@@ -281,31 +344,39 @@ static cudaError_t run_rows(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t 
     return cudaSuccess;
 }
 
-// N-D: residues of axis 0 (strided, Cn = product of the inner input
-// extents, Cw of the inner output extents), the inner (N-1)-D convolution on
-// every transformed row, inverse and unfold of the window of axis 0.
+// N-D: residues of axis 0 (strided; Cn, Cf = products of the inner extents
+// of g and f, Cw of the inner output extents), the inner (N-1)-D
+// convolution on every transformed row, inverse and unfold of the window of
+// axis 0.  f's rows are placed next to the rows of g they multiply (residue
+// matching along axis 0 when lam > 1).
 template <typename T>
 static cudaError_t run_nd(int dims, const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t B,
                           const Axis* ax, cx<T>* ws, cudaStream_t st, int64_t r_lo = 0, int64_t r_hi = -1)
 {
-    if (dims == 1) return run_rows<T>(f, g, out, B, ax[0].L, ax[0].Lw, ax[0], ws, st, r_lo, r_hi);
+    if (dims == 1) return run_rows<T>(f, g, out, B, ax[0].Lf, ax[0].L, ax[0].Lw, ax[0], ws, st, r_lo, r_hi);
     if (r_hi < 0) r_hi = ax[0].q;
-    int64_t Cn = 1, Cw = 1;
-    for (int i = 1; i < dims; ++i) { Cn *= ax[i].L; Cw *= ax[i].Lw; }
+    int64_t Cn = 1, Cf = 1, Cw = 1;
+    for (int i = 1; i < dims; ++i) { Cn *= ax[i].L; Cf *= ax[i].Lf; Cw *= ax[i].Lw; }
     const Axis& a = ax[0];
     const int64_t rows = a.D * B * a.m;
     cx<T>* wf = ws;
-    cx<T>* wg = wf + rows * Cn;
+    cx<T>* wg = wf + rows * Cf;
     cx<T>* wh = wg + rows * Cn;
     cx<T>* inner = wh + rows * Cw;
-    const int64_t bstride = a.L * Cn;
     const int64_t ostride = a.Lw * Cw;
     const double scale = 1.0 / (double)a.N;
     for (int64_t r0 = r_lo; r0 < r_hi; r0 += a.D) {
         const int64_t Dg = (a.D < r_hi - r0) ? a.D : (r_hi - r0);
         const int first = (r0 == r_lo), last = (r0 + Dg >= r_hi);
-        HDC_TRY(launch_fold_fft_cols<T>(f, g, wf, wg, B, bstride, Cn, a.m, a.p, a.q, a.N, 1, 0,
-                                        a.L * Cn, r0, Dg, 0, st));
+        const ColSide<T> sf{ f, wf, a.Lf * Cf, a.Lf * Cf, (int)a.pf, (int)(a.q * a.lam), (int)a.q, (int)a.lam };
+        const ColSide<T> sg{ g, wg, a.L * Cn, a.L * Cn, (int)a.p, (int)a.q, 0, 1 };
+        if (a.lam == 1 && Cf == Cn) {
+            const ColSide<T> both[2] = { sf, sg };
+            HDC_TRY(launch_fold_fft_cols<T>(both, 2, B, Cn, a.m, a.N, 1, 0, r0, Dg, 0, st));
+        } else {
+            HDC_TRY(launch_fold_fft_cols<T>(&sg, 1, B, Cn, a.m, a.N, 1, 0, r0, Dg, 0, st));
+            HDC_TRY(launch_fold_fft_cols<T>(&sf, 1, B, Cf, a.mf, a.N, 1, 0, r0, Dg, 0, st));
+        }
         HDC_TRY(run_nd<T>(dims - 1, wf, wg, wh, Dg * B * a.m, ax + 1, inner, st));
         HDC_TRY(launch_ifft_cols<T>(wh, B, Cw, a.m, a.q, a.N, Dg, 0, st));
         HDC_TRY(launch_unfold<T>(out, wh, B, ostride, Cw, a.m, a.pout, a.q, a.N, 1, 0, a.o * Cw,
@@ -324,7 +395,7 @@ static int conv_nd(int dims, const void* f, const void* g, void* h, const Axis* 
     bool same_shape = true;
     for (int i = 0; i < dims; ++i) {
         tot *= ax[i].L;
-        same_shape = same_shape && ax[i].o == 0 && ax[i].Lw == ax[i].L;
+        same_shape = same_shape && ax[i].o == 0 && ax[i].Lw == ax[i].L && ax[i].Lf == ax[i].L && ax[i].lam == 1;
     }
     const bool af = (h == f), ag = (h == g);
     if ((af || ag) && (!inplace || !same_shape)) return HDC_ERR_PARAM;
@@ -361,6 +432,21 @@ static int resolve_all(int dims, const int64_t* L, const int64_t* M, const int64
         if (rc != HDC_OK) return rc;
         // an axis with inner axes runs its whole m-point FFT in one column tile
         if (i < dims - 1 && m[i] > (dtype == HDC_C128 ? max_col_fft<double>() : max_col_fft<float>()))
+            return HDC_ERR_UNSUPPORTED_SIZE;
+    }
+    return HDC_OK;
+}
+
+static int resolve_all_uneq(int dims, const int64_t* Lf, const int64_t* Lg, const int64_t* M, const int64_t* m,
+                            const int64_t* lam, const int64_t* D, const int64_t* o, const int64_t* Lw, int dtype,
+                            Axis* ax)
+{
+    if (dims < 1 || dims > HDC_MAX_DIMS || !Lf || !Lg || !m) return HDC_ERR_PARAM;
+    for (int i = 0; i < dims; ++i) {
+        int rc = resolve_axis_uneq(Lf[i], Lg[i], M ? M[i] : 0, m[i], lam ? lam[i] : 1, D ? D[i] : 0, dtype, &ax[i],
+                                   o ? o[i] : 0, Lw ? Lw[i] : -1);
+        if (rc != HDC_OK) return rc;
+        if (i < dims - 1 && ax[i].m > (dtype == HDC_C128 ? max_col_fft<double>() : max_col_fft<float>()))
             return HDC_ERR_UNSUPPORTED_SIZE;
     }
     return HDC_OK;
@@ -656,6 +742,49 @@ HDC_EXPORT int hdc_convnd_residues(int dims, const void* f, const void* g, void*
     if (dtype == HDC_C128)
         return conv_nd<double>(dims, f, g, h, ax, 0, batch, workspace, ws_bytes_given, st, r_lo, r_hi);
     return conv_nd<float>(dims, f, g, h, ax, 0, batch, workspace, ws_bytes_given, st, r_lo, r_hi);
+}
+
+HDC_EXPORT int hdc_validate_unequal_axis(int64_t Lf, int64_t Lg, int64_t M, int64_t m, int64_t lam, int64_t D,
+                                         int dtype, int64_t* pf, int64_t* pg, int64_t* qg, int64_t* D_out)
+{
+    Axis a;
+    int rc = resolve_axis_uneq(Lf, Lg, M, m, lam, D, dtype, &a, 0, -1);
+    if (rc != HDC_OK) return rc;
+    if (pf) *pf = a.pf;
+    if (pg) *pg = a.p;
+    if (qg) *qg = a.q;
+    if (D_out) *D_out = a.D;
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_workspace_size_unequal(int dims, const int64_t* Lf, const int64_t* Lg, const int64_t* M,
+                                          const int64_t* m, const int64_t* lam, const int64_t* D, const int64_t* o,
+                                          const int64_t* Lw, int dtype, int64_t batch, size_t* bytes)
+{
+    if (!bytes || batch < 0) return HDC_ERR_PARAM;
+    Axis ax[HDC_MAX_DIMS];
+    int rc = resolve_all_uneq(dims, Lf, Lg, M, m, lam, D, o, Lw, dtype, ax);
+    if (rc != HDC_OK) return rc;
+    *bytes = ws_bytes(dims, ax, batch, dtype == HDC_C128 ? 16 : 8, 0);
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_convnd_unequal(int dims, const void* f, const void* g, void* h, const int64_t* Lf,
+                                  const int64_t* Lg, const int64_t* M, const int64_t* m, const int64_t* lam,
+                                  const int64_t* D, const int64_t* o, const int64_t* Lw, int dtype, int64_t batch,
+                                  void* workspace, size_t ws_bytes_given, void* stream)
+{
+    Axis ax[HDC_MAX_DIMS];
+    int rc = resolve_all_uneq(dims, Lf, Lg, M, m, lam, D, o, Lw, dtype, ax);
+    if (rc != HDC_OK) return rc;
+    if (batch < 0) return HDC_ERR_PARAM;
+    if (batch == 0) return HDC_OK;
+    if (!f || !g || !h || h == f || h == g) return HDC_ERR_PARAM;
+    const uintptr_t al = dtype == HDC_C128 ? 15 : 7;
+    if (((uintptr_t)f & al) || ((uintptr_t)g & al) || ((uintptr_t)h & al)) return HDC_ERR_PARAM;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == HDC_C128) return conv_nd<double>(dims, f, g, h, ax, 0, batch, workspace, ws_bytes_given, st);
+    return conv_nd<float>(dims, f, g, h, ax, 0, batch, workspace, ws_bytes_given, st);
 }
 
 HDC_EXPORT int hdc_release_caches(void)

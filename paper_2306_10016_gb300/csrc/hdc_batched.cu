@@ -117,17 +117,17 @@ k_batched(const BConv<V>* __restrict__ convs, const BItem* __restrict__ it0, con
                 const V* x = which ? gp_[itm.conv] : fp_[itm.conv];
                 V* yb = cws + (int64_t)which * cv.q * cv.m + (int64_t)r * cv.m;
                 fold_fft_cols_body<V>(x, yb, cv.m2, cv.m1, cv.p, cv.q, cv.N, cv.m2, 1, cv.L, r, (int64_t)ct * cv.C,
-                                      cv.C, 1, cv.twN, cv.twm1, cv.twm1l, cv.fpm1, smem, tid, nthr);
+                                      cv.C, 1, cv.m2, cv.twN, cv.twm1, cv.twm1l, cv.fpm1, smem, tid, nthr);
             } else if (ph == 1) {
                 if (cv.m1 == 0) {
                     const int r = itm.a;
-                    residue_row_body<V>(fp_[itm.conv], gp_[itm.conv], cws + (int64_t)r * cv.m, cv.L, cv.m, cv.p,
+                    residue_row_body<V>(fp_[itm.conv], gp_[itm.conv], cws + (int64_t)r * cv.m, cv.L, cv.L, cv.m, cv.p,
                                         cv.q, r, cv.twN, cv.twm, cv.twml, cv.fpm, smem, tid, nthr);
                 } else {
                     const int64_t row = itm.a;
                     V* yf = cws + row * cv.m2;
                     const V* yg = cws + (int64_t)cv.q * cv.m + row * cv.m2;
-                    residue_row_body<V>(yf, yg, yf, cv.m2, cv.m2, 1, 1, 0, cv.twm, cv.twm, cv.twml, cv.fpm, smem, tid,
+                    residue_row_body<V>(yf, yg, yf, cv.m2, cv.m2, cv.m2, 1, 1, 0, cv.twm, cv.twm, cv.twml, cv.fpm, smem, tid,
                                         nthr);
                 }
             } else if (ph == 2) {

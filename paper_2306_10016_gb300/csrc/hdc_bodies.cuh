@@ -12,11 +12,12 @@ namespace hdc {
 // One residue r of one row: fold (Eq. 1 inner sum, then zeta_N^{r s}) of f
 // and g, m-point forward FFTs, pointwise product (Section 2.4), inverse FFT
 // (Eq. 2 inner sum); the unscaled result goes to hr[0..m).  smem: three
-// padded buffers of m (3 padded_len(m) elements).  With p = q = 1 and
-// L >= m the fold is a plain copy of the rows.
+// padded buffers of m (3 padded_len(m) elements).  g has L valid elements,
+// f has Lf <= L (zero beyond).  With p = q = 1 and Lf = L >= m the fold is a
+// plain copy of the rows.
 template <class V>
-__device__ __forceinline__ void residue_row_body(const V* fr, const V* gr, V* hr, int64_t L, int m, int p, int q,
-                                                 int r, const V* __restrict__ twN, const V* __restrict__ twm,
+__device__ __forceinline__ void residue_row_body(const V* fr, const V* gr, V* hr, int64_t L, int64_t Lf, int m, int p,
+                                                 int q, int r, const V* __restrict__ twN, const V* __restrict__ twm,
                                                  const V* __restrict__ twml, const FftPlan& fp, V* smem, int tid,
                                                  int nthr)
 {
@@ -24,7 +25,7 @@ __device__ __forceinline__ void residue_row_body(const V* fr, const V* gr, V* hr
     V* sa = smem;
     V* sb = sa + plen;
     V* sc = sb + plen;
-    if (p == 1 && q == 1 && L >= m) {
+    if (p == 1 && q == 1 && L >= m && Lf == L) {
         for (int s = tid; s < m; s += nthr) {
             sa[sidx<true>(s)] = fr[s];
             sb[sidx<true>(s)] = gr[s];
@@ -35,7 +36,7 @@ __device__ __forceinline__ void residue_row_body(const V* fr, const V* gr, V* hr
             for (int t = 0; t < p; ++t) {
                 const int64_t j = (int64_t)t * m + s;
                 if (j >= L) break;
-                const V fv = fr[j], gv = gr[j];
+                const V fv = j < Lf ? fr[j] : czero<V>(), gv = gr[j];
                 if (r == 0) {
                     af = cadd(af, fv);
                     ag = cadd(ag, gv);
@@ -64,14 +65,74 @@ __device__ __forceinline__ void residue_row_body(const V* fr, const V* gr, V* hr
     __syncthreads();
 }
 
+// Fold (Eq. 1 inner sum) of one input row x of L valid elements into the
+// padded buffer dst: dst[s] = zeta_N^{r s} sum_{t < p} zeta_q^{r t} x[t m + s],
+// s < m, with N = q m; no barrier.
+template <class V>
+__device__ __forceinline__ void fold_row(const V* x, int64_t L, int m, int p, int q, int r, const V* __restrict__ twN,
+                                         V* dst, int tid, int nthr)
+{
+    for (int s = tid; s < m; s += nthr) {
+        V a = czero<V>();
+        for (int t = 0; t < p; ++t) {
+            const int64_t j = (int64_t)t * m + s;
+            if (j >= L) break;
+            if (r == 0) a = cadd(a, x[j]);
+            else a = cfma(x[j], __ldg(twN + (((int64_t)r * t) % q) * m), a);
+        }
+        if (r != 0) a = cmul(a, __ldg(twN + (int64_t)r * s));
+        dst[sidx<true>(s)] = a;
+    }
+}
+
+// Unequal lengths with residue matching (Section 3.5, final algorithm for
+// one dimension): g is transformed at mg = lam mf points with qg residues,
+// f at mf points with qf = lam qg residues, both over the same N = qg mg.
+// The DFT index qg lg + rg equals qf lf + rf for lg = lam lf + l, rf = qg l +
+// rg, so residue rg of g pairs bin lam lf + l with bin lf of residue
+// qg l + rg of f, l = 0 .. lam-1.  One block: fold g (residue rg), mg-point
+// FFT; for each l: fold f (residue qg l + rg), mf-point FFT, multiply into
+// the bins lam lf + l; inverse mg-point FFT; unscaled result to hr[0..mg).
+// smem: three padded buffers of mg.
+template <class V>
+__device__ __forceinline__ void residue_row_lam_body(const V* fr, const V* gr, V* hr, int64_t Lf, int64_t Lg, int mf,
+                                                     int mg, int lam, int pf, int pg, int qg, int rg,
+                                                     const V* __restrict__ twN, const V* __restrict__ twf,
+                                                     const V* __restrict__ twfl, const FftPlan& fpf,
+                                                     const V* __restrict__ twg, const V* __restrict__ twgl,
+                                                     const FftPlan& fpg, V* smem, int tid, int nthr)
+{
+    const int plen = (int)padded_len(mg);
+    V* sa = smem;
+    V* sb = sa + plen;
+    V* sc = sb + plen;
+    const int qf = qg * lam;
+    fold_row<V>(gr, Lg, mg, pg, qg, rg, twN, sa, tid, nthr);
+    __syncthreads();
+    fft_smem<V, false, true>(sa, sc, fpg, 1, 1, mg, twg, twgl, tid, nthr);
+    for (int l = 0; l < lam; ++l) {
+        fold_row<V>(fr, Lf, mf, pf, qf, qg * l + rg, twN, sb, tid, nthr);
+        __syncthreads();
+        fft_smem<V, false, true>(sb, sc, fpf, 1, 1, mf, twf, twfl, tid, nthr);
+        for (int lf = tid; lf < mf; lf += nthr) {
+            const int k = sidx<true>(lf * lam + l);
+            sa[k] = cmul(sa[k], sb[sidx<true>(lf)]);
+        }
+        __syncthreads();
+    }
+    fft_smem<V, true, true>(sa, sc, fpg, 1, 1, mg, twg, twgl, tid, nthr);
+    for (int s = tid; s < mg; s += nthr) hr[s] = sa[sidx<true>(s)];
+    __syncthreads();
+}
+
 // Fold along a strided axis and FFT of size ma over it, for the columns
 // c0 .. c0+C-1 (< Cn) of one input x (view x[a][c], a = t ma + i, element
-// valid iff a Cn + c < Lvalid); residue r; result to yb[l][c] (row length
-// Cn), times zeta_{Nf/q}^{l c} if post.  smem: 2 ma C.
+// valid iff a Cn + c < Lvalid); residue r; result to yb[l ystride + c],
+// times zeta_{Nf/q}^{l c} if post.  smem: 2 ma C.
 template <class V>
 __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn, int ma, int p, int q, int64_t Nf,
                                                    int64_t cs, int64_t cc, int64_t Lvalid, int r, int64_t c0, int C,
-                                                   int post, const V* __restrict__ twNf,
+                                                   int post, int64_t ystride, const V* __restrict__ twNf,
                                                    const V* __restrict__ twma, const V* __restrict__ twmal,
                                                    const FftPlan& fp, V* smem, int tid, int nthr)
 {
@@ -102,7 +163,7 @@ __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn
         if (c >= Cn) continue;
         V v = buf[e];
         if (post && l != 0 && c != 0) v = cmul(v, __ldg(twNf + (int64_t)l * c * q));
-        yb[(int64_t)l * Cn + c] = v;
+        yb[(int64_t)l * ystride + c] = v;
     }
     __syncthreads();
 }

@@ -62,24 +62,45 @@ template <typename T> const cx<T>* twiddles_lf(int64_t n, cudaError_t* err);
 
 // Fused residue kernel over rows: for every row b < B and residue
 // r = r0 + rr (rr < D, r < q): fold the row of f and g (period m, p blocks,
-// valid elements j < L), m-point FFTs, product, inverse FFT, and write the
-// unscaled result to h + ((rr * B + b) * m).
+// valid elements j < Lf of f at stride ld_f, j < L of g at stride ld_g),
+// m-point FFTs, product, inverse FFT, and write the unscaled result to
+// h + ((rr * B + b) * m).
 template <typename T>
-cudaError_t launch_residue_rows(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_t B,
-                                int64_t ld_in, int64_t L, int64_t m, int64_t p, int64_t q,
-                                int64_t r0, int64_t D, cudaStream_t st);
+cudaError_t launch_residue_rows(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_t B, int64_t ld_f, int64_t ld_g,
+                                int64_t Lf, int64_t L, int64_t m, int64_t p, int64_t q, int64_t r0, int64_t D,
+                                cudaStream_t st);
 
-// Fold along a strided axis + FFT of size ma over that axis, for f (which 0)
-// and g (which 1), column tile of width C.  Array view x[b][a][c] with
-// a < A (axis), c < Cn; element valid iff a * Cn + c < Lvalid.  Output
-// y[which][rr][b][l][c] for rr < D.  Fold twiddle zeta_Nf^{r (i cs + c cc)};
-// if post != 0 the transformed value is multiplied by zeta_{Nf/q}^{l c}
-// (the inner twiddle of a split m = ma * Cn transform).
+// Fused residue kernel with residue matching (unequal lengths): g rows at
+// mg = lam mf points (pg blocks, qg residues, Lg valid), f rows at mf points
+// (pf blocks, lam qg residues, Lf valid); residues rg = r0 + rr of g, each
+// with its lam matching residues of f; unscaled mg-point results to
+// h + ((rr * B + b) * mg).
 template <typename T>
-cudaError_t launch_fold_fft_cols(const cx<T>* f, const cx<T>* g, cx<T>* yf, cx<T>* yg,
-                                 int64_t B, int64_t bstride, int64_t Cn, int64_t ma, int64_t p,
-                                 int64_t q, int64_t Nf, int64_t cs, int64_t cc, int64_t Lvalid,
-                                 int64_t r0, int64_t D, int post, cudaStream_t st);
+cudaError_t launch_residue_rows_lam(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_t B, int64_t ld_f,
+                                    int64_t ld_g, int64_t Lf, int64_t Lg, int64_t mf, int64_t lam, int64_t pf,
+                                    int64_t pg, int64_t qg, int64_t r0, int64_t D, cudaStream_t st);
+
+// One input of the strided fold + column FFT pass.  Array view
+// x[b][a][c] (batch stride bstride) with a < A (axis), c < Cn; element valid
+// iff a * Cn + c < Lvalid; p fold blocks, q residues.  Residue block (l, rr),
+// l < lam, rr < D, is residue r0 + rr + l * rmul; its output row i goes to
+// row i * lam + l of y[rr][b] (rows of Cn, lam * ma rows per (rr, b)).  The
+// equal-length case is lam = 1, rmul = 0.
+template <typename T> struct ColSide {
+    const cx<T>* x;
+    cx<T>* y;
+    int64_t bstride, Lvalid;
+    int p, q, rmul, lam;
+};
+
+// Fold along a strided axis + FFT of size ma over that axis, for nside
+// inputs (one launch; with two, both have lam = 1), column tile of width C.
+// Fold twiddle zeta_Nf^{r (i cs + c cc)}; if post != 0 the transformed
+// value is multiplied by zeta_{Nf/q}^{l c} (the inner twiddle of a split
+// ma * Cn transform).
+template <typename T>
+cudaError_t launch_fold_fft_cols(const ColSide<T>* sides, int nside, int64_t B, int64_t Cn, int64_t ma, int64_t Nf,
+                                 int64_t cs, int64_t cc, int64_t r0, int64_t D, int post, cudaStream_t st);
 
 // In-place inverse FFT of size ma along the strided axis of y[rr][b][l][c],
 // preceded by multiplication with conj(zeta_{Nf/q}^{l c}) if pre != 0.

@@ -109,20 +109,20 @@ static cudaError_t allow_smem(K kernel, size_t bytes)
 
 template <class V>
 __global__ void __launch_bounds__(kMaxThreads, 2)
-k_residue_rows(const V* f, const V* g, V* h, int64_t B, int64_t ld_in, int64_t L, int m, int p,
-               int q, int r0, int Dg, const V* __restrict__ twN, const V* __restrict__ twm,
+k_residue_rows(const V* f, const V* g, V* h, int64_t B, int64_t ld_f, int64_t ld_g, int64_t Lf, int64_t L, int m,
+               int p, int q, int r0, int Dg, const V* __restrict__ twN, const V* __restrict__ twm,
                const V* __restrict__ twml, FftPlan fp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int64_t b = blockIdx.x % B;
     const int rr = (int)(blockIdx.x / B);
-    residue_row_body<V>(f + b * ld_in, g + b * ld_in, h + ((int64_t)rr * B + b) * m, L, m, p, q, r0 + rr, twN, twm,
-                        twml, fp, reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
+    residue_row_body<V>(f + b * ld_f, g + b * ld_g, h + ((int64_t)rr * B + b) * m, L, Lf, m, p, q, r0 + rr, twN,
+                        twm, twml, fp, reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
 }
 
 template <typename T>
-cudaError_t launch_residue_rows(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_t B, int64_t ld_in,
-                                int64_t L, int64_t m, int64_t p, int64_t q, int64_t r0, int64_t D,
+cudaError_t launch_residue_rows(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_t B, int64_t ld_f, int64_t ld_g,
+                                int64_t Lf, int64_t L, int64_t m, int64_t p, int64_t q, int64_t r0, int64_t D,
                                 cudaStream_t st)
 {
     using V = cx<T>;
@@ -144,11 +144,67 @@ cudaError_t launch_residue_rows(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_
     // model: 3 FFTs + product per residue, and the fold of f and g (8 flops
     // per element each) unless the fold is a plain copy (p = q = 1)
     const double Lrow = (double)((L < p * m) ? L : p * m);
-    const double fold = (p == 1 && q == 1) ? 0.0 : 16.0 * Lrow;
+    const double Lfrow = (double)((Lf < p * m) ? Lf : p * m);
+    const double fold = (p == 1 && q == 1 && Lf == L) ? 0.0 : 8.0 * (Lrow + Lfrow);
     LaunchScope ls(K_RESIDUE_ROWS, st, (double)(B * Dg) * (3.0 * fft_flops((double)m) + 6.0 * m + fold),
-                   (2.0 * B * Lrow + (double)(Dg * B * m)) * sizeof(V));
-    kern<<<(unsigned)blocks, thr, smem, st>>>(f, g, h, B, ld_in, L, (int)m, (int)p, (int)q, (int)r0,
+                   (B * (Lrow + Lfrow) + (double)(Dg * B * m)) * sizeof(V));
+    kern<<<(unsigned)blocks, thr, smem, st>>>(f, g, h, B, ld_f, ld_g, Lf, L, (int)m, (int)p, (int)q, (int)r0,
                                               (int)Dg, twN, twm, twml, fp);
+    return cudaGetLastError();
+}
+
+template <class V>
+__global__ void __launch_bounds__(kMaxThreads, 2)
+k_residue_rows_lam(const V* f, const V* g, V* h, int64_t B, int64_t ld_f, int64_t ld_g, int64_t Lf, int64_t Lg,
+                   int mf, int lam, int pf, int pg, int qg, int r0, int Dg, const V* __restrict__ twN,
+                   const V* __restrict__ twf, const V* __restrict__ twfl, FftPlan fpf, const V* __restrict__ twg,
+                   const V* __restrict__ twgl, FftPlan fpg)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int64_t b = blockIdx.x % B;
+    const int rr = (int)(blockIdx.x / B);
+    const int mg = mf * lam;
+    residue_row_lam_body<V>(f + b * ld_f, g + b * ld_g, h + ((int64_t)rr * B + b) * mg, Lf, Lg, mf, mg, lam, pf, pg,
+                            qg, r0 + rr, twN, twf, twfl, fpf, twg, twgl, fpg, reinterpret_cast<V*>(smraw),
+                            threadIdx.x, blockDim.x);
+}
+
+template <typename T>
+cudaError_t launch_residue_rows_lam(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_t B, int64_t ld_f,
+                                    int64_t ld_g, int64_t Lf, int64_t Lg, int64_t mf, int64_t lam, int64_t pf,
+                                    int64_t pg, int64_t qg, int64_t r0, int64_t D, cudaStream_t st)
+{
+    using V = cx<T>;
+    const int64_t Dg = (D < qg - r0) ? D : (qg - r0);
+    if (B <= 0 || Dg <= 0) return cudaSuccess;
+    const int64_t mg = mf * lam;
+    cudaError_t e = cudaSuccess;
+    const V* twN = twiddles<T>(qg * mg, &e);
+    if (e != cudaSuccess) return e;
+    const V* twf = twiddles<T>(mf, &e);
+    if (e != cudaSuccess) return e;
+    const V* twfl = twiddles_lf<T>(mf, &e);
+    if (e != cudaSuccess) return e;
+    const V* twg = twiddles<T>(mg, &e);
+    if (e != cudaSuccess) return e;
+    const V* twgl = twiddles_lf<T>(mg, &e);
+    if (e != cudaSuccess) return e;
+    const FftPlan fpf = make_fft_plan(mf), fpg = make_fft_plan(mg);
+    const int thr = threads_for(mg);
+    const size_t smem = (size_t)(3 * padded_len(mg)) * sizeof(V);
+    auto kern = k_residue_rows_lam<V>;
+    if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
+    const int64_t blocks = B * Dg;
+    // model per (row, residue of g): 2 mg-point FFTs, lam mf-point FFTs,
+    // lam mf products, and the folds (8 flops per valid element per residue)
+    const double Lgr = (double)((Lg < pg * mg) ? Lg : pg * mg);
+    const double Lfr = (double)((Lf < pf * mf) ? Lf : pf * mf);
+    LaunchScope ls(K_RESIDUE_ROWS, st,
+                   (double)(B * Dg) * (2.0 * fft_flops((double)mg) + lam * fft_flops((double)mf) + 6.0 * mg +
+                                       8.0 * (Lgr + lam * Lfr)),
+                   (B * (Lgr + Lfr) + (double)(Dg * B * mg)) * sizeof(V));
+    kern<<<(unsigned)blocks, thr, smem, st>>>(f, g, h, B, ld_f, ld_g, Lf, Lg, (int)mf, (int)lam, (int)pf, (int)pg,
+                                              (int)qg, (int)r0, (int)Dg, twN, twf, twfl, fpf, twg, twgl, fpg);
     return cudaGetLastError();
 }
 
@@ -162,35 +218,46 @@ static int col_tile(int64_t Cn, int64_t ma, int64_t elems_max)
     return (int)C;
 }
 
+template <class V> struct ColSideK {
+    const V* x;
+    V* y;
+    int64_t bstride, Lvalid;
+    int p, q, rmul, lam;
+};
+
 template <class V>
 __global__ void __launch_bounds__(kMaxThreads, 2)
-k_fold_fft_cols(const V* __restrict__ f, const V* __restrict__ g, V* yf, V* yg, int64_t B,
-                int64_t bstride, int64_t Cn, int ma, int p, int q, int64_t Nf, int64_t cs,
-                int64_t cc, int64_t Lvalid, int r0, int Dg, int C, int nct, int post,
-                const V* __restrict__ twNf, const V* __restrict__ twma, const V* __restrict__ twmal, FftPlan fp)
+k_fold_fft_cols(ColSideK<V> s0, ColSideK<V> s1, int nside, int64_t B, int64_t Cn, int ma, int64_t Nf, int64_t cs,
+                int64_t cc, int r0, int Dg, int C, int nct, int post, const V* __restrict__ twNf,
+                const V* __restrict__ twma, const V* __restrict__ twmal, FftPlan fp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     int64_t blk = blockIdx.x;
     const int ct = (int)(blk % nct);
     blk /= nct;
-    const int rr = (int)(blk % Dg);
-    blk /= Dg;
-    const int which = (int)(blk & 1);
-    const int64_t b = blk >> 1;
-    const V* x = (which ? g : f) + b * bstride;
-    V* yb = (which ? yg : yf) + ((int64_t)rr * B + b) * ma * Cn;
-    fold_fft_cols_body<V>(x, yb, Cn, ma, p, q, Nf, cs, cc, Lvalid, r0 + rr, (int64_t)ct * C, C, post, twNf, twma,
-                          twmal, fp, reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
+    const int which = (nside == 2) ? (int)(blk & 1) : 0;
+    if (nside == 2) blk >>= 1;
+    const ColSideK<V>& sd = which ? s1 : s0;
+    const int nres = Dg * sd.lam;
+    const int rt = (int)(blk % nres);
+    const int64_t b = blk / nres;
+    const int l = rt / Dg, rr = rt - l * Dg;
+    const V* x = sd.x + b * sd.bstride;
+    V* yb = sd.y + ((int64_t)rr * B + b) * ((int64_t)ma * sd.lam) * Cn + (int64_t)l * Cn;
+    fold_fft_cols_body<V>(x, yb, Cn, ma, sd.p, sd.q, Nf, cs, cc, sd.Lvalid, r0 + rr + l * sd.rmul, (int64_t)ct * C,
+                          C, post, (int64_t)sd.lam * Cn, twNf, twma, twmal, fp, reinterpret_cast<V*>(smraw),
+                          threadIdx.x, blockDim.x);
 }
 
 template <typename T>
-cudaError_t launch_fold_fft_cols(const cx<T>* f, const cx<T>* g, cx<T>* yf, cx<T>* yg, int64_t B,
-                                 int64_t bstride, int64_t Cn, int64_t ma, int64_t p, int64_t q,
-                                 int64_t Nf, int64_t cs, int64_t cc, int64_t Lvalid, int64_t r0,
-                                 int64_t D, int post, cudaStream_t st)
+cudaError_t launch_fold_fft_cols(const ColSide<T>* sides, int nside, int64_t B, int64_t Cn, int64_t ma, int64_t Nf,
+                                 int64_t cs, int64_t cc, int64_t r0, int64_t D, int post, cudaStream_t st)
 {
     using V = cx<T>;
-    const int64_t Dg = (D < q - r0) ? D : (q - r0);
+    if (nside < 1 || nside > 2) return cudaErrorInvalidValue;
+    if (nside == 2 && (sides[0].lam != 1 || sides[1].lam != 1)) return cudaErrorInvalidValue;
+    const int64_t q0 = sides[nside - 1].q;
+    const int64_t Dg = (D < q0 - r0) ? D : (q0 - r0);
     if (B <= 0 || Dg <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
     const V* twNf = twiddles<T>(Nf, &e);
@@ -206,13 +273,20 @@ cudaError_t launch_fold_fft_cols(const cx<T>* f, const cx<T>* g, cx<T>* yf, cx<T
     const size_t smem = (size_t)(2 * ma * C) * sizeof(V);
     auto kern = k_fold_fft_cols<V>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
-    const int64_t blocks = (int64_t)nct * Dg * 2 * B;
-    LaunchScope ls(K_FOLD_FFT_COLS, st,
-                   2.0 * Dg * B * (8.0 * Lvalid + (double)Cn * fft_flops((double)ma)),
-                   (2.0 * B * Lvalid + 2.0 * Dg * B * ma * Cn) * sizeof(V));
-    kern<<<(unsigned)blocks, thr, smem, st>>>(f, g, yf, yg, B, bstride, Cn, (int)ma, (int)p, (int)q,
-                                              Nf, cs, cc, Lvalid, (int)r0, (int)Dg, C, nct, post,
-                                              twNf, twma, twmal, fp);
+    ColSideK<V> k[2];
+    double flops = 0.0, bytes = 0.0;
+    for (int i = 0; i < 2; ++i) {
+        const ColSide<T>& sd = sides[i < nside ? i : 0];
+        k[i] = ColSideK<V>{ sd.x, sd.y, sd.bstride, sd.Lvalid, sd.p, sd.q, sd.rmul, sd.lam };
+        if (i < nside) {
+            flops += (double)Dg * sd.lam * B * (8.0 * sd.Lvalid + (double)Cn * fft_flops((double)ma));
+            bytes += (B * (double)sd.Lvalid + (double)Dg * sd.lam * B * ma * Cn) * sizeof(V);
+        }
+    }
+    const int64_t blocks = (int64_t)nct * Dg * sides[0].lam * nside * B;
+    LaunchScope ls(K_FOLD_FFT_COLS, st, flops, bytes);
+    kern<<<(unsigned)blocks, thr, smem, st>>>(k[0], k[1], nside, B, Cn, (int)ma, Nf, cs, cc, (int)r0, (int)Dg, C, nct,
+                                              post, twNf, twma, twmal, fp);
     return cudaGetLastError();
 }
 
@@ -373,7 +447,7 @@ cudaError_t launch_residue_rows_tw(const cx<T>* f, const cx<T>* g, cx<T>* h, int
     const double fold = (p == 1 && q == 1) ? 0.0 : 16.0 * Lrow;
     LaunchScope ls(K_RESIDUE_ROWS, st, (double)(B * Dg) * (3.0 * fft_flops((double)m) + 6.0 * m + fold),
                    (2.0 * B * Lrow + (double)(Dg * B * m)) * sizeof(V));
-    kern<<<(unsigned)blocks, thr, smem, st>>>(f, g, h, B, ld_in, L, (int)m, (int)p, (int)q, (int)r0,
+    kern<<<(unsigned)blocks, thr, smem, st>>>(f, g, h, B, ld_in, ld_in, L, L, (int)m, (int)p, (int)q, (int)r0,
                                               (int)Dg, twN, twm, twml, fp);
     return cudaGetLastError();
 }
@@ -417,9 +491,11 @@ HDC_INST_TW(float)
 #define HDC_INST(T)                                                                                       \
     template cudaError_t launch_residue_rows<T>(const cx<T>*, const cx<T>*, cx<T>*, int64_t, int64_t,   \
                                                 int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,   \
-                                                cudaStream_t);                                          \
-    template cudaError_t launch_fold_fft_cols<T>(const cx<T>*, const cx<T>*, cx<T>*, cx<T>*, int64_t,   \
-                                                 int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,  \
+                                                int64_t, int64_t, cudaStream_t);                        \
+    template cudaError_t launch_residue_rows_lam<T>(const cx<T>*, const cx<T>*, cx<T>*, int64_t, int64_t, \
+                                                    int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, \
+                                                    int64_t, int64_t, int64_t, int64_t, cudaStream_t);    \
+    template cudaError_t launch_fold_fft_cols<T>(const ColSide<T>*, int, int64_t, int64_t, int64_t,     \
                                                  int64_t, int64_t, int64_t, int64_t, int64_t, int,      \
                                                  cudaStream_t);                                         \
     template cudaError_t launch_ifft_cols<T>(cx<T>*, int64_t, int64_t, int64_t, int64_t, int64_t,      \
