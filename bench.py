@@ -501,6 +501,52 @@ def main():
                                "outputs": (2 * K - 1) * K, "by_m": herm}
     del fh, gh, hh
 
+    # --- unequal lengths (Section 3.5, FP64): g of 2^22 points with f of
+    # 2^10, 2^16 and 2^20 points, first 2^22 outputs.  Residue matching tuned
+    # over (m, lam, D); beside it the best lam = 1 tuple of the same search
+    # and the equal-length path on f zero-padded to g's length (M = 2 Lg - 1,
+    # tuned), the way a caller without the unequal algorithm would run it.
+    uneq = {}
+    Lg = 1 << 22
+    gu = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 40, (Lg,))).to(dev)
+    hu = torch.empty_like(gu)
+    for lf_log in (10, 16, 20):
+        Lf = 1 << lf_log
+        fu = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 41 + lf_log, (Lf,))).to(dev)
+        t0 = time.perf_counter()
+        bu, tru = hdc.tune_unequal(fu, gu, 1, max_ratio=1.5, reps=2)
+        ttu = time.perf_counter() - t0
+        lam1 = [t[0] for t in tru if t[0]["lam"] == 1]
+        rows = {"matched": bu[0]}
+        if lam1:
+            rows["lam1"] = min(lam1, key=lambda t: t["ms"])
+        res = {}
+        for key, b in rows.items():
+            nbu = hdc.workspace_size_unequal([Lf], [Lg], [b["m"]], [b["lam"]], D=[b["D"]])
+            wsu = torch.empty(max(1, nbu), dtype=torch.uint8, device=dev)
+            msu, flu = graph_time(lambda s_: hdc.convnd_unequal(fu, gu, 1, b["m"], b["lam"], D=b["D"], out=hu,
+                                                                workspace=wsu, stream=s_), args.steps)
+            res[key] = {"ms": round(msu, 4), "m": b["m"], "lam": b["lam"], "q": b["q"], "D": b["D"],
+                        "model_tflops": round(flu / (msu * 1e-3) / 1e12, 4)}
+            del wsu
+        fpad = torch.zeros_like(gu)
+        fpad[:Lf] = fu
+        bp, _ = hdc.tune(fpad, gu, 1, max_ratio=1.3, reps=2)
+        nbp = hdc.workspace_size([Lg], [2 * Lg - 1], [bp[0]["m"]], D=[bp[0]["D"]])
+        wsp = torch.empty(nbp, dtype=torch.uint8, device=dev)
+        msp, flp = graph_time(lambda s_: hdc.convnd(fpad, gu, 1, [bp[0]["m"]], D=[bp[0]["D"]], out=hu,
+                                                    workspace=wsp, stream=s_), args.steps)
+        res["padded_equal"] = {"ms": round(msp, 4), "m": bp[0]["m"], "q": bp[0]["q"], "D": bp[0]["D"],
+                               "model_tflops": round(flp / (msp * 1e-3) / 1e12, 4)}
+        best_ms = res["matched"]["ms"]
+        uneq[f"Lf2^{lf_log}_Lg2^22"] = {
+            "value": world * Lg / (best_ms * 1e-3), "ms": best_ms,
+            "roofline_frac": round(res["matched"]["model_tflops"] / peak64, 4),
+            "speedup_vs_padded": round(res["padded_equal"]["ms"] / best_ms, 4),
+            "tuning_s": round(ttu, 1), "candidates_timed": len(tru), **{k: v for k, v in res.items()}}
+        del fu, fpad, wsp
+    del gu, hu
+
     # --- end to end through the host-buffer C call (FP64)
     pinned = []
     for i, L in enumerate(sizes):
@@ -573,6 +619,7 @@ def main():
                      "hybrid_speedup": round(ms_ex / ms64, 4)},
         "fp32": {"value": world * outs / (ms32 * 1e-3), "ms_per_step": ms32},
         "nd_fp64": nd,
+        "unequal_fp64": uneq,
         "batched_fp64": batched64,
         "batched_fp32": batched32,
         "per_size_fp64": per_size,

@@ -351,6 +351,40 @@ int hdc_tune_conv1d(int64_t L, int64_t M, int dtype, int64_t batch,
                     int64_t m_min, void* stream, hdc_tuple* best,
                     hdc_tuple* trials, int64_t cap, int64_t* ntrials);
 
+/* The same search for unequal lengths (hdc_convnd_unequal, first Lg
+ * outputs per axis).  Candidates of an axis: for every qg, the g transform
+ * sizes mg that pad M least (as above, mg >= m_min), each with lam = 1 and
+ * every lam = 2^a or 3 * 2^a dividing mg whose f size m = mg / lam lies in
+ * [Lf / 2, 2 Lf] (f's cost 5 mg log2 m + 8 lam Lf per g residue is least
+ * near m = Lf); kept when
+ * the model flops
+ *   F_u = qg (10 mg log2 mg + 5 lam m log2 m + 6 mg + 8 (Lg + lam Lf + Lg)) + 2 Lg
+ * are within max_ratio of the axis minimum, sorted by F_u.  M = NULL (or
+ * M[i] <= 0) takes the least alias-free M = Lf + Lg - 1.  hdc_tune_unequal
+ * times them on the caller's buffers (f: batch x prod(Lf), g and h:
+ * batch x prod(Lg)) like hdc_tune_convnd; with a non-NULL tuning_db it
+ * first looks the problem up there and appends what it finds. */
+typedef struct hdc_unequal_tuple {
+    int64_t m, lam, q, D; /* f size m, g size lam m, g residues qg, per pass */
+    double model_flops;   /* F_u of the axis                               */
+    double ms;            /* median device time of the whole call, or -1   */
+} hdc_unequal_tuple;
+int hdc_tune_unequal_candidates(int64_t Lf, int64_t Lg, int64_t M, int dtype,
+                                double max_ratio, int64_t m_min,
+                                hdc_unequal_tuple* out, int64_t cap,
+                                int64_t* n);
+int hdc_tune_unequal_workspace_size(int dims, const int64_t* Lf,
+                                    const int64_t* Lg, const int64_t* M,
+                                    int dtype, int64_t batch, double max_ratio,
+                                    int64_t m_min, size_t* bytes);
+int hdc_tune_unequal(int dims, const int64_t* Lf, const int64_t* Lg,
+                     const int64_t* M, int dtype, int64_t batch, const void* f,
+                     const void* g, void* h, void* workspace, size_t ws_bytes,
+                     int warmup, int reps, double max_ratio, int64_t m_min,
+                     const char* tuning_db, void* stream,
+                     hdc_unequal_tuple* best, hdc_unequal_tuple* trials,
+                     int64_t cap, int64_t* ntrials);
+
 /* ---------------------------------------------------------------- plans
  * A plan fixes (m, p, q, D) per axis for one (dims, L, M, dtype, batch).
  * HDC_TUNE_EXHAUSTIVE looks the problem up in the text database at

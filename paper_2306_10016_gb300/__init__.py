@@ -90,8 +90,24 @@ class Tuple(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class UTuple(C.Structure):
+    """hdc_unequal_tuple: one axis' (m, lam, qg, D) of the unequal-length
+    path, its model flops and measured ms."""
+    _fields_ = [("m", C.c_int64), ("lam", C.c_int64), ("q", C.c_int64), ("D", C.c_int64),
+                ("model_flops", C.c_double), ("ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _tp = C.POINTER(Tuple)
+_utp = C.POINTER(UTuple)
 _SIGS += [
+    ("hdc_tune_unequal_candidates", C.c_int, [_i64, _i64, _i64, C.c_int, C.c_double, _i64, _utp, _i64, _i64p]),
+    ("hdc_tune_unequal_workspace_size", C.c_int, [C.c_int, _i64p, _i64p, _i64p, C.c_int, _i64, C.c_double, _i64,
+                                                  C.POINTER(_sz)]),
+    ("hdc_tune_unequal", C.c_int, [C.c_int, _i64p, _i64p, _i64p, C.c_int, _i64, _vp, _vp, _vp, _vp, _sz, C.c_int,
+                                   C.c_int, C.c_double, _i64, C.c_char_p, _vp, _utp, _utp, _i64, _i64p]),
     ("hdc_workspace_size_host", C.c_int, [C.c_int, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, C.c_int, _i64,
                                           C.POINTER(_sz)]),
     ("hdc_convnd_host", C.c_int, [C.c_int, _vp, _vp, _vp, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, C.c_int,
@@ -569,6 +585,48 @@ def tune(f, g, dims, M=None, max_ratio=2.0, m_min=16, warmup=1, reps=3, out=None
         _check(lib().hdc_tune_convnd(dims, _arr(L), _arr(Mv), dt, batch, f.data_ptr(), g.data_ptr(), h.data_ptr(),
                                      ws.data_ptr(), nb.value, warmup, reps, max_ratio, m_min, st.cuda_stream, best,
                                      trials, cap, C.byref(nt)), "tune_convnd")
+    tr = [[trials[i * dims + a].as_dict() for a in range(dims)] for i in range(min(nt.value, cap))]
+    return [best[a].as_dict() for a in range(dims)], tr
+
+
+def tune_unequal_candidates(Lf: int, Lg: int, M: int = 0, dtype=HDC_C128, max_ratio=1.5, m_min=16):
+    """Candidate (m, lam, qg) of one unequal-length axis, by model flops."""
+    n = C.c_int64()
+    _check(lib().hdc_tune_unequal_candidates(Lf, Lg, M, dtype, max_ratio, m_min, None, 0, C.byref(n)),
+           "tune_unequal_candidates")
+    buf = (UTuple * max(1, n.value))()
+    _check(lib().hdc_tune_unequal_candidates(Lf, Lg, M, dtype, max_ratio, m_min, buf, n.value, C.byref(n)),
+           "tune_unequal_candidates")
+    return [buf[i].as_dict() for i in range(n.value)]
+
+
+def tune_unequal(f, g, dims, M=None, max_ratio=1.5, m_min=16, warmup=1, reps=3, tuning_db=None, stream=None):
+    """Grid search of (m, lam, D) per axis for hdc_convnd_unequal on the given
+    device tensors (first Lg outputs); returns (best per axis, trials).  With
+    tuning_db, a stored result is returned without timing (trials empty)."""
+    torch = _torch()
+    dt = dtype_code(f.dtype)
+    Lf = [int(x) for x in f.shape[f.dim() - dims:]]
+    Lg = [int(x) for x in g.shape[g.dim() - dims:]]
+    batch = 1
+    for x in f.shape[: f.dim() - dims]:
+        batch *= int(x)
+    Mv = _per_axis(M, dims, "M")
+    nb = C.c_size_t()
+    _check(lib().hdc_tune_unequal_workspace_size(dims, _arr(Lf), _arr(Lg), _arr(Mv), dt, batch, max_ratio, m_min,
+                                                 C.byref(nb)), "tune_unequal_workspace_size")
+    ws = torch.empty(max(1, nb.value), dtype=torch.uint8, device=f.device)
+    h = torch.empty(list(g.shape), dtype=g.dtype, device=g.device)
+    cap = 4096
+    best = (UTuple * dims)()
+    trials = (UTuple * (cap * dims))()
+    nt = C.c_int64()
+    st = stream if stream is not None else torch.cuda.current_stream(f.device)
+    db = os.fsencode(tuning_db) if tuning_db else None
+    with torch.cuda.device(f.device):
+        _check(lib().hdc_tune_unequal(dims, _arr(Lf), _arr(Lg), _arr(Mv), dt, batch, f.data_ptr(), g.data_ptr(),
+                                      h.data_ptr(), ws.data_ptr(), nb.value, warmup, reps, max_ratio, m_min, db,
+                                      st.cuda_stream, best, trials, cap, C.byref(nt)), "tune_unequal")
     tr = [[trials[i * dims + a].as_dict() for a in range(dims)] for i in range(min(nt.value, cap))]
     return [best[a].as_dict() for a in range(dims)], tr
 

@@ -210,6 +210,187 @@ double time_config(int dims, const void* f, const void* g, void* h, const int64_
     return res;
 }
 
+// ----------------------------------------------------- unequal lengths
+
+double model_flops_uneq(int64_t Lf, int64_t Lg, int64_t mg, int64_t lam, int64_t qg)
+{
+    const double md = (double)mg, mf = (double)(mg / lam);
+    const double lg = mg > 1 ? std::log2(md) : 0.0, lf = mf > 1 ? std::log2(mf) : 0.0;
+    return (double)qg * (10.0 * md * lg + 5.0 * lam * mf * lf + 6.0 * md +
+                         8.0 * ((double)Lg + (double)lam * Lf + (double)Lg)) +
+           2.0 * (double)Lg;
+}
+
+std::vector<hdc_unequal_tuple> candidates_uneq(int64_t Lf, int64_t Lg, int64_t M, int dtype, double max_ratio,
+                                               int64_t m_min)
+{
+    std::vector<hdc_unequal_tuple> out;
+    if (m_min < 1) m_min = 1;
+    const int64_t top = hdc_next_good_size(M);
+    if (top > 0 && top < m_min) m_min = top;
+    double best = 1e300;
+    std::vector<int64_t> ms;
+    for (int64_t q = 1;; ++q) {
+        const int64_t lo = (M + q - 1) / q;
+        if (lo < m_min && q > 1) break;
+        if (16.0 * (double)q * (double)Lg > max_ratio * best) break;
+        int64_t m = lo;
+        for (int k = 0; k < 3; ++k) {
+            m = hdc_next_good_size(m);
+            if (m < 1) break;
+            ms.push_back(m);
+            best = std::min(best, model_flops_uneq(Lf, Lg, m, 1, (M + m - 1) / m));
+            ++m;
+        }
+        ms.push_back(next_pow2_times(lo, 1));
+        ms.push_back(next_pow2_times(lo, 3));
+    }
+    std::sort(ms.begin(), ms.end());
+    ms.erase(std::unique(ms.begin(), ms.end()), ms.end());
+    for (int64_t mg : ms) {
+        if (mg < m_min) continue;
+        for (int64_t base : { (int64_t)1, (int64_t)3 })
+            for (int64_t lam = base; lam <= mg; lam *= 2) {
+                if (mg % lam) continue;
+                // f's cost 5 mg log2(m) + 8 lam Lf per residue of g is least
+                // near m = mg / lam ~ Lf: keep lam = 1 and m in [Lf/2, 2 Lf]
+                const int64_t mf = mg / lam;
+                if (lam > 1 && (2 * mf < Lf || mf > 2 * Lf)) continue;
+                int64_t pf = 0, pg = 0, qg = 0, D = 0;
+                if (hdc_validate_unequal_axis(Lf, Lg, M, mg / lam, lam, 0, dtype, &pf, &pg, &qg, &D) != HDC_OK)
+                    continue;
+                hdc_unequal_tuple t;
+                t.m = mg / lam; t.lam = lam; t.q = qg; t.D = qg;
+                t.model_flops = model_flops_uneq(Lf, Lg, mg, lam, qg);
+                t.ms = -1.0;
+                out.push_back(t);
+            }
+    }
+    if (out.empty()) return out;
+    best = out[0].model_flops;
+    for (auto& t : out) best = std::min(best, t.model_flops);
+    std::vector<hdc_unequal_tuple> kept;
+    for (auto& t : out)
+        if (t.model_flops <= max_ratio * best) kept.push_back(t);
+    std::sort(kept.begin(), kept.end(), [](const hdc_unequal_tuple& a, const hdc_unequal_tuple& b) {
+        return a.model_flops < b.model_flops;
+    });
+    return kept;
+}
+
+std::string db_key_uneq(int dims, const int64_t* Lf, const int64_t* Lg, const int64_t* M, int dtype, int64_t batch)
+{
+    std::string k = "u1 " + device_key() + " " + std::to_string(dtype) + " " + std::to_string(batch) + " " +
+                    std::to_string(dims);
+    for (int i = 0; i < dims; ++i) k += " " + std::to_string(Lf[i]);
+    for (int i = 0; i < dims; ++i) k += " " + std::to_string(Lg[i]);
+    for (int i = 0; i < dims; ++i) k += " " + std::to_string(M[i]);
+    return k;
+}
+
+// Records "key | m lam q D (per axis) ms"; the last valid matching line wins.
+bool db_lookup_uneq(const char* path, const std::string& key, int dims, hdc_unequal_tuple* best)
+{
+    if (!path || !*path) return false;
+    std::lock_guard<std::mutex> lk(g_db_mu);
+    FILE* fp = fopen(path, "r");
+    if (!fp) return false;
+    char line[4096];
+    bool found = false;
+    while (fgets(line, sizeof line, fp)) {
+        char* bar = strchr(line, '|');
+        if (!bar) continue;
+        std::string k(line, bar - line);
+        while (!k.empty() && k.back() == ' ') k.pop_back();
+        if (k != key) continue;
+        const char* s = bar + 1;
+        hdc_unequal_tuple t[HDC_MAX_DIMS];
+        bool ok = true;
+        int used = 0;
+        for (int i = 0; i < dims && ok; ++i) {
+            long long m, lam, q, D;
+            if (sscanf(s, " %lld %lld %lld %lld%n", &m, &lam, &q, &D, &used) != 4) ok = false;
+            s += used;
+            t[i].m = m; t[i].lam = lam; t[i].q = q; t[i].D = D;
+            t[i].model_flops = 0.0;
+        }
+        double ms = -1.0;
+        if (ok && sscanf(s, " %lf", &ms) != 1) ok = false;
+        if (!ok) continue;
+        for (int i = 0; i < dims; ++i) {
+            t[i].ms = ms;
+            best[i] = t[i];
+        }
+        found = true;
+    }
+    fclose(fp);
+    return found;
+}
+
+void db_store_uneq(const char* path, const std::string& key, int dims, const hdc_unequal_tuple* best)
+{
+    if (!path || !*path) return;
+    std::lock_guard<std::mutex> lk(g_db_mu);
+    FILE* fp = fopen(path, "a");
+    if (!fp) return;
+    fprintf(fp, "%s |", key.c_str());
+    for (int i = 0; i < dims; ++i)
+        fprintf(fp, " %lld %lld %lld %lld", (long long)best[i].m, (long long)best[i].lam, (long long)best[i].q,
+                (long long)best[i].D);
+    fprintf(fp, " %.6f\n", best[0].ms);
+    fclose(fp);
+}
+
+double time_config_uneq(int dims, const void* f, const void* g, void* h, const int64_t* Lf, const int64_t* Lg,
+                        const int64_t* M, const hdc_unequal_tuple* t, int dtype, int64_t batch, void* ws,
+                        size_t ws_bytes, int warmup, int reps, cudaStream_t st)
+{
+    int64_t m[HDC_MAX_DIMS], lam[HDC_MAX_DIMS], D[HDC_MAX_DIMS];
+    for (int i = 0; i < dims; ++i) { m[i] = t[i].m; lam[i] = t[i].lam; D[i] = t[i].D; }
+    size_t need = 0;
+    if (hdc_workspace_size_unequal(dims, Lf, Lg, M, m, lam, D, nullptr, nullptr, dtype, batch, &need) != HDC_OK ||
+        need > ws_bytes)
+        return -1.0;
+    auto call = [&]() {
+        return hdc_convnd_unequal(dims, f, g, h, Lf, Lg, M, m, lam, D, nullptr, nullptr, dtype, batch, ws, ws_bytes,
+                                  st);
+    };
+    for (int w = 0; w < warmup; ++w)
+        if (call() != HDC_OK) return -1.0;
+    std::vector<float> ts;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return -1.0;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return -1.0; }
+    double res = -1.0;
+    for (int r = 0; r < reps; ++r) {
+        cudaEventRecord(e0, st);
+        if (call() != HDC_OK) break;
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ts.push_back(ms);
+    }
+    if ((int)ts.size() == reps && reps > 0) {
+        std::sort(ts.begin(), ts.end());
+        res = ts[ts.size() / 2];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return res;
+}
+
+int resolve_M_uneq(int dims, const int64_t* Lf, const int64_t* Lg, const int64_t* M, int64_t* Mo)
+{
+    if (dims < 1 || dims > HDC_MAX_DIMS || !Lf || !Lg) return HDC_ERR_PARAM;
+    for (int i = 0; i < dims; ++i) {
+        if (Lf[i] < 1 || Lg[i] < 1) return HDC_ERR_PARAM;
+        Mo[i] = (M && M[i] > 0) ? M[i] : Lf[i] + Lg[i] - 1;
+        if (Mo[i] < Lf[i] + Lg[i] - 1) return HDC_ERR_ALIAS;
+    }
+    return HDC_OK;
+}
+
 } // namespace
 
 // ------------------------------------------------------------------ ABI
@@ -329,6 +510,128 @@ HDC_EXPORT int hdc_tune_conv1d(int64_t L, int64_t M, int dtype, int64_t batch, c
 {
     return hdc_tune_convnd(1, &L, &M, dtype, batch, f, g, h, ws, ws_bytes, warmup, reps, max_ratio, m_min, stream,
                            best, trials, cap, ntrials);
+}
+
+HDC_EXPORT int hdc_tune_unequal_candidates(int64_t Lf, int64_t Lg, int64_t M, int dtype, double max_ratio,
+                                           int64_t m_min, hdc_unequal_tuple* out, int64_t cap, int64_t* n)
+{
+    if (!n || max_ratio < 1.0) return HDC_ERR_PARAM;
+    if (dtype != HDC_C64 && dtype != HDC_C128) return HDC_ERR_DTYPE;
+    int64_t Mv = 0;
+    int rc = resolve_M_uneq(1, &Lf, &Lg, &M, &Mv);
+    if (rc != HDC_OK) return rc;
+    auto c = candidates_uneq(Lf, Lg, Mv, dtype, max_ratio, m_min);
+    *n = (int64_t)c.size();
+    for (int64_t i = 0; i < cap && i < (int64_t)c.size(); ++i) out[i] = c[i];
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_tune_unequal_workspace_size(int dims, const int64_t* Lf, const int64_t* Lg, const int64_t* M,
+                                               int dtype, int64_t batch, double max_ratio, int64_t m_min,
+                                               size_t* bytes)
+{
+    if (!bytes) return HDC_ERR_PARAM;
+    int64_t Mv[HDC_MAX_DIMS];
+    int rc = resolve_M_uneq(dims, Lf, Lg, M, Mv);
+    if (rc != HDC_OK) return rc;
+    std::vector<hdc_unequal_tuple> c[HDC_MAX_DIMS];
+    for (int i = 0; i < dims; ++i) {
+        c[i] = candidates_uneq(Lf[i], Lg[i], Mv[i], dtype, max_ratio, m_min);
+        if (c[i].empty()) return HDC_ERR_UNSUPPORTED_SIZE;
+    }
+    size_t worst = 0;
+    int64_t m[HDC_MAX_DIMS], lam[HDC_MAX_DIMS], D[HDC_MAX_DIMS];
+    int64_t idx[HDC_MAX_DIMS] = { 0, 0, 0 };
+    while (true) {
+        for (int i = 0; i < dims; ++i) {
+            const hdc_unequal_tuple& t = c[i][idx[i]];
+            m[i] = t.m; lam[i] = t.lam; D[i] = t.q;
+        }
+        size_t b = 0;
+        if (hdc_workspace_size_unequal(dims, Lf, Lg, Mv, m, lam, D, nullptr, nullptr, dtype, batch, &b) == HDC_OK)
+            worst = std::max(worst, b);
+        int k = dims - 1;
+        while (k >= 0 && ++idx[k] == (int64_t)c[k].size()) idx[k--] = 0;
+        if (k < 0) break;
+    }
+    *bytes = worst;
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_tune_unequal(int dims, const int64_t* Lf, const int64_t* Lg, const int64_t* M, int dtype,
+                                int64_t batch, const void* f, const void* g, void* h, void* ws, size_t ws_bytes,
+                                int warmup, int reps, double max_ratio, int64_t m_min, const char* tuning_db,
+                                void* stream, hdc_unequal_tuple* best, hdc_unequal_tuple* trials, int64_t cap,
+                                int64_t* ntrials)
+{
+    if (!best || !f || !g || !h || reps < 1) return HDC_ERR_PARAM;
+    int64_t Mv[HDC_MAX_DIMS];
+    int rc = resolve_M_uneq(dims, Lf, Lg, M, Mv);
+    if (rc != HDC_OK) return rc;
+    const std::string key = db_key_uneq(dims, Lf, Lg, Mv, dtype, batch);
+    if (db_lookup_uneq(tuning_db, key, dims, best)) {
+        if (ntrials) *ntrials = 0;
+        return HDC_OK;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<hdc_unequal_tuple> c[HDC_MAX_DIMS];
+    hdc_unequal_tuple cur[HDC_MAX_DIMS];
+    for (int i = 0; i < dims; ++i) {
+        c[i] = candidates_uneq(Lf[i], Lg[i], Mv[i], dtype, max_ratio, m_min);
+        if (c[i].empty()) return HDC_ERR_UNSUPPORTED_SIZE;
+        cur[i] = c[i][0];
+    }
+    int64_t nt = 0;
+    auto record = [&](const hdc_unequal_tuple* t, double ms) {
+        if (trials && nt < cap) {
+            for (int i = 0; i < dims; ++i) {
+                trials[nt * dims + i] = t[i];
+                trials[nt * dims + i].ms = ms;
+            }
+        }
+        ++nt;
+    };
+    double best_ms = -1.0;
+    for (int ax = dims - 1; ax >= 0; --ax) {
+        std::vector<std::pair<double, hdc_unequal_tuple>> timed;
+        for (const auto& cand : c[ax]) {
+            hdc_unequal_tuple t[HDC_MAX_DIMS];
+            for (int i = 0; i < dims; ++i) t[i] = cur[i];
+            t[ax] = cand;
+            const double ms =
+                time_config_uneq(dims, f, g, h, Lf, Lg, Mv, t, dtype, batch, ws, ws_bytes, warmup, reps, st);
+            if (ms < 0) continue;
+            record(t, ms);
+            timed.emplace_back(ms, cand);
+        }
+        if (timed.empty()) return HDC_ERR_CUDA;
+        std::sort(timed.begin(), timed.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+        hdc_unequal_tuple bax = timed[0].second;
+        double bms = timed[0].first;
+        for (size_t k = 0; k < timed.size() && k < 3; ++k) {
+            const hdc_unequal_tuple base = timed[k].second;
+            for (int64_t Dv = 1; Dv < base.q; Dv *= 2) {
+                hdc_unequal_tuple t[HDC_MAX_DIMS];
+                for (int i = 0; i < dims; ++i) t[i] = cur[i];
+                t[ax] = base;
+                t[ax].D = Dv;
+                const double ms =
+                    time_config_uneq(dims, f, g, h, Lf, Lg, Mv, t, dtype, batch, ws, ws_bytes, warmup, reps, st);
+                if (ms < 0) continue;
+                record(t, ms);
+                if (ms < bms) { bms = ms; bax = t[ax]; }
+            }
+        }
+        cur[ax] = bax;
+        best_ms = bms;
+    }
+    for (int i = 0; i < dims; ++i) {
+        best[i] = cur[i];
+        best[i].ms = best_ms;
+    }
+    db_store_uneq(tuning_db, key, dims, best);
+    if (ntrials) *ntrials = nt;
+    return HDC_OK;
 }
 
 // ---------------------------------------------------------------- plans

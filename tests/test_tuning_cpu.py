@@ -97,3 +97,33 @@ def test_plan_fixed_and_explicit_on_host(lib):
     # the literal p = 1 of the L=1024, m=512 configuration cannot be planned either
     assert lib.hdc_plan_create(C.byref(h), 1, arr(1024), arr(2046), arr(512), None, hdc.HDC_C128, 1,
                                hdc.HDC_FIXED, None, None) == hdc.HDC_ERR_ALIAS
+
+
+def test_unequal_candidates_valid_and_near_lf():
+    """Every unequal candidate validates; lam > 1 only with f's size m in
+    [Lf/2, 2 Lf]; lam = 1 is always among them; sorted by model flops."""
+    for Lf, Lg in ((1024, 1 << 22), (100, 1000), (7, 20), (1, 50), (5000, 5000)):
+        c = hdc.tune_unequal_candidates(Lf, Lg)
+        assert c
+        assert any(t["lam"] == 1 for t in c)
+        fl = [t["model_flops"] for t in c]
+        assert fl == sorted(fl)
+        for t in c:
+            mg = t["m"] * t["lam"]
+            pf, pg, qg, D = hdc.validate_unequal_axis(Lf, Lg, t["m"], t["lam"])
+            assert qg == t["q"] == -(-(Lf + Lg - 1) // mg)
+            if t["lam"] > 1:
+                assert 2 * t["m"] >= Lf and t["m"] <= 2 * Lf
+
+
+def test_unequal_validation_errors():
+    with pytest.raises(hdc.HDCError) as e:
+        hdc.validate_unequal_axis(7, 20, 4, 2, M=25)
+    assert e.value.code == hdc.HDC_ERR_ALIAS
+    with pytest.raises(hdc.HDCError) as e:
+        hdc.validate_unequal_axis(7, 20, 4, 11)
+    assert e.value.code == hdc.HDC_ERR_UNSUPPORTED_SIZE
+    with pytest.raises(hdc.HDCError) as e:
+        hdc.validate_unequal_axis(0, 20, 4, 1)
+    assert e.value.code == hdc.HDC_ERR_PARAM
+    assert hdc.validate_unequal_axis(7, 20, 4, 2) == (2, 3, 4, 4)

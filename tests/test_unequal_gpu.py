@@ -234,3 +234,21 @@ def test_errors(hdc):
     with pytest.raises(hdc.HDCError) as e:
         hdc.convnd_unequal(f, g, 1, 4, 2, o=5, Lw=22, M=40)
     assert e.value.code == hdc.HDC_ERR_PARAM
+
+
+# --------------------------------------------------------------- tuner
+
+def test_tuner_picks_a_valid_fast_tuple_and_caches(hdc, tmp_path):
+    Lf, Lg = 300, 20000
+    f = dev(synth.unit_disk(95, (Lf,)))
+    g = dev(synth.unit_disk(96, (Lg,)))
+    db = str(tmp_path / "tune.txt")
+    best, trials = hdc.tune_unequal(f, g, 1, reps=2, tuning_db=db)
+    assert trials and all(t[0]["ms"] > 0 for t in trials)
+    b = best[0]
+    assert b["ms"] <= min(t[0]["ms"] for t in trials) + 1e-9
+    h = hdc.convnd_unequal(f, g, 1, b["m"], b["lam"], D=b["D"]).cpu().numpy()
+    ref = full_conv(f.cpu().numpy(), g.cpu().numpy(), 1, "fft")[:Lg]
+    assert rel_max_err(h, ref) < TOL64
+    again, tr2 = hdc.tune_unequal(f, g, 1, reps=2, tuning_db=db)
+    assert tr2 == [] and (again[0]["m"], again[0]["lam"], again[0]["D"]) == (b["m"], b["lam"], b["D"])
