@@ -250,6 +250,27 @@ int hdc_convnd_unequal(int dims, const void* f, const void* g, void* h,
                        int64_t batch, void* workspace, size_t ws_bytes,
                        void* stream);
 
+/* Multi-convolution of n arrays (n = 2..8; the paper's extension of the
+ * method to N arrays, read as the n-fold convolution): the first L outputs
+ * per axis of x_0 * x_1 * ... * x_{n-1}, all inputs of one shape.  Per
+ * residue every input is folded and transformed (Eq. 1), the n transforms
+ * are multiplied, and one inverse transform and unfold follow (Eq. 2).
+ * The n-fold result has length n (L - 1) + 1 per axis, so M >= n (L - 1) + 1
+ * (else HDC_ERR_ALIAS); M = NULL (or M[i] <= 0) takes that least M.  m, p,
+ * q, D as in hdc_convnd.  inputs: n device pointers, each batch x prod(L)
+ * complex; h: batch x prod(L), distinct from every input (else
+ * HDC_ERR_PARAM).  Workspace: hdc_workspace_size_multi. */
+int hdc_workspace_size_multi(int dims, int n, const int64_t* L,
+                             const int64_t* M, const int64_t* m,
+                             const int64_t* p, const int64_t* q,
+                             const int64_t* D, int dtype, int64_t batch,
+                             size_t* bytes);
+int hdc_convnd_multi(int dims, int n, const void* const* inputs, void* h,
+                     const int64_t* L, const int64_t* M, const int64_t* m,
+                     const int64_t* p, const int64_t* q, const int64_t* D,
+                     int dtype, int64_t batch, void* workspace,
+                     size_t ws_bytes, void* stream);
+
 /* The share of residues [r_lo, r_hi) of axis 0 (0 <= r_lo < r_hi <= q[0]):
  * the outer sum of Eq. 2 restricted to that range, scaled by 1/N, so the
  * shares of disjoint ranges add up to the convolution.  Residues are

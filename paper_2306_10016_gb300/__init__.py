@@ -144,6 +144,10 @@ _SIGS += [
                                              C.c_int, _i64, C.POINTER(_sz)]),
     ("hdc_convnd_unequal", C.c_int, [C.c_int, _vp, _vp, _vp, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p,
                                      _i64p, C.c_int, _i64, _vp, _sz, _vp]),
+    ("hdc_workspace_size_multi", C.c_int, [C.c_int, C.c_int, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, C.c_int,
+                                           _i64, C.POINTER(_sz)]),
+    ("hdc_convnd_multi", C.c_int, [C.c_int, C.c_int, C.POINTER(_vp), _vp, _i64p, _i64p, _i64p, _i64p, _i64p,
+                                   _i64p, C.c_int, _i64, _vp, _sz, _vp]),
     ("hdc_workspace_size_hermitian", C.c_int, [_i64, _i64p, _i64p, C.c_int, _i64, C.POINTER(_sz)]),
     ("hdc_conv2d_hermitian", C.c_int, [_vp, _vp, _vp, _i64, _i64p, _i64p, C.c_int, _i64, _vp, _sz, _vp]),
     ("hdc_mlp_create", C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, C.c_int]),
@@ -364,6 +368,48 @@ def convnd_window(f, g, dims, m, o, Lw, M=None, p=0, q=0, D=0, out=None, workspa
                                        _arr(pv), _arr(qv), _arr(Dv), _arr(ov), _arr(Lwv), dt, batch,
                                        workspace.data_ptr(), workspace.numel() * workspace.element_size(),
                                        st.cuda_stream), "hdc_convnd_window")
+    return h
+
+
+def workspace_size_multi(n, L, m, M=None, p=0, q=0, D=0, dtype=HDC_C128, batch=1) -> int:
+    dims = len(L)
+    mv, Mv, pv, qv, Dv = (_per_axis(v, dims, k) for v, k in ((m, "m"), (M, "M"), (p, "p"), (q, "q"), (D, "D")))
+    nb = C.c_size_t()
+    _check(lib().hdc_workspace_size_multi(dims, int(n), _arr(L), _arr(Mv), _arr(mv), _arr(pv), _arr(qv), _arr(Dv),
+                                          dtype, int(batch), C.byref(nb)), "workspace_size_multi")
+    return nb.value
+
+
+def convnd_multi(xs, dims, m, M=None, p=0, q=0, D=0, out=None, workspace=None, stream=None):
+    """First L outputs per axis of the n-fold convolution xs[0] * ... *
+    xs[n-1] over the last `dims` axes (hdc_convnd_multi); xs: a list of
+    2..8 CUDA tensors of one shape and dtype (leading axes are a batch)."""
+    torch = _torch()
+    xs = list(xs)
+    n = len(xs)
+    x0 = xs[0]
+    for x in xs:
+        if not x.is_cuda or x.shape != x0.shape or x.dtype != x0.dtype or not x.is_contiguous():
+            raise ValueError("inputs must be contiguous CUDA tensors of one shape and dtype")
+    dt = dtype_code(x0.dtype)
+    L = [int(v) for v in x0.shape[x0.dim() - dims:]]
+    batch = 1
+    for v in x0.shape[: x0.dim() - dims]:
+        batch *= int(v)
+    mv, Mv, pv, qv, Dv = (_per_axis(v, dims, k) for v, k in ((m, "m"), (M, "M"), (p, "p"), (q, "q"), (D, "D")))
+    h = out if out is not None else torch.empty_like(x0)
+    nb = C.c_size_t()
+    _check(lib().hdc_workspace_size_multi(dims, n, _arr(L), _arr(Mv), _arr(mv), _arr(pv), _arr(qv), _arr(Dv), dt,
+                                          batch, C.byref(nb)), "workspace_size_multi")
+    if workspace is None or workspace.numel() * workspace.element_size() < nb.value:
+        workspace = torch.empty(max(1, nb.value), dtype=torch.uint8, device=x0.device)
+    ptrs = (_vp * n)(*[x.data_ptr() for x in xs])
+    st = stream if stream is not None else torch.cuda.current_stream(x0.device)
+    with torch.cuda.device(x0.device):
+        _check(lib().hdc_convnd_multi(dims, n, ptrs, h.data_ptr(), _arr(L), _arr(Mv), _arr(mv), _arr(pv), _arr(qv),
+                                      _arr(Dv), dt, batch, workspace.data_ptr(),
+                                      workspace.numel() * workspace.element_size(), st.cuda_stream),
+               "hdc_convnd_multi")
     return h
 
 

@@ -250,30 +250,30 @@ static int resolve_axis_uneq(int64_t Lf, int64_t Lg, int64_t M, int64_t mf, int6
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Elements (complex) of workspace for the N-D problem over axes[0..dims),
-// batch B, shapes L[0..dims).
-static int64_t ws_elems(int dims, const Axis* ax, int64_t B)
+// batch B, nin inputs (2: f and g).
+static int64_t ws_elems(int dims, const Axis* ax, int64_t B, int nin = 2)
 {
     if (dims == 1) {
         const Axis& a = ax[0];
         int64_t m1 = 0, m2 = 0;
         route(a, B, a.dtype, &m1, &m2);
         if (m1 == 0) return a.D * B * a.m;
-        return 2 * a.D * B * a.m;
+        return nin * a.D * B * a.m;
     }
     int64_t Cn = 1, Cf = 1, Cw = 1;
     for (int i = 1; i < dims; ++i) { Cn *= ax[i].L; Cf *= ax[i].Lf; Cw *= ax[i].Lw; }
     const Axis& a = ax[0];
     const int64_t rows = a.D * B * a.m;
-    return rows * (Cf + Cn + Cw) + ws_elems(dims - 1, ax + 1, rows);
+    return rows * (Cf + (nin - 1) * Cn + Cw) + ws_elems(dims - 1, ax + 1, rows, nin);
 }
 
-static size_t ws_bytes(int dims, const Axis* ax, int64_t B, size_t esz, int ncopy)
+static size_t ws_bytes(int dims, const Axis* ax, int64_t B, size_t esz, int ncopy, int nin = 2)
 {
     int64_t tot = 1;
     for (int i = 0; i < dims; ++i) tot *= ax[i].L;
     size_t b = 0;
     b += (size_t)ncopy * align_up((size_t)(B * tot) * esz);
-    b += align_up((size_t)ws_elems(dims, ax, B) * esz);
+    b += align_up((size_t)ws_elems(dims, ax, B, nin) * esz);
     return b + 256;
 }
 
@@ -285,18 +285,26 @@ static size_t ws_bytes(int dims, const Axis* ax, int64_t B, size_t esz, int ncop
         if (_e != cudaSuccess) return _e;           \
     } while (0)
 
-// 1-D convolution of B rows (input row strides ld_f, ld_g, output row
-// stride ldo) along a contiguous axis; outputs [a.o, a.o + a.Lw) of every row.
-// Residues [r_lo, r_hi) of g only (all: 0, q): the result is that range's
-// share of the sum over residues, already scaled by 1/N, so the shares of
-// disjoint ranges add up to the convolution.
+// The inputs of one convolution: n = 2 is f (x[0]) and g (x[1]), possibly
+// of unequal lengths; n > 2 is a multi-convolution of equal-length inputs.
+template <typename T> struct Ins {
+    const cx<T>* x[kMaxInputs];
+    int n;
+};
+
+// 1-D convolution of B rows (input row strides ld_f for x[0], ld_g for the
+// others, output row stride ldo) along a contiguous axis; outputs
+// [a.o, a.o + a.Lw) of every row.  Residues [r_lo, r_hi) of g only (all:
+// 0, q): the result is that range's share of the sum over residues, already
+// scaled by 1/N, so the shares of disjoint ranges add up to the convolution.
 template <typename T>
-static cudaError_t run_rows(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t B, int64_t ld_f, int64_t ld_g,
-                            int64_t ldo, const Axis& a, cx<T>* ws, cudaStream_t st, int64_t r_lo = 0,
-                            int64_t r_hi = -1)
+static cudaError_t run_rows(const Ins<T>& in, cx<T>* out, int64_t B, int64_t ld_f, int64_t ld_g, int64_t ldo,
+                            const Axis& a, cx<T>* ws, cudaStream_t st, int64_t r_lo = 0, int64_t r_hi = -1)
 {
     const double scale = 1.0 / (double)a.N;
     if (r_hi < 0) r_hi = a.q;
+    const cx<T>* f = in.x[0];
+    const cx<T>* g = in.x[1];
     int64_t m1 = 0, m2 = 0;
     route(a, B, a.dtype, &m1, &m2);
     if (m1 == 0) {
@@ -305,7 +313,9 @@ static cudaError_t run_rows(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t 
             const int first = (r0 == r_lo), last = (r0 + Dp >= r_hi);
             // with one transform size the fold runs over the longer input's
             // blocks; the inputs commute, so the longer one goes second
-            if (a.lam == 1 && a.Lf <= a.L)
+            if (in.n > 2)
+                HDC_TRY(launch_residue_rows_multi<T>(in.x, in.n, ws, B, ld_g, a.L, a.m, a.p, a.q, r0, Dp, st));
+            else if (a.lam == 1 && a.Lf <= a.L)
                 HDC_TRY(launch_residue_rows<T>(f, g, ws, B, ld_f, ld_g, a.Lf, a.L, a.m, a.p, a.q, r0, Dp, st));
             else if (a.lam == 1)
                 HDC_TRY(launch_residue_rows<T>(g, f, ws, B, ld_g, ld_f, a.L, a.Lf, a.m, a.pf, a.q, r0, Dp, st));
@@ -321,24 +331,32 @@ static cudaError_t run_rows(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t 
     // inner twiddle zeta_m^{l1 s2}; m2-point row transforms, product and
     // inverse; inverse m1-point FFTs; unfold.  With lam > 1, f's transform
     // splits as (m1 / lam) m2 and its row l1' of residue q l + r lands on row
-    // lam l1' + l, next to the row of g it multiplies.
-    cx<T>* yf = ws;
-    cx<T>* yg = ws + a.D * B * a.m;
+    // lam l1' + l, next to the row of g it multiplies.  Input i works in
+    // y[i] = ws + i D B m; the product lands in y[0].
+    cx<T>* y[kMaxInputs];
+    for (int i = 0; i < in.n; ++i) y[i] = ws + (int64_t)i * a.D * B * a.m;
     for (int64_t r0 = r_lo; r0 < r_hi; r0 += a.D) {
         const int64_t Dg = (a.D < r_hi - r0) ? a.D : (r_hi - r0);
         const int first = (r0 == r_lo), last = (r0 + Dg >= r_hi);
-        const ColSide<T> sf{ f, yf, ld_f, a.Lf, (int)a.pf, (int)(a.q * a.lam), (int)a.q, (int)a.lam };
-        const ColSide<T> sg{ g, yg, ld_g, a.L, (int)a.p, (int)a.q, 0, 1 };
-        if (a.lam == 1) {
-            const ColSide<T> both[2] = { sf, sg };
-            HDC_TRY(launch_fold_fft_cols<T>(both, 2, B, m2, m1, a.N, m2, 1, r0, Dg, 1, st));
+        if (in.n > 2) {
+            ColSide<T> sides[kMaxInputs];
+            for (int i = 0; i < in.n; ++i) sides[i] = ColSide<T>{ in.x[i], y[i], ld_g, a.L, (int)a.p, (int)a.q, 0, 1 };
+            HDC_TRY(launch_fold_fft_cols<T>(sides, in.n, B, m2, m1, a.N, m2, 1, r0, Dg, 1, st));
+            HDC_TRY(launch_residue_rows_multi<T>(y, in.n, y[0], Dg * B * m1, m2, m2, m2, 1, 1, 0, 1, st));
         } else {
-            HDC_TRY(launch_fold_fft_cols<T>(&sg, 1, B, m2, m1, a.N, m2, 1, r0, Dg, 1, st));
-            HDC_TRY(launch_fold_fft_cols<T>(&sf, 1, B, m2, m1 / a.lam, a.N, m2, 1, r0, Dg, 1, st));
+            const ColSide<T> sf{ f, y[0], ld_f, a.Lf, (int)a.pf, (int)(a.q * a.lam), (int)a.q, (int)a.lam };
+            const ColSide<T> sg{ g, y[1], ld_g, a.L, (int)a.p, (int)a.q, 0, 1 };
+            if (a.lam == 1) {
+                const ColSide<T> both[2] = { sf, sg };
+                HDC_TRY(launch_fold_fft_cols<T>(both, 2, B, m2, m1, a.N, m2, 1, r0, Dg, 1, st));
+            } else {
+                HDC_TRY(launch_fold_fft_cols<T>(&sg, 1, B, m2, m1, a.N, m2, 1, r0, Dg, 1, st));
+                HDC_TRY(launch_fold_fft_cols<T>(&sf, 1, B, m2, m1 / a.lam, a.N, m2, 1, r0, Dg, 1, st));
+            }
+            HDC_TRY(launch_residue_rows<T>(y[0], y[1], y[0], Dg * B * m1, m2, m2, m2, m2, m2, 1, 1, 0, 1, st));
         }
-        HDC_TRY(launch_residue_rows<T>(yf, yg, yf, Dg * B * m1, m2, m2, m2, m2, m2, 1, 1, 0, 1, st));
-        HDC_TRY(launch_ifft_cols<T>(yf, B, m2, m1, a.q, a.N, Dg, 1, st));
-        HDC_TRY(launch_unfold<T>(out, yf, B, ldo, m2, m1, a.pout, a.q, a.N, m2, 1, a.o, a.o + a.Lw, r0,
+        HDC_TRY(launch_ifft_cols<T>(y[0], B, m2, m1, a.q, a.N, Dg, 1, st));
+        HDC_TRY(launch_unfold<T>(out, y[0], B, ldo, m2, m1, a.pout, a.q, a.N, m2, 1, a.o, a.o + a.Lw, r0,
                                  Dg, first, last, scale, st));
     }
     return cudaSuccess;
@@ -350,34 +368,39 @@ static cudaError_t run_rows(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t 
 // axis 0.  f's rows are placed next to the rows of g they multiply (residue
 // matching along axis 0 when lam > 1).
 template <typename T>
-static cudaError_t run_nd(int dims, const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t B,
-                          const Axis* ax, cx<T>* ws, cudaStream_t st, int64_t r_lo = 0, int64_t r_hi = -1)
+static cudaError_t run_nd(int dims, const Ins<T>& in, cx<T>* out, int64_t B, const Axis* ax, cx<T>* ws,
+                          cudaStream_t st, int64_t r_lo = 0, int64_t r_hi = -1)
 {
-    if (dims == 1) return run_rows<T>(f, g, out, B, ax[0].Lf, ax[0].L, ax[0].Lw, ax[0], ws, st, r_lo, r_hi);
+    if (dims == 1) return run_rows<T>(in, out, B, ax[0].Lf, ax[0].L, ax[0].Lw, ax[0], ws, st, r_lo, r_hi);
     if (r_hi < 0) r_hi = ax[0].q;
     int64_t Cn = 1, Cf = 1, Cw = 1;
     for (int i = 1; i < dims; ++i) { Cn *= ax[i].L; Cf *= ax[i].Lf; Cw *= ax[i].Lw; }
     const Axis& a = ax[0];
     const int64_t rows = a.D * B * a.m;
-    cx<T>* wf = ws;
-    cx<T>* wg = wf + rows * Cf;
-    cx<T>* wh = wg + rows * Cn;
+    Ins<T> w;
+    w.n = in.n;
+    cx<T>* wi[kMaxInputs];
+    wi[0] = ws;
+    for (int i = 1; i < in.n; ++i) wi[i] = ws + rows * Cf + (int64_t)(i - 1) * rows * Cn;
+    for (int i = 0; i < in.n; ++i) w.x[i] = wi[i];
+    cx<T>* wh = ws + rows * Cf + (int64_t)(in.n - 1) * rows * Cn;
     cx<T>* inner = wh + rows * Cw;
     const int64_t ostride = a.Lw * Cw;
     const double scale = 1.0 / (double)a.N;
     for (int64_t r0 = r_lo; r0 < r_hi; r0 += a.D) {
         const int64_t Dg = (a.D < r_hi - r0) ? a.D : (r_hi - r0);
         const int first = (r0 == r_lo), last = (r0 + Dg >= r_hi);
-        const ColSide<T> sf{ f, wf, a.Lf * Cf, a.Lf * Cf, (int)a.pf, (int)(a.q * a.lam), (int)a.q, (int)a.lam };
-        const ColSide<T> sg{ g, wg, a.L * Cn, a.L * Cn, (int)a.p, (int)a.q, 0, 1 };
+        ColSide<T> sides[kMaxInputs];
+        sides[0] = ColSide<T>{ in.x[0], wi[0], a.Lf * Cf, a.Lf * Cf, (int)a.pf, (int)(a.q * a.lam), (int)a.q,
+                               (int)a.lam };
+        for (int i = 1; i < in.n; ++i) sides[i] = ColSide<T>{ in.x[i], wi[i], a.L * Cn, a.L * Cn, (int)a.p, (int)a.q, 0, 1 };
         if (a.lam == 1 && Cf == Cn) {
-            const ColSide<T> both[2] = { sf, sg };
-            HDC_TRY(launch_fold_fft_cols<T>(both, 2, B, Cn, a.m, a.N, 1, 0, r0, Dg, 0, st));
+            HDC_TRY(launch_fold_fft_cols<T>(sides, in.n, B, Cn, a.m, a.N, 1, 0, r0, Dg, 0, st));
         } else {
-            HDC_TRY(launch_fold_fft_cols<T>(&sg, 1, B, Cn, a.m, a.N, 1, 0, r0, Dg, 0, st));
-            HDC_TRY(launch_fold_fft_cols<T>(&sf, 1, B, Cf, a.mf, a.N, 1, 0, r0, Dg, 0, st));
+            HDC_TRY(launch_fold_fft_cols<T>(&sides[1], 1, B, Cn, a.m, a.N, 1, 0, r0, Dg, 0, st));
+            HDC_TRY(launch_fold_fft_cols<T>(&sides[0], 1, B, Cf, a.mf, a.N, 1, 0, r0, Dg, 0, st));
         }
-        HDC_TRY(run_nd<T>(dims - 1, wf, wg, wh, Dg * B * a.m, ax + 1, inner, st));
+        HDC_TRY(run_nd<T>(dims - 1, w, wh, Dg * B * a.m, ax + 1, inner, st));
         HDC_TRY(launch_ifft_cols<T>(wh, B, Cw, a.m, a.q, a.N, Dg, 0, st));
         HDC_TRY(launch_unfold<T>(out, wh, B, ostride, Cw, a.m, a.pout, a.q, a.N, 1, 0, a.o * Cw,
                                  (a.o + a.Lw) * Cw, r0, Dg, first, last, scale, st));
@@ -417,7 +440,28 @@ static int conv_nd(int dims, const void* f, const void* g, void* h, const Axis* 
         gin = (const V*)base;
         base += align_up(arr);
     }
-    cudaError_t e = run_nd<T>(dims, fin, gin, (V*)h, B, ax, (V*)base, st, r_lo, r_hi);
+    Ins<T> in;
+    in.n = 2;
+    in.x[0] = fin;
+    in.x[1] = gin;
+    cudaError_t e = run_nd<T>(dims, in, (V*)h, B, ax, (V*)base, st, r_lo, r_hi);
+    return e == cudaSuccess ? HDC_OK : HDC_ERR_CUDA;
+}
+
+// Multi-convolution of n equal-shape inputs (device pointers, distinct from
+// h); workspace of ws_bytes(..., nin = n).
+template <typename T>
+static int conv_nd_multi(int dims, int n, const void* const* xs, void* h, const Axis* ax, int64_t B, void* ws,
+                         size_t ws_bytes_given, cudaStream_t st)
+{
+    using V = cx<T>;
+    const size_t need = ws_bytes(dims, ax, B, sizeof(V), 0, n);
+    if (ws == nullptr || ws_bytes_given < need) return HDC_ERR_WORKSPACE;
+    uintptr_t base = ((uintptr_t)ws + 255) & ~(uintptr_t)255;
+    Ins<T> in;
+    in.n = n;
+    for (int i = 0; i < n; ++i) in.x[i] = (const V*)xs[i];
+    cudaError_t e = run_nd<T>(dims, in, (V*)h, B, ax, (V*)base, st);
     return e == cudaSuccess ? HDC_OK : HDC_ERR_CUDA;
 }
 
@@ -450,6 +494,21 @@ static int resolve_all_uneq(int dims, const int64_t* Lf, const int64_t* Lg, cons
             return HDC_ERR_UNSUPPORTED_SIZE;
     }
     return HDC_OK;
+}
+
+// Multi-convolution of n equal-length inputs: the first L outputs of the
+// n-fold convolution per axis are alias-free when M >= n (L - 1) + 1.
+static int resolve_all_multi(int dims, int n, const int64_t* L, const int64_t* M, const int64_t* m,
+                             const int64_t* p, const int64_t* q, const int64_t* D, int dtype, Axis* ax)
+{
+    if (n < 2 || n > kMaxInputs || dims < 1 || dims > HDC_MAX_DIMS || !L || !m) return HDC_ERR_PARAM;
+    int64_t Mv[HDC_MAX_DIMS];
+    for (int i = 0; i < dims; ++i) {
+        if (L[i] < 1) return HDC_ERR_PARAM;
+        Mv[i] = (M && M[i] > 0) ? M[i] : n * (L[i] - 1) + 1;
+        if (Mv[i] < n * (L[i] - 1) + 1) return HDC_ERR_ALIAS;
+    }
+    return resolve_all(dims, L, Mv, m, p, q, D, dtype, ax);
 }
 
 } // namespace hdc
@@ -785,6 +844,37 @@ HDC_EXPORT int hdc_convnd_unequal(int dims, const void* f, const void* g, void* 
     cudaStream_t st = (cudaStream_t)stream;
     if (dtype == HDC_C128) return conv_nd<double>(dims, f, g, h, ax, 0, batch, workspace, ws_bytes_given, st);
     return conv_nd<float>(dims, f, g, h, ax, 0, batch, workspace, ws_bytes_given, st);
+}
+
+HDC_EXPORT int hdc_workspace_size_multi(int dims, int n, const int64_t* L, const int64_t* M, const int64_t* m,
+                                        const int64_t* p, const int64_t* q, const int64_t* D, int dtype,
+                                        int64_t batch, size_t* bytes)
+{
+    if (!bytes || batch < 0) return HDC_ERR_PARAM;
+    Axis ax[HDC_MAX_DIMS];
+    int rc = resolve_all_multi(dims, n, L, M, m, p, q, D, dtype, ax);
+    if (rc != HDC_OK) return rc;
+    *bytes = ws_bytes(dims, ax, batch, dtype == HDC_C128 ? 16 : 8, 0, n);
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_convnd_multi(int dims, int n, const void* const* inputs, void* h, const int64_t* L,
+                                const int64_t* M, const int64_t* m, const int64_t* p, const int64_t* q,
+                                const int64_t* D, int dtype, int64_t batch, void* workspace, size_t ws_bytes_given,
+                                void* stream)
+{
+    Axis ax[HDC_MAX_DIMS];
+    int rc = resolve_all_multi(dims, n, L, M, m, p, q, D, dtype, ax);
+    if (rc != HDC_OK) return rc;
+    if (batch < 0 || !inputs || !h) return HDC_ERR_PARAM;
+    if (batch == 0) return HDC_OK;
+    const uintptr_t al = dtype == HDC_C128 ? 15 : 7;
+    if ((uintptr_t)h & al) return HDC_ERR_PARAM;
+    for (int i = 0; i < n; ++i)
+        if (!inputs[i] || inputs[i] == h || ((uintptr_t)inputs[i] & al)) return HDC_ERR_PARAM;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == HDC_C128) return conv_nd_multi<double>(dims, n, inputs, h, ax, batch, workspace, ws_bytes_given, st);
+    return conv_nd_multi<float>(dims, n, inputs, h, ax, batch, workspace, ws_bytes_given, st);
 }
 
 HDC_EXPORT int hdc_release_caches(void)

@@ -85,6 +85,40 @@ __device__ __forceinline__ void fold_row(const V* x, int64_t L, int m, int p, in
     }
 }
 
+// Up to kMaxInputs input arrays of a multi-convolution (kernel argument).
+template <class V> struct InPtrs {
+    const V* x[kMaxInputs];
+};
+
+// Multi-convolution, one residue r of one row (offset boff into every
+// input): fold (Eq. 1 inner sum) and m-point FFT of each of the nin inputs,
+// the product of all nin transforms, inverse FFT; the unscaled result goes
+// to hr[0..m).  smem: three padded buffers of m.
+template <class V>
+__device__ __forceinline__ void residue_row_multi_body(const InPtrs<V>& in, int nin, int64_t boff, V* hr, int64_t L,
+                                                       int m, int p, int q, int r, const V* __restrict__ twN,
+                                                       const V* __restrict__ twm, const V* __restrict__ twml,
+                                                       const FftPlan& fp, V* smem, int tid, int nthr)
+{
+    const int plen = (int)padded_len(m);
+    V* sa = smem;
+    V* sb = sa + plen;
+    V* sc = sb + plen;
+    fold_row<V>(in.x[0] + boff, L, m, p, q, r, twN, sa, tid, nthr);
+    __syncthreads();
+    fft_smem<V, false, true>(sa, sc, fp, 1, 1, m, twm, twml, tid, nthr);
+    for (int i = 1; i < nin; ++i) {
+        fold_row<V>(in.x[i] + boff, L, m, p, q, r, twN, sb, tid, nthr);
+        __syncthreads();
+        fft_smem<V, false, true>(sb, sc, fp, 1, 1, m, twm, twml, tid, nthr);
+        for (int s = tid; s < m; s += nthr) sa[sidx<true>(s)] = cmul(sa[sidx<true>(s)], sb[sidx<true>(s)]);
+        __syncthreads();
+    }
+    fft_smem<V, true, true>(sa, sc, fp, 1, 1, m, twm, twml, tid, nthr);
+    for (int s = tid; s < m; s += nthr) hr[s] = sa[sidx<true>(s)];
+    __syncthreads();
+}
+
 // Unequal lengths with residue matching (Section 3.5, final algorithm for
 // one dimension): g is transformed at mg = lam mf points with qg residues,
 // f at mf points with qf = lam qg residues, both over the same N = qg mg.

@@ -319,6 +319,9 @@ template <class V, bool INV> struct DftLF<V, 8, INV> {
 
 #define HDC_MAX_STAGES 32
 
+// Most inputs of one multi-convolution (the n-fold product per residue).
+constexpr int kMaxInputs = 8;
+
 struct FftPlan {
     int n;                      // transform size
     int nst;                    // number of stages

@@ -80,6 +80,13 @@ cudaError_t launch_residue_rows_lam(const cx<T>* f, const cx<T>* g, cx<T>* h, in
                                     int64_t ld_g, int64_t Lf, int64_t Lg, int64_t mf, int64_t lam, int64_t pf,
                                     int64_t pg, int64_t qg, int64_t r0, int64_t D, cudaStream_t st);
 
+// Multi-convolution rows: like launch_residue_rows for nin (<= kMaxInputs)
+// equal-length inputs xs[i] (row stride ld, L valid): the product of all nin
+// transforms per residue, unscaled results to h + ((rr * B + b) * m).
+template <typename T>
+cudaError_t launch_residue_rows_multi(const cx<T>* const* xs, int nin, cx<T>* h, int64_t B, int64_t ld, int64_t L,
+                                      int64_t m, int64_t p, int64_t q, int64_t r0, int64_t D, cudaStream_t st);
+
 // One input of the strided fold + column FFT pass.  Array view
 // x[b][a][c] (batch stride bstride) with a < A (axis), c < Cn; element valid
 // iff a * Cn + c < Lvalid; p fold blocks, q residues.  Residue block (l, rr),
@@ -93,8 +100,9 @@ template <typename T> struct ColSide {
     int p, q, rmul, lam;
 };
 
-// Fold along a strided axis + FFT of size ma over that axis, for nside
-// inputs (one launch; with two, both have lam = 1), column tile of width C.
+// Fold along a strided axis + FFT of size ma over that axis, for nside <=
+// kMaxInputs inputs (one launch; with more than one, all have lam = 1),
+// column tile of width C.
 // Fold twiddle zeta_Nf^{r (i cs + c cc)}; if post != 0 the transformed
 // value is multiplied by zeta_{Nf/q}^{l c} (the inner twiddle of a split
 // ma * Cn transform).

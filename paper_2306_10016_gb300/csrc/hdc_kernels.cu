@@ -208,6 +208,53 @@ cudaError_t launch_residue_rows_lam(const cx<T>* f, const cx<T>* g, cx<T>* h, in
     return cudaGetLastError();
 }
 
+template <class V>
+__global__ void __launch_bounds__(kMaxThreads, 2)
+k_residue_rows_multi(InPtrs<V> in, int nin, V* h, int64_t B, int64_t ld, int64_t L, int m, int p, int q, int r0,
+                     int Dg, const V* __restrict__ twN, const V* __restrict__ twm, const V* __restrict__ twml,
+                     FftPlan fp)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int64_t b = blockIdx.x % B;
+    const int rr = (int)(blockIdx.x / B);
+    residue_row_multi_body<V>(in, nin, b * ld, h + ((int64_t)rr * B + b) * m, L, m, p, q, r0 + rr, twN, twm, twml,
+                              fp, reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
+}
+
+template <typename T>
+cudaError_t launch_residue_rows_multi(const cx<T>* const* xs, int nin, cx<T>* h, int64_t B, int64_t ld, int64_t L,
+                                      int64_t m, int64_t p, int64_t q, int64_t r0, int64_t D, cudaStream_t st)
+{
+    using V = cx<T>;
+    if (nin < 1 || nin > kMaxInputs) return cudaErrorInvalidValue;
+    const int64_t Dg = (D < q - r0) ? D : (q - r0);
+    if (B <= 0 || Dg <= 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    const V* twN = twiddles<T>(q * m, &e);
+    if (e != cudaSuccess) return e;
+    const V* twm = twiddles<T>(m, &e);
+    if (e != cudaSuccess) return e;
+    const V* twml = twiddles_lf<T>(m, &e);
+    if (e != cudaSuccess) return e;
+    const FftPlan fp = make_fft_plan(m);
+    const int thr = threads_for(m);
+    const size_t smem = (size_t)(3 * padded_len(m)) * sizeof(V);
+    auto kern = k_residue_rows_multi<V>;
+    if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
+    InPtrs<V> in;
+    for (int i = 0; i < kMaxInputs; ++i) in.x[i] = xs[i < nin ? i : 0];
+    const int64_t blocks = B * Dg;
+    // model: nin forward FFTs, one inverse, nin - 1 products, the folds
+    const double Lrow = (double)((L < p * m) ? L : p * m);
+    const double fold = (p == 1 && q == 1) ? 0.0 : 8.0 * nin * Lrow;
+    LaunchScope ls(K_RESIDUE_ROWS, st,
+                   (double)(B * Dg) * ((nin + 1.0) * fft_flops((double)m) + 6.0 * (nin - 1) * m + fold),
+                   (nin * B * Lrow + (double)(Dg * B * m)) * sizeof(V));
+    kern<<<(unsigned)blocks, thr, smem, st>>>(in, nin, h, B, ld, L, (int)m, (int)p, (int)q, (int)r0, (int)Dg, twN,
+                                              twm, twml, fp);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------ strided-axis passes
 
 static int col_tile(int64_t Cn, int64_t ma, int64_t elems_max)
@@ -224,20 +271,23 @@ template <class V> struct ColSideK {
     int64_t bstride, Lvalid;
     int p, q, rmul, lam;
 };
+template <class V> struct ColSidesK {
+    ColSideK<V> s[kMaxInputs];
+};
 
 template <class V>
 __global__ void __launch_bounds__(kMaxThreads, 2)
-k_fold_fft_cols(ColSideK<V> s0, ColSideK<V> s1, int nside, int64_t B, int64_t Cn, int ma, int64_t Nf, int64_t cs,
-                int64_t cc, int r0, int Dg, int C, int nct, int post, const V* __restrict__ twNf,
-                const V* __restrict__ twma, const V* __restrict__ twmal, FftPlan fp)
+k_fold_fft_cols(ColSidesK<V> sides, int nside, int64_t B, int64_t Cn, int ma, int64_t Nf, int64_t cs, int64_t cc,
+                int r0, int Dg, int C, int nct, int post, const V* __restrict__ twNf, const V* __restrict__ twma,
+                const V* __restrict__ twmal, FftPlan fp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     int64_t blk = blockIdx.x;
     const int ct = (int)(blk % nct);
     blk /= nct;
-    const int which = (nside == 2) ? (int)(blk & 1) : 0;
-    if (nside == 2) blk >>= 1;
-    const ColSideK<V>& sd = which ? s1 : s0;
+    const int which = (int)(blk % nside);
+    blk /= nside;
+    const ColSideK<V>& sd = sides.s[which];
     const int nres = Dg * sd.lam;
     const int rt = (int)(blk % nres);
     const int64_t b = blk / nres;
@@ -254,8 +304,9 @@ cudaError_t launch_fold_fft_cols(const ColSide<T>* sides, int nside, int64_t B, 
                                  int64_t cs, int64_t cc, int64_t r0, int64_t D, int post, cudaStream_t st)
 {
     using V = cx<T>;
-    if (nside < 1 || nside > 2) return cudaErrorInvalidValue;
-    if (nside == 2 && (sides[0].lam != 1 || sides[1].lam != 1)) return cudaErrorInvalidValue;
+    if (nside < 1 || nside > kMaxInputs) return cudaErrorInvalidValue;
+    for (int i = 0; i < nside && nside > 1; ++i)
+        if (sides[i].lam != 1) return cudaErrorInvalidValue;
     const int64_t q0 = sides[nside - 1].q;
     const int64_t Dg = (D < q0 - r0) ? D : (q0 - r0);
     if (B <= 0 || Dg <= 0) return cudaSuccess;
@@ -273,11 +324,11 @@ cudaError_t launch_fold_fft_cols(const ColSide<T>* sides, int nside, int64_t B, 
     const size_t smem = (size_t)(2 * ma * C) * sizeof(V);
     auto kern = k_fold_fft_cols<V>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
-    ColSideK<V> k[2];
+    ColSidesK<V> k;
     double flops = 0.0, bytes = 0.0;
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kMaxInputs; ++i) {
         const ColSide<T>& sd = sides[i < nside ? i : 0];
-        k[i] = ColSideK<V>{ sd.x, sd.y, sd.bstride, sd.Lvalid, sd.p, sd.q, sd.rmul, sd.lam };
+        k.s[i] = ColSideK<V>{ sd.x, sd.y, sd.bstride, sd.Lvalid, sd.p, sd.q, sd.rmul, sd.lam };
         if (i < nside) {
             flops += (double)Dg * sd.lam * B * (8.0 * sd.Lvalid + (double)Cn * fft_flops((double)ma));
             bytes += (B * (double)sd.Lvalid + (double)Dg * sd.lam * B * ma * Cn) * sizeof(V);
@@ -285,8 +336,8 @@ cudaError_t launch_fold_fft_cols(const ColSide<T>* sides, int nside, int64_t B, 
     }
     const int64_t blocks = (int64_t)nct * Dg * sides[0].lam * nside * B;
     LaunchScope ls(K_FOLD_FFT_COLS, st, flops, bytes);
-    kern<<<(unsigned)blocks, thr, smem, st>>>(k[0], k[1], nside, B, Cn, (int)ma, Nf, cs, cc, (int)r0, (int)Dg, C, nct,
-                                              post, twNf, twma, twmal, fp);
+    kern<<<(unsigned)blocks, thr, smem, st>>>(k, nside, B, Cn, (int)ma, Nf, cs, cc, (int)r0, (int)Dg, C, nct, post,
+                                              twNf, twma, twmal, fp);
     return cudaGetLastError();
 }
 
@@ -495,6 +546,9 @@ HDC_INST_TW(float)
     template cudaError_t launch_residue_rows_lam<T>(const cx<T>*, const cx<T>*, cx<T>*, int64_t, int64_t, \
                                                     int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, \
                                                     int64_t, int64_t, int64_t, int64_t, cudaStream_t);    \
+    template cudaError_t launch_residue_rows_multi<T>(const cx<T>* const*, int, cx<T>*, int64_t, int64_t, \
+                                                      int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, \
+                                                      cudaStream_t);                                        \
     template cudaError_t launch_fold_fft_cols<T>(const ColSide<T>*, int, int64_t, int64_t, int64_t,     \
                                                  int64_t, int64_t, int64_t, int64_t, int64_t, int,      \
                                                  cudaStream_t);                                         \
