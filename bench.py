@@ -547,6 +547,53 @@ def main():
         del fu, fpad, wsp
     del gu, hu
 
+    # --- multi-convolution (FP64), inputs of 2^20 points: the n-fold
+    # convolution of n = 3 and 4 inputs in one residue pass (tuned) against
+    # chaining n - 1 tuned two-input convolutions of the running result; the
+    # sum of n/2 pairwise convolutions (n = 4, 8) in one pass against n/2
+    # tuned two-input convolutions summed by torch
+    multi = {}
+    Lm = 1 << 20
+    for op, nin in (("product", 3), ("product", 4), ("dot", 4), ("dot", 8)):
+        xs = [torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 50 + i, (Lm,))).to(dev) for i in range(nin)]
+        hm = torch.empty_like(xs[0])
+        t0 = time.perf_counter()
+        bm_, _ = hdc.tune_multi(xs, 1, op=op, max_ratio=1.3, reps=2)
+        ttm = time.perf_counter() - t0
+        nbm = hdc.workspace_size_multi(nin, [Lm], [bm_[0]["m"]], op=op, D=[bm_[0]["D"]])
+        wsm = torch.empty(nbm, dtype=torch.uint8, device=dev)
+        msm, flm = graph_time(lambda s_: hdc.convnd_multi(xs, 1, [bm_[0]["m"]], op=op, D=[bm_[0]["D"]], out=hm,
+                                                          workspace=wsm, stream=s_), args.steps)
+        bp2, _ = hdc.tune(xs[0], xs[1], 1, max_ratio=1.3, reps=2)
+        nb2 = hdc.workspace_size([Lm], [2 * Lm - 1], [bp2[0]["m"]], D=[bp2[0]["D"]])
+        ws2 = torch.empty(nb2, dtype=torch.uint8, device=dev)
+        tmp = [torch.empty_like(xs[0]), torch.empty_like(xs[0])]
+
+        def chain(s_):
+            cur = xs[0]
+            for i in range(1, nin):
+                nxt = tmp[i % 2]
+                hdc.convnd(cur, xs[i], 1, [bp2[0]["m"]], D=[bp2[0]["D"]], out=nxt, workspace=ws2, stream=s_)
+                cur = nxt
+
+        def separate(s_):
+            hdc.convnd(xs[0], xs[1], 1, [bp2[0]["m"]], D=[bp2[0]["D"]], out=tmp[0], workspace=ws2, stream=s_)
+            for i in range(2, nin, 2):
+                hdc.convnd(xs[i], xs[i + 1], 1, [bp2[0]["m"]], D=[bp2[0]["D"]], out=tmp[1], workspace=ws2,
+                           stream=s_)
+                with torch.cuda.stream(s_):
+                    tmp[0].add_(tmp[1])
+
+        msc, flc = graph_time(chain if op == "product" else separate, args.steps)
+        base = "chained_pairwise" if op == "product" else "separate_pairs_summed"
+        multi[f"{op}_n{nin}_L2^20"] = {
+            "value": world * Lm / (msm * 1e-3), "ms": round(msm, 4), "m": bm_[0]["m"], "q": bm_[0]["q"],
+            "D": bm_[0]["D"], "model_tflops": round(flm / (msm * 1e-3) / 1e12, 4),
+            "roofline_frac": round(flm / (msm * 1e-3) / 1e12 / peak64, 4), "tuning_s": round(ttm, 1),
+            base: {"ms": round(msc, 4), "m": bp2[0]["m"], "q": bp2[0]["q"], "D": bp2[0]["D"]},
+            "speedup": round(msc / msm, 4)}
+        del xs, hm, wsm, ws2, tmp
+
     # --- end to end through the host-buffer C call (FP64)
     pinned = []
     for i, L in enumerate(sizes):
@@ -620,6 +667,7 @@ def main():
         "fp32": {"value": world * outs / (ms32 * 1e-3), "ms_per_step": ms32},
         "nd_fp64": nd,
         "unequal_fp64": uneq,
+        "multi_fp64": multi,
         "batched_fp64": batched64,
         "batched_fp32": batched32,
         "per_size_fp64": per_size,

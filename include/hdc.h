@@ -250,22 +250,27 @@ int hdc_convnd_unequal(int dims, const void* f, const void* g, void* h,
                        int64_t batch, void* workspace, size_t ws_bytes,
                        void* stream);
 
-/* Multi-convolution of n arrays (n = 2..8; the paper's extension of the
- * method to N arrays, read as the n-fold convolution): the first L outputs
- * per axis of x_0 * x_1 * ... * x_{n-1}, all inputs of one shape.  Per
- * residue every input is folded and transformed (Eq. 1), the n transforms
- * are multiplied, and one inverse transform and unfold follow (Eq. 2).
- * The n-fold result has length n (L - 1) + 1 per axis, so M >= n (L - 1) + 1
- * (else HDC_ERR_ALIAS); M = NULL (or M[i] <= 0) takes that least M.  m, p,
- * q, D as in hdc_convnd.  inputs: n device pointers, each batch x prod(L)
- * complex; h: batch x prod(L), distinct from every input (else
- * HDC_ERR_PARAM).  Workspace: hdc_workspace_size_multi. */
-int hdc_workspace_size_multi(int dims, int n, const int64_t* L,
+/* Multi-convolution of n arrays (n = 2..8; the paper extends the method
+ * to N arrays), all inputs of one shape, first L outputs per axis, with one
+ * of two operators applied per DFT index of each residue:
+ *   HDC_MULTI_PRODUCT: the n-fold convolution x_0 * x_1 * ... * x_{n-1}
+ *     (product of all n transforms); its result has length n (L - 1) + 1
+ *     per axis, so M >= n (L - 1) + 1 (else HDC_ERR_ALIAS);
+ *   HDC_MULTI_DOT: the sum of pairwise convolutions
+ *     x_0 * x_1 + x_2 * x_3 + ... (n even, else HDC_ERR_PARAM), M >= 2L - 1.
+ * Per residue every input is folded and transformed (Eq. 1), the operator
+ * is applied, and one inverse transform and unfold follow (Eq. 2).  M =
+ * NULL (or M[i] <= 0) takes the least alias-free M.  m, p, q, D as in
+ * hdc_convnd.  inputs: n device pointers, each batch x prod(L) complex; h:
+ * batch x prod(L), distinct from every input (else HDC_ERR_PARAM).
+ * Workspace: hdc_workspace_size_multi. */
+enum hdc_multi_op { HDC_MULTI_PRODUCT = 0, HDC_MULTI_DOT = 1 };
+int hdc_workspace_size_multi(int dims, int n, int op, const int64_t* L,
                              const int64_t* M, const int64_t* m,
                              const int64_t* p, const int64_t* q,
                              const int64_t* D, int dtype, int64_t batch,
                              size_t* bytes);
-int hdc_convnd_multi(int dims, int n, const void* const* inputs, void* h,
+int hdc_convnd_multi(int dims, int n, int op, const void* const* inputs, void* h,
                      const int64_t* L, const int64_t* M, const int64_t* m,
                      const int64_t* p, const int64_t* q, const int64_t* D,
                      int dtype, int64_t batch, void* workspace,
@@ -405,6 +410,21 @@ int hdc_tune_unequal(int dims, const int64_t* Lf, const int64_t* Lg,
                      const char* tuning_db, void* stream,
                      hdc_unequal_tuple* best, hdc_unequal_tuple* trials,
                      int64_t cap, int64_t* ntrials);
+
+/* The same search for the multi-convolution of n inputs with operator op
+ * (hdc_convnd_multi): the candidates of hdc_tune_candidates for (L, M) per
+ * axis (M alias-free for op, else HDC_ERR_ALIAS), timed on the caller's
+ * inputs[n] and h. */
+int hdc_tune_multi_workspace_size(int dims, int n, int op, const int64_t* L,
+                                  const int64_t* M, int dtype, int64_t batch,
+                                  double max_ratio, int64_t m_min,
+                                  size_t* bytes);
+int hdc_tune_multi(int dims, int n, int op, const int64_t* L, const int64_t* M,
+                   int dtype, int64_t batch, const void* const* inputs,
+                   void* h, void* workspace, size_t ws_bytes, int warmup,
+                   int reps, double max_ratio, int64_t m_min, void* stream,
+                   hdc_tuple* best, hdc_tuple* trials, int64_t cap,
+                   int64_t* ntrials);
 
 /* ---------------------------------------------------------------- plans
  * A plan fixes (m, p, q, D) per axis for one (dims, L, M, dtype, batch).

@@ -19,8 +19,8 @@ formula each one writes out):
   parameter predictor's network in FP64 (O7)
 * ``conv_unequal(f, g, m, lam, M, o, Lw)`` -- unequal lengths with residue
   matching, Section 3.5 (O8)
-* ``conv_multi(xs, m, p, q)`` -- first L outputs of the n-fold convolution
-  of n arrays (O9)
+* ``conv_multi(xs, m, p, q, op)`` -- first L outputs of the n-fold
+  convolution of n arrays, or of the sum of pairwise convolutions (O9)
 """
 from __future__ import annotations
 
@@ -55,7 +55,7 @@ def lib():
         L.hdco_residue_forward_1d.argtypes = [_dp, _i64, _i64, _i64, _i64, _dp]
         L.hdco_residue_backward_1d.argtypes = [_dp, _i64, _i64, _i64, _i64, _dp]
         L.hdco_conv_hybrid_1d.argtypes = [_dp, _dp, _i64, _i64, _i64, _i64, _dp]
-        L.hdco_conv_multi_1d.argtypes = [_dp, C.c_int, _i64, _i64, _i64, _i64, _dp]
+        L.hdco_conv_multi_1d.argtypes = [_dp, C.c_int, C.c_int, _i64, _i64, _i64, _i64, _dp]
         L.hdco_conv_unequal_1d.argtypes = [_dp, _i64, _dp, _i64, _i64, _i64, _i64, _i64, _i64, _dp]
         L.hdco_conv_hermitian_2d_direct.argtypes = [_dp, _dp, _i64, _dp]
         L.hdco_conv_hermitian_2d_fft.argtypes = [_dp, _dp, _i64, _dp]
@@ -208,18 +208,20 @@ def conv_unequal(f, g, m: int, lam: int = 1, M: int | None = None, o: int = 0, L
     return h
 
 
-def conv_multi(xs, m: int, p: int = 0, q: int = 0):
-    """First L outputs of x_0 * x_1 * ... * x_{n-1} for xs of shape (n, L),
-    by the residue transforms (O9); p, q default to ceil(L/m) and
-    ceil((n (L - 1) + 1) / m)."""
+def conv_multi(xs, m: int, p: int = 0, q: int = 0, op: str = "product"):
+    """First L outputs, for xs of shape (n, L), of x_0 * x_1 * ... * x_{n-1}
+    (op 'product') or x_0 * x_1 + x_2 * x_3 + ... (op 'dot'), by the residue
+    transforms (O9); p, q default to ceil(L/m) and the least alias-free q."""
     xs = np.ascontiguousarray(xs, dtype=np.complex128)
     n, L = xs.shape
+    opc = {"product": 0, "dot": 1}[op]
     if p == 0:
         p = -(-L // m)
     if q == 0:
-        q = -(-(n * (L - 1) + 1) // m)
+        span = n * (L - 1) + 1 if opc == 0 else 2 * L - 1
+        q = -(-span // m)
     h = np.empty(L, dtype=np.complex128)
-    _check(lib().hdco_conv_multi_1d(_dptr(xs), n, L, m, p, q, _dptr(h)), "conv_multi")
+    _check(lib().hdco_conv_multi_1d(_dptr(xs), n, opc, L, m, p, q, _dptr(h)), "conv_multi")
     return h
 
 

@@ -20,8 +20,8 @@
  *   O7  the parameter predictor's MLP: loss and gradients in FP64, Adam
  *   O8  unequal lengths with residue matching (Section 3.5, the final
  *       algorithm for one dimension), built from O5's Eq. 1 and Eq. 2
- *   O9  multi-convolution of n arrays (the n-fold convolution), by the
- *       same residue transforms with the product taken over all n inputs
+ *   O9  multi-convolution of n arrays: the n-fold convolution, or the sum
+ *       of pairwise convolutions, by the same residue transforms
  *
  * Sign convention (the paper's Eq. 1 and Eq. 2): zeta_n = exp(2 pi i / n),
  * forward transforms use zeta^{+kj} unscaled, backward use zeta^{-kj}/n.
@@ -646,32 +646,52 @@ HDCO_API int hdco_conv_unequal_1d(const double* f, int64_t Lf, const double* g, 
 
 /* ------------------------------------------- O9 multi-convolution, 1-D */
 
-/* First L outputs of the n-fold linear convolution x_0 * x_1 * ... * x_{n-1}
- * of n length-L inputs (concatenated in xs, input i at xs + 2 i L), by the
- * residue transforms: Eq. 1 for every input with the same (m, p, q), the
- * product of all n transforms at every DFT index, Eq. 2.  The full result
- * has length n (L - 1) + 1, so the first L outputs are alias-free when
- * q m >= n (L - 1) + 1.  Returns 0, -1 on invalid parameters, -3 on
- * allocation failure. */
-HDCO_API int hdco_conv_multi_1d(const double* xs, int n, int64_t L, int64_t m, int64_t p, int64_t q, double* h)
+/* First L outputs of a multi-convolution of n length-L inputs
+ * (concatenated in xs, input i at xs + 2 i L) by the residue transforms:
+ * Eq. 1 for every input with the same (m, p, q); at every DFT index either
+ * the product of all n transforms (op 0: the n-fold convolution
+ * x_0 * x_1 * ... * x_{n-1}, full length n (L - 1) + 1, alias-free when
+ * q m >= n (L - 1) + 1) or the sum of the pairwise products
+ * F_0 F_1 + F_2 F_3 + ... (op 1, n even: x_0 * x_1 + x_2 * x_3 + ...,
+ * alias-free when q m >= 2 L - 1); then Eq. 2.  Returns 0, -1 on invalid
+ * parameters, -3 on allocation failure. */
+HDCO_API int hdco_conv_multi_1d(const double* xs, int n, int op, int64_t L, int64_t m, int64_t p, int64_t q,
+                                double* h)
 {
-    if (n < 1 || L < 1 || m < 1 || p * m < L || q < 1) return -1;
+    if (n < 1 || L < 1 || m < 1 || p * m < L || q < 1 || (op != 0 && op != 1)) return -1;
+    if (op == 1 && (n % 2)) return -1;
     const int64_t N = q * m;
-    if (N < (int64_t)n * (L - 1) + 1) return -1;
-    double* H = (double*)malloc(sizeof(double) * 2 * (size_t)N);
+    const int64_t span = op == 0 ? (int64_t)n * (L - 1) + 1 : 2 * L - 1;
+    if (N < span) return -1;
+    double* H = (double*)calloc(2 * (size_t)N, sizeof(double));
+    double* A = (double*)malloc(sizeof(double) * 2 * (size_t)N);
     double* F = (double*)malloc(sizeof(double) * 2 * (size_t)N);
-    if (!H || !F) { free(H); free(F); return -3; }
-    int rc = hdco_residue_forward_1d(xs, L, m, p, q, H);
-    for (int i = 1; i < n && rc == 0; ++i) {
-        rc = hdco_residue_forward_1d(xs + 2 * (size_t)i * (size_t)L, L, m, p, q, F);
-        for (int64_t k = 0; k < N && rc == 0; ++k) {
-            const double a = H[2 * k], b = H[2 * k + 1], c = F[2 * k], d = F[2 * k + 1];
-            H[2 * k] = a * c - b * d;
-            H[2 * k + 1] = a * d + b * c;
+    if (!H || !A || !F) { free(H); free(A); free(F); return -3; }
+    int rc = 0;
+    if (op == 0) {
+        rc = hdco_residue_forward_1d(xs, L, m, p, q, H);
+        for (int i = 1; i < n && rc == 0; ++i) {
+            rc = hdco_residue_forward_1d(xs + 2 * (size_t)i * (size_t)L, L, m, p, q, F);
+            for (int64_t k = 0; k < N && rc == 0; ++k) {
+                const double a = H[2 * k], b = H[2 * k + 1], c = F[2 * k], d = F[2 * k + 1];
+                H[2 * k] = a * c - b * d;
+                H[2 * k + 1] = a * d + b * c;
+            }
+        }
+    } else {
+        for (int i = 0; i + 1 < n && rc == 0; i += 2) {
+            rc = hdco_residue_forward_1d(xs + 2 * (size_t)i * (size_t)L, L, m, p, q, A);
+            rc |= hdco_residue_forward_1d(xs + 2 * (size_t)(i + 1) * (size_t)L, L, m, p, q, F);
+            for (int64_t k = 0; k < N && rc == 0; ++k) {
+                const double a = A[2 * k], b = A[2 * k + 1], c = F[2 * k], d = F[2 * k + 1];
+                H[2 * k] += a * c - b * d;
+                H[2 * k + 1] += a * d + b * c;
+            }
         }
     }
     if (rc == 0) rc = hdco_residue_backward_1d(H, L, m, p, q, h);
     free(H);
+    free(A);
     free(F);
     return rc ? -1 : 0;
 }

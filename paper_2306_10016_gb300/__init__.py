@@ -40,6 +40,10 @@ HDC_ERR_CUDA = -6
 HDC_ERR_TIMEOUT = -7
 HDC_ERR_NOT_TUNED = -8
 HDC_ERR_WORKSPACE = -9
+HDC_MULTI_PRODUCT = 0
+HDC_MULTI_DOT = 1
+_MULTI_OPS = {"product": HDC_MULTI_PRODUCT, "dot": HDC_MULTI_DOT, HDC_MULTI_PRODUCT: HDC_MULTI_PRODUCT,
+              HDC_MULTI_DOT: HDC_MULTI_DOT}
 
 LIB_PATH = _build_ext.LIB
 # the predictor network trained on this GPU's grid-search timings (a
@@ -103,6 +107,10 @@ class UTuple(C.Structure):
 _tp = C.POINTER(Tuple)
 _utp = C.POINTER(UTuple)
 _SIGS += [
+    ("hdc_tune_multi_workspace_size", C.c_int, [C.c_int, C.c_int, C.c_int, _i64p, _i64p, C.c_int, _i64, C.c_double,
+                                                _i64, C.POINTER(_sz)]),
+    ("hdc_tune_multi", C.c_int, [C.c_int, C.c_int, C.c_int, _i64p, _i64p, C.c_int, _i64, C.POINTER(_vp), _vp, _vp,
+                                 _sz, C.c_int, C.c_int, C.c_double, _i64, _vp, _tp, _tp, _i64, _i64p]),
     ("hdc_tune_unequal_candidates", C.c_int, [_i64, _i64, _i64, C.c_int, C.c_double, _i64, _utp, _i64, _i64p]),
     ("hdc_tune_unequal_workspace_size", C.c_int, [C.c_int, _i64p, _i64p, _i64p, C.c_int, _i64, C.c_double, _i64,
                                                   C.POINTER(_sz)]),
@@ -144,10 +152,10 @@ _SIGS += [
                                              C.c_int, _i64, C.POINTER(_sz)]),
     ("hdc_convnd_unequal", C.c_int, [C.c_int, _vp, _vp, _vp, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p,
                                      _i64p, C.c_int, _i64, _vp, _sz, _vp]),
-    ("hdc_workspace_size_multi", C.c_int, [C.c_int, C.c_int, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, C.c_int,
-                                           _i64, C.POINTER(_sz)]),
-    ("hdc_convnd_multi", C.c_int, [C.c_int, C.c_int, C.POINTER(_vp), _vp, _i64p, _i64p, _i64p, _i64p, _i64p,
-                                   _i64p, C.c_int, _i64, _vp, _sz, _vp]),
+    ("hdc_workspace_size_multi", C.c_int, [C.c_int, C.c_int, C.c_int, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p,
+                                           C.c_int, _i64, C.POINTER(_sz)]),
+    ("hdc_convnd_multi", C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(_vp), _vp, _i64p, _i64p, _i64p, _i64p,
+                                   _i64p, _i64p, C.c_int, _i64, _vp, _sz, _vp]),
     ("hdc_workspace_size_hermitian", C.c_int, [_i64, _i64p, _i64p, C.c_int, _i64, C.POINTER(_sz)]),
     ("hdc_conv2d_hermitian", C.c_int, [_vp, _vp, _vp, _i64, _i64p, _i64p, C.c_int, _i64, _vp, _sz, _vp]),
     ("hdc_mlp_create", C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, C.c_int]),
@@ -371,19 +379,27 @@ def convnd_window(f, g, dims, m, o, Lw, M=None, p=0, q=0, D=0, out=None, workspa
     return h
 
 
-def workspace_size_multi(n, L, m, M=None, p=0, q=0, D=0, dtype=HDC_C128, batch=1) -> int:
+def _multi_op(op) -> int:
+    if op not in _MULTI_OPS:
+        raise ValueError("op must be 'product' or 'dot'")
+    return _MULTI_OPS[op]
+
+
+def workspace_size_multi(n, L, m, op="product", M=None, p=0, q=0, D=0, dtype=HDC_C128, batch=1) -> int:
     dims = len(L)
     mv, Mv, pv, qv, Dv = (_per_axis(v, dims, k) for v, k in ((m, "m"), (M, "M"), (p, "p"), (q, "q"), (D, "D")))
     nb = C.c_size_t()
-    _check(lib().hdc_workspace_size_multi(dims, int(n), _arr(L), _arr(Mv), _arr(mv), _arr(pv), _arr(qv), _arr(Dv),
-                                          dtype, int(batch), C.byref(nb)), "workspace_size_multi")
+    _check(lib().hdc_workspace_size_multi(dims, int(n), _multi_op(op), _arr(L), _arr(Mv), _arr(mv), _arr(pv),
+                                          _arr(qv), _arr(Dv), dtype, int(batch), C.byref(nb)), "workspace_size_multi")
     return nb.value
 
 
-def convnd_multi(xs, dims, m, M=None, p=0, q=0, D=0, out=None, workspace=None, stream=None):
-    """First L outputs per axis of the n-fold convolution xs[0] * ... *
-    xs[n-1] over the last `dims` axes (hdc_convnd_multi); xs: a list of
-    2..8 CUDA tensors of one shape and dtype (leading axes are a batch)."""
+def convnd_multi(xs, dims, m, op="product", M=None, p=0, q=0, D=0, out=None, workspace=None, stream=None):
+    """First L outputs per axis over the last `dims` axes of the n-fold
+    convolution xs[0] * ... * xs[n-1] (op 'product') or of the sum of
+    pairwise convolutions xs[0] * xs[1] + xs[2] * xs[3] + ... (op 'dot');
+    xs: a list of 2..8 CUDA tensors of one shape and dtype (leading axes
+    are a batch).  hdc_convnd_multi."""
     torch = _torch()
     xs = list(xs)
     n = len(xs)
@@ -399,14 +415,15 @@ def convnd_multi(xs, dims, m, M=None, p=0, q=0, D=0, out=None, workspace=None, s
     mv, Mv, pv, qv, Dv = (_per_axis(v, dims, k) for v, k in ((m, "m"), (M, "M"), (p, "p"), (q, "q"), (D, "D")))
     h = out if out is not None else torch.empty_like(x0)
     nb = C.c_size_t()
-    _check(lib().hdc_workspace_size_multi(dims, n, _arr(L), _arr(Mv), _arr(mv), _arr(pv), _arr(qv), _arr(Dv), dt,
+    opc = _multi_op(op)
+    _check(lib().hdc_workspace_size_multi(dims, n, opc, _arr(L), _arr(Mv), _arr(mv), _arr(pv), _arr(qv), _arr(Dv), dt,
                                           batch, C.byref(nb)), "workspace_size_multi")
     if workspace is None or workspace.numel() * workspace.element_size() < nb.value:
         workspace = torch.empty(max(1, nb.value), dtype=torch.uint8, device=x0.device)
     ptrs = (_vp * n)(*[x.data_ptr() for x in xs])
     st = stream if stream is not None else torch.cuda.current_stream(x0.device)
     with torch.cuda.device(x0.device):
-        _check(lib().hdc_convnd_multi(dims, n, ptrs, h.data_ptr(), _arr(L), _arr(Mv), _arr(mv), _arr(pv), _arr(qv),
+        _check(lib().hdc_convnd_multi(dims, n, opc, ptrs, h.data_ptr(), _arr(L), _arr(Mv), _arr(mv), _arr(pv), _arr(qv),
                                       _arr(Dv), dt, batch, workspace.data_ptr(),
                                       workspace.numel() * workspace.element_size(), st.cuda_stream),
                "hdc_convnd_multi")
@@ -673,6 +690,41 @@ def tune_unequal(f, g, dims, M=None, max_ratio=1.5, m_min=16, warmup=1, reps=3, 
         _check(lib().hdc_tune_unequal(dims, _arr(Lf), _arr(Lg), _arr(Mv), dt, batch, f.data_ptr(), g.data_ptr(),
                                       h.data_ptr(), ws.data_ptr(), nb.value, warmup, reps, max_ratio, m_min, db,
                                       st.cuda_stream, best, trials, cap, C.byref(nt)), "tune_unequal")
+    tr = [[trials[i * dims + a].as_dict() for a in range(dims)] for i in range(min(nt.value, cap))]
+    return [best[a].as_dict() for a in range(dims)], tr
+
+
+def tune_multi(xs, dims, op="product", M=None, max_ratio=1.5, m_min=16, warmup=1, reps=3, stream=None):
+    """Grid search of (m, D) per axis for hdc_convnd_multi with operator op
+    on the given inputs (a list of 2..8 CUDA tensors of one shape); returns
+    (best per axis, trials)."""
+    torch = _torch()
+    xs = list(xs)
+    n = len(xs)
+    x0 = xs[0]
+    dt = dtype_code(x0.dtype)
+    L = [int(v) for v in x0.shape[x0.dim() - dims:]]
+    batch = 1
+    for v in x0.shape[: x0.dim() - dims]:
+        batch *= int(v)
+    opc = _multi_op(op)
+    k = n if opc == HDC_MULTI_PRODUCT else 2
+    Mv = _per_axis(M, dims, "M") or [k * (l - 1) + 1 for l in L]
+    nb = C.c_size_t()
+    _check(lib().hdc_tune_multi_workspace_size(dims, n, opc, _arr(L), _arr(Mv), dt, batch, max_ratio, m_min,
+                                               C.byref(nb)), "tune_multi_workspace_size")
+    ws = torch.empty(max(1, nb.value), dtype=torch.uint8, device=x0.device)
+    h = torch.empty_like(x0)
+    cap = 4096
+    best = (Tuple * dims)()
+    trials = (Tuple * (cap * dims))()
+    nt = C.c_int64()
+    ptrs = (_vp * n)(*[x.data_ptr() for x in xs])
+    st = stream if stream is not None else torch.cuda.current_stream(x0.device)
+    with torch.cuda.device(x0.device):
+        _check(lib().hdc_tune_multi(dims, n, opc, _arr(L), _arr(Mv), dt, batch, ptrs, h.data_ptr(), ws.data_ptr(),
+                                    nb.value, warmup, reps, max_ratio, m_min, st.cuda_stream, best, trials, cap,
+                                    C.byref(nt)), "tune_multi")
     tr = [[trials[i * dims + a].as_dict() for a in range(dims)] for i in range(min(nt.value, cap))]
     return [best[a].as_dict() for a in range(dims)], tr
 

@@ -286,10 +286,12 @@ static size_t ws_bytes(int dims, const Axis* ax, int64_t B, size_t esz, int ncop
     } while (0)
 
 // The inputs of one convolution: n = 2 is f (x[0]) and g (x[1]), possibly
-// of unequal lengths; n > 2 is a multi-convolution of equal-length inputs.
+// of unequal lengths; n > 2 is a multi-convolution of equal-length inputs,
+// op 0 the n-fold product, op 1 the sum of pairwise products.
 template <typename T> struct Ins {
     const cx<T>* x[kMaxInputs];
     int n;
+    int op;
 };
 
 // 1-D convolution of B rows (input row strides ld_f for x[0], ld_g for the
@@ -314,7 +316,7 @@ static cudaError_t run_rows(const Ins<T>& in, cx<T>* out, int64_t B, int64_t ld_
             // with one transform size the fold runs over the longer input's
             // blocks; the inputs commute, so the longer one goes second
             if (in.n > 2)
-                HDC_TRY(launch_residue_rows_multi<T>(in.x, in.n, ws, B, ld_g, a.L, a.m, a.p, a.q, r0, Dp, st));
+                HDC_TRY(launch_residue_rows_multi<T>(in.x, in.n, in.op, ws, B, ld_g, a.L, a.m, a.p, a.q, r0, Dp, st));
             else if (a.lam == 1 && a.Lf <= a.L)
                 HDC_TRY(launch_residue_rows<T>(f, g, ws, B, ld_f, ld_g, a.Lf, a.L, a.m, a.p, a.q, r0, Dp, st));
             else if (a.lam == 1)
@@ -342,7 +344,7 @@ static cudaError_t run_rows(const Ins<T>& in, cx<T>* out, int64_t B, int64_t ld_
             ColSide<T> sides[kMaxInputs];
             for (int i = 0; i < in.n; ++i) sides[i] = ColSide<T>{ in.x[i], y[i], ld_g, a.L, (int)a.p, (int)a.q, 0, 1 };
             HDC_TRY(launch_fold_fft_cols<T>(sides, in.n, B, m2, m1, a.N, m2, 1, r0, Dg, 1, st));
-            HDC_TRY(launch_residue_rows_multi<T>(y, in.n, y[0], Dg * B * m1, m2, m2, m2, 1, 1, 0, 1, st));
+            HDC_TRY(launch_residue_rows_multi<T>(y, in.n, in.op, y[0], Dg * B * m1, m2, m2, m2, 1, 1, 0, 1, st));
         } else {
             const ColSide<T> sf{ f, y[0], ld_f, a.Lf, (int)a.pf, (int)(a.q * a.lam), (int)a.q, (int)a.lam };
             const ColSide<T> sg{ g, y[1], ld_g, a.L, (int)a.p, (int)a.q, 0, 1 };
@@ -379,6 +381,7 @@ static cudaError_t run_nd(int dims, const Ins<T>& in, cx<T>* out, int64_t B, con
     const int64_t rows = a.D * B * a.m;
     Ins<T> w;
     w.n = in.n;
+    w.op = in.op;
     cx<T>* wi[kMaxInputs];
     wi[0] = ws;
     for (int i = 1; i < in.n; ++i) wi[i] = ws + rows * Cf + (int64_t)(i - 1) * rows * Cn;
@@ -442,6 +445,7 @@ static int conv_nd(int dims, const void* f, const void* g, void* h, const Axis* 
     }
     Ins<T> in;
     in.n = 2;
+    in.op = 0;
     in.x[0] = fin;
     in.x[1] = gin;
     cudaError_t e = run_nd<T>(dims, in, (V*)h, B, ax, (V*)base, st, r_lo, r_hi);
@@ -449,10 +453,10 @@ static int conv_nd(int dims, const void* f, const void* g, void* h, const Axis* 
 }
 
 // Multi-convolution of n equal-shape inputs (device pointers, distinct from
-// h); workspace of ws_bytes(..., nin = n).
+// h), operator op; workspace of ws_bytes(..., nin = n).
 template <typename T>
-static int conv_nd_multi(int dims, int n, const void* const* xs, void* h, const Axis* ax, int64_t B, void* ws,
-                         size_t ws_bytes_given, cudaStream_t st)
+static int conv_nd_multi(int dims, int n, int op, const void* const* xs, void* h, const Axis* ax, int64_t B,
+                         void* ws, size_t ws_bytes_given, cudaStream_t st)
 {
     using V = cx<T>;
     const size_t need = ws_bytes(dims, ax, B, sizeof(V), 0, n);
@@ -460,6 +464,7 @@ static int conv_nd_multi(int dims, int n, const void* const* xs, void* h, const 
     uintptr_t base = ((uintptr_t)ws + 255) & ~(uintptr_t)255;
     Ins<T> in;
     in.n = n;
+    in.op = op;
     for (int i = 0; i < n; ++i) in.x[i] = (const V*)xs[i];
     cudaError_t e = run_nd<T>(dims, in, (V*)h, B, ax, (V*)base, st);
     return e == cudaSuccess ? HDC_OK : HDC_ERR_CUDA;
@@ -497,16 +502,20 @@ static int resolve_all_uneq(int dims, const int64_t* Lf, const int64_t* Lg, cons
 }
 
 // Multi-convolution of n equal-length inputs: the first L outputs of the
-// n-fold convolution per axis are alias-free when M >= n (L - 1) + 1.
-static int resolve_all_multi(int dims, int n, const int64_t* L, const int64_t* M, const int64_t* m,
+// n-fold convolution per axis are alias-free when M >= n (L - 1) + 1; the
+// sum of pairwise products (n even) needs the two-input M >= 2 L - 1.
+static int resolve_all_multi(int dims, int n, int op, const int64_t* L, const int64_t* M, const int64_t* m,
                              const int64_t* p, const int64_t* q, const int64_t* D, int dtype, Axis* ax)
 {
     if (n < 2 || n > kMaxInputs || dims < 1 || dims > HDC_MAX_DIMS || !L || !m) return HDC_ERR_PARAM;
+    if (op != HDC_MULTI_PRODUCT && op != HDC_MULTI_DOT) return HDC_ERR_PARAM;
+    if (op == HDC_MULTI_DOT && (n & 1)) return HDC_ERR_PARAM;
+    const int fold = op == HDC_MULTI_PRODUCT ? n : 2;
     int64_t Mv[HDC_MAX_DIMS];
     for (int i = 0; i < dims; ++i) {
         if (L[i] < 1) return HDC_ERR_PARAM;
-        Mv[i] = (M && M[i] > 0) ? M[i] : n * (L[i] - 1) + 1;
-        if (Mv[i] < n * (L[i] - 1) + 1) return HDC_ERR_ALIAS;
+        Mv[i] = (M && M[i] > 0) ? M[i] : fold * (L[i] - 1) + 1;
+        if (Mv[i] < fold * (L[i] - 1) + 1) return HDC_ERR_ALIAS;
     }
     return resolve_all(dims, L, Mv, m, p, q, D, dtype, ax);
 }
@@ -846,25 +855,25 @@ HDC_EXPORT int hdc_convnd_unequal(int dims, const void* f, const void* g, void* 
     return conv_nd<float>(dims, f, g, h, ax, 0, batch, workspace, ws_bytes_given, st);
 }
 
-HDC_EXPORT int hdc_workspace_size_multi(int dims, int n, const int64_t* L, const int64_t* M, const int64_t* m,
-                                        const int64_t* p, const int64_t* q, const int64_t* D, int dtype,
-                                        int64_t batch, size_t* bytes)
+HDC_EXPORT int hdc_workspace_size_multi(int dims, int n, int op, const int64_t* L, const int64_t* M,
+                                        const int64_t* m, const int64_t* p, const int64_t* q, const int64_t* D,
+                                        int dtype, int64_t batch, size_t* bytes)
 {
     if (!bytes || batch < 0) return HDC_ERR_PARAM;
     Axis ax[HDC_MAX_DIMS];
-    int rc = resolve_all_multi(dims, n, L, M, m, p, q, D, dtype, ax);
+    int rc = resolve_all_multi(dims, n, op, L, M, m, p, q, D, dtype, ax);
     if (rc != HDC_OK) return rc;
     *bytes = ws_bytes(dims, ax, batch, dtype == HDC_C128 ? 16 : 8, 0, n);
     return HDC_OK;
 }
 
-HDC_EXPORT int hdc_convnd_multi(int dims, int n, const void* const* inputs, void* h, const int64_t* L,
+HDC_EXPORT int hdc_convnd_multi(int dims, int n, int op, const void* const* inputs, void* h, const int64_t* L,
                                 const int64_t* M, const int64_t* m, const int64_t* p, const int64_t* q,
                                 const int64_t* D, int dtype, int64_t batch, void* workspace, size_t ws_bytes_given,
                                 void* stream)
 {
     Axis ax[HDC_MAX_DIMS];
-    int rc = resolve_all_multi(dims, n, L, M, m, p, q, D, dtype, ax);
+    int rc = resolve_all_multi(dims, n, op, L, M, m, p, q, D, dtype, ax);
     if (rc != HDC_OK) return rc;
     if (batch < 0 || !inputs || !h) return HDC_ERR_PARAM;
     if (batch == 0) return HDC_OK;
@@ -873,8 +882,9 @@ HDC_EXPORT int hdc_convnd_multi(int dims, int n, const void* const* inputs, void
     for (int i = 0; i < n; ++i)
         if (!inputs[i] || inputs[i] == h || ((uintptr_t)inputs[i] & al)) return HDC_ERR_PARAM;
     cudaStream_t st = (cudaStream_t)stream;
-    if (dtype == HDC_C128) return conv_nd_multi<double>(dims, n, inputs, h, ax, batch, workspace, ws_bytes_given, st);
-    return conv_nd_multi<float>(dims, n, inputs, h, ax, batch, workspace, ws_bytes_given, st);
+    if (dtype == HDC_C128)
+        return conv_nd_multi<double>(dims, n, op, inputs, h, ax, batch, workspace, ws_bytes_given, st);
+    return conv_nd_multi<float>(dims, n, op, inputs, h, ax, batch, workspace, ws_bytes_given, st);
 }
 
 HDC_EXPORT int hdc_release_caches(void)

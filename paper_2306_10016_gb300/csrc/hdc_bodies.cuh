@@ -92,28 +92,42 @@ template <class V> struct InPtrs {
 
 // Multi-convolution, one residue r of one row (offset boff into every
 // input): fold (Eq. 1 inner sum) and m-point FFT of each of the nin inputs,
-// the product of all nin transforms, inverse FFT; the unscaled result goes
-// to hr[0..m).  smem: three padded buffers of m.
+// then per DFT index either the product of all nin transforms (op 0, the
+// nin-fold convolution) or the sum of the pairwise products
+// F_0 F_1 + F_2 F_3 + ... (op 1, nin even); inverse FFT; the unscaled result
+// goes to hr[0..m).  The sum accumulates in hr itself (each thread owns the
+// same elements in every pass).  smem: three padded buffers of m.
 template <class V>
-__device__ __forceinline__ void residue_row_multi_body(const InPtrs<V>& in, int nin, int64_t boff, V* hr, int64_t L,
-                                                       int m, int p, int q, int r, const V* __restrict__ twN,
-                                                       const V* __restrict__ twm, const V* __restrict__ twml,
-                                                       const FftPlan& fp, V* smem, int tid, int nthr)
+__device__ __forceinline__ void residue_row_multi_body(const InPtrs<V>& in, int nin, int op, int64_t boff, V* hr,
+                                                       int64_t L, int m, int p, int q, int r,
+                                                       const V* __restrict__ twN, const V* __restrict__ twm,
+                                                       const V* __restrict__ twml, const FftPlan& fp, V* smem,
+                                                       int tid, int nthr)
 {
     const int plen = (int)padded_len(m);
     V* sa = smem;
     V* sb = sa + plen;
     V* sc = sb + plen;
-    fold_row<V>(in.x[0] + boff, L, m, p, q, r, twN, sa, tid, nthr);
-    __syncthreads();
-    fft_smem<V, false, true>(sa, sc, fp, 1, 1, m, twm, twml, tid, nthr);
-    for (int i = 1; i < nin; ++i) {
-        fold_row<V>(in.x[i] + boff, L, m, p, q, r, twN, sb, tid, nthr);
+    for (int i = 0; i < nin; ++i) {
+        // op 0: sa accumulates the product; op 1: sa holds F_{2j}, sb F_{2j+1}
+        V* dst = (i == 0 || (op == 1 && (i & 1) == 0)) ? sa : sb;
+        fold_row<V>(in.x[i] + boff, L, m, p, q, r, twN, dst, tid, nthr);
         __syncthreads();
-        fft_smem<V, false, true>(sb, sc, fp, 1, 1, m, twm, twml, tid, nthr);
-        for (int s = tid; s < m; s += nthr) sa[sidx<true>(s)] = cmul(sa[sidx<true>(s)], sb[sidx<true>(s)]);
-        __syncthreads();
+        fft_smem<V, false, true>(dst, sc, fp, 1, 1, m, twm, twml, tid, nthr);
+        if (op == 0 && i > 0) {
+            for (int s = tid; s < m; s += nthr) sa[sidx<true>(s)] = cmul(sa[sidx<true>(s)], sb[sidx<true>(s)]);
+            __syncthreads();
+        } else if (op == 1 && (i & 1)) {
+            for (int s = tid; s < m; s += nthr) {
+                const V v = cmul(sa[sidx<true>(s)], sb[sidx<true>(s)]);
+                hr[s] = (i == 1) ? v : cadd(hr[s], v);
+            }
+            __syncthreads();
+        }
     }
+    if (op == 1)
+        for (int s = tid; s < m; s += nthr) sa[sidx<true>(s)] = hr[s];
+    __syncthreads();
     fft_smem<V, true, true>(sa, sc, fp, 1, 1, m, twm, twml, tid, nthr);
     for (int s = tid; s < m; s += nthr) hr[s] = sa[sidx<true>(s)];
     __syncthreads();

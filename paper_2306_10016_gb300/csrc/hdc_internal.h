@@ -81,11 +81,13 @@ cudaError_t launch_residue_rows_lam(const cx<T>* f, const cx<T>* g, cx<T>* h, in
                                     int64_t pg, int64_t qg, int64_t r0, int64_t D, cudaStream_t st);
 
 // Multi-convolution rows: like launch_residue_rows for nin (<= kMaxInputs)
-// equal-length inputs xs[i] (row stride ld, L valid): the product of all nin
-// transforms per residue, unscaled results to h + ((rr * B + b) * m).
+// equal-length inputs xs[i] (row stride ld, L valid): per residue the
+// product of all nin transforms (op 0) or the sum of the pairwise products
+// F_0 F_1 + F_2 F_3 + ... (op 1), unscaled results to h + ((rr * B + b) * m).
 template <typename T>
-cudaError_t launch_residue_rows_multi(const cx<T>* const* xs, int nin, cx<T>* h, int64_t B, int64_t ld, int64_t L,
-                                      int64_t m, int64_t p, int64_t q, int64_t r0, int64_t D, cudaStream_t st);
+cudaError_t launch_residue_rows_multi(const cx<T>* const* xs, int nin, int op, cx<T>* h, int64_t B, int64_t ld,
+                                      int64_t L, int64_t m, int64_t p, int64_t q, int64_t r0, int64_t D,
+                                      cudaStream_t st);
 
 // One input of the strided fold + column FFT pass.  Array view
 // x[b][a][c] (batch stride bstride) with a < A (axis), c < Cn; element valid

@@ -210,23 +210,24 @@ cudaError_t launch_residue_rows_lam(const cx<T>* f, const cx<T>* g, cx<T>* h, in
 
 template <class V>
 __global__ void __launch_bounds__(kMaxThreads, 2)
-k_residue_rows_multi(InPtrs<V> in, int nin, V* h, int64_t B, int64_t ld, int64_t L, int m, int p, int q, int r0,
-                     int Dg, const V* __restrict__ twN, const V* __restrict__ twm, const V* __restrict__ twml,
-                     FftPlan fp)
+k_residue_rows_multi(InPtrs<V> in, int nin, int op, V* h, int64_t B, int64_t ld, int64_t L, int m, int p, int q,
+                     int r0, int Dg, const V* __restrict__ twN, const V* __restrict__ twm,
+                     const V* __restrict__ twml, FftPlan fp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int64_t b = blockIdx.x % B;
     const int rr = (int)(blockIdx.x / B);
-    residue_row_multi_body<V>(in, nin, b * ld, h + ((int64_t)rr * B + b) * m, L, m, p, q, r0 + rr, twN, twm, twml,
-                              fp, reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
+    residue_row_multi_body<V>(in, nin, op, b * ld, h + ((int64_t)rr * B + b) * m, L, m, p, q, r0 + rr, twN, twm,
+                              twml, fp, reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
 }
 
 template <typename T>
-cudaError_t launch_residue_rows_multi(const cx<T>* const* xs, int nin, cx<T>* h, int64_t B, int64_t ld, int64_t L,
-                                      int64_t m, int64_t p, int64_t q, int64_t r0, int64_t D, cudaStream_t st)
+cudaError_t launch_residue_rows_multi(const cx<T>* const* xs, int nin, int op, cx<T>* h, int64_t B, int64_t ld,
+                                      int64_t L, int64_t m, int64_t p, int64_t q, int64_t r0, int64_t D,
+                                      cudaStream_t st)
 {
     using V = cx<T>;
-    if (nin < 1 || nin > kMaxInputs) return cudaErrorInvalidValue;
+    if (nin < 1 || nin > kMaxInputs || op < 0 || op > 1 || (op == 1 && (nin & 1))) return cudaErrorInvalidValue;
     const int64_t Dg = (D < q - r0) ? D : (q - r0);
     if (B <= 0 || Dg <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
@@ -244,14 +245,15 @@ cudaError_t launch_residue_rows_multi(const cx<T>* const* xs, int nin, cx<T>* h,
     InPtrs<V> in;
     for (int i = 0; i < kMaxInputs; ++i) in.x[i] = xs[i < nin ? i : 0];
     const int64_t blocks = B * Dg;
-    // model: nin forward FFTs, one inverse, nin - 1 products, the folds
+    // model: nin forward FFTs, one inverse, nin - 1 products (op 0) or
+    // nin / 2 products and nin / 2 - 1 sums (op 1), the folds
     const double Lrow = (double)((L < p * m) ? L : p * m);
     const double fold = (p == 1 && q == 1) ? 0.0 : 8.0 * nin * Lrow;
-    LaunchScope ls(K_RESIDUE_ROWS, st,
-                   (double)(B * Dg) * ((nin + 1.0) * fft_flops((double)m) + 6.0 * (nin - 1) * m + fold),
+    const double pointwise = op == 0 ? 6.0 * (nin - 1) * m : (6.0 * (nin / 2) + 2.0 * (nin / 2 - 1)) * m;
+    LaunchScope ls(K_RESIDUE_ROWS, st, (double)(B * Dg) * ((nin + 1.0) * fft_flops((double)m) + pointwise + fold),
                    (nin * B * Lrow + (double)(Dg * B * m)) * sizeof(V));
-    kern<<<(unsigned)blocks, thr, smem, st>>>(in, nin, h, B, ld, L, (int)m, (int)p, (int)q, (int)r0, (int)Dg, twN,
-                                              twm, twml, fp);
+    kern<<<(unsigned)blocks, thr, smem, st>>>(in, nin, op, h, B, ld, L, (int)m, (int)p, (int)q, (int)r0, (int)Dg,
+                                              twN, twm, twml, fp);
     return cudaGetLastError();
 }
 
@@ -546,9 +548,9 @@ HDC_INST_TW(float)
     template cudaError_t launch_residue_rows_lam<T>(const cx<T>*, const cx<T>*, cx<T>*, int64_t, int64_t, \
                                                     int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, \
                                                     int64_t, int64_t, int64_t, int64_t, cudaStream_t);    \
-    template cudaError_t launch_residue_rows_multi<T>(const cx<T>* const*, int, cx<T>*, int64_t, int64_t, \
+    template cudaError_t launch_residue_rows_multi<T>(const cx<T>* const*, int, int, cx<T>*, int64_t,      \
                                                       int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, \
-                                                      cudaStream_t);                                        \
+                                                      int64_t, cudaStream_t);                               \
     template cudaError_t launch_fold_fft_cols<T>(const ColSide<T>*, int, int64_t, int64_t, int64_t,     \
                                                  int64_t, int64_t, int64_t, int64_t, int64_t, int,      \
                                                  cudaStream_t);                                         \

@@ -176,39 +176,6 @@ void db_store(const char* path, const std::string& key, int dims, const hdc_tupl
     fclose(fp);
 }
 
-// Median device time of one configuration (ms), or < 0 on error.
-double time_config(int dims, const void* f, const void* g, void* h, const int64_t* L, const int64_t* M,
-                   const hdc_tuple* t, int dtype, int64_t batch, void* ws, size_t ws_bytes, int warmup, int reps,
-                   cudaStream_t st)
-{
-    int64_t m[HDC_MAX_DIMS], p[HDC_MAX_DIMS], q[HDC_MAX_DIMS], D[HDC_MAX_DIMS];
-    for (int i = 0; i < dims; ++i) { m[i] = t[i].m; p[i] = t[i].p; q[i] = t[i].q; D[i] = t[i].D; }
-    size_t need = 0;
-    if (hdc_workspace_size(dims, L, M, m, p, q, D, dtype, batch, 0, &need) != HDC_OK || need > ws_bytes) return -1.0;
-    for (int w = 0; w < warmup; ++w)
-        if (hdc_convnd(dims, f, g, h, L, M, m, p, q, D, 0, dtype, batch, ws, ws_bytes, st) != HDC_OK) return -1.0;
-    std::vector<float> ts;
-    cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess) return -1.0;
-    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return -1.0; }
-    double res = -1.0;
-    for (int r = 0; r < reps; ++r) {
-        cudaEventRecord(e0, st);
-        if (hdc_convnd(dims, f, g, h, L, M, m, p, q, D, 0, dtype, batch, ws, ws_bytes, st) != HDC_OK) break;
-        cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess) break;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        ts.push_back(ms);
-    }
-    if ((int)ts.size() == reps && reps > 0) {
-        std::sort(ts.begin(), ts.end());
-        res = ts[ts.size() / 2];
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    return res;
-}
 
 // ----------------------------------------------------- unequal lengths
 
@@ -341,20 +308,22 @@ void db_store_uneq(const char* path, const std::string& key, int dims, const hdc
     fclose(fp);
 }
 
-double time_config_uneq(int dims, const void* f, const void* g, void* h, const int64_t* Lf, const int64_t* Lg,
-                        const int64_t* M, const hdc_unequal_tuple* t, int dtype, int64_t batch, void* ws,
-                        size_t ws_bytes, int warmup, int reps, cudaStream_t st)
+
+int resolve_M_uneq(int dims, const int64_t* Lf, const int64_t* Lg, const int64_t* M, int64_t* Mo)
 {
-    int64_t m[HDC_MAX_DIMS], lam[HDC_MAX_DIMS], D[HDC_MAX_DIMS];
-    for (int i = 0; i < dims; ++i) { m[i] = t[i].m; lam[i] = t[i].lam; D[i] = t[i].D; }
-    size_t need = 0;
-    if (hdc_workspace_size_unequal(dims, Lf, Lg, M, m, lam, D, nullptr, nullptr, dtype, batch, &need) != HDC_OK ||
-        need > ws_bytes)
-        return -1.0;
-    auto call = [&]() {
-        return hdc_convnd_unequal(dims, f, g, h, Lf, Lg, M, m, lam, D, nullptr, nullptr, dtype, batch, ws, ws_bytes,
-                                  st);
-    };
+    if (dims < 1 || dims > HDC_MAX_DIMS || !Lf || !Lg) return HDC_ERR_PARAM;
+    for (int i = 0; i < dims; ++i) {
+        if (Lf[i] < 1 || Lg[i] < 1) return HDC_ERR_PARAM;
+        Mo[i] = (M && M[i] > 0) ? M[i] : Lf[i] + Lg[i] - 1;
+        if (Mo[i] < Lf[i] + Lg[i] - 1) return HDC_ERR_ALIAS;
+    }
+    return HDC_OK;
+}
+
+// Median device time (ms) of `reps` calls after `warmup` untimed ones, or
+// < 0 if a call fails.
+template <class CallFn> double median_ms(CallFn call, int warmup, int reps, cudaStream_t st)
+{
     for (int w = 0; w < warmup; ++w)
         if (call() != HDC_OK) return -1.0;
     std::vector<float> ts;
@@ -380,14 +349,111 @@ double time_config_uneq(int dims, const void* f, const void* g, void* h, const i
     return res;
 }
 
-int resolve_M_uneq(int dims, const int64_t* Lf, const int64_t* Lg, const int64_t* M, int64_t* Mo)
+// Median device time of one configuration of each kind (ms), or < 0 on error.
+double time_config(int dims, const void* f, const void* g, void* h, const int64_t* L, const int64_t* M,
+                   const hdc_tuple* t, int dtype, int64_t batch, void* ws, size_t ws_bytes, int warmup, int reps,
+                   cudaStream_t st)
 {
-    if (dims < 1 || dims > HDC_MAX_DIMS || !Lf || !Lg) return HDC_ERR_PARAM;
-    for (int i = 0; i < dims; ++i) {
-        if (Lf[i] < 1 || Lg[i] < 1) return HDC_ERR_PARAM;
-        Mo[i] = (M && M[i] > 0) ? M[i] : Lf[i] + Lg[i] - 1;
-        if (Mo[i] < Lf[i] + Lg[i] - 1) return HDC_ERR_ALIAS;
+    int64_t m[HDC_MAX_DIMS], p[HDC_MAX_DIMS], q[HDC_MAX_DIMS], D[HDC_MAX_DIMS];
+    for (int i = 0; i < dims; ++i) { m[i] = t[i].m; p[i] = t[i].p; q[i] = t[i].q; D[i] = t[i].D; }
+    size_t need = 0;
+    if (hdc_workspace_size(dims, L, M, m, p, q, D, dtype, batch, 0, &need) != HDC_OK || need > ws_bytes) return -1.0;
+    return median_ms([&]() { return hdc_convnd(dims, f, g, h, L, M, m, p, q, D, 0, dtype, batch, ws, ws_bytes, st); },
+                     warmup, reps, st);
+}
+
+double time_config_uneq(int dims, const void* f, const void* g, void* h, const int64_t* Lf, const int64_t* Lg,
+                        const int64_t* M, const hdc_unequal_tuple* t, int dtype, int64_t batch, void* ws,
+                        size_t ws_bytes, int warmup, int reps, cudaStream_t st)
+{
+    int64_t m[HDC_MAX_DIMS], lam[HDC_MAX_DIMS], D[HDC_MAX_DIMS];
+    for (int i = 0; i < dims; ++i) { m[i] = t[i].m; lam[i] = t[i].lam; D[i] = t[i].D; }
+    size_t need = 0;
+    if (hdc_workspace_size_unequal(dims, Lf, Lg, M, m, lam, D, nullptr, nullptr, dtype, batch, &need) != HDC_OK ||
+        need > ws_bytes)
+        return -1.0;
+    return median_ms(
+        [&]() {
+            return hdc_convnd_unequal(dims, f, g, h, Lf, Lg, M, m, lam, D, nullptr, nullptr, dtype, batch, ws,
+                                      ws_bytes, st);
+        },
+        warmup, reps, st);
+}
+
+double time_config_multi(int dims, int n, int op, const void* const* xs, void* h, const int64_t* L,
+                         const int64_t* M, const hdc_tuple* t, int dtype, int64_t batch, void* ws, size_t ws_bytes,
+                         int warmup, int reps, cudaStream_t st)
+{
+    int64_t m[HDC_MAX_DIMS], p[HDC_MAX_DIMS], q[HDC_MAX_DIMS], D[HDC_MAX_DIMS];
+    for (int i = 0; i < dims; ++i) { m[i] = t[i].m; p[i] = t[i].p; q[i] = t[i].q; D[i] = t[i].D; }
+    size_t need = 0;
+    if (hdc_workspace_size_multi(dims, n, op, L, M, m, p, q, D, dtype, batch, &need) != HDC_OK || need > ws_bytes)
+        return -1.0;
+    return median_ms(
+        [&]() { return hdc_convnd_multi(dims, n, op, xs, h, L, M, m, p, q, D, dtype, batch, ws, ws_bytes, st); },
+        warmup, reps, st);
+}
+
+// The separable search of Section 4.2 over per-axis candidate lists c[ax]
+// (tuples with q, D and ms fields): axes from the last to the first, each
+// swept with the others at their best so far (the smallest model flops to
+// start), then the three fastest of the axis re-timed with D = 1, 2, 4, ...
+// below q.  time(t) is the median ms of the whole call for the tuple array
+// t (< 0: unusable).  trials (cap records of dims tuples) gets every timed
+// configuration, *ntrials their count.
+template <class Tup, class TimeFn>
+int separable_search(int dims, const std::vector<Tup>* c, TimeFn time, Tup* best, Tup* trials, int64_t cap,
+                     int64_t* ntrials)
+{
+    Tup cur[HDC_MAX_DIMS];
+    for (int i = 0; i < dims; ++i) cur[i] = c[i][0];
+    int64_t nt = 0;
+    auto record = [&](const Tup* t, double ms) {
+        if (trials && nt < cap) {
+            for (int i = 0; i < dims; ++i) {
+                trials[nt * dims + i] = t[i];
+                trials[nt * dims + i].ms = ms;
+            }
+        }
+        ++nt;
+    };
+    double best_ms = -1.0;
+    for (int ax = dims - 1; ax >= 0; --ax) {
+        std::vector<std::pair<double, Tup>> timed;
+        for (const auto& cand : c[ax]) {
+            Tup t[HDC_MAX_DIMS];
+            for (int i = 0; i < dims; ++i) t[i] = cur[i];
+            t[ax] = cand;
+            const double ms = time(t);
+            if (ms < 0) continue;
+            record(t, ms);
+            timed.emplace_back(ms, cand);
+        }
+        if (timed.empty()) return HDC_ERR_CUDA;
+        std::sort(timed.begin(), timed.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+        Tup bax = timed[0].second;
+        double bms = timed[0].first;
+        for (size_t k = 0; k < timed.size() && k < 3; ++k) {
+            const Tup base = timed[k].second;
+            for (int64_t Dv = 1; Dv < base.q; Dv *= 2) {
+                Tup t[HDC_MAX_DIMS];
+                for (int i = 0; i < dims; ++i) t[i] = cur[i];
+                t[ax] = base;
+                t[ax].D = Dv;
+                const double ms = time(t);
+                if (ms < 0) continue;
+                record(t, ms);
+                if (ms < bms) { bms = ms; bax = t[ax]; }
+            }
+        }
+        cur[ax] = bax;
+        best_ms = bms;
     }
+    for (int i = 0; i < dims; ++i) {
+        best[i] = cur[i];
+        best[i].ms = best_ms;
+    }
+    if (ntrials) *ntrials = nt;
     return HDC_OK;
 }
 
@@ -444,63 +510,17 @@ HDC_EXPORT int hdc_tune_convnd(int dims, const int64_t* L, const int64_t* M, int
     if (dims < 1 || dims > HDC_MAX_DIMS || !L || !M || !best || !f || !g || !h || reps < 1) return HDC_ERR_PARAM;
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<hdc_tuple> c[HDC_MAX_DIMS];
-    hdc_tuple cur[HDC_MAX_DIMS];
     for (int i = 0; i < dims; ++i) {
         if (M[i] < 2 * L[i] - 1) return HDC_ERR_ALIAS;
         c[i] = candidates(L[i], M[i], dtype, max_ratio, m_min);
         if (c[i].empty()) return HDC_ERR_UNSUPPORTED_SIZE;
-        cur[i] = c[i][0]; // the smallest model flops as the starting point
     }
-    int64_t nt = 0;
-    auto record = [&](const hdc_tuple* t, double ms) {
-        if (trials && nt < cap * dims) {
-            for (int i = 0; i < dims; ++i) {
-                trials[nt * dims + i] = t[i];
-                trials[nt * dims + i].ms = ms;
-            }
-        }
-        ++nt;
-    };
-    double best_ms = -1.0;
-    for (int ax = dims - 1; ax >= 0; --ax) {
-        // sweep m for this axis with D = q
-        std::vector<std::pair<double, hdc_tuple>> timed;
-        for (const auto& cand : c[ax]) {
-            hdc_tuple t[HDC_MAX_DIMS];
-            for (int i = 0; i < dims; ++i) t[i] = cur[i];
-            t[ax] = cand;
-            const double ms = time_config(dims, f, g, h, L, M, t, dtype, batch, ws, ws_bytes, warmup, reps, st);
-            if (ms < 0) continue;
-            record(t, ms);
-            timed.emplace_back(ms, cand);
-        }
-        if (timed.empty()) return HDC_ERR_CUDA;
-        std::sort(timed.begin(), timed.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
-        hdc_tuple bax = timed[0].second;
-        double bms = timed[0].first;
-        // D below q for the three fastest m
-        for (size_t k = 0; k < timed.size() && k < 3; ++k) {
-            hdc_tuple base = timed[k].second;
-            for (int64_t Dv = 1; Dv < base.q; Dv *= 2) {
-                hdc_tuple t[HDC_MAX_DIMS];
-                for (int i = 0; i < dims; ++i) t[i] = cur[i];
-                t[ax] = base;
-                t[ax].D = Dv;
-                const double ms = time_config(dims, f, g, h, L, M, t, dtype, batch, ws, ws_bytes, warmup, reps, st);
-                if (ms < 0) continue;
-                record(t, ms);
-                if (ms < bms) { bms = ms; bax = t[ax]; }
-            }
-        }
-        cur[ax] = bax;
-        best_ms = bms;
-    }
-    for (int i = 0; i < dims; ++i) {
-        best[i] = cur[i];
-        best[i].ms = best_ms;
-    }
-    if (ntrials) *ntrials = nt;
-    return HDC_OK;
+    return separable_search<hdc_tuple>(
+        dims, c,
+        [&](const hdc_tuple* t) {
+            return time_config(dims, f, g, h, L, M, t, dtype, batch, ws, ws_bytes, warmup, reps, st);
+        },
+        best, trials, cap, ntrials);
 }
 
 HDC_EXPORT int hdc_tune_conv1d(int64_t L, int64_t M, int dtype, int64_t batch, const void* f, const void* g,
@@ -575,63 +595,70 @@ HDC_EXPORT int hdc_tune_unequal(int dims, const int64_t* Lf, const int64_t* Lg, 
     }
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<hdc_unequal_tuple> c[HDC_MAX_DIMS];
-    hdc_unequal_tuple cur[HDC_MAX_DIMS];
     for (int i = 0; i < dims; ++i) {
         c[i] = candidates_uneq(Lf[i], Lg[i], Mv[i], dtype, max_ratio, m_min);
         if (c[i].empty()) return HDC_ERR_UNSUPPORTED_SIZE;
-        cur[i] = c[i][0];
     }
-    int64_t nt = 0;
-    auto record = [&](const hdc_unequal_tuple* t, double ms) {
-        if (trials && nt < cap) {
-            for (int i = 0; i < dims; ++i) {
-                trials[nt * dims + i] = t[i];
-                trials[nt * dims + i].ms = ms;
-            }
-        }
-        ++nt;
-    };
-    double best_ms = -1.0;
-    for (int ax = dims - 1; ax >= 0; --ax) {
-        std::vector<std::pair<double, hdc_unequal_tuple>> timed;
-        for (const auto& cand : c[ax]) {
-            hdc_unequal_tuple t[HDC_MAX_DIMS];
-            for (int i = 0; i < dims; ++i) t[i] = cur[i];
-            t[ax] = cand;
-            const double ms =
-                time_config_uneq(dims, f, g, h, Lf, Lg, Mv, t, dtype, batch, ws, ws_bytes, warmup, reps, st);
-            if (ms < 0) continue;
-            record(t, ms);
-            timed.emplace_back(ms, cand);
-        }
-        if (timed.empty()) return HDC_ERR_CUDA;
-        std::sort(timed.begin(), timed.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
-        hdc_unequal_tuple bax = timed[0].second;
-        double bms = timed[0].first;
-        for (size_t k = 0; k < timed.size() && k < 3; ++k) {
-            const hdc_unequal_tuple base = timed[k].second;
-            for (int64_t Dv = 1; Dv < base.q; Dv *= 2) {
-                hdc_unequal_tuple t[HDC_MAX_DIMS];
-                for (int i = 0; i < dims; ++i) t[i] = cur[i];
-                t[ax] = base;
-                t[ax].D = Dv;
-                const double ms =
-                    time_config_uneq(dims, f, g, h, Lf, Lg, Mv, t, dtype, batch, ws, ws_bytes, warmup, reps, st);
-                if (ms < 0) continue;
-                record(t, ms);
-                if (ms < bms) { bms = ms; bax = t[ax]; }
-            }
-        }
-        cur[ax] = bax;
-        best_ms = bms;
-    }
-    for (int i = 0; i < dims; ++i) {
-        best[i] = cur[i];
-        best[i].ms = best_ms;
-    }
+    rc = separable_search<hdc_unequal_tuple>(
+        dims, c,
+        [&](const hdc_unequal_tuple* t) {
+            return time_config_uneq(dims, f, g, h, Lf, Lg, Mv, t, dtype, batch, ws, ws_bytes, warmup, reps, st);
+        },
+        best, trials, cap, ntrials);
+    if (rc != HDC_OK) return rc;
     db_store_uneq(tuning_db, key, dims, best);
-    if (ntrials) *ntrials = nt;
     return HDC_OK;
+}
+
+HDC_EXPORT int hdc_tune_multi_workspace_size(int dims, int n, int op, const int64_t* L, const int64_t* M,
+                                             int dtype, int64_t batch, double max_ratio, int64_t m_min,
+                                             size_t* bytes)
+{
+    if (!bytes || dims < 1 || dims > HDC_MAX_DIMS || !L || !M) return HDC_ERR_PARAM;
+    std::vector<hdc_tuple> c[HDC_MAX_DIMS];
+    for (int i = 0; i < dims; ++i) {
+        c[i] = candidates(L[i], M[i], dtype, max_ratio, m_min);
+        if (c[i].empty()) return HDC_ERR_UNSUPPORTED_SIZE;
+    }
+    size_t worst = 0;
+    int64_t m[HDC_MAX_DIMS], p[HDC_MAX_DIMS], q[HDC_MAX_DIMS], D[HDC_MAX_DIMS];
+    int64_t idx[HDC_MAX_DIMS] = { 0, 0, 0 };
+    while (true) {
+        for (int i = 0; i < dims; ++i) {
+            const hdc_tuple& t = c[i][idx[i]];
+            m[i] = t.m; p[i] = t.p; q[i] = t.q; D[i] = t.q;
+        }
+        size_t b = 0;
+        if (hdc_workspace_size_multi(dims, n, op, L, M, m, p, q, D, dtype, batch, &b) == HDC_OK)
+            worst = std::max(worst, b);
+        int k = dims - 1;
+        while (k >= 0 && ++idx[k] == (int64_t)c[k].size()) idx[k--] = 0;
+        if (k < 0) break;
+    }
+    *bytes = worst;
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_tune_multi(int dims, int n, int op, const int64_t* L, const int64_t* M, int dtype,
+                              int64_t batch, const void* const* inputs, void* h, void* ws, size_t ws_bytes,
+                              int warmup, int reps, double max_ratio, int64_t m_min, void* stream, hdc_tuple* best,
+                              hdc_tuple* trials, int64_t cap, int64_t* ntrials)
+{
+    if (dims < 1 || dims > HDC_MAX_DIMS || !L || !M || !best || !inputs || !h || reps < 1) return HDC_ERR_PARAM;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<hdc_tuple> c[HDC_MAX_DIMS];
+    const int fold = op == HDC_MULTI_PRODUCT ? n : 2;
+    for (int i = 0; i < dims; ++i) {
+        if (M[i] < fold * (L[i] - 1) + 1) return HDC_ERR_ALIAS;
+        c[i] = candidates(L[i], M[i], dtype, max_ratio, m_min);
+        if (c[i].empty()) return HDC_ERR_UNSUPPORTED_SIZE;
+    }
+    return separable_search<hdc_tuple>(
+        dims, c,
+        [&](const hdc_tuple* t) {
+            return time_config_multi(dims, n, op, inputs, h, L, M, t, dtype, batch, ws, ws_bytes, warmup, reps, st);
+        },
+        best, trials, cap, ntrials);
 }
 
 // ---------------------------------------------------------------- plans

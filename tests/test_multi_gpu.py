@@ -156,3 +156,77 @@ def test_errors(hdc):
     with pytest.raises(hdc.HDCError) as e:
         hdc.convnd_multi(xs * 3, 1, 512)               # nine inputs
     assert e.value.code == hdc.HDC_ERR_PARAM
+
+
+def test_tuner(hdc):
+    xs = [dev(synth.unit_disk(1800 + i, (2, 3000))) for i in range(3)]
+    best, trials = hdc.tune_multi(xs, 1, reps=2)
+    assert trials and best[0]["ms"] <= min(t[0]["ms"] for t in trials) + 1e-9
+    h = hdc.convnd_multi(xs, 1, best[0]["m"], D=best[0]["D"]).cpu().numpy()
+    ref = np.stack([iterated([x.cpu().numpy()[b] for x in xs], "fft") for b in range(2)])
+    assert rel_max_err(h, ref) < TOL64
+
+
+# ------------------------------------------------- sum of pairwise products
+
+def pairwise(xs, method="direct"):
+    fn = oracle.conv_direct if method == "direct" else oracle.conv_fft
+    return sum(fn(np.asarray(xs[i]), np.asarray(xs[i + 1])) for i in range(0, len(xs), 2))
+
+
+def test_dot_grid_small_against_o9(hdc):
+    cnt = 0
+    for n in (2, 4, 8):
+        for L in (1, 6, 23):
+            xs = synth.unit_disk(1900 + 10 * n + L, (n, 2, L))
+            M = 2 * L - 1
+            for m in [k for k in range(1, 2 * M + 2) if good(k)][:: max(1, M // 8)]:
+                q = -(-M // m)
+                for D in sorted({1, q}):
+                    h = run(hdc, xs, 1, m, op="dot", D=D)
+                    for b in range(2):
+                        ref = oracle.conv_multi(xs[:, b, :], m, op="dot")
+                        assert rel_max_err(h[b], ref) < TOL64, (n, L, m, D)
+                    cnt += 1
+    assert cnt > 30
+
+
+def test_dot_routes_nd_and_integers(hdc):
+    xs = synth.unit_disk(2001, (4, 3, 20000))
+    ref = np.stack([pairwise(xs[:, b], "fft") for b in range(3)])
+    for m, D in ((40000, 0), (65536, 0), (1250, 4), (2048, 0)):
+        h = run(hdc, xs, 1, m, op="dot", D=D)
+        assert rel_max_err(h, ref) < TOL64, (m, D)
+    xs = synth.unit_disk(2002, (6, 20, 24))
+    h = run(hdc, xs, 2, [40, 48], op="dot")
+    assert rel_max_err(h, pairwise(xs)) < TOL64
+    xs = synth.unit_disk(2003, (4, 5, 6, 7))
+    h = run(hdc, xs, 3, [9, 12, 14], op="dot")
+    assert rel_max_err(h, pairwise(xs)) < TOL64
+    parts = [synth.small_ints(2100 + i, (2000,)) for i in range(8)]
+    re = np.zeros(2000, dtype=np.int64)
+    im = np.zeros(2000, dtype=np.int64)
+    for i in range(0, 8, 2):
+        a, b = oracle.conv_int_exact(*parts[i], *parts[i + 1])
+        re += a
+        im += b
+    h = run(hdc, [r + 1j * i for r, i in parts], 1, 4000, op="dot")
+    assert np.array_equal(np.rint(h.real).astype(np.int64), re)
+    assert np.array_equal(np.rint(h.imag).astype(np.int64), im)
+    h = run(hdc, [r + 1j * i for r, i in parts], 1, 4000, op="dot", dtype=np.complex64)
+    assert rel_max_err(h, re + 1j * im) < TOL32
+
+
+def test_dot_two_inputs_match_convnd_bitwise_and_errors(hdc):
+    f = synth.unit_disk(2201, (2, 3000))
+    g = synth.unit_disk(2202, (2, 3000))
+    a = run(hdc, [f, g], 1, 6000, op="dot")
+    b = hdc.convnd(dev(f), dev(g), 1, 6000).cpu().numpy()
+    assert np.array_equal(a, b)
+    xs = [dev(synth.unit_disk(2300 + i, (30,))) for i in range(3)]
+    with pytest.raises(hdc.HDCError) as e:
+        hdc.convnd_multi(xs, 1, 64, op="dot")           # odd number of inputs
+    assert e.value.code == hdc.HDC_ERR_PARAM
+    with pytest.raises(hdc.HDCError) as e:
+        hdc.convnd_multi(xs[:2] * 2, 1, 64, op="dot", M=58)
+    assert e.value.code == hdc.HDC_ERR_ALIAS

@@ -1,5 +1,5 @@
 """Pins of the multi-convolution oracle (O9): the n-fold convolution of n
-arrays, first L outputs.
+arrays and the sum of pairwise convolutions, first L outputs.
 
 * iterated numpy convolution (library) and iterated O1 (direct sums);
 * exact integer n-fold convolution (iterated O3);
@@ -86,3 +86,39 @@ def test_o9_aliasing():
         oracle.conv_multi(xs, 4, 3, 6)
     with pytest.raises(RuntimeError):
         oracle.conv_multi(xs, 19, 1, 1)     # 2 L - 1 = 19
+
+
+def pairwise_sum(xs):
+    L = xs.shape[1]
+    return sum(np.convolve(xs[i], xs[i + 1])[:L] for i in range(0, xs.shape[0], 2))
+
+
+@pytest.mark.parametrize("n,L,m", [(2, 9, 6), (4, 10, 4), (4, 10, 19), (6, 7, 5), (8, 33, 16), (4, 1, 1)])
+def test_o9_dot_against_library_and_direct(n, L, m):
+    xs = synth.unit_disk(800 + 10 * n + L, (n, L))
+    h = oracle.conv_multi(xs, m, op="dot")
+    assert rel_max_err(h, pairwise_sum(xs)) < 1e-13
+    direct = sum(oracle.conv_direct(xs[i], xs[i + 1]) for i in range(0, n, 2))
+    assert rel_max_err(h, direct) < 1e-13
+
+
+def test_o9_dot_exact_integers_and_aliasing():
+    n, L = 6, 300
+    parts = [synth.small_ints(950 + i, (L,)) for i in range(n)]
+    re = np.zeros(L, dtype=np.int64)
+    im = np.zeros(L, dtype=np.int64)
+    for i in range(0, n, 2):
+        a, b = oracle.conv_int_exact(*parts[i], *parts[i + 1])
+        re += a
+        im += b
+    xs = np.array([r + 1j * i for r, i in parts])
+    for m in (64, 599, 128):
+        h = oracle.conv_multi(xs, m, op="dot")
+        assert np.array_equal(np.rint(h.real).astype(np.int64), re), m
+        assert np.array_equal(np.rint(h.imag).astype(np.int64), im), m
+    # 2 L - 1 suffices for the pairwise sum, one less does not; odd n is invalid
+    oracle.conv_multi(xs, 599, 1, 1, op="dot")
+    with pytest.raises(RuntimeError):
+        oracle.conv_multi(xs, 598, 1, 1, op="dot")
+    with pytest.raises(RuntimeError):
+        oracle.conv_multi(xs[:5], 599, op="dot")
