@@ -80,7 +80,11 @@ typedef enum hdc_mode {
     HDC_PREDICT_MLP = 2,      /* learned predictor of the parameters                 */
     HDC_EXPLICIT = 3,         /* explicit padding m = nextgood(M), p = q = 1 (3.1)   */
     HDC_TUNE_CACHED_ONLY = 4, /* tuning database only; HDC_ERR_NOT_TUNED if absent   */
-    HDC_PREDICT_MLP_SEARCH = 5 /* time the predictor's 3 best classes per axis        */
+    HDC_PREDICT_MLP_SEARCH = 5, /* time the predictor's 3 best classes per axis       */
+    HDC_TUNE_RANDOM = 6,        /* random search (Section 4.3, A1): a quarter of the  */
+                                /* candidates, cached                                 */
+    HDC_TUNE_PROXY = 7          /* per axis, search the rectangle with the other axes */
+                                /* cut to 32 points (Section 6.3 heuristic), cached   */
 } hdc_mode;
 
 /* One parameter choice of one axis and its measured time. */
@@ -425,6 +429,32 @@ int hdc_tune_multi(int dims, int n, int op, const int64_t* L, const int64_t* M,
                    int reps, double max_ratio, int64_t m_min, void* stream,
                    hdc_tuple* best, hdc_tuple* trials, int64_t cap,
                    int64_t* ntrials);
+
+/* Cheap searches (Section 4.3, A1: random search and reuse of a
+ * rectangle's parameters; Section 6.3: the height-32 rectangle), same
+ * buffers and results as hdc_tune_convnd.
+ * hdc_tune_convnd_random: random search; per axis n_samples candidates
+ * (<= 0: a quarter of them, at least 3) drawn without replacement with a
+ * SplitMix64 stream seeded by `seed`, then the separable search over those.
+ * hdc_tune_convnd_proxy: for each axis, the separable search on the
+ * rectangle in which every other axis longer than Lproxy is cut to Lproxy
+ * points (M = 2 Lproxy - 1), run on prefixes of f, g, h; the axis keeps the
+ * rectangle's choice for itself.  The workspace of hdc_tune_workspace_size
+ * for the full problem suffices (else HDC_ERR_WORKSPACE). *ntrials: timed
+ * configurations in all. */
+int hdc_tune_convnd_random(int dims, const int64_t* L, const int64_t* M,
+                           int dtype, int64_t batch, const void* f,
+                           const void* g, void* h, void* workspace,
+                           size_t ws_bytes, int warmup, int reps,
+                           double max_ratio, int64_t m_min, int64_t n_samples,
+                           uint64_t seed, void* stream, hdc_tuple* best,
+                           hdc_tuple* trials, int64_t cap, int64_t* ntrials);
+int hdc_tune_convnd_proxy(int dims, const int64_t* L, const int64_t* M,
+                          int dtype, int64_t batch, const void* f,
+                          const void* g, void* h, void* workspace,
+                          size_t ws_bytes, int warmup, int reps,
+                          double max_ratio, int64_t m_min, int64_t Lproxy,
+                          void* stream, hdc_tuple* best, int64_t* ntrials);
 
 /* ---------------------------------------------------------------- plans
  * A plan fixes (m, p, q, D) per axis for one (dims, L, M, dtype, batch).

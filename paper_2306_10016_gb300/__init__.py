@@ -29,6 +29,8 @@ HDC_PREDICT_MLP = 2
 HDC_EXPLICIT = 3
 HDC_TUNE_CACHED_ONLY = 4
 HDC_PREDICT_MLP_SEARCH = 5
+HDC_TUNE_RANDOM = 6
+HDC_TUNE_PROXY = 7
 
 HDC_OK = 0
 HDC_ERR_PARAM = -1
@@ -107,6 +109,10 @@ class UTuple(C.Structure):
 _tp = C.POINTER(Tuple)
 _utp = C.POINTER(UTuple)
 _SIGS += [
+    ("hdc_tune_convnd_random", C.c_int, [C.c_int, _i64p, _i64p, C.c_int, _i64, _vp, _vp, _vp, _vp, _sz, C.c_int,
+                                         C.c_int, C.c_double, _i64, _i64, C.c_uint64, _vp, _tp, _tp, _i64, _i64p]),
+    ("hdc_tune_convnd_proxy", C.c_int, [C.c_int, _i64p, _i64p, C.c_int, _i64, _vp, _vp, _vp, _vp, _sz, C.c_int,
+                                        C.c_int, C.c_double, _i64, _i64, _vp, _tp, _i64p]),
     ("hdc_tune_multi_workspace_size", C.c_int, [C.c_int, C.c_int, C.c_int, _i64p, _i64p, C.c_int, _i64, C.c_double,
                                                 _i64, C.POINTER(_sz)]),
     ("hdc_tune_multi", C.c_int, [C.c_int, C.c_int, C.c_int, _i64p, _i64p, C.c_int, _i64, C.POINTER(_vp), _vp, _vp,
@@ -650,6 +656,60 @@ def tune(f, g, dims, M=None, max_ratio=2.0, m_min=16, warmup=1, reps=3, out=None
                                      trials, cap, C.byref(nt)), "tune_convnd")
     tr = [[trials[i * dims + a].as_dict() for a in range(dims)] for i in range(min(nt.value, cap))]
     return [best[a].as_dict() for a in range(dims)], tr
+
+
+def _tune_setup(f, g, dims, M, max_ratio, m_min):
+    torch = _torch()
+    dt = dtype_code(f.dtype)
+    L = [int(x) for x in f.shape[f.dim() - dims:]]
+    batch = 1
+    for x in f.shape[: f.dim() - dims]:
+        batch *= int(x)
+    Mv = _per_axis(M, dims, "M") or [2 * l - 1 for l in L]
+    nb = C.c_size_t()
+    _check(lib().hdc_tune_workspace_size(dims, _arr(L), _arr(Mv), dt, batch, max_ratio, m_min, C.byref(nb)),
+           "tune_workspace_size")
+    ws = torch.empty(max(1, nb.value), dtype=torch.uint8, device=f.device)
+    return dt, L, batch, Mv, ws, nb.value
+
+
+def tune_random(f, g, dims, n_samples=0, seed=230610016, M=None, max_ratio=2.0, m_min=16, warmup=1, reps=3,
+                stream=None):
+    """Random search (Section 4.3, A1): n_samples candidates per axis (0: a
+    quarter, at least 3) drawn with a seeded SplitMix64 stream, then the
+    separable search; returns (best per axis, trials)."""
+    torch = _torch()
+    dt, L, batch, Mv, ws, wsb = _tune_setup(f, g, dims, M, max_ratio, m_min)
+    h = torch.empty_like(f)
+    cap = 4096
+    best = (Tuple * dims)()
+    trials = (Tuple * (cap * dims))()
+    nt = C.c_int64()
+    st = stream if stream is not None else torch.cuda.current_stream(f.device)
+    with torch.cuda.device(f.device):
+        _check(lib().hdc_tune_convnd_random(dims, _arr(L), _arr(Mv), dt, batch, f.data_ptr(), g.data_ptr(),
+                                            h.data_ptr(), ws.data_ptr(), wsb, warmup, reps, max_ratio, m_min,
+                                            int(n_samples), int(seed), st.cuda_stream, best, trials, cap,
+                                            C.byref(nt)), "tune_convnd_random")
+    tr = [[trials[i * dims + a].as_dict() for a in range(dims)] for i in range(min(nt.value, cap))]
+    return [best[a].as_dict() for a in range(dims)], tr
+
+
+def tune_proxy(f, g, dims, Lproxy=32, M=None, max_ratio=2.0, m_min=16, warmup=1, reps=3, stream=None):
+    """Per axis, the separable search on the rectangle with every other axis
+    cut to Lproxy points (Section 6.3 heuristic); returns (best per axis,
+    number of timed configurations)."""
+    torch = _torch()
+    dt, L, batch, Mv, ws, wsb = _tune_setup(f, g, dims, M, max_ratio, m_min)
+    h = torch.empty_like(f)
+    best = (Tuple * dims)()
+    nt = C.c_int64()
+    st = stream if stream is not None else torch.cuda.current_stream(f.device)
+    with torch.cuda.device(f.device):
+        _check(lib().hdc_tune_convnd_proxy(dims, _arr(L), _arr(Mv), dt, batch, f.data_ptr(), g.data_ptr(),
+                                           h.data_ptr(), ws.data_ptr(), wsb, warmup, reps, max_ratio, m_min,
+                                           int(Lproxy), st.cuda_stream, best, C.byref(nt)), "tune_convnd_proxy")
+    return [best[a].as_dict() for a in range(dims)], nt.value
 
 
 def tune_unequal_candidates(Lf: int, Lg: int, M: int = 0, dtype=HDC_C128, max_ratio=1.5, m_min=16):

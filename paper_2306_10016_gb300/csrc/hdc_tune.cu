@@ -661,12 +661,110 @@ HDC_EXPORT int hdc_tune_multi(int dims, int n, int op, const int64_t* L, const i
         best, trials, cap, ntrials);
 }
 
+// --------------------------------------------------- cheap tuners (A1)
+
+namespace {
+
+// SplitMix64 (Steele, Lea and Flood 2014): the seeded stream the random
+// search draws its samples from.
+uint64_t splitmix64_next(uint64_t* state)
+{
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// n distinct entries of c drawn uniformly (partial Fisher-Yates), kept in
+// model-flops order; all of c when n >= |c|.
+std::vector<hdc_tuple> sample_candidates(const std::vector<hdc_tuple>& c, int64_t n, uint64_t* state)
+{
+    if (n >= (int64_t)c.size()) return c;
+    std::vector<size_t> idx(c.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+    for (int64_t k = 0; k < n; ++k) {
+        const size_t j = (size_t)k + (size_t)(splitmix64_next(state) % (uint64_t)(idx.size() - (size_t)k));
+        std::swap(idx[(size_t)k], idx[j]);
+    }
+    std::vector<size_t> pick(idx.begin(), idx.begin() + n);
+    std::sort(pick.begin(), pick.end());
+    std::vector<hdc_tuple> out;
+    for (size_t i : pick) out.push_back(c[i]);
+    return out;
+}
+
+} // namespace
+
+HDC_EXPORT int hdc_tune_convnd_random(int dims, const int64_t* L, const int64_t* M, int dtype, int64_t batch,
+                                      const void* f, const void* g, void* h, void* ws, size_t ws_bytes, int warmup,
+                                      int reps, double max_ratio, int64_t m_min, int64_t n_samples, uint64_t seed,
+                                      void* stream, hdc_tuple* best, hdc_tuple* trials, int64_t cap,
+                                      int64_t* ntrials)
+{
+    if (dims < 1 || dims > HDC_MAX_DIMS || !L || !M || !best || !f || !g || !h || reps < 1) return HDC_ERR_PARAM;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<hdc_tuple> c[HDC_MAX_DIMS];
+    uint64_t state = seed;
+    for (int i = 0; i < dims; ++i) {
+        if (M[i] < 2 * L[i] - 1) return HDC_ERR_ALIAS;
+        const auto all = candidates(L[i], M[i], dtype, max_ratio, m_min);
+        if (all.empty()) return HDC_ERR_UNSUPPORTED_SIZE;
+        const int64_t n = n_samples > 0 ? n_samples : std::max<int64_t>(3, ((int64_t)all.size() + 3) / 4);
+        c[i] = sample_candidates(all, n, &state);
+    }
+    return separable_search<hdc_tuple>(
+        dims, c,
+        [&](const hdc_tuple* t) {
+            return time_config(dims, f, g, h, L, M, t, dtype, batch, ws, ws_bytes, warmup, reps, st);
+        },
+        best, trials, cap, ntrials);
+}
+
+HDC_EXPORT int hdc_tune_convnd_proxy(int dims, const int64_t* L, const int64_t* M, int dtype, int64_t batch,
+                                     const void* f, const void* g, void* h, void* ws, size_t ws_bytes, int warmup,
+                                     int reps, double max_ratio, int64_t m_min, int64_t Lproxy, void* stream,
+                                     hdc_tuple* best, int64_t* ntrials)
+{
+    if (dims < 1 || dims > HDC_MAX_DIMS || !L || !M || !best || !f || !g || !h || reps < 1 || Lproxy < 1)
+        return HDC_ERR_PARAM;
+    int64_t total = 0;
+    for (int ax = 0; ax < dims; ++ax) {
+        if (M[ax] < 2 * L[ax] - 1) return HDC_ERR_ALIAS;
+        // the rectangle: this axis at full length, every other axis cut to
+        // Lproxy (with its least alias-free padding)
+        int64_t Lp[HDC_MAX_DIMS], Mp[HDC_MAX_DIMS];
+        for (int j = 0; j < dims; ++j) {
+            const bool cut = j != ax && L[j] > Lproxy;
+            Lp[j] = cut ? Lproxy : L[j];
+            Mp[j] = cut ? 2 * Lproxy - 1 : M[j];
+        }
+        size_t need = 0;
+        int rc = hdc_tune_workspace_size(dims, Lp, Mp, dtype, batch, max_ratio, m_min, &need);
+        if (rc != HDC_OK) return rc;
+        if (need > ws_bytes) return HDC_ERR_WORKSPACE;
+        hdc_tuple pb[HDC_MAX_DIMS];
+        int64_t nt = 0;
+        // the rectangle's arrays are prefixes of the caller's buffers
+        rc = hdc_tune_convnd(dims, Lp, Mp, dtype, batch, f, g, h, ws, ws_bytes, warmup, reps, max_ratio, m_min,
+                             stream, pb, nullptr, 0, &nt);
+        if (rc != HDC_OK) return rc;
+        best[ax] = pb[ax];
+        total += nt;
+    }
+    if (ntrials) *ntrials = total;
+    return HDC_OK;
+}
+
 // ---------------------------------------------------------------- plans
 
 // Search bounds of plans made with HDC_TUNE_EXHAUSTIVE: candidates within
 // 1.5x of the smallest model flops, m >= 16.
 constexpr double kPlanRatio = 1.5;
 constexpr int64_t kPlanMmin = 16;
+// HDC_TUNE_RANDOM: a quarter of each axis' candidates (at least 3), drawn
+// with this seed; HDC_TUNE_PROXY: the other axes cut to 32 points.
+constexpr uint64_t kPlanSeed = 230610016ULL;
+constexpr int64_t kPlanProxy = 32;
 
 struct hdc_plan {
     int dims;
@@ -842,6 +940,35 @@ HDC_EXPORT int hdc_plan_create(hdc_plan** out, int dims, const int64_t* L, const
             cudaFree(bf); cudaFree(bg); cudaFree(bh); cudaFree(bw);
             if (rc != HDC_OK) return rc;
             db_store(tuning_db, key, dims, pl.t);
+        }
+    } else if (mode == HDC_TUNE_RANDOM || mode == HDC_TUNE_PROXY) {
+        const std::string k2 = key + (mode == HDC_TUNE_RANDOM ? " random" : " proxy");
+        if (!db_lookup(tuning_db, k2, dims, pl.t)) {
+            int64_t tot = batch;
+            for (int i = 0; i < dims; ++i) tot *= L[i];
+            const size_t esz = dtype == HDC_C128 ? 16 : 8;
+            size_t wsb = 0;
+            int rc = hdc_tune_workspace_size(dims, L, M, dtype, batch, kPlanRatio, kPlanMmin, &wsb);
+            if (rc != HDC_OK) return rc;
+            void *bf = nullptr, *bg = nullptr, *bh = nullptr, *bw = nullptr;
+            cudaStream_t st = (cudaStream_t)stream;
+            if (cudaMalloc(&bf, tot * esz) != cudaSuccess || cudaMalloc(&bg, tot * esz) != cudaSuccess ||
+                cudaMalloc(&bh, tot * esz) != cudaSuccess || cudaMalloc(&bw, wsb) != cudaSuccess) {
+                cudaFree(bf); cudaFree(bg); cudaFree(bh); cudaFree(bw);
+                return HDC_ERR_ALLOC;
+            }
+            cudaMemsetAsync(bf, 0, tot * esz, st);
+            cudaMemsetAsync(bg, 0, tot * esz, st);
+            if (mode == HDC_TUNE_RANDOM)
+                rc = hdc_tune_convnd_random(dims, L, M, dtype, batch, bf, bg, bh, bw, wsb, 1, 3, kPlanRatio, kPlanMmin,
+                                            0, kPlanSeed, stream, pl.t, nullptr, 0, nullptr);
+            else
+                rc = hdc_tune_convnd_proxy(dims, L, M, dtype, batch, bf, bg, bh, bw, wsb, 1, 3, kPlanRatio, kPlanMmin,
+                                           kPlanProxy, stream, pl.t, nullptr);
+            cudaStreamSynchronize(st);
+            cudaFree(bf); cudaFree(bg); cudaFree(bh); cudaFree(bw);
+            if (rc != HDC_OK) return rc;
+            db_store(tuning_db, k2, dims, pl.t);
         }
     } else if (mode == HDC_PREDICT_MLP || mode == HDC_PREDICT_MLP_SEARCH) {
         int rc = predict_mlp(dims, L, M, dtype, batch, tuning_db, (cudaStream_t)stream, pl.t,

@@ -256,7 +256,7 @@ EVAL_PROBLEMS = [(768, 768), (1024, 1024), (2048, 512), (2048, 1024), (3072, 153
                  (32, 32, 32), (64, 64, 64), (128, 128, 128), (256, 256, 256)]
 
 
-KEYS = ("mlp", "mlp_top3", "explicit", "q2")
+KEYS = ("mlp", "mlp_top3", "random25", "proxy32", "explicit", "q2")
 
 
 def evaluate(weights, problems=None, dtype=None, reps=5, log=None):
@@ -273,21 +273,34 @@ def evaluate(weights, problems=None, dtype=None, reps=5, log=None):
         f = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 90 + k, shape)).to("cuda", tdt)
         g = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 9090 + k, shape)).to("cuda", tdt)
         t0 = time.perf_counter()
-        best, _ = hdc.tune(f, g, dims, max_ratio=1.5, reps=3)
+        best, search_trials = hdc.tune(f, g, dims, max_ratio=1.5, reps=3)
         t_search = time.perf_counter() - t0
+        # the paper's cheap searches (Section 4.3 random search, Section 6.3
+        # height-32 rectangle) as baselines for the predictor
+        t0 = time.perf_counter()
+        rbest, rtrials = hdc.tune_random(f, g, dims, max_ratio=1.5, reps=3)
+        t_random = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        xbest, xtimed = hdc.tune_proxy(f, g, dims, 32, max_ratio=1.5, reps=3)
+        t_proxy = time.perf_counter() - t0
         t0 = time.perf_counter()
         pred = hdc.Plan(list(shape), dtype=dtype, mode=hdc.HDC_PREDICT_MLP, tuning_db=str(weights)).params
         t_pred = time.perf_counter() - t0
         t0 = time.perf_counter()
         guided, n_timed = _guided(net, f, g, shape, dtype, 3, reps)
         t_guided = time.perf_counter() - t0
-        cand = {"search": [dict(m=b["m"], p=b["p"], q=b["q"], D=b["D"]) for b in best], "mlp": pred,
-                "mlp_top3": guided, "explicit": _rule_params(shape, 1, dtype), "q2": _rule_params(shape, 2, dtype)}
+        def prm(bs):
+            return [dict(m=b["m"], p=b["p"], q=b["q"], D=b["D"]) for b in bs]
+
+        cand = {"search": prm(best), "mlp": pred, "mlp_top3": guided, "random25": prm(rbest), "proxy32": prm(xbest),
+                "explicit": _rule_params(shape, 1, dtype), "q2": _rule_params(shape, 2, dtype)}
         t = {k2: _time_params(f, g, dims, v, reps) for k2, v in cand.items()}
         row = {"shape": list(shape), "ms": {k2: round(v, 4) for k2, v in t.items()},
                "regret": {k2: round(t[k2] / t["search"] - 1.0, 4) for k2 in KEYS},
-               "params": cand, "search_s": round(t_search, 2), "predict_s": round(t_pred, 4),
-               "top3_s": round(t_guided, 2), "top3_timed": n_timed}
+               "params": cand, "search_s": round(t_search, 2), "search_timed": len(search_trials),
+               "predict_s": round(t_pred, 4), "top3_s": round(t_guided, 2), "top3_timed": n_timed,
+               "random_s": round(t_random, 2), "random_timed": len(rtrials), "proxy_s": round(t_proxy, 2),
+               "proxy_timed": int(xtimed)}
         rows.append(row)
         if log:
             log(f"eval {shape}: {row['ms']} regret {row['regret']}")

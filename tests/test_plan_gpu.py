@@ -106,3 +106,46 @@ def test_launch_stats(hdc):
 def test_fma_probe(hdc):
     assert hdc.probe_fma_peak(hdc.HDC_C128, iters=1 << 12, reps=2) > 0.1
     assert hdc.probe_fma_peak(hdc.HDC_C64, iters=1 << 12, reps=2) > 1.0
+
+
+def test_cheap_tuners_random_and_proxy(hdc):
+    """Random search and the height-32 rectangle return valid tuples whose
+    convolution matches the oracle; random search times fewer
+    configurations than the grid search; plan modes cache their choice."""
+    import numpy as np
+    import oracle
+    from paper_2306_10016_gb300 import synth
+    from conftest import rel_max_err
+    shape = (96, 200)
+    f = torch.from_numpy(synth.unit_disk(3101, shape)).cuda()
+    g = torch.from_numpy(synth.unit_disk(3102, shape)).cuda()
+    full, ftr = hdc.tune(f, g, 2, max_ratio=1.5, reps=2)
+    rb, rtr = hdc.tune_random(f, g, 2, max_ratio=1.5, reps=2)
+    assert 0 < len(rtr) < len(ftr)
+    xb, xn = hdc.tune_proxy(f, g, 2, 32, max_ratio=1.5, reps=2)
+    assert xn > 0
+    ref = oracle.conv_fft(f.cpu().numpy(), g.cpu().numpy())
+    for b in (rb, xb):
+        h = hdc.convnd(f, g, 2, [t["m"] for t in b], D=[t["D"] for t in b]).cpu().numpy()
+        assert rel_max_err(h, ref) < 1e-12
+    again = hdc.tune_random(f, g, 2, max_ratio=1.5, reps=2)[0]
+    assert [t["m"] for t in again] and len(again) == 2
+
+
+def test_plan_modes_random_and_proxy(hdc, tmp_path):
+    from paper_2306_10016_gb300 import synth
+    import oracle
+    from conftest import rel_max_err
+    shape = [64, 150]
+    f = torch.from_numpy(synth.unit_disk(3201, shape)).cuda()
+    g = torch.from_numpy(synth.unit_disk(3202, shape)).cuda()
+    ref = oracle.conv_fft(f.cpu().numpy(), g.cpu().numpy())
+    db = str(tmp_path / "db.txt")
+    for mode in (hdc.HDC_TUNE_RANDOM, hdc.HDC_TUNE_PROXY):
+        pl = hdc.Plan(shape, mode=mode, tuning_db=db)
+        h = pl.execute(f, g).cpu().numpy()
+        assert rel_max_err(h, ref) < 1e-12
+        again = hdc.Plan(shape, mode=mode, tuning_db=db)
+        assert again.params == pl.params
+    lines = open(db).read().splitlines()
+    assert sum(" random |" in x for x in lines) == 1 and sum(" proxy |" in x for x in lines) == 1
