@@ -100,6 +100,28 @@ std::vector<hdc_tuple> candidates(int64_t L, int64_t M, int dtype, double max_ra
     return kept;
 }
 
+// Candidates of axis i of a dims-axis problem: an axis with inner axes runs
+// its transform in one column tile, so m above hdc_max_outer_fft_size is
+// dropped there (it would be rejected with HDC_ERR_UNSUPPORTED_SIZE).
+int64_t transform_size(const hdc_tuple& t) { return t.m; }
+int64_t transform_size(const hdc_unequal_tuple& t) { return t.m * t.lam; }
+
+template <class Tup> std::vector<Tup> drop_outer_oversize(std::vector<Tup> c, int i, int dims, int dtype)
+{
+    if (i >= dims - 1) return c;
+    const int64_t lim = hdc_max_outer_fft_size(dtype);
+    std::vector<Tup> out;
+    for (const auto& t : c)
+        if (transform_size(t) <= lim) out.push_back(t);
+    return out;
+}
+
+std::vector<hdc_tuple> axis_candidates(const int64_t* L, const int64_t* M, int i, int dims, int dtype,
+                                       double max_ratio, int64_t m_min)
+{
+    return drop_outer_oversize(candidates(L[i], M[i], dtype, max_ratio, m_min), i, dims, dtype);
+}
+
 std::string device_key()
 {
     int dev = 0;
@@ -480,7 +502,7 @@ HDC_EXPORT int hdc_tune_workspace_size(int dims, const int64_t* L, const int64_t
     // (with every D) needs while the other axes take their worst candidate
     std::vector<hdc_tuple> c[HDC_MAX_DIMS];
     for (int i = 0; i < dims; ++i) {
-        c[i] = candidates(L[i], M[i], dtype, max_ratio, m_min);
+        c[i] = axis_candidates(L, M, i, dims, dtype, max_ratio, m_min);
         if (c[i].empty()) return HDC_ERR_UNSUPPORTED_SIZE;
     }
     size_t worst = 0;
@@ -512,7 +534,7 @@ HDC_EXPORT int hdc_tune_convnd(int dims, const int64_t* L, const int64_t* M, int
     std::vector<hdc_tuple> c[HDC_MAX_DIMS];
     for (int i = 0; i < dims; ++i) {
         if (M[i] < 2 * L[i] - 1) return HDC_ERR_ALIAS;
-        c[i] = candidates(L[i], M[i], dtype, max_ratio, m_min);
+        c[i] = axis_candidates(L, M, i, dims, dtype, max_ratio, m_min);
         if (c[i].empty()) return HDC_ERR_UNSUPPORTED_SIZE;
     }
     return separable_search<hdc_tuple>(
@@ -556,7 +578,7 @@ HDC_EXPORT int hdc_tune_unequal_workspace_size(int dims, const int64_t* Lf, cons
     if (rc != HDC_OK) return rc;
     std::vector<hdc_unequal_tuple> c[HDC_MAX_DIMS];
     for (int i = 0; i < dims; ++i) {
-        c[i] = candidates_uneq(Lf[i], Lg[i], Mv[i], dtype, max_ratio, m_min);
+        c[i] = drop_outer_oversize(candidates_uneq(Lf[i], Lg[i], Mv[i], dtype, max_ratio, m_min), i, dims, dtype);
         if (c[i].empty()) return HDC_ERR_UNSUPPORTED_SIZE;
     }
     size_t worst = 0;
@@ -596,7 +618,7 @@ HDC_EXPORT int hdc_tune_unequal(int dims, const int64_t* Lf, const int64_t* Lg, 
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<hdc_unequal_tuple> c[HDC_MAX_DIMS];
     for (int i = 0; i < dims; ++i) {
-        c[i] = candidates_uneq(Lf[i], Lg[i], Mv[i], dtype, max_ratio, m_min);
+        c[i] = drop_outer_oversize(candidates_uneq(Lf[i], Lg[i], Mv[i], dtype, max_ratio, m_min), i, dims, dtype);
         if (c[i].empty()) return HDC_ERR_UNSUPPORTED_SIZE;
     }
     rc = separable_search<hdc_unequal_tuple>(
@@ -617,7 +639,7 @@ HDC_EXPORT int hdc_tune_multi_workspace_size(int dims, int n, int op, const int6
     if (!bytes || dims < 1 || dims > HDC_MAX_DIMS || !L || !M) return HDC_ERR_PARAM;
     std::vector<hdc_tuple> c[HDC_MAX_DIMS];
     for (int i = 0; i < dims; ++i) {
-        c[i] = candidates(L[i], M[i], dtype, max_ratio, m_min);
+        c[i] = axis_candidates(L, M, i, dims, dtype, max_ratio, m_min);
         if (c[i].empty()) return HDC_ERR_UNSUPPORTED_SIZE;
     }
     size_t worst = 0;
@@ -650,7 +672,7 @@ HDC_EXPORT int hdc_tune_multi(int dims, int n, int op, const int64_t* L, const i
     const int fold = op == HDC_MULTI_PRODUCT ? n : 2;
     for (int i = 0; i < dims; ++i) {
         if (M[i] < fold * (L[i] - 1) + 1) return HDC_ERR_ALIAS;
-        c[i] = candidates(L[i], M[i], dtype, max_ratio, m_min);
+        c[i] = axis_candidates(L, M, i, dims, dtype, max_ratio, m_min);
         if (c[i].empty()) return HDC_ERR_UNSUPPORTED_SIZE;
     }
     return separable_search<hdc_tuple>(
@@ -707,7 +729,7 @@ HDC_EXPORT int hdc_tune_convnd_random(int dims, const int64_t* L, const int64_t*
     uint64_t state = seed;
     for (int i = 0; i < dims; ++i) {
         if (M[i] < 2 * L[i] - 1) return HDC_ERR_ALIAS;
-        const auto all = candidates(L[i], M[i], dtype, max_ratio, m_min);
+        const auto all = axis_candidates(L, M, i, dims, dtype, max_ratio, m_min);
         if (all.empty()) return HDC_ERR_UNSUPPORTED_SIZE;
         const int64_t n = n_samples > 0 ? n_samples : std::max<int64_t>(3, ((int64_t)all.size() + 3) / 4);
         c[i] = sample_candidates(all, n, &state);

@@ -149,3 +149,17 @@ def test_plan_modes_random_and_proxy(hdc, tmp_path):
         assert again.params == pl.params
     lines = open(db).read().splitlines()
     assert sum(" random |" in x for x in lines) == 1 and sum(" proxy |" in x for x in lines) == 1
+
+
+def test_cheap_tuners_respect_the_outer_axis_limit(hdc):
+    """Outer-axis candidates above hdc_max_outer_fft_size are never drawn
+    (a random start there used to fail every timing of the inner axis)."""
+    from paper_2306_10016_gb300 import synth
+    lim = hdc.max_outer_fft_size(hdc.HDC_C128)
+    f = torch.from_numpy(synth.unit_disk(3301, (2048, 40))).cuda()
+    g = torch.from_numpy(synth.unit_disk(3302, (2048, 40))).cuda()
+    for seed in (1, 2, 3, 4):
+        best, trials = hdc.tune_random(f, g, 2, seed=seed, max_ratio=1.5, reps=1)
+        assert best[0]["m"] <= lim and all(t[0]["m"] <= lim for t in trials)
+    best, _ = hdc.tune(f, g, 2, max_ratio=1.5, reps=1)
+    assert best[0]["m"] <= lim
