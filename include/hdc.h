@@ -80,7 +80,8 @@ typedef enum hdc_mode {
     HDC_PREDICT_MLP = 2,      /* learned predictor of the parameters                 */
     HDC_EXPLICIT = 3,         /* explicit padding m = nextgood(M), p = q = 1 (3.1)   */
     HDC_TUNE_CACHED_ONLY = 4, /* tuning database only; HDC_ERR_NOT_TUNED if absent   */
-    HDC_PREDICT_MLP_SEARCH = 5, /* time the predictor's 3 best classes per axis       */
+    HDC_PREDICT_MLP_SEARCH = 5, /* time the predictor's 3 best classes per axis and  */
+                                /* the q-neighbours of its best two                   */
     HDC_TUNE_RANDOM = 6,        /* random search (Section 4.3, A1): a quarter of the  */
                                 /* candidates, cached                                 */
     HDC_TUNE_PROXY = 7          /* per axis, search the rectangle with the other axes */
@@ -466,9 +467,11 @@ int hdc_tune_convnd_proxy(int dims, const int64_t* L, const int64_t* M,
  * HDC_PREDICT_MLP reads the network checkpoint at `tuning_db` (written by
  * hdc_mlp_save with HDC_MLP_FEATURES inputs, HDC_MLP_HIDDEN hidden units and
  * hdc_mlp_num_q_classes() + 2 outputs) and runs its inference kernels;
- * HDC_PREDICT_MLP_SEARCH then times the network's three most likely classes
- * of every axis (one axis at a time, last first, the others held) on
- * scratch buffers it allocates and frees, and keeps the fastest. */
+ * HDC_PREDICT_MLP_SEARCH then times, for every axis, the network's three
+ * most likely valid classes and the valid neighbouring q classes (one down,
+ * one up) of its best two, at most six distinct m (one axis at a time, last
+ * first, the others held), on scratch buffers it allocates and frees, and
+ * keeps the fastest. */
 int hdc_plan_create(hdc_plan** plan, int dims, const int64_t* L,
                     const int64_t* M, const int64_t* m, const int64_t* D,
                     int dtype, int64_t batch, int mode, const char* tuning_db,
@@ -478,6 +481,9 @@ int hdc_plan_params(const hdc_plan* plan, int64_t* m, int64_t* p, int64_t* q,
                     int64_t* D);
 /* Device workspace bytes hdc_plan_execute needs (in-place included). */
 size_t hdc_plan_workspace(const hdc_plan* plan);
+/* Configurations timed on the device while the plan was made (0 for the
+ * fixed and explicit modes, a database hit or the top-class prediction). */
+int64_t hdc_plan_timed(const hdc_plan* plan);
 int hdc_plan_execute(const hdc_plan* plan, const void* f, const void* g,
                      void* h, void* workspace, size_t ws_bytes, void* stream);
 int hdc_plan_destroy(hdc_plan* plan);
@@ -578,6 +584,13 @@ int hdc_mlp_axis_features(int dims, const int64_t* L, const int64_t* M,
  * whose tuple is valid with m <= max_m (0: no bound), m = nextgood(ceil(M /
  * q)), D from the D head.  rank > 0 skips the `rank` most likely valid
  * classes (the k-th best guess, for searches over the top classes). */
+/* Parameters of one axis for the q class with index k
+ * (hdc_mlp_q_class(k)): m = nextgood(ceil(M / q_k)), D = 1 if one else q;
+ * HDC_ERR_UNSUPPORTED_SIZE when m > max_m (max_m > 0) or the tuple is not
+ * valid. */
+int hdc_mlp_decode_class(int k, int one, int64_t L, int64_t M, int dtype,
+                         int64_t max_m, int64_t* m, int64_t* p, int64_t* q,
+                         int64_t* D);
 int hdc_mlp_decode_axis(const float* logits, int n_q, int64_t L, int64_t M,
                         int dtype, int64_t max_m, int rank, int64_t* m,
                         int64_t* p, int64_t* q, int64_t* D);

@@ -179,6 +179,8 @@ _SIGS += [
     ("hdc_mlp_q_class", _i64, [C.c_int]),
     ("hdc_mlp_q_to_class", C.c_int, [_i64]),
     ("hdc_mlp_axis_features", C.c_int, [C.c_int, _i64p, _i64p, C.c_int, _i64, C.POINTER(C.c_float)]),
+    ("hdc_plan_timed", _i64, [_vp]),
+    ("hdc_mlp_decode_class", C.c_int, [C.c_int, C.c_int, _i64, _i64, C.c_int, _i64, _i64p, _i64p, _i64p, _i64p]),
     ("hdc_mlp_decode_axis", C.c_int, [C.POINTER(C.c_float), C.c_int, _i64, _i64, C.c_int, _i64, C.c_int, _i64p,
                                       _i64p, _i64p, _i64p]),
     ("hdc_convnd_residues", C.c_int, [C.c_int, _vp, _vp, _vp, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, _i64, _i64,
@@ -820,6 +822,11 @@ class Plan:
     @property
     def workspace_bytes(self) -> int:
         return int(lib().hdc_plan_workspace(self._h))
+
+    @property
+    def timed(self) -> int:
+        """Configurations timed while the plan was made."""
+        return int(lib().hdc_plan_timed(self._h))
 
     def execute(self, f, g, out=None, workspace=None, stream=None):
         torch = _torch()

@@ -417,6 +417,26 @@ HDC_EXPORT int hdc_mlp_axis_features(int dims, const int64_t* L, const int64_t* 
     return HDC_OK;
 }
 
+// Parameters of one axis for q class k (m = nextgood(ceil(M / q_k)), D = 1
+// if one, else q), or an error if that tuple is not valid (m above max_m
+// when max_m > 0, or rejected by hdc_validate_axis).
+HDC_EXPORT int hdc_mlp_decode_class(int k, int one, int64_t L, int64_t M, int dtype, int64_t max_m, int64_t* m,
+                                    int64_t* p, int64_t* q, int64_t* D)
+{
+    if (k < 0 || k >= kNQ || !m || !p || !q || !D) return HDC_ERR_PARAM;
+    const int64_t qc = kQClasses[k];
+    const int64_t mm = hdc_next_good_size((M + qc - 1) / qc);
+    if (mm < 1 || (max_m > 0 && mm > max_m)) return HDC_ERR_UNSUPPORTED_SIZE;
+    int64_t pp = 0, qq = 0, DD = 0;
+    const int rc = hdc_validate_axis(L, M, mm, 0, 0, one ? 1 : 0, dtype, &pp, &qq, &DD);
+    if (rc != HDC_OK) return rc;
+    *m = mm;
+    *p = pp;
+    *q = qq;
+    *D = DD;
+    return HDC_OK;
+}
+
 // Parameters of one axis from its n_q + 2 logits.
 HDC_EXPORT int hdc_mlp_decode_axis(const float* logits, int n_q, int64_t L, int64_t M, int dtype, int64_t max_m,
                                    int rank, int64_t* m, int64_t* p, int64_t* q, int64_t* D)
@@ -431,11 +451,8 @@ HDC_EXPORT int hdc_mlp_decode_axis(const float* logits, int n_q, int64_t L, int6
     const bool one = logits[kNQ + 1] > logits[kNQ];
     int seen = 0;
     for (int k : order) {
-        const int64_t qc = kQClasses[k];
-        const int64_t mm = hdc_next_good_size((M + qc - 1) / qc);
-        if (mm < 1 || (max_m > 0 && mm > max_m)) continue;
-        int64_t pp = 0, qq = 0, DD = 0;
-        if (hdc_validate_axis(L, M, mm, 0, 0, one ? 1 : 0, dtype, &pp, &qq, &DD) != HDC_OK) continue;
+        int64_t mm = 0, pp = 0, qq = 0, DD = 0;
+        if (hdc_mlp_decode_class(k, one, L, M, dtype, max_m, &mm, &pp, &qq, &DD) != HDC_OK) continue;
         if (seen++ < rank) continue;
         *m = mm;
         *p = pp;

@@ -795,6 +795,7 @@ struct hdc_plan {
     int64_t L[HDC_MAX_DIMS], M[HDC_MAX_DIMS];
     hdc_tuple t[HDC_MAX_DIMS];
     size_t ws;
+    int64_t timed; // configurations timed while the plan was made
 };
 
 // Logits of the learned predictor for every axis: features, one forward
@@ -849,8 +850,47 @@ static int mlp_axis_choice(const std::vector<float>& logits, int dims, int i, co
 // (search) the fastest of its `topk` most likely classes per axis, timed
 // one axis at a time with the others held (last axis first) on scratch
 // buffers allocated here.
+// Candidates of axis i for the guided search: the valid classes in
+// decreasing score, the first topk of them, then the valid q-neighbours (one
+// class down and one up) of the first two, at most 2 topk, distinct m.  The
+// network locates the region; the neighbours cover a best q that sits
+// between its top classes, as on axes longer than any it was trained on.
+static std::vector<hdc_tuple> guided_candidates(const std::vector<float>& logits, int dims, int i, const int64_t* L,
+                                                const int64_t* M, int dtype, int topk)
+{
+    const int nq = hdc_mlp_num_q_classes();
+    const float* lg = logits.data() + (size_t)i * (nq + 2);
+    const int one = lg[nq + 1] > lg[nq] ? 1 : 0;
+    const int64_t max_m = i < dims - 1 ? hdc_max_outer_fft_size(dtype) : 0;
+    std::vector<int> order(nq);
+    for (int k = 0; k < nq; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lg[a] > lg[b]; });
+    std::vector<hdc_tuple> out;
+    std::vector<int> top;
+    auto add = [&](int k) {
+        if (k < 0 || k >= nq || (int)out.size() >= 2 * topk) return false;
+        hdc_tuple c;
+        if (hdc_mlp_decode_class(k, one, L[i], M[i], dtype, max_m, &c.m, &c.p, &c.q, &c.D) != HDC_OK) return false;
+        for (const auto& o : out)
+            if (o.m == c.m) return false;
+        c.model_flops = model_flops_axis(L[i], c.m, c.q);
+        c.ms = -1.0;
+        out.push_back(c);
+        return true;
+    };
+    for (int k : order) {
+        if ((int)top.size() >= topk) break;
+        if (add(k)) top.push_back(k);
+    }
+    for (size_t j = 0; j < top.size() && j < 2; ++j) {
+        add(top[j] - 1);
+        add(top[j] + 1);
+    }
+    return out;
+}
+
 static int predict_mlp(int dims, const int64_t* L, const int64_t* M, int dtype, int64_t batch, const char* path,
-                       cudaStream_t st, hdc_tuple* t, int topk)
+                       cudaStream_t st, hdc_tuple* t, int topk, int64_t* timed)
 {
     std::vector<float> logits;
     int rc = mlp_logits(dims, L, M, dtype, batch, path, st, logits);
@@ -863,24 +903,25 @@ static int predict_mlp(int dims, const int64_t* L, const int64_t* M, int dtype, 
     int64_t tot = batch;
     for (int i = 0; i < dims; ++i) tot *= L[i];
     const size_t esz = dtype == HDC_C128 ? 16 : 8;
-    // the largest workspace of the candidates
-    size_t wsb = 0;
     std::vector<hdc_tuple> cand[HDC_MAX_DIMS];
-    for (int i = 0; i < dims; ++i)
-        for (int r = 0; r < topk; ++r) {
-            hdc_tuple c;
-            if (mlp_axis_choice(logits, dims, i, L, M, dtype, r, &c) == HDC_OK) cand[i].push_back(c);
+    for (int i = 0; i < dims; ++i) cand[i] = guided_candidates(logits, dims, i, L, M, dtype, topk);
+    // the largest workspace of any combination the search can time
+    size_t wsb = 0;
+    int64_t idx[HDC_MAX_DIMS] = { 0, 0, 0 };
+    while (true) {
+        int64_t mm[HDC_MAX_DIMS], DD[HDC_MAX_DIMS];
+        for (int j = 0; j < dims; ++j) {
+            const hdc_tuple& c = cand[j].empty() ? t[j] : cand[j][idx[j]];
+            mm[j] = c.m;
+            DD[j] = c.D;
         }
-    for (int i = 0; i < dims; ++i)
-        for (const auto& c : cand[i]) {
-            int64_t mm[HDC_MAX_DIMS], DD[HDC_MAX_DIMS];
-            for (int j = 0; j < dims; ++j) { mm[j] = t[j].m; DD[j] = t[j].D; }
-            mm[i] = c.m;
-            DD[i] = c.D;
-            size_t b = 0;
-            if (hdc_workspace_size(dims, L, M, mm, nullptr, nullptr, DD, dtype, batch, 0, &b) == HDC_OK)
-                wsb = std::max(wsb, b);
-        }
+        size_t b = 0;
+        if (hdc_workspace_size(dims, L, M, mm, nullptr, nullptr, DD, dtype, batch, 0, &b) == HDC_OK)
+            wsb = std::max(wsb, b);
+        int k = dims - 1;
+        while (k >= 0 && ++idx[k] >= (int64_t)std::max<size_t>(1, cand[k].size())) idx[k--] = 0;
+        if (k < 0) break;
+    }
     void *bf = nullptr, *bg = nullptr, *bh = nullptr, *bw = nullptr;
     if (cudaMalloc(&bf, tot * esz) != cudaSuccess || cudaMalloc(&bg, tot * esz) != cudaSuccess ||
         cudaMalloc(&bh, tot * esz) != cudaSuccess || cudaMalloc(&bw, wsb) != cudaSuccess) {
@@ -897,6 +938,7 @@ static int predict_mlp(int dims, const int64_t* L, const int64_t* M, int dtype, 
             for (int j = 0; j < dims; ++j) trial[j] = t[j];
             trial[i] = c;
             const double ms = time_config(dims, bf, bg, bh, L, M, trial, dtype, batch, bw, wsb, 1, 3, st);
+            if (timed) ++*timed;
             if (ms >= 0 && (best < 0 || ms < best)) { best = ms; pick = c; }
         }
         t[i] = pick;
@@ -957,7 +999,7 @@ HDC_EXPORT int hdc_plan_create(hdc_plan** out, int dims, const int64_t* L, const
             cudaMemsetAsync(bf, 0, tot * esz, st);
             cudaMemsetAsync(bg, 0, tot * esz, st);
             rc = hdc_tune_convnd(dims, L, M, dtype, batch, bf, bg, bh, bw, wsb, 1, 3, kPlanRatio, kPlanMmin, stream, pl.t, nullptr,
-                                 0, nullptr);
+                                 0, &pl.timed);
             cudaStreamSynchronize(st);
             cudaFree(bf); cudaFree(bg); cudaFree(bh); cudaFree(bw);
             if (rc != HDC_OK) return rc;
@@ -983,10 +1025,10 @@ HDC_EXPORT int hdc_plan_create(hdc_plan** out, int dims, const int64_t* L, const
             cudaMemsetAsync(bg, 0, tot * esz, st);
             if (mode == HDC_TUNE_RANDOM)
                 rc = hdc_tune_convnd_random(dims, L, M, dtype, batch, bf, bg, bh, bw, wsb, 1, 3, kPlanRatio, kPlanMmin,
-                                            0, kPlanSeed, stream, pl.t, nullptr, 0, nullptr);
+                                            0, kPlanSeed, stream, pl.t, nullptr, 0, &pl.timed);
             else
                 rc = hdc_tune_convnd_proxy(dims, L, M, dtype, batch, bf, bg, bh, bw, wsb, 1, 3, kPlanRatio, kPlanMmin,
-                                           kPlanProxy, stream, pl.t, nullptr);
+                                           kPlanProxy, stream, pl.t, &pl.timed);
             cudaStreamSynchronize(st);
             cudaFree(bf); cudaFree(bg); cudaFree(bh); cudaFree(bw);
             if (rc != HDC_OK) return rc;
@@ -994,7 +1036,7 @@ HDC_EXPORT int hdc_plan_create(hdc_plan** out, int dims, const int64_t* L, const
         }
     } else if (mode == HDC_PREDICT_MLP || mode == HDC_PREDICT_MLP_SEARCH) {
         int rc = predict_mlp(dims, L, M, dtype, batch, tuning_db, (cudaStream_t)stream, pl.t,
-                             mode == HDC_PREDICT_MLP_SEARCH ? 3 : 1);
+                             mode == HDC_PREDICT_MLP_SEARCH ? 3 : 1, &pl.timed);
         if (rc != HDC_OK) return rc;
     } else {
         return HDC_ERR_PARAM;
@@ -1022,6 +1064,7 @@ HDC_EXPORT int hdc_plan_params(const hdc_plan* pl, int64_t* m, int64_t* p, int64
 }
 
 HDC_EXPORT size_t hdc_plan_workspace(const hdc_plan* pl) { return pl ? pl->ws : 0; }
+HDC_EXPORT int64_t hdc_plan_timed(const hdc_plan* pl) { return pl ? pl->timed : -1; }
 
 HDC_EXPORT int hdc_plan_execute(const hdc_plan* pl, const void* f, const void* g, void* h, void* ws,
                                 size_t ws_bytes, void* stream)

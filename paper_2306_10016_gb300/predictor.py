@@ -217,41 +217,6 @@ def _rule_params(L, q, dtype=None):
     return out
 
 
-def _guided(net, f, g, shape, dtype, k=3, reps=5):
-    """The predictor's k best classes per axis, each timed with the other
-    axes at their top class (Section 4.2's separable search over k
-    candidates instead of all): the fastest per axis."""
-    import torch
-
-    import paper_2306_10016_gb300 as hdc
-    feats = hdc.mlp_axis_features(list(shape), None, dtype, 1)
-    logits = net.forward(torch.from_numpy(feats).cuda()).cpu().numpy()
-    dims = len(shape)
-    cands = []
-    for a, L in enumerate(shape):
-        mx = hdc.max_outer_fft_size(dtype) if a < dims - 1 else 0
-        ca = []
-        for r in range(k):
-            try:
-                ca.append(hdc.mlp_decode_axis(logits[a], L, 2 * L - 1, dtype, max_m=mx, rank=r))
-            except hdc.HDCError:
-                break
-        cands.append(ca)
-    cur = [c[0] for c in cands]
-    timed = 0
-    for a in range(dims - 1, -1, -1):
-        best_t, best_c = None, cur[a]
-        for c in cands[a]:
-            trial = list(cur)
-            trial[a] = c
-            t = _time_params(f, g, dims, trial, reps)
-            timed += 1
-            if best_t is None or t < best_t:
-                best_t, best_c = t, c
-        cur[a] = best_c
-    return cur, timed
-
-
 EVAL_PROBLEMS = [(768, 768), (1024, 1024), (2048, 512), (2048, 1024), (3072, 1536), (4096, 2048),
                  (32, 32, 32), (64, 64, 64), (128, 128, 128), (256, 256, 256)]
 
@@ -264,8 +229,6 @@ def evaluate(weights, problems=None, dtype=None, reps=5, log=None):
 
     import paper_2306_10016_gb300 as hdc
     dtype = hdc.HDC_C128 if dtype is None else dtype
-    net = hdc.MLP()
-    net.load(weights)
     tdt = torch.complex128 if dtype == hdc.HDC_C128 else torch.complex64
     rows = []
     for k, shape in enumerate(problems or EVAL_PROBLEMS):
@@ -287,7 +250,8 @@ def evaluate(weights, problems=None, dtype=None, reps=5, log=None):
         pred = hdc.Plan(list(shape), dtype=dtype, mode=hdc.HDC_PREDICT_MLP, tuning_db=str(weights)).params
         t_pred = time.perf_counter() - t0
         t0 = time.perf_counter()
-        guided, n_timed = _guided(net, f, g, shape, dtype, 3, reps)
+        gplan = hdc.Plan(list(shape), dtype=dtype, mode=hdc.HDC_PREDICT_MLP_SEARCH, tuning_db=str(weights))
+        guided, n_timed = gplan.params, gplan.timed
         t_guided = time.perf_counter() - t0
         def prm(bs):
             return [dict(m=b["m"], p=b["p"], q=b["q"], D=b["D"]) for b in bs]

@@ -148,3 +148,26 @@ def test_plan_predict_mlp_search_packaged(hdc):
     h = pl.execute(torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda())
     torch.cuda.synchronize()
     assert rel_max_err(h.cpu().numpy(), oracle.conv_fft(f, g)) < 1e-12
+
+
+def test_guided_search_candidates_and_decode_class(hdc):
+    """The packaged guided search times at most six candidates per axis, and
+    decoding a class index agrees with decoding the top-ranked logits."""
+    import numpy as np
+    pl = hdc.Plan([1024, 384], mode=hdc.HDC_PREDICT_MLP_SEARCH)
+    assert 2 <= pl.timed <= 12
+    assert hdc.Plan([1024, 384], mode=hdc.HDC_PREDICT_MLP).timed == 0
+    nq = hdc.mlp_num_q_classes() if hasattr(hdc, "mlp_num_q_classes") else 8
+    for k in range(nq):
+        lg = np.full(nq + 2, -5.0, dtype=np.float32)
+        lg[k] = 5.0
+        lg[nq] = 1.0                       # D head: D = q
+        try:
+            want = hdc.mlp_decode_axis(lg, 3000, 5999, hdc.HDC_C128)
+        except hdc.HDCError:
+            continue
+        m, p, q, D = (hdc.C.c_int64() for _ in range(4))
+        rc = hdc.lib().hdc_mlp_decode_class(k, 0, 3000, 5999, hdc.HDC_C128, 0, hdc.C.byref(m), hdc.C.byref(p),
+                                            hdc.C.byref(q), hdc.C.byref(D))
+        if rc == 0 and want["m"] == m.value:
+            assert (want["p"], want["q"], want["D"]) == (p.value, q.value, D.value)
