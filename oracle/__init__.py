@@ -21,6 +21,8 @@ formula each one writes out):
   matching, Section 3.5 (O8)
 * ``conv_multi(xs, m, p, q, op)`` -- first L outputs of the n-fold
   convolution of n arrays, or of the sum of pairwise convolutions (O9)
+* ``conv_real(f, g, m, p, q)`` -- real inputs through the packed sequence
+  f + i g and conjugate residue pairs (O10)
 """
 from __future__ import annotations
 
@@ -55,6 +57,7 @@ def lib():
         L.hdco_residue_forward_1d.argtypes = [_dp, _i64, _i64, _i64, _i64, _dp]
         L.hdco_residue_backward_1d.argtypes = [_dp, _i64, _i64, _i64, _i64, _dp]
         L.hdco_conv_hybrid_1d.argtypes = [_dp, _dp, _i64, _i64, _i64, _i64, _dp]
+        L.hdco_conv_real_1d.argtypes = [_dp, _dp, _i64, _i64, _i64, _i64, _dp]
         L.hdco_conv_multi_1d.argtypes = [_dp, C.c_int, C.c_int, _i64, _i64, _i64, _i64, _dp]
         L.hdco_conv_unequal_1d.argtypes = [_dp, _i64, _dp, _i64, _i64, _i64, _i64, _i64, _i64, _dp]
         L.hdco_conv_hermitian_2d_direct.argtypes = [_dp, _dp, _i64, _dp]
@@ -222,6 +225,21 @@ def conv_multi(xs, m: int, p: int = 0, q: int = 0, op: str = "product"):
         q = -(-span // m)
     h = np.empty(L, dtype=np.complex128)
     _check(lib().hdco_conv_multi_1d(_dptr(xs), n, opc, L, m, p, q, _dptr(h)), "conv_multi")
+    return h
+
+
+def conv_real(f, g, m: int, p: int = 0, q: int = 0):
+    """First L outputs of the convolution of real 1-D f and g by O10; p, q
+    default to ceil(L/m) and ceil((2L - 1)/m)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    L = f.size
+    if p == 0:
+        p = -(-L // m)
+    if q == 0:
+        q = -(-(2 * L - 1) // m)
+    h = np.empty(L, dtype=np.float64)
+    _check(lib().hdco_conv_real_1d(_dptr(f), _dptr(g), L, m, p, q, _dptr(h)), "conv_real")
     return h
 
 

@@ -22,6 +22,8 @@
  *       algorithm for one dimension), built from O5's Eq. 1 and Eq. 2
  *   O9  multi-convolution of n arrays: the n-fold convolution, or the sum
  *       of pairwise convolutions, by the same residue transforms
+ *   O10 convolution of real inputs by the residue transforms of the packed
+ *       sequence z = f + i g and the conjugate pairing of residues
  *
  * Sign convention (the paper's Eq. 1 and Eq. 2): zeta_n = exp(2 pi i / n),
  * forward transforms use zeta^{+kj} unscaled, backward use zeta^{-kj}/n.
@@ -693,6 +695,78 @@ HDCO_API int hdco_conv_multi_1d(const double* xs, int n, int op, int64_t L, int6
     free(H);
     free(A);
     free(F);
+    return rc ? -1 : 0;
+}
+
+/* ------------------------------------------ O10 real inputs, 1-D */
+
+/* First L outputs of the convolution of real f and g (length L) through the
+ * residue transforms of the complex sequence z = f + i g (Eq. 1 with
+ * (m, p, q)).  Since f and g are real, F and G at DFT index K follow from Z
+ * at K and N - K:  F_K = (Z_K + conj Z_{N-K}) / 2,  G_K = (Z_K - conj Z_{N-K})
+ * / (2 i).  With K = q l + r, the index N - K lies in residue r' = (q - r)
+ * mod q at bin (m - l) mod m when r = 0 and m - 1 - l otherwise.  Only the
+ * residues r <= q / 2 are formed; the backward transform (Eq. 2) of residue
+ * r' is the complex conjugate of that of r, so each output is the real part
+ * of the residue-r contributions, doubled when r' != r.  Returns 0, or -1 on
+ * invalid parameters (q m < 2 L - 1 included), -3 on allocation failure. */
+HDCO_API int hdco_conv_real_1d(const double* f, const double* g, int64_t L, int64_t m, int64_t p, int64_t q,
+                               double* h)
+{
+    if (L < 1 || m < 1 || p * m < L || q < 1 || q * m < 2 * L - 1) return -1;
+    const int64_t N = q * m;
+    double* z = (double*)malloc(sizeof(double) * 2 * (size_t)L);
+    double* Z = (double*)malloc(sizeof(double) * 2 * (size_t)N);
+    double* H = (double*)malloc(sizeof(double) * 2 * (size_t)N);
+    double* x = (double*)malloc(sizeof(double) * 2 * (size_t)L);
+    if (!z || !Z || !H || !x) { free(z); free(Z); free(H); free(x); return -3; }
+    for (int64_t j = 0; j < L; ++j) { z[2 * j] = f[j]; z[2 * j + 1] = g[j]; }
+    int rc = hdco_residue_forward_1d(z, L, m, p, q, Z);
+    memset(H, 0, sizeof(double) * 2 * (size_t)N);
+    for (int64_t r = 0; 2 * r <= q && rc == 0; ++r) {
+        const int64_t rp = (q - r) % q;
+        for (int64_t l = 0; l < m; ++l) {
+            const int64_t lp = r == 0 ? (m - l) % m : m - 1 - l;
+            const double* a = Z + 2 * (q * l + r);
+            const double* b = Z + 2 * (q * lp + rp);
+            /* F = (a + conj b) / 2, G = (a - conj b) / (2 i) */
+            const double Fr = 0.5 * (a[0] + b[0]), Fi = 0.5 * (a[1] - b[1]);
+            const double Dr = 0.5 * (a[0] - b[0]), Di = 0.5 * (a[1] + b[1]);
+            const double Gr = Di, Gi = -Dr;
+            double* c = H + 2 * (q * l + r);
+            c[0] = Fr * Gr - Fi * Gi;
+            c[1] = Fr * Gi + Fi * Gr;
+        }
+    }
+    /* Eq. 2 over the kept residues only, weighted: residue r stands for
+     * itself and, when r' != r, for its conjugate partner */
+    for (int64_t j = 0; j < L && rc == 0; ++j) {
+        const int64_t t = j / m, s = j % m;
+        double acc = 0.0;
+        for (int64_t r = 0; 2 * r <= q; ++r) {
+            const int64_t rp = (q - r) % q;
+            const double w = rp == r ? 1.0 : 2.0;
+            /* u = sum_l zeta_m^{-s l} H_{q l + r}; term = zeta_q^{-t r} zeta_N^{-s r} u */
+            double ur = 0.0, ui = 0.0;
+            for (int64_t l = 0; l < m; ++l) {
+                double cc, sn;
+                root_of_unity((l * s) % m, m, &cc, &sn);
+                sn = -sn;
+                const double* Hk = H + 2 * (q * l + r);
+                ur += Hk[0] * cc - Hk[1] * sn;
+                ui += Hk[0] * sn + Hk[1] * cc;
+            }
+            double c1, s1, c2, s2;
+            root_of_unity((t * r) % q, q, &c1, &s1);
+            root_of_unity((s * r) % N, N, &c2, &s2);
+            const double wr = c1 * c2 - s1 * s2, wi = -(c1 * s2 + s1 * c2);
+            acc += w * (ur * wr - ui * wi);
+        }
+        x[2 * j] = acc / (double)N;
+    }
+    if (rc == 0)
+        for (int64_t j = 0; j < L; ++j) h[j] = x[2 * j];
+    free(z); free(Z); free(H); free(x);
     return rc ? -1 : 0;
 }
 
