@@ -281,6 +281,30 @@ int hdc_convnd_multi(int dims, int n, int op, const void* const* inputs, void* h
                      int dtype, int64_t batch, void* workspace,
                      size_t ws_bytes, void* stream);
 
+/* Convolution of real inputs (the paper's future work on the real case,
+ * Section 7): f, g and h are REAL arrays (dtype HDC_C128: double, HDC_C64:
+ * float), batch x prod(L), first L outputs per axis, same (L, M, m, p, q)
+ * rules as hdc_convnd.  The two inputs are packed as one complex sequence
+ * z = f + i g; since f and g are real, F and G at DFT index K follow from Z
+ * at K and at -K, and -K of residue r (axis 0) lies in residue
+ * (q - r) mod q.  Only the residues r <= q / 2 of axis 0 are formed, each
+ * from its pair of transforms, and each output is the real part of their
+ * contributions with the partner's folded in (factor 2 unless r = 0 or
+ * 2 r = q): two forward and one inverse transform per pair of residues
+ * instead of six.  Inner axes (N-D) run the complex convolution of the F
+ * and G rows.  D[0] counts kept residues per pass (clamped to q / 2 + 1).
+ * Workspace (device, caller-owned): hdc_workspace_size_real; h distinct
+ * from f and g (else HDC_ERR_PARAM). */
+int hdc_workspace_size_real(int dims, const int64_t* L, const int64_t* M,
+                            const int64_t* m, const int64_t* p,
+                            const int64_t* q, const int64_t* D, int dtype,
+                            int64_t batch, size_t* bytes);
+int hdc_convnd_real(int dims, const void* f, const void* g, void* h,
+                    const int64_t* L, const int64_t* M, const int64_t* m,
+                    const int64_t* p, const int64_t* q, const int64_t* D,
+                    int dtype, int64_t batch, void* workspace,
+                    size_t ws_bytes, void* stream);
+
 /* The share of residues [r_lo, r_hi) of axis 0 (0 <= r_lo < r_hi <= q[0]):
  * the outer sum of Eq. 2 restricted to that range, scaled by 1/N, so the
  * shares of disjoint ranges add up to the convolution.  Residues are

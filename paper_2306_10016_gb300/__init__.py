@@ -162,6 +162,10 @@ _SIGS += [
                                            C.c_int, _i64, C.POINTER(_sz)]),
     ("hdc_convnd_multi", C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(_vp), _vp, _i64p, _i64p, _i64p, _i64p,
                                    _i64p, _i64p, C.c_int, _i64, _vp, _sz, _vp]),
+    ("hdc_workspace_size_real", C.c_int, [C.c_int, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, C.c_int, _i64,
+                                          C.POINTER(_sz)]),
+    ("hdc_convnd_real", C.c_int, [C.c_int, _vp, _vp, _vp, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, C.c_int, _i64,
+                                  _vp, _sz, _vp]),
     ("hdc_workspace_size_hermitian", C.c_int, [_i64, _i64p, _i64p, C.c_int, _i64, C.POINTER(_sz)]),
     ("hdc_conv2d_hermitian", C.c_int, [_vp, _vp, _vp, _i64, _i64p, _i64p, C.c_int, _i64, _vp, _sz, _vp]),
     ("hdc_mlp_create", C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, C.c_int]),
@@ -435,6 +439,53 @@ def convnd_multi(xs, dims, m, op="product", M=None, p=0, q=0, D=0, out=None, wor
                                       _arr(Dv), dt, batch, workspace.data_ptr(),
                                       workspace.numel() * workspace.element_size(), st.cuda_stream),
                "hdc_convnd_multi")
+    return h
+
+
+def workspace_size_real(L, m, M=None, p=0, q=0, D=0, dtype=HDC_C128, batch=1) -> int:
+    dims = len(L)
+    mv, Mv, pv, qv, Dv = (_per_axis(v, dims, k) for v, k in ((m, "m"), (M, "M"), (p, "p"), (q, "q"), (D, "D")))
+    Mv = Mv or [2 * l - 1 for l in L]
+    nb = C.c_size_t()
+    _check(lib().hdc_workspace_size_real(dims, _arr(L), _arr(Mv), _arr(mv), _arr(pv), _arr(qv), _arr(Dv), dtype,
+                                         int(batch), C.byref(nb)), "workspace_size_real")
+    return nb.value
+
+
+def convnd_real(f, g, dims, m, M=None, p=0, q=0, D=0, out=None, workspace=None, stream=None):
+    """First L outputs per axis of the convolution of REAL f and g (float64
+    or float32 CUDA tensors of one shape) over their last `dims` axes, by the
+    packed transform of f + i g and conjugate residue pairs
+    (hdc_convnd_real); the result is real."""
+    torch = _torch()
+    if not (f.is_cuda and g.is_cuda) or f.shape != g.shape or f.dtype != g.dtype:
+        raise ValueError("f and g must be CUDA tensors of one shape and dtype")
+    if not (f.is_contiguous() and g.is_contiguous()):
+        raise ValueError("f and g must be contiguous")
+    if f.dtype == torch.float64:
+        dt = HDC_C128
+    elif f.dtype == torch.float32:
+        dt = HDC_C64
+    else:
+        raise TypeError(f"unsupported dtype {f.dtype}: use torch.float32 or torch.float64")
+    L = [int(x) for x in f.shape[f.dim() - dims:]]
+    batch = 1
+    for x in f.shape[: f.dim() - dims]:
+        batch *= int(x)
+    mv, Mv, pv, qv, Dv = (_per_axis(v, dims, k) for v, k in ((m, "m"), (M, "M"), (p, "p"), (q, "q"), (D, "D")))
+    Mv = Mv or [2 * l - 1 for l in L]
+    h = out if out is not None else torch.empty_like(f)
+    nb = C.c_size_t()
+    _check(lib().hdc_workspace_size_real(dims, _arr(L), _arr(Mv), _arr(mv), _arr(pv), _arr(qv), _arr(Dv), dt, batch,
+                                         C.byref(nb)), "workspace_size_real")
+    if workspace is None or workspace.numel() * workspace.element_size() < nb.value:
+        workspace = torch.empty(max(1, nb.value), dtype=torch.uint8, device=f.device)
+    st = stream if stream is not None else torch.cuda.current_stream(f.device)
+    with torch.cuda.device(f.device):
+        _check(lib().hdc_convnd_real(dims, f.data_ptr(), g.data_ptr(), h.data_ptr(), _arr(L), _arr(Mv), _arr(mv),
+                                     _arr(pv), _arr(qv), _arr(Dv), dt, batch, workspace.data_ptr(),
+                                     workspace.numel() * workspace.element_size(), st.cuda_stream),
+               "hdc_convnd_real")
     return h
 
 

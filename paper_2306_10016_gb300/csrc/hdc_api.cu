@@ -411,6 +411,123 @@ static cudaError_t run_nd(int dims, const Ins<T>& in, cx<T>* out, int64_t B, con
     return cudaSuccess;
 }
 
+// ------------------------------------------------------- real inputs
+// f and g real, packed as z = f + i g; only the residues r <= q / 2 of the
+// first axis are formed (r' = q - r is the conjugate partner), so D counts
+// kept residues per pass.
+
+static int64_t kept_residues(const Axis& a) { return a.q / 2 + 1; }
+
+static int64_t ws_elems_real(int dims, const Axis* ax, int64_t B)
+{
+    const Axis& a = ax[0];
+    const int64_t D = a.D < kept_residues(a) ? a.D : kept_residues(a);
+    if (dims == 1) {
+        int64_t m1 = 0, m2 = 0;
+        route(a, B, a.dtype, &m1, &m2);
+        return (m1 == 0 ? 1 : 2) * D * B * a.m;
+    }
+    int64_t Cn = 1, Cw = 1;
+    for (int i = 1; i < dims; ++i) { Cn *= ax[i].L; Cw *= ax[i].Lw; }
+    const int64_t rows = D * B * a.m;
+    return rows * (3 * Cn + Cw) + ws_elems(dims - 1, ax + 1, rows);
+}
+
+static size_t ws_bytes_real(int dims, const Axis* ax, int64_t B, size_t esz)
+{
+    int64_t tot = 1;
+    for (int i = 0; i < dims; ++i) tot *= ax[i].L;
+    return align_up((size_t)(B * tot) * esz) + align_up((size_t)ws_elems_real(dims, ax, B) * esz) + 256;
+}
+
+template <typename T>
+static cudaError_t run_rows_real(const cx<T>* z, T* out, int64_t B, const Axis& a, cx<T>* ws, cudaStream_t st)
+{
+    const double scale = 1.0 / (double)a.N;
+    const int64_t S = kept_residues(a);
+    const int64_t D = a.D < S ? a.D : S;
+    int64_t m1 = 0, m2 = 0;
+    route(a, B, a.dtype, &m1, &m2);
+    cx<T>* ya = ws;
+    cx<T>* yb = ws + D * B * a.m;
+    for (int64_t r0 = 0; r0 < S; r0 += D) {
+        const int64_t Dp = (D < S - r0) ? D : (S - r0);
+        const int first = (r0 == 0), last = (r0 + Dp >= S);
+        if (m1 == 0) {
+            HDC_TRY(launch_residue_rows_real<T>(z, ya, B, a.L, a.L, a.m, a.p, a.q, r0, Dp, st));
+            HDC_TRY(launch_unfold_real<T>(out, ya, B, a.L, 1, a.m, a.pout, a.q, a.N, 1, 0, 0, a.L, r0, Dp, first,
+                                          last, scale, st));
+            continue;
+        }
+        ColSide<T> sides[2];
+        sides[0] = ColSide<T>{ z, ya, a.L, a.L, (int)a.p, (int)a.q, 0, 1 };
+        sides[1] = ColSide<T>{ z, yb, a.L, a.L, (int)a.p, (int)a.q, 0, 1 };
+        sides[1].rneg = 1;
+        HDC_TRY(launch_fold_fft_cols<T>(sides, 2, B, m2, m1, a.N, m2, 1, r0, Dp, 1, st));
+        HDC_TRY(launch_rows_real_pair<T>(ya, yb, ya, B, m1, m2, r0, Dp, st));
+        HDC_TRY(launch_ifft_cols<T>(ya, B, m2, m1, a.q, a.N, Dp, 1, st));
+        HDC_TRY(launch_unfold_real<T>(out, ya, B, a.L, m2, m1, a.pout, a.q, a.N, m2, 1, 0, a.L, r0, Dp, first, last,
+                                      scale, st));
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+static cudaError_t run_nd_real(int dims, const cx<T>* z, T* out, int64_t B, const Axis* ax, cx<T>* ws,
+                               cudaStream_t st)
+{
+    if (dims == 1) return run_rows_real<T>(z, out, B, ax[0], ws, st);
+    const Axis& a = ax[0];
+    int64_t Cn = 1, Cw = 1;
+    for (int i = 1; i < dims; ++i) { Cn *= ax[i].L; Cw *= ax[i].Lw; }
+    const int64_t S = kept_residues(a);
+    const int64_t D = a.D < S ? a.D : S;
+    const int64_t rows = D * B * a.m;
+    cx<T>* wa = ws;
+    cx<T>* wb = wa + rows * Cn;
+    cx<T>* wg = wb + rows * Cn;
+    cx<T>* wh = wg + rows * Cn;
+    cx<T>* inner = wh + rows * Cw;
+    const double scale = 1.0 / (double)a.N;
+    Ins<T> in;
+    in.n = 2;
+    in.op = 0;
+    in.x[0] = wa;
+    in.x[1] = wg;
+    for (int64_t r0 = 0; r0 < S; r0 += D) {
+        const int64_t Dp = (D < S - r0) ? D : (S - r0);
+        const int first = (r0 == 0), last = (r0 + Dp >= S);
+        ColSide<T> sides[2];
+        sides[0] = ColSide<T>{ z, wa, a.L * Cn, a.L * Cn, (int)a.p, (int)a.q, 0, 1 };
+        sides[1] = ColSide<T>{ z, wb, a.L * Cn, a.L * Cn, (int)a.p, (int)a.q, 0, 1 };
+        sides[1].rneg = 1;
+        HDC_TRY(launch_fold_fft_cols<T>(sides, 2, B, Cn, a.m, a.N, 1, 0, r0, Dp, 0, st));
+        HDC_TRY(launch_pair_rows_real<T>(wa, wb, wg, B, Cn, a.m, r0, Dp, st));
+        HDC_TRY(run_nd<T>(dims - 1, in, wh, Dp * B * a.m, ax + 1, inner, st));
+        HDC_TRY(launch_ifft_cols<T>(wh, B, Cw, a.m, a.q, a.N, Dp, 0, st));
+        HDC_TRY(launch_unfold_real<T>(out, wh, B, a.L * Cw, Cw, a.m, a.pout, a.q, a.N, 1, 0, 0, a.L * Cw, r0, Dp,
+                                      first, last, scale, st));
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+static int conv_nd_real(int dims, const void* f, const void* g, void* h, const Axis* ax, int64_t B, void* ws,
+                        size_t ws_bytes_given, cudaStream_t st)
+{
+    using V = cx<T>;
+    const size_t need = ws_bytes_real(dims, ax, B, sizeof(V));
+    if (ws == nullptr || ws_bytes_given < need) return HDC_ERR_WORKSPACE;
+    int64_t tot = B;
+    for (int i = 0; i < dims; ++i) tot *= ax[i].L;
+    uintptr_t base = ((uintptr_t)ws + 255) & ~(uintptr_t)255;
+    V* z = (V*)base;
+    V* w = (V*)(base + align_up((size_t)tot * sizeof(V)));
+    if (launch_pack_real<T>((const T*)f, (const T*)g, z, tot, st) != cudaSuccess) return HDC_ERR_CUDA;
+    cudaError_t e = run_nd_real<T>(dims, z, (T*)h, B, ax, w, st);
+    return e == cudaSuccess ? HDC_OK : HDC_ERR_CUDA;
+}
+
 template <typename T>
 static int conv_nd(int dims, const void* f, const void* g, void* h, const Axis* ax, int inplace,
                    int64_t B, void* ws, size_t ws_bytes_given, cudaStream_t st, int64_t r_lo = 0,
@@ -885,6 +1002,35 @@ HDC_EXPORT int hdc_convnd_multi(int dims, int n, int op, const void* const* inpu
     if (dtype == HDC_C128)
         return conv_nd_multi<double>(dims, n, op, inputs, h, ax, batch, workspace, ws_bytes_given, st);
     return conv_nd_multi<float>(dims, n, op, inputs, h, ax, batch, workspace, ws_bytes_given, st);
+}
+
+HDC_EXPORT int hdc_workspace_size_real(int dims, const int64_t* L, const int64_t* M, const int64_t* m,
+                                       const int64_t* p, const int64_t* q, const int64_t* D, int dtype, int64_t batch,
+                                       size_t* bytes)
+{
+    if (!bytes || batch < 0) return HDC_ERR_PARAM;
+    Axis ax[HDC_MAX_DIMS];
+    int rc = resolve_all(dims, L, M, m, p, q, D, dtype, ax);
+    if (rc != HDC_OK) return rc;
+    *bytes = ws_bytes_real(dims, ax, batch, dtype == HDC_C128 ? 16 : 8);
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_convnd_real(int dims, const void* f, const void* g, void* h, const int64_t* L, const int64_t* M,
+                               const int64_t* m, const int64_t* p, const int64_t* q, const int64_t* D, int dtype,
+                               int64_t batch, void* workspace, size_t ws_bytes_given, void* stream)
+{
+    Axis ax[HDC_MAX_DIMS];
+    int rc = resolve_all(dims, L, M, m, p, q, D, dtype, ax);
+    if (rc != HDC_OK) return rc;
+    if (batch < 0) return HDC_ERR_PARAM;
+    if (batch == 0) return HDC_OK;
+    if (!f || !g || !h || h == f || h == g) return HDC_ERR_PARAM;
+    const uintptr_t al = dtype == HDC_C128 ? 7 : 3;
+    if (((uintptr_t)f & al) || ((uintptr_t)g & al) || ((uintptr_t)h & al)) return HDC_ERR_PARAM;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == HDC_C128) return conv_nd_real<double>(dims, f, g, h, ax, batch, workspace, ws_bytes_given, st);
+    return conv_nd_real<float>(dims, f, g, h, ax, batch, workspace, ws_bytes_given, st);
 }
 
 HDC_EXPORT int hdc_release_caches(void)

@@ -173,6 +173,85 @@ __device__ __forceinline__ void residue_row_lam_body(const V* fr, const V* gr, V
     __syncthreads();
 }
 
+// Real inputs (packed as z = f + i g): F and G at one DFT index from Z there
+// (a) and Z at the mirrored index (b):  F = (a + conj b) / 2,
+// G = (a - conj b) / (2 i);  returns their product H = F G.
+template <class V> __device__ __forceinline__ V real_pair_product(V a, V b)
+{
+    using T = typename real_of<V>::type;
+    const T h = (T)0.5;
+    const V F = mkc<V>(h * (a.x + b.x), h * (a.y - b.y));
+    const V G = mkc<V>(h * (a.y + b.y), -h * (a.x - b.x));
+    return cmul(F, G);
+}
+
+// One kept residue r (2 r <= q) of one packed real row z: fold and m-point FFT
+// of residue r and of its conjugate partner r' = (q - r) mod q, F and G from
+// the pair (bin l of r against bin (m - l) mod m of r' = 0 when r = 0, bin
+// m - 1 - l of r' otherwise), H = F G, inverse FFT; the unscaled result goes
+// to hr[0..m).  smem: three padded buffers of m.
+template <class V>
+__device__ __forceinline__ void residue_row_real_body(const V* zr, V* hr, int64_t L, int m, int p, int q, int r,
+                                                      const V* __restrict__ twN, const V* __restrict__ twm,
+                                                      const V* __restrict__ twml, const FftPlan& fp, V* smem, int tid,
+                                                      int nthr)
+{
+    const int plen = (int)padded_len(m);
+    V* sa = smem;
+    V* sb = sa + plen;
+    V* sc = sb + plen;
+    const int rp = (q - r) % q;
+    fold_row<V>(zr, L, m, p, q, r, twN, sa, tid, nthr);
+    __syncthreads();
+    fft_smem<V, false, true>(sa, sc, fp, 1, 1, m, twm, twml, tid, nthr);
+    V* pb = sa;
+    if (rp != r) {
+        fold_row<V>(zr, L, m, p, q, rp, twN, sb, tid, nthr);
+        __syncthreads();
+        fft_smem<V, false, true>(sb, sc, fp, 1, 1, m, twm, twml, tid, nthr);
+        pb = sb;
+    }
+    for (int l = tid; l < m; l += nthr) {
+        const int lp = r == 0 ? (m - l) % m : m - 1 - l;
+        sc[sidx<true>(l)] = real_pair_product(sa[sidx<true>(l)], pb[sidx<true>(lp)]);
+    }
+    __syncthreads();
+    fft_smem<V, true, true>(sc, sa, fp, 1, 1, m, twm, twml, tid, nthr);
+    for (int s = tid; s < m; s += nthr) hr[s] = sc[sidx<true>(s)];
+    __syncthreads();
+}
+
+// Split route, real inputs: row l1 of kept residue r (ya, after the column
+// pass) against row l1' of its partner (yb): m2-point FFTs of both, H = F G
+// per bin (bin l2 against (m2 - l2) mod m2 when r = 0 and l1 = 0, else
+// m2 - 1 - l2), inverse FFT into yh.  smem: three padded buffers of m2.
+template <class V>
+__device__ __forceinline__ void rows_real_pair_body(const V* ya, const V* yb, V* yh, int m2, int r, int l1,
+                                                    const V* __restrict__ twm, const V* __restrict__ twml,
+                                                    const FftPlan& fp, V* smem, int tid, int nthr)
+{
+    const int plen = (int)padded_len(m2);
+    V* sa = smem;
+    V* sb = sa + plen;
+    V* sc = sb + plen;
+    for (int s = tid; s < m2; s += nthr) {
+        sa[sidx<true>(s)] = ya[s];
+        sb[sidx<true>(s)] = yb[s];
+    }
+    __syncthreads();
+    fft_smem<V, false, true>(sa, sc, fp, 1, 1, m2, twm, twml, tid, nthr);
+    fft_smem<V, false, true>(sb, sc, fp, 1, 1, m2, twm, twml, tid, nthr);
+    const bool wrap = r == 0 && l1 == 0;
+    for (int l = tid; l < m2; l += nthr) {
+        const int lp = wrap ? (m2 - l) % m2 : m2 - 1 - l;
+        sc[sidx<true>(l)] = real_pair_product(sa[sidx<true>(l)], sb[sidx<true>(lp)]);
+    }
+    __syncthreads();
+    fft_smem<V, true, true>(sc, sa, fp, 1, 1, m2, twm, twml, tid, nthr);
+    for (int s = tid; s < m2; s += nthr) yh[s] = sc[sidx<true>(s)];
+    __syncthreads();
+}
+
 // Fold along a strided axis and FFT of size ma over it, for the columns
 // c0 .. c0+C-1 (< Cn) of one input x (view x[a][c], a = t ma + i, element
 // valid iff a Cn + c < Lvalid); residue r; result to yb[l ystride + c],

@@ -100,6 +100,7 @@ template <typename T> struct ColSide {
     cx<T>* y;
     int64_t bstride, Lvalid;
     int p, q, rmul, lam;
+    int rneg = 0; // 1: residue block rr is residue (q - (r0 + rr)) mod q
 };
 
 // Fold along a strided axis + FFT of size ma over that axis, for nside <=
@@ -111,6 +112,34 @@ template <typename T> struct ColSide {
 template <typename T>
 cudaError_t launch_fold_fft_cols(const ColSide<T>* sides, int nside, int64_t B, int64_t Cn, int64_t ma, int64_t Nf,
                                  int64_t cs, int64_t cc, int64_t r0, int64_t D, int post, cudaStream_t st);
+
+// Real inputs (packed z = f + i g; only the residues r <= q / 2 are kept,
+// each with its conjugate partner r' = (q - r) mod q):
+//  launch_pack_real      z[i] = f[i] + i g[i], n elements;
+//  launch_residue_rows_real  fused rows: kept residues r0 .. r0 + Dg - 1 of
+//                        every row of z (stride ld, L valid), unscaled H
+//                        transforms' inverses to h[rr][b][0..m);
+//  launch_rows_real_pair split rows: row l1 of ya[rr][b] with the mirrored
+//                        row of yb[rr][b] (the partners' column pass), into
+//                        yh (may be ya);
+//  launch_pair_rows_real outer axis of N-D: wa <- F, wg <- G elementwise from
+//                        wa and the mirrored rows of wb;
+//  launch_unfold_real    the weighted real part of the kept residues'
+//                        contributions, real output.
+template <typename T> cudaError_t launch_pack_real(const T* f, const T* g, cx<T>* z, int64_t n, cudaStream_t st);
+template <typename T>
+cudaError_t launch_residue_rows_real(const cx<T>* z, cx<T>* h, int64_t B, int64_t ld, int64_t L, int64_t m,
+                                     int64_t p, int64_t q, int64_t r0, int64_t Dg, cudaStream_t st);
+template <typename T>
+cudaError_t launch_rows_real_pair(const cx<T>* ya, const cx<T>* yb, cx<T>* yh, int64_t B, int64_t m1, int64_t m2,
+                                  int64_t r0, int64_t Dg, cudaStream_t st);
+template <typename T>
+cudaError_t launch_pair_rows_real(cx<T>* wa, const cx<T>* wb, cx<T>* wg, int64_t B, int64_t Cn, int64_t m0,
+                                  int64_t r0, int64_t Dg, cudaStream_t st);
+template <typename T>
+cudaError_t launch_unfold_real(T* out, const cx<T>* h, int64_t B, int64_t bstride, int64_t Cn, int64_t ma,
+                               int64_t p, int64_t q, int64_t Nf, int64_t cs, int64_t cc, int64_t lo, int64_t hi,
+                               int64_t r0, int64_t Dg, int first, int last, double scale, cudaStream_t st);
 
 // In-place inverse FFT of size ma along the strided axis of y[rr][b][l][c],
 // preceded by multiplication with conj(zeta_{Nf/q}^{l c}) if pre != 0.

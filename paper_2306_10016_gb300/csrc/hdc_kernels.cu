@@ -271,7 +271,7 @@ template <class V> struct ColSideK {
     const V* x;
     V* y;
     int64_t bstride, Lvalid;
-    int p, q, rmul, lam;
+    int p, q, rmul, lam, rneg;
 };
 template <class V> struct ColSidesK {
     ColSideK<V> s[kMaxInputs];
@@ -296,9 +296,10 @@ k_fold_fft_cols(ColSidesK<V> sides, int nside, int64_t B, int64_t Cn, int ma, in
     const int l = rt / Dg, rr = rt - l * Dg;
     const V* x = sd.x + b * sd.bstride;
     V* yb = sd.y + ((int64_t)rr * B + b) * ((int64_t)ma * sd.lam) * Cn + (int64_t)l * Cn;
-    fold_fft_cols_body<V>(x, yb, Cn, ma, sd.p, sd.q, Nf, cs, cc, sd.Lvalid, r0 + rr + l * sd.rmul, (int64_t)ct * C,
-                          C, post, (int64_t)sd.lam * Cn, twNf, twma, twmal, fp, reinterpret_cast<V*>(smraw),
-                          threadIdx.x, blockDim.x);
+    const int r = sd.rneg ? (sd.q - (r0 + rr)) % sd.q : r0 + rr + l * sd.rmul;
+    fold_fft_cols_body<V>(x, yb, Cn, ma, sd.p, sd.q, Nf, cs, cc, sd.Lvalid, r, (int64_t)ct * C, C, post,
+                          (int64_t)sd.lam * Cn, twNf, twma, twmal, fp, reinterpret_cast<V*>(smraw), threadIdx.x,
+                          blockDim.x);
 }
 
 template <typename T>
@@ -330,7 +331,7 @@ cudaError_t launch_fold_fft_cols(const ColSide<T>* sides, int nside, int64_t B, 
     double flops = 0.0, bytes = 0.0;
     for (int i = 0; i < kMaxInputs; ++i) {
         const ColSide<T>& sd = sides[i < nside ? i : 0];
-        k.s[i] = ColSideK<V>{ sd.x, sd.y, sd.bstride, sd.Lvalid, sd.p, sd.q, sd.rmul, sd.lam };
+        k.s[i] = ColSideK<V>{ sd.x, sd.y, sd.bstride, sd.Lvalid, sd.p, sd.q, sd.rmul, sd.lam, sd.rneg };
         if (i < nside) {
             flops += (double)Dg * sd.lam * B * (8.0 * sd.Lvalid + (double)Cn * fft_flops((double)ma));
             bytes += (B * (double)sd.Lvalid + (double)Dg * sd.lam * B * ma * Cn) * sizeof(V);
@@ -425,6 +426,210 @@ cudaError_t launch_unfold(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstride
     k_unfold<V, 4><<<(unsigned)blocks, thr, 0, st>>>(out, h, B, bstride, Cn, ma, (int)p, (int)q, Nf,
                                                      cs, cc, lo, hi, (int)r0, (int)Dg, first, last,
                                                      (T)scale, twNf);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- real inputs
+
+template <typename T> __global__ void k_pack_real(const T* __restrict__ f, const T* __restrict__ g, cx<T>* z, int64_t n)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) z[i] = mkc<cx<T>>(f[i], g[i]);
+}
+
+template <typename T> cudaError_t launch_pack_real(const T* f, const T* g, cx<T>* z, int64_t n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int thr = 256;
+    LaunchScope ls(K_UNFOLD, st, 0.0, (double)n * (2.0 * sizeof(T) + sizeof(cx<T>)));
+    k_pack_real<T><<<(unsigned)((n + thr - 1) / thr), thr, 0, st>>>(f, g, z, n);
+    return cudaGetLastError();
+}
+
+template <class V>
+__global__ void __launch_bounds__(kMaxThreads, 2)
+k_residue_rows_real(const V* z, V* h, int64_t B, int64_t ld, int64_t L, int m, int p, int q, int r0,
+                    const V* __restrict__ twN, const V* __restrict__ twm, const V* __restrict__ twml, FftPlan fp)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int64_t b = blockIdx.x % B;
+    const int rr = (int)(blockIdx.x / B);
+    residue_row_real_body<V>(z + b * ld, h + ((int64_t)rr * B + b) * m, L, m, p, q, r0 + rr, twN, twm, twml, fp,
+                             reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
+}
+
+template <typename T>
+cudaError_t launch_residue_rows_real(const cx<T>* z, cx<T>* h, int64_t B, int64_t ld, int64_t L, int64_t m,
+                                     int64_t p, int64_t q, int64_t r0, int64_t Dg, cudaStream_t st)
+{
+    using V = cx<T>;
+    if (B <= 0 || Dg <= 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    const V* twN = twiddles<T>(q * m, &e);
+    if (e != cudaSuccess) return e;
+    const V* twm = twiddles<T>(m, &e);
+    if (e != cudaSuccess) return e;
+    const V* twml = twiddles_lf<T>(m, &e);
+    if (e != cudaSuccess) return e;
+    const FftPlan fp = make_fft_plan(m);
+    const int thr = threads_for(m);
+    const size_t smem = (size_t)(3 * padded_len(m)) * sizeof(V);
+    auto kern = k_residue_rows_real<V>;
+    if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
+    // model per kept residue: two forward FFTs (one when self-paired, counted
+    // as two), one inverse, the pair product, the folds of z
+    const double Lrow = (double)((L < p * m) ? L : p * m);
+    LaunchScope ls(K_RESIDUE_ROWS, st, (double)(B * Dg) * (3.0 * fft_flops((double)m) + 14.0 * m + 16.0 * Lrow),
+                   (B * Lrow + (double)(Dg * B * m)) * sizeof(V));
+    kern<<<(unsigned)(B * Dg), thr, smem, st>>>(z, h, B, ld, L, (int)m, (int)p, (int)q, (int)r0, twN, twm, twml, fp);
+    return cudaGetLastError();
+}
+
+// Split route rows, real inputs: block (rr, b, l1) pairs row l1 of ya[rr][b]
+// with row l1' of yb[rr][b] (l1' = (m1 - l1) mod m1 for residue 0, else
+// m1 - 1 - l1) and writes row l1 of yh[rr][b]; rows of m2.
+template <class V>
+__global__ void __launch_bounds__(kMaxThreads, 2)
+k_rows_real_pair(const V* ya, const V* yb, V* yh, int64_t B, int m1, int m2, int r0, const V* __restrict__ twm,
+                 const V* __restrict__ twml, FftPlan fp)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    int64_t blk = blockIdx.x;
+    const int l1 = (int)(blk % m1);
+    blk /= m1;
+    const int64_t b = blk % B;
+    const int rr = (int)(blk / B);
+    const int r = r0 + rr;
+    const int l1p = r == 0 ? (m1 - l1) % m1 : m1 - 1 - l1;
+    const int64_t base = ((int64_t)rr * B + b) * m1;
+    rows_real_pair_body<V>(ya + (base + l1) * m2, yb + (base + l1p) * m2, yh + (base + l1) * m2, m2, r, l1, twm,
+                           twml, fp, reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
+}
+
+template <typename T>
+cudaError_t launch_rows_real_pair(const cx<T>* ya, const cx<T>* yb, cx<T>* yh, int64_t B, int64_t m1, int64_t m2,
+                                  int64_t r0, int64_t Dg, cudaStream_t st)
+{
+    using V = cx<T>;
+    if (B <= 0 || Dg <= 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    const V* twm = twiddles<T>(m2, &e);
+    if (e != cudaSuccess) return e;
+    const V* twml = twiddles_lf<T>(m2, &e);
+    if (e != cudaSuccess) return e;
+    const FftPlan fp = make_fft_plan(m2);
+    const int thr = threads_for(m2);
+    const size_t smem = (size_t)(3 * padded_len(m2)) * sizeof(V);
+    auto kern = k_rows_real_pair<V>;
+    if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
+    const int64_t rows = Dg * B * m1;
+    LaunchScope ls(K_RESIDUE_ROWS, st, (double)rows * (3.0 * fft_flops((double)m2) + 14.0 * m2),
+                   3.0 * rows * m2 * sizeof(V));
+    kern<<<(unsigned)rows, thr, smem, st>>>(ya, yb, yh, B, (int)m1, (int)m2, (int)r0, twm, twml, fp);
+    return cudaGetLastError();
+}
+
+// Outer axis of an N-D problem, real inputs: in the mixed domain (axis 0
+// transformed, inner axes not) the partner of row l0 of kept residue r is
+// row l0' of r' at the same inner position, so F and G rows are formed
+// elementwise:  wa <- F, wg <- G.  Layout [rr][b][l0][c], c < Cn.
+template <class V>
+__global__ void k_pair_rows_real(V* wa, const V* __restrict__ wb, V* wg, int64_t B, int64_t Cn, int m0, int r0,
+                                 int Dg)
+{
+    const int64_t per = (int64_t)m0 * Cn;
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)Dg * B * per) return;
+    const int64_t blkrow = gid / per;
+    const int64_t e = gid - blkrow * per;
+    const int l0 = (int)(e / Cn);
+    const int64_t c = e - (int64_t)l0 * Cn;
+    const int rr = (int)(blkrow / B);
+    const int r = r0 + rr;
+    const int l0p = r == 0 ? (m0 - l0) % m0 : m0 - 1 - l0;
+    using T = typename real_of<V>::type;
+    const T h = (T)0.5;
+    const V a = wa[gid];
+    const V bb = wb[blkrow * per + (int64_t)l0p * Cn + c];
+    wa[gid] = mkc<V>(h * (a.x + bb.x), h * (a.y - bb.y));
+    wg[gid] = mkc<V>(h * (a.y + bb.y), -h * (a.x - bb.x));
+}
+
+template <typename T>
+cudaError_t launch_pair_rows_real(cx<T>* wa, const cx<T>* wb, cx<T>* wg, int64_t B, int64_t Cn, int64_t m0,
+                                  int64_t r0, int64_t Dg, cudaStream_t st)
+{
+    const int64_t n = Dg * B * m0 * Cn;
+    if (n <= 0) return cudaSuccess;
+    const int thr = 256;
+    LaunchScope ls(K_UNFOLD, st, 8.0 * n, 4.0 * n * sizeof(cx<T>));
+    k_pair_rows_real<cx<T>><<<(unsigned)((n + thr - 1) / thr), thr, 0, st>>>(wa, wb, wg, B, Cn, (int)m0, (int)r0,
+                                                                           (int)Dg);
+    return cudaGetLastError();
+}
+
+// Unfold of kept residues into a real output: out[b][lin - lo] for
+// lin = (t ma + i) Cn + c in [lo, hi) gets sum_rr w_r Re(conj(zeta_Nf^{r (i cs +
+// c cc)}) conj(zeta_q^{r t}) h[rr][b][i][c]) with w_r = 1 for the
+// self-paired residues (r = 0, 2 r = q) and 2 otherwise; added to the
+// previous contents unless first, scaled if last.
+template <class V>
+__global__ void k_unfold_real(typename real_of<V>::type* out, const V* __restrict__ h, int64_t B, int64_t bstride,
+                              int64_t Cn, int64_t ma, int p, int q, int64_t Nf, int64_t cs, int64_t cc, int64_t lo,
+                              int64_t hi, int r0, int Dg, int first, int last, typename real_of<V>::type scale,
+                              const V* __restrict__ twNf)
+{
+    using T = typename real_of<V>::type;
+    const int64_t per = ma * Cn;
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gid >= per * B) return;
+    const int64_t b = gid / per;
+    const int64_t e = gid - b * per;
+    const int64_t i = e / Cn, c = e - i * Cn;
+    const int64_t mq = Nf / q;
+    T* ob = out + b * bstride;
+    const V* hb = h + b * per;
+    const int64_t hstride = B * per;
+    for (int t = 0; t < p; ++t) {
+        const int64_t lin = ((int64_t)t * ma + i) * Cn + c;
+        if (lin >= hi) break;
+        if (lin < lo) continue;
+        T acc = 0;
+        for (int rr = 0; rr < Dg; ++rr) {
+            const int r = r0 + rr;
+            const T w = (r == 0 || 2 * r == q) ? (T)1 : (T)2;
+            V hv = hb[(int64_t)rr * hstride + i * Cn + c];
+            if (r != 0) {
+                hv = cmulc(hv, __ldg(twNf + (int64_t)r * (i * cs + c * cc)));
+                if (t != 0) hv = cmulc(hv, __ldg(twNf + (((int64_t)r * t) % q) * mq));
+            }
+            acc += w * hv.x;
+        }
+        T v = acc;
+        if (!first) v += ob[lin - lo];
+        if (last) v *= scale;
+        ob[lin - lo] = v;
+    }
+}
+
+template <typename T>
+cudaError_t launch_unfold_real(T* out, const cx<T>* h, int64_t B, int64_t bstride, int64_t Cn, int64_t ma,
+                               int64_t p, int64_t q, int64_t Nf, int64_t cs, int64_t cc, int64_t lo, int64_t hi,
+                               int64_t r0, int64_t Dg, int first, int last, double scale, cudaStream_t st)
+{
+    using V = cx<T>;
+    if (B <= 0 || Dg <= 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    const V* twNf = twiddles<T>(Nf, &e);
+    if (e != cudaSuccess) return e;
+    const int thr = 256;
+    const int64_t total = ma * Cn * B;
+    const double nout = (double)(hi - lo);
+    LaunchScope ls(K_UNFOLD, st, (double)(Dg * B) * 8.0 * nout,
+                   ((double)(Dg * B * ma * Cn) * sizeof(V) + (first ? 1.0 : 2.0) * B * nout * sizeof(T)));
+    k_unfold_real<V><<<(unsigned)((total + thr - 1) / thr), thr, 0, st>>>(out, h, B, bstride, Cn, ma, (int)p, (int)q,
+                                                                        Nf, cs, cc, lo, hi, (int)r0, (int)Dg, first,
+                                                                        last, (T)scale, twNf);
     return cudaGetLastError();
 }
 
@@ -540,6 +745,22 @@ HDC_INST_TW(double)
 HDC_INST_TW(float)
 
 // ------------------------------------------------------ instantiations
+
+#define HDC_INST_REAL(T)                                                                                  \
+    template cudaError_t launch_pack_real<T>(const T*, const T*, cx<T>*, int64_t, cudaStream_t);        \
+    template cudaError_t launch_residue_rows_real<T>(const cx<T>*, cx<T>*, int64_t, int64_t, int64_t,    \
+                                                     int64_t, int64_t, int64_t, int64_t, int64_t,        \
+                                                     cudaStream_t);                                      \
+    template cudaError_t launch_rows_real_pair<T>(const cx<T>*, const cx<T>*, cx<T>*, int64_t, int64_t,  \
+                                                  int64_t, int64_t, int64_t, cudaStream_t);              \
+    template cudaError_t launch_pair_rows_real<T>(cx<T>*, const cx<T>*, cx<T>*, int64_t, int64_t,        \
+                                                  int64_t, int64_t, int64_t, cudaStream_t);              \
+    template cudaError_t launch_unfold_real<T>(T*, const cx<T>*, int64_t, int64_t, int64_t, int64_t,     \
+                                               int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,     \
+                                               int64_t, int64_t, int64_t, int, int, double, cudaStream_t);
+
+HDC_INST_REAL(double)
+HDC_INST_REAL(float)
 
 #define HDC_INST(T)                                                                                       \
     template cudaError_t launch_residue_rows<T>(const cx<T>*, const cx<T>*, cx<T>*, int64_t, int64_t,   \
