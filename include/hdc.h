@@ -455,6 +455,18 @@ int hdc_tune_multi(int dims, int n, int op, const int64_t* L, const int64_t* M,
                    hdc_tuple* best, hdc_tuple* trials, int64_t cap,
                    int64_t* ntrials);
 
+/* The same search for hdc_convnd_real on the caller's real buffers f, g,
+ * h (batch x prod(L)); workspace from hdc_tune_real_workspace_size. */
+int hdc_tune_real_workspace_size(int dims, const int64_t* L, const int64_t* M,
+                                 int dtype, int64_t batch, double max_ratio,
+                                 int64_t m_min, size_t* bytes);
+int hdc_tune_real(int dims, const int64_t* L, const int64_t* M, int dtype,
+                  int64_t batch, const void* f, const void* g, void* h,
+                  void* workspace, size_t ws_bytes, int warmup, int reps,
+                  double max_ratio, int64_t m_min, void* stream,
+                  hdc_tuple* best, hdc_tuple* trials, int64_t cap,
+                  int64_t* ntrials);
+
 /* Cheap searches (Section 4.3, A1: random search and reuse of a
  * rectangle's parameters; Section 6.3: the height-32 rectangle), same
  * buffers and results as hdc_tune_convnd.

@@ -109,6 +109,10 @@ class UTuple(C.Structure):
 _tp = C.POINTER(Tuple)
 _utp = C.POINTER(UTuple)
 _SIGS += [
+    ("hdc_tune_real_workspace_size", C.c_int, [C.c_int, _i64p, _i64p, C.c_int, _i64, C.c_double, _i64,
+                                               C.POINTER(_sz)]),
+    ("hdc_tune_real", C.c_int, [C.c_int, _i64p, _i64p, C.c_int, _i64, _vp, _vp, _vp, _vp, _sz, C.c_int, C.c_int,
+                                C.c_double, _i64, _vp, _tp, _tp, _i64, _i64p]),
     ("hdc_tune_convnd_random", C.c_int, [C.c_int, _i64p, _i64p, C.c_int, _i64, _vp, _vp, _vp, _vp, _sz, C.c_int,
                                          C.c_int, C.c_double, _i64, _i64, C.c_uint64, _vp, _tp, _tp, _i64, _i64p]),
     ("hdc_tune_convnd_proxy", C.c_int, [C.c_int, _i64p, _i64p, C.c_int, _i64, _vp, _vp, _vp, _vp, _sz, C.c_int,
@@ -724,6 +728,34 @@ def _tune_setup(f, g, dims, M, max_ratio, m_min):
            "tune_workspace_size")
     ws = torch.empty(max(1, nb.value), dtype=torch.uint8, device=f.device)
     return dt, L, batch, Mv, ws, nb.value
+
+
+def tune_real(f, g, dims, M=None, max_ratio=1.5, m_min=16, warmup=1, reps=3, stream=None):
+    """Grid search of (m, D) per axis for hdc_convnd_real on real CUDA
+    tensors f, g; returns (best per axis, trials)."""
+    torch = _torch()
+    dt = HDC_C128 if f.dtype == torch.float64 else HDC_C64
+    L = [int(x) for x in f.shape[f.dim() - dims:]]
+    batch = 1
+    for x in f.shape[: f.dim() - dims]:
+        batch *= int(x)
+    Mv = _per_axis(M, dims, "M") or [2 * l - 1 for l in L]
+    nb = C.c_size_t()
+    _check(lib().hdc_tune_real_workspace_size(dims, _arr(L), _arr(Mv), dt, batch, max_ratio, m_min, C.byref(nb)),
+           "tune_real_workspace_size")
+    ws = torch.empty(max(1, nb.value), dtype=torch.uint8, device=f.device)
+    h = torch.empty_like(f)
+    cap = 4096
+    best = (Tuple * dims)()
+    trials = (Tuple * (cap * dims))()
+    nt = C.c_int64()
+    st = stream if stream is not None else torch.cuda.current_stream(f.device)
+    with torch.cuda.device(f.device):
+        _check(lib().hdc_tune_real(dims, _arr(L), _arr(Mv), dt, batch, f.data_ptr(), g.data_ptr(), h.data_ptr(),
+                                   ws.data_ptr(), nb.value, warmup, reps, max_ratio, m_min, st.cuda_stream, best,
+                                   trials, cap, C.byref(nt)), "tune_real")
+    tr = [[trials[i * dims + a].as_dict() for a in range(dims)] for i in range(min(nt.value, cap))]
+    return [best[a].as_dict() for a in range(dims)], tr
 
 
 def tune_random(f, g, dims, n_samples=0, seed=230610016, M=None, max_ratio=2.0, m_min=16, warmup=1, reps=3,

@@ -425,12 +425,12 @@ static int64_t ws_elems_real(int dims, const Axis* ax, int64_t B)
     if (dims == 1) {
         int64_t m1 = 0, m2 = 0;
         route(a, B, a.dtype, &m1, &m2);
-        return (m1 == 0 ? 1 : 2) * D * B * a.m;
+        return (m1 == 0 ? 1 : 3) * D * B * a.m;
     }
     int64_t Cn = 1, Cw = 1;
     for (int i = 1; i < dims; ++i) { Cn *= ax[i].L; Cw *= ax[i].Lw; }
     const int64_t rows = D * B * a.m;
-    return rows * (3 * Cn + Cw) + ws_elems(dims - 1, ax + 1, rows);
+    return rows * (4 * Cn + Cw) + ws_elems(dims - 1, ax + 1, rows);
 }
 
 static size_t ws_bytes_real(int dims, const Axis* ax, int64_t B, size_t esz)
@@ -450,6 +450,7 @@ static cudaError_t run_rows_real(const cx<T>* z, T* out, int64_t B, const Axis& 
     route(a, B, a.dtype, &m1, &m2);
     cx<T>* ya = ws;
     cx<T>* yb = ws + D * B * a.m;
+    cx<T>* yh = ws + 2 * D * B * a.m;
     for (int64_t r0 = 0; r0 < S; r0 += D) {
         const int64_t Dp = (D < S - r0) ? D : (S - r0);
         const int first = (r0 == 0), last = (r0 + Dp >= S);
@@ -464,9 +465,9 @@ static cudaError_t run_rows_real(const cx<T>* z, T* out, int64_t B, const Axis& 
         sides[1] = ColSide<T>{ z, yb, a.L, a.L, (int)a.p, (int)a.q, 0, 1 };
         sides[1].rneg = 1;
         HDC_TRY(launch_fold_fft_cols<T>(sides, 2, B, m2, m1, a.N, m2, 1, r0, Dp, 1, st));
-        HDC_TRY(launch_rows_real_pair<T>(ya, yb, ya, B, m1, m2, r0, Dp, st));
-        HDC_TRY(launch_ifft_cols<T>(ya, B, m2, m1, a.q, a.N, Dp, 1, st));
-        HDC_TRY(launch_unfold_real<T>(out, ya, B, a.L, m2, m1, a.pout, a.q, a.N, m2, 1, 0, a.L, r0, Dp, first, last,
+        HDC_TRY(launch_rows_real_pair<T>(ya, yb, yh, B, m1, m2, a.q, r0, Dp, st));
+        HDC_TRY(launch_ifft_cols<T>(yh, B, m2, m1, a.q, a.N, Dp, 1, st));
+        HDC_TRY(launch_unfold_real<T>(out, yh, B, a.L, m2, m1, a.pout, a.q, a.N, m2, 1, 0, a.L, r0, Dp, first, last,
                                       scale, st));
     }
     return cudaSuccess;
@@ -485,14 +486,15 @@ static cudaError_t run_nd_real(int dims, const cx<T>* z, T* out, int64_t B, cons
     const int64_t rows = D * B * a.m;
     cx<T>* wa = ws;
     cx<T>* wb = wa + rows * Cn;
-    cx<T>* wg = wb + rows * Cn;
+    cx<T>* wf = wb + rows * Cn;
+    cx<T>* wg = wf + rows * Cn;
     cx<T>* wh = wg + rows * Cn;
     cx<T>* inner = wh + rows * Cw;
     const double scale = 1.0 / (double)a.N;
     Ins<T> in;
     in.n = 2;
     in.op = 0;
-    in.x[0] = wa;
+    in.x[0] = wf;
     in.x[1] = wg;
     for (int64_t r0 = 0; r0 < S; r0 += D) {
         const int64_t Dp = (D < S - r0) ? D : (S - r0);
@@ -502,7 +504,7 @@ static cudaError_t run_nd_real(int dims, const cx<T>* z, T* out, int64_t B, cons
         sides[1] = ColSide<T>{ z, wb, a.L * Cn, a.L * Cn, (int)a.p, (int)a.q, 0, 1 };
         sides[1].rneg = 1;
         HDC_TRY(launch_fold_fft_cols<T>(sides, 2, B, Cn, a.m, a.N, 1, 0, r0, Dp, 0, st));
-        HDC_TRY(launch_pair_rows_real<T>(wa, wb, wg, B, Cn, a.m, r0, Dp, st));
+        HDC_TRY(launch_pair_rows_real<T>(wa, wb, wf, wg, B, Cn, a.m, a.q, r0, Dp, st));
         HDC_TRY(run_nd<T>(dims - 1, in, wh, Dp * B * a.m, ax + 1, inner, st));
         HDC_TRY(launch_ifft_cols<T>(wh, B, Cw, a.m, a.q, a.N, Dp, 0, st));
         HDC_TRY(launch_unfold_real<T>(out, wh, B, a.L * Cw, Cw, a.m, a.pout, a.q, a.N, 1, 0, 0, a.L * Cw, r0, Dp,

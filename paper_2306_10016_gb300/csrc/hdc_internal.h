@@ -120,10 +120,12 @@ cudaError_t launch_fold_fft_cols(const ColSide<T>* sides, int nside, int64_t B, 
 //                        every row of z (stride ld, L valid), unscaled H
 //                        transforms' inverses to h[rr][b][0..m);
 //  launch_rows_real_pair split rows: row l1 of ya[rr][b] with the mirrored
-//                        row of yb[rr][b] (the partners' column pass), into
-//                        yh (may be ya);
-//  launch_pair_rows_real outer axis of N-D: wa <- F, wg <- G elementwise from
-//                        wa and the mirrored rows of wb;
+//                        row of yb[rr][b] (the partners' column pass; ya for
+//                        a self-paired residue, whose partner pass is
+//                        skipped), into yh (distinct from ya and yb);
+//  launch_pair_rows_real outer axis of N-D: wf <- F, wg <- G elementwise from
+//                        wa and the mirrored rows of wb (of wa when
+//                        self-paired);
 //  launch_unfold_real    the weighted real part of the kept residues'
 //                        contributions, real output.
 template <typename T> cudaError_t launch_pack_real(const T* f, const T* g, cx<T>* z, int64_t n, cudaStream_t st);
@@ -132,10 +134,10 @@ cudaError_t launch_residue_rows_real(const cx<T>* z, cx<T>* h, int64_t B, int64_
                                      int64_t p, int64_t q, int64_t r0, int64_t Dg, cudaStream_t st);
 template <typename T>
 cudaError_t launch_rows_real_pair(const cx<T>* ya, const cx<T>* yb, cx<T>* yh, int64_t B, int64_t m1, int64_t m2,
-                                  int64_t r0, int64_t Dg, cudaStream_t st);
+                                  int64_t q, int64_t r0, int64_t Dg, cudaStream_t st);
 template <typename T>
-cudaError_t launch_pair_rows_real(cx<T>* wa, const cx<T>* wb, cx<T>* wg, int64_t B, int64_t Cn, int64_t m0,
-                                  int64_t r0, int64_t Dg, cudaStream_t st);
+cudaError_t launch_pair_rows_real(const cx<T>* wa, const cx<T>* wb, cx<T>* wf, cx<T>* wg, int64_t B, int64_t Cn,
+                                  int64_t m0, int64_t q, int64_t r0, int64_t Dg, cudaStream_t st);
 template <typename T>
 cudaError_t launch_unfold_real(T* out, const cx<T>* h, int64_t B, int64_t bstride, int64_t Cn, int64_t ma,
                                int64_t p, int64_t q, int64_t Nf, int64_t cs, int64_t cc, int64_t lo, int64_t hi,

@@ -297,6 +297,9 @@ k_fold_fft_cols(ColSidesK<V> sides, int nside, int64_t B, int64_t Cn, int ma, in
     const V* x = sd.x + b * sd.bstride;
     V* yb = sd.y + ((int64_t)rr * B + b) * ((int64_t)ma * sd.lam) * Cn + (int64_t)l * Cn;
     const int r = sd.rneg ? (sd.q - (r0 + rr)) % sd.q : r0 + rr + l * sd.rmul;
+    // a self-paired residue's partner is itself: its column pass is already
+    // done by the other side (the whole block leaves before any barrier)
+    if (sd.rneg && r == r0 + rr) return;
     fold_fft_cols_body<V>(x, yb, Cn, ma, sd.p, sd.q, Nf, cs, cc, sd.Lvalid, r, (int64_t)ct * C, C, post,
                           (int64_t)sd.lam * Cn, twNf, twma, twmal, fp, reinterpret_cast<V*>(smraw), threadIdx.x,
                           blockDim.x);
@@ -486,12 +489,13 @@ cudaError_t launch_residue_rows_real(const cx<T>* z, cx<T>* h, int64_t B, int64_
 }
 
 // Split route rows, real inputs: block (rr, b, l1) pairs row l1 of ya[rr][b]
-// with row l1' of yb[rr][b] (l1' = (m1 - l1) mod m1 for residue 0, else
-// m1 - 1 - l1) and writes row l1 of yh[rr][b]; rows of m2.
+// with row l1' of yb[rr][b] (of ya[rr][b] for a self-paired residue;
+// l1' = (m1 - l1) mod m1 for residue 0, else m1 - 1 - l1) and writes row l1
+// of yh[rr][b], which must not alias ya or yb; rows of m2.
 template <class V>
 __global__ void __launch_bounds__(kMaxThreads, 2)
-k_rows_real_pair(const V* ya, const V* yb, V* yh, int64_t B, int m1, int m2, int r0, const V* __restrict__ twm,
-                 const V* __restrict__ twml, FftPlan fp)
+k_rows_real_pair(const V* ya, const V* yb, V* yh, int64_t B, int m1, int m2, int q, int r0,
+                 const V* __restrict__ twm, const V* __restrict__ twml, FftPlan fp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     int64_t blk = blockIdx.x;
@@ -502,13 +506,15 @@ k_rows_real_pair(const V* ya, const V* yb, V* yh, int64_t B, int m1, int m2, int
     const int r = r0 + rr;
     const int l1p = r == 0 ? (m1 - l1) % m1 : m1 - 1 - l1;
     const int64_t base = ((int64_t)rr * B + b) * m1;
-    rows_real_pair_body<V>(ya + (base + l1) * m2, yb + (base + l1p) * m2, yh + (base + l1) * m2, m2, r, l1, twm,
+    // self-paired residues (r = 0, 2 r = q) find their partner rows in ya
+    const V* src = (r == 0 || 2 * r == q) ? ya : yb;
+    rows_real_pair_body<V>(ya + (base + l1) * m2, src + (base + l1p) * m2, yh + (base + l1) * m2, m2, r, l1, twm,
                            twml, fp, reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
 }
 
 template <typename T>
 cudaError_t launch_rows_real_pair(const cx<T>* ya, const cx<T>* yb, cx<T>* yh, int64_t B, int64_t m1, int64_t m2,
-                                  int64_t r0, int64_t Dg, cudaStream_t st)
+                                  int64_t q, int64_t r0, int64_t Dg, cudaStream_t st)
 {
     using V = cx<T>;
     if (B <= 0 || Dg <= 0) return cudaSuccess;
@@ -525,17 +531,18 @@ cudaError_t launch_rows_real_pair(const cx<T>* ya, const cx<T>* yb, cx<T>* yh, i
     const int64_t rows = Dg * B * m1;
     LaunchScope ls(K_RESIDUE_ROWS, st, (double)rows * (3.0 * fft_flops((double)m2) + 14.0 * m2),
                    3.0 * rows * m2 * sizeof(V));
-    kern<<<(unsigned)rows, thr, smem, st>>>(ya, yb, yh, B, (int)m1, (int)m2, (int)r0, twm, twml, fp);
+    kern<<<(unsigned)rows, thr, smem, st>>>(ya, yb, yh, B, (int)m1, (int)m2, (int)q, (int)r0, twm, twml, fp);
     return cudaGetLastError();
 }
 
 // Outer axis of an N-D problem, real inputs: in the mixed domain (axis 0
 // transformed, inner axes not) the partner of row l0 of kept residue r is
-// row l0' of r' at the same inner position, so F and G rows are formed
-// elementwise:  wa <- F, wg <- G.  Layout [rr][b][l0][c], c < Cn.
+// row l0' of r' at the same inner position (in wa itself for the
+// self-paired residues r = 0 and 2 r = q, else in wb), so F and G rows are
+// formed elementwise into wf and wg.  Layout [rr][b][l0][c], c < Cn.
 template <class V>
-__global__ void k_pair_rows_real(V* wa, const V* __restrict__ wb, V* wg, int64_t B, int64_t Cn, int m0, int r0,
-                                 int Dg)
+__global__ void k_pair_rows_real(const V* __restrict__ wa, const V* __restrict__ wb, V* wf, V* wg, int64_t B,
+                                 int64_t Cn, int m0, int q, int r0, int Dg)
 {
     const int64_t per = (int64_t)m0 * Cn;
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -550,21 +557,22 @@ __global__ void k_pair_rows_real(V* wa, const V* __restrict__ wb, V* wg, int64_t
     using T = typename real_of<V>::type;
     const T h = (T)0.5;
     const V a = wa[gid];
-    const V bb = wb[blkrow * per + (int64_t)l0p * Cn + c];
-    wa[gid] = mkc<V>(h * (a.x + bb.x), h * (a.y - bb.y));
+    const V* src = (r == 0 || 2 * r == q) ? wa : wb;
+    const V bb = src[blkrow * per + (int64_t)l0p * Cn + c];
+    wf[gid] = mkc<V>(h * (a.x + bb.x), h * (a.y - bb.y));
     wg[gid] = mkc<V>(h * (a.y + bb.y), -h * (a.x - bb.x));
 }
 
 template <typename T>
-cudaError_t launch_pair_rows_real(cx<T>* wa, const cx<T>* wb, cx<T>* wg, int64_t B, int64_t Cn, int64_t m0,
-                                  int64_t r0, int64_t Dg, cudaStream_t st)
+cudaError_t launch_pair_rows_real(const cx<T>* wa, const cx<T>* wb, cx<T>* wf, cx<T>* wg, int64_t B, int64_t Cn,
+                                  int64_t m0, int64_t q, int64_t r0, int64_t Dg, cudaStream_t st)
 {
     const int64_t n = Dg * B * m0 * Cn;
     if (n <= 0) return cudaSuccess;
     const int thr = 256;
     LaunchScope ls(K_UNFOLD, st, 8.0 * n, 4.0 * n * sizeof(cx<T>));
-    k_pair_rows_real<cx<T>><<<(unsigned)((n + thr - 1) / thr), thr, 0, st>>>(wa, wb, wg, B, Cn, (int)m0, (int)r0,
-                                                                           (int)Dg);
+    k_pair_rows_real<cx<T>><<<(unsigned)((n + thr - 1) / thr), thr, 0, st>>>(wa, wb, wf, wg, B, Cn, (int)m0, (int)q,
+                                                                           (int)r0, (int)Dg);
     return cudaGetLastError();
 }
 
@@ -752,9 +760,10 @@ HDC_INST_TW(float)
                                                      int64_t, int64_t, int64_t, int64_t, int64_t,        \
                                                      cudaStream_t);                                      \
     template cudaError_t launch_rows_real_pair<T>(const cx<T>*, const cx<T>*, cx<T>*, int64_t, int64_t,  \
-                                                  int64_t, int64_t, int64_t, cudaStream_t);              \
-    template cudaError_t launch_pair_rows_real<T>(cx<T>*, const cx<T>*, cx<T>*, int64_t, int64_t,        \
-                                                  int64_t, int64_t, int64_t, cudaStream_t);              \
+                                                  int64_t, int64_t, int64_t, int64_t, cudaStream_t);     \
+    template cudaError_t launch_pair_rows_real<T>(const cx<T>*, const cx<T>*, cx<T>*, cx<T>*, int64_t,   \
+                                                  int64_t, int64_t, int64_t, int64_t, int64_t,           \
+                                                  cudaStream_t);                                         \
     template cudaError_t launch_unfold_real<T>(T*, const cx<T>*, int64_t, int64_t, int64_t, int64_t,     \
                                                int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,     \
                                                int64_t, int64_t, int64_t, int, int, double, cudaStream_t);

@@ -416,6 +416,19 @@ double time_config_multi(int dims, int n, int op, const void* const* xs, void* h
         warmup, reps, st);
 }
 
+double time_config_real(int dims, const void* f, const void* g, void* h, const int64_t* L, const int64_t* M,
+                        const hdc_tuple* t, int dtype, int64_t batch, void* ws, size_t ws_bytes, int warmup, int reps,
+                        cudaStream_t st)
+{
+    int64_t m[HDC_MAX_DIMS], p[HDC_MAX_DIMS], q[HDC_MAX_DIMS], D[HDC_MAX_DIMS];
+    for (int i = 0; i < dims; ++i) { m[i] = t[i].m; p[i] = t[i].p; q[i] = t[i].q; D[i] = t[i].D; }
+    size_t need = 0;
+    if (hdc_workspace_size_real(dims, L, M, m, p, q, D, dtype, batch, &need) != HDC_OK || need > ws_bytes)
+        return -1.0;
+    return median_ms([&]() { return hdc_convnd_real(dims, f, g, h, L, M, m, p, q, D, dtype, batch, ws, ws_bytes, st); },
+                     warmup, reps, st);
+}
+
 // The separable search of Section 4.2 over per-axis candidate lists c[ax]
 // (tuples with q, D and ms fields): axes from the last to the first, each
 // swept with the others at their best so far (the smallest model flops to
@@ -679,6 +692,54 @@ HDC_EXPORT int hdc_tune_multi(int dims, int n, int op, const int64_t* L, const i
         dims, c,
         [&](const hdc_tuple* t) {
             return time_config_multi(dims, n, op, inputs, h, L, M, t, dtype, batch, ws, ws_bytes, warmup, reps, st);
+        },
+        best, trials, cap, ntrials);
+}
+
+HDC_EXPORT int hdc_tune_real_workspace_size(int dims, const int64_t* L, const int64_t* M, int dtype, int64_t batch,
+                                            double max_ratio, int64_t m_min, size_t* bytes)
+{
+    if (!bytes || dims < 1 || dims > HDC_MAX_DIMS || !L || !M) return HDC_ERR_PARAM;
+    std::vector<hdc_tuple> c[HDC_MAX_DIMS];
+    for (int i = 0; i < dims; ++i) {
+        c[i] = candidates(L[i], M[i], dtype, max_ratio, m_min);
+        if (c[i].empty()) return HDC_ERR_UNSUPPORTED_SIZE;
+    }
+    size_t worst = 0;
+    int64_t m[HDC_MAX_DIMS], p[HDC_MAX_DIMS], q[HDC_MAX_DIMS], D[HDC_MAX_DIMS];
+    int64_t idx[HDC_MAX_DIMS] = { 0, 0, 0 };
+    while (true) {
+        for (int i = 0; i < dims; ++i) {
+            const hdc_tuple& t = c[i][idx[i]];
+            m[i] = t.m; p[i] = t.p; q[i] = t.q; D[i] = t.q;
+        }
+        size_t b = 0;
+        if (hdc_workspace_size_real(dims, L, M, m, p, q, D, dtype, batch, &b) == HDC_OK) worst = std::max(worst, b);
+        int k = dims - 1;
+        while (k >= 0 && ++idx[k] == (int64_t)c[k].size()) idx[k--] = 0;
+        if (k < 0) break;
+    }
+    *bytes = worst;
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_tune_real(int dims, const int64_t* L, const int64_t* M, int dtype, int64_t batch, const void* f,
+                             const void* g, void* h, void* ws, size_t ws_bytes, int warmup, int reps, double max_ratio,
+                             int64_t m_min, void* stream, hdc_tuple* best, hdc_tuple* trials, int64_t cap,
+                             int64_t* ntrials)
+{
+    if (dims < 1 || dims > HDC_MAX_DIMS || !L || !M || !best || !f || !g || !h || reps < 1) return HDC_ERR_PARAM;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<hdc_tuple> c[HDC_MAX_DIMS];
+    for (int i = 0; i < dims; ++i) {
+        if (M[i] < 2 * L[i] - 1) return HDC_ERR_ALIAS;
+        c[i] = axis_candidates(L, M, i, dims, dtype, max_ratio, m_min);
+        if (c[i].empty()) return HDC_ERR_UNSUPPORTED_SIZE;
+    }
+    return separable_search<hdc_tuple>(
+        dims, c,
+        [&](const hdc_tuple* t) {
+            return time_config_real(dims, f, g, h, L, M, t, dtype, batch, ws, ws_bytes, warmup, reps, st);
         },
         best, trials, cap, ntrials);
 }

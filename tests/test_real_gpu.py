@@ -143,3 +143,14 @@ def test_errors(hdc):
     assert e.value.code == hdc.HDC_ERR_PARAM
     with pytest.raises(TypeError):
         hdc.convnd_real(f.to(torch.complex128), g.to(torch.complex128), 1, 16)
+
+
+def test_tuner(hdc):
+    f, g = real_pair(701, (2, 5000))
+    ft = torch.from_numpy(f).cuda()
+    gt = torch.from_numpy(g).cuda()
+    best, trials = hdc.tune_real(ft, gt, 1, reps=2)
+    assert trials and best[0]["ms"] <= min(t[0]["ms"] for t in trials) + 1e-9
+    h = run(hdc, f, g, 1, best[0]["m"], D=best[0]["D"])
+    ref = np.stack([cref(f[b], g[b], "fft") for b in range(2)])
+    assert rel_max_err(h, ref) < TOL64
