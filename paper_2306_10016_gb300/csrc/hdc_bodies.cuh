@@ -32,8 +32,9 @@ __device__ __forceinline__ void residue_row_body(const V* fr, const V* gr, V* hr
         }
     } else {
         for (int s = tid; s < m; s += nthr) {
-            V af = czero<V>(), ag = czero<V>();
-            for (int t = 0; t < p; ++t) {
+            // block t = 0 carries zeta_q^0 = 1: no multiplication
+            V af = s < Lf ? fr[s] : czero<V>(), ag = s < L ? gr[s] : czero<V>();
+            for (int t = 1; t < p; ++t) {
                 const int64_t j = (int64_t)t * m + s;
                 if (j >= L) break;
                 const V fv = j < Lf ? fr[j] : czero<V>(), gv = gr[j];
@@ -73,8 +74,8 @@ __device__ __forceinline__ void fold_row(const V* x, int64_t L, int m, int p, in
                                          V* dst, int tid, int nthr)
 {
     for (int s = tid; s < m; s += nthr) {
-        V a = czero<V>();
-        for (int t = 0; t < p; ++t) {
+        V a = s < L ? x[s] : czero<V>(); // block t = 0: zeta_q^0 = 1
+        for (int t = 1; t < p; ++t) {
             const int64_t j = (int64_t)t * m + s;
             if (j >= L) break;
             if (r == 0) a = cadd(a, x[j]);
@@ -266,21 +267,44 @@ __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn
     V* buf = smem;
     V* tmp = buf + ma * C;
     const int64_t mq = Nf / q;
-    for (int e = tid; e < ma * C; e += nthr) {
-        const int i = e / C, cl = e - i * C;
-        const int64_t c = c0 + cl;
-        V acc = czero<V>();
-        if (c < Cn) {
-            for (int t = 0; t < p; ++t) {
-                const int64_t lin = ((int64_t)t * ma + i) * Cn + c;
-                if (lin >= Lvalid) break;
-                const V xv = x[lin];
-                if (r == 0) acc = cadd(acc, xv);
-                else acc = cfma(xv, __ldg(twNf + (((int64_t)r * t) % q) * mq), acc);
-            }
-            if (r != 0) acc = cmul(acc, __ldg(twNf + (int64_t)r * (i * cs + c * cc)));
+    // four elements per thread at a time, so their loads are in flight
+    // together; element e = i C + cl of the tile is column c0 + cl, row i
+    constexpr int U = 4;
+    const int n = ma * C;
+    for (int e0 = tid; e0 < n; e0 += U * nthr) {
+        V acc[U];
+        int64_t base[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * nthr;
+            const int i = e / C, cl = e - i * C;
+            const int64_t c = c0 + cl;
+            base[u] = (e < n && c < Cn) ? (int64_t)i * Cn + c : -1;
+            // block t = 0 carries zeta_q^0 = 1: no multiplication
+            acc[u] = (base[u] >= 0 && base[u] < Lvalid) ? x[base[u]] : czero<V>();
         }
-        buf[e] = acc;
+        for (int t = 1; t < p; ++t) {
+            const int64_t off = (int64_t)t * ma * Cn;
+            if (off >= Lvalid) break;
+            const V w = r == 0 ? czero<V>() : __ldg(twNf + (((int64_t)r * t) % q) * mq);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (base[u] < 0 || base[u] + off >= Lvalid) continue;
+                const V xv = x[base[u] + off];
+                acc[u] = r == 0 ? cadd(acc[u], xv) : cfma(xv, w, acc[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * nthr;
+            if (e >= n) break;
+            V a = acc[u];
+            if (r != 0 && base[u] >= 0) {
+                const int i = e / C, cl = e - i * C;
+                a = cmul(a, __ldg(twNf + (int64_t)r * (i * cs + (c0 + cl) * cc)));
+            }
+            buf[e] = a;
+        }
     }
     __syncthreads();
     if (ma > 1) fft_smem<V, false>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);

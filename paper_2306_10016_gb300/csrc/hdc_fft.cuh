@@ -111,24 +111,25 @@ template <class V, bool INV> struct Dft<V, 8, INV> {
         V o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
         dft4<V, INV>(e0, e1, e2, e3);
         dft4<V, INV>(o0, o1, o2, o3);
-        // o_k *= zeta_8^{+-k}
-        V w1, w3;
+        // e_k +- zeta_8^{+-k} o_k for k = 1, 3 as e +- h d with the sums and
+        // differences d of o's parts: one add and two FMAs per component
+        T d1x, d1y, d3x, d3y;
         if (!INV) {
-            w1 = mkc<V>(h * (o1.x - o1.y), h * (o1.x + o1.y));
-            w3 = mkc<V>(-h * (o3.x + o3.y), h * (o3.x - o3.y));
+            d1x = o1.x - o1.y; d1y = o1.x + o1.y;
+            d3x = -(o3.x + o3.y); d3y = o3.x - o3.y;
         } else {
-            w1 = mkc<V>(h * (o1.x + o1.y), h * (o1.y - o1.x));
-            w3 = mkc<V>(h * (o3.y - o3.x), -h * (o3.x + o3.y));
+            d1x = o1.x + o1.y; d1y = o1.y - o1.x;
+            d3x = o3.y - o3.x; d3y = -(o3.x + o3.y);
         }
         V w2 = rot90<V, INV>(o2);
         v[0] = cadd(e0, o0);
         v[4] = csub(e0, o0);
-        v[1] = cadd(e1, w1);
-        v[5] = csub(e1, w1);
+        v[1] = mkc<V>(fma(h, d1x, e1.x), fma(h, d1y, e1.y));
+        v[5] = mkc<V>(fma(-h, d1x, e1.x), fma(-h, d1y, e1.y));
         v[2] = cadd(e2, w2);
         v[6] = csub(e2, w2);
-        v[3] = cadd(e3, w3);
-        v[7] = csub(e3, w3);
+        v[3] = mkc<V>(fma(h, d3x, e3.x), fma(h, d3y, e3.y));
+        v[7] = mkc<V>(fma(-h, d3x, e3.x), fma(-h, d3y, e3.y));
     }
 };
 
