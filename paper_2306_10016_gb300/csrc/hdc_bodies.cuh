@@ -26,6 +26,7 @@ __device__ __forceinline__ void residue_row_body(const V* fr, const V* gr, V* hr
     V* sb = sa + plen;
     V* sc = sb + plen;
     if (p == 1 && q == 1 && L >= m && Lf == L) {
+#pragma unroll 4
         for (int s = tid; s < m; s += nthr) {
             sa[sidx<true>(s)] = fr[s];
             sb[sidx<true>(s)] = gr[s];
@@ -330,15 +331,28 @@ __device__ __forceinline__ void ifft_cols_body(V* yb, int64_t Cn, int ma, int q,
 {
     V* buf = smem;
     V* tmp = buf + ma * C;
-    for (int e = tid; e < ma * C; e += nthr) {
-        const int l = e / C, cl = e - l * C;
-        const int64_t c = c0 + cl;
-        V v = czero<V>();
-        if (c < Cn) {
-            v = yb[(int64_t)l * Cn + c];
-            if (pre && l != 0 && c != 0) v = cmulc(v, __ldg(twNf + (int64_t)l * c * q));
+    // four elements per thread at a time, so their loads are in flight
+    // together
+    constexpr int U = 4;
+    const int n = ma * C;
+    for (int e0 = tid; e0 < n; e0 += U * nthr) {
+        V v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * nthr;
+            const int l = e / C, cl = e - l * C;
+            const int64_t c = c0 + cl;
+            v[u] = (e < n && c < Cn) ? yb[(int64_t)l * Cn + c] : czero<V>();
         }
-        buf[e] = v;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * nthr;
+            if (e >= n) break;
+            const int l = e / C, cl = e - l * C;
+            const int64_t c = c0 + cl;
+            if (pre && l != 0 && c != 0 && c < Cn) v[u] = cmulc(v[u], __ldg(twNf + (int64_t)l * c * q));
+            buf[e] = v[u];
+        }
     }
     __syncthreads();
     if (ma > 1) fft_smem<V, true>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);
