@@ -12,6 +12,15 @@ library is missing or no GPU is present, the calls raise.
 Parameters follow Section 2.5 of the paper, per axis: M (padded length,
 default 2L-1), m (FFT size), p and q (0: ceil(L/m), ceil(M/m)), D (residues
 per pass, 0: q) and inplace (the result overwrites f).
+
+Beyond the two-input convolution: ``convnd_window`` (slices of the linear
+convolution), ``conv2d_hermitian``, ``convnd_unequal`` (unequal lengths,
+residue matching), ``convnd_multi`` (n-fold product or pairwise sum of up to
+8 inputs), ``convnd_real`` (real inputs), ``BatchedPlan`` (many 1-D
+convolutions in one launch), ``convnd_residues`` (one rank's share),
+``conv1d_noalloc`` and ``convnd_host``; searches ``tune``, ``tune_unequal``,
+``tune_multi``, ``tune_real``, ``tune_random``, ``tune_proxy`` and the plan
+modes of ``Plan`` (including the learned predictor, ``MLP``).
 """
 from __future__ import annotations
 
