@@ -331,7 +331,8 @@ static cudaError_t run_rows(const Ins<T>& in, cx<T>* out, int64_t B, int64_t ld_
     }
     // m = m1 m2: fold + m1-point FFTs along the strided view [p m1][m2] with the
     // inner twiddle zeta_m^{l1 s2}; m2-point row transforms, product and
-    // inverse; inverse m1-point FFTs; unfold.  With lam > 1, f's transform
+    // inverse; inverse m1-point FFTs and unfold (one fused pass when there are
+    // enough column tiles).  With lam > 1, f's transform
     // splits as (m1 / lam) m2 and its row l1' of residue q l + r lands on row
     // lam l1' + l, next to the row of g it multiplies.  Input i works in
     // y[i] = ws + i D B m; the product lands in y[0].
@@ -357,9 +358,8 @@ static cudaError_t run_rows(const Ins<T>& in, cx<T>* out, int64_t B, int64_t ld_
             }
             HDC_TRY(launch_residue_rows<T>(y[0], y[1], y[0], Dg * B * m1, m2, m2, m2, m2, m2, 1, 1, 0, 1, st));
         }
-        HDC_TRY(launch_ifft_cols<T>(y[0], B, m2, m1, a.q, a.N, Dg, 1, st));
-        HDC_TRY(launch_unfold<T>(out, y[0], B, ldo, m2, m1, a.pout, a.q, a.N, m2, 1, a.o, a.o + a.Lw, r0,
-                                 Dg, first, last, scale, st));
+        HDC_TRY(launch_ifft_unfold<T>(y[0], out, B, ldo, m2, m1, a.pout, a.q, a.N, m2, 1, a.o, a.o + a.Lw, r0, Dg,
+                                      first, last, scale, 1, st));
     }
     return cudaSuccess;
 }
@@ -404,9 +404,8 @@ static cudaError_t run_nd(int dims, const Ins<T>& in, cx<T>* out, int64_t B, con
             HDC_TRY(launch_fold_fft_cols<T>(&sides[0], 1, B, Cf, a.mf, a.N, 1, 0, r0, Dg, 0, st));
         }
         HDC_TRY(run_nd<T>(dims - 1, w, wh, Dg * B * a.m, ax + 1, inner, st));
-        HDC_TRY(launch_ifft_cols<T>(wh, B, Cw, a.m, a.q, a.N, Dg, 0, st));
-        HDC_TRY(launch_unfold<T>(out, wh, B, ostride, Cw, a.m, a.pout, a.q, a.N, 1, 0, a.o * Cw,
-                                 (a.o + a.Lw) * Cw, r0, Dg, first, last, scale, st));
+        HDC_TRY(launch_ifft_unfold<T>(wh, out, B, ostride, Cw, a.m, a.pout, a.q, a.N, 1, 0, a.o * Cw,
+                                      (a.o + a.Lw) * Cw, r0, Dg, first, last, scale, 0, st));
     }
     return cudaSuccess;
 }

@@ -364,6 +364,73 @@ __device__ __forceinline__ void ifft_cols_body(V* yb, int64_t Cn, int ma, int q,
     __syncthreads();
 }
 
+// Inverse FFT of size ma along the strided axis and unfold, fused: for the
+// columns c0 .. c0+C-1 of one row, residues r = r0 + rr (rr < Dg) in order:
+// load y_rr = y + rr * rstride (times conj(zeta_{Nf/q}^{l c}) if pre),
+// inverse FFT, then add conj(zeta_Nf^{r (i cs + c cc)}) conj(zeta_q^{r t})
+// h[i][c] to the output at lin = (t ma + i) Cn + c, t < p, lo <= lin < hi,
+// stored at ob[lin - lo]: these outputs belong to this tile alone.  The
+// first residue of the first pass writes instead of adding; the last of the
+// last pass scales.  smem: 2 ma C.
+template <class V>
+__device__ __forceinline__ void ifft_unfold_cols_body(const V* y, int64_t rstride, V* ob, int64_t Cn, int ma, int p,
+                                                      int q, int64_t Nf, int64_t cs, int64_t cc, int64_t lo,
+                                                      int64_t hi, int r0, int Dg, int first, int last,
+                                                      typename real_of<V>::type scale, int64_t c0, int C, int pre,
+                                                      const V* __restrict__ twNf, const V* __restrict__ twma,
+                                                      const V* __restrict__ twmal, const FftPlan& fp, V* smem,
+                                                      int tid, int nthr)
+{
+    V* buf = smem;
+    V* tmp = buf + ma * C;
+    const int64_t mq = Nf / q;
+    constexpr int U = 4;
+    const int n = ma * C;
+    for (int rr = 0; rr < Dg; ++rr) {
+        const int r = r0 + rr;
+        const V* yb = y + (int64_t)rr * rstride;
+        for (int e0 = tid; e0 < n; e0 += U * nthr) {
+            V v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * nthr;
+                const int l = e / C, cl = e - l * C;
+                const int64_t c = c0 + cl;
+                v[u] = (e < n && c < Cn) ? yb[(int64_t)l * Cn + c] : czero<V>();
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * nthr;
+                if (e >= n) break;
+                const int l = e / C, cl = e - l * C;
+                const int64_t c = c0 + cl;
+                if (pre && l != 0 && c != 0 && c < Cn) v[u] = cmulc(v[u], __ldg(twNf + (int64_t)l * c * q));
+                buf[e] = v[u];
+            }
+        }
+        __syncthreads();
+        if (ma > 1) fft_smem<V, true>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);
+        const bool init = first && rr == 0, fin = last && rr == Dg - 1;
+        for (int e = tid; e < n; e += nthr) {
+            const int i = e / C, cl = e - i * C;
+            const int64_t c = c0 + cl;
+            if (c >= Cn) continue;
+            V hv = buf[e];
+            if (r != 0) hv = cmulc(hv, __ldg(twNf + (int64_t)r * (i * cs + c * cc)));
+            for (int t = 0; t < p; ++t) {
+                const int64_t lin = ((int64_t)t * ma + i) * Cn + c;
+                if (lin >= hi) break;
+                if (lin < lo) continue;
+                V v = (r != 0 && t != 0) ? cmulc(hv, __ldg(twNf + (((int64_t)r * t) % q) * mq)) : hv;
+                if (!init) v = cadd(ob[lin - lo], v);
+                if (fin) v = cscale(v, scale);
+                ob[lin - lo] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Unfold of one element (i, c) of one row: the output at linear index
 // lin = (t ma + i) Cn + c, for every t < p with lo <= lin < hi, is
 // sum_{rr < Dg} conj(zeta_Nf^{r (i cs + c cc)}) conj(zeta_q^{r t}) h_rr[i][c]

@@ -39,7 +39,8 @@ FftPlan make_fft_plan(int64_t n);
 // bytes of the launch; when timing is on it also brackets the launch with
 // CUDA events on its stream.
 
-enum KernelId { K_TWIDDLE = 0, K_RESIDUE_ROWS, K_FOLD_FFT_COLS, K_IFFT_COLS, K_UNFOLD, K_BATCHED, K_COUNT };
+enum KernelId { K_TWIDDLE = 0, K_RESIDUE_ROWS, K_FOLD_FFT_COLS, K_IFFT_COLS, K_UNFOLD, K_BATCHED, K_IFFT_UNFOLD,
+                K_COUNT };
 
 struct LaunchScope {
     int kid;
@@ -148,6 +149,18 @@ cudaError_t launch_unfold_real(T* out, const cx<T>* h, int64_t B, int64_t bstrid
 template <typename T>
 cudaError_t launch_ifft_cols(cx<T>* y, int64_t B, int64_t Cn, int64_t ma, int64_t q, int64_t Nf,
                              int64_t D, int pre, cudaStream_t st);
+
+// Inverse column FFTs and unfold in one pass for one residue per pass when
+// the column tiles of all rows give at least two blocks per SM: each block
+// takes a column tile of one row through its inverse FFT and adds its unfold
+// contribution to the outputs only it covers, so the residue's result never
+// goes back to memory (the kernel also runs several residues in order, but
+// that was measured slower than the two passes); otherwise launch_ifft_cols
+// then launch_unfold.  Arguments as for those two.
+template <typename T>
+cudaError_t launch_ifft_unfold(cx<T>* y, cx<T>* out, int64_t B, int64_t bstride, int64_t Cn, int64_t ma, int64_t p,
+                               int64_t q, int64_t Nf, int64_t cs, int64_t cc, int64_t lo, int64_t hi, int64_t r0,
+                               int64_t D, int first, int last, double scale, int pre, cudaStream_t st);
 
 // Unfold-accumulate: the output at lin = (t ma + i) Cn + c, t < p, kept iff
 // lo <= lin < hi and stored at out[b * bstride + lin - lo], gets

@@ -432,6 +432,69 @@ cudaError_t launch_unfold(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstride
     return cudaGetLastError();
 }
 
+// ------------------------------------------ inverse + unfold, fused
+
+template <class V>
+__global__ void __launch_bounds__(kMaxThreads, 2)
+k_ifft_unfold_cols(const V* y, V* out, int64_t B, int64_t bstride, int64_t Cn, int ma, int p, int q, int64_t Nf,
+                   int64_t cs, int64_t cc, int64_t lo, int64_t hi, int r0, int Dg, int first, int last,
+                   typename real_of<V>::type scale, int C, int nct, int pre, const V* __restrict__ twNf,
+                   const V* __restrict__ twma, const V* __restrict__ twmal, FftPlan fp)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    int64_t blk = blockIdx.x;
+    const int ct = (int)(blk % nct);
+    const int64_t b = blk / nct;
+    const int64_t per = (int64_t)ma * Cn;
+    ifft_unfold_cols_body<V>(y + b * per, B * per, out + b * bstride, Cn, ma, p, q, Nf, cs, cc, lo, hi, r0, Dg,
+                             first, last, scale, (int64_t)ct * C, C, pre, twNf, twma, twmal, fp,
+                             reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
+}
+
+template <typename T>
+cudaError_t launch_ifft_unfold(cx<T>* y, cx<T>* out, int64_t B, int64_t bstride, int64_t Cn, int64_t ma, int64_t p,
+                               int64_t q, int64_t Nf, int64_t cs, int64_t cc, int64_t lo, int64_t hi, int64_t r0,
+                               int64_t D, int first, int last, double scale, int pre, cudaStream_t st)
+{
+    using V = cx<T>;
+    const int64_t Dg = (D < q - r0) ? D : (q - r0);
+    if (B <= 0 || Dg <= 0) return cudaSuccess;
+    const int C = col_tile(Cn, ma, col_tile_target<T>());
+    const int nct = (int)((Cn + C - 1) / C);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+        sms = 152;
+    // with several residues per pass the fused form has D times fewer blocks
+    // and re-reads its outputs once per residue: measured slower than the two
+    // passes, so it is taken for one residue per pass only
+    if (Dg != 1 || B * nct < 2 * (int64_t)sms) {
+        cudaError_t e = launch_ifft_cols<T>(y, B, Cn, ma, q, Nf, Dg, pre, st);
+        if (e != cudaSuccess) return e;
+        return launch_unfold<T>(out, y, B, bstride, Cn, ma, p, q, Nf, cs, cc, lo, hi, r0, Dg, first, last, scale, st);
+    }
+    cudaError_t e = cudaSuccess;
+    const V* twNf = twiddles<T>(Nf, &e);
+    if (e != cudaSuccess) return e;
+    const V* twma = twiddles<T>(ma, &e);
+    if (e != cudaSuccess) return e;
+    const V* twmal = twiddles_lf<T>(ma, &e);
+    if (e != cudaSuccess) return e;
+    const FftPlan fp = make_fft_plan(ma);
+    const int thr = threads_for(ma * C);
+    const size_t smem = (size_t)(2 * ma * C) * sizeof(V);
+    auto kern = k_ifft_unfold_cols<V>;
+    if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
+    const double nout = (double)(hi - lo);
+    LaunchScope ls(K_IFFT_UNFOLD, st,
+                   (double)(Dg * B) * ((double)Cn * fft_flops((double)ma) + 8.0 * nout) + (last ? 2.0 * B * nout : 0.0),
+                   ((double)(Dg * B * ma * Cn) + (first ? 1.0 : 2.0) * B * nout) * sizeof(V));
+    kern<<<(unsigned)(B * nct), thr, smem, st>>>(y, out, B, bstride, Cn, (int)ma, (int)p, (int)q, Nf, cs, cc, lo, hi,
+                                                 (int)r0, (int)Dg, first, last, (T)scale, C, nct, pre, twNf, twma,
+                                                 twmal, fp);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------- real inputs
 
 template <typename T> __global__ void k_pack_real(const T* __restrict__ f, const T* __restrict__ g, cx<T>* z, int64_t n)
@@ -753,6 +816,14 @@ HDC_INST_TW(double)
 HDC_INST_TW(float)
 
 // ------------------------------------------------------ instantiations
+
+#define HDC_INST_IU(T)                                                                                    \
+    template cudaError_t launch_ifft_unfold<T>(cx<T>*, cx<T>*, int64_t, int64_t, int64_t, int64_t, int64_t, \
+                                               int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,        \
+                                               int64_t, int64_t, int, int, double, int, cudaStream_t);
+
+HDC_INST_IU(double)
+HDC_INST_IU(float)
 
 #define HDC_INST_REAL(T)                                                                                  \
     template cudaError_t launch_pack_real<T>(const T*, const T*, cx<T>*, int64_t, cudaStream_t);        \

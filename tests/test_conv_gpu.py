@@ -268,3 +268,29 @@ def test_large_integer_bit_exact(hdc):
     h = run(hdc, synth.ints_to_complex(fr, fi), synth.ints_to_complex(gr, gi), 1, 1 << 21)
     assert np.array_equal(np.rint(h.real).astype(np.int64), hr)
     assert np.array_equal(np.rint(h.imag).astype(np.int64), hi)
+
+
+def test_fused_inverse_unfold_against_separate_passes(hdc):
+    """Split-route sizes with enough column tiles (m1 = 320 or 512 columns
+    of 2048-point rows) and one residue per pass take the fused inverse +
+    unfold kernel; their results match the oracle, beside several residues
+    per pass (the separate passes) and a window that starts past the input
+    length."""
+    hdc.stats_reset()
+    hdc.stats_timing(True)
+    L = 600000
+    f = synth.unit_disk(5101, (L,))
+    g = synth.unit_disk(5102, (L,))
+    fp = np.concatenate([f, np.zeros(L, dtype=complex)])
+    gp = np.concatenate([g, np.zeros(L, dtype=complex)])
+    full = oracle.conv_fft(fp, gp)
+    for m, D in ((1048576, 0), (1048576, 1), (655360, 0)):
+        h = run(hdc, f, g, 1, m, D=D)
+        assert rel_max_err(h, full[:L]) < TOL64, (m, D)
+    ft = torch.from_numpy(f).cuda()
+    gt = torch.from_numpy(g).cuda()
+    hw = hdc.convnd_window(ft, gt, 1, 1048576, 200000, 700000, M=2 * L - 1).cpu().numpy()
+    assert rel_max_err(hw, full[200000:900000]) < TOL64
+    torch.cuda.synchronize()
+    hdc.stats_timing(False)
+    assert hdc.stats()["k_ifft_unfold_cols"]["launches"] > 0
