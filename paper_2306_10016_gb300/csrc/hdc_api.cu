@@ -313,13 +313,13 @@ static cudaError_t run_rows(const Ins<T>& in, cx<T>* out, int64_t B, int64_t ld_
         for (int64_t r0 = r_lo; r0 < r_hi; r0 += a.D) {
             const int64_t Dp = (a.D < r_hi - r0) ? a.D : (r_hi - r0);
             const int first = (r0 == r_lo), last = (r0 + Dp >= r_hi);
-            // with one transform size the fold runs over the longer input's
-            // blocks; the inputs commute, so the longer one goes second
             if (in.n > 2)
                 HDC_TRY(launch_residue_rows_multi<T>(in.x, in.n, in.op, ws, B, ld_g, a.L, a.m, a.p, a.q, r0, Dp, st));
             else if (a.lam == 1 && a.Lf <= a.L)
                 HDC_TRY(launch_residue_rows<T>(f, g, ws, B, ld_f, ld_g, a.Lf, a.L, a.m, a.p, a.q, r0, Dp, st));
-            else if (a.lam == 1)
+            else if (a.lam == 1) // one transform size: the fold runs over the
+                                 // longer input's blocks, so (as the inputs
+                                 // commute) the longer one goes second
                 HDC_TRY(launch_residue_rows<T>(g, f, ws, B, ld_g, ld_f, a.L, a.Lf, a.m, a.pf, a.q, r0, Dp, st));
             else
                 HDC_TRY(launch_residue_rows_lam<T>(f, g, ws, B, ld_f, ld_g, a.Lf, a.L, a.mf, a.lam, a.pf, a.p, a.q,
@@ -331,8 +331,8 @@ static cudaError_t run_rows(const Ins<T>& in, cx<T>* out, int64_t B, int64_t ld_
     }
     // m = m1 m2: fold + m1-point FFTs along the strided view [p m1][m2] with the
     // inner twiddle zeta_m^{l1 s2}; m2-point row transforms, product and
-    // inverse; inverse m1-point FFTs and unfold (one fused pass when there are
-    // enough column tiles).  With lam > 1, f's transform
+    // inverse; inverse m1-point FFTs and unfold (one fused pass for one residue
+    // per pass when there are enough column tiles).  With lam > 1, f's transform
     // splits as (m1 / lam) m2 and its row l1' of residue q l + r lands on row
     // lam l1' + l, next to the row of g it multiplies.  Input i works in
     // y[i] = ws + i D B m; the product lands in y[0].
