@@ -131,10 +131,14 @@ int hdc_validate_axis(int64_t L, int64_t M, int64_t m, int64_t p, int64_t q,
                       int64_t D, int dtype, int64_t* p_out, int64_t* q_out,
                       int64_t* D_out);
 
-/* Largest FFT size m and padded size q m accepted for a dtype.  An axis that
- * has inner axes (all but the last of a 2-D / 3-D call) runs its m-point
- * FFT in one column tile: m <= hdc_max_outer_fft_size (4096 for
- * complex<double>, 8192 for complex<float>), else HDC_ERR_UNSUPPORTED_SIZE. */
+/* Largest FFT size m and padded size q m accepted for a dtype: m up to
+ * 2^23 for complex<double> and 2^25 for complex<float> (the product of the
+ * row and column tile limits; a larger m, or one that does not factor as a
+ * row length <= 2048 / 4096 times a column length <= 4096 / 8192, is
+ * HDC_ERR_UNSUPPORTED_SIZE), q m up to 2^25 / 2^26.  An axis that has inner
+ * axes (all but the last of a 2-D / 3-D call) runs its m-point FFT in one
+ * column tile: m <= hdc_max_outer_fft_size (4096 for complex<double>, 8192
+ * for complex<float>), else HDC_ERR_UNSUPPORTED_SIZE. */
 int64_t hdc_max_fft_size(int dtype);
 int64_t hdc_max_padded_size(int dtype);
 int64_t hdc_max_outer_fft_size(int dtype);

@@ -179,7 +179,14 @@ static void route(const Axis& a, int64_t B, int dtype, int64_t* m1, int64_t* m2)
     else route_for<float>(a, B, m1, m2);
 }
 
-static int64_t max_fft(int dtype) { return dtype == HDC_C128 ? (int64_t)1 << 24 : (int64_t)1 << 25; }
+// the largest split m1 m2 within the row and column tile limits (2^23 in
+// FP64, 2^25 in FP32); an m of that size whose factors do not fit both
+// limits is still rejected when the axis is resolved
+static int64_t max_fft(int dtype)
+{
+    return dtype == HDC_C128 ? max_row_fft<double>() * max_col_fft<double>()
+                             : max_row_fft<float>() * max_col_fft<float>();
+}
 static int64_t max_padded(int dtype) { return dtype == HDC_C128 ? (int64_t)1 << 25 : (int64_t)1 << 26; }
 
 // One axis.  The output window [o, o + Lw) of the full linear convolution

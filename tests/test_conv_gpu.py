@@ -294,3 +294,22 @@ def test_fused_inverse_unfold_against_separate_passes(hdc):
     torch.cuda.synchronize()
     hdc.stats_timing(False)
     assert hdc.stats()["k_ifft_unfold_cols"]["launches"] > 0
+
+
+@pytest.mark.parametrize("dtype", [np.complex128, np.complex64])
+def test_maximum_transform_size(hdc, dtype):
+    """The largest transform of each dtype (2^23 points in FP64, 2^25 in
+    FP32, one split into the largest row and column tiles): L = m / 2 with
+    q = 1 and L = m with q = 2, sampled outputs against O1; one size more is
+    rejected."""
+    dt = hdc.HDC_C128 if dtype == np.complex128 else hdc.HDC_C64
+    mx = hdc.max_fft_size(dt)
+    tol = TOL64 if dtype == np.complex128 else TOL32
+    rng = np.random.default_rng(11)
+    for L, q in ((mx // 2, 1), (mx, 2)):
+        f = synth.unit_disk(5201, (L,))
+        g = synth.unit_disk(5202, (L,))
+        h = run(hdc, f, g, 1, mx, dtype=dtype)
+        idx = np.concatenate([[0, 1, L - 1], rng.integers(0, L, 21)]).astype(np.int64)
+        assert rel_max_err(h[idx], oracle.conv_direct_at(f, g, idx)) < tol, (L, q)
+    assert hdc.validate_axis(mx, 2 * mx - 1, 2 * mx, dtype=dt)[0] == hdc.HDC_ERR_UNSUPPORTED_SIZE
