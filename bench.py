@@ -41,7 +41,7 @@ FP32_FMA_PER_CLK = 128
 # dominant kernel, averaged over its launches in one ncu capture of this
 # sweep's timed steps (eager launches); to be re-taken whenever that kernel
 # changes (and None until then).
-NCU_TRAFFIC_PER_LAUNCH = {"k_residue_rows": 4.463e+07}
+NCU_TRAFFIC_PER_LAUNCH = {"k_residue_rows": 4.461e+07}
 
 
 def sweep_sizes():
@@ -637,12 +637,21 @@ def main():
         pinned.append((f, g, torch.empty_like(f).pin_memory()))
     wsh = max(hdc.workspace_size_host([L], [2 * L - 1], [p.params[0]["m"]], D=[p.params[0]["D"]])
               for L, p in zip(sizes, plans64))
-    wsh_t = torch.empty(wsh, dtype=torch.uint8, device=dev)
+    # the sizes rotate over three streams, each with its own workspace, so
+    # one size's host copies overlap another's kernels; one synchronisation
+    # per step
+    n_e2e_streams = 3
+    e2e_streams = [torch.cuda.Stream(dev) for _ in range(n_e2e_streams)]
+    wsh_ts = [torch.empty(wsh, dtype=torch.uint8, device=dev) for _ in range(n_e2e_streams)]
 
     def e2e_step():
-        for L, p, (f, g, h) in zip(sizes, plans64, pinned):
+        for i, (L, p, (f, g, h)) in enumerate(zip(sizes, plans64, pinned)):
             prm = p.params[0]
-            hdc.convnd_host(f, g, h, 1, prm["m"], p=prm["p"], q=prm["q"], D=prm["D"], workspace=wsh_t)
+            k = i % n_e2e_streams
+            hdc.convnd_host(f, g, h, 1, prm["m"], p=prm["p"], q=prm["q"], D=prm["D"], workspace=wsh_ts[k],
+                            stream=e2e_streams[k], sync=False)
+        for s_ in e2e_streams:
+            s_.synchronize()
 
     for _ in range(args.warmup):
         e2e_step()
@@ -656,6 +665,25 @@ def main():
     e2e_s = rank_max((time.perf_counter() - t0) / args.steps)
     h2d = sum(2 * L * 16 for L in sizes)
     d2h = sum(L * 16 for L in sizes)
+    # the same host copies alone (same buffers, sizes and streams, no
+    # convolution): what the overlap in the end-to-end step hides
+    dbufs = [(torch.empty_like(f, device=dev), torch.empty_like(g, device=dev)) for f, g, _ in pinned]
+
+    def copies_step():
+        for i, ((f, g, h), (df, dg)) in enumerate(zip(pinned, dbufs)):
+            with torch.cuda.stream(e2e_streams[i % n_e2e_streams]):
+                df.copy_(f, non_blocking=True)
+                dg.copy_(g, non_blocking=True)
+                h.copy_(df, non_blocking=True)
+        for s_ in e2e_streams:
+            s_.synchronize()
+
+    copies_step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        copies_step()
+    copy_s = rank_max((time.perf_counter() - t0) / args.steps)
+    del dbufs
 
     # --- roofline of the dominant kernel (FP64 ALU bound)
     dom = max((k for k in kstats if kstats[k]["ms"] > 0), key=lambda k: kstats[k]["ms"])
@@ -709,7 +737,9 @@ def main():
         "per_size_fp64": per_size,
         "roofline": roofline,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * outs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": world * outs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "streams": n_e2e_streams, "ms_per_step": round(e2e_s * 1e3, 4),
+                "copies_alone_ms_per_step": round(copy_s * 1e3, 4)},
         "gpu_launches": launches,
         "clocks": clocks,
         "step_ms": [round(x, 4) for x in ms_list],

@@ -660,10 +660,13 @@ def workspace_size_host(L, M, m, p=0, q=0, D=0, dtype=HDC_C128, batch=1) -> int:
     return nb.value
 
 
-def convnd_host(f, g, h, dims, m, M=None, p=0, q=0, D=0, workspace=None, stream=None):
+def convnd_host(f, g, h, dims, m, M=None, p=0, q=0, D=0, workspace=None, stream=None, sync=True):
     """The convolution on host tensors f, g -> h (CPU torch tensors, pinned
     for overlap); copies in, convolution and copy out all run through one C
-    call on the device.  Synchronises the stream before returning."""
+    call on the device.  With sync (default) the stream is synchronised
+    before returning; without it h is valid once the stream has reached this
+    point, so calls on several streams (each with its own workspace) overlap
+    one call's copies with another's kernels."""
     torch = _torch()
     for t in (f, g, h):
         if t.is_cuda or not t.is_contiguous():
@@ -682,7 +685,8 @@ def convnd_host(f, g, h, dims, m, M=None, p=0, q=0, D=0, workspace=None, stream=
     _check(lib().hdc_convnd_host(dims, f.data_ptr(), g.data_ptr(), h.data_ptr(), _arr(L), _arr(Mv),
                                  *[_arr(a) for a in args], dt, batch, workspace.data_ptr(),
                                  workspace.numel() * workspace.element_size(), st.cuda_stream), "convnd_host")
-    st.synchronize()
+    if sync:
+        st.synchronize()
     return h
 
 
