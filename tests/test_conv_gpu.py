@@ -313,3 +313,31 @@ def test_maximum_transform_size(hdc, dtype):
         idx = np.concatenate([[0, 1, L - 1], rng.integers(0, L, 21)]).astype(np.int64)
         assert rel_max_err(h[idx], oracle.conv_direct_at(f, g, idx)) < tol, (L, q)
     assert hdc.validate_axis(mx, 2 * mx - 1, 2 * mx, dtype=dt)[0] == hdc.HDC_ERR_UNSUPPORTED_SIZE
+
+
+def test_brute_force_all_tuples_up_to_64(hdc):
+    """Every L <= 64, M in {2L-1, 2L+1, 3L, 4L}, every valid m up to
+    nextgood(M), D in {1, 2, q}: FP64 against O1 within 1e-12, and for
+    integer inputs the rounded result equals the exact convolution for every
+    tuple (every tuple gives the same integers)."""
+    n = 0
+    for L in range(1, 65):
+        f = synth.unit_disk(7000 + L, (L,))
+        g = synth.unit_disk(8000 + L, (L,))
+        ref = oracle.conv_direct(f, g)
+        fre, fim = synth.small_ints(9000 + L, (L,))
+        gre, gim = synth.small_ints(9500 + L, (L,))
+        ire, iim = oracle.conv_int_exact(fre, fim, gre, gim, method="direct")
+        fi = fre + 1j * fim
+        gi = gre + 1j * gim
+        for M in sorted({2 * L - 1, 2 * L + 1, 3 * L, 4 * L}):
+            for m in good_sizes(1, hdc.next_good_size(M)):
+                q = -(-M // m)
+                for D in sorted({1, min(2, q), q}):
+                    h = run(hdc, f, g, 1, m, M=M, D=D)
+                    assert rel_max_err(h, ref) < TOL64, (L, M, m, D)
+                    n += 1
+                hi = run(hdc, fi, gi, 1, m, M=M)
+                assert np.array_equal(np.rint(hi.real).astype(np.int64), ire), (L, M, m)
+                assert np.array_equal(np.rint(hi.imag).astype(np.int64), iim), (L, M, m)
+    assert n > 20000
