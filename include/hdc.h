@@ -649,6 +649,23 @@ int64_t hdc_stats_total_launches(void);
 int hdc_stats_get(int id, int64_t* launches, double* ms, double* flops,
                   double* bytes);
 
+/* -------------------------------------------------------- load path, status
+ * The strided fold (the column pass of a split axis and of the outer axes
+ * of 2-D/3-D) stages its tiles in shared memory with TMA tensor copies when
+ * the input meets the copy rules (16-byte aligned base and row strides,
+ * at most two fold blocks per tile), else with plain loads; both give the
+ * same result.  hdc_set_tma(0) forces the plain loads for later launches,
+ * hdc_set_tma(1) (the default) allows the copies.  Not thread-safe against
+ * launches in flight on other host threads.
+ *
+ * A kernel whose wait for a copy runs past about a second records
+ * HDC_ERR_TIMEOUT in a device status word instead of waiting on (the
+ * launch's output is then not valid).  hdc_device_status stores the word
+ * (0 when no kernel gave up) in *status after synchronising with the
+ * device's current work, and clears it if `clear` is non-zero. */
+int hdc_set_tma(int enable);
+int hdc_device_status(int* status, int clear);
+
 /* ------------------------------------------------------------ measurement
  * Vector FMA throughput probe: the arithmetic roofline of this path (it runs
  * on the FP64/FP32 pipes, not on tensor cores).  Launches `blocks` x

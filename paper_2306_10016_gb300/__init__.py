@@ -202,6 +202,8 @@ _SIGS += [
                                       _i64p, _i64p, _i64p]),
     ("hdc_convnd_residues", C.c_int, [C.c_int, _vp, _vp, _vp, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, _i64, _i64,
                                       C.c_int, _i64, _vp, _sz, _vp]),
+    ("hdc_set_tma", C.c_int, [C.c_int]),
+    ("hdc_device_status", C.c_int, [C.POINTER(C.c_int), C.c_int]),
     ("hdc_stats_reset", C.c_int, []),
     ("hdc_stats_timing", C.c_int, [C.c_int]),
     ("hdc_stats_kernel_count", C.c_int, []),
@@ -1113,6 +1115,22 @@ class MLP:
         if getattr(self, "_h", None) and _lib is not None:
             _lib.hdc_mlp_destroy(self._h)
             self._h = None
+
+
+# ------------------------------------------------------ load path, status
+
+def set_tma(enable: bool) -> None:
+    """Allow (default) or forbid the TMA-staged loads of the strided fold
+    for later launches; both paths give the same result."""
+    _check(lib().hdc_set_tma(int(bool(enable))), "set_tma")
+
+
+def device_status(clear: bool = True) -> int:
+    """0, or HDC_ERR_TIMEOUT if a kernel gave up waiting for a copy since the
+    last clear (synchronises with the device)."""
+    st = C.c_int()
+    _check(lib().hdc_device_status(C.byref(st), int(bool(clear))), "device_status")
+    return st.value
 
 
 # ------------------------------------------------------- launch statistics

@@ -191,9 +191,12 @@ template <typename T> bool batched_route(int64_t m, int64_t* m1, int64_t* m2)
     return false;
 }
 
+// Column tile of the batched kernel: as wide as the tile budget allows (up
+// to 256 columns), since its blocks always have kMaxThreads threads: a short
+// axis then still gives whole warps of butterflies.
 template <typename T> int col_tile_b(int64_t Cn, int64_t ma)
 {
-    int64_t C = 16;
+    int64_t C = 256;
     while (C > 1 && ma * C > batched_col_elems<T>()) C >>= 1;
     while (C > 1 && C / 2 >= Cn) C >>= 1;
     return (int)C;
@@ -252,8 +255,8 @@ template <typename T> int build(hdc_batched* b)
         b->m1[i] = m1;
         b->m2[i] = m2;
         convs[(size_t)i] = cv;
-        smem = std::max(smem, (size_t)(3 * padded_len(m1 ? m2 : b->m[i])) * sizeof(V));
-        if (m1) smem = std::max(smem, (size_t)(2 * m1 * cv.C) * sizeof(V));
+        smem = std::max(smem, (size_t)(3 * smem_len<V>(m1 ? m2 : b->m[i])) * sizeof(V));
+        if (m1) smem = std::max(smem, (size_t)(2 * smem_len<V>(m1 * cv.C)) * sizeof(V));
         cost.emplace_back((double)cv.q * cv.m * std::log2((double)cv.m + 1.0) + (double)cv.q * cv.L, i);
     }
     // largest convolutions first in every phase: the tail of each phase is

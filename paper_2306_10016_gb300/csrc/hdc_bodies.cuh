@@ -12,7 +12,7 @@ namespace hdc {
 // One residue r of one row: fold (Eq. 1 inner sum, then zeta_N^{r s}) of f
 // and g, m-point forward FFTs, pointwise product (Section 2.4), inverse FFT
 // (Eq. 2 inner sum); the unscaled result goes to hr[0..m).  smem: three
-// padded buffers of m (3 padded_len(m) elements).  g has L valid elements,
+// swizzled buffers of m (3 smem_len(m) elements).  g has L valid elements,
 // f has Lf <= L (zero beyond).  With p = q = 1 and Lf = L >= m the fold is a
 // plain copy of the rows.
 template <class V>
@@ -21,15 +21,15 @@ __device__ __forceinline__ void residue_row_body(const V* fr, const V* gr, V* hr
                                                  const V* __restrict__ twml, const FftPlan& fp, V* smem, int tid,
                                                  int nthr)
 {
-    const int plen = (int)padded_len(m);
+    const int plen = (int)smem_len<V>(m);
     V* sa = smem;
     V* sb = sa + plen;
     V* sc = sb + plen;
     if (p == 1 && q == 1 && L >= m && Lf == L) {
 #pragma unroll 4
         for (int s = tid; s < m; s += nthr) {
-            sa[sidx<true>(s)] = fr[s];
-            sb[sidx<true>(s)] = gr[s];
+            sa[sidx<V, true>(s)] = fr[s];
+            sb[sidx<V, true>(s)] = gr[s];
         }
     } else {
         for (int s = tid; s < m; s += nthr) {
@@ -53,22 +53,22 @@ __device__ __forceinline__ void residue_row_body(const V* fr, const V* gr, V* hr
                 af = cmul(af, w);
                 ag = cmul(ag, w);
             }
-            sa[sidx<true>(s)] = af;
-            sb[sidx<true>(s)] = ag;
+            sa[sidx<V, true>(s)] = af;
+            sb[sidx<V, true>(s)] = ag;
         }
     }
     __syncthreads();
     fft_smem<V, false, true>(sa, sc, fp, 1, 1, m, twm, twml, tid, nthr);
     fft_smem<V, false, true>(sb, sc, fp, 1, 1, m, twm, twml, tid, nthr);
-    for (int s = tid; s < m; s += nthr) sa[sidx<true>(s)] = cmul(sa[sidx<true>(s)], sb[sidx<true>(s)]);
+    for (int s = tid; s < m; s += nthr) sa[sidx<V, true>(s)] = cmul(sa[sidx<V, true>(s)], sb[sidx<V, true>(s)]);
     __syncthreads();
     fft_smem<V, true, true>(sa, sc, fp, 1, 1, m, twm, twml, tid, nthr);
-    for (int s = tid; s < m; s += nthr) hr[s] = sa[sidx<true>(s)];
+    for (int s = tid; s < m; s += nthr) hr[s] = sa[sidx<V, true>(s)];
     __syncthreads();
 }
 
 // Fold (Eq. 1 inner sum) of one input row x of L valid elements into the
-// padded buffer dst: dst[s] = zeta_N^{r s} sum_{t < p} zeta_q^{r t} x[t m + s],
+// swizzled buffer dst: dst[s] = zeta_N^{r s} sum_{t < p} zeta_q^{r t} x[t m + s],
 // s < m, with N = q m; no barrier.
 template <class V>
 __device__ __forceinline__ void fold_row(const V* x, int64_t L, int m, int p, int q, int r, const V* __restrict__ twN,
@@ -83,7 +83,7 @@ __device__ __forceinline__ void fold_row(const V* x, int64_t L, int m, int p, in
             else a = cfma(x[j], __ldg(twN + (((int64_t)r * t) % q) * m), a);
         }
         if (r != 0) a = cmul(a, __ldg(twN + (int64_t)r * s));
-        dst[sidx<true>(s)] = a;
+        dst[sidx<V, true>(s)] = a;
     }
 }
 
@@ -98,7 +98,7 @@ template <class V> struct InPtrs {
 // nin-fold convolution) or the sum of the pairwise products
 // F_0 F_1 + F_2 F_3 + ... (op 1, nin even); inverse FFT; the unscaled result
 // goes to hr[0..m).  The sum accumulates in hr itself (each thread owns the
-// same elements in every pass).  smem: three padded buffers of m.
+// same elements in every pass).  smem: three swizzled buffers of m.
 template <class V>
 __device__ __forceinline__ void residue_row_multi_body(const InPtrs<V>& in, int nin, int op, int64_t boff, V* hr,
                                                        int64_t L, int m, int p, int q, int r,
@@ -106,7 +106,7 @@ __device__ __forceinline__ void residue_row_multi_body(const InPtrs<V>& in, int 
                                                        const V* __restrict__ twml, const FftPlan& fp, V* smem,
                                                        int tid, int nthr)
 {
-    const int plen = (int)padded_len(m);
+    const int plen = (int)smem_len<V>(m);
     V* sa = smem;
     V* sb = sa + plen;
     V* sc = sb + plen;
@@ -117,21 +117,21 @@ __device__ __forceinline__ void residue_row_multi_body(const InPtrs<V>& in, int 
         __syncthreads();
         fft_smem<V, false, true>(dst, sc, fp, 1, 1, m, twm, twml, tid, nthr);
         if (op == 0 && i > 0) {
-            for (int s = tid; s < m; s += nthr) sa[sidx<true>(s)] = cmul(sa[sidx<true>(s)], sb[sidx<true>(s)]);
+            for (int s = tid; s < m; s += nthr) sa[sidx<V, true>(s)] = cmul(sa[sidx<V, true>(s)], sb[sidx<V, true>(s)]);
             __syncthreads();
         } else if (op == 1 && (i & 1)) {
             for (int s = tid; s < m; s += nthr) {
-                const V v = cmul(sa[sidx<true>(s)], sb[sidx<true>(s)]);
+                const V v = cmul(sa[sidx<V, true>(s)], sb[sidx<V, true>(s)]);
                 hr[s] = (i == 1) ? v : cadd(hr[s], v);
             }
             __syncthreads();
         }
     }
     if (op == 1)
-        for (int s = tid; s < m; s += nthr) sa[sidx<true>(s)] = hr[s];
+        for (int s = tid; s < m; s += nthr) sa[sidx<V, true>(s)] = hr[s];
     __syncthreads();
     fft_smem<V, true, true>(sa, sc, fp, 1, 1, m, twm, twml, tid, nthr);
-    for (int s = tid; s < m; s += nthr) hr[s] = sa[sidx<true>(s)];
+    for (int s = tid; s < m; s += nthr) hr[s] = sa[sidx<V, true>(s)];
     __syncthreads();
 }
 
@@ -143,7 +143,7 @@ __device__ __forceinline__ void residue_row_multi_body(const InPtrs<V>& in, int 
 // qg l + rg of f, l = 0 .. lam-1.  One block: fold g (residue rg), mg-point
 // FFT; for each l: fold f (residue qg l + rg), mf-point FFT, multiply into
 // the bins lam lf + l; inverse mg-point FFT; unscaled result to hr[0..mg).
-// smem: three padded buffers of mg.
+// smem: three swizzled buffers of mg.
 template <class V>
 __device__ __forceinline__ void residue_row_lam_body(const V* fr, const V* gr, V* hr, int64_t Lf, int64_t Lg, int mf,
                                                      int mg, int lam, int pf, int pg, int qg, int rg,
@@ -152,7 +152,7 @@ __device__ __forceinline__ void residue_row_lam_body(const V* fr, const V* gr, V
                                                      const V* __restrict__ twg, const V* __restrict__ twgl,
                                                      const FftPlan& fpg, V* smem, int tid, int nthr)
 {
-    const int plen = (int)padded_len(mg);
+    const int plen = (int)smem_len<V>(mg);
     V* sa = smem;
     V* sb = sa + plen;
     V* sc = sb + plen;
@@ -165,13 +165,13 @@ __device__ __forceinline__ void residue_row_lam_body(const V* fr, const V* gr, V
         __syncthreads();
         fft_smem<V, false, true>(sb, sc, fpf, 1, 1, mf, twf, twfl, tid, nthr);
         for (int lf = tid; lf < mf; lf += nthr) {
-            const int k = sidx<true>(lf * lam + l);
-            sa[k] = cmul(sa[k], sb[sidx<true>(lf)]);
+            const int k = sidx<V, true>(lf * lam + l);
+            sa[k] = cmul(sa[k], sb[sidx<V, true>(lf)]);
         }
         __syncthreads();
     }
     fft_smem<V, true, true>(sa, sc, fpg, 1, 1, mg, twg, twgl, tid, nthr);
-    for (int s = tid; s < mg; s += nthr) hr[s] = sa[sidx<true>(s)];
+    for (int s = tid; s < mg; s += nthr) hr[s] = sa[sidx<V, true>(s)];
     __syncthreads();
 }
 
@@ -191,14 +191,14 @@ template <class V> __device__ __forceinline__ V real_pair_product(V a, V b)
 // of residue r and of its conjugate partner r' = (q - r) mod q, F and G from
 // the pair (bin l of r against bin (m - l) mod m of r' = 0 when r = 0, bin
 // m - 1 - l of r' otherwise), H = F G, inverse FFT; the unscaled result goes
-// to hr[0..m).  smem: three padded buffers of m.
+// to hr[0..m).  smem: three swizzled buffers of m.
 template <class V>
 __device__ __forceinline__ void residue_row_real_body(const V* zr, V* hr, int64_t L, int m, int p, int q, int r,
                                                       const V* __restrict__ twN, const V* __restrict__ twm,
                                                       const V* __restrict__ twml, const FftPlan& fp, V* smem, int tid,
                                                       int nthr)
 {
-    const int plen = (int)padded_len(m);
+    const int plen = (int)smem_len<V>(m);
     V* sa = smem;
     V* sb = sa + plen;
     V* sc = sb + plen;
@@ -215,30 +215,30 @@ __device__ __forceinline__ void residue_row_real_body(const V* zr, V* hr, int64_
     }
     for (int l = tid; l < m; l += nthr) {
         const int lp = r == 0 ? (m - l) % m : m - 1 - l;
-        sc[sidx<true>(l)] = real_pair_product(sa[sidx<true>(l)], pb[sidx<true>(lp)]);
+        sc[sidx<V, true>(l)] = real_pair_product(sa[sidx<V, true>(l)], pb[sidx<V, true>(lp)]);
     }
     __syncthreads();
     fft_smem<V, true, true>(sc, sa, fp, 1, 1, m, twm, twml, tid, nthr);
-    for (int s = tid; s < m; s += nthr) hr[s] = sc[sidx<true>(s)];
+    for (int s = tid; s < m; s += nthr) hr[s] = sc[sidx<V, true>(s)];
     __syncthreads();
 }
 
 // Split route, real inputs: row l1 of kept residue r (ya, after the column
 // pass) against row l1' of its partner (yb): m2-point FFTs of both, H = F G
 // per bin (bin l2 against (m2 - l2) mod m2 when r = 0 and l1 = 0, else
-// m2 - 1 - l2), inverse FFT into yh.  smem: three padded buffers of m2.
+// m2 - 1 - l2), inverse FFT into yh.  smem: three swizzled buffers of m2.
 template <class V>
 __device__ __forceinline__ void rows_real_pair_body(const V* ya, const V* yb, V* yh, int m2, int r, int l1,
                                                     const V* __restrict__ twm, const V* __restrict__ twml,
                                                     const FftPlan& fp, V* smem, int tid, int nthr)
 {
-    const int plen = (int)padded_len(m2);
+    const int plen = (int)smem_len<V>(m2);
     V* sa = smem;
     V* sb = sa + plen;
     V* sc = sb + plen;
     for (int s = tid; s < m2; s += nthr) {
-        sa[sidx<true>(s)] = ya[s];
-        sb[sidx<true>(s)] = yb[s];
+        sa[sidx<V, true>(s)] = ya[s];
+        sb[sidx<V, true>(s)] = yb[s];
     }
     __syncthreads();
     fft_smem<V, false, true>(sa, sc, fp, 1, 1, m2, twm, twml, tid, nthr);
@@ -246,18 +246,44 @@ __device__ __forceinline__ void rows_real_pair_body(const V* ya, const V* yb, V*
     const bool wrap = r == 0 && l1 == 0;
     for (int l = tid; l < m2; l += nthr) {
         const int lp = wrap ? (m2 - l) % m2 : m2 - 1 - l;
-        sc[sidx<true>(l)] = real_pair_product(sa[sidx<true>(l)], sb[sidx<true>(lp)]);
+        sc[sidx<V, true>(l)] = real_pair_product(sa[sidx<V, true>(l)], sb[sidx<V, true>(lp)]);
     }
     __syncthreads();
     fft_smem<V, true, true>(sc, sa, fp, 1, 1, m2, twm, twml, tid, nthr);
-    for (int s = tid; s < m2; s += nthr) yh[s] = sc[sidx<true>(s)];
+    for (int s = tid; s < m2; s += nthr) yh[s] = sc[sidx<V, true>(s)];
+    __syncthreads();
+}
+
+// Loads a thread of a column-tile body keeps in flight at a time: an FP32
+// tile needs more of them to cover the memory latency.
+template <class V> constexpr int kColLoads = sizeof(V) == 8 ? 8 : 4;
+
+// Second half of the strided fold + FFT pass: the folded tile (ma x C,
+// element i C + cl) is in buf and the block is synchronised; FFT of size ma
+// over the tile's columns, then column c0 + cl (< Cn) of row l goes to
+// yb[l ystride + c], times zeta_{Nf/q}^{l c} if post.
+template <class V>
+__device__ __forceinline__ void fft_cols_store_body(V* buf, V* tmp, V* yb, int64_t Cn, int ma, int q, int64_t c0,
+                                                    int C, int post, int64_t ystride, const V* __restrict__ twNf,
+                                                    const V* __restrict__ twma, const V* __restrict__ twmal,
+                                                    const FftPlan& fp, int tid, int nthr)
+{
+    if (ma > 1) fft_smem<V, false>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);
+    for (int e = tid; e < ma * C; e += nthr) {
+        const int l = e / C, cl = e - l * C;
+        const int64_t c = c0 + cl;
+        if (c >= Cn) continue;
+        V v = buf[e];
+        if (post && l != 0 && c != 0) v = cmul(v, __ldg(twNf + (int64_t)l * c * q));
+        yb[(int64_t)l * ystride + c] = v;
+    }
     __syncthreads();
 }
 
 // Fold along a strided axis and FFT of size ma over it, for the columns
 // c0 .. c0+C-1 (< Cn) of one input x (view x[a][c], a = t ma + i, element
 // valid iff a Cn + c < Lvalid); residue r; result to yb[l ystride + c],
-// times zeta_{Nf/q}^{l c} if post.  smem: 2 ma C.
+// times zeta_{Nf/q}^{l c} if post.  smem: 2 smem_len(ma C).
 template <class V>
 __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn, int ma, int p, int q, int64_t Nf,
                                                    int64_t cs, int64_t cc, int64_t Lvalid, int r, int64_t c0, int C,
@@ -266,10 +292,12 @@ __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn
                                                    const FftPlan& fp, V* smem, int tid, int nthr)
 {
     V* buf = smem;
-    V* tmp = buf + ma * C;
+    V* tmp = buf + smem_len<V>(ma * C);
     const int64_t mq = Nf / q;
     // four elements per thread at a time, so their loads are in flight
-    // together; element e = i C + cl of the tile is column c0 + cl, row i
+    // together (in FP32 also two fold blocks of each: the FP32 pass is bound
+    // by memory latency, the FP64 one by its arithmetic, which this would
+    // slow); element e = i C + cl of the tile is column c0 + cl, row i
     constexpr int U = 4;
     const int n = ma * C;
     for (int e0 = tid; e0 < n; e0 += U * nthr) {
@@ -281,18 +309,41 @@ __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn
             const int i = e / C, cl = e - i * C;
             const int64_t c = c0 + cl;
             base[u] = (e < n && c < Cn) ? (int64_t)i * Cn + c : -1;
-            // block t = 0 carries zeta_q^0 = 1: no multiplication
-            acc[u] = (base[u] >= 0 && base[u] < Lvalid) ? x[base[u]] : czero<V>();
         }
-        for (int t = 1; t < p; ++t) {
-            const int64_t off = (int64_t)t * ma * Cn;
-            if (off >= Lvalid) break;
-            const V w = r == 0 ? czero<V>() : __ldg(twNf + (((int64_t)r * t) % q) * mq);
+        if constexpr (sizeof(V) == 8) {
+            for (int t = 0; t < p; t += 2) {
+                const int64_t off = (int64_t)t * ma * Cn, off2 = off + (int64_t)ma * Cn;
+                V xa[U], xb[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (base[u] < 0 || base[u] + off >= Lvalid) continue;
-                const V xv = x[base[u] + off];
-                acc[u] = r == 0 ? cadd(acc[u], xv) : cfma(xv, w, acc[u]);
+                for (int u = 0; u < U; ++u) {
+                    xa[u] = (base[u] >= 0 && base[u] + off < Lvalid) ? x[base[u] + off] : czero<V>();
+                    xb[u] = (t + 1 < p && base[u] >= 0 && base[u] + off2 < Lvalid) ? x[base[u] + off2] : czero<V>();
+                }
+                // block t = 0 carries zeta_q^0 = 1: no multiplication
+                const V wa = (r == 0 || t == 0) ? czero<V>() : __ldg(twNf + (((int64_t)r * t) % q) * mq);
+                const V wb = r == 0 ? czero<V>() : __ldg(twNf + (((int64_t)r * (t + 1)) % q) * mq);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (t == 0) acc[u] = xa[u];
+                    else acc[u] = r == 0 ? cadd(acc[u], xa[u]) : cfma(xa[u], wa, acc[u]);
+                    if (t + 1 < p) acc[u] = r == 0 ? cadd(acc[u], xb[u]) : cfma(xb[u], wb, acc[u]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                // block t = 0 carries zeta_q^0 = 1: no multiplication
+                acc[u] = (base[u] >= 0 && base[u] < Lvalid) ? x[base[u]] : czero<V>();
+            for (int t = 1; t < p; ++t) {
+                const int64_t off = (int64_t)t * ma * Cn;
+                if (off >= Lvalid) break;
+                const V w = r == 0 ? czero<V>() : __ldg(twNf + (((int64_t)r * t) % q) * mq);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (base[u] < 0 || base[u] + off >= Lvalid) continue;
+                    const V xv = x[base[u] + off];
+                    acc[u] = r == 0 ? cadd(acc[u], xv) : cfma(xv, w, acc[u]);
+                }
             }
         }
 #pragma unroll
@@ -308,21 +359,12 @@ __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn
         }
     }
     __syncthreads();
-    if (ma > 1) fft_smem<V, false>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);
-    for (int e = tid; e < ma * C; e += nthr) {
-        const int l = e / C, cl = e - l * C;
-        const int64_t c = c0 + cl;
-        if (c >= Cn) continue;
-        V v = buf[e];
-        if (post && l != 0 && c != 0) v = cmul(v, __ldg(twNf + (int64_t)l * c * q));
-        yb[(int64_t)l * ystride + c] = v;
-    }
-    __syncthreads();
+    fft_cols_store_body<V>(buf, tmp, yb, Cn, ma, q, c0, C, post, ystride, twNf, twma, twmal, fp, tid, nthr);
 }
 
 // Inverse FFT of size ma along the strided axis of yb[l][c] (row length Cn)
 // for columns c0 .. c0+C-1, in place, after multiplying by
-// conj(zeta_{Nf/q}^{l c}) if pre.  smem: 2 ma C.
+// conj(zeta_{Nf/q}^{l c}) if pre.  smem: 2 smem_len(ma C).
 template <class V>
 __device__ __forceinline__ void ifft_cols_body(V* yb, int64_t Cn, int ma, int q, int64_t Nf, int64_t c0, int C,
                                                int pre, const V* __restrict__ twNf, const V* __restrict__ twma,
@@ -330,10 +372,9 @@ __device__ __forceinline__ void ifft_cols_body(V* yb, int64_t Cn, int ma, int q,
                                                int nthr)
 {
     V* buf = smem;
-    V* tmp = buf + ma * C;
-    // four elements per thread at a time, so their loads are in flight
-    // together
-    constexpr int U = 4;
+    V* tmp = buf + smem_len<V>(ma * C);
+    // U elements per thread at a time, so their loads are in flight together
+    constexpr int U = kColLoads<V>;
     const int n = ma * C;
     for (int e0 = tid; e0 < n; e0 += U * nthr) {
         V v[U];
@@ -371,7 +412,7 @@ __device__ __forceinline__ void ifft_cols_body(V* yb, int64_t Cn, int ma, int q,
 // h[i][c] to the output at lin = (t ma + i) Cn + c, t < p, lo <= lin < hi,
 // stored at ob[lin - lo]: these outputs belong to this tile alone.  The
 // first residue of the first pass writes instead of adding; the last of the
-// last pass scales.  smem: 2 ma C.
+// last pass scales.  smem: 2 smem_len(ma C).
 template <class V>
 __device__ __forceinline__ void ifft_unfold_cols_body(const V* y, int64_t rstride, V* ob, int64_t Cn, int ma, int p,
                                                       int q, int64_t Nf, int64_t cs, int64_t cc, int64_t lo,
@@ -382,9 +423,9 @@ __device__ __forceinline__ void ifft_unfold_cols_body(const V* y, int64_t rstrid
                                                       int tid, int nthr)
 {
     V* buf = smem;
-    V* tmp = buf + ma * C;
+    V* tmp = buf + smem_len<V>(ma * C);
     const int64_t mq = Nf / q;
-    constexpr int U = 4;
+    constexpr int U = kColLoads<V>;
     const int n = ma * C;
     for (int rr = 0; rr < Dg; ++rr) {
         const int r = r0 + rr;

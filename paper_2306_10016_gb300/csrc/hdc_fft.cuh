@@ -332,16 +332,30 @@ struct FftPlan {
 // ---------------------------------------------------------- one stage
 // src -> dst (distinct shared buffers); one barrier at the end.
 //
-// With PAD, logical element x lives at x + x/8: the first stage's outputs go
-// to positions R apart, and without the pad slot every lane of a warp would
-// hit the same banks (R = 8 complex values = 128 bytes in FP64, 64 in FP32).
+// With SWZ, logical element x lives at x ^ ((x / S) & (S - 1)), S = 128 /
+// sizeof(V) elements per 128-byte bank row: the low bits are XORed with the
+// row number, so the elements of one bank row stay in it but a run of
+// elements with stride S (the first stage's outputs, R apart with R = 8)
+// spreads over all banks.  Unlike a pad slot this keeps every buffer at its
+// logical size.  The row buffers use it; the column tiles (ld = C, cs = 1)
+// keep the plain layout, where neighbouring threads already take
+// neighbouring columns and the index arithmetic measured slower.
 
-template <bool PAD> __device__ __forceinline__ int sidx(int x) { return PAD ? x + (x >> 3) : x; }
+template <class V, bool SWZ> __device__ __forceinline__ int sidx(int x)
+{
+    constexpr int S = 128 / (int)sizeof(V);
+    return SWZ ? x ^ ((x / S) & (S - 1)) : x;
+}
 
-// shared-memory elements a padded buffer of n logical elements occupies
-__host__ __device__ constexpr int64_t padded_len(int64_t n) { return n + (n >> 3) + 1; }
+// shared-memory elements a buffer of n logical elements occupies (whole bank
+// rows, so the swizzle stays inside it)
+template <class V> __host__ __device__ constexpr int64_t smem_len(int64_t n)
+{
+    constexpr int64_t S = 128 / (int64_t)sizeof(V);
+    return (n + S - 1) / S * S;
+}
 
-template <class V, int R, bool INV, bool PAD>
+template <class V, int R, bool INV, bool SWZ>
 __device__ __forceinline__ void fft_stage(const V* src, V* dst, int n, int ncol, int ld, int cs, int Ns,
                                           const V* __restrict__ tw, const V* __restrict__ twl, int tid, int nthr)
 {
@@ -355,7 +369,7 @@ __device__ __forceinline__ void fft_stage(const V* src, V* dst, int n, int ncol,
         const int base = c * cs;
         V v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[sidx<PAD>(base + (j + r * nb) * ld)];
+        for (int r = 0; r < R; ++r) v[r] = src[sidx<V, SWZ>(base + (j + r * nb) * ld)];
         const int jm = j % Ns;
         if (kLF && Ns > 1) {
             // every butterfly of the stage carries its twiddles (W = 1 when jm = 0)
@@ -373,7 +387,7 @@ __device__ __forceinline__ void fft_stage(const V* src, V* dst, int n, int ncol,
         }
         const int o = base + ((j - jm) * R + jm) * ld;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[sidx<PAD>(o + r * Ns * ld)] = v[r];
+        for (int r = 0; r < R; ++r) dst[sidx<V, SWZ>(o + r * Ns * ld)] = v[r];
     }
     __syncthreads();
 }
@@ -382,7 +396,7 @@ __device__ __forceinline__ void fft_stage(const V* src, V* dst, int n, int ncol,
 // addressing) as the other half of the ping-pong.  The caller must have
 // synchronised after filling buf; on return the result is in buf and the
 // block is synchronised.
-template <class V, bool INV, bool PAD = false>
+template <class V, bool INV, bool SWZ = false>
 __device__ __forceinline__ void fft_smem(V* buf, V* tmp, const FftPlan& fp, int ncol, int ld, int cs,
                                          const V* __restrict__ tw, const V* __restrict__ twl, int tid, int nthr)
 {
@@ -393,12 +407,12 @@ __device__ __forceinline__ void fft_smem(V* buf, V* tmp, const FftPlan& fp, int 
     for (int s = 0; s < fp.nst; ++s) {
         const int R = fp.rad[s];
         switch (R) {
-        case 8: fft_stage<V, 8, INV, PAD>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
-        case 4: fft_stage<V, 4, INV, PAD>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
-        case 2: fft_stage<V, 2, INV, PAD>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
-        case 3: fft_stage<V, 3, INV, PAD>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
-        case 5: fft_stage<V, 5, INV, PAD>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
-        case 7: fft_stage<V, 7, INV, PAD>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
+        case 8: fft_stage<V, 8, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
+        case 4: fft_stage<V, 4, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
+        case 2: fft_stage<V, 2, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
+        case 3: fft_stage<V, 3, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
+        case 5: fft_stage<V, 5, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
+        case 7: fft_stage<V, 7, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
         default: break;
         }
         Ns *= R;
@@ -410,7 +424,7 @@ __device__ __forceinline__ void fft_smem(V* buf, V* tmp, const FftPlan& fp, int 
         const int tot = n * ncol;
         for (int e = tid; e < tot; e += nthr) {
             const int i = e / ncol, c = e - i * ncol;
-            buf[sidx<PAD>(c * cs + i * ld)] = a[sidx<PAD>(c * cs + i * ld)];
+            buf[sidx<V, SWZ>(c * cs + i * ld)] = a[sidx<V, SWZ>(c * cs + i * ld)];
         }
         __syncthreads();
     }

@@ -15,20 +15,20 @@ namespace hdc {
 // two blocks share an SM.
 constexpr int kMaxThreads = 256;
 // Shared-memory budgets.  The fused residue kernel holds f, g and one
-// ping-pong buffer of m elements, each padded by one slot per 8 (3
-// padded_len(m)): 112 KiB still keeps two blocks per SM, so one block's
-// loads and barriers overlap the other's arithmetic.  The
-// strided-axis kernels hold a tile of ma x C elements and its ping-pong twin
-// (2 ma C): C is chosen so a tile fits 64 KiB (three blocks per SM), and a
-// single column may use up to 128 KiB.
+// ping-pong buffer of m elements (3 smem_len(m), 96 KiB at the largest m),
+// which keeps two blocks per SM, so one block's loads and barriers overlap
+// the other's arithmetic.  The strided-axis kernels hold a tile of ma x C
+// elements and its ping-pong twin (2 smem_len(ma C)): C is chosen so a tile
+// fits 64 KiB (three blocks per SM), and a single column may use up to
+// 128 KiB.
 constexpr int64_t kRowBytes = 112 * 1024;
 constexpr int64_t kColTargetBytes = 64 * 1024;
 constexpr int64_t kColMaxBytes = 128 * 1024;
 
-// largest power-of-two-rounded m whose three padded buffers fit kRowBytes
+// largest power-of-two-rounded m whose three buffers fit kRowBytes
 template <typename T> constexpr int64_t max_row_fft() { return (int64_t)1 << (sizeof(cx<T>) == 16 ? 11 : 12); }
-static_assert(3 * padded_len(2048) * 16 <= kRowBytes, "FP64 row tile exceeds its budget");
-static_assert(3 * padded_len(4096) * 8 <= kRowBytes, "FP32 row tile exceeds its budget");
+static_assert(3 * smem_len<cx<double>>(2048) * 16 <= kRowBytes, "FP64 row tile exceeds its budget");
+static_assert(3 * smem_len<cx<float>>(4096) * 8 <= kRowBytes, "FP32 row tile exceeds its budget");
 template <typename T> constexpr int64_t col_tile_target() { return kColTargetBytes / (2 * (int64_t)sizeof(cx<T>)); }
 template <typename T> constexpr int64_t max_col_fft() { return kColMaxBytes / (2 * (int64_t)sizeof(cx<T>)); }
 
@@ -39,8 +39,10 @@ FftPlan make_fft_plan(int64_t n);
 // bytes of the launch; when timing is on it also brackets the launch with
 // CUDA events on its stream.
 
+// K_FOLD_TMA counts the launches of k_fold_fft_cols that stage their tiles
+// with TMA copies (K_FOLD_FFT_COLS those on plain loads).
 enum KernelId { K_TWIDDLE = 0, K_RESIDUE_ROWS, K_FOLD_FFT_COLS, K_IFFT_COLS, K_UNFOLD, K_BATCHED, K_IFFT_UNFOLD,
-                K_COUNT };
+                K_FOLD_TMA, K_COUNT };
 
 struct LaunchScope {
     int kid;

@@ -6,17 +6,35 @@
 //                   m-point inverse FFT (Eq. 2 inner sum); unscaled result
 //  k_fold_fft_cols  fold along a strided axis + FFT over that axis, a tile of
 //                   C neighbouring columns per block (N-D outer axes, and the
-//                   first half of a split m = m1 m2 transform)
+//                   first half of a split m = m1 m2 transform); the tile's
+//                   fold blocks arrive by TMA box copies when the layout
+//                   allows it
 //  k_ifft_cols      inverse FFT over a strided axis, in place
 //  k_unfold         twiddled unfold-accumulate of the first L outputs (Eq. 2
 //                   outer sums), residues summed in increasing r, one scale
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
+#include <atomic>
+#include <cudaTypedefs.h>
+#include <mutex>
+
+#include "hdc.h"
 #include "hdc_bodies.cuh"
 #include "hdc_internal.h"
+#include "hdc_tma.cuh"
+
+#define HDC_EXPORT extern "C" __attribute__((visibility("default")))
 
 namespace hdc {
+
+// First error a kernel of this file recorded instead of waiting forever
+// (HDC_ERR_TIMEOUT); read and cleared by hdc_device_status.
+__device__ int g_device_status = 0;
+
+// TMA-staged loads in the strided fold (hdc_set_tma).
+static std::atomic<int> g_fold_tma{ 1 };
 
 // ------------------------------------------------------------- twiddles
 
@@ -137,7 +155,7 @@ cudaError_t launch_residue_rows(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_
     if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(m);
     const int thr = threads_for(m);
-    const size_t smem = (size_t)(3 * padded_len(m)) * sizeof(V);
+    const size_t smem = (size_t)(3 * smem_len<V>(m)) * sizeof(V);
     auto kern = k_residue_rows<V>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     const int64_t blocks = B * Dg;
@@ -191,7 +209,7 @@ cudaError_t launch_residue_rows_lam(const cx<T>* f, const cx<T>* g, cx<T>* h, in
     if (e != cudaSuccess) return e;
     const FftPlan fpf = make_fft_plan(mf), fpg = make_fft_plan(mg);
     const int thr = threads_for(mg);
-    const size_t smem = (size_t)(3 * padded_len(mg)) * sizeof(V);
+    const size_t smem = (size_t)(3 * smem_len<V>(mg)) * sizeof(V);
     auto kern = k_residue_rows_lam<V>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     const int64_t blocks = B * Dg;
@@ -239,7 +257,7 @@ cudaError_t launch_residue_rows_multi(const cx<T>* const* xs, int nin, int op, c
     if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(m);
     const int thr = threads_for(m);
-    const size_t smem = (size_t)(3 * padded_len(m)) * sizeof(V);
+    const size_t smem = (size_t)(3 * smem_len<V>(m)) * sizeof(V);
     auto kern = k_residue_rows_multi<V>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     InPtrs<V> in;
@@ -259,10 +277,40 @@ cudaError_t launch_residue_rows_multi(const cx<T>* const* xs, int nin, int op, c
 
 // ------------------------------------------------ strided-axis passes
 
-static int col_tile(int64_t Cn, int64_t ma, int64_t elems_max)
+// Blocks per SM the column kernels are compiled for: three in FP32, whose
+// passes wait on memory and want the extra warps; two in FP64, whose
+// transforms want the registers.
+template <class V> constexpr int kColBlocks = sizeof(V) == 8 ? 3 : 2;
+
+static int sm_count()
 {
-    int64_t C = 16;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+        sms = 152;
+    return sms;
+}
+
+// Column tile width C.  FP32 passes wait on memory: the widest power of two
+// up to 256 whose tile (ma C elements) fits elems_max, narrowed (down to 16)
+// while the launch would have fewer than four blocks per SM (`others` blocks
+// per tile position).  FP64 passes are bound by their arithmetic and run
+// best in small blocks: 16 columns, or as many as give a short axis (ma <
+// 32) 512 elements, i.e. 64 threads of work.  Never wider than the columns
+// need.
+template <typename T> static int col_tile(int64_t Cn, int64_t ma, int64_t elems_max, int64_t others)
+{
+    int64_t C = 256;
+    if (sizeof(T) == 8) {
+        int64_t c16 = 16;
+        while (c16 < 256 && ma * c16 < 512) c16 <<= 1;
+        C = c16;
+    }
     while (C > 1 && ma * C > elems_max) C >>= 1;
+    if (sizeof(T) == 4) {
+        const int64_t want = 4 * (int64_t)sm_count();
+        while (C > 16 && others * ((Cn + C - 1) / C) < want) C >>= 1;
+    }
     while (C > 1 && C / 2 >= Cn) C >>= 1;
     return (int)C;
 }
@@ -277,32 +325,216 @@ template <class V> struct ColSidesK {
     ColSideK<V> s[kMaxInputs];
 };
 
+// One tensor map per input of the strided fold: x[b][a][c] as 8-byte units,
+// dims (Cn * sizeof(V) / 8, full rows, B), box (C columns, tma_rows rows, 1).
+struct ColMapsK {
+    CUtensorMap m[kMaxInputs];
+};
+
+// Give up on a copy after about a second of SM clocks.
+constexpr long long kTmaWaitCycles = 2000000000LL;
+
+// Fold of the tile's p <= 2 blocks from the TMA-staged copies: block t of
+// the tile (rows t ma .. t ma + ma - 1) was copied to buf + t * stride as far
+// as it holds full rows of x (a < afull = Lvalid / Cn); the partial row
+// a = afull (when Lvalid is not a multiple of Cn) is read here with plain
+// loads and the rows past it are zero.  The folded tile goes to buf.
 template <class V>
-__global__ void __launch_bounds__(kMaxThreads, 2)
+__device__ __forceinline__ void fold_staged_tile(V* buf, int stride, const V* x, int64_t Cn, int ma, int p, int q,
+                                                 int64_t Nf, int64_t cs, int64_t cc, int64_t Lvalid, int r,
+                                                 int64_t c0, int C, const V* __restrict__ twNf, int tid, int nthr)
+{
+    const int64_t mq = Nf / q;
+    const int64_t afull = Lvalid / Cn;
+    const int n = ma * C;
+    for (int e = tid; e < n; e += nthr) {
+        const int i = e / C, cl = e - i * C;
+        const int64_t c = c0 + cl;
+        V acc = czero<V>();
+        for (int t = 0; t < p; ++t) {
+            const int64_t a = (int64_t)t * ma + i;
+            V v = czero<V>();
+            if (a < afull) v = buf[t * stride + e];
+            else if (a == afull && c < Cn && a * Cn + c < Lvalid) v = x[a * Cn + c];
+            // block t = 0 carries zeta_q^0 = 1: no multiplication
+            if (t == 0) acc = v;
+            else if (r == 0) acc = cadd(acc, v);
+            else acc = cfma(v, __ldg(twNf + (((int64_t)r * t) % q) * mq), acc);
+        }
+        if (r != 0 && c < Cn) acc = cmul(acc, __ldg(twNf + (int64_t)r * (i * cs + c * cc)));
+        buf[e] = acc;
+    }
+}
+
+// The block of the strided fold: column tile ct, input `which`, residue
+// block (l, rr) of batch row b; residue r, input row x, output yb.  skip: a
+// self-paired residue's partner, whose column pass the other side does.
+template <class V> struct FoldBlock {
+    int which, r, skip;
+    int64_t b, c0;
+    const V* x;
+    V* yb;
+};
+
+template <class V>
+__device__ __forceinline__ FoldBlock<V> fold_block(const ColSidesK<V>& sides, int nside, int64_t B, int64_t Cn, int ma,
+                                                   int r0, int Dg, int C, int nct)
+{
+    FoldBlock<V> fb;
+    int64_t blk = blockIdx.x;
+    const int ct = (int)(blk % nct);
+    blk /= nct;
+    fb.which = (int)(blk % nside);
+    blk /= nside;
+    const ColSideK<V>& sd = sides.s[fb.which];
+    const int nres = Dg * sd.lam;
+    const int rt = (int)(blk % nres);
+    fb.b = blk / nres;
+    const int l = rt / Dg, rr = rt - l * Dg;
+    fb.x = sd.x + fb.b * sd.bstride;
+    fb.yb = sd.y + ((int64_t)rr * B + fb.b) * ((int64_t)ma * sd.lam) * Cn + (int64_t)l * Cn;
+    fb.r = sd.rneg ? (sd.q - (r0 + rr)) % sd.q : r0 + rr + l * sd.rmul;
+    fb.skip = sd.rneg && fb.r == r0 + rr;
+    fb.c0 = (int64_t)ct * C;
+    return fb;
+}
+
+template <class V>
+__global__ void __launch_bounds__(kMaxThreads, kColBlocks<V>)
 k_fold_fft_cols(ColSidesK<V> sides, int nside, int64_t B, int64_t Cn, int ma, int64_t Nf, int64_t cs, int64_t cc,
                 int r0, int Dg, int C, int nct, int post, const V* __restrict__ twNf, const V* __restrict__ twma,
                 const V* __restrict__ twmal, FftPlan fp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    int64_t blk = blockIdx.x;
-    const int ct = (int)(blk % nct);
-    blk /= nct;
-    const int which = (int)(blk % nside);
-    blk /= nside;
-    const ColSideK<V>& sd = sides.s[which];
-    const int nres = Dg * sd.lam;
-    const int rt = (int)(blk % nres);
-    const int64_t b = blk / nres;
-    const int l = rt / Dg, rr = rt - l * Dg;
-    const V* x = sd.x + b * sd.bstride;
-    V* yb = sd.y + ((int64_t)rr * B + b) * ((int64_t)ma * sd.lam) * Cn + (int64_t)l * Cn;
-    const int r = sd.rneg ? (sd.q - (r0 + rr)) % sd.q : r0 + rr + l * sd.rmul;
-    // a self-paired residue's partner is itself: its column pass is already
-    // done by the other side (the whole block leaves before any barrier)
-    if (sd.rneg && r == r0 + rr) return;
-    fold_fft_cols_body<V>(x, yb, Cn, ma, sd.p, sd.q, Nf, cs, cc, sd.Lvalid, r, (int64_t)ct * C, C, post,
+    const FoldBlock<V> fb = fold_block<V>(sides, nside, B, Cn, ma, r0, Dg, C, nct);
+    // (the whole block leaves before any barrier)
+    if (fb.skip) return;
+    const ColSideK<V>& sd = sides.s[fb.which];
+    fold_fft_cols_body<V>(fb.x, fb.yb, Cn, ma, sd.p, sd.q, Nf, cs, cc, sd.Lvalid, fb.r, fb.c0, C, post,
                           (int64_t)sd.lam * Cn, twNf, twma, twmal, fp, reinterpret_cast<V*>(smraw), threadIdx.x,
                           blockDim.x);
+}
+
+// The same pass with the tile's fold blocks staged by TMA box copies of
+// tma_rows rows (the host has checked every copy rule; a block whose shared
+// memory is not 128-byte aligned uses the plain loads).
+template <class V>
+__global__ void __launch_bounds__(kMaxThreads, kColBlocks<V>)
+k_fold_fft_cols_tma(ColSidesK<V> sides, const __grid_constant__ ColMapsK maps, int tma_rows, int nside, int64_t B,
+                    int64_t Cn, int ma, int64_t Nf, int64_t cs, int64_t cc, int r0, int Dg, int C, int nct, int post,
+                    const V* __restrict__ twNf, const V* __restrict__ twma, const V* __restrict__ twmal, FftPlan fp)
+{
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ uint64_t bar;
+    const FoldBlock<V> fb = fold_block<V>(sides, nside, B, Cn, ma, r0, Dg, C, nct);
+    if (fb.skip) return;
+    const ColSideK<V>& sd = sides.s[fb.which];
+    V* buf = reinterpret_cast<V*>(smraw);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    if ((smem_u32(buf) & 127) != 0) {
+        fold_fft_cols_body<V>(fb.x, fb.yb, Cn, ma, sd.p, sd.q, Nf, cs, cc, sd.Lvalid, fb.r, fb.c0, C, post,
+                              (int64_t)sd.lam * Cn, twNf, twma, twmal, fp, buf, tid, nthr);
+        return;
+    }
+    const int n = ma * C;
+    const int stride = (int)smem_len<V>(n);
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // boxes that start past the last full row are not copied (their rows
+        // are zero or the partial row); a box that runs past it is filled
+        // with zeros there and still delivers all its bytes
+        constexpr int kUnits = (int)(sizeof(V) / 8);
+        const int64_t afull = sd.Lvalid / Cn;
+        uint32_t nbox = 0;
+        for (int t = 0; t < sd.p; ++t)
+            for (int j = 0; j * tma_rows < ma; ++j) nbox += (int64_t)t * ma + j * tma_rows < afull;
+        mbar_arrive_expect_tx(&bar, nbox * (uint32_t)(tma_rows * C * sizeof(V)));
+        for (int t = 0; t < sd.p; ++t)
+            for (int j = 0; j * tma_rows < ma; ++j)
+                if ((int64_t)t * ma + j * tma_rows < afull)
+                    tma_load_3d(buf + t * stride + j * tma_rows * C, &maps.m[fb.which], (int)(fb.c0 * kUnits),
+                                t * ma + j * tma_rows, (int)fb.b, &bar);
+    }
+    const bool ok = mbar_wait_bounded(&bar, 0, kTmaWaitCycles);
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicCAS(&g_device_status, 0, (int)HDC_ERR_TIMEOUT);
+        return;
+    }
+    fold_staged_tile<V>(buf, stride, fb.x, Cn, ma, sd.p, sd.q, Nf, cs, cc, sd.Lvalid, fb.r, fb.c0, C, twNf, tid,
+                        nthr);
+    __syncthreads();
+    fft_cols_store_body<V>(buf, buf + stride, fb.yb, Cn, ma, sd.q, fb.c0, C, post, (int64_t)sd.lam * Cn, twNf, twma,
+                           twmal, fp, tid, nthr);
+}
+
+// cuTensorMapEncodeTiled from the driver (no link-time dependency on it);
+// null if the driver does not offer it.
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) ==
+                cudaSuccess &&
+            qr == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// Rows per TMA box for a tile of ma rows x C columns of es-byte elements: a
+// divisor of ma of at most 256 (the box limit) such that every box starts
+// 128-byte aligned in shared memory; 0 if none of at least 8 rows exists.
+static int tma_box_rows(int64_t ma, int64_t C, int64_t es)
+{
+    for (int64_t d = ma < 256 ? ma : 256; d >= 8; --d)
+        if (ma % d == 0 && (d == ma || (d * C * es) % 128 == 0)) return (int)d;
+    return ma < 8 ? (int)ma : 0;
+}
+
+// Tensor maps for the TMA-staged fold of every input, or 0 when one of them
+// does not meet the copy rules (then the plain loads are used).  Returns the
+// rows per box.
+template <class V>
+static int make_fold_maps(ColMapsK* maps, const ColSidesK<V>& k, int nside, int64_t B, int64_t Cn, int64_t ma,
+                          int C)
+{
+    const int64_t es = (int64_t)sizeof(V);
+    const int64_t units = es / 8;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc || C * units > 256 || (C * es) % 16 != 0 || (Cn * es) % 16 != 0) return 0;
+    const int rows = tma_box_rows(ma, C, es);
+    if (rows == 0) return 0;
+    // the boxes the kernel issues, checked here: each destination 128-byte
+    // aligned inside its block's half of the 2 smem_len(ma C) buffer, the
+    // bytes one barrier expects below its 2^20 limit
+    const int64_t n = ma * C, stride = smem_len<V>(n);
+    if (ma % rows != 0 || (stride * es) % 128 != 0 || 2 * n * es >= ((int64_t)1 << 20)) return 0;
+    for (int64_t j = 0; j * rows < ma; ++j)
+        if ((j * rows * C * es) % 128 != 0 || (j + 1) * rows * C > n) return 0;
+    for (int i = 0; i < nside; ++i) {
+        const ColSideK<V>& sd = k.s[i];
+        const int64_t afull = sd.Lvalid / Cn;
+        if (sd.p > 2 || afull < 1 || ((uintptr_t)sd.x % 16) != 0) return 0;
+        if (B > 1 && (sd.bstride * es) % 16 != 0) return 0;
+        if (afull > ((int64_t)1 << 31) || Cn * units > ((int64_t)1 << 31) || B > ((int64_t)1 << 31)) return 0;
+        const cuuint64_t dims[3] = { (cuuint64_t)(Cn * units), (cuuint64_t)afull, (cuuint64_t)B };
+        const int64_t bs = B > 1 ? sd.bstride * es : (afull * Cn * es + 15) / 16 * 16;
+        const cuuint64_t strides[2] = { (cuuint64_t)(Cn * es), (cuuint64_t)bs };
+        const cuuint32_t box[3] = { (cuuint32_t)(C * units), (cuuint32_t)rows, 1 };
+        const cuuint32_t estr[3] = { 1, 1, 1 };
+        if (enc(&maps->m[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, (void*)sd.x, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return 0;
+    }
+    return rows;
 }
 
 template <typename T>
@@ -324,12 +556,10 @@ cudaError_t launch_fold_fft_cols(const ColSide<T>* sides, int nside, int64_t B, 
     const V* twmal = twiddles_lf<T>(ma, &e);
     if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(ma);
-    const int C = col_tile(Cn, ma, col_tile_target<T>());
+    const int C = col_tile<T>(Cn, ma, col_tile_target<T>(), Dg * sides[0].lam * nside * B);
     const int nct = (int)((Cn + C - 1) / C);
     const int thr = threads_for(ma * C);
-    const size_t smem = (size_t)(2 * ma * C) * sizeof(V);
-    auto kern = k_fold_fft_cols<V>;
-    if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
+    const size_t smem = (size_t)(2 * smem_len<V>(ma * C)) * sizeof(V);
     ColSidesK<V> k;
     double flops = 0.0, bytes = 0.0;
     for (int i = 0; i < kMaxInputs; ++i) {
@@ -341,6 +571,19 @@ cudaError_t launch_fold_fft_cols(const ColSide<T>* sides, int nside, int64_t B, 
         }
     }
     const int64_t blocks = (int64_t)nct * Dg * sides[0].lam * nside * B;
+    ColMapsK maps;
+    memset(&maps, 0, sizeof maps);
+    const int tma_rows = g_fold_tma ? make_fold_maps<V>(&maps, k, nside, B, Cn, ma, C) : 0;
+    if (tma_rows > 0) {
+        auto kern = k_fold_fft_cols_tma<V>;
+        if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
+        LaunchScope ls(K_FOLD_TMA, st, flops, bytes);
+        kern<<<(unsigned)blocks, thr, smem, st>>>(k, maps, tma_rows, nside, B, Cn, (int)ma, Nf, cs, cc, (int)r0,
+                                                  (int)Dg, C, nct, post, twNf, twma, twmal, fp);
+        return cudaGetLastError();
+    }
+    auto kern = k_fold_fft_cols<V>;
+    if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     LaunchScope ls(K_FOLD_FFT_COLS, st, flops, bytes);
     kern<<<(unsigned)blocks, thr, smem, st>>>(k, nside, B, Cn, (int)ma, Nf, cs, cc, (int)r0, (int)Dg, C, nct, post,
                                               twNf, twma, twmal, fp);
@@ -348,7 +591,7 @@ cudaError_t launch_fold_fft_cols(const ColSide<T>* sides, int nside, int64_t B, 
 }
 
 template <class V>
-__global__ void __launch_bounds__(kMaxThreads, 2)
+__global__ void __launch_bounds__(kMaxThreads, kColBlocks<V>)
 k_ifft_cols(V* y, int64_t B, int64_t Cn, int ma, int q, int64_t Nf, int Dg, int C, int nct, int pre,
             const V* __restrict__ twNf, const V* __restrict__ twma, const V* __restrict__ twmal, FftPlan fp)
 {
@@ -376,10 +619,10 @@ cudaError_t launch_ifft_cols(cx<T>* y, int64_t B, int64_t Cn, int64_t ma, int64_
     const V* twmal = twiddles_lf<T>(ma, &e);
     if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(ma);
-    const int C = col_tile(Cn, ma, col_tile_target<T>());
+    const int C = col_tile<T>(Cn, ma, col_tile_target<T>(), D * B);
     const int nct = (int)((Cn + C - 1) / C);
     const int thr = threads_for(ma * C);
-    const size_t smem = (size_t)(2 * ma * C) * sizeof(V);
+    const size_t smem = (size_t)(2 * smem_len<V>(ma * C)) * sizeof(V);
     auto kern = k_ifft_cols<V>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     const int64_t blocks = (int64_t)nct * D * B;
@@ -435,7 +678,7 @@ cudaError_t launch_unfold(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstride
 // ------------------------------------------ inverse + unfold, fused
 
 template <class V>
-__global__ void __launch_bounds__(kMaxThreads, 2)
+__global__ void __launch_bounds__(kMaxThreads, kColBlocks<V>)
 k_ifft_unfold_cols(const V* y, V* out, int64_t B, int64_t bstride, int64_t Cn, int ma, int p, int q, int64_t Nf,
                    int64_t cs, int64_t cc, int64_t lo, int64_t hi, int r0, int Dg, int first, int last,
                    typename real_of<V>::type scale, int C, int nct, int pre, const V* __restrict__ twNf,
@@ -459,12 +702,9 @@ cudaError_t launch_ifft_unfold(cx<T>* y, cx<T>* out, int64_t B, int64_t bstride,
     using V = cx<T>;
     const int64_t Dg = (D < q - r0) ? D : (q - r0);
     if (B <= 0 || Dg <= 0) return cudaSuccess;
-    const int C = col_tile(Cn, ma, col_tile_target<T>());
+    const int C = col_tile<T>(Cn, ma, col_tile_target<T>(), B);
     const int nct = (int)((Cn + C - 1) / C);
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
-                                                  cudaSuccess)
-        sms = 152;
+    const int sms = sm_count();
     // with several residues per pass the fused form has D times fewer blocks
     // and re-reads its outputs once per residue: measured slower than the two
     // passes, so it is taken for one residue per pass only
@@ -482,7 +722,7 @@ cudaError_t launch_ifft_unfold(cx<T>* y, cx<T>* out, int64_t B, int64_t bstride,
     if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(ma);
     const int thr = threads_for(ma * C);
-    const size_t smem = (size_t)(2 * ma * C) * sizeof(V);
+    const size_t smem = (size_t)(2 * smem_len<V>(ma * C)) * sizeof(V);
     auto kern = k_ifft_unfold_cols<V>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     const double nout = (double)(hi - lo);
@@ -539,7 +779,7 @@ cudaError_t launch_residue_rows_real(const cx<T>* z, cx<T>* h, int64_t B, int64_
     if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(m);
     const int thr = threads_for(m);
-    const size_t smem = (size_t)(3 * padded_len(m)) * sizeof(V);
+    const size_t smem = (size_t)(3 * smem_len<V>(m)) * sizeof(V);
     auto kern = k_residue_rows_real<V>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     // model per kept residue: two forward FFTs (one when self-paired, counted
@@ -588,7 +828,7 @@ cudaError_t launch_rows_real_pair(const cx<T>* ya, const cx<T>* yb, cx<T>* yh, i
     if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(m2);
     const int thr = threads_for(m2);
-    const size_t smem = (size_t)(3 * padded_len(m2)) * sizeof(V);
+    const size_t smem = (size_t)(3 * smem_len<V>(m2)) * sizeof(V);
     auto kern = k_rows_real_pair<V>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     const int64_t rows = Dg * B * m1;
@@ -768,7 +1008,7 @@ cudaError_t launch_residue_rows_tw(const cx<T>* f, const cx<T>* g, cx<T>* h, int
     cudaError_t e = cudaSuccess;
     const FftPlan fp = make_fft_plan(m);
     const int thr = threads_for(m);
-    const size_t smem = (size_t)(3 * padded_len(m)) * sizeof(V);
+    const size_t smem = (size_t)(3 * smem_len<V>(m)) * sizeof(V);
     auto kern = k_residue_rows<V>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     const int64_t blocks = B * Dg;
@@ -865,3 +1105,21 @@ HDC_INST(double)
 HDC_INST(float)
 
 } // namespace hdc
+
+HDC_EXPORT int hdc_set_tma(int enable)
+{
+    hdc::g_fold_tma.store(enable ? 1 : 0);
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_device_status(int* status, int clear)
+{
+    if (!status) return HDC_ERR_PARAM;
+    if (cudaDeviceSynchronize() != cudaSuccess) return HDC_ERR_CUDA;
+    if (cudaMemcpyFromSymbol(status, hdc::g_device_status, sizeof(int)) != cudaSuccess) return HDC_ERR_CUDA;
+    if (clear && *status != 0) {
+        const int zero = 0;
+        if (cudaMemcpyToSymbol(hdc::g_device_status, &zero, sizeof(int)) != cudaSuccess) return HDC_ERR_CUDA;
+    }
+    return HDC_OK;
+}

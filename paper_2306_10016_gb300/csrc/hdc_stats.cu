@@ -30,7 +30,7 @@ std::atomic<int> g_timing{ 0 };
 std::atomic<int64_t> g_total{ 0 };
 std::vector<cudaEvent_t> g_pool;
 const char* g_names[K_COUNT] = { "k_twiddle", "k_residue_rows", "k_fold_fft_cols", "k_ifft_cols", "k_unfold",
-                                 "k_batched", "k_ifft_unfold_cols" };
+                                 "k_batched", "k_ifft_unfold_cols", "k_fold_fft_cols_tma" };
 
 // Inside a stream capture an event record must be an external record node
 // for the event to carry a time stamp when the graph replays.

@@ -58,6 +58,29 @@ def test_batched_fixed_m(hdc, dt, tol):
     _check(fs, gs, ht, tol)
 
 
+@pytest.mark.parametrize("dt,tol", [(torch.complex128, 1e-12), (torch.complex64, 5e-5)])
+def test_batched_small_rows_and_short_columns(hdc, dt, tol):
+    """Many short convolutions of shared sizes, and a split convolution whose
+    rows are far below a row tile and whose column axis is short (wide
+    column tiles)."""
+    Ls, fs, gs, ft, gt, ht = _problem(60, 40, 700, 17, dt, extra=(100,) * 9 + (97, 128, 33, 5000))
+    ms = []
+    for i, L in enumerate(Ls):
+        M = 2 * L - 1
+        ms.append(hdc.next_good_size(M) if i % 3 == 0 else hdc.next_good_size((M + 3) // 4))
+    # split with rows well below a row tile: 16807 = 49 x 343 (FP64),
+    # 30625 = 25 x 1225 (FP32)
+    ms[-1] = 16807 if dt == torch.complex128 else 30625
+    plan = hdc.BatchedPlan(Ls, ms, hdc.dtype_code(dt))
+    assert plan.params[-1]["m1"] > 0 and plan.params[-1]["m2"] in (343, 1225)
+    ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+    plan.bind(ft, gt, ht)
+    plan.execute(ws)
+    torch.cuda.synchronize()
+    assert hdc.BatchedPlan.status(ws) == 0
+    _check(fs, gs, ht, tol)
+
+
 def test_batched_tuned_and_graph_replay(hdc):
     dt = torch.complex128
     Ls, fs, gs, ft, gt, ht = _problem(48, 64, 8192, 11, dt)
