@@ -33,6 +33,19 @@ METRIC = "conv outputs/s & %roofline, tuned hybrid vs explicit, FP64 err≤1e-12
 UNIT = "outputs/s"
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
+
+
+def _measured_hbm_gbs() -> float:
+    """HBM copy bandwidth measured on this machine's GPUs (MEASURED_PEAKS.json
+    beside this file), else the 6.8 TB/s fallback of an earlier measurement."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
+
+
+HBM_GBS = _measured_hbm_gbs()
 # FP64 / FP32 vector FMA units per SM of GB300 (2 DFMA and 128 FFMA per clock),
 # 2 flops per FMA: peak = SMs x units x 2 x max SM clock.
 FP64_FMA_PER_CLK = 2
@@ -41,7 +54,7 @@ FP32_FMA_PER_CLK = 128
 # dominant kernel, averaged over its launches in one ncu capture of this
 # sweep's timed steps (eager launches); to be re-taken whenever that kernel
 # changes (and None until then).
-NCU_TRAFFIC_PER_LAUNCH = {"k_residue_rows": 4.461e+07}
+NCU_TRAFFIC_PER_LAUNCH: dict = {}
 
 
 def sweep_sizes():
@@ -366,6 +379,7 @@ def main():
     plans32 = make_plans(hdc.HDC_C64, hdc.HDC_TUNE_EXHAUSTIVE)
     ms32, _, _, _ = time_sweep(plans32, ins32, args.steps, args.warmup)
     ms32 = rank_max(ms32)
+    _, _, _, kstats32 = time_sweep(plans32, ins32, 1, 1, stats=True)
     del ins32
 
     # --- batched: 4096 convolutions, L log-uniform in [64, 65536], one
@@ -711,6 +725,20 @@ def main():
                      for L, pt in zip(sizes, plans64))
     roofline["whole_step_frac"] = round(step_flops / (ms64 * 1e-3) / (peak * 1e12), 4)
 
+    def fp32_roofline(ks, ms):
+        """The FP32 step against its roofline: the slower of its model flops at
+        the FP32 vector peak and its algorithmic bytes at the measured HBM
+        copy bandwidth, over the measured step time."""
+        fl = sum(v["flops"] for v in ks.values())
+        by = sum(v["bytes"] for v in ks.values())
+        peak32 = SM_COUNT * FP32_FMA_PER_CLK * 2 * SM_MAX_MHZ * 1e6
+        t_roof = max(fl / peak32, by / (HBM_GBS * 1e9))
+        return {"model_tflops": round(fl / (ms * 1e-3) / 1e12, 4),
+                "algorithmic_GBps": round(by / (ms * 1e-3) / 1e9, 1),
+                "roofline_frac": round(t_roof / (ms * 1e-3), 4),
+                "roofline_basis": "max(model flops / FP32 peak (152 x 128 FMA x 2 x 2070 MHz), "
+                                  "algorithmic bytes / measured HBM copy bandwidth) over the step time"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(sizes)
@@ -727,7 +755,7 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "explicit": {"value": world * outs / (ms_ex * 1e-3), "ms_per_step": ms_ex,
                      "hybrid_speedup": round(ms_ex / ms64, 4)},
-        "fp32": {"value": world * outs / (ms32 * 1e-3), "ms_per_step": ms32},
+        "fp32": {"value": world * outs / (ms32 * 1e-3), "ms_per_step": ms32, **fp32_roofline(kstats32, ms32)},
         "nd_fp64": nd,
         "unequal_fp64": uneq,
         "multi_fp64": multi,
