@@ -104,6 +104,11 @@ typedef struct hdc_plan hdc_plan;
 /* Human-readable text for an hdc_status. Never NULL. */
 const char* hdc_strerror(int status);
 
+/* The cudaError_t code (0 if none yet) behind the most recent HDC_ERR_CUDA
+ * that a convolution entry point returned, and its name (cudaGetErrorName). */
+int hdc_last_cuda_error(void);
+const char* hdc_last_cuda_error_name(void);
+
 /* Library version as major*10000 + minor*100 + patch. */
 int hdc_version(void);
 
@@ -556,6 +561,12 @@ int hdc_batched_execute(hdc_batched* plan, const void* const* f,
 /* Status word of the last execute in `workspace` (synchronous copy; call
  * after the stream has finished): 0 or HDC_ERR_TIMEOUT. */
 int hdc_batched_status(const void* workspace, int* status);
+/* Durations (ms, from the GPU's global timer) of the four phases of the last
+ * execute in `workspace` (column folds and FFTs, rows, inverse column FFTs,
+ * unfolds), each from the grid barrier that opens it to the one that closes
+ * it, the last to the end of the last block (synchronous copy; call after
+ * the stream has finished). */
+int hdc_batched_phase_ms(const void* workspace, double* ms);
 /* Barrier limits: spin iterations (about 64 ns each) before giving up, and
  * arrivals the barrier waits for beyond the grid (0 in normal use; a
  * positive value makes every barrier wait for blocks that do not exist,

@@ -157,6 +157,7 @@ _SIGS += [
     ("hdc_batched_params", C.c_int, [_vp, _i64p, _i64p, _i64p, _i64p, _i64p]),
     ("hdc_batched_execute", C.c_int, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     ("hdc_batched_status", C.c_int, [_vp, C.POINTER(C.c_int)]),
+    ("hdc_batched_phase_ms", C.c_int, [_vp, C.POINTER(C.c_double)]),
     ("hdc_batched_set_barrier", C.c_int, [_vp, C.c_longlong, C.c_int]),
     ("hdc_batched_destroy", C.c_int, [_vp]),
     ("hdc_batched_tune", C.c_int, [_i64, _i64p, C.c_int, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.c_int,
@@ -202,6 +203,8 @@ _SIGS += [
                                       _i64p, _i64p, _i64p]),
     ("hdc_convnd_residues", C.c_int, [C.c_int, _vp, _vp, _vp, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, _i64, _i64,
                                       C.c_int, _i64, _vp, _sz, _vp]),
+    ("hdc_last_cuda_error", C.c_int, []),
+    ("hdc_last_cuda_error_name", C.c_char_p, []),
     ("hdc_set_tma", C.c_int, [C.c_int]),
     ("hdc_device_status", C.c_int, [C.POINTER(C.c_int), C.c_int]),
     ("hdc_stats_reset", C.c_int, []),
@@ -246,6 +249,8 @@ def lib() -> C.CDLL:
 
 def _check(rc: int, what: str) -> None:
     if rc != HDC_OK:
+        if rc == HDC_ERR_CUDA:
+            what = f"{what} [{lib().hdc_last_cuda_error_name().decode()}]"
         raise HDCError(rc, what)
 
 
@@ -1010,6 +1015,14 @@ class BatchedPlan:
         v = C.c_int()
         _check(lib().hdc_batched_status(workspace.data_ptr(), C.byref(v)), "batched_status")
         return v.value
+
+    @staticmethod
+    def phase_ms(workspace) -> list:
+        """Durations (ms) of the last execute's four phases: column folds and
+        FFTs, rows, inverse column FFTs, unfolds."""
+        v = (C.c_double * 4)()
+        _check(lib().hdc_batched_phase_ms(workspace.data_ptr(), v), "batched_phase_ms")
+        return [float(x) for x in v]
 
     def set_barrier(self, spin_limit: int, extra_arrivals: int = 0):
         _check(lib().hdc_batched_set_barrier(self._h, int(spin_limit), int(extra_arrivals)), "batched_set_barrier")

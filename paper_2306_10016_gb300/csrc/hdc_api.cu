@@ -4,6 +4,7 @@
 // hdc_kernels.cu for 1-D rows and the N-D recursion over axes (Section 3.6).
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <stdint.h>
@@ -16,6 +17,17 @@
 #define HDC_EXPORT extern "C" __attribute__((visibility("default")))
 
 namespace hdc {
+
+// The CUDA error behind the last HDC_ERR_CUDA of a convolution call
+// (hdc_last_cuda_error).
+static std::atomic<int> g_last_cuda_error{ 0 };
+
+static int cuda_rc(cudaError_t e)
+{
+    if (e == cudaSuccess) return HDC_OK;
+    g_last_cuda_error.store((int)e);
+    return HDC_ERR_CUDA;
+}
 
 template <typename T> cudaError_t launch_twiddle(cx<T>* tw, int64_t n, cudaStream_t st);
 template <typename T> cudaError_t launch_twiddle_lf(cx<T>* tw, int64_t n, cudaStream_t st);
@@ -533,7 +545,7 @@ static int conv_nd_real(int dims, const void* f, const void* g, void* h, const A
     V* w = (V*)(base + align_up((size_t)tot * sizeof(V)));
     if (launch_pack_real<T>((const T*)f, (const T*)g, z, tot, st) != cudaSuccess) return HDC_ERR_CUDA;
     cudaError_t e = run_nd_real<T>(dims, z, (T*)h, B, ax, w, st);
-    return e == cudaSuccess ? HDC_OK : HDC_ERR_CUDA;
+    return cuda_rc(e);
 }
 
 template <typename T>
@@ -574,7 +586,7 @@ static int conv_nd(int dims, const void* f, const void* g, void* h, const Axis* 
     in.x[0] = fin;
     in.x[1] = gin;
     cudaError_t e = run_nd<T>(dims, in, (V*)h, B, ax, (V*)base, st, r_lo, r_hi);
-    return e == cudaSuccess ? HDC_OK : HDC_ERR_CUDA;
+    return cuda_rc(e);
 }
 
 // Multi-convolution of n equal-shape inputs (device pointers, distinct from
@@ -592,7 +604,7 @@ static int conv_nd_multi(int dims, int n, int op, const void* const* xs, void* h
     in.op = op;
     for (int i = 0; i < n; ++i) in.x[i] = (const V*)xs[i];
     cudaError_t e = run_nd<T>(dims, in, (V*)h, B, ax, (V*)base, st);
-    return e == cudaSuccess ? HDC_OK : HDC_ERR_CUDA;
+    return cuda_rc(e);
 }
 
 static int resolve_all(int dims, const int64_t* L, const int64_t* M, const int64_t* m, const int64_t* p,
@@ -650,6 +662,13 @@ static int resolve_all_multi(int dims, int n, int op, const int64_t* L, const in
 using namespace hdc;
 
 // ------------------------------------------------------------------ ABI
+
+HDC_EXPORT int hdc_last_cuda_error(void) { return g_last_cuda_error.load(); }
+
+HDC_EXPORT const char* hdc_last_cuda_error_name(void)
+{
+    return cudaGetErrorName((cudaError_t)g_last_cuda_error.load());
+}
 
 HDC_EXPORT const char* hdc_strerror(int status)
 {

@@ -51,16 +51,27 @@ struct BItem {
     int conv, a, b, c;
 };
 
-// Workspace header (the first 256 bytes): phase counters, barrier, status.
+// Workspace header (the first 256 bytes): phase counters, barrier, status,
+// and the global-timer readings that split the launch into its phases: t[0]
+// when block 0 starts, t[1..3] when block 0 leaves each grid barrier, t[4]
+// when the last block ends.
 struct BHeader {
     unsigned int ctr[4];
     unsigned int arrive;
     int status;
-    unsigned int pad[58];
+    unsigned long long t[5];
+    unsigned int pad[48];
 };
 static_assert(sizeof(BHeader) == 256, "header must stay 256 bytes");
 
 constexpr int kUnfoldChunk = 1024; // outputs per unfold item
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ bool grid_barrier(BHeader* hd, unsigned int target, long long spin_limit)
 {
@@ -98,6 +109,7 @@ k_batched(const BConv<V>* __restrict__ convs, const BItem* __restrict__ it0, con
     __shared__ int s_idx;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const BItem* lists[4] = { it0, it1, it2, it3 };
+    if (blockIdx.x == 0 && tid == 0) hd->t[0] = global_ns();
     const int counts[4] = { n0, n1, n2, n3 };
     for (int ph = 0; ph < 4; ++ph) {
         const BItem* items = lists[ph];
@@ -152,8 +164,10 @@ k_batched(const BConv<V>* __restrict__ convs, const BItem* __restrict__ it0, con
         if (ph < 3) {
             const unsigned int target = (unsigned int)(gridDim.x * (ph + 1)) + (unsigned int)extra_arrivals;
             if (!grid_barrier(hd, target, spin_limit)) return;
+            if (blockIdx.x == 0 && tid == 0) hd->t[ph + 1] = global_ns();
         }
     }
+    if (tid == 0) atomicMax(&hd->t[4], global_ns());
 }
 
 } // namespace hdc
@@ -400,6 +414,17 @@ HDC_EXPORT int hdc_batched_status(const void* workspace, int* status)
         cudaSuccess)
         return HDC_ERR_CUDA;
     *status = v;
+    return HDC_OK;
+}
+
+HDC_EXPORT int hdc_batched_phase_ms(const void* workspace, double* ms)
+{
+    if (!workspace || !ms) return HDC_ERR_PARAM;
+    uintptr_t base = ((uintptr_t)workspace + 255) & ~(uintptr_t)255;
+    unsigned long long t[5];
+    if (cudaMemcpy(t, (const void*)(base + offsetof(BHeader, t)), sizeof t, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return HDC_ERR_CUDA;
+    for (int i = 0; i < 4; ++i) ms[i] = t[i + 1] >= t[i] ? (double)(t[i + 1] - t[i]) * 1e-6 : 0.0;
     return HDC_OK;
 }
 

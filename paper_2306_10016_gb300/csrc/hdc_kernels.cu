@@ -116,10 +116,16 @@ static int threads_for(int64_t elems)
     return (int)t;
 }
 
+// Opt a kernel in to `bytes` of dynamic shared memory when that passes the
+// default limit, which is 48 KiB minus the kernel's static shared memory
+// (the TMA fold's barrier, for one).
 template <typename K>
 static cudaError_t allow_smem(K kernel, size_t bytes)
 {
-    if (bytes <= 48 * 1024) return cudaSuccess;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    if (bytes + fa.sharedSizeBytes <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 

@@ -55,6 +55,9 @@ def test_batched_fixed_m(hdc, dt, tol):
     plan.execute(ws)
     torch.cuda.synchronize()
     assert hdc.BatchedPlan.status(ws) == 0
+    # the four phases of the launch, from the GPU's global timer
+    ph = hdc.BatchedPlan.phase_ms(ws)
+    assert len(ph) == 4 and all(t >= 0 for t in ph) and sum(ph) > 0
     _check(fs, gs, ht, tol)
 
 

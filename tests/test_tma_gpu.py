@@ -102,3 +102,27 @@ def test_multi_and_real_tma_match_plain(hdc):
     gr = torch.from_numpy(synth.standard_normal(7511, 30000)).cuda()
     a, b, n_tma = _both(hdc, lambda: hdc.convnd_real(fr, gr, 1, [16384]))
     assert n_tma > 0 and np.array_equal(a, b)
+
+
+def test_first_launch_at_the_shared_memory_threshold(hdc):
+    """A fresh process whose first TMA fold needs 48 KiB of dynamic shared
+    memory (ma = 384, C = 4): with the barrier's static bytes that is past the
+    default limit, so the launcher must opt the kernel in first (it used to
+    fail with cudaErrorInvalidValue until a larger launch had done so)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import numpy as np, torch, oracle\n"
+            "import paper_2306_10016_gb300 as hdc\n"
+            "from paper_2306_10016_gb300 import synth\n"
+            "f = synth.unit_disk(7600, (49152,)); g = synth.unit_disk(7601, (49152,))\n"
+            "hdc.stats_reset()\n"
+            "h = hdc.conv1d(torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda(), 49152, D=2).cpu().numpy()\n"
+            "assert hdc.stats()['k_fold_fft_cols_tma']['launches'] > 0\n"
+            "ref = oracle.conv_fft(f, g)\n"
+            "print(float(np.max(np.abs(h - ref)) / np.max(np.abs(ref))))\n")
+    env = dict(os.environ, PYTHONPATH=root + os.pathsep + os.environ.get("PYTHONPATH", ""))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert float(r.stdout.strip().splitlines()[-1]) < 1e-12
