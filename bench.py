@@ -57,6 +57,48 @@ FP32_FMA_PER_CLK = 128
 NCU_TRAFFIC_PER_LAUNCH: dict = {"k_residue_rows": 4.460e+07}
 
 
+def _good(n: int) -> bool:
+    for f in (2, 3, 5, 7):
+        while n % f == 0:
+            n //= f
+    return n == 1
+
+
+def model_flops(L: int, m: int, q: int) -> float:
+    """F1 = q (15 m log2 m + 6 m + 24 L) + 2 L: three transforms, the product,
+    the folds and the unfold of every residue, and the scaling."""
+    return q * (15 * m * math.log2(m) + 6 * m + 24 * L) + 2 * L
+
+
+def smooth_upto(n: int) -> list:
+    """The 7-smooth numbers 2^a 3^b 5^c 7^d <= n."""
+    out = []
+    p7 = 1
+    while p7 <= n:
+        p5 = p7
+        while p5 <= n:
+            p3 = p5
+            while p3 <= n:
+                x = p3
+                while x <= n:
+                    out.append(x)
+                    x *= 2
+                p3 *= 3
+            p5 *= 5
+        p7 *= 7
+    return sorted(out)
+
+
+def floor_flops(L: int) -> float:
+    """The least model flops over the valid tuples of one 1-D axis (M = 2L - 1):
+    every 7-smooth m from 16 up to the explicit size, q = ceil(M / m)."""
+    M = 2 * L - 1
+    top = M
+    while not _good(top):
+        top += 1
+    return min(model_flops(L, m, -(-M // m)) for m in smooth_upto(top) if m >= 16)
+
+
 def sweep_sizes():
     s = [1 << k for k in range(10, 23)] + [3 << k for k in range(9, 21)]
     return sorted(s)
@@ -435,15 +477,65 @@ def main():
             del graph, plan, wsb
         res["convolutions"] = nconv
         res["outputs"] = tot
+        res["lengths"] = Ls
         res["tuning_s"] = round(tune_b, 1)
         return res
 
     batched64 = batched_run(torch.complex128, hdc.HDC_C128)
+    blens = batched64.pop("lengths")
     batched64["roofline_frac"] = round(batched64["tuned"]["model_tflops"] / (
         SM_COUNT * FP64_FMA_PER_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12), 4)
     batched32 = batched_run(torch.complex64, hdc.HDC_C64)
+    batched32.pop("lengths")
     batched32["roofline_frac"] = round(batched32["tuned"]["model_tflops"] / (
         SM_COUNT * FP32_FMA_PER_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12), 4)
+
+    # --- the single small convolution: L = 1024, M = 2047, fixed (m, p, q, D)
+    # = (512, 2, 4, 1) (p = 2, the least p with p m >= L); latency of one call,
+    # and throughput of 16384 copies as the rows of one call
+    def config1():
+        L1 = 1024
+        f1 = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 1, (16384, L1))).to(dev)
+        g1 = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 101, (16384, L1))).to(dev)
+        h1 = torch.empty_like(f1)
+        ws1 = torch.empty(hdc.workspace_size([L1], [2 * L1 - 1], [512], p=[2], q=[4], D=[1], batch=16384),
+                          dtype=torch.uint8, device=dev)
+        st = torch.cuda.current_stream(dev)
+        one = lambda: hdc.convnd(f1[0], g1[0], 1, [512], p=[2], q=[4], D=[1], out=h1[0], workspace=ws1,  # noqa: E731
+                                 stream=st)
+        for _ in range(5):
+            one()
+        torch.cuda.synchronize(dev)
+        lat = []
+        for _ in range(21):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            one()
+            e1.record(st)
+            e1.synchronize()
+            lat.append(e0.elapsed_time(e1) * 1e3)
+        lat.sort()
+        msr, _ = graph_time(lambda s_: hdc.convnd(f1, g1, 1, [512], p=[2], q=[4], D=[1], out=h1, workspace=ws1,
+                                                  stream=s_), max(args.steps, 5))
+        return {"params": {"m": 512, "p": 2, "q": 4, "D": 1},
+                "latency_us": {"median": round(lat[10], 2), "p10": round(lat[2], 2), "p90": round(lat[18], 2),
+                               "calls": 21},
+                "replicated": {"copies": 16384, "ms": round(msr, 4),
+                               "value": world * 16384 * L1 / (msr * 1e-3)}}
+
+    # --- the sweep against the roofline of its least-flop tuples: T* = max(
+    # 3 sum L * bytes / HBM, sum F_floor / vector peak), both dtypes (the
+    # tuned and the explicit paths are scored against the same T*)
+    def floor_roofline(ms, es, peak_flops, Ls=None):
+        Ls = sizes if Ls is None else Ls
+        ff = sum(floor_flops(L) for L in Ls)
+        bb = 3.0 * sum(Ls) * es
+        t_star = max(bb / (HBM_GBS * 1e9), ff / peak_flops)
+        return {"frac": round(t_star / (ms * 1e-3), 4), "t_star_ms": round(t_star * 1e3, 4),
+                "floor_gflop": round(ff / 1e9, 3), "bytes_mb": round(bb / 1e6, 1),
+                "basis": "T* = max(3 sum L x element bytes / measured HBM, sum of least model flops over valid "
+                         "tuples / vector FMA peak), over the measured step time"}
 
     # --- N-D and Hermitian configurations (FP64): tuned 2-D 1024^2 and 3-D
     # 128^3, and the centered Hermitian 2-D convolution of 1024^2 real fields
@@ -517,6 +609,10 @@ def main():
                                "roofline_frac": round(herm[bm]["model_tflops"] / peak64, 4),
                                "outputs": (2 * K - 1) * K, "by_m": herm}
     del fh, gh, hh
+    cfg1 = config1()
+    batched64["floor"] = floor_roofline(batched64["tuned"]["ms"], 16, peak64 * 1e12, blens)
+    batched32["floor"] = floor_roofline(batched32["tuned"]["ms"], 8,
+                                        SM_COUNT * FP32_FMA_PER_CLK * 2 * SM_MAX_MHZ * 1e6, blens)
 
     # --- unequal lengths (Section 3.5, FP64): g of 2^22 points with f of
     # 2^10, 2^16 and 2^20 points, first 2^22 outputs.  Residue matching tuned
@@ -724,6 +820,8 @@ def main():
                                          + 6 * pt.params[0]["m"] + 24 * L) + 2 * L
                      for L, pt in zip(sizes, plans64))
     roofline["whole_step_frac"] = round(step_flops / (ms64 * 1e-3) / (peak * 1e12), 4)
+    roofline["floor"] = floor_roofline(ms64, 16, peak * 1e12)
+    roofline["floor"]["explicit_frac"] = round(roofline["floor"]["t_star_ms"] / ms_ex, 4)
 
     def fp32_roofline(ks, ms):
         """The FP32 step against its roofline: the slower of its model flops at
@@ -755,13 +853,15 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "explicit": {"value": world * outs / (ms_ex * 1e-3), "ms_per_step": ms_ex,
                      "hybrid_speedup": round(ms_ex / ms64, 4)},
-        "fp32": {"value": world * outs / (ms32 * 1e-3), "ms_per_step": ms32, **fp32_roofline(kstats32, ms32)},
+        "fp32": {"value": world * outs / (ms32 * 1e-3), "ms_per_step": ms32, **fp32_roofline(kstats32, ms32),
+                 "floor": floor_roofline(ms32, 8, SM_COUNT * FP32_FMA_PER_CLK * 2 * SM_MAX_MHZ * 1e6)},
         "nd_fp64": nd,
         "unequal_fp64": uneq,
         "multi_fp64": multi,
         "real_fp64": real,
         "batched_fp64": batched64,
         "batched_fp32": batched32,
+        "config1_fp64": cfg1,
         "per_size_fp64": per_size,
         "roofline": roofline,
         "cpu_baseline": cpu,
