@@ -48,6 +48,15 @@ FftPlan make_fft_plan(int64_t n)
     while (k % 5 == 0 && ns < HDC_MAX_STAGES) { fp.rad[ns++] = 5; k /= 5; }
     while (k % 3 == 0 && ns < HDC_MAX_STAGES) { fp.rad[ns++] = 3; k /= 3; }
     fp.nst = ns;
+    // packed twiddle table: a sub-table of Ns R entries per stage after the
+    // first
+    int64_t ns_done = 1, off = 0;
+    for (int s = 0; s < ns; ++s) {
+        fp.toff[s] = (int32_t)off;
+        if (ns_done > 1) off += ns_done * fp.rad[s];
+        ns_done *= fp.rad[s];
+    }
+    fp.tlen = (int32_t)(off > 0 ? off : 1);
     return fp;
 }
 
@@ -86,6 +95,37 @@ template <typename T> static const cx<T>* twiddle_table(int64_t n, bool lf, cuda
     g_tw[key] = p;
     return reinterpret_cast<const cx<T>*>(p);
 }
+
+// Packed per-stage twiddle tables of the n-point transform (FftPlan), plain
+// or twiddle-merged form; cached like the full tables.
+template <typename T> const cx<T>* twiddles_fft(int64_t n, bool lf, cudaError_t* err)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { *err = e; return nullptr; }
+    const int dt = (sizeof(T) == 8 ? 1 : 0) + (lf ? 2 : 0) + 4;
+    std::lock_guard<std::mutex> lk(g_tw_mu);
+    auto key = std::make_tuple(dev, n, dt);
+    auto it = g_tw.find(key);
+    if (it != g_tw.end()) return reinterpret_cast<const cx<T>*>(it->second);
+    const FftPlan fp = make_fft_plan(n);
+    void* p = nullptr;
+    e = cudaMalloc(&p, (size_t)fp.tlen * sizeof(cx<T>));
+    if (e != cudaSuccess) { *err = e; return nullptr; }
+    cudaStream_t s;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        e = launch_twiddle_fft_into<T>(reinterpret_cast<cx<T>*>(p), fp, lf, s);
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = e2;
+        cudaStreamDestroy(s);
+    }
+    if (e != cudaSuccess) { cudaFree(p); *err = e; return nullptr; }
+    g_tw[key] = p;
+    return reinterpret_cast<const cx<T>*>(p);
+}
+template const cx<double>* twiddles_fft<double>(int64_t, bool, cudaError_t*);
+template const cx<float>* twiddles_fft<float>(int64_t, bool, cudaError_t*);
 
 template <typename T> const cx<T>* twiddles(int64_t n, cudaError_t* err) { return twiddle_table<T>(n, false, err); }
 template <typename T> const cx<T>* twiddles_lf(int64_t n, cudaError_t* err) { return twiddle_table<T>(n, true, err); }

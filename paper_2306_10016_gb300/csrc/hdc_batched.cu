@@ -37,8 +37,8 @@ namespace hdc {
 
 template <class V> struct BConv {
     const V* twN;
-    const V* twm;  // m-point table (fused) or m2-point table (split rows)
-    const V* twm1; // m1-point table (split columns)
+    const V* twm;  // packed stage tables of the m-point (fused) or m2-point (split rows) transform
+    const V* twm1; // packed stage tables of the m1-point transform (split columns)
     const V* twml;  // the same two tables in scale-tangent form
     const V* twm1l;
     int64_t L, N, ws_off;
@@ -249,15 +249,15 @@ template <typename T> int build(hdc_batched* b)
         cv.m2 = (int)m2;
         cv.twN = twiddles<T>(cv.N, &e);
         if (e != cudaSuccess) return HDC_ERR_CUDA;
-        cv.twm = twiddles<T>(m1 ? m2 : b->m[i], &e);
+        cv.twm = twiddles_fft<T>(m1 ? m2 : b->m[i], false, &e);
         if (e != cudaSuccess) return HDC_ERR_CUDA;
-        cv.twml = twiddles_lf<T>(m1 ? m2 : b->m[i], &e);
+        cv.twml = twiddles_fft<T>(m1 ? m2 : b->m[i], true, &e);
         if (e != cudaSuccess) return HDC_ERR_CUDA;
         cv.fpm = make_fft_plan(m1 ? m2 : b->m[i]);
         if (m1) {
-            cv.twm1 = twiddles<T>(m1, &e);
+            cv.twm1 = twiddles_fft<T>(m1, false, &e);
             if (e != cudaSuccess) return HDC_ERR_CUDA;
-            cv.twm1l = twiddles_lf<T>(m1, &e);
+            cv.twm1l = twiddles_fft<T>(m1, true, &e);
             if (e != cudaSuccess) return HDC_ERR_CUDA;
             cv.fpm1 = make_fft_plan(m1);
             cv.C = col_tile_b<T>(m2, m1);

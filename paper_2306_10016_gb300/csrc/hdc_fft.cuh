@@ -323,10 +323,19 @@ template <class V, bool INV> struct DftLF<V, 8, INV> {
 // Most inputs of one multi-convolution (the n-fold product per residue).
 constexpr int kMaxInputs = 8;
 
+// The twiddles of the stages live in one packed table per transform size:
+// stage s, of radix R after Ns points have been combined (Ns > 1), reads the
+// sub-table zeta_{Ns R}^e, e < Ns R, at toff[s]; its butterfly jm (< Ns)
+// needs the entries r jm (r < R) and, in the twiddle-merged form, jm plus
+// multiples of Ns R / 8.  A warp's butterflies so read neighbouring entries
+// of a small table instead of entries r jm n / (Ns R) apart in the n-entry
+// one.
 struct FftPlan {
-    int n;                      // transform size
-    int nst;                    // number of stages
-    int8_t rad[HDC_MAX_STAGES]; // radix per stage, product = n
+    int n;                          // transform size
+    int nst;                        // number of stages
+    int8_t rad[HDC_MAX_STAGES];     // radix per stage, product = n
+    int32_t toff[HDC_MAX_STAGES];   // offset of the stage's twiddle sub-table
+    int32_t tlen;                   // entries of the packed table (>= 1)
 };
 
 // ---------------------------------------------------------- one stage
@@ -355,6 +364,7 @@ template <class V> __host__ __device__ constexpr int64_t smem_len(int64_t n)
     return (n + S - 1) / S * S;
 }
 
+// tw / twl: the stage's sub-table zeta_{Ns R}^e (plain / twiddle-merged form).
 template <class V, int R, bool INV, bool SWZ>
 __device__ __forceinline__ void fft_stage(const V* src, V* dst, int n, int ncol, int ld, int cs, int Ns,
                                           const V* __restrict__ tw, const V* __restrict__ twl, int tid, int nthr)
@@ -362,7 +372,6 @@ __device__ __forceinline__ void fft_stage(const V* src, V* dst, int n, int ncol,
     constexpr bool kLF = (R == 2 || R == 4 || R == 8);
     const int nb = n / R;
     const int total = nb * ncol;
-    const int tstep = n / (Ns * R);
     for (int b = tid; b < total; b += nthr) {
         const int j = b / ncol;
         const int c = b - j * ncol;
@@ -373,13 +382,12 @@ __device__ __forceinline__ void fft_stage(const V* src, V* dst, int n, int ncol,
         const int jm = j % Ns;
         if (kLF && Ns > 1) {
             // every butterfly of the stage carries its twiddles (W = 1 when jm = 0)
-            DftLF<V, kLF ? R : 2, INV>::run(v, twl, jm * tstep, n);
+            DftLF<V, kLF ? R : 2, INV>::run(v, twl, jm, Ns * R);
         } else {
             if (jm != 0) {
-                const int k = jm * tstep;
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    const V w = ldg_c(tw + r * k);
+                    const V w = ldg_c(tw + r * jm);
                     v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
                 }
             }
@@ -393,9 +401,10 @@ __device__ __forceinline__ void fft_stage(const V* src, V* dst, int n, int ncol,
 }
 
 // Whole transform of the ncol columns in buf, using tmp (same size and
-// addressing) as the other half of the ping-pong.  The caller must have
-// synchronised after filling buf; on return the result is in buf and the
-// block is synchronised.
+// addressing) as the other half of the ping-pong.  tw / twl: the packed
+// twiddle tables of fp (plain / twiddle-merged form, see FftPlan).  The
+// caller must have synchronised after filling buf; on return the result is
+// in buf and the block is synchronised.
 template <class V, bool INV, bool SWZ = false>
 __device__ __forceinline__ void fft_smem(V* buf, V* tmp, const FftPlan& fp, int ncol, int ld, int cs,
                                          const V* __restrict__ tw, const V* __restrict__ twl, int tid, int nthr)
@@ -406,13 +415,15 @@ __device__ __forceinline__ void fft_smem(V* buf, V* tmp, const FftPlan& fp, int 
     V* b = tmp;
     for (int s = 0; s < fp.nst; ++s) {
         const int R = fp.rad[s];
+        const V* ts = tw + fp.toff[s];
+        const V* tl = twl + fp.toff[s];
         switch (R) {
-        case 8: fft_stage<V, 8, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
-        case 4: fft_stage<V, 4, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
-        case 2: fft_stage<V, 2, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
-        case 3: fft_stage<V, 3, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
-        case 5: fft_stage<V, 5, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
-        case 7: fft_stage<V, 7, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, tw, twl, tid, nthr); break;
+        case 8: fft_stage<V, 8, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
+        case 4: fft_stage<V, 4, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
+        case 2: fft_stage<V, 2, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
+        case 3: fft_stage<V, 3, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
+        case 5: fft_stage<V, 5, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
+        case 7: fft_stage<V, 7, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
         default: break;
         }
         Ns *= R;

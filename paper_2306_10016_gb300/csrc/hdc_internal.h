@@ -60,6 +60,9 @@ double fft_flops(double n);
 // butterflies (see lf_bfly).
 template <typename T> const cx<T>* twiddles(int64_t n, cudaError_t* err);
 template <typename T> const cx<T>* twiddles_lf(int64_t n, cudaError_t* err);
+// The packed per-stage tables of the n-point transform's plan (FftPlan::toff),
+// plain (lf = false) or twiddle-merged form: what fft_smem reads.
+template <typename T> const cx<T>* twiddles_fft(int64_t n, bool lf, cudaError_t* err);
 
 // ------------------------------------------------------------ launchers
 
@@ -179,10 +182,12 @@ template <typename T>
 cudaError_t launch_hermitian_expand(const cx<T>* half, cx<T>* full, int64_t K, int64_t B, cudaStream_t st);
 
 // The same launches with caller-provided twiddle tables (no library cache):
-// twN = zeta_{q m}^k (q m entries), twm = zeta_m^k (m entries), twNf as in
-// launch_unfold; launch_twiddle_into fills a table of n entries on `st`.
+// twN = zeta_{q m}^k (q m entries), twm / twml the packed stage tables of the
+// m-point transform (launch_twiddle_fft_into), twNf as in launch_unfold;
+// launch_twiddle_into fills a table of n entries on `st`.
 template <typename T> cudaError_t launch_twiddle_into(cx<T>* tw, int64_t n, cudaStream_t st);
-template <typename T> cudaError_t launch_twiddle_lf_into(cx<T>* tw, int64_t n, cudaStream_t st);
+// Fills a packed table of fp.tlen entries (see FftPlan) on `st`.
+template <typename T> cudaError_t launch_twiddle_fft_into(cx<T>* tw, const FftPlan& fp, bool lf, cudaStream_t st);
 template <typename T>
 cudaError_t launch_residue_rows_tw(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_t B, int64_t ld_in,
                                    int64_t L, int64_t m, int64_t p, int64_t q, int64_t r0, int64_t D,

@@ -17,6 +17,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <map>
 #include <cudaTypedefs.h>
 #include <mutex>
 
@@ -118,15 +119,30 @@ static int threads_for(int64_t elems)
 
 // Opt a kernel in to `bytes` of dynamic shared memory when that passes the
 // default limit, which is 48 KiB minus the kernel's static shared memory
-// (the TMA fold's barrier, for one).
+// (the TMA fold's barrier, for one).  The limit each kernel already has is
+// remembered, so a launch costs one lookup.
 template <typename K>
 static cudaError_t allow_smem(K kernel, size_t bytes)
 {
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> granted; // (device, kernel) -> bytes allowed
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (bytes + fa.sharedSizeBytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    const auto key = std::make_pair(dev, reinterpret_cast<const void*>(kernel));
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = granted.find(key);
+    if (it != granted.end() && bytes <= it->second) return cudaSuccess;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, kernel)) != cudaSuccess) return e;
+    size_t limit = 48 * 1024 > fa.sharedSizeBytes ? 48 * 1024 - fa.sharedSizeBytes : 0;
+    if (bytes > limit) {
+        if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess)
+            return e;
+        limit = bytes;
+    }
+    granted[key] = it != granted.end() && it->second > limit ? it->second : limit;
+    return cudaSuccess;
 }
 
 // ------------------------------------------------------- residue rows
@@ -155,9 +171,9 @@ cudaError_t launch_residue_rows(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_
     cudaError_t e = cudaSuccess;
     const V* twN = twiddles<T>(q * m, &e);
     if (e != cudaSuccess) return e;
-    const V* twm = twiddles<T>(m, &e);
+    const V* twm = twiddles_fft<T>(m, false, &e);
     if (e != cudaSuccess) return e;
-    const V* twml = twiddles_lf<T>(m, &e);
+    const V* twml = twiddles_fft<T>(m, true, &e);
     if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(m);
     const int thr = threads_for(m);
@@ -205,13 +221,13 @@ cudaError_t launch_residue_rows_lam(const cx<T>* f, const cx<T>* g, cx<T>* h, in
     cudaError_t e = cudaSuccess;
     const V* twN = twiddles<T>(qg * mg, &e);
     if (e != cudaSuccess) return e;
-    const V* twf = twiddles<T>(mf, &e);
+    const V* twf = twiddles_fft<T>(mf, false, &e);
     if (e != cudaSuccess) return e;
-    const V* twfl = twiddles_lf<T>(mf, &e);
+    const V* twfl = twiddles_fft<T>(mf, true, &e);
     if (e != cudaSuccess) return e;
-    const V* twg = twiddles<T>(mg, &e);
+    const V* twg = twiddles_fft<T>(mg, false, &e);
     if (e != cudaSuccess) return e;
-    const V* twgl = twiddles_lf<T>(mg, &e);
+    const V* twgl = twiddles_fft<T>(mg, true, &e);
     if (e != cudaSuccess) return e;
     const FftPlan fpf = make_fft_plan(mf), fpg = make_fft_plan(mg);
     const int thr = threads_for(mg);
@@ -257,9 +273,9 @@ cudaError_t launch_residue_rows_multi(const cx<T>* const* xs, int nin, int op, c
     cudaError_t e = cudaSuccess;
     const V* twN = twiddles<T>(q * m, &e);
     if (e != cudaSuccess) return e;
-    const V* twm = twiddles<T>(m, &e);
+    const V* twm = twiddles_fft<T>(m, false, &e);
     if (e != cudaSuccess) return e;
-    const V* twml = twiddles_lf<T>(m, &e);
+    const V* twml = twiddles_fft<T>(m, true, &e);
     if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(m);
     const int thr = threads_for(m);
@@ -557,9 +573,9 @@ cudaError_t launch_fold_fft_cols(const ColSide<T>* sides, int nside, int64_t B, 
     cudaError_t e = cudaSuccess;
     const V* twNf = twiddles<T>(Nf, &e);
     if (e != cudaSuccess) return e;
-    const V* twma = twiddles<T>(ma, &e);
+    const V* twma = twiddles_fft<T>(ma, false, &e);
     if (e != cudaSuccess) return e;
-    const V* twmal = twiddles_lf<T>(ma, &e);
+    const V* twmal = twiddles_fft<T>(ma, true, &e);
     if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(ma);
     const int C = col_tile<T>(Cn, ma, col_tile_target<T>(), Dg * sides[0].lam * nside * B);
@@ -620,9 +636,9 @@ cudaError_t launch_ifft_cols(cx<T>* y, int64_t B, int64_t Cn, int64_t ma, int64_
     cudaError_t e = cudaSuccess;
     const V* twNf = twiddles<T>(Nf, &e);
     if (e != cudaSuccess) return e;
-    const V* twma = twiddles<T>(ma, &e);
+    const V* twma = twiddles_fft<T>(ma, false, &e);
     if (e != cudaSuccess) return e;
-    const V* twmal = twiddles_lf<T>(ma, &e);
+    const V* twmal = twiddles_fft<T>(ma, true, &e);
     if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(ma);
     const int C = col_tile<T>(Cn, ma, col_tile_target<T>(), D * B);
@@ -722,9 +738,9 @@ cudaError_t launch_ifft_unfold(cx<T>* y, cx<T>* out, int64_t B, int64_t bstride,
     cudaError_t e = cudaSuccess;
     const V* twNf = twiddles<T>(Nf, &e);
     if (e != cudaSuccess) return e;
-    const V* twma = twiddles<T>(ma, &e);
+    const V* twma = twiddles_fft<T>(ma, false, &e);
     if (e != cudaSuccess) return e;
-    const V* twmal = twiddles_lf<T>(ma, &e);
+    const V* twmal = twiddles_fft<T>(ma, true, &e);
     if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(ma);
     const int thr = threads_for(ma * C);
@@ -779,9 +795,9 @@ cudaError_t launch_residue_rows_real(const cx<T>* z, cx<T>* h, int64_t B, int64_
     cudaError_t e = cudaSuccess;
     const V* twN = twiddles<T>(q * m, &e);
     if (e != cudaSuccess) return e;
-    const V* twm = twiddles<T>(m, &e);
+    const V* twm = twiddles_fft<T>(m, false, &e);
     if (e != cudaSuccess) return e;
-    const V* twml = twiddles_lf<T>(m, &e);
+    const V* twml = twiddles_fft<T>(m, true, &e);
     if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(m);
     const int thr = threads_for(m);
@@ -828,9 +844,9 @@ cudaError_t launch_rows_real_pair(const cx<T>* ya, const cx<T>* yb, cx<T>* yh, i
     using V = cx<T>;
     if (B <= 0 || Dg <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-    const V* twm = twiddles<T>(m2, &e);
+    const V* twm = twiddles_fft<T>(m2, false, &e);
     if (e != cudaSuccess) return e;
-    const V* twml = twiddles_lf<T>(m2, &e);
+    const V* twml = twiddles_fft<T>(m2, true, &e);
     if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(m2);
     const int thr = threads_for(m2);
@@ -998,9 +1014,18 @@ cudaError_t launch_twiddle_into(cx<T>* tw, int64_t n, cudaStream_t st)
 }
 
 template <typename T>
-cudaError_t launch_twiddle_lf_into(cx<T>* tw, int64_t n, cudaStream_t st)
+cudaError_t launch_twiddle_fft_into(cx<T>* tw, const FftPlan& fp, bool lf, cudaStream_t st)
 {
-    return launch_twiddle_lf<T>(tw, n, st);
+    int64_t ns = 1;
+    for (int s = 0; s < fp.nst; ++s) {
+        if (ns > 1) {
+            const int64_t len = ns * fp.rad[s];
+            cudaError_t e = lf ? launch_twiddle_lf<T>(tw + fp.toff[s], len, st) : launch_twiddle<T>(tw + fp.toff[s], len, st);
+            if (e != cudaSuccess) return e;
+        }
+        ns *= fp.rad[s];
+    }
+    return cudaSuccess;
 }
 
 template <typename T>
@@ -1049,7 +1074,7 @@ cudaError_t launch_unfold_tw(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstr
 
 #define HDC_INST_TW(T)                                                                                    \
     template cudaError_t launch_twiddle_into<T>(cx<T>*, int64_t, cudaStream_t);                          \
-    template cudaError_t launch_twiddle_lf_into<T>(cx<T>*, int64_t, cudaStream_t);                       \
+    template cudaError_t launch_twiddle_fft_into<T>(cx<T>*, const FftPlan&, bool, cudaStream_t);          \
     template cudaError_t launch_residue_rows_tw<T>(const cx<T>*, const cx<T>*, cx<T>*, int64_t, int64_t, \
                                                    int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, \
                                                    const cx<T>*, const cx<T>*, const cx<T>*, cudaStream_t); \

@@ -61,7 +61,8 @@ int run(const void* f, const void* g, void* h, int64_t L, int64_t m, int64_t p, 
     if (m > max_row_fft<T>()) return HDC_ERR_UNSUPPORTED_SIZE;
     const int64_t N = q * m;
     const size_t b_twN = align256((size_t)N * sizeof(V));
-    const size_t b_twm = align256((size_t)m * sizeof(V));
+    const FftPlan fpm = make_fft_plan(m);
+    const size_t b_twm = align256((size_t)fpm.tlen * sizeof(V));
     const size_t b_ws = align256((size_t)(D * batch * m) * sizeof(V));
     if (b_twN + 2 * b_twm + b_ws > kScratchBytes) return HDC_ERR_UNSUPPORTED_SIZE;
     void* base = nullptr;
@@ -74,8 +75,8 @@ int run(const void* f, const void* g, void* h, int64_t L, int64_t m, int64_t p, 
     // every call rewrites the tables and the workspace it reads, so nothing
     // left from an earlier call is used
     if (launch_twiddle_into<T>(twN, N, st) != cudaSuccess) return HDC_ERR_CUDA;
-    if (launch_twiddle_into<T>(twm, m, st) != cudaSuccess) return HDC_ERR_CUDA;
-    if (launch_twiddle_lf_into<T>(twml, m, st) != cudaSuccess) return HDC_ERR_CUDA;
+    if (launch_twiddle_fft_into<T>(twm, fpm, false, st) != cudaSuccess) return HDC_ERR_CUDA;
+    if (launch_twiddle_fft_into<T>(twml, fpm, true, st) != cudaSuccess) return HDC_ERR_CUDA;
     const double scale = 1.0 / (double)N;
     for (int64_t r0 = 0; r0 < q; r0 += D) {
         const int first = (r0 == 0), last = (r0 + D >= q);
