@@ -31,6 +31,8 @@ static int cuda_rc(cudaError_t e)
 
 template <typename T> cudaError_t launch_twiddle(cx<T>* tw, int64_t n, cudaStream_t st);
 template <typename T> cudaError_t launch_twiddle_lf(cx<T>* tw, int64_t n, cudaStream_t st);
+template <typename T>
+cudaError_t launch_twiddle_strided(cx<T>* tw, int64_t count, int64_t N, int64_t stride, cudaStream_t st);
 
 // ----------------------------------------------------------- FFT plans
 
@@ -126,6 +128,59 @@ template <typename T> const cx<T>* twiddles_fft(int64_t n, bool lf, cudaError_t*
 }
 template const cx<double>* twiddles_fft<double>(int64_t, bool, cudaError_t*);
 template const cx<float>* twiddles_fft<float>(int64_t, bool, cudaError_t*);
+
+// An FP32 fold/unfold table of N entries is kept whole up to this size; a
+// larger one is two tables of about sqrt(N) entries (TwTab).
+constexpr int64_t kTwFullMax = (int64_t)1 << 16;
+
+template <typename T> static const cx<T>* strided_table(int64_t count, int64_t N, int64_t stride, int kind,
+                                                        cudaError_t* err)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { *err = e; return nullptr; }
+    // kinds 8 / 16 + dtype: the lo / hi table of N; the key's size field is N
+    const int dt = (sizeof(T) == 8 ? 1 : 0) + kind;
+    std::lock_guard<std::mutex> lk(g_tw_mu);
+    auto key = std::make_tuple(dev, N, dt);
+    auto it = g_tw.find(key);
+    if (it != g_tw.end()) return reinterpret_cast<const cx<T>*>(it->second);
+    void* p = nullptr;
+    e = cudaMalloc(&p, (size_t)count * sizeof(cx<T>));
+    if (e != cudaSuccess) { *err = e; return nullptr; }
+    cudaStream_t s;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        e = launch_twiddle_strided<T>(reinterpret_cast<cx<T>*>(p), count, N, stride, s);
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = e2;
+        cudaStreamDestroy(s);
+    }
+    if (e != cudaSuccess) { cudaFree(p); *err = e; return nullptr; }
+    g_tw[key] = p;
+    return reinterpret_cast<const cx<T>*>(p);
+}
+
+template <typename T> TwTab<cx<T>> tw_table(int64_t N, cudaError_t* err)
+{
+    TwTab<cx<T>> t{ nullptr, nullptr, nullptr, 0 };
+    // FP64 keeps one table: its kernels are bound by FP64 arithmetic, which
+    // the extra complex product would add to
+    if (sizeof(T) == 8 || N <= kTwFullMax) {
+        t.full = twiddle_table<T>(N, false, err);
+        return t;
+    }
+    int lb = 0;
+    while (((int64_t)1 << (2 * lb)) < N) ++lb;
+    const int64_t S = (int64_t)1 << lb;
+    t.lb = lb;
+    t.lo = strided_table<T>(S, N, 1, 8, err);
+    if (!t.lo) return t;
+    t.hi = strided_table<T>((N + S - 1) / S, N, S, 16, err);
+    return t;
+}
+template TwTab<cx<double>> tw_table<double>(int64_t, cudaError_t*);
+template TwTab<cx<float>> tw_table<float>(int64_t, cudaError_t*);
 
 template <typename T> const cx<T>* twiddles(int64_t n, cudaError_t* err) { return twiddle_table<T>(n, false, err); }
 template <typename T> const cx<T>* twiddles_lf(int64_t n, cudaError_t* err) { return twiddle_table<T>(n, true, err); }

@@ -36,7 +36,7 @@
 namespace hdc {
 
 template <class V> struct BConv {
-    const V* twN;
+    TwTab<V> twN;
     const V* twm;  // packed stage tables of the m-point (fused) or m2-point (split rows) transform
     const V* twm1; // packed stage tables of the m1-point transform (split columns)
     const V* twml;  // the same two tables in scale-tangent form
@@ -139,7 +139,7 @@ k_batched(const BConv<V>* __restrict__ convs, const BItem* __restrict__ it0, con
                     const int64_t row = itm.a;
                     V* yf = cws + row * cv.m2;
                     const V* yg = cws + (int64_t)cv.q * cv.m + row * cv.m2;
-                    residue_row_body<V>(yf, yg, yf, cv.m2, cv.m2, cv.m2, 1, 1, 0, cv.twm, cv.twm, cv.twml, cv.fpm, smem, tid,
+                    residue_row_body<V>(yf, yg, yf, cv.m2, cv.m2, cv.m2, 1, 1, 0, cv.twN, cv.twm, cv.twml, cv.fpm, smem, tid,
                                         nthr);
                 }
             } else if (ph == 2) {
@@ -247,7 +247,7 @@ template <typename T> int build(hdc_batched* b)
         cv.N = b->q[i] * b->m[i];
         cv.m1 = (int)m1;
         cv.m2 = (int)m2;
-        cv.twN = twiddles<T>(cv.N, &e);
+        cv.twN = tw_table<T>(cv.N, &e);
         if (e != cudaSuccess) return HDC_ERR_CUDA;
         cv.twm = twiddles_fft<T>(m1 ? m2 : b->m[i], false, &e);
         if (e != cudaSuccess) return HDC_ERR_CUDA;

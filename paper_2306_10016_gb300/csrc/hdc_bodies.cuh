@@ -17,7 +17,7 @@ namespace hdc {
 // plain copy of the rows.
 template <class V>
 __device__ __forceinline__ void residue_row_body(const V* fr, const V* gr, V* hr, int64_t L, int64_t Lf, int m, int p,
-                                                 int q, int r, const V* __restrict__ twN, const V* __restrict__ twm,
+                                                 int q, int r, const TwTab<V> twN, const V* __restrict__ twm,
                                                  const V* __restrict__ twml, const FftPlan& fp, V* smem, int tid,
                                                  int nthr)
 {
@@ -43,13 +43,13 @@ __device__ __forceinline__ void residue_row_body(const V* fr, const V* gr, V* hr
                     af = cadd(af, fv);
                     ag = cadd(ag, gv);
                 } else {
-                    const V w = __ldg(twN + (((int64_t)r * t) % q) * m);
+                    const V w = twn(twN, (((int64_t)r * t) % q) * m);
                     af = cfma(fv, w, af);
                     ag = cfma(gv, w, ag);
                 }
             }
             if (r != 0) {
-                const V w = __ldg(twN + (int64_t)r * s);
+                const V w = twn(twN, (int64_t)r * s);
                 af = cmul(af, w);
                 ag = cmul(ag, w);
             }
@@ -71,7 +71,7 @@ __device__ __forceinline__ void residue_row_body(const V* fr, const V* gr, V* hr
 // swizzled buffer dst: dst[s] = zeta_N^{r s} sum_{t < p} zeta_q^{r t} x[t m + s],
 // s < m, with N = q m; no barrier.
 template <class V>
-__device__ __forceinline__ void fold_row(const V* x, int64_t L, int m, int p, int q, int r, const V* __restrict__ twN,
+__device__ __forceinline__ void fold_row(const V* x, int64_t L, int m, int p, int q, int r, const TwTab<V> twN,
                                          V* dst, int tid, int nthr)
 {
     for (int s = tid; s < m; s += nthr) {
@@ -80,9 +80,9 @@ __device__ __forceinline__ void fold_row(const V* x, int64_t L, int m, int p, in
             const int64_t j = (int64_t)t * m + s;
             if (j >= L) break;
             if (r == 0) a = cadd(a, x[j]);
-            else a = cfma(x[j], __ldg(twN + (((int64_t)r * t) % q) * m), a);
+            else a = cfma(x[j], twn(twN, (((int64_t)r * t) % q) * m), a);
         }
-        if (r != 0) a = cmul(a, __ldg(twN + (int64_t)r * s));
+        if (r != 0) a = cmul(a, twn(twN, (int64_t)r * s));
         dst[sidx<V, true>(s)] = a;
     }
 }
@@ -102,7 +102,7 @@ template <class V> struct InPtrs {
 template <class V>
 __device__ __forceinline__ void residue_row_multi_body(const InPtrs<V>& in, int nin, int op, int64_t boff, V* hr,
                                                        int64_t L, int m, int p, int q, int r,
-                                                       const V* __restrict__ twN, const V* __restrict__ twm,
+                                                       const TwTab<V> twN, const V* __restrict__ twm,
                                                        const V* __restrict__ twml, const FftPlan& fp, V* smem,
                                                        int tid, int nthr)
 {
@@ -147,7 +147,7 @@ __device__ __forceinline__ void residue_row_multi_body(const InPtrs<V>& in, int 
 template <class V>
 __device__ __forceinline__ void residue_row_lam_body(const V* fr, const V* gr, V* hr, int64_t Lf, int64_t Lg, int mf,
                                                      int mg, int lam, int pf, int pg, int qg, int rg,
-                                                     const V* __restrict__ twN, const V* __restrict__ twf,
+                                                     const TwTab<V> twN, const V* __restrict__ twf,
                                                      const V* __restrict__ twfl, const FftPlan& fpf,
                                                      const V* __restrict__ twg, const V* __restrict__ twgl,
                                                      const FftPlan& fpg, V* smem, int tid, int nthr)
@@ -194,7 +194,7 @@ template <class V> __device__ __forceinline__ V real_pair_product(V a, V b)
 // to hr[0..m).  smem: three swizzled buffers of m.
 template <class V>
 __device__ __forceinline__ void residue_row_real_body(const V* zr, V* hr, int64_t L, int m, int p, int q, int r,
-                                                      const V* __restrict__ twN, const V* __restrict__ twm,
+                                                      const TwTab<V> twN, const V* __restrict__ twm,
                                                       const V* __restrict__ twml, const FftPlan& fp, V* smem, int tid,
                                                       int nthr)
 {
@@ -264,7 +264,7 @@ template <class V> constexpr int kColLoads = sizeof(V) == 8 ? 8 : 4;
 // yb[l ystride + c], times zeta_{Nf/q}^{l c} if post.
 template <class V>
 __device__ __forceinline__ void fft_cols_store_body(V* buf, V* tmp, V* yb, int64_t Cn, int ma, int q, int64_t c0,
-                                                    int C, int post, int64_t ystride, const V* __restrict__ twNf,
+                                                    int C, int post, int64_t ystride, const TwTab<V> twNf,
                                                     const V* __restrict__ twma, const V* __restrict__ twmal,
                                                     const FftPlan& fp, int tid, int nthr)
 {
@@ -274,7 +274,7 @@ __device__ __forceinline__ void fft_cols_store_body(V* buf, V* tmp, V* yb, int64
         const int64_t c = c0 + cl;
         if (c >= Cn) continue;
         V v = buf[e];
-        if (post && l != 0 && c != 0) v = cmul(v, __ldg(twNf + (int64_t)l * c * q));
+        if (post && l != 0 && c != 0) v = cmul(v, twn(twNf, (int64_t)l * c * q));
         yb[(int64_t)l * ystride + c] = v;
     }
     __syncthreads();
@@ -287,7 +287,7 @@ __device__ __forceinline__ void fft_cols_store_body(V* buf, V* tmp, V* yb, int64
 template <class V>
 __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn, int ma, int p, int q, int64_t Nf,
                                                    int64_t cs, int64_t cc, int64_t Lvalid, int r, int64_t c0, int C,
-                                                   int post, int64_t ystride, const V* __restrict__ twNf,
+                                                   int post, int64_t ystride, const TwTab<V> twNf,
                                                    const V* __restrict__ twma, const V* __restrict__ twmal,
                                                    const FftPlan& fp, V* smem, int tid, int nthr)
 {
@@ -320,8 +320,8 @@ __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn
                     xb[u] = (t + 1 < p && base[u] >= 0 && base[u] + off2 < Lvalid) ? x[base[u] + off2] : czero<V>();
                 }
                 // block t = 0 carries zeta_q^0 = 1: no multiplication
-                const V wa = (r == 0 || t == 0) ? czero<V>() : __ldg(twNf + (((int64_t)r * t) % q) * mq);
-                const V wb = r == 0 ? czero<V>() : __ldg(twNf + (((int64_t)r * (t + 1)) % q) * mq);
+                const V wa = (r == 0 || t == 0) ? czero<V>() : twn(twNf, (((int64_t)r * t) % q) * mq);
+                const V wb = r == 0 ? czero<V>() : twn(twNf, (((int64_t)r * (t + 1)) % q) * mq);
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     if (t == 0) acc[u] = xa[u];
@@ -337,7 +337,7 @@ __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn
             for (int t = 1; t < p; ++t) {
                 const int64_t off = (int64_t)t * ma * Cn;
                 if (off >= Lvalid) break;
-                const V w = r == 0 ? czero<V>() : __ldg(twNf + (((int64_t)r * t) % q) * mq);
+                const V w = r == 0 ? czero<V>() : twn(twNf, (((int64_t)r * t) % q) * mq);
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     if (base[u] < 0 || base[u] + off >= Lvalid) continue;
@@ -353,7 +353,7 @@ __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn
             V a = acc[u];
             if (r != 0 && base[u] >= 0) {
                 const int i = e / C, cl = e - i * C;
-                a = cmul(a, __ldg(twNf + (int64_t)r * (i * cs + (c0 + cl) * cc)));
+                a = cmul(a, twn(twNf, (int64_t)r * (i * cs + (c0 + cl) * cc)));
             }
             buf[e] = a;
         }
@@ -367,7 +367,7 @@ __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn
 // conj(zeta_{Nf/q}^{l c}) if pre.  smem: 2 smem_len(ma C).
 template <class V>
 __device__ __forceinline__ void ifft_cols_body(V* yb, int64_t Cn, int ma, int q, int64_t Nf, int64_t c0, int C,
-                                               int pre, const V* __restrict__ twNf, const V* __restrict__ twma,
+                                               int pre, const TwTab<V> twNf, const V* __restrict__ twma,
                                                const V* __restrict__ twmal, const FftPlan& fp, V* smem, int tid,
                                                int nthr)
 {
@@ -391,7 +391,7 @@ __device__ __forceinline__ void ifft_cols_body(V* yb, int64_t Cn, int ma, int q,
             if (e >= n) break;
             const int l = e / C, cl = e - l * C;
             const int64_t c = c0 + cl;
-            if (pre && l != 0 && c != 0 && c < Cn) v[u] = cmulc(v[u], __ldg(twNf + (int64_t)l * c * q));
+            if (pre && l != 0 && c != 0 && c < Cn) v[u] = cmulc(v[u], twn(twNf, (int64_t)l * c * q));
             buf[e] = v[u];
         }
     }
@@ -418,7 +418,7 @@ __device__ __forceinline__ void ifft_unfold_cols_body(const V* y, int64_t rstrid
                                                       int q, int64_t Nf, int64_t cs, int64_t cc, int64_t lo,
                                                       int64_t hi, int r0, int Dg, int first, int last,
                                                       typename real_of<V>::type scale, int64_t c0, int C, int pre,
-                                                      const V* __restrict__ twNf, const V* __restrict__ twma,
+                                                      const TwTab<V> twNf, const V* __restrict__ twma,
                                                       const V* __restrict__ twmal, const FftPlan& fp, V* smem,
                                                       int tid, int nthr)
 {
@@ -445,7 +445,7 @@ __device__ __forceinline__ void ifft_unfold_cols_body(const V* y, int64_t rstrid
                 if (e >= n) break;
                 const int l = e / C, cl = e - l * C;
                 const int64_t c = c0 + cl;
-                if (pre && l != 0 && c != 0 && c < Cn) v[u] = cmulc(v[u], __ldg(twNf + (int64_t)l * c * q));
+                if (pre && l != 0 && c != 0 && c < Cn) v[u] = cmulc(v[u], twn(twNf, (int64_t)l * c * q));
                 buf[e] = v[u];
             }
         }
@@ -457,12 +457,12 @@ __device__ __forceinline__ void ifft_unfold_cols_body(const V* y, int64_t rstrid
             const int64_t c = c0 + cl;
             if (c >= Cn) continue;
             V hv = buf[e];
-            if (r != 0) hv = cmulc(hv, __ldg(twNf + (int64_t)r * (i * cs + c * cc)));
+            if (r != 0) hv = cmulc(hv, twn(twNf, (int64_t)r * (i * cs + c * cc)));
             for (int t = 0; t < p; ++t) {
                 const int64_t lin = ((int64_t)t * ma + i) * Cn + c;
                 if (lin >= hi) break;
                 if (lin < lo) continue;
-                V v = (r != 0 && t != 0) ? cmulc(hv, __ldg(twNf + (((int64_t)r * t) % q) * mq)) : hv;
+                V v = (r != 0 && t != 0) ? cmulc(hv, twn(twNf, (((int64_t)r * t) % q) * mq)) : hv;
                 if (!init) v = cadd(ob[lin - lo], v);
                 if (fin) v = cscale(v, scale);
                 ob[lin - lo] = v;
@@ -482,7 +482,7 @@ template <class V, int PT>
 __device__ __forceinline__ void unfold_elem(V* ob, const V* __restrict__ h, int64_t hstride, int64_t Cn,
                                             int64_t ma, int64_t i, int64_t c, int p, int q, int64_t Nf, int64_t cs,
                                             int64_t cc, int64_t lo, int64_t hi, int r0, int Dg, int first, int last,
-                                            typename real_of<V>::type scale, const V* __restrict__ twNf)
+                                            typename real_of<V>::type scale, const TwTab<V> twNf)
 {
     const int64_t mq = Nf / q;
     for (int t0 = 0; t0 < p; t0 += PT) {
@@ -495,13 +495,13 @@ __device__ __forceinline__ void unfold_elem(V* ob, const V* __restrict__ h, int6
         for (int rr = 0; rr < Dg; ++rr) {
             const int r = r0 + rr;
             V hv = h[(int64_t)rr * hstride + i * Cn + c];
-            if (r != 0) hv = cmulc(hv, __ldg(twNf + (int64_t)r * (i * cs + c * cc)));
+            if (r != 0) hv = cmulc(hv, twn(twNf, (int64_t)r * (i * cs + c * cc)));
 #pragma unroll
             for (int tt = 0; tt < PT; ++tt) {
                 const int t = t0 + tt;
                 if (t < p) {
                     if (r == 0 || t == 0) acc[tt] = cadd(acc[tt], hv);
-                    else acc[tt] = cfmac(hv, __ldg(twNf + (((int64_t)r * t) % q) * mq), acc[tt]);
+                    else acc[tt] = cfmac(hv, twn(twNf, (((int64_t)r * t) % q) * mq), acc[tt]);
                 }
             }
         }

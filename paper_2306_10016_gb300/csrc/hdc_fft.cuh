@@ -316,6 +316,34 @@ template <class V, bool INV> struct DftLF<V, 8, INV> {
     }
 };
 
+// ------------------------------------------------ zeta_N^k of a fold/unfold
+// The fold and unfold twiddles zeta_N^k, k < N = q m, come from one table of
+// N entries (`full`) while it is small, and always in FP64; a large FP32 one
+// is replaced by two tables,
+// zeta_N^k = hi[k >> lb] lo[k & (2^lb - 1)] with hi[j] = zeta_N^{j 2^lb} and
+// lo[j] = zeta_N^j, each entry one exact-angle FP64 sincospi rounded once:
+// one more rounding and a complex product per twiddle instead of a gather
+// from a table of up to 2^25 entries, whose misses went to DRAM.
+template <class V> struct TwTab {
+    const V* full; // N entries, or null
+    const V* hi;   // ceil(N / 2^lb) entries
+    const V* lo;   // 2^lb entries
+    int lb;
+};
+
+template <class V> __device__ __forceinline__ V twn(const TwTab<V>& t, int64_t k)
+{
+    if constexpr (sizeof(V) == 16) {
+        return __ldg(t.full + k); // FP64 keeps whole tables (see tw_table)
+    } else {
+        if (t.full) return __ldg(t.full + k);
+        // the product in explicit FMAs, so it rounds the same wherever the
+        // compiler inlines it
+        const V h = __ldg(t.hi + (k >> t.lb)), l = __ldg(t.lo + (k & (((int64_t)1 << t.lb) - 1)));
+        return mkc<V>(fma(h.x, l.x, -(h.y * l.y)), fma(h.x, l.y, h.y * l.x));
+    }
+}
+
 // ---------------------------------------------------------- FFT plan
 
 #define HDC_MAX_STAGES 32

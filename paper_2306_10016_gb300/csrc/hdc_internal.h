@@ -63,6 +63,8 @@ template <typename T> const cx<T>* twiddles_lf(int64_t n, cudaError_t* err);
 // The packed per-stage tables of the n-point transform's plan (FftPlan::toff),
 // plain (lf = false) or twiddle-merged form: what fft_smem reads.
 template <typename T> const cx<T>* twiddles_fft(int64_t n, bool lf, cudaError_t* err);
+// zeta_N^k for the folds and unfolds: one table, or two for a large N (TwTab).
+template <typename T> TwTab<cx<T>> tw_table(int64_t N, cudaError_t* err);
 
 // ------------------------------------------------------------ launchers
 

@@ -150,7 +150,7 @@ static cudaError_t allow_smem(K kernel, size_t bytes)
 template <class V>
 __global__ void __launch_bounds__(kMaxThreads, 2)
 k_residue_rows(const V* f, const V* g, V* h, int64_t B, int64_t ld_f, int64_t ld_g, int64_t Lf, int64_t L, int m,
-               int p, int q, int r0, int Dg, const V* __restrict__ twN, const V* __restrict__ twm,
+               int p, int q, int r0, int Dg, const TwTab<V> twN, const V* __restrict__ twm,
                const V* __restrict__ twml, FftPlan fp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -169,7 +169,7 @@ cudaError_t launch_residue_rows(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_
     const int64_t Dg = (D < q - r0) ? D : (q - r0);
     if (B <= 0 || Dg <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-    const V* twN = twiddles<T>(q * m, &e);
+    const TwTab<V> twN = tw_table<T>(q * m, &e);
     if (e != cudaSuccess) return e;
     const V* twm = twiddles_fft<T>(m, false, &e);
     if (e != cudaSuccess) return e;
@@ -196,7 +196,7 @@ cudaError_t launch_residue_rows(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_
 template <class V>
 __global__ void __launch_bounds__(kMaxThreads, 2)
 k_residue_rows_lam(const V* f, const V* g, V* h, int64_t B, int64_t ld_f, int64_t ld_g, int64_t Lf, int64_t Lg,
-                   int mf, int lam, int pf, int pg, int qg, int r0, int Dg, const V* __restrict__ twN,
+                   int mf, int lam, int pf, int pg, int qg, int r0, int Dg, const TwTab<V> twN,
                    const V* __restrict__ twf, const V* __restrict__ twfl, FftPlan fpf, const V* __restrict__ twg,
                    const V* __restrict__ twgl, FftPlan fpg)
 {
@@ -219,7 +219,7 @@ cudaError_t launch_residue_rows_lam(const cx<T>* f, const cx<T>* g, cx<T>* h, in
     if (B <= 0 || Dg <= 0) return cudaSuccess;
     const int64_t mg = mf * lam;
     cudaError_t e = cudaSuccess;
-    const V* twN = twiddles<T>(qg * mg, &e);
+    const TwTab<V> twN = tw_table<T>(qg * mg, &e);
     if (e != cudaSuccess) return e;
     const V* twf = twiddles_fft<T>(mf, false, &e);
     if (e != cudaSuccess) return e;
@@ -251,7 +251,7 @@ cudaError_t launch_residue_rows_lam(const cx<T>* f, const cx<T>* g, cx<T>* h, in
 template <class V>
 __global__ void __launch_bounds__(kMaxThreads, 2)
 k_residue_rows_multi(InPtrs<V> in, int nin, int op, V* h, int64_t B, int64_t ld, int64_t L, int m, int p, int q,
-                     int r0, int Dg, const V* __restrict__ twN, const V* __restrict__ twm,
+                     int r0, int Dg, const TwTab<V> twN, const V* __restrict__ twm,
                      const V* __restrict__ twml, FftPlan fp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -271,7 +271,7 @@ cudaError_t launch_residue_rows_multi(const cx<T>* const* xs, int nin, int op, c
     const int64_t Dg = (D < q - r0) ? D : (q - r0);
     if (B <= 0 || Dg <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-    const V* twN = twiddles<T>(q * m, &e);
+    const TwTab<V> twN = tw_table<T>(q * m, &e);
     if (e != cudaSuccess) return e;
     const V* twm = twiddles_fft<T>(m, false, &e);
     if (e != cudaSuccess) return e;
@@ -364,7 +364,7 @@ constexpr long long kTmaWaitCycles = 2000000000LL;
 template <class V>
 __device__ __forceinline__ void fold_staged_tile(V* buf, int stride, const V* x, int64_t Cn, int ma, int p, int q,
                                                  int64_t Nf, int64_t cs, int64_t cc, int64_t Lvalid, int r,
-                                                 int64_t c0, int C, const V* __restrict__ twNf, int tid, int nthr)
+                                                 int64_t c0, int C, const TwTab<V> twNf, int tid, int nthr)
 {
     const int64_t mq = Nf / q;
     const int64_t afull = Lvalid / Cn;
@@ -381,9 +381,9 @@ __device__ __forceinline__ void fold_staged_tile(V* buf, int stride, const V* x,
             // block t = 0 carries zeta_q^0 = 1: no multiplication
             if (t == 0) acc = v;
             else if (r == 0) acc = cadd(acc, v);
-            else acc = cfma(v, __ldg(twNf + (((int64_t)r * t) % q) * mq), acc);
+            else acc = cfma(v, twn(twNf, (((int64_t)r * t) % q) * mq), acc);
         }
-        if (r != 0 && c < Cn) acc = cmul(acc, __ldg(twNf + (int64_t)r * (i * cs + c * cc)));
+        if (r != 0 && c < Cn) acc = cmul(acc, twn(twNf, (int64_t)r * (i * cs + c * cc)));
         buf[e] = acc;
     }
 }
@@ -424,7 +424,7 @@ __device__ __forceinline__ FoldBlock<V> fold_block(const ColSidesK<V>& sides, in
 template <class V>
 __global__ void __launch_bounds__(kMaxThreads, kColBlocks<V>)
 k_fold_fft_cols(ColSidesK<V> sides, int nside, int64_t B, int64_t Cn, int ma, int64_t Nf, int64_t cs, int64_t cc,
-                int r0, int Dg, int C, int nct, int post, const V* __restrict__ twNf, const V* __restrict__ twma,
+                int r0, int Dg, int C, int nct, int post, const TwTab<V> twNf, const V* __restrict__ twma,
                 const V* __restrict__ twmal, FftPlan fp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -444,7 +444,7 @@ template <class V>
 __global__ void __launch_bounds__(kMaxThreads, kColBlocks<V>)
 k_fold_fft_cols_tma(ColSidesK<V> sides, const __grid_constant__ ColMapsK maps, int tma_rows, int nside, int64_t B,
                     int64_t Cn, int ma, int64_t Nf, int64_t cs, int64_t cc, int r0, int Dg, int C, int nct, int post,
-                    const V* __restrict__ twNf, const V* __restrict__ twma, const V* __restrict__ twmal, FftPlan fp)
+                    const TwTab<V> twNf, const V* __restrict__ twma, const V* __restrict__ twmal, FftPlan fp)
 {
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ uint64_t bar;
@@ -571,7 +571,7 @@ cudaError_t launch_fold_fft_cols(const ColSide<T>* sides, int nside, int64_t B, 
     const int64_t Dg = (D < q0 - r0) ? D : (q0 - r0);
     if (B <= 0 || Dg <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-    const V* twNf = twiddles<T>(Nf, &e);
+    const TwTab<V> twNf = tw_table<T>(Nf, &e);
     if (e != cudaSuccess) return e;
     const V* twma = twiddles_fft<T>(ma, false, &e);
     if (e != cudaSuccess) return e;
@@ -615,7 +615,7 @@ cudaError_t launch_fold_fft_cols(const ColSide<T>* sides, int nside, int64_t B, 
 template <class V>
 __global__ void __launch_bounds__(kMaxThreads, kColBlocks<V>)
 k_ifft_cols(V* y, int64_t B, int64_t Cn, int ma, int q, int64_t Nf, int Dg, int C, int nct, int pre,
-            const V* __restrict__ twNf, const V* __restrict__ twma, const V* __restrict__ twmal, FftPlan fp)
+            const TwTab<V> twNf, const V* __restrict__ twma, const V* __restrict__ twmal, FftPlan fp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     int64_t blk = blockIdx.x;
@@ -634,7 +634,7 @@ cudaError_t launch_ifft_cols(cx<T>* y, int64_t B, int64_t Cn, int64_t ma, int64_
     using V = cx<T>;
     if (B <= 0 || D <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-    const V* twNf = twiddles<T>(Nf, &e);
+    const TwTab<V> twNf = tw_table<T>(Nf, &e);
     if (e != cudaSuccess) return e;
     const V* twma = twiddles_fft<T>(ma, false, &e);
     if (e != cudaSuccess) return e;
@@ -661,7 +661,7 @@ template <class V, int PT>
 __global__ void __launch_bounds__(256)
 k_unfold(V* out, const V* __restrict__ h, int64_t B, int64_t bstride, int64_t Cn, int64_t ma,
          int p, int q, int64_t Nf, int64_t cs, int64_t cc, int64_t lo, int64_t hi, int r0, int Dg,
-         int first, int last, typename real_of<V>::type scale, const V* __restrict__ twNf)
+         int first, int last, typename real_of<V>::type scale, const TwTab<V> twNf)
 {
     const int64_t per = ma * Cn;
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -683,7 +683,7 @@ cudaError_t launch_unfold(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstride
     const int64_t Dg = (D < q - r0) ? D : (q - r0);
     if (B <= 0 || Dg <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-    const V* twNf = twiddles<T>(Nf, &e);
+    const TwTab<V> twNf = tw_table<T>(Nf, &e);
     if (e != cudaSuccess) return e;
     const int thr = 256;
     const int64_t total = ma * Cn * B;
@@ -703,7 +703,7 @@ template <class V>
 __global__ void __launch_bounds__(kMaxThreads, kColBlocks<V>)
 k_ifft_unfold_cols(const V* y, V* out, int64_t B, int64_t bstride, int64_t Cn, int ma, int p, int q, int64_t Nf,
                    int64_t cs, int64_t cc, int64_t lo, int64_t hi, int r0, int Dg, int first, int last,
-                   typename real_of<V>::type scale, int C, int nct, int pre, const V* __restrict__ twNf,
+                   typename real_of<V>::type scale, int C, int nct, int pre, const TwTab<V> twNf,
                    const V* __restrict__ twma, const V* __restrict__ twmal, FftPlan fp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -736,7 +736,7 @@ cudaError_t launch_ifft_unfold(cx<T>* y, cx<T>* out, int64_t B, int64_t bstride,
         return launch_unfold<T>(out, y, B, bstride, Cn, ma, p, q, Nf, cs, cc, lo, hi, r0, Dg, first, last, scale, st);
     }
     cudaError_t e = cudaSuccess;
-    const V* twNf = twiddles<T>(Nf, &e);
+    const TwTab<V> twNf = tw_table<T>(Nf, &e);
     if (e != cudaSuccess) return e;
     const V* twma = twiddles_fft<T>(ma, false, &e);
     if (e != cudaSuccess) return e;
@@ -777,7 +777,7 @@ template <typename T> cudaError_t launch_pack_real(const T* f, const T* g, cx<T>
 template <class V>
 __global__ void __launch_bounds__(kMaxThreads, 2)
 k_residue_rows_real(const V* z, V* h, int64_t B, int64_t ld, int64_t L, int m, int p, int q, int r0,
-                    const V* __restrict__ twN, const V* __restrict__ twm, const V* __restrict__ twml, FftPlan fp)
+                    const TwTab<V> twN, const V* __restrict__ twm, const V* __restrict__ twml, FftPlan fp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int64_t b = blockIdx.x % B;
@@ -793,7 +793,7 @@ cudaError_t launch_residue_rows_real(const cx<T>* z, cx<T>* h, int64_t B, int64_
     using V = cx<T>;
     if (B <= 0 || Dg <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-    const V* twN = twiddles<T>(q * m, &e);
+    const TwTab<V> twN = tw_table<T>(q * m, &e);
     if (e != cudaSuccess) return e;
     const V* twm = twiddles_fft<T>(m, false, &e);
     if (e != cudaSuccess) return e;
@@ -910,7 +910,7 @@ template <class V>
 __global__ void k_unfold_real(typename real_of<V>::type* out, const V* __restrict__ h, int64_t B, int64_t bstride,
                               int64_t Cn, int64_t ma, int p, int q, int64_t Nf, int64_t cs, int64_t cc, int64_t lo,
                               int64_t hi, int r0, int Dg, int first, int last, typename real_of<V>::type scale,
-                              const V* __restrict__ twNf)
+                              const TwTab<V> twNf)
 {
     using T = typename real_of<V>::type;
     const int64_t per = ma * Cn;
@@ -933,8 +933,8 @@ __global__ void k_unfold_real(typename real_of<V>::type* out, const V* __restric
             const T w = (r == 0 || 2 * r == q) ? (T)1 : (T)2;
             V hv = hb[(int64_t)rr * hstride + i * Cn + c];
             if (r != 0) {
-                hv = cmulc(hv, __ldg(twNf + (int64_t)r * (i * cs + c * cc)));
-                if (t != 0) hv = cmulc(hv, __ldg(twNf + (((int64_t)r * t) % q) * mq));
+                hv = cmulc(hv, twn(twNf, (int64_t)r * (i * cs + c * cc)));
+                if (t != 0) hv = cmulc(hv, twn(twNf, (((int64_t)r * t) % q) * mq));
             }
             acc += w * hv.x;
         }
@@ -953,7 +953,7 @@ cudaError_t launch_unfold_real(T* out, const cx<T>* h, int64_t B, int64_t bstrid
     using V = cx<T>;
     if (B <= 0 || Dg <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-    const V* twNf = twiddles<T>(Nf, &e);
+    const TwTab<V> twNf = tw_table<T>(Nf, &e);
     if (e != cudaSuccess) return e;
     const int thr = 256;
     const int64_t total = ma * Cn * B;
@@ -1013,6 +1013,31 @@ cudaError_t launch_twiddle_into(cx<T>* tw, int64_t n, cudaStream_t st)
     return launch_twiddle<T>(tw, n, st);
 }
 
+// tw[i] = zeta_N^{(i stride) mod N}, i < count, from one FP64 sincospi of the
+// exact integer angle each (the two tables of a large TwTab)
+template <class V>
+__global__ void k_twiddle_strided(V* tw, int64_t count, int64_t N, int64_t stride)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int64_t k = (int64_t)(((unsigned long long)i * (unsigned long long)stride) % (unsigned long long)N);
+    const int64_t kk = (2 * k > N) ? k - N : k;
+    double s, c;
+    sincospi(2.0 * (double)kk / (double)N, &s, &c);
+    using T = typename real_of<V>::type;
+    tw[i] = mkc<V>((T)c, (T)s);
+}
+
+template <typename T>
+cudaError_t launch_twiddle_strided(cx<T>* tw, int64_t count, int64_t N, int64_t stride, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    const int thr = 256;
+    LaunchScope ls(K_TWIDDLE, st, 0.0, 16.0 * count);
+    k_twiddle_strided<cx<T>><<<(unsigned)((count + thr - 1) / thr), thr, 0, st>>>(tw, count, N, stride);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_twiddle_fft_into(cx<T>* tw, const FftPlan& fp, bool lf, cudaStream_t st)
 {
@@ -1048,7 +1073,7 @@ cudaError_t launch_residue_rows_tw(const cx<T>* f, const cx<T>* g, cx<T>* h, int
     LaunchScope ls(K_RESIDUE_ROWS, st, (double)(B * Dg) * (3.0 * fft_flops((double)m) + 6.0 * m + fold),
                    (2.0 * B * Lrow + (double)(Dg * B * m)) * sizeof(V));
     kern<<<(unsigned)blocks, thr, smem, st>>>(f, g, h, B, ld_in, ld_in, L, L, (int)m, (int)p, (int)q, (int)r0,
-                                              (int)Dg, twN, twm, twml, fp);
+                                              (int)Dg, TwTab<V>{ twN, nullptr, nullptr, 0 }, twm, twml, fp);
     return cudaGetLastError();
 }
 
@@ -1068,13 +1093,14 @@ cudaError_t launch_unfold_tw(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstr
                    ((double)(Dg * B * ma * Cn) + (first ? 1.0 : 2.0) * B * Lvalid) * sizeof(V));
     k_unfold<V, 4><<<(unsigned)blocks, thr, 0, st>>>(out, h, B, bstride, Cn, ma, (int)p, (int)q, Nf, cs, cc,
                                                      (int64_t)0, Lvalid, (int)r0, (int)Dg, first, last, (T)scale,
-                                                     twNf);
+                                                     TwTab<V>{ twNf, nullptr, nullptr, 0 });
     return cudaGetLastError();
 }
 
 #define HDC_INST_TW(T)                                                                                    \
     template cudaError_t launch_twiddle_into<T>(cx<T>*, int64_t, cudaStream_t);                          \
     template cudaError_t launch_twiddle_fft_into<T>(cx<T>*, const FftPlan&, bool, cudaStream_t);          \
+    template cudaError_t launch_twiddle_strided<T>(cx<T>*, int64_t, int64_t, int64_t, cudaStream_t);      \
     template cudaError_t launch_residue_rows_tw<T>(const cx<T>*, const cx<T>*, cx<T>*, int64_t, int64_t, \
                                                    int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, \
                                                    const cx<T>*, const cx<T>*, const cx<T>*, cudaStream_t); \

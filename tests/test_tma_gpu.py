@@ -1,8 +1,10 @@
 """The strided fold's two load paths: tiles staged by TMA box copies and the
-plain loads.  Both fold the same values in the same order, so their outputs
-are bit-identical; the cases cover partial last rows, one and two fold
-blocks, several boxes per block, batches, 2-D/3-D outer axes, several
-inputs per launch, and layouts that must fall back to the plain loads."""
+plain loads.  Both fold the same values in the same order: in FP64 their
+outputs are bit-identical; in FP32, whose large fold twiddles are products of
+two table entries formed inside each kernel, they agree to rounding.  The
+cases cover partial last rows, one and two fold blocks, several boxes per
+block, batches, 2-D/3-D outer axes, several inputs per launch, and layouts
+that must fall back to the plain loads."""
 import numpy as np
 import pytest
 
@@ -39,6 +41,13 @@ def _both(hdc, run):
     return a, b, n_tma
 
 
+def _same(a, b):
+    """Bit-identical in FP64; within 2e-6 of the larger magnitude in FP32."""
+    if a.dtype in (np.complex128, np.float64):
+        return np.array_equal(a, b)
+    return float(np.max(np.abs(a - b))) <= 2e-6 * float(np.max(np.abs(a)))
+
+
 def _inputs(shape, seed, dt):
     f = synth.unit_disk(seed, shape)
     g = synth.unit_disk(seed + 1, shape)
@@ -61,7 +70,7 @@ def test_split_1d_tma_matches_plain(hdc, dt, tol, L, m, D):
     f, g, ft, gt = _inputs((L,), 7100 + L % 97, dt)
     a, b, n_tma = _both(hdc, lambda: hdc.conv1d(ft, gt, m, D=D))
     assert n_tma > 0
-    assert np.array_equal(a, b)
+    assert _same(a, b)
     assert rel_max_err(b, oracle.conv_fft(f, g)) < tol
 
 
@@ -69,7 +78,7 @@ def test_split_1d_tma_matches_plain(hdc, dt, tol, L, m, D):
 def test_batched_rows_tma_matches_plain(hdc, dt, tol):
     f, g, ft, gt = _inputs((3, 20000), 7200, dt)
     a, b, n_tma = _both(hdc, lambda: hdc.conv1d(ft, gt, 16384, D=2))
-    assert n_tma > 0 and np.array_equal(a, b)
+    assert n_tma > 0 and _same(a, b)
     for i in range(3):
         assert rel_max_err(b[i], oracle.conv_fft(f[i], g[i])) < tol
 
@@ -80,7 +89,7 @@ def test_batched_rows_tma_matches_plain(hdc, dt, tol):
 def test_outer_axes_tma_matches_plain(hdc, dt, tol, shape, m):
     f, g, ft, gt = _inputs(shape, 7300 + len(shape), dt)
     a, b, n_tma = _both(hdc, lambda: hdc.convnd(ft, gt, len(shape), m))
-    assert n_tma > 0 and np.array_equal(a, b)
+    assert n_tma > 0 and _same(a, b)
     assert rel_max_err(b, oracle.conv_fft(f, g)) < tol
 
 
@@ -89,7 +98,7 @@ def test_odd_row_length_falls_back(hdc):
     the fold takes the plain loads (and the result is the same)."""
     f, g, ft, gt = _inputs((60, 201), 7400, torch.complex64)
     a, b, n_tma = _both(hdc, lambda: hdc.convnd(ft, gt, 2, [128, 405]))
-    assert n_tma == 0 and np.array_equal(a, b)
+    assert n_tma == 0 and _same(a, b)
     assert rel_max_err(b, oracle.conv_fft(f, g)) < 5e-5
 
 
@@ -97,11 +106,11 @@ def test_multi_and_real_tma_match_plain(hdc):
     xs_np = [synth.unit_disk(7500 + i, (30000,)) for i in range(4)]
     xs = [torch.from_numpy(x).cuda() for x in xs_np]
     a, b, n_tma = _both(hdc, lambda: hdc.convnd_multi(xs, 1, [16384], op="dot"))
-    assert n_tma > 0 and np.array_equal(a, b)
+    assert n_tma > 0 and _same(a, b)
     fr = torch.from_numpy(synth.standard_normal(7510, 30000)).cuda()
     gr = torch.from_numpy(synth.standard_normal(7511, 30000)).cuda()
     a, b, n_tma = _both(hdc, lambda: hdc.convnd_real(fr, gr, 1, [16384]))
-    assert n_tma > 0 and np.array_equal(a, b)
+    assert n_tma > 0 and _same(a, b)
 
 
 def test_first_launch_at_the_shared_memory_threshold(hdc):
