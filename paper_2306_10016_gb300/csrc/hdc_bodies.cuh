@@ -492,16 +492,28 @@ __device__ __forceinline__ void unfold_elem(V* ob, const V* __restrict__ h, int6
         V acc[PT];
 #pragma unroll
         for (int tt = 0; tt < PT; ++tt) acc[tt] = czero<V>();
-        for (int rr = 0; rr < Dg; ++rr) {
-            const int r = r0 + rr;
-            V hv = h[(int64_t)rr * hstride + i * Cn + c];
-            if (r != 0) hv = cmulc(hv, twn(twNf, (int64_t)r * (i * cs + c * cc)));
+        // FP32: the residues' values are loaded four at a time before they
+        // are used, so their loads are in flight together (FP64, bound by
+        // its arithmetic, measured 1-3 % slower that way)
+        constexpr int RB = sizeof(V) == 8 ? 4 : 1;
+        for (int rb = 0; rb < Dg; rb += RB) {
+            V hb[RB];
 #pragma unroll
-            for (int tt = 0; tt < PT; ++tt) {
-                const int t = t0 + tt;
-                if (t < p) {
-                    if (r == 0 || t == 0) acc[tt] = cadd(acc[tt], hv);
-                    else acc[tt] = cfmac(hv, twn(twNf, (((int64_t)r * t) % q) * mq), acc[tt]);
+            for (int k = 0; k < RB; ++k)
+                hb[k] = rb + k < Dg ? h[(int64_t)(rb + k) * hstride + i * Cn + c] : czero<V>();
+#pragma unroll
+            for (int k = 0; k < RB; ++k) {
+                if (rb + k >= Dg) break;
+                const int r = r0 + rb + k;
+                V hv = hb[k];
+                if (r != 0) hv = cmulc(hv, twn(twNf, (int64_t)r * (i * cs + c * cc)));
+#pragma unroll
+                for (int tt = 0; tt < PT; ++tt) {
+                    const int t = t0 + tt;
+                    if (t < p) {
+                        if (r == 0 || t == 0) acc[tt] = cadd(acc[tt], hv);
+                        else acc[tt] = cfmac(hv, twn(twNf, (((int64_t)r * t) % q) * mq), acc[tt]);
+                    }
                 }
             }
         }
