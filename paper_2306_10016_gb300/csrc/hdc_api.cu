@@ -183,9 +183,6 @@ template TwTab<cx<double>> tw_table<double>(int64_t, cudaError_t*);
 template TwTab<cx<float>> tw_table<float>(int64_t, cudaError_t*);
 
 template <typename T> const cx<T>* twiddles(int64_t n, cudaError_t* err) { return twiddle_table<T>(n, false, err); }
-template <typename T> const cx<T>* twiddles_lf(int64_t n, cudaError_t* err) { return twiddle_table<T>(n, true, err); }
-template const cx<double>* twiddles_lf<double>(int64_t, cudaError_t*);
-template const cx<float>* twiddles_lf<float>(int64_t, cudaError_t*);
 template const cx<double>* twiddles<double>(int64_t, cudaError_t*);
 template const cx<float>* twiddles<float>(int64_t, cudaError_t*);
 

@@ -55,13 +55,11 @@ struct LaunchScope {
 // 5 n log2(n): the flop count convention of one n-point complex FFT.
 double fft_flops(double n);
 
-// Twiddle table zeta_n^k, k < n, of dtype T on the current device (cached),
-// and the same values in the scale-tangent form of the twiddle-merged
-// butterflies (see lf_bfly).
+// Twiddle table zeta_n^k, k < n, of dtype T on the current device (cached).
 template <typename T> const cx<T>* twiddles(int64_t n, cudaError_t* err);
-template <typename T> const cx<T>* twiddles_lf(int64_t n, cudaError_t* err);
 // The packed per-stage tables of the n-point transform's plan (FftPlan::toff),
-// plain (lf = false) or twiddle-merged form: what fft_smem reads.
+// plain (lf = false) or in the scale-tangent form of the twiddle-merged
+// butterflies (lf = true, see lf_bfly): what fft_smem reads.
 template <typename T> const cx<T>* twiddles_fft(int64_t n, bool lf, cudaError_t* err);
 // zeta_N^k for the folds and unfolds: one table, or two for a large N (TwTab).
 template <typename T> TwTab<cx<T>> tw_table(int64_t N, cudaError_t* err);
