@@ -33,6 +33,7 @@ template <typename T> cudaError_t launch_twiddle(cx<T>* tw, int64_t n, cudaStrea
 template <typename T> cudaError_t launch_twiddle_lf(cx<T>* tw, int64_t n, cudaStream_t st);
 template <typename T>
 cudaError_t launch_twiddle_strided(cx<T>* tw, int64_t count, int64_t N, int64_t stride, cudaStream_t st);
+template <typename T> cudaError_t launch_twiddle_colmajor(cx<T>* tw, int64_t ma, int64_t Cn, cudaStream_t st);
 
 // ----------------------------------------------------------- FFT plans
 
@@ -179,6 +180,36 @@ template <typename T> TwTab<cx<T>> tw_table(int64_t N, cudaError_t* err)
     t.hi = strided_table<T>((N + S - 1) / S, N, S, 16, err);
     return t;
 }
+// The column-major four-step twiddles of an ma x Cn split (cached per pair).
+template <typename T> const cx<T>* twiddles_colmajor(int64_t ma, int64_t Cn, cudaError_t* err)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { *err = e; return nullptr; }
+    // kind 32 + dtype, with ma folded into the kind so the key is (ma, Cn)
+    const int dt = (sizeof(T) == 8 ? 1 : 0) + 32 + (int)ma * 64;
+    std::lock_guard<std::mutex> lk(g_tw_mu);
+    auto key = std::make_tuple(dev, Cn, dt);
+    auto it = g_tw.find(key);
+    if (it != g_tw.end()) return reinterpret_cast<const cx<T>*>(it->second);
+    void* p = nullptr;
+    e = cudaMalloc(&p, (size_t)(ma * Cn) * sizeof(cx<T>));
+    if (e != cudaSuccess) { *err = e; return nullptr; }
+    cudaStream_t s;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        e = launch_twiddle_colmajor<T>(reinterpret_cast<cx<T>*>(p), ma, Cn, s);
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = e2;
+        cudaStreamDestroy(s);
+    }
+    if (e != cudaSuccess) { cudaFree(p); *err = e; return nullptr; }
+    g_tw[key] = p;
+    return reinterpret_cast<const cx<T>*>(p);
+}
+template const cx<double>* twiddles_colmajor<double>(int64_t, int64_t, cudaError_t*);
+template const cx<float>* twiddles_colmajor<float>(int64_t, int64_t, cudaError_t*);
+
 template TwTab<cx<double>> tw_table<double>(int64_t, cudaError_t*);
 template TwTab<cx<float>> tw_table<float>(int64_t, cudaError_t*);
 

@@ -41,6 +41,7 @@ template <class V> struct BConv {
     const V* twm1; // packed stage tables of the m1-point transform (split columns)
     const V* twml;  // the same two tables in scale-tangent form
     const V* twm1l;
+    const V* tpm;   // split: zeta_m^{l1 c} at c m1 + l1 (column-major four-step twiddles)
     int64_t L, N, ws_off;
     int m, p, q, m1, m2, C, nct, per; // m1 == 0: fused; per = outputs per residue block
     FftPlan fpm;                      // plan of m (fused) or m2 (split rows)
@@ -129,7 +130,7 @@ k_batched(const BConv<V>* __restrict__ convs, const BItem* __restrict__ it0, con
                 const V* x = which ? gp_[itm.conv] : fp_[itm.conv];
                 V* yb = cws + (int64_t)which * cv.q * cv.m + (int64_t)r * cv.m;
                 fold_fft_cols_body<V>(x, yb, cv.m2, cv.m1, cv.p, cv.q, cv.N, cv.m2, 1, cv.L, r, (int64_t)ct * cv.C,
-                                      cv.C, 1, cv.m2, cv.twN, cv.twm1, cv.twm1l, cv.fpm1, smem, tid, nthr);
+                                      cv.C, 1, cv.m2, cv.twN, cv.tpm, cv.twm1, cv.twm1l, cv.fpm1, smem, tid, nthr);
             } else if (ph == 1) {
                 if (cv.m1 == 0) {
                     const int r = itm.a;
@@ -145,7 +146,7 @@ k_batched(const BConv<V>* __restrict__ convs, const BItem* __restrict__ it0, con
             } else if (ph == 2) {
                 const int r = itm.a, ct = itm.c;
                 ifft_cols_body<V>(cws + (int64_t)r * cv.m, cv.m2, cv.m1, cv.q, cv.N, (int64_t)ct * cv.C, cv.C, 1,
-                                  cv.twN, cv.twm1, cv.twm1l, cv.fpm1, smem, tid, nthr);
+                                  cv.twN, cv.tpm, cv.twm1, cv.twm1l, cv.fpm1, smem, tid, nthr);
             } else {
                 const int64_t e0 = (int64_t)itm.a * kUnfoldChunk;
                 const int64_t e1 = min((int64_t)cv.per, e0 + kUnfoldChunk);
@@ -259,6 +260,10 @@ template <typename T> int build(hdc_batched* b)
             if (e != cudaSuccess) return HDC_ERR_CUDA;
             cv.twm1l = twiddles_fft<T>(m1, true, &e);
             if (e != cudaSuccess) return HDC_ERR_CUDA;
+            if (sizeof(T) == 8) {   // FP64 only, as in the one-pass kernels
+                cv.tpm = twiddles_colmajor<T>(m1, m2, &e);
+                if (e != cudaSuccess) return HDC_ERR_CUDA;
+            }
             cv.fpm1 = make_fft_plan(m1);
             cv.C = col_tile_b<T>(m2, m1);
             cv.nct = (int)((m2 + cv.C - 1) / cv.C);

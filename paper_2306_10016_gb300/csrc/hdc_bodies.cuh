@@ -261,10 +261,12 @@ template <class V> constexpr int kColLoads = sizeof(V) == 8 ? 8 : 4;
 // Second half of the strided fold + FFT pass: the folded tile (ma x C,
 // element i C + cl) is in buf and the block is synchronised; FFT of size ma
 // over the tile's columns, then column c0 + cl (< Cn) of row l goes to
-// yb[l ystride + c], times zeta_{Nf/q}^{l c} if post.
+// yb[l ystride + c], times zeta_{Nf/q}^{l c} if post: in FP64 from tpm[c ma + l]
+// when the caller has that column-major table (Nf/q = ma Cn), else from twNf.
 template <class V>
 __device__ __forceinline__ void fft_cols_store_body(V* buf, V* tmp, V* yb, int64_t Cn, int ma, int q, int64_t c0,
                                                     int C, int post, int64_t ystride, const TwTab<V> twNf,
+                                                    const V* __restrict__ tpm,
                                                     const V* __restrict__ twma, const V* __restrict__ twmal,
                                                     const FftPlan& fp, int tid, int nthr)
 {
@@ -274,7 +276,7 @@ __device__ __forceinline__ void fft_cols_store_body(V* buf, V* tmp, V* yb, int64
         const int64_t c = c0 + cl;
         if (c >= Cn) continue;
         V v = buf[e];
-        if (post && l != 0 && c != 0) v = cmul(v, twn(twNf, (int64_t)l * c * q));
+        if (post && l != 0 && c != 0) v = cmul(v, (sizeof(V) == 16 && tpm) ? __ldg(tpm + c * ma + l) : twn(twNf, (int64_t)l * c * q));
         yb[(int64_t)l * ystride + c] = v;
     }
     __syncthreads();
@@ -288,6 +290,7 @@ template <class V>
 __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn, int ma, int p, int q, int64_t Nf,
                                                    int64_t cs, int64_t cc, int64_t Lvalid, int r, int64_t c0, int C,
                                                    int post, int64_t ystride, const TwTab<V> twNf,
+                                                   const V* __restrict__ tpm,
                                                    const V* __restrict__ twma, const V* __restrict__ twmal,
                                                    const FftPlan& fp, V* smem, int tid, int nthr)
 {
@@ -359,7 +362,7 @@ __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn
         }
     }
     __syncthreads();
-    fft_cols_store_body<V>(buf, tmp, yb, Cn, ma, q, c0, C, post, ystride, twNf, twma, twmal, fp, tid, nthr);
+    fft_cols_store_body<V>(buf, tmp, yb, Cn, ma, q, c0, C, post, ystride, twNf, tpm, twma, twmal, fp, tid, nthr);
 }
 
 // Inverse FFT of size ma along the strided axis of yb[l][c] (row length Cn)
@@ -367,7 +370,8 @@ __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn
 // conj(zeta_{Nf/q}^{l c}) if pre.  smem: 2 smem_len(ma C).
 template <class V>
 __device__ __forceinline__ void ifft_cols_body(V* yb, int64_t Cn, int ma, int q, int64_t Nf, int64_t c0, int C,
-                                               int pre, const TwTab<V> twNf, const V* __restrict__ twma,
+                                               int pre, const TwTab<V> twNf, const V* __restrict__ tpm,
+                                               const V* __restrict__ twma,
                                                const V* __restrict__ twmal, const FftPlan& fp, V* smem, int tid,
                                                int nthr)
 {
@@ -391,7 +395,8 @@ __device__ __forceinline__ void ifft_cols_body(V* yb, int64_t Cn, int ma, int q,
             if (e >= n) break;
             const int l = e / C, cl = e - l * C;
             const int64_t c = c0 + cl;
-            if (pre && l != 0 && c != 0 && c < Cn) v[u] = cmulc(v[u], twn(twNf, (int64_t)l * c * q));
+            if (pre && l != 0 && c != 0 && c < Cn)
+                    v[u] = cmulc(v[u], (sizeof(V) == 16 && tpm) ? __ldg(tpm + c * ma + l) : twn(twNf, (int64_t)l * c * q));
             buf[e] = v[u];
         }
     }
@@ -418,7 +423,8 @@ __device__ __forceinline__ void ifft_unfold_cols_body(const V* y, int64_t rstrid
                                                       int q, int64_t Nf, int64_t cs, int64_t cc, int64_t lo,
                                                       int64_t hi, int r0, int Dg, int first, int last,
                                                       typename real_of<V>::type scale, int64_t c0, int C, int pre,
-                                                      const TwTab<V> twNf, const V* __restrict__ twma,
+                                                      const TwTab<V> twNf, const V* __restrict__ tpm,
+                                                      const V* __restrict__ twma,
                                                       const V* __restrict__ twmal, const FftPlan& fp, V* smem,
                                                       int tid, int nthr)
 {
@@ -445,7 +451,8 @@ __device__ __forceinline__ void ifft_unfold_cols_body(const V* y, int64_t rstrid
                 if (e >= n) break;
                 const int l = e / C, cl = e - l * C;
                 const int64_t c = c0 + cl;
-                if (pre && l != 0 && c != 0 && c < Cn) v[u] = cmulc(v[u], twn(twNf, (int64_t)l * c * q));
+                if (pre && l != 0 && c != 0 && c < Cn)
+                    v[u] = cmulc(v[u], (sizeof(V) == 16 && tpm) ? __ldg(tpm + c * ma + l) : twn(twNf, (int64_t)l * c * q));
                 buf[e] = v[u];
             }
         }

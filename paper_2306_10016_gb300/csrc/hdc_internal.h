@@ -70,6 +70,9 @@ template <typename T> const cx<T>* twiddles(int64_t n, cudaError_t* err);
 template <typename T> const cx<T>* twiddles_fft(int64_t n, bool lf, cudaError_t* err);
 // zeta_N^k for the folds and unfolds: one table, or two for a large N (TwTab).
 template <typename T> TwTab<cx<T>> tw_table(int64_t N, cudaError_t* err);
+// zeta_{ma Cn}^{l c} at c ma + l (l < ma, c < Cn): the four-step twiddles of an
+// ma x Cn split in the order a column tile reads them.
+template <typename T> const cx<T>* twiddles_colmajor(int64_t ma, int64_t Cn, cudaError_t* err);
 
 // ------------------------------------------------------------ launchers
 

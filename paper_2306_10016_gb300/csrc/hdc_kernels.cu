@@ -424,8 +424,8 @@ __device__ __forceinline__ FoldBlock<V> fold_block(const ColSidesK<V>& sides, in
 template <class V>
 __global__ void __launch_bounds__(kMaxThreads, kColBlocks<V>)
 k_fold_fft_cols(ColSidesK<V> sides, int nside, int64_t B, int64_t Cn, int ma, int64_t Nf, int64_t cs, int64_t cc,
-                int r0, int Dg, int C, int nct, int post, const TwTab<V> twNf, const V* __restrict__ twma,
-                const V* __restrict__ twmal, FftPlan fp)
+                int r0, int Dg, int C, int nct, int post, const TwTab<V> twNf, const V* __restrict__ tpm,
+                const V* __restrict__ twma, const V* __restrict__ twmal, FftPlan fp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const FoldBlock<V> fb = fold_block<V>(sides, nside, B, Cn, ma, r0, Dg, C, nct);
@@ -433,7 +433,7 @@ k_fold_fft_cols(ColSidesK<V> sides, int nside, int64_t B, int64_t Cn, int ma, in
     if (fb.skip) return;
     const ColSideK<V>& sd = sides.s[fb.which];
     fold_fft_cols_body<V>(fb.x, fb.yb, Cn, ma, sd.p, sd.q, Nf, cs, cc, sd.Lvalid, fb.r, fb.c0, C, post,
-                          (int64_t)sd.lam * Cn, twNf, twma, twmal, fp, reinterpret_cast<V*>(smraw), threadIdx.x,
+                          (int64_t)sd.lam * Cn, twNf, tpm, twma, twmal, fp, reinterpret_cast<V*>(smraw), threadIdx.x,
                           blockDim.x);
 }
 
@@ -444,7 +444,8 @@ template <class V>
 __global__ void __launch_bounds__(kMaxThreads, kColBlocks<V>)
 k_fold_fft_cols_tma(ColSidesK<V> sides, const __grid_constant__ ColMapsK maps, int tma_rows, int nside, int64_t B,
                     int64_t Cn, int ma, int64_t Nf, int64_t cs, int64_t cc, int r0, int Dg, int C, int nct, int post,
-                    const TwTab<V> twNf, const V* __restrict__ twma, const V* __restrict__ twmal, FftPlan fp)
+                    const TwTab<V> twNf, const V* __restrict__ tpm, const V* __restrict__ twma,
+                    const V* __restrict__ twmal, FftPlan fp)
 {
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ uint64_t bar;
@@ -455,7 +456,7 @@ k_fold_fft_cols_tma(ColSidesK<V> sides, const __grid_constant__ ColMapsK maps, i
     const int tid = threadIdx.x, nthr = blockDim.x;
     if ((smem_u32(buf) & 127) != 0) {
         fold_fft_cols_body<V>(fb.x, fb.yb, Cn, ma, sd.p, sd.q, Nf, cs, cc, sd.Lvalid, fb.r, fb.c0, C, post,
-                              (int64_t)sd.lam * Cn, twNf, twma, twmal, fp, buf, tid, nthr);
+                              (int64_t)sd.lam * Cn, twNf, tpm, twma, twmal, fp, buf, tid, nthr);
         return;
     }
     const int n = ma * C;
@@ -489,8 +490,21 @@ k_fold_fft_cols_tma(ColSidesK<V> sides, const __grid_constant__ ColMapsK maps, i
     fold_staged_tile<V>(buf, stride, fb.x, Cn, ma, sd.p, sd.q, Nf, cs, cc, sd.Lvalid, fb.r, fb.c0, C, twNf, tid,
                         nthr);
     __syncthreads();
-    fft_cols_store_body<V>(buf, buf + stride, fb.yb, Cn, ma, sd.q, fb.c0, C, post, (int64_t)sd.lam * Cn, twNf, twma,
-                           twmal, fp, tid, nthr);
+    fft_cols_store_body<V>(buf, buf + stride, fb.yb, Cn, ma, sd.q, fb.c0, C, post, (int64_t)sd.lam * Cn, twNf, tpm,
+                           twma, twmal, fp, tid, nthr);
+}
+
+// The column-major four-step twiddle table of an FP64 ma x Cn split when a
+// pass applies those twiddles (flag set and Nf / q = ma Cn), else null (the
+// kernels then read zeta_{Nf/q}^{l c} from the fold/unfold table).  FP32
+// reads its large fold tables as two small ones (TwTab), which measured
+// faster than this m-entry table (2^22: 6 % slower with it); FP64 gains
+// 1-4 % with it.
+template <typename T>
+static const cx<T>* fourstep_table(int flag, int64_t Nf, int64_t q, int64_t ma, int64_t Cn, cudaError_t* e)
+{
+    if (sizeof(T) != 8 || !flag || q <= 0 || Nf % q != 0 || Nf / q != ma * Cn) return nullptr;
+    return twiddles_colmajor<T>(ma, Cn, e);
 }
 
 // cuTensorMapEncodeTiled from the driver (no link-time dependency on it);
@@ -578,6 +592,10 @@ cudaError_t launch_fold_fft_cols(const ColSide<T>* sides, int nside, int64_t B, 
     const V* twmal = twiddles_fft<T>(ma, true, &e);
     if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(ma);
+    bool same_q = true;
+    for (int i = 1; i < nside; ++i) same_q = same_q && sides[i].q == sides[0].q && sides[i].lam == 1;
+    const V* tpm = (same_q && sides[0].lam == 1) ? fourstep_table<T>(post, Nf, q0, ma, Cn, &e) : nullptr;
+    if (e != cudaSuccess) return e;
     const int C = col_tile<T>(Cn, ma, col_tile_target<T>(), Dg * sides[0].lam * nside * B);
     const int nct = (int)((Cn + C - 1) / C);
     const int thr = threads_for(ma * C);
@@ -601,21 +619,22 @@ cudaError_t launch_fold_fft_cols(const ColSide<T>* sides, int nside, int64_t B, 
         if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
         LaunchScope ls(K_FOLD_TMA, st, flops, bytes);
         kern<<<(unsigned)blocks, thr, smem, st>>>(k, maps, tma_rows, nside, B, Cn, (int)ma, Nf, cs, cc, (int)r0,
-                                                  (int)Dg, C, nct, post, twNf, twma, twmal, fp);
+                                                  (int)Dg, C, nct, post, twNf, tpm, twma, twmal, fp);
         return cudaGetLastError();
     }
     auto kern = k_fold_fft_cols<V>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     LaunchScope ls(K_FOLD_FFT_COLS, st, flops, bytes);
     kern<<<(unsigned)blocks, thr, smem, st>>>(k, nside, B, Cn, (int)ma, Nf, cs, cc, (int)r0, (int)Dg, C, nct, post,
-                                              twNf, twma, twmal, fp);
+                                              twNf, tpm, twma, twmal, fp);
     return cudaGetLastError();
 }
 
 template <class V>
 __global__ void __launch_bounds__(kMaxThreads, kColBlocks<V>)
 k_ifft_cols(V* y, int64_t B, int64_t Cn, int ma, int q, int64_t Nf, int Dg, int C, int nct, int pre,
-            const TwTab<V> twNf, const V* __restrict__ twma, const V* __restrict__ twmal, FftPlan fp)
+            const TwTab<V> twNf, const V* __restrict__ tpm, const V* __restrict__ twma, const V* __restrict__ twmal,
+            FftPlan fp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     int64_t blk = blockIdx.x;
@@ -623,8 +642,8 @@ k_ifft_cols(V* y, int64_t B, int64_t Cn, int ma, int q, int64_t Nf, int Dg, int 
     blk /= nct;
     const int rr = (int)(blk % Dg);
     const int64_t b = blk / Dg;
-    ifft_cols_body<V>(y + ((int64_t)rr * B + b) * ma * Cn, Cn, ma, q, Nf, (int64_t)ct * C, C, pre, twNf, twma, twmal,
-                      fp, reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
+    ifft_cols_body<V>(y + ((int64_t)rr * B + b) * ma * Cn, Cn, ma, q, Nf, (int64_t)ct * C, C, pre, twNf, tpm, twma,
+                      twmal, fp, reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
 }
 
 template <typename T>
@@ -641,6 +660,8 @@ cudaError_t launch_ifft_cols(cx<T>* y, int64_t B, int64_t Cn, int64_t ma, int64_
     const V* twmal = twiddles_fft<T>(ma, true, &e);
     if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(ma);
+    const V* tpm = fourstep_table<T>(pre, Nf, q, ma, Cn, &e);
+    if (e != cudaSuccess) return e;
     const int C = col_tile<T>(Cn, ma, col_tile_target<T>(), D * B);
     const int nct = (int)((Cn + C - 1) / C);
     const int thr = threads_for(ma * C);
@@ -651,7 +672,7 @@ cudaError_t launch_ifft_cols(cx<T>* y, int64_t B, int64_t Cn, int64_t ma, int64_
     LaunchScope ls(K_IFFT_COLS, st, (double)(D * B) * (double)Cn * fft_flops((double)ma),
                    2.0 * D * B * ma * Cn * sizeof(V));
     kern<<<(unsigned)blocks, thr, smem, st>>>(y, B, Cn, (int)ma, (int)q, Nf, (int)D, C, nct, pre, twNf,
-                                              twma, twmal, fp);
+                                              tpm, twma, twmal, fp);
     return cudaGetLastError();
 }
 
@@ -704,7 +725,7 @@ __global__ void __launch_bounds__(kMaxThreads, kColBlocks<V>)
 k_ifft_unfold_cols(const V* y, V* out, int64_t B, int64_t bstride, int64_t Cn, int ma, int p, int q, int64_t Nf,
                    int64_t cs, int64_t cc, int64_t lo, int64_t hi, int r0, int Dg, int first, int last,
                    typename real_of<V>::type scale, int C, int nct, int pre, const TwTab<V> twNf,
-                   const V* __restrict__ twma, const V* __restrict__ twmal, FftPlan fp)
+                   const V* __restrict__ tpm, const V* __restrict__ twma, const V* __restrict__ twmal, FftPlan fp)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     int64_t blk = blockIdx.x;
@@ -712,7 +733,7 @@ k_ifft_unfold_cols(const V* y, V* out, int64_t B, int64_t bstride, int64_t Cn, i
     const int64_t b = blk / nct;
     const int64_t per = (int64_t)ma * Cn;
     ifft_unfold_cols_body<V>(y + b * per, B * per, out + b * bstride, Cn, ma, p, q, Nf, cs, cc, lo, hi, r0, Dg,
-                             first, last, scale, (int64_t)ct * C, C, pre, twNf, twma, twmal, fp,
+                             first, last, scale, (int64_t)ct * C, C, pre, twNf, tpm, twma, twmal, fp,
                              reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
 }
 
@@ -743,6 +764,8 @@ cudaError_t launch_ifft_unfold(cx<T>* y, cx<T>* out, int64_t B, int64_t bstride,
     const V* twmal = twiddles_fft<T>(ma, true, &e);
     if (e != cudaSuccess) return e;
     const FftPlan fp = make_fft_plan(ma);
+    const V* tpm = fourstep_table<T>(pre, Nf, q, ma, Cn, &e);
+    if (e != cudaSuccess) return e;
     const int thr = threads_for(ma * C);
     const size_t smem = (size_t)(2 * smem_len<V>(ma * C)) * sizeof(V);
     auto kern = k_ifft_unfold_cols<V>;
@@ -752,8 +775,8 @@ cudaError_t launch_ifft_unfold(cx<T>* y, cx<T>* out, int64_t B, int64_t bstride,
                    (double)(Dg * B) * ((double)Cn * fft_flops((double)ma) + 8.0 * nout) + (last ? 2.0 * B * nout : 0.0),
                    ((double)(Dg * B * ma * Cn) + (first ? 1.0 : 2.0) * B * nout) * sizeof(V));
     kern<<<(unsigned)(B * nct), thr, smem, st>>>(y, out, B, bstride, Cn, (int)ma, (int)p, (int)q, Nf, cs, cc, lo, hi,
-                                                 (int)r0, (int)Dg, first, last, (T)scale, C, nct, pre, twNf, twma,
-                                                 twmal, fp);
+                                                 (int)r0, (int)Dg, first, last, (T)scale, C, nct, pre, twNf, tpm,
+                                                 twma, twmal, fp);
     return cudaGetLastError();
 }
 
@@ -1038,6 +1061,34 @@ cudaError_t launch_twiddle_strided(cx<T>* tw, int64_t count, int64_t N, int64_t 
     return cudaGetLastError();
 }
 
+// tw[c ma + l] = zeta_{ma Cn}^{l c}, l < ma, c < Cn: the four-step twiddles
+// of an ma x Cn split in the order a column tile reads them
+template <class V>
+__global__ void k_twiddle_colmajor(V* tw, int64_t ma, int64_t Cn)
+{
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n = ma * Cn;
+    if (idx >= n) return;
+    const int64_t c = idx / ma, l = idx - c * ma;
+    const int64_t k = (l * c) % n;
+    const int64_t kk = (2 * k > n) ? k - n : k;
+    double s, co;
+    sincospi(2.0 * (double)kk / (double)n, &s, &co);
+    using T = typename real_of<V>::type;
+    tw[idx] = mkc<V>((T)co, (T)s);
+}
+
+template <typename T>
+cudaError_t launch_twiddle_colmajor(cx<T>* tw, int64_t ma, int64_t Cn, cudaStream_t st)
+{
+    const int64_t n = ma * Cn;
+    if (n <= 0) return cudaSuccess;
+    const int thr = 256;
+    LaunchScope ls(K_TWIDDLE, st, 0.0, 16.0 * n);
+    k_twiddle_colmajor<cx<T>><<<(unsigned)((n + thr - 1) / thr), thr, 0, st>>>(tw, ma, Cn);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_twiddle_fft_into(cx<T>* tw, const FftPlan& fp, bool lf, cudaStream_t st)
 {
@@ -1101,6 +1152,7 @@ cudaError_t launch_unfold_tw(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstr
     template cudaError_t launch_twiddle_into<T>(cx<T>*, int64_t, cudaStream_t);                          \
     template cudaError_t launch_twiddle_fft_into<T>(cx<T>*, const FftPlan&, bool, cudaStream_t);          \
     template cudaError_t launch_twiddle_strided<T>(cx<T>*, int64_t, int64_t, int64_t, cudaStream_t);      \
+    template cudaError_t launch_twiddle_colmajor<T>(cx<T>*, int64_t, int64_t, cudaStream_t);              \
     template cudaError_t launch_residue_rows_tw<T>(const cx<T>*, const cx<T>*, cx<T>*, int64_t, int64_t, \
                                                    int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, \
                                                    const cx<T>*, const cx<T>*, const cx<T>*, cudaStream_t); \
