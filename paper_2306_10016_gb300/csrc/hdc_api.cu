@@ -37,13 +37,21 @@ template <typename T> cudaError_t launch_twiddle_colmajor(cx<T>* tw, int64_t ma,
 
 // ----------------------------------------------------------- FFT plans
 
-FftPlan make_fft_plan(int64_t n)
+FftPlan make_fft_plan(int64_t n, bool r16)
 {
     FftPlan fp;
     memset(&fp, 0, sizeof(fp));
     fp.n = (int)n;
     int64_t k = n;
     int ns = 0;
+    if (r16) {
+        // radix-16 stages only where they save a stage over radix 8 on the
+        // power-of-two part 2^e: ceil(e / 4) < ceil(e / 3)
+        int e = 0;
+        for (int64_t t = n; t % 2 == 0; t /= 2) ++e;
+        if ((e + 3) / 4 < (e + 2) / 3)
+            while (k % 16 == 0 && ns < HDC_MAX_STAGES) { fp.rad[ns++] = 16; k /= 16; }
+    }
     while (k % 8 == 0 && ns < HDC_MAX_STAGES) { fp.rad[ns++] = 8; k /= 8; }
     while (k % 4 == 0 && ns < HDC_MAX_STAGES) { fp.rad[ns++] = 4; k /= 4; }
     while (k % 2 == 0 && ns < HDC_MAX_STAGES) { fp.rad[ns++] = 2; k /= 2; }
@@ -101,17 +109,19 @@ template <typename T> static const cx<T>* twiddle_table(int64_t n, bool lf, cuda
 
 // Packed per-stage twiddle tables of the n-point transform (FftPlan), plain
 // or twiddle-merged form; cached like the full tables.
-template <typename T> const cx<T>* twiddles_fft(int64_t n, bool lf, cudaError_t* err)
+template <typename T> const cx<T>* twiddles_fft(int64_t n, bool lf, cudaError_t* err, bool r16ok)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) { *err = e; return nullptr; }
-    const int dt = (sizeof(T) == 8 ? 1 : 0) + (lf ? 2 : 0) + 4;
+    // two plans of one size differ at most in their radix-16 stages, which
+    // the key tells apart
+    const FftPlan fp = fft_plan<T>(n, r16ok);
+    const int dt = (sizeof(T) == 8 ? 1 : 0) + (lf ? 2 : 0) + 4 + (fp.nst > 0 && fp.rad[0] == 16 ? 8 : 0);
     std::lock_guard<std::mutex> lk(g_tw_mu);
     auto key = std::make_tuple(dev, n, dt);
     auto it = g_tw.find(key);
     if (it != g_tw.end()) return reinterpret_cast<const cx<T>*>(it->second);
-    const FftPlan fp = make_fft_plan(n);
     void* p = nullptr;
     e = cudaMalloc(&p, (size_t)fp.tlen * sizeof(cx<T>));
     if (e != cudaSuccess) { *err = e; return nullptr; }
@@ -127,8 +137,8 @@ template <typename T> const cx<T>* twiddles_fft(int64_t n, bool lf, cudaError_t*
     g_tw[key] = p;
     return reinterpret_cast<const cx<T>*>(p);
 }
-template const cx<double>* twiddles_fft<double>(int64_t, bool, cudaError_t*);
-template const cx<float>* twiddles_fft<float>(int64_t, bool, cudaError_t*);
+template const cx<double>* twiddles_fft<double>(int64_t, bool, cudaError_t*, bool);
+template const cx<float>* twiddles_fft<float>(int64_t, bool, cudaError_t*, bool);
 
 // An FP32 fold/unfold table of N entries is kept whole up to this size; a
 // larger one is two tables of about sqrt(N) entries (TwTab).

@@ -254,7 +254,7 @@ template <typename T> int build(hdc_batched* b)
         if (e != cudaSuccess) return HDC_ERR_CUDA;
         cv.twml = twiddles_fft<T>(m1 ? m2 : b->m[i], true, &e);
         if (e != cudaSuccess) return HDC_ERR_CUDA;
-        cv.fpm = make_fft_plan(m1 ? m2 : b->m[i]);
+        cv.fpm = fft_plan<T>(m1 ? m2 : b->m[i]);
         if (m1) {
             cv.twm1 = twiddles_fft<T>(m1, false, &e);
             if (e != cudaSuccess) return HDC_ERR_CUDA;
@@ -264,7 +264,7 @@ template <typename T> int build(hdc_batched* b)
                 cv.tpm = twiddles_colmajor<T>(m1, m2, &e);
                 if (e != cudaSuccess) return HDC_ERR_CUDA;
             }
-            cv.fpm1 = make_fft_plan(m1);
+            cv.fpm1 = fft_plan<T>(m1);
             cv.C = col_tile_b<T>(m2, m1);
             cv.nct = (int)((m2 + cv.C - 1) / cv.C);
         }

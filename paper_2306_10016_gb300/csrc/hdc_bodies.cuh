@@ -15,7 +15,7 @@ namespace hdc {
 // swizzled buffers of m (3 smem_len(m) elements).  g has L valid elements,
 // f has Lf <= L (zero beyond).  With p = q = 1 and Lf = L >= m the fold is a
 // plain copy of the rows.
-template <class V>
+template <class V, bool R16 = false>
 __device__ __forceinline__ void residue_row_body(const V* fr, const V* gr, V* hr, int64_t L, int64_t Lf, int m, int p,
                                                  int q, int r, const TwTab<V> twN, const V* __restrict__ twm,
                                                  const V* __restrict__ twml, const FftPlan& fp, V* smem, int tid,
@@ -58,11 +58,11 @@ __device__ __forceinline__ void residue_row_body(const V* fr, const V* gr, V* hr
         }
     }
     __syncthreads();
-    fft_smem<V, false, true>(sa, sc, fp, 1, 1, m, twm, twml, tid, nthr);
-    fft_smem<V, false, true>(sb, sc, fp, 1, 1, m, twm, twml, tid, nthr);
+    fft_smem<V, false, true, R16>(sa, sc, fp, 1, 1, m, twm, twml, tid, nthr);
+    fft_smem<V, false, true, R16>(sb, sc, fp, 1, 1, m, twm, twml, tid, nthr);
     for (int s = tid; s < m; s += nthr) sa[sidx<V, true>(s)] = cmul(sa[sidx<V, true>(s)], sb[sidx<V, true>(s)]);
     __syncthreads();
-    fft_smem<V, true, true>(sa, sc, fp, 1, 1, m, twm, twml, tid, nthr);
+    fft_smem<V, true, true, R16>(sa, sc, fp, 1, 1, m, twm, twml, tid, nthr);
     for (int s = tid; s < m; s += nthr) hr[s] = sa[sidx<V, true>(s)];
     __syncthreads();
 }
@@ -263,14 +263,14 @@ template <class V> constexpr int kColLoads = sizeof(V) == 8 ? 8 : 4;
 // over the tile's columns, then column c0 + cl (< Cn) of row l goes to
 // yb[l ystride + c], times zeta_{Nf/q}^{l c} if post: in FP64 from tpm[c ma + l]
 // when the caller has that column-major table (Nf/q = ma Cn), else from twNf.
-template <class V>
+template <class V, bool R16 = false>
 __device__ __forceinline__ void fft_cols_store_body(V* buf, V* tmp, V* yb, int64_t Cn, int ma, int q, int64_t c0,
                                                     int C, int post, int64_t ystride, const TwTab<V> twNf,
                                                     const V* __restrict__ tpm,
                                                     const V* __restrict__ twma, const V* __restrict__ twmal,
                                                     const FftPlan& fp, int tid, int nthr)
 {
-    if (ma > 1) fft_smem<V, false>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);
+    if (ma > 1) fft_smem<V, false, false, R16>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);
     for (int e = tid; e < ma * C; e += nthr) {
         const int l = e / C, cl = e - l * C;
         const int64_t c = c0 + cl;
@@ -286,7 +286,7 @@ __device__ __forceinline__ void fft_cols_store_body(V* buf, V* tmp, V* yb, int64
 // c0 .. c0+C-1 (< Cn) of one input x (view x[a][c], a = t ma + i, element
 // valid iff a Cn + c < Lvalid); residue r; result to yb[l ystride + c],
 // times zeta_{Nf/q}^{l c} if post.  smem: 2 smem_len(ma C).
-template <class V>
+template <class V, bool R16 = false>
 __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn, int ma, int p, int q, int64_t Nf,
                                                    int64_t cs, int64_t cc, int64_t Lvalid, int r, int64_t c0, int C,
                                                    int post, int64_t ystride, const TwTab<V> twNf,
@@ -362,13 +362,13 @@ __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn
         }
     }
     __syncthreads();
-    fft_cols_store_body<V>(buf, tmp, yb, Cn, ma, q, c0, C, post, ystride, twNf, tpm, twma, twmal, fp, tid, nthr);
+    fft_cols_store_body<V, R16>(buf, tmp, yb, Cn, ma, q, c0, C, post, ystride, twNf, tpm, twma, twmal, fp, tid, nthr);
 }
 
 // Inverse FFT of size ma along the strided axis of yb[l][c] (row length Cn)
 // for columns c0 .. c0+C-1, in place, after multiplying by
 // conj(zeta_{Nf/q}^{l c}) if pre.  smem: 2 smem_len(ma C).
-template <class V>
+template <class V, bool R16 = false>
 __device__ __forceinline__ void ifft_cols_body(V* yb, int64_t Cn, int ma, int q, int64_t Nf, int64_t c0, int C,
                                                int pre, const TwTab<V> twNf, const V* __restrict__ tpm,
                                                const V* __restrict__ twma,
@@ -401,7 +401,7 @@ __device__ __forceinline__ void ifft_cols_body(V* yb, int64_t Cn, int ma, int q,
         }
     }
     __syncthreads();
-    if (ma > 1) fft_smem<V, true>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);
+    if (ma > 1) fft_smem<V, true, false, R16>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);
     for (int e = tid; e < ma * C; e += nthr) {
         const int s = e / C, cl = e - s * C;
         const int64_t c = c0 + cl;
@@ -418,7 +418,7 @@ __device__ __forceinline__ void ifft_cols_body(V* yb, int64_t Cn, int ma, int q,
 // stored at ob[lin - lo]: these outputs belong to this tile alone.  The
 // first residue of the first pass writes instead of adding; the last of the
 // last pass scales.  smem: 2 smem_len(ma C).
-template <class V>
+template <class V, bool R16 = false>
 __device__ __forceinline__ void ifft_unfold_cols_body(const V* y, int64_t rstride, V* ob, int64_t Cn, int ma, int p,
                                                       int q, int64_t Nf, int64_t cs, int64_t cc, int64_t lo,
                                                       int64_t hi, int r0, int Dg, int first, int last,
@@ -457,7 +457,7 @@ __device__ __forceinline__ void ifft_unfold_cols_body(const V* y, int64_t rstrid
             }
         }
         __syncthreads();
-        if (ma > 1) fft_smem<V, true>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);
+        if (ma > 1) fft_smem<V, true, false, R16>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);
         const bool init = first && rr == 0, fin = last && rr == Dg - 1;
         for (int e = tid; e < n; e += nthr) {
             const int i = e / C, cl = e - i * C;

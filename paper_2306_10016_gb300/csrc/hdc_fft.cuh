@@ -133,6 +133,50 @@ template <class V, bool INV> struct Dft<V, 8, INV> {
     }
 };
 
+// 16 points as 4 x 4: with n = 4 n1 + n2 and k = k1 + 4 k2, 4-point DFTs over
+// n1 for each n2, the products by zeta_16^{n2 k1} (conjugated for the
+// inverse), then 4-point DFTs over n2 for each k1.  Used by the FP32
+// transforms, whose stages are bound by shared-memory passes rather than
+// arithmetic: 4096 points take three stages instead of four.
+template <class V, bool INV> struct Dft<V, 16, INV> {
+    static __device__ __forceinline__ V wmul(V a, typename real_of<V>::type c, typename real_of<V>::type s)
+    {
+        // a * (c + i s) forward, a * (c - i s) inverse
+        return INV ? mkc<V>(a.x * c + a.y * s, a.y * c - a.x * s) : mkc<V>(a.x * c - a.y * s, a.y * c + a.x * s);
+    }
+    static __device__ __forceinline__ void run(V* v)
+    {
+        using T = typename real_of<V>::type;
+        const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173; // zeta_16
+        const T h = (T)0.70710678118654752440;                                   // zeta_8
+        V a0[4] = { v[0], v[4], v[8], v[12] }, a1[4] = { v[1], v[5], v[9], v[13] };
+        V a2[4] = { v[2], v[6], v[10], v[14] }, a3[4] = { v[3], v[7], v[11], v[15] };
+        dft4<V, INV>(a0[0], a0[1], a0[2], a0[3]);
+        dft4<V, INV>(a1[0], a1[1], a1[2], a1[3]);
+        dft4<V, INV>(a2[0], a2[1], a2[2], a2[3]);
+        dft4<V, INV>(a3[0], a3[1], a3[2], a3[3]);
+        // zeta_16^{n2 k1}: n2 = 1: k1 = 1, 2, 3; n2 = 2: 2, 4, 6; n2 = 3: 3, 6, 9
+        a1[1] = wmul(a1[1], c1, s1);
+        a1[2] = wmul(a1[2], h, h);
+        a1[3] = wmul(a1[3], s1, c1);
+        a2[1] = wmul(a2[1], h, h);
+        a2[2] = rot90<V, INV>(a2[2]);
+        a2[3] = wmul(a2[3], -h, h);
+        a3[1] = wmul(a3[1], s1, c1);
+        a3[2] = wmul(a3[2], -h, h);
+        a3[3] = wmul(a3[3], -c1, -s1);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            V x0 = a0[k1], x1 = a1[k1], x2 = a2[k1], x3 = a3[k1];
+            dft4<V, INV>(x0, x1, x2, x3);
+            v[k1] = x0;
+            v[k1 + 4] = x1;
+            v[k1 + 8] = x2;
+            v[k1 + 12] = x3;
+        }
+    }
+};
+
 // Odd radix R = 2H+1: X_k = x0 + sum_j cos(2 pi jk/R)(x_j + x_{R-j})
 //                            +- i sum_j sin(2 pi jk/R)(x_j - x_{R-j}),
 // X_{R-k} the same with the sine part negated.
@@ -411,6 +455,26 @@ __device__ __forceinline__ void fft_stage(const V* src, V* dst, int n, int ncol,
         if (kLF && Ns > 1) {
             // every butterfly of the stage carries its twiddles (W = 1 when jm = 0)
             DftLF<V, kLF ? R : 2, INV>::run(v, twl, jm, Ns * R);
+        } else if constexpr (R == 16) {
+            if (jm != 0) {
+                // four table entries w^1, w^2, w^4, w^8 (w = zeta_{Ns R}^jm)
+                // and the other powers as their products: at most four
+                // correctly rounded factors per twiddle, a quarter of the
+                // table loads of one entry per input
+                const V w1 = ldg_c(tw + jm), w2 = ldg_c(tw + 2 * jm);
+                const V w4 = ldg_c(tw + 4 * jm), w8 = ldg_c(tw + 8 * jm);
+                const V w3 = cmul(w1, w2), w5 = cmul(w1, w4), w6 = cmul(w2, w4), w7 = cmul(w3, w4);
+                const V wp[8] = { czero<V>(), w1, w2, w3, w4, w5, w6, w7 };
+#pragma unroll
+                for (int r = 1; r < 8; ++r) v[r] = INV ? cmulc(v[r], wp[r]) : cmul(v[r], wp[r]);
+                v[8] = INV ? cmulc(v[8], w8) : cmul(v[8], w8);
+#pragma unroll
+                for (int r = 9; r < 16; ++r) {
+                    const V w = cmul(wp[r - 8], w8);
+                    v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+                }
+            }
+            Dft<V, R, INV>::run(v);
         } else {
             if (jm != 0) {
 #pragma unroll
@@ -433,7 +497,7 @@ __device__ __forceinline__ void fft_stage(const V* src, V* dst, int n, int ncol,
 // twiddle tables of fp (plain / twiddle-merged form, see FftPlan).  The
 // caller must have synchronised after filling buf; on return the result is
 // in buf and the block is synchronised.
-template <class V, bool INV, bool SWZ = false>
+template <class V, bool INV, bool SWZ = false, bool R16 = false>
 __device__ __forceinline__ void fft_smem(V* buf, V* tmp, const FftPlan& fp, int ncol, int ld, int cs,
                                          const V* __restrict__ tw, const V* __restrict__ twl, int tid, int nthr)
 {
@@ -446,6 +510,9 @@ __device__ __forceinline__ void fft_smem(V* buf, V* tmp, const FftPlan& fp, int 
         const V* ts = tw + fp.toff[s];
         const V* tl = twl + fp.toff[s];
         switch (R) {
+        case 16:  // FP32 plans only; compiled into the kernels that take them
+            if constexpr (R16 && sizeof(V) == 8) fft_stage<V, 16, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr);
+            break;
         case 8: fft_stage<V, 8, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
         case 4: fft_stage<V, 4, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
         case 2: fft_stage<V, 2, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;

@@ -39,7 +39,26 @@ template <typename T> constexpr int64_t col_tile_target()
 }
 template <typename T> constexpr int64_t max_col_fft() { return kColMaxBytes / (2 * (int64_t)sizeof(cx<T>)); }
 
-FftPlan make_fft_plan(int64_t n);
+// Stages of an n-point transform: radix 8 first (16 first when r16), then 4,
+// 2, 7, 5, 3, with the offsets of their twiddle sub-tables.
+FftPlan make_fft_plan(int64_t n, bool r16 = false);
+// The plan the kernels use for element type T.  FP32 transforms whose
+// kernel is built with radix-16 stages (r16ok) take them where they save a
+// stage: FP32 stages are bound by shared-memory passes, which radix 16 makes
+// fewer.  FP64 transforms are bound by FP64 arithmetic, which the
+// twiddle-merged radix-2/4/8 butterflies keep lowest, and never take them.
+template <typename T> inline FftPlan fft_plan(int64_t n, bool r16ok = false)
+{
+    return make_fft_plan(n, sizeof(T) == 4 && r16ok);
+}
+// A row transform runs n / 8 threads (at most kMaxThreads): below 16
+// kMaxThreads points a radix-16 stage would leave some of them idle, so rows
+// take radix 16 from there on.  Column tiles hold a butterfly per column and
+// take it at any size.
+inline bool rows_r16(int64_t n) { return n >= 16 * (int64_t)kMaxThreads; }
+// kernels with radix-16 stages exist for FP32 only
+template <class V> constexpr bool kHas16 = sizeof(V) == 8;
+template <class V> inline bool takes_r16(const FftPlan& fp) { return kHas16<V> && fp.nst > 0 && fp.rad[0] == 16; }
 
 // ------------------------------------------------------ launch statistics
 // Every launcher counts its launches and the model flops / algorithmic
@@ -67,7 +86,8 @@ template <typename T> const cx<T>* twiddles(int64_t n, cudaError_t* err);
 // The packed per-stage tables of the n-point transform's plan (FftPlan::toff),
 // plain (lf = false) or in the scale-tangent form of the twiddle-merged
 // butterflies (lf = true, see lf_bfly): what fft_smem reads.
-template <typename T> const cx<T>* twiddles_fft(int64_t n, bool lf, cudaError_t* err);
+// packed per-stage tables of fft_plan<T>(n, r16ok), plain or twiddle-merged
+template <typename T> const cx<T>* twiddles_fft(int64_t n, bool lf, cudaError_t* err, bool r16ok = false);
 // zeta_N^k for the folds and unfolds: one table, or two for a large N (TwTab).
 template <typename T> TwTab<cx<T>> tw_table(int64_t N, cudaError_t* err);
 // zeta_{ma Cn}^{l c} at c ma + l (l < ma, c < Cn): the four-step twiddles of an

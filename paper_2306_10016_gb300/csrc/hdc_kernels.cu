@@ -147,7 +147,7 @@ static cudaError_t allow_smem(K kernel, size_t bytes)
 
 // ------------------------------------------------------- residue rows
 
-template <class V>
+template <class V, bool R16>
 __global__ void __launch_bounds__(kMaxThreads, 2)
 k_residue_rows(const V* f, const V* g, V* h, int64_t B, int64_t ld_f, int64_t ld_g, int64_t Lf, int64_t L, int m,
                int p, int q, int r0, int Dg, const TwTab<V> twN, const V* __restrict__ twm,
@@ -156,7 +156,7 @@ k_residue_rows(const V* f, const V* g, V* h, int64_t B, int64_t ld_f, int64_t ld
     extern __shared__ __align__(16) unsigned char smraw[];
     const int64_t b = blockIdx.x % B;
     const int rr = (int)(blockIdx.x / B);
-    residue_row_body<V>(f + b * ld_f, g + b * ld_g, h + ((int64_t)rr * B + b) * m, L, Lf, m, p, q, r0 + rr, twN,
+    residue_row_body<V, R16>(f + b * ld_f, g + b * ld_g, h + ((int64_t)rr * B + b) * m, L, Lf, m, p, q, r0 + rr, twN,
                         twm, twml, fp, reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
 }
 
@@ -171,14 +171,14 @@ cudaError_t launch_residue_rows(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_
     cudaError_t e = cudaSuccess;
     const TwTab<V> twN = tw_table<T>(q * m, &e);
     if (e != cudaSuccess) return e;
-    const V* twm = twiddles_fft<T>(m, false, &e);
+    const V* twm = twiddles_fft<T>(m, false, &e, rows_r16(m));
     if (e != cudaSuccess) return e;
-    const V* twml = twiddles_fft<T>(m, true, &e);
+    const V* twml = twiddles_fft<T>(m, true, &e, rows_r16(m));
     if (e != cudaSuccess) return e;
-    const FftPlan fp = make_fft_plan(m);
+    const FftPlan fp = fft_plan<T>(m, rows_r16(m));
     const int thr = threads_for(m);
     const size_t smem = (size_t)(3 * smem_len<V>(m)) * sizeof(V);
-    auto kern = k_residue_rows<V>;
+    auto kern = takes_r16<V>(fp) ? k_residue_rows<V, kHas16<V>> : k_residue_rows<V, false>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     const int64_t blocks = B * Dg;
     // model: 3 FFTs + product per residue, and the fold of f and g (8 flops
@@ -229,7 +229,7 @@ cudaError_t launch_residue_rows_lam(const cx<T>* f, const cx<T>* g, cx<T>* h, in
     if (e != cudaSuccess) return e;
     const V* twgl = twiddles_fft<T>(mg, true, &e);
     if (e != cudaSuccess) return e;
-    const FftPlan fpf = make_fft_plan(mf), fpg = make_fft_plan(mg);
+    const FftPlan fpf = fft_plan<T>(mf), fpg = fft_plan<T>(mg);
     const int thr = threads_for(mg);
     const size_t smem = (size_t)(3 * smem_len<V>(mg)) * sizeof(V);
     auto kern = k_residue_rows_lam<V>;
@@ -277,7 +277,7 @@ cudaError_t launch_residue_rows_multi(const cx<T>* const* xs, int nin, int op, c
     if (e != cudaSuccess) return e;
     const V* twml = twiddles_fft<T>(m, true, &e);
     if (e != cudaSuccess) return e;
-    const FftPlan fp = make_fft_plan(m);
+    const FftPlan fp = fft_plan<T>(m);
     const int thr = threads_for(m);
     const size_t smem = (size_t)(3 * smem_len<V>(m)) * sizeof(V);
     auto kern = k_residue_rows_multi<V>;
@@ -421,7 +421,7 @@ __device__ __forceinline__ FoldBlock<V> fold_block(const ColSidesK<V>& sides, in
     return fb;
 }
 
-template <class V>
+template <class V, bool R16>
 __global__ void __launch_bounds__(kMaxThreads, kColBlocks<V>)
 k_fold_fft_cols(ColSidesK<V> sides, int nside, int64_t B, int64_t Cn, int ma, int64_t Nf, int64_t cs, int64_t cc,
                 int r0, int Dg, int C, int nct, int post, const TwTab<V> twNf, const V* __restrict__ tpm,
@@ -432,7 +432,7 @@ k_fold_fft_cols(ColSidesK<V> sides, int nside, int64_t B, int64_t Cn, int ma, in
     // (the whole block leaves before any barrier)
     if (fb.skip) return;
     const ColSideK<V>& sd = sides.s[fb.which];
-    fold_fft_cols_body<V>(fb.x, fb.yb, Cn, ma, sd.p, sd.q, Nf, cs, cc, sd.Lvalid, fb.r, fb.c0, C, post,
+    fold_fft_cols_body<V, R16>(fb.x, fb.yb, Cn, ma, sd.p, sd.q, Nf, cs, cc, sd.Lvalid, fb.r, fb.c0, C, post,
                           (int64_t)sd.lam * Cn, twNf, tpm, twma, twmal, fp, reinterpret_cast<V*>(smraw), threadIdx.x,
                           blockDim.x);
 }
@@ -440,7 +440,7 @@ k_fold_fft_cols(ColSidesK<V> sides, int nside, int64_t B, int64_t Cn, int ma, in
 // The same pass with the tile's fold blocks staged by TMA box copies of
 // tma_rows rows (the host has checked every copy rule; a block whose shared
 // memory is not 128-byte aligned uses the plain loads).
-template <class V>
+template <class V, bool R16>
 __global__ void __launch_bounds__(kMaxThreads, kColBlocks<V>)
 k_fold_fft_cols_tma(ColSidesK<V> sides, const __grid_constant__ ColMapsK maps, int tma_rows, int nside, int64_t B,
                     int64_t Cn, int ma, int64_t Nf, int64_t cs, int64_t cc, int r0, int Dg, int C, int nct, int post,
@@ -455,7 +455,7 @@ k_fold_fft_cols_tma(ColSidesK<V> sides, const __grid_constant__ ColMapsK maps, i
     V* buf = reinterpret_cast<V*>(smraw);
     const int tid = threadIdx.x, nthr = blockDim.x;
     if ((smem_u32(buf) & 127) != 0) {
-        fold_fft_cols_body<V>(fb.x, fb.yb, Cn, ma, sd.p, sd.q, Nf, cs, cc, sd.Lvalid, fb.r, fb.c0, C, post,
+        fold_fft_cols_body<V, R16>(fb.x, fb.yb, Cn, ma, sd.p, sd.q, Nf, cs, cc, sd.Lvalid, fb.r, fb.c0, C, post,
                               (int64_t)sd.lam * Cn, twNf, tpm, twma, twmal, fp, buf, tid, nthr);
         return;
     }
@@ -490,7 +490,7 @@ k_fold_fft_cols_tma(ColSidesK<V> sides, const __grid_constant__ ColMapsK maps, i
     fold_staged_tile<V>(buf, stride, fb.x, Cn, ma, sd.p, sd.q, Nf, cs, cc, sd.Lvalid, fb.r, fb.c0, C, twNf, tid,
                         nthr);
     __syncthreads();
-    fft_cols_store_body<V>(buf, buf + stride, fb.yb, Cn, ma, sd.q, fb.c0, C, post, (int64_t)sd.lam * Cn, twNf, tpm,
+    fft_cols_store_body<V, R16>(buf, buf + stride, fb.yb, Cn, ma, sd.q, fb.c0, C, post, (int64_t)sd.lam * Cn, twNf, tpm,
                            twma, twmal, fp, tid, nthr);
 }
 
@@ -587,11 +587,11 @@ cudaError_t launch_fold_fft_cols(const ColSide<T>* sides, int nside, int64_t B, 
     cudaError_t e = cudaSuccess;
     const TwTab<V> twNf = tw_table<T>(Nf, &e);
     if (e != cudaSuccess) return e;
-    const V* twma = twiddles_fft<T>(ma, false, &e);
+    const V* twma = twiddles_fft<T>(ma, false, &e, true);
     if (e != cudaSuccess) return e;
-    const V* twmal = twiddles_fft<T>(ma, true, &e);
+    const V* twmal = twiddles_fft<T>(ma, true, &e, true);
     if (e != cudaSuccess) return e;
-    const FftPlan fp = make_fft_plan(ma);
+    const FftPlan fp = fft_plan<T>(ma, true);
     bool same_q = true;
     for (int i = 1; i < nside; ++i) same_q = same_q && sides[i].q == sides[0].q && sides[i].lam == 1;
     const V* tpm = (same_q && sides[0].lam == 1) ? fourstep_table<T>(post, Nf, q0, ma, Cn, &e) : nullptr;
@@ -615,14 +615,14 @@ cudaError_t launch_fold_fft_cols(const ColSide<T>* sides, int nside, int64_t B, 
     memset(&maps, 0, sizeof maps);
     const int tma_rows = g_fold_tma ? make_fold_maps<V>(&maps, k, nside, B, Cn, ma, C) : 0;
     if (tma_rows > 0) {
-        auto kern = k_fold_fft_cols_tma<V>;
+        auto kern = takes_r16<V>(fp) ? k_fold_fft_cols_tma<V, kHas16<V>> : k_fold_fft_cols_tma<V, false>;
         if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
         LaunchScope ls(K_FOLD_TMA, st, flops, bytes);
         kern<<<(unsigned)blocks, thr, smem, st>>>(k, maps, tma_rows, nside, B, Cn, (int)ma, Nf, cs, cc, (int)r0,
                                                   (int)Dg, C, nct, post, twNf, tpm, twma, twmal, fp);
         return cudaGetLastError();
     }
-    auto kern = k_fold_fft_cols<V>;
+    auto kern = takes_r16<V>(fp) ? k_fold_fft_cols<V, kHas16<V>> : k_fold_fft_cols<V, false>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     LaunchScope ls(K_FOLD_FFT_COLS, st, flops, bytes);
     kern<<<(unsigned)blocks, thr, smem, st>>>(k, nside, B, Cn, (int)ma, Nf, cs, cc, (int)r0, (int)Dg, C, nct, post,
@@ -630,7 +630,7 @@ cudaError_t launch_fold_fft_cols(const ColSide<T>* sides, int nside, int64_t B, 
     return cudaGetLastError();
 }
 
-template <class V>
+template <class V, bool R16>
 __global__ void __launch_bounds__(kMaxThreads, kColBlocks<V>)
 k_ifft_cols(V* y, int64_t B, int64_t Cn, int ma, int q, int64_t Nf, int Dg, int C, int nct, int pre,
             const TwTab<V> twNf, const V* __restrict__ tpm, const V* __restrict__ twma, const V* __restrict__ twmal,
@@ -642,7 +642,7 @@ k_ifft_cols(V* y, int64_t B, int64_t Cn, int ma, int q, int64_t Nf, int Dg, int 
     blk /= nct;
     const int rr = (int)(blk % Dg);
     const int64_t b = blk / Dg;
-    ifft_cols_body<V>(y + ((int64_t)rr * B + b) * ma * Cn, Cn, ma, q, Nf, (int64_t)ct * C, C, pre, twNf, tpm, twma,
+    ifft_cols_body<V, R16>(y + ((int64_t)rr * B + b) * ma * Cn, Cn, ma, q, Nf, (int64_t)ct * C, C, pre, twNf, tpm, twma,
                       twmal, fp, reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
 }
 
@@ -655,18 +655,18 @@ cudaError_t launch_ifft_cols(cx<T>* y, int64_t B, int64_t Cn, int64_t ma, int64_
     cudaError_t e = cudaSuccess;
     const TwTab<V> twNf = tw_table<T>(Nf, &e);
     if (e != cudaSuccess) return e;
-    const V* twma = twiddles_fft<T>(ma, false, &e);
+    const V* twma = twiddles_fft<T>(ma, false, &e, true);
     if (e != cudaSuccess) return e;
-    const V* twmal = twiddles_fft<T>(ma, true, &e);
+    const V* twmal = twiddles_fft<T>(ma, true, &e, true);
     if (e != cudaSuccess) return e;
-    const FftPlan fp = make_fft_plan(ma);
+    const FftPlan fp = fft_plan<T>(ma, true);
     const V* tpm = fourstep_table<T>(pre, Nf, q, ma, Cn, &e);
     if (e != cudaSuccess) return e;
     const int C = col_tile<T>(Cn, ma, col_tile_target<T>(), D * B);
     const int nct = (int)((Cn + C - 1) / C);
     const int thr = threads_for(ma * C);
     const size_t smem = (size_t)(2 * smem_len<V>(ma * C)) * sizeof(V);
-    auto kern = k_ifft_cols<V>;
+    auto kern = takes_r16<V>(fp) ? k_ifft_cols<V, kHas16<V>> : k_ifft_cols<V, false>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     const int64_t blocks = (int64_t)nct * D * B;
     LaunchScope ls(K_IFFT_COLS, st, (double)(D * B) * (double)Cn * fft_flops((double)ma),
@@ -720,7 +720,7 @@ cudaError_t launch_unfold(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstride
 
 // ------------------------------------------ inverse + unfold, fused
 
-template <class V>
+template <class V, bool R16>
 __global__ void __launch_bounds__(kMaxThreads, kColBlocks<V>)
 k_ifft_unfold_cols(const V* y, V* out, int64_t B, int64_t bstride, int64_t Cn, int ma, int p, int q, int64_t Nf,
                    int64_t cs, int64_t cc, int64_t lo, int64_t hi, int r0, int Dg, int first, int last,
@@ -732,7 +732,7 @@ k_ifft_unfold_cols(const V* y, V* out, int64_t B, int64_t bstride, int64_t Cn, i
     const int ct = (int)(blk % nct);
     const int64_t b = blk / nct;
     const int64_t per = (int64_t)ma * Cn;
-    ifft_unfold_cols_body<V>(y + b * per, B * per, out + b * bstride, Cn, ma, p, q, Nf, cs, cc, lo, hi, r0, Dg,
+    ifft_unfold_cols_body<V, R16>(y + b * per, B * per, out + b * bstride, Cn, ma, p, q, Nf, cs, cc, lo, hi, r0, Dg,
                              first, last, scale, (int64_t)ct * C, C, pre, twNf, tpm, twma, twmal, fp,
                              reinterpret_cast<V*>(smraw), threadIdx.x, blockDim.x);
 }
@@ -759,16 +759,16 @@ cudaError_t launch_ifft_unfold(cx<T>* y, cx<T>* out, int64_t B, int64_t bstride,
     cudaError_t e = cudaSuccess;
     const TwTab<V> twNf = tw_table<T>(Nf, &e);
     if (e != cudaSuccess) return e;
-    const V* twma = twiddles_fft<T>(ma, false, &e);
+    const V* twma = twiddles_fft<T>(ma, false, &e, true);
     if (e != cudaSuccess) return e;
-    const V* twmal = twiddles_fft<T>(ma, true, &e);
+    const V* twmal = twiddles_fft<T>(ma, true, &e, true);
     if (e != cudaSuccess) return e;
-    const FftPlan fp = make_fft_plan(ma);
+    const FftPlan fp = fft_plan<T>(ma, true);
     const V* tpm = fourstep_table<T>(pre, Nf, q, ma, Cn, &e);
     if (e != cudaSuccess) return e;
     const int thr = threads_for(ma * C);
     const size_t smem = (size_t)(2 * smem_len<V>(ma * C)) * sizeof(V);
-    auto kern = k_ifft_unfold_cols<V>;
+    auto kern = takes_r16<V>(fp) ? k_ifft_unfold_cols<V, kHas16<V>> : k_ifft_unfold_cols<V, false>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     const double nout = (double)(hi - lo);
     LaunchScope ls(K_IFFT_UNFOLD, st,
@@ -822,7 +822,7 @@ cudaError_t launch_residue_rows_real(const cx<T>* z, cx<T>* h, int64_t B, int64_
     if (e != cudaSuccess) return e;
     const V* twml = twiddles_fft<T>(m, true, &e);
     if (e != cudaSuccess) return e;
-    const FftPlan fp = make_fft_plan(m);
+    const FftPlan fp = fft_plan<T>(m);
     const int thr = threads_for(m);
     const size_t smem = (size_t)(3 * smem_len<V>(m)) * sizeof(V);
     auto kern = k_residue_rows_real<V>;
@@ -871,7 +871,7 @@ cudaError_t launch_rows_real_pair(const cx<T>* ya, const cx<T>* yb, cx<T>* yh, i
     if (e != cudaSuccess) return e;
     const V* twml = twiddles_fft<T>(m2, true, &e);
     if (e != cudaSuccess) return e;
-    const FftPlan fp = make_fft_plan(m2);
+    const FftPlan fp = fft_plan<T>(m2);
     const int thr = threads_for(m2);
     const size_t smem = (size_t)(3 * smem_len<V>(m2)) * sizeof(V);
     auto kern = k_rows_real_pair<V>;
@@ -1113,10 +1113,10 @@ cudaError_t launch_residue_rows_tw(const cx<T>* f, const cx<T>* g, cx<T>* h, int
     const int64_t Dg = (D < q - r0) ? D : (q - r0);
     if (B <= 0 || Dg <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-    const FftPlan fp = make_fft_plan(m);
+    const FftPlan fp = fft_plan<T>(m, rows_r16(m));
     const int thr = threads_for(m);
     const size_t smem = (size_t)(3 * smem_len<V>(m)) * sizeof(V);
-    auto kern = k_residue_rows<V>;
+    auto kern = takes_r16<V>(fp) ? k_residue_rows<V, kHas16<V>> : k_residue_rows<V, false>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     const int64_t blocks = B * Dg;
     const double Lrow = (double)((L < p * m) ? L : p * m);

@@ -61,7 +61,7 @@ int run(const void* f, const void* g, void* h, int64_t L, int64_t m, int64_t p, 
     if (m > max_row_fft<T>()) return HDC_ERR_UNSUPPORTED_SIZE;
     const int64_t N = q * m;
     const size_t b_twN = align256((size_t)N * sizeof(V));
-    const FftPlan fpm = make_fft_plan(m);
+    const FftPlan fpm = fft_plan<T>(m, rows_r16(m));
     const size_t b_twm = align256((size_t)fpm.tlen * sizeof(V));
     const size_t b_ws = align256((size_t)(D * batch * m) * sizeof(V));
     if (b_twN + 2 * b_twm + b_ws > kScratchBytes) return HDC_ERR_UNSUPPORTED_SIZE;
