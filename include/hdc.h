@@ -148,6 +148,28 @@ int64_t hdc_max_fft_size(int dtype);
 int64_t hdc_max_padded_size(int dtype);
 int64_t hdc_max_outer_fft_size(int dtype);
 
+/* Kinds of shared-memory transform, for hdc_fft_stages. */
+enum hdc_fft_kind {
+    HDC_FFT_ROWS = 0,   /* residue rows: 1-D rows, the split's rows, the last axis */
+    HDC_FFT_COLS = 1,   /* column tiles: the split's columns, the outer axes       */
+    HDC_FFT_OTHER = 2   /* rows of the real-input, unequal-length and multi-
+                           convolution kernels; rows and columns of the batched
+                           kernel                                                 */
+};
+
+/* The stages of the n-point FFT (Section 2.2's radix-2 split generalised to
+ * mixed radix, Stockham order) that a kernel of the given kind runs:
+ * writes the radices, first stage first, to radices[0..cap) and returns
+ * their number (0 for n = 1); their product is n.  Radix 8 first, then 4,
+ * 2, 7, 5, 3; complex<float> transforms of kind HDC_FFT_COLS, and of kind
+ * HDC_FFT_ROWS from 4096 points on, start with radix-16 stages where those
+ * save a stage on the power-of-two part 2^e of n (ceil(e/4) < ceil(e/3)).
+ * Host only, no GPU needed.  Errors: HDC_ERR_PARAM (radices NULL, cap < 0,
+ * cap below the stage count, kind unknown), HDC_ERR_UNSUPPORTED_SIZE (n < 1,
+ * n not 7-smooth, n above the kind's tile: 2048 / 4096 points for rows,
+ * hdc_max_outer_fft_size for columns), HDC_ERR_DTYPE. */
+int hdc_fft_stages(int64_t n, int dtype, int kind, int* radices, int cap);
+
 /* Bytes of device workspace an N-D call needs (dims in 1..3; arrays of
  * length dims; p/q/D entries may be 0 = derive).  Writes *bytes. */
 int hdc_workspace_size(int dims, const int64_t* L, const int64_t* M,

@@ -79,6 +79,7 @@ _SIGS = [
     ("hdc_max_fft_size", _i64, [C.c_int]),
     ("hdc_max_padded_size", _i64, [C.c_int]),
     ("hdc_max_outer_fft_size", _i64, [C.c_int]),
+    ("hdc_fft_stages", C.c_int, [_i64, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int]),
     ("hdc_workspace_size", C.c_int, [C.c_int, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, C.c_int, _i64,
                                      C.c_int, C.POINTER(_sz)]),
     ("hdc_conv1d", C.c_int, [_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _i64, C.c_int, C.c_int, _i64,
@@ -300,6 +301,19 @@ def max_fft_size(dtype=HDC_C128) -> int:
 
 def max_padded_size(dtype=HDC_C128) -> int:
     return int(lib().hdc_max_padded_size(dtype))
+
+
+FFT_ROWS, FFT_COLS, FFT_OTHER = 0, 1, 2
+
+
+def fft_stages(n: int, dtype=HDC_C128, kind=FFT_ROWS) -> list:
+    """hdc_fft_stages: the radices, first stage first, of the n-point
+    transform a kernel of the given kind runs (host only)."""
+    buf = (C.c_int * 32)()
+    rc = lib().hdc_fft_stages(n, dtype, kind, buf, 32)
+    if rc < 0:
+        _check(rc, "hdc_fft_stages")
+    return list(buf[:rc])
 
 
 def _per_axis(v, dims, name):

@@ -869,6 +869,25 @@ HDC_EXPORT int64_t hdc_max_outer_fft_size(int dtype)
 }
 HDC_EXPORT int64_t hdc_max_padded_size(int dtype) { return max_padded(dtype); }
 
+template <typename T> static int fft_stages(int64_t n, int kind, int* radices, int cap)
+{
+    const int64_t lim = kind == HDC_FFT_COLS ? max_col_fft<T>() : max_row_fft<T>();
+    if (n > lim) return HDC_ERR_UNSUPPORTED_SIZE;
+    const bool r16ok = kind == HDC_FFT_COLS || (kind == HDC_FFT_ROWS && rows_r16(n));
+    const FftPlan fp = fft_plan<T>(n, r16ok);
+    if (fp.nst > cap) return HDC_ERR_PARAM;
+    for (int s = 0; s < fp.nst; ++s) radices[s] = fp.rad[s];
+    return fp.nst;
+}
+
+HDC_EXPORT int hdc_fft_stages(int64_t n, int dtype, int kind, int* radices, int cap)
+{
+    if (!radices || cap < 0 || kind < HDC_FFT_ROWS || kind > HDC_FFT_OTHER) return HDC_ERR_PARAM;
+    if (dtype != HDC_C128 && dtype != HDC_C64) return HDC_ERR_DTYPE;
+    if (n < 1 || !hdc_is_good_size(n)) return HDC_ERR_UNSUPPORTED_SIZE;
+    return dtype == HDC_C128 ? fft_stages<double>(n, kind, radices, cap) : fft_stages<float>(n, kind, radices, cap);
+}
+
 HDC_EXPORT int hdc_workspace_size(int dims, const int64_t* L, const int64_t* M, const int64_t* m,
                                   const int64_t* p, const int64_t* q, const int64_t* D, int dtype,
                                   int64_t batch, int inplace, size_t* bytes)
