@@ -13,10 +13,12 @@
 //   twiddle zeta_{Ns R}^{r (j mod Ns)}        (Ns = product of earlier radices)
 //   outputs (j div Ns) Ns R + (j mod Ns) + r Ns
 // after which the data of the next stage is in order, so no bit reversal is
-// ever needed.  Twiddles come from a table tw[k] = zeta_n^k, k < n, made in
-// FP64 from exact integer angles; radix-2, 4 and 8 stages after the first
-// merge them into their butterflies from a second table twl of the same
-// values in scale-tangent form (see lf_bfly).
+// ever needed.  Twiddles come from per-stage tables of zeta_{Ns R}^e (see
+// FftPlan) made in FP64 from exact integer angles; radix-2, 4 and 8 stages
+// after the first merge them into their butterflies from a second set of
+// the same values in scale-tangent form (see lf_bfly).  FP32 plans may start
+// with radix-16 stages (Dft<V, 16>), whose twiddles are products of four
+// table entries.
 #pragma once
 
 #include <cuda_runtime.h>
