@@ -498,7 +498,8 @@ __device__ __forceinline__ void fft_stage(const V* src, V* dst, int n, int ncol,
 // addressing) as the other half of the ping-pong.  tw / twl: the packed
 // twiddle tables of fp (plain / twiddle-merged form, see FftPlan).  The
 // caller must have synchronised after filling buf; on return the result is
-// in buf and the block is synchronised.
+// in buf and the block is synchronised.  R16: the kernel is built with the
+// radix-16 stage (FP32 only); a plan that has one must be run with R16.
 template <class V, bool INV, bool SWZ = false, bool R16 = false>
 __device__ __forceinline__ void fft_smem(V* buf, V* tmp, const FftPlan& fp, int ncol, int ld, int cs,
                                          const V* __restrict__ tw, const V* __restrict__ twl, int tid, int nthr)

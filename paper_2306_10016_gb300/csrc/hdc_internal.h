@@ -85,8 +85,8 @@ double fft_flops(double n);
 template <typename T> const cx<T>* twiddles(int64_t n, cudaError_t* err);
 // The packed per-stage tables of the n-point transform's plan (FftPlan::toff),
 // plain (lf = false) or in the scale-tangent form of the twiddle-merged
-// butterflies (lf = true, see lf_bfly): what fft_smem reads.
-// packed per-stage tables of fft_plan<T>(n, r16ok), plain or twiddle-merged
+// butterflies (lf = true, see lf_bfly): what fft_smem reads; of the plan
+// fft_plan<T>(n, r16ok).
 template <typename T> const cx<T>* twiddles_fft(int64_t n, bool lf, cudaError_t* err, bool r16ok = false);
 // zeta_N^k for the folds and unfolds: one table, or two for a large N (TwTab).
 template <typename T> TwTab<cx<T>> tw_table(int64_t N, cudaError_t* err);
