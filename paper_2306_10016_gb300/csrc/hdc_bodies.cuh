@@ -58,12 +58,14 @@ __device__ __forceinline__ void residue_row_body(const V* fr, const V* gr, V* hr
         }
     }
     __syncthreads();
-    fft_smem<V, false, true, R16>(sa, sc, fp, 1, 1, m, twm, twml, tid, nthr);
-    fft_smem<V, false, true, R16>(sb, sc, fp, 1, 1, m, twm, twml, tid, nthr);
-    for (int s = tid; s < m; s += nthr) sa[sidx<V, true>(s)] = cmul(sa[sidx<V, true>(s)], sb[sidx<V, true>(s)]);
+    // each transform leaves its result where its last stage wrote it; the
+    // next one takes a buffer that is free at that point as its scratch
+    V* F = fft_smem_any<V, false, true, R16>(sa, sc, fp, 1, 1, m, twm, twml, tid, nthr);
+    V* G = fft_smem_any<V, false, true, R16>(sb, F == sa ? sc : sa, fp, 1, 1, m, twm, twml, tid, nthr);
+    for (int s = tid; s < m; s += nthr) F[sidx<V, true>(s)] = cmul(F[sidx<V, true>(s)], G[sidx<V, true>(s)]);
     __syncthreads();
-    fft_smem<V, true, true, R16>(sa, sc, fp, 1, 1, m, twm, twml, tid, nthr);
-    for (int s = tid; s < m; s += nthr) hr[s] = sa[sidx<V, true>(s)];
+    const V* H = fft_smem_any<V, true, true, R16>(F, G, fp, 1, 1, m, twm, twml, tid, nthr);
+    for (int s = tid; s < m; s += nthr) hr[s] = H[sidx<V, true>(s)];
     __syncthreads();
 }
 
@@ -270,12 +272,13 @@ __device__ __forceinline__ void fft_cols_store_body(V* buf, V* tmp, V* yb, int64
                                                     const V* __restrict__ twma, const V* __restrict__ twmal,
                                                     const FftPlan& fp, int tid, int nthr)
 {
-    if (ma > 1) fft_smem<V, false, false, R16>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);
+    const V* res = buf;
+    if (ma > 1) res = fft_smem_any<V, false, false, R16>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);
     for (int e = tid; e < ma * C; e += nthr) {
         const int l = e / C, cl = e - l * C;
         const int64_t c = c0 + cl;
         if (c >= Cn) continue;
-        V v = buf[e];
+        V v = res[e];
         if (post && l != 0 && c != 0) v = cmul(v, (sizeof(V) == 16 && tpm) ? __ldg(tpm + c * ma + l) : twn(twNf, (int64_t)l * c * q));
         yb[(int64_t)l * ystride + c] = v;
     }
@@ -401,11 +404,12 @@ __device__ __forceinline__ void ifft_cols_body(V* yb, int64_t Cn, int ma, int q,
         }
     }
     __syncthreads();
-    if (ma > 1) fft_smem<V, true, false, R16>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);
+    const V* res = buf;
+    if (ma > 1) res = fft_smem_any<V, true, false, R16>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);
     for (int e = tid; e < ma * C; e += nthr) {
         const int s = e / C, cl = e - s * C;
         const int64_t c = c0 + cl;
-        if (c < Cn) yb[(int64_t)s * Cn + c] = buf[e];
+        if (c < Cn) yb[(int64_t)s * Cn + c] = res[e];
     }
     __syncthreads();
 }
@@ -457,13 +461,14 @@ __device__ __forceinline__ void ifft_unfold_cols_body(const V* y, int64_t rstrid
             }
         }
         __syncthreads();
-        if (ma > 1) fft_smem<V, true, false, R16>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);
+        const V* res = buf;
+        if (ma > 1) res = fft_smem_any<V, true, false, R16>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);
         const bool init = first && rr == 0, fin = last && rr == Dg - 1;
         for (int e = tid; e < n; e += nthr) {
             const int i = e / C, cl = e - i * C;
             const int64_t c = c0 + cl;
             if (c >= Cn) continue;
-            V hv = buf[e];
+            V hv = res[e];
             if (r != 0) hv = cmulc(hv, twn(twNf, (int64_t)r * (i * cs + c * cc)));
             for (int t = 0; t < p; ++t) {
                 const int64_t lin = ((int64_t)t * ma + i) * Cn + c;

@@ -497,12 +497,14 @@ __device__ __forceinline__ void fft_stage(const V* src, V* dst, int n, int ncol,
 // Whole transform of the ncol columns in buf, using tmp (same size and
 // addressing) as the other half of the ping-pong.  tw / twl: the packed
 // twiddle tables of fp (plain / twiddle-merged form, see FftPlan).  The
-// caller must have synchronised after filling buf; on return the result is
-// in buf and the block is synchronised.  R16: the kernel is built with the
-// radix-16 stage (FP32 only); a plan that has one must be run with R16.
+// caller must have synchronised after filling buf; the result is left where
+// the last stage wrote it (buf after an even number of stages, tmp after an
+// odd one), which is returned, and the block is synchronised.  R16: the
+// kernel is built with the radix-16 stage (FP32 only); a plan that has one
+// must be run with R16.
 template <class V, bool INV, bool SWZ = false, bool R16 = false>
-__device__ __forceinline__ void fft_smem(V* buf, V* tmp, const FftPlan& fp, int ncol, int ld, int cs,
-                                         const V* __restrict__ tw, const V* __restrict__ twl, int tid, int nthr)
+__device__ __forceinline__ V* fft_smem_any(V* buf, V* tmp, const FftPlan& fp, int ncol, int ld, int cs,
+                                           const V* __restrict__ tw, const V* __restrict__ twl, int tid, int nthr)
 {
     int Ns = 1;
     const int n = fp.n;
@@ -529,8 +531,17 @@ __device__ __forceinline__ void fft_smem(V* buf, V* tmp, const FftPlan& fp, int 
         a = b;
         b = t;
     }
+    return a;
+}
+
+// The same with the result copied back into buf when it ended in tmp.
+template <class V, bool INV, bool SWZ = false, bool R16 = false>
+__device__ __forceinline__ void fft_smem(V* buf, V* tmp, const FftPlan& fp, int ncol, int ld, int cs,
+                                         const V* __restrict__ tw, const V* __restrict__ twl, int tid, int nthr)
+{
+    const V* a = fft_smem_any<V, INV, SWZ, R16>(buf, tmp, fp, ncol, ld, cs, tw, twl, tid, nthr);
     if (a != buf) {
-        const int tot = n * ncol;
+        const int tot = fp.n * ncol;
         for (int e = tid; e < tot; e += nthr) {
             const int i = e / ncol, c = e - i * ncol;
             buf[sidx<V, SWZ>(c * cs + i * ld)] = a[sidx<V, SWZ>(c * cs + i * ld)];
