@@ -58,14 +58,27 @@ __device__ __forceinline__ void residue_row_body(const V* fr, const V* gr, V* hr
         }
     }
     __syncthreads();
-    // each transform leaves its result where its last stage wrote it; the
-    // next one takes a buffer that is free at that point as its scratch
-    V* F = fft_smem_any<V, false, true, R16>(sa, sc, fp, 1, 1, m, twm, twml, tid, nthr);
-    V* G = fft_smem_any<V, false, true, R16>(sb, F == sa ? sc : sa, fp, 1, 1, m, twm, twml, tid, nthr);
-    for (int s = tid; s < m; s += nthr) F[sidx<V, true>(s)] = cmul(F[sidx<V, true>(s)], G[sidx<V, true>(s)]);
-    __syncthreads();
-    const V* H = fft_smem_any<V, true, true, R16>(F, G, fp, 1, 1, m, twm, twml, tid, nthr);
-    for (int s = tid; s < m; s += nthr) hr[s] = H[sidx<V, true>(s)];
+    if constexpr (sizeof(V) == 8) {
+        // FP32, bound by shared-memory passes: each transform leaves its
+        // result where its last stage wrote it, and the next one takes a
+        // buffer that is free at that point as its scratch
+        V* F = fft_smem_any<V, false, true, R16>(sa, sc, fp, 1, 1, m, twm, twml, tid, nthr);
+        V* G = fft_smem_any<V, false, true, R16>(sb, F == sa ? sc : sa, fp, 1, 1, m, twm, twml, tid, nthr);
+        for (int s = tid; s < m; s += nthr) F[sidx<V, true>(s)] = cmul(F[sidx<V, true>(s)], G[sidx<V, true>(s)]);
+        __syncthreads();
+        const V* H = fft_smem_any<V, true, true, R16>(F, G, fp, 1, 1, m, twm, twml, tid, nthr);
+        for (int s = tid; s < m; s += nthr) hr[s] = H[sidx<V, true>(s)];
+    } else {
+        // FP64, bound by the FP64 pipe: most row plans up to 2048 points
+        // have an even number of stages, and leaving the odd ones in place
+        // measured no difference, so the results are copied back
+        fft_smem<V, false, true, R16>(sa, sc, fp, 1, 1, m, twm, twml, tid, nthr);
+        fft_smem<V, false, true, R16>(sb, sc, fp, 1, 1, m, twm, twml, tid, nthr);
+        for (int s = tid; s < m; s += nthr) sa[sidx<V, true>(s)] = cmul(sa[sidx<V, true>(s)], sb[sidx<V, true>(s)]);
+        __syncthreads();
+        fft_smem<V, true, true, R16>(sa, sc, fp, 1, 1, m, twm, twml, tid, nthr);
+        for (int s = tid; s < m; s += nthr) hr[s] = sa[sidx<V, true>(s)];
+    }
     __syncthreads();
 }
 
