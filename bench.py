@@ -13,6 +13,11 @@ reported beside it.
 Prints one JSON line.  Under torchrun (N > 1) every rank runs the same
 independent sweep (the convolutions shard with no exchange: weak scaling),
 the time is the max over ranks and value counts every rank's outputs.
+
+The CPU leg (rank 0, after every timed region) runs the oracle twice over:
+timed on the host cores as the CPU baseline, and untimed as the FP64
+reference of every result the GPU arm produced (``max_rel_err`` and the
+per-size errors), which is the only use of the oracle here.
 """
 from __future__ import annotations
 
@@ -97,6 +102,23 @@ def floor_flops(L: int) -> float:
     while not _good(top):
         top += 1
     return min(model_flops(L, m, -(-M // m)) for m in smooth_upto(top) if m >= 16)
+
+
+def valid_tuple_count(L: int) -> int:
+    """Valid (m, p, q, D) of one axis with M = 2L - 1: every 7-smooth m from
+    16 up to the explicit size, p and q derived, D in {1, 2, 4, ...} below q
+    and D = q."""
+    M = 2 * L - 1
+    top = M
+    while not _good(top):
+        top += 1
+    n = 0
+    for m in smooth_upto(top):
+        if m < 16:
+            continue
+        q = -(-M // m)
+        n += len({d for d in (1 << k for k in range(0, 40)) if d < q} | {q})
+    return n
 
 
 def sweep_sizes():
@@ -192,6 +214,46 @@ def cpu_baseline(sizes, budget_s=20.0, seed_base=0):
                       f"{done[0]}..{done[-1]} ({len(done)} of {len(sizes)} sizes, each once), {t_tot:.1f} s"}
 
 
+def rel_max_err(x, ref) -> float:
+    """max |x - ref| / max |ref| (the per-result error of Section 2.3's
+    convolution, Eq. 4, against its FP64 reference)."""
+    import numpy as np
+    x = np.asarray(x)
+    ref = np.asarray(ref)
+    den = float(np.max(np.abs(ref))) if ref.size else 0.0
+    num = float(np.max(np.abs(x - ref))) if ref.size else 0.0
+    return num / den if den > 0 else num
+
+
+def oracle_errors(pending):
+    """The CPU leg's second part, after every timed region: the FP64 oracle's
+    reference of each result the GPU arm produced, and the result's relative
+    max-norm error against it.  pending: (name, result, key, ref_fn) with
+    ref_fn(oracle) -> reference; references are cached by key, so the FP64,
+    explicit, FP32 and end-to-end results of one input share one.  A key
+    starting with "int:" marks integer-valued inputs, whose FP64 result must
+    round to the exact integer convolution: those report exact = True/False."""
+    import numpy as np
+    import oracle
+    oracle.lib()
+    cache, out = {}, {}
+    t0 = time.perf_counter()
+    for name, got, key, ref_fn in pending:
+        if key not in cache:
+            cache[key] = ref_fn(oracle)
+        ref = cache[key]
+        if isinstance(ref, list):
+            out[name] = max(rel_max_err(a, b) for a, b in zip(got, ref))
+        elif key.startswith("int:"):
+            hre, him = ref
+            out[name] = {"exact": bool(np.array_equal(np.rint(got.real).astype(np.int64), hre)
+                                       and np.array_equal(np.rint(got.imag).astype(np.int64), him)),
+                         "max_abs_err": float(np.max(np.abs(got - (hre + 1j * him))))}
+        else:
+            out[name] = rel_max_err(got, ref)
+    return out, time.perf_counter() - t0
+
+
 def run_reference(args):
     """--impl reference: the oracle timed on the host cores, bounded sample per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -267,12 +329,26 @@ def main():
 
     sizes = [int(x) for x in args.sizes.split(",")] if args.sizes else sweep_sizes()
     os.makedirs(os.path.dirname(args.tuning_db), exist_ok=True)
+    # results to check against the oracle once every timed region is over:
+    # (name, result on the host, reference key, reference builder)
+    pending = []
+
+    def sweep_inputs(i, L):
+        return synth.unit_disk(synth.BASE_SEED + 10 + i, (L,)), synth.unit_disk(synth.BASE_SEED + 1010 + i, (L,))
+
+    def sweep_ref(i, L):
+        return lambda o: o.conv_fft(*sweep_inputs(i, L))
+
+    def check_sweep(tag, ins):
+        for i, (L, (_, _, h)) in enumerate(zip(sizes, ins)):
+            pending.append((f"{tag}/L={L}", h.cpu().numpy().astype(np.complex128), f"sweep{i}", sweep_ref(i, L)))
 
     def make_inputs(tdt):
         ins = []
         for i, L in enumerate(sizes):
-            f = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 10 + i, (L,))).to(dev, tdt)
-            g = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 1010 + i, (L,))).to(dev, tdt)
+            fn, gn = sweep_inputs(i, L)
+            f = torch.from_numpy(fn).to(dev, tdt)
+            g = torch.from_numpy(gn).to(dev, tdt)
             ins.append((f, g, torch.empty_like(f)))
         return ins
 
@@ -385,6 +461,7 @@ def main():
     # per-kernel split of the roofline comes from a second, instrumented run
     ms64, launches, ms_list, _ = time_sweep(plans64, ins64, args.steps, args.warmup, nvtx="hdc_fp64_timed")
     clocks = sampler.stop()
+    check_sweep("sweep_fp64", ins64)
     _, _, _, kstats = time_sweep(plans64, ins64, args.steps, 1, stats=True)
     if kstats is None:
         raise RuntimeError("per-kernel event times unavailable")
@@ -405,15 +482,40 @@ def main():
     plans_ex = make_plans(hdc.HDC_C128, hdc.HDC_EXPLICIT)
     ms_ex, _, _, _ = time_sweep(plans_ex, ins64, args.steps, args.warmup)
     ms_ex = rank_max(ms_ex)
+    check_sweep("explicit_fp64", ins64)
+
+    # integer inputs in [-8, 8] through the tuned plans of four sweep sizes
+    # (one untimed call each): the FP64 result must round to the exact
+    # integer convolution
+    for L in [x for x in (1 << 16, 1 << 20, 3 << 20, 1 << 22) if x in sizes]:
+        i = sizes.index(L)
+        fr, fi = synth.small_ints(synth.BASE_SEED + 20 + i, (L,))
+        gr, gi = synth.small_ints(synth.BASE_SEED + 1020 + i, (L,))
+        fz = torch.from_numpy(synth.ints_to_complex(fr, fi)).to(dev)
+        gz = torch.from_numpy(synth.ints_to_complex(gr, gi)).to(dev)
+        hz = torch.empty_like(fz)
+        wz = torch.empty(plans64[i].workspace_bytes, dtype=torch.uint8, device=dev)
+        plans64[i].execute(fz, gz, out=hz, workspace=wz)
+        torch.cuda.synchronize(dev)
+        pending.append((f"integer_fp64/L={L}", hz.cpu().numpy(), f"int:{L}",
+                        lambda o, a=(fr, fi, gr, gi): o.conv_int_exact(*a, method="ntt")))
+        del fz, gz, hz, wz
 
     # --- per-size hybrid vs explicit (device time, FP64)
+    # per size, the tuned and the explicit tuple timed alternately (three
+    # rounds, median), each as graph replays of ten calls after an L2 flush
     per_size = []
     for L, pt, pe, (f, g, h) in zip(sizes, plans64, plans_ex, ins64):
-        t_h, _, _, _ = time_sweep([pt], [(f, g, h)], 3, 1, reps=10)
-        t_e, _, _, _ = time_sweep([pe], [(f, g, h)], 3, 1, reps=10)
+        th, te = [], []
+        for _ in range(3):
+            th.append(time_sweep([pt], [(f, g, h)], 3, 1, reps=10)[0])
+            te.append(time_sweep([pe], [(f, g, h)], 3, 1, reps=10)[0])
         prm = pt.params[0]
         per_size.append({"L": L, "m": prm["m"], "p": prm["p"], "q": prm["q"], "D": prm["D"],
-                         "hybrid_ms": round(t_h, 5), "explicit_ms": round(t_e, 5)})
+                         "hybrid_ms": round(statistics.median(th), 5),
+                         "explicit_ms": round(statistics.median(te), 5),
+                         "same_tuple_as_explicit": prm["q"] == 1 and prm["m"] == pe.params[0]["m"],
+                         "valid_tuples": valid_tuple_count(L), "timed_tuples": pt.timed})
     del ins64
 
     # --- FP32 tuned hybrid
@@ -421,6 +523,7 @@ def main():
     plans32 = make_plans(hdc.HDC_C64, hdc.HDC_TUNE_EXHAUSTIVE)
     ms32, _, _, _ = time_sweep(plans32, ins32, args.steps, args.warmup)
     ms32 = rank_max(ms32)
+    check_sweep("sweep_fp32", ins32)
     _, _, _, kstats32 = time_sweep(plans32, ins32, 1, 1, stats=True)
     del ins32
 
@@ -436,6 +539,18 @@ def main():
         fs = [fa[offs[i]:offs[i + 1]] for i in range(nconv)]
         gs = [ga[offs[i]:offs[i + 1]] for i in range(nconv)]
         hs = [ha[offs[i]:offs[i + 1]] for i in range(nconv)]
+        # the convolutions checked against the oracle: every one with
+        # L <= 2048 and a seeded sample of 64 longer ones
+        rng = np.random.default_rng(synth.BASE_SEED + 4)
+        longer = [i for i in range(nconv) if Ls[i] > 2048]
+        sel = [i for i in range(nconv) if Ls[i] <= 2048] + sorted(
+            rng.choice(longer, size=min(64, len(longer)), replace=False).tolist())
+
+        def batched_ref(o):
+            fa_n = synth.unit_disk(synth.BASE_SEED + 40, (tot,))
+            ga_n = synth.unit_disk(synth.BASE_SEED + 41, (tot,))
+            return [o.conv_fft(fa_n[offs[i]:offs[i + 1]], ga_n[offs[i]:offs[i + 1]]) for i in sel]
+
         t0 = time.perf_counter()
         ms_t, _ = hdc.batched_tune(fs, gs, hs, reps=3, max_cands=8)
         tune_b = time.perf_counter() - t0
@@ -469,6 +584,10 @@ def main():
                 ev.append((e0, e1))
             torch.cuda.synchronize(dev)
             ok = hdc.BatchedPlan.status(wsb) == 0
+            hh = ha.cpu().numpy().astype(np.complex128)
+            pending.append((f"batched_{'fp64' if dcode == hdc.HDC_C128 else 'fp32'}_{name}",
+                            [hh[offs[i]:offs[i + 1]] for i in sel], "batched", batched_ref))
+            del hh
             msb = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
             fl = sum(pp["q"] * (15 * pp["m"] * math.log2(pp["m"]) + 6 * pp["m"] + 24 * pp["L"]) + 2 * pp["L"]
                      for pp in plan.params)
@@ -476,6 +595,7 @@ def main():
                          "model_tflops": round(fl / (msb * 1e-3) / 1e12, 4)}
             del graph, plan, wsb
         res["convolutions"] = nconv
+        res["checked_against_oracle"] = len(sel)
         res["outputs"] = tot
         res["lengths"] = Ls
         res["tuning_s"] = round(tune_b, 1)
@@ -524,6 +644,15 @@ def main():
                                                      workspace=ws1, stream=s_), 21)
         msr, _ = graph_time(lambda s_: hdc.convnd(f1, g1, 1, [512], p=[2], q=[4], D=[1], out=h1, workspace=ws1,
                                                   stream=s_), max(args.steps, 5))
+        rows = [0, 1, 8191, 16383]
+        hrows = h1[rows].cpu().numpy()
+
+        def c1_ref(o):
+            fn = synth.unit_disk(synth.BASE_SEED + 1, (16384, L1))
+            gn = synth.unit_disk(synth.BASE_SEED + 101, (16384, L1))
+            return [o.conv_direct(fn[r], gn[r]) for r in rows]
+
+        pending.append(("config1_fp64", [hrows[k] for k in range(len(rows))], "config1", c1_ref))
         return {"params": {"m": 512, "p": 2, "q": 4, "D": 1},
                 "latency_us": {"graph_replay": round(ms_one * 1e3, 2),
                                "eager_call_median": round(lat[10], 2), "eager_call_p10": round(lat[2], 2),
@@ -586,7 +715,7 @@ def main():
         g = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 31, shape)).to(dev)
         h = torch.empty_like(f)
         t0 = time.perf_counter()
-        best, _ = hdc.tune(f, g, len(shape), max_ratio=1.3, reps=2)
+        best, _ = hdc.tune(f, g, len(shape), max_ratio=1.3, reps=5)
         tt = time.perf_counter() - t0
         mv = [b["m"] for b in best]
         Dv = [b["D"] for b in best]
@@ -595,6 +724,9 @@ def main():
         msn, fl = graph_time(lambda s_: hdc.convnd(f, g, len(shape), mv, D=Dv, out=h, workspace=wsn, stream=s_),
                              args.steps)
         outs_n = int(np.prod(shape))
+        pending.append((f"nd_fp64/{name}", h.cpu().numpy(), f"nd:{name}",
+                        lambda o, sh=shape: o.conv_fft(synth.unit_disk(synth.BASE_SEED + 30, sh),
+                                                       synth.unit_disk(synth.BASE_SEED + 31, sh))))
         nd[name] = {"value": world * outs_n / (msn * 1e-3), "ms": round(msn, 4), "m": mv, "D": Dv,
                     "model_tflops": round(fl / (msn * 1e-3) / 1e12, 4),
                     "roofline_frac": round(fl / (msn * 1e-3) / 1e12 / peak64, 4), "tuning_s": round(tt, 1)}
@@ -610,6 +742,9 @@ def main():
         except hdc.HDCError:
             continue
         herm[str(mh)] = {"ms": round(msh, 4), "model_tflops": round(fl / (msh * 1e-3) / 1e12, 4)}
+        pending.append((f"hermitian_fp64/m={mh}", hh.cpu().numpy(), "herm",
+                        lambda o: o.conv_hermitian_fft(synth.hermitian_normal(synth.BASE_SEED + 32, K),
+                                                       synth.hermitian_normal(synth.BASE_SEED + 33, K))))
     bm = min(herm, key=lambda k: herm[k]["ms"])
     nd["hermitian_2d_K512"] = {"value": world * (2 * K - 1) * K / (herm[bm]["ms"] * 1e-3), "ms": herm[bm]["ms"],
                                "m": int(bm), "model_tflops": herm[bm]["model_tflops"],
@@ -633,6 +768,12 @@ def main():
     for lf_log in (10, 16, 20):
         Lf = 1 << lf_log
         fu = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 41 + lf_log, (Lf,))).to(dev)
+
+        def uneq_ref(o, Lf=Lf, lf_log=lf_log):
+            fpad = np.zeros(Lg, dtype=np.complex128)
+            fpad[:Lf] = synth.unit_disk(synth.BASE_SEED + 41 + lf_log, (Lf,))
+            return o.conv_fft(fpad, synth.unit_disk(synth.BASE_SEED + 40, (Lg,)))
+
         t0 = time.perf_counter()
         bu, tru = hdc.tune_unequal(fu, gu, 1, max_ratio=1.5, reps=2)
         ttu = time.perf_counter() - t0
@@ -648,6 +789,7 @@ def main():
                                                                 workspace=wsu, stream=s_), args.steps)
             res[key] = {"ms": round(msu, 4), "m": b["m"], "lam": b["lam"], "q": b["q"], "D": b["D"],
                         "model_tflops": round(flu / (msu * 1e-3) / 1e12, 4)}
+            pending.append((f"unequal_fp64/Lf=2^{lf_log}/{key}", hu.cpu().numpy(), f"uneq:{lf_log}", uneq_ref))
             del wsu
         fpad = torch.zeros_like(gu)
         fpad[:Lf] = fu
@@ -658,6 +800,7 @@ def main():
                                                     workspace=wsp, stream=s_), args.steps)
         res["padded_equal"] = {"ms": round(msp, 4), "m": bp[0]["m"], "q": bp[0]["q"], "D": bp[0]["D"],
                                "model_tflops": round(flp / (msp * 1e-3) / 1e12, 4)}
+        pending.append((f"unequal_fp64/Lf=2^{lf_log}/padded_equal", hu.cpu().numpy(), f"uneq:{lf_log}", uneq_ref))
         best_ms = res["matched"]["ms"]
         uneq[f"Lf2^{lf_log}_Lg2^22"] = {
             "value": world * Lg / (best_ms * 1e-3), "ms": best_ms,
@@ -684,6 +827,17 @@ def main():
         wsm = torch.empty(nbm, dtype=torch.uint8, device=dev)
         msm, flm = graph_time(lambda s_: hdc.convnd_multi(xs, 1, [bm_[0]["m"]], op=op, D=[bm_[0]["D"]], out=hm,
                                                           workspace=wsm, stream=s_), args.steps)
+
+        def multi_ref(o, op=op, nin=nin):
+            xn = [synth.unit_disk(synth.BASE_SEED + 50 + i, (Lm,)) for i in range(nin)]
+            if op == "product":
+                acc = xn[0]
+                for x in xn[1:]:
+                    acc = o.conv_fft(acc, x)     # first Lm outputs depend on first Lm only
+                return acc
+            return sum(o.conv_fft(xn[i], xn[i + 1]) for i in range(0, nin, 2))
+
+        pending.append((f"multi_fp64/{op}_n{nin}", hm.cpu().numpy(), f"multi:{op}{nin}", multi_ref))
         bp2, _ = hdc.tune(xs[0], xs[1], 1, max_ratio=1.3, reps=2)
         nb2 = hdc.workspace_size([Lm], [2 * Lm - 1], [bp2[0]["m"]], D=[bp2[0]["D"]])
         ws2 = torch.empty(nb2, dtype=torch.uint8, device=dev)
@@ -731,6 +885,12 @@ def main():
         wsr = torch.empty(nbr, dtype=torch.uint8, device=dev)
         msr, flr = graph_time(lambda s_: hdc.convnd_real(fr, gr, dims, [b["m"] for b in br], D=[b["D"] for b in br],
                                                          out=hr, workspace=wsr, stream=s_), args.steps)
+
+        def real_ref(o, sh=shape):
+            zz = synth.unit_disk(synth.BASE_SEED + 60, sh)
+            return o.conv_fft(zz.real.astype(np.complex128), zz.imag.astype(np.complex128)).real
+
+        pending.append((f"real_fp64/{name}", hr.cpu().numpy(), f"real:{name}", real_ref))
         fc = fr.to(torch.complex128)
         gc = gr.to(torch.complex128)
         hc = torch.empty_like(fc)
@@ -739,6 +899,7 @@ def main():
         wsc = torch.empty(nbc, dtype=torch.uint8, device=dev)
         msc, _ = graph_time(lambda s_: hdc.convnd(fc, gc, dims, [b["m"] for b in bc], D=[b["D"] for b in bc], out=hc,
                                                   workspace=wsc, stream=s_), args.steps)
+        pending.append((f"real_fp64/{name}/complex_path", hc.cpu().numpy().real.copy(), f"real:{name}", real_ref))
         outs_r = int(np.prod(shape))
         real[name] = {"value": world * outs_r / (msr * 1e-3), "ms": round(msr, 4), "m": [b["m"] for b in br],
                       "D": [b["D"] for b in br], "model_tflops": round(flr / (msr * 1e-3) / 1e12, 4),
@@ -780,6 +941,8 @@ def main():
         e2e_step()
     torch.cuda.synchronize(dev)
     e2e_s = rank_max((time.perf_counter() - t0) / args.steps)
+    for i, (L, (_, _, h)) in enumerate(zip(sizes, pinned)):
+        pending.append((f"e2e_fp64/L={L}", h.numpy().copy(), f"sweep{i}", sweep_ref(i, L)))
     h2d = sum(2 * L * 16 for L in sizes)
     d2h = sum(L * 16 for L in sizes)
     # the same host copies alone (same buffers, sizes and streams, no
@@ -847,6 +1010,35 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(sizes)
+    # every result above against the FP64 oracle (rank 0; untimed)
+    errs, err_s = ({}, 0.0) if rank != 0 else oracle_errors(pending)
+    del pending
+    for r in per_size:
+        r["hybrid_err"] = errs.get(f"sweep_fp64/L={r['L']}")
+        r["explicit_err"] = errs.get(f"explicit_fp64/L={r['L']}")
+        r["fp32_err"] = errs.get(f"sweep_fp32/L={r['L']}")
+
+    def emax(prefix):
+        v = [x for k, x in errs.items() if k.startswith(prefix) and isinstance(x, float)]
+        return max(v) if v else None
+
+    max_err = {
+        "basis": "relative max-norm error max|h - h*| / max|h*| against the FP64 oracle (explicitly padded "
+                 "FFT convolution O2; direct sum O1 for the single small configuration; O6 for the Hermitian "
+                 "case; exact integers O3), each result taken from the timed runs' outputs",
+        "sweep_fp64": emax("sweep_fp64/"), "explicit_fp64": emax("explicit_fp64/"),
+        "sweep_fp32": emax("sweep_fp32/"), "e2e_fp64": emax("e2e_fp64/"),
+        "integer_fp64_exact": {k.split("/", 1)[1]: v for k, v in errs.items() if k.startswith("integer_fp64/")},
+        "config1_fp64": errs.get("config1_fp64"),
+        "nd_fp64": {k.split("/", 1)[1]: v for k, v in errs.items() if k.startswith("nd_fp64/")},
+        "hermitian_fp64": {k.split("/", 1)[1]: v for k, v in errs.items() if k.startswith("hermitian_fp64/")},
+        "batched_fp64": {k.rsplit("_", 1)[1]: v for k, v in errs.items() if k.startswith("batched_fp64_")},
+        "batched_fp32": {k.rsplit("_", 1)[1]: v for k, v in errs.items() if k.startswith("batched_fp32_")},
+        "unequal_fp64": {k.split("/", 1)[1]: v for k, v in errs.items() if k.startswith("unequal_fp64/")},
+        "multi_fp64": {k.split("/", 1)[1]: v for k, v in errs.items() if k.startswith("multi_fp64/")},
+        "real_fp64": {k.split("/", 1)[1]: v for k, v in errs.items() if k.startswith("real_fp64/")},
+        "oracle_s": round(err_s, 1),
+    }
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -870,6 +1062,7 @@ def main():
         "batched_fp32": batched32,
         "config1_fp64": cfg1,
         "per_size_fp64": per_size,
+        "max_rel_err": max_err,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": world * outs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -33,10 +33,15 @@
  *  - f, g, h and the workspace are DEVICE pointers owned by the caller,
  *    16-byte aligned, on the current CUDA device.  f and g are read-only
  *    unless inplace = 1, in which case h may equal f or g.
- *  - The library allocates device memory only for its own twiddle tables
- *    (zeta_n^k for exact integer k, made once per (n, dtype, device) with
- *    FP64 sincospi and kept until hdc_release_caches()).  The caller
- *    allocates the workspace; query its size with hdc_workspace_size().
+ *  - The convolution calls allocate nothing and never synchronise.  The
+ *    twiddle tables they read (zeta_n^k for exact integer k, one FP64
+ *    sincospi each, made once per (n, dtype, device) and kept until
+ *    hdc_release_caches()) are made by the preparation calls: hdc_prepare*
+ *    (one per kind of convolution call, same arguments minus the data),
+ *    hdc_plan_create, the tuners and hdc_batched_create.  A convolution call
+ *    whose tables are missing returns HDC_ERR_NOT_PREPARED and launches
+ *    nothing.  The caller allocates the workspace; query its size with
+ *    hdc_workspace_size().
  *  - Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default)
  *    and is asynchronous; nothing is synchronised.
  *  - Every error is a return code (hdc_status).  Nothing throws across the
@@ -65,7 +70,8 @@ typedef enum hdc_status {
     HDC_ERR_CUDA = -6,             /* a CUDA runtime call or kernel launch failed           */
     HDC_ERR_TIMEOUT = -7,          /* a bounded device-side wait gave up                    */
     HDC_ERR_NOT_TUNED = -8,        /* no tuning record / predictor for the request          */
-    HDC_ERR_WORKSPACE = -9         /* workspace missing or smaller than required            */
+    HDC_ERR_WORKSPACE = -9,        /* workspace missing or smaller than required            */
+    HDC_ERR_NOT_PREPARED = -10     /* twiddle tables not made: call hdc_prepare* first      */
 } hdc_status;
 
 typedef enum hdc_dtype {
@@ -367,8 +373,46 @@ int hdc_conv2d_hermitian(const void* f, const void* g, void* h, int64_t K,
                          int64_t batch, void* workspace, size_t ws_bytes,
                          void* stream);
 
+/* ---------------------------------------------------------- preparation
+ * Make, on the current device, every twiddle table the matching convolution
+ * call with these arguments reads (the zeta_N^k of the folds and unfolds,
+ * N = q m per axis, and the per-stage tables of the m-point transforms of
+ * its route; Section 2.2).  This is where the library allocates: each
+ * missing table is a cudaMalloc and a kernel on a private stream that is
+ * waited for, so prepare before any stream capture.  Tables already made
+ * cost a lookup.  Nothing is launched on the caller's streams and no data
+ * pointer is needed.  The batch count matters (it selects the route).
+ *   hdc_prepare           for hdc_convnd / conv1d / conv2d / conv3d,
+ *                         hdc_convnd_host and hdc_convnd_residues
+ *   hdc_prepare_window    for hdc_convnd_window
+ *   hdc_prepare_hermitian for hdc_conv2d_hermitian
+ *   hdc_prepare_unequal   for hdc_convnd_unequal
+ *   hdc_prepare_multi     for hdc_convnd_multi
+ *   hdc_prepare_real      for hdc_convnd_real
+ * Errors: those of the convolution call's parameter checks, HDC_ERR_CUDA. */
+int hdc_prepare(int dims, const int64_t* L, const int64_t* M, const int64_t* m,
+                const int64_t* p, const int64_t* q, const int64_t* D, int dtype,
+                int64_t batch);
+int hdc_prepare_window(int dims, const int64_t* L, const int64_t* M,
+                       const int64_t* m, const int64_t* p, const int64_t* q,
+                       const int64_t* D, const int64_t* o, const int64_t* Lw,
+                       int dtype, int64_t batch);
+int hdc_prepare_hermitian(int64_t K, const int64_t* m, const int64_t* D,
+                          int dtype, int64_t batch);
+int hdc_prepare_unequal(int dims, const int64_t* Lf, const int64_t* Lg,
+                        const int64_t* M, const int64_t* m, const int64_t* lam,
+                        const int64_t* D, const int64_t* o, const int64_t* Lw,
+                        int dtype, int64_t batch);
+int hdc_prepare_multi(int dims, int n, int op, const int64_t* L,
+                      const int64_t* M, const int64_t* m, const int64_t* p,
+                      const int64_t* q, const int64_t* D, int dtype,
+                      int64_t batch);
+int hdc_prepare_real(int dims, const int64_t* L, const int64_t* M,
+                     const int64_t* m, const int64_t* p, const int64_t* q,
+                     const int64_t* D, int dtype, int64_t batch);
+
 /* Free the cached twiddle tables on every device (call with no work in
- * flight that uses them). */
+ * flight that uses them; later convolution calls need a new preparation). */
 int hdc_release_caches(void);
 
 /* ------------------------------------------------- allocation-free call
@@ -393,7 +437,17 @@ int hdc_release_caches(void);
  *    errors as hdc_conv1d.
  *  - The first call on a device, with that device current, looks up the
  *    array's device address (cudaGetSymbolAddress) and keeps it; make that
- *    first call before any stream capture.
+ *    first call before any stream capture.  Under CUDA's default lazy
+ *    module loading that first call is also when the driver loads the
+ *    library's kernels and places the array in device memory (an implicit
+ *    allocation and synchronisation by the driver), so make one call per
+ *    device before the phase that must not allocate, or set
+ *    CUDA_MODULE_LOADING=EAGER so the driver does it when the library is
+ *    loaded.
+ *  - The fold/unfold twiddles zeta_N^k come from one table of N = q m
+ *    entries in both dtypes (the regular complex<float> route splits a table
+ *    above 2^16 entries into two smaller ones); every entry is one FP64
+ *    sincospi rounded once, so the results agree to rounding.
  *  - All calls share the one array and every call rewrites what it reads,
  *    so nothing from an earlier call leaks into a result; but calls whose
  *    work overlaps on the GPU (other streams, other host threads) race on
@@ -538,7 +592,9 @@ int hdc_tune_convnd_proxy(int dims, const int64_t* L, const int64_t* M,
  * most likely valid classes and the valid neighbouring q classes (one down,
  * one up) of its best two, at most six distinct m (one axis at a time, last
  * first, the others held), on scratch buffers it allocates and frees, and
- * keeps the fastest. */
+ * keeps the fastest.  Every mode ends by making the twiddle tables the
+ * plan's execution reads (hdc_prepare), so hdc_plan_execute allocates
+ * nothing and may be captured in a CUDA graph from its first call. */
 int hdc_plan_create(hdc_plan** plan, int dims, const int64_t* L,
                     const int64_t* M, const int64_t* m, const int64_t* D,
                     int dtype, int64_t batch, int mode, const char* tuning_db,

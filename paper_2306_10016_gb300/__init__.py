@@ -51,6 +51,7 @@ HDC_ERR_CUDA = -6
 HDC_ERR_TIMEOUT = -7
 HDC_ERR_NOT_TUNED = -8
 HDC_ERR_WORKSPACE = -9
+HDC_ERR_NOT_PREPARED = -10
 HDC_MULTI_PRODUCT = 0
 HDC_MULTI_DOT = 1
 _MULTI_OPS = {"product": HDC_MULTI_PRODUCT, "dot": HDC_MULTI_DOT, HDC_MULTI_PRODUCT: HDC_MULTI_PRODUCT,
@@ -91,6 +92,15 @@ _SIGS = [
     ("hdc_convnd", C.c_int, [C.c_int, _vp, _vp, _vp, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, C.c_int,
                              C.c_int, _i64, _vp, _sz, _vp]),
     ("hdc_release_caches", C.c_int, []),
+    ("hdc_prepare", C.c_int, [C.c_int, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, C.c_int, _i64]),
+    ("hdc_prepare_window", C.c_int, [C.c_int, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, C.c_int,
+                                     _i64]),
+    ("hdc_prepare_hermitian", C.c_int, [_i64, _i64p, _i64p, C.c_int, _i64]),
+    ("hdc_prepare_unequal", C.c_int, [C.c_int, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, C.c_int,
+                                      _i64]),
+    ("hdc_prepare_multi", C.c_int, [C.c_int, C.c_int, C.c_int, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, C.c_int,
+                                    _i64]),
+    ("hdc_prepare_real", C.c_int, [C.c_int, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p, C.c_int, _i64]),
     ("hdc_probe_fma", C.c_int, [C.c_int, _i64, C.c_int, C.c_int, _vp, _vp, C.POINTER(C.c_double)]),
     ("hdc_conv1d_noalloc", C.c_int, [_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _i64, C.c_int, _i64, _vp]),
 ]
@@ -352,6 +362,28 @@ def dtype_code(t) -> int:
     raise TypeError(f"unsupported dtype {t}: use torch.complex64 or torch.complex128")
 
 
+def _prepare(name: str, *args) -> None:
+    """Make the twiddle tables a convolution call reads (hdc_prepare*) on the
+    current device, unless a stream capture is running: the convolution
+    calls themselves allocate nothing, and a table made during a capture
+    would break it (the call then fails with HDC_ERR_NOT_PREPARED)."""
+    torch = _torch()
+    if torch.cuda.is_current_stream_capturing():
+        return
+    _check(getattr(lib(), name)(*args), name)
+
+
+def prepare(L, m, M=None, p=0, q=0, D=0, dtype=HDC_C128, batch=1) -> None:
+    """hdc_prepare: the twiddle tables of convnd / conv1d-3d / convnd_host /
+    convnd_residues for these per-axis parameters (lists) on the current
+    device."""
+    dims = len(L)
+    Mv = _per_axis(M, dims, "M") or [2 * int(x) - 1 for x in L]
+    _check(lib().hdc_prepare(dims, _arr(L), _arr(Mv), _arr(_per_axis(m, dims, "m")), _arr(_per_axis(p, dims, "p")),
+                             _arr(_per_axis(q, dims, "q")), _arr(_per_axis(D, dims, "D")), dtype, batch),
+           "hdc_prepare")
+
+
 def convnd(f, g, dims: int, m, M=None, p=0, q=0, D=0, out=None, inplace=False, workspace=None,
            stream=None):
     """First L outputs per axis of the linear convolution of f and g over
@@ -387,6 +419,7 @@ def convnd(f, g, dims: int, m, M=None, p=0, q=0, D=0, out=None, inplace=False, w
         workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=f.device)
     st = stream if stream is not None else torch.cuda.current_stream(f.device)
     with torch.cuda.device(f.device):
+        _prepare("hdc_prepare", dims, _arr(L), _arr(Mv), _arr(mv), _arr(pv), _arr(qv), _arr(Dv), dt, batch)
         rc = lib().hdc_convnd(dims, f.data_ptr(), g.data_ptr(), h.data_ptr(), _arr(L), _arr(Mv), _arr(mv),
                               _arr(pv), _arr(qv), _arr(Dv), int(bool(inplace)), dt, batch,
                               workspace.data_ptr(), workspace.numel() * workspace.element_size(),
@@ -418,6 +451,8 @@ def convnd_window(f, g, dims, m, o, Lw, M=None, p=0, q=0, D=0, out=None, workspa
         workspace = torch.empty(max(1, nb.value), dtype=torch.uint8, device=f.device)
     st = stream if stream is not None else torch.cuda.current_stream(f.device)
     with torch.cuda.device(f.device):
+        _prepare("hdc_prepare_window", dims, _arr(L), _arr(Mv), _arr(mv), _arr(pv), _arr(qv), _arr(Dv), _arr(ov),
+                 _arr(Lwv), dt, batch)
         _check(lib().hdc_convnd_window(dims, f.data_ptr(), g.data_ptr(), h.data_ptr(), _arr(L), _arr(Mv), _arr(mv),
                                        _arr(pv), _arr(qv), _arr(Dv), _arr(ov), _arr(Lwv), dt, batch,
                                        workspace.data_ptr(), workspace.numel() * workspace.element_size(),
@@ -469,6 +504,8 @@ def convnd_multi(xs, dims, m, op="product", M=None, p=0, q=0, D=0, out=None, wor
     ptrs = (_vp * n)(*[x.data_ptr() for x in xs])
     st = stream if stream is not None else torch.cuda.current_stream(x0.device)
     with torch.cuda.device(x0.device):
+        _prepare("hdc_prepare_multi", dims, n, opc, _arr(L), _arr(Mv), _arr(mv), _arr(pv), _arr(qv), _arr(Dv), dt,
+                 batch)
         _check(lib().hdc_convnd_multi(dims, n, opc, ptrs, h.data_ptr(), _arr(L), _arr(Mv), _arr(mv), _arr(pv), _arr(qv),
                                       _arr(Dv), dt, batch, workspace.data_ptr(),
                                       workspace.numel() * workspace.element_size(), st.cuda_stream),
@@ -516,6 +553,7 @@ def convnd_real(f, g, dims, m, M=None, p=0, q=0, D=0, out=None, workspace=None, 
         workspace = torch.empty(max(1, nb.value), dtype=torch.uint8, device=f.device)
     st = stream if stream is not None else torch.cuda.current_stream(f.device)
     with torch.cuda.device(f.device):
+        _prepare("hdc_prepare_real", dims, _arr(L), _arr(Mv), _arr(mv), _arr(pv), _arr(qv), _arr(Dv), dt, batch)
         _check(lib().hdc_convnd_real(dims, f.data_ptr(), g.data_ptr(), h.data_ptr(), _arr(L), _arr(Mv), _arr(mv),
                                      _arr(pv), _arr(qv), _arr(Dv), dt, batch, workspace.data_ptr(),
                                      workspace.numel() * workspace.element_size(), st.cuda_stream),
@@ -575,6 +613,8 @@ def convnd_unequal(f, g, dims, m, lam=1, M=None, D=0, o=None, Lw=None, out=None,
         workspace = torch.empty(max(1, nb.value), dtype=torch.uint8, device=f.device)
     st = stream if stream is not None else torch.cuda.current_stream(f.device)
     with torch.cuda.device(f.device):
+        _prepare("hdc_prepare_unequal", dims, _arr(Lf), _arr(Lg), _arr(Mv), _arr(mv), _arr(lv), _arr(Dv), _arr(ov),
+                 _arr(Lwv), dt, batch)
         _check(lib().hdc_convnd_unequal(dims, f.data_ptr(), g.data_ptr(), h.data_ptr(), _arr(Lf), _arr(Lg),
                                         _arr(Mv), _arr(mv), _arr(lv), _arr(Dv), _arr(ov), _arr(Lwv), dt, batch,
                                         workspace.data_ptr(), workspace.numel() * workspace.element_size(),
@@ -602,6 +642,7 @@ def conv2d_hermitian(f, g, m=None, D=0, out=None, workspace=None, stream=None):
         workspace = torch.empty(max(1, nb.value), dtype=torch.uint8, device=f.device)
     st = stream if stream is not None else torch.cuda.current_stream(f.device)
     with torch.cuda.device(f.device):
+        _prepare("hdc_prepare_hermitian", K, mv, Dv, dt, batch)
         _check(lib().hdc_conv2d_hermitian(f.data_ptr(), g.data_ptr(), h.data_ptr(), K, mv, Dv, dt, batch,
                                           workspace.data_ptr(), workspace.numel() * workspace.element_size(),
                                           st.cuda_stream), "hdc_conv2d_hermitian")
@@ -627,6 +668,7 @@ def convnd_residues(f, g, dims, m, r_lo, r_hi, M=None, p=0, q=0, D=0, out=None, 
         workspace = torch.empty(nbytes, dtype=torch.uint8, device=f.device)
     st = stream if stream is not None else torch.cuda.current_stream(f.device)
     with torch.cuda.device(f.device):
+        _prepare("hdc_prepare", dims, _arr(L), _arr(Mv), _arr(mv), _arr(pv), _arr(qv), _arr(Dv), dt, batch)
         _check(lib().hdc_convnd_residues(dims, f.data_ptr(), g.data_ptr(), h.data_ptr(), _arr(L), _arr(Mv), _arr(mv),
                                          _arr(pv), _arr(qv), _arr(Dv), int(r_lo), int(r_hi), dt, batch,
                                          workspace.data_ptr(), workspace.numel() * workspace.element_size(),
@@ -703,6 +745,8 @@ def convnd_host(f, g, h, dims, m, M=None, p=0, q=0, D=0, workspace=None, stream=
     if workspace is None or workspace.numel() * workspace.element_size() < nbytes:
         workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
     st = stream if stream is not None else torch.cuda.current_stream(workspace.device)
+    with torch.cuda.device(workspace.device):
+        _prepare("hdc_prepare", dims, _arr(L), _arr(Mv), *[_arr(a) for a in args], dt, batch)
     _check(lib().hdc_convnd_host(dims, f.data_ptr(), g.data_ptr(), h.data_ptr(), _arr(L), _arr(Mv),
                                  *[_arr(a) for a in args], dt, batch, workspace.data_ptr(),
                                  workspace.numel() * workspace.element_size(), st.cuda_stream), "convnd_host")

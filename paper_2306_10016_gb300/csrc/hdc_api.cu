@@ -25,6 +25,10 @@ static std::atomic<int> g_last_cuda_error{ 0 };
 static int cuda_rc(cudaError_t e)
 {
     if (e == cudaSuccess) return HDC_OK;
+    if (tables_missing()) {
+        tables_missing() = false;
+        return HDC_ERR_NOT_PREPARED;
+    }
     g_last_cuda_error.store((int)e);
     return HDC_ERR_CUDA;
 }
@@ -76,66 +80,89 @@ FftPlan make_fft_plan(int64_t n, bool r16)
 namespace {
 std::mutex g_tw_mu;
 std::map<std::tuple<int, int64_t, int>, void*> g_tw;
+thread_local int t_table_mode = kTablesLookup;
+thread_local bool t_tables_missing = false;
 } // namespace
 
-template <typename T> static const cx<T>* twiddle_table(int64_t n, bool lf, cudaError_t* err)
+TableScope::TableScope(int mode) : saved(t_table_mode) { t_table_mode = mode; }
+TableScope::~TableScope() { t_table_mode = saved; }
+int table_mode() { return t_table_mode; }
+bool& tables_missing() { return t_tables_missing; }
+
+// The cached table under (current device, n, kind), made by `fill` (a
+// launcher writing `count` elements of `esz` bytes on the given stream) when
+// it is missing and the thread's table mode allows it.  A new table is
+// built on a private stream and waited for, so it is complete before any
+// stream of the caller can read it.  In lookup mode a missing table sets
+// tables_missing() and fails (cudaErrorInvalidResourceHandle).
+template <class Fill>
+static void* cached_table(int64_t n, int kind, size_t bytes, Fill fill, cudaError_t* err)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) { *err = e; return nullptr; }
-    const int dt = (sizeof(T) == 8 ? 1 : 0) + (lf ? 2 : 0);
     std::lock_guard<std::mutex> lk(g_tw_mu);
-    auto key = std::make_tuple(dev, n, dt);
+    auto key = std::make_tuple(dev, n, kind);
     auto it = g_tw.find(key);
-    if (it != g_tw.end()) return reinterpret_cast<const cx<T>*>(it->second);
+    if (it != g_tw.end()) return it->second;
+    if (t_table_mode == kTablesLookup) {
+        t_tables_missing = true;
+        *err = cudaErrorInvalidResourceHandle;
+        return nullptr;
+    }
     void* p = nullptr;
-    e = cudaMalloc(&p, (size_t)n * sizeof(cx<T>));
+    e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) { *err = e; return nullptr; }
-    // built on a private stream and waited for, so the table is complete
-    // before any stream of the caller can read it
     cudaStream_t s;
     e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e == cudaSuccess) {
-        e = lf ? launch_twiddle_lf<T>(reinterpret_cast<cx<T>*>(p), n, s)
-               : launch_twiddle<T>(reinterpret_cast<cx<T>*>(p), n, s);
+        e = fill(p, s);
         cudaError_t e2 = cudaStreamSynchronize(s);
         if (e == cudaSuccess) e = e2;
         cudaStreamDestroy(s);
     }
     if (e != cudaSuccess) { cudaFree(p); *err = e; return nullptr; }
     g_tw[key] = p;
-    return reinterpret_cast<const cx<T>*>(p);
+    return p;
+}
+
+// A 256 MiB device buffer per device that the tuners overwrite before each
+// timed replay to evict the 129 MB L2 (kept with the tables, freed by
+// hdc_release_caches); null if it cannot be made.
+void* tuning_flush_buffer(size_t* bytes)
+{
+    constexpr size_t kFlush = (size_t)256 << 20;
+    cudaError_t e = cudaSuccess;
+    void* p = cached_table(
+        (int64_t)kFlush, -2, kFlush, [&](void* q, cudaStream_t s) { return cudaMemsetAsync(q, 0, kFlush, s); }, &e);
+    *bytes = kFlush;
+    return p;
+}
+
+template <typename T> static const cx<T>* twiddle_table(int64_t n, bool lf, cudaError_t* err)
+{
+    const int kind = (sizeof(T) == 8 ? 1 : 0) + (lf ? 2 : 0);
+    return reinterpret_cast<const cx<T>*>(cached_table(
+        n, kind, (size_t)n * sizeof(cx<T>),
+        [&](void* p, cudaStream_t s) {
+            return lf ? launch_twiddle_lf<T>(reinterpret_cast<cx<T>*>(p), n, s)
+                      : launch_twiddle<T>(reinterpret_cast<cx<T>*>(p), n, s);
+        },
+        err));
 }
 
 // Packed per-stage twiddle tables of the n-point transform (FftPlan), plain
 // or twiddle-merged form; cached like the full tables.
 template <typename T> const cx<T>* twiddles_fft(int64_t n, bool lf, cudaError_t* err, bool r16ok)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) { *err = e; return nullptr; }
     // two plans of one size differ at most in their radix-16 stages, which
     // the key tells apart
     const FftPlan fp = fft_plan<T>(n, r16ok);
-    const int dt = (sizeof(T) == 8 ? 1 : 0) + (lf ? 2 : 0) + 4 + (fp.nst > 0 && fp.rad[0] == 16 ? 8 : 0);
-    std::lock_guard<std::mutex> lk(g_tw_mu);
-    auto key = std::make_tuple(dev, n, dt);
-    auto it = g_tw.find(key);
-    if (it != g_tw.end()) return reinterpret_cast<const cx<T>*>(it->second);
-    void* p = nullptr;
-    e = cudaMalloc(&p, (size_t)fp.tlen * sizeof(cx<T>));
-    if (e != cudaSuccess) { *err = e; return nullptr; }
-    cudaStream_t s;
-    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-    if (e == cudaSuccess) {
-        e = launch_twiddle_fft_into<T>(reinterpret_cast<cx<T>*>(p), fp, lf, s);
-        cudaError_t e2 = cudaStreamSynchronize(s);
-        if (e == cudaSuccess) e = e2;
-        cudaStreamDestroy(s);
-    }
-    if (e != cudaSuccess) { cudaFree(p); *err = e; return nullptr; }
-    g_tw[key] = p;
-    return reinterpret_cast<const cx<T>*>(p);
+    const int kind = (sizeof(T) == 8 ? 1 : 0) + (lf ? 2 : 0) + 4 + (fp.nst > 0 && fp.rad[0] == 16 ? 8 : 0);
+    return reinterpret_cast<const cx<T>*>(cached_table(
+        n, kind, (size_t)fp.tlen * sizeof(cx<T>),
+        [&](void* p, cudaStream_t s) { return launch_twiddle_fft_into<T>(reinterpret_cast<cx<T>*>(p), fp, lf, s); },
+        err));
 }
 template const cx<double>* twiddles_fft<double>(int64_t, bool, cudaError_t*, bool);
 template const cx<float>* twiddles_fft<float>(int64_t, bool, cudaError_t*, bool);
@@ -147,29 +174,13 @@ constexpr int64_t kTwFullMax = (int64_t)1 << 16;
 template <typename T> static const cx<T>* strided_table(int64_t count, int64_t N, int64_t stride, int kind,
                                                         cudaError_t* err)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) { *err = e; return nullptr; }
     // kinds 8 / 16 + dtype: the lo / hi table of N; the key's size field is N
-    const int dt = (sizeof(T) == 8 ? 1 : 0) + kind;
-    std::lock_guard<std::mutex> lk(g_tw_mu);
-    auto key = std::make_tuple(dev, N, dt);
-    auto it = g_tw.find(key);
-    if (it != g_tw.end()) return reinterpret_cast<const cx<T>*>(it->second);
-    void* p = nullptr;
-    e = cudaMalloc(&p, (size_t)count * sizeof(cx<T>));
-    if (e != cudaSuccess) { *err = e; return nullptr; }
-    cudaStream_t s;
-    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-    if (e == cudaSuccess) {
-        e = launch_twiddle_strided<T>(reinterpret_cast<cx<T>*>(p), count, N, stride, s);
-        cudaError_t e2 = cudaStreamSynchronize(s);
-        if (e == cudaSuccess) e = e2;
-        cudaStreamDestroy(s);
-    }
-    if (e != cudaSuccess) { cudaFree(p); *err = e; return nullptr; }
-    g_tw[key] = p;
-    return reinterpret_cast<const cx<T>*>(p);
+    return reinterpret_cast<const cx<T>*>(cached_table(
+        N, (sizeof(T) == 8 ? 1 : 0) + kind, (size_t)count * sizeof(cx<T>),
+        [&](void* p, cudaStream_t s) {
+            return launch_twiddle_strided<T>(reinterpret_cast<cx<T>*>(p), count, N, stride, s);
+        },
+        err));
 }
 
 template <typename T> TwTab<cx<T>> tw_table(int64_t N, cudaError_t* err)
@@ -193,29 +204,11 @@ template <typename T> TwTab<cx<T>> tw_table(int64_t N, cudaError_t* err)
 // The column-major four-step twiddles of an ma x Cn split (cached per pair).
 template <typename T> const cx<T>* twiddles_colmajor(int64_t ma, int64_t Cn, cudaError_t* err)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) { *err = e; return nullptr; }
     // kind 32 + dtype, with ma folded into the kind so the key is (ma, Cn)
-    const int dt = (sizeof(T) == 8 ? 1 : 0) + 32 + (int)ma * 64;
-    std::lock_guard<std::mutex> lk(g_tw_mu);
-    auto key = std::make_tuple(dev, Cn, dt);
-    auto it = g_tw.find(key);
-    if (it != g_tw.end()) return reinterpret_cast<const cx<T>*>(it->second);
-    void* p = nullptr;
-    e = cudaMalloc(&p, (size_t)(ma * Cn) * sizeof(cx<T>));
-    if (e != cudaSuccess) { *err = e; return nullptr; }
-    cudaStream_t s;
-    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-    if (e == cudaSuccess) {
-        e = launch_twiddle_colmajor<T>(reinterpret_cast<cx<T>*>(p), ma, Cn, s);
-        cudaError_t e2 = cudaStreamSynchronize(s);
-        if (e == cudaSuccess) e = e2;
-        cudaStreamDestroy(s);
-    }
-    if (e != cudaSuccess) { cudaFree(p); *err = e; return nullptr; }
-    g_tw[key] = p;
-    return reinterpret_cast<const cx<T>*>(p);
+    return reinterpret_cast<const cx<T>*>(cached_table(
+        Cn, (sizeof(T) == 8 ? 1 : 0) + 32 + (int)ma * 64, (size_t)(ma * Cn) * sizeof(cx<T>),
+        [&](void* p, cudaStream_t s) { return launch_twiddle_colmajor<T>(reinterpret_cast<cx<T>*>(p), ma, Cn, s); },
+        err));
 }
 template const cx<double>* twiddles_colmajor<double>(int64_t, int64_t, cudaError_t*);
 template const cx<float>* twiddles_colmajor<float>(int64_t, int64_t, cudaError_t*);
@@ -670,13 +663,13 @@ static int conv_nd_real(int dims, const void* f, const void* g, void* h, const A
 {
     using V = cx<T>;
     const size_t need = ws_bytes_real(dims, ax, B, sizeof(V));
-    if (ws == nullptr || ws_bytes_given < need) return HDC_ERR_WORKSPACE;
+    if (!preparing() && (ws == nullptr || ws_bytes_given < need)) return HDC_ERR_WORKSPACE;
     int64_t tot = B;
     for (int i = 0; i < dims; ++i) tot *= ax[i].L;
     uintptr_t base = ((uintptr_t)ws + 255) & ~(uintptr_t)255;
     V* z = (V*)base;
     V* w = (V*)(base + align_up((size_t)tot * sizeof(V)));
-    if (launch_pack_real<T>((const T*)f, (const T*)g, z, tot, st) != cudaSuccess) return HDC_ERR_CUDA;
+    if (!preparing() && launch_pack_real<T>((const T*)f, (const T*)g, z, tot, st) != cudaSuccess) return HDC_ERR_CUDA;
     cudaError_t e = run_nd_real<T>(dims, z, (T*)h, B, ax, w, st);
     return cuda_rc(e);
 }
@@ -697,18 +690,18 @@ static int conv_nd(int dims, const void* f, const void* g, void* h, const Axis* 
     if ((af || ag) && (!inplace || !same_shape)) return HDC_ERR_PARAM;
     const int ncopy = (int)af + (int)(ag && g != f);
     const size_t need = ws_bytes(dims, ax, B, sizeof(V), ncopy);
-    if (ws == nullptr || ws_bytes_given < need) return HDC_ERR_WORKSPACE;
+    if (!preparing() && (ws == nullptr || ws_bytes_given < need)) return HDC_ERR_WORKSPACE;
     uintptr_t base = ((uintptr_t)ws + 255) & ~(uintptr_t)255;
     const V* fin = (const V*)f;
     const V* gin = (const V*)g;
     const size_t arr = (size_t)(B * tot) * sizeof(V);
-    if (af) {
+    if (af && !preparing()) {
         if (cudaMemcpyAsync((void*)base, f, arr, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return HDC_ERR_CUDA;
         fin = (const V*)base;
         if (g == f) gin = fin;
         base += align_up(arr);
     }
-    if (ag && g != f) {
+    if (ag && g != f && !preparing()) {
         if (cudaMemcpyAsync((void*)base, g, arr, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return HDC_ERR_CUDA;
         gin = (const V*)base;
         base += align_up(arr);
@@ -730,7 +723,7 @@ static int conv_nd_multi(int dims, int n, int op, const void* const* xs, void* h
 {
     using V = cx<T>;
     const size_t need = ws_bytes(dims, ax, B, sizeof(V), 0, n);
-    if (ws == nullptr || ws_bytes_given < need) return HDC_ERR_WORKSPACE;
+    if (!preparing() && (ws == nullptr || ws_bytes_given < need)) return HDC_ERR_WORKSPACE;
     uintptr_t base = ((uintptr_t)ws + 255) & ~(uintptr_t)255;
     Ins<T> in;
     in.n = n;
@@ -816,6 +809,7 @@ HDC_EXPORT const char* hdc_strerror(int status)
     case HDC_ERR_TIMEOUT: return "device wait timed out";
     case HDC_ERR_NOT_TUNED: return "no tuning record or predictor for this request";
     case HDC_ERR_WORKSPACE: return "workspace missing or too small";
+    case HDC_ERR_NOT_PREPARED: return "twiddle tables not made for this problem: call hdc_prepare* or create a plan first";
     default: return "unknown status";
     }
 }
@@ -1210,6 +1204,111 @@ HDC_EXPORT int hdc_convnd_real(int dims, const void* f, const void* g, void* h, 
     cudaStream_t st = (cudaStream_t)stream;
     if (dtype == HDC_C128) return conv_nd_real<double>(dims, f, g, h, ax, batch, workspace, ws_bytes_given, st);
     return conv_nd_real<float>(dims, f, g, h, ax, batch, workspace, ws_bytes_given, st);
+}
+
+// ------------------------------------------------------------ preparation
+// Each hdc_prepare* walks the drivers of its convolution call in the
+// kTablesPrepare mode: every launcher fetches (and so makes) the tables it
+// reads and returns before launching.  The data pointers of that walk are
+// distinct stand-in addresses that nothing reads or writes.
+
+static const void* no_data(int k) { return reinterpret_cast<const void*>(((uintptr_t)1 << 40) + ((uintptr_t)k << 20)); }
+
+template <class Run> static int prepare_walk(Run run)
+{
+    TableScope ts(kTablesPrepare);
+    tables_missing() = false;
+    const int rc = run();
+    tables_missing() = false;
+    return rc;
+}
+
+HDC_EXPORT int hdc_prepare(int dims, const int64_t* L, const int64_t* M, const int64_t* m, const int64_t* p,
+                           const int64_t* q, const int64_t* D, int dtype, int64_t batch)
+{
+    Axis ax[HDC_MAX_DIMS];
+    int rc = resolve_all(dims, L, M, m, p, q, D, dtype, ax);
+    if (rc != HDC_OK) return rc;
+    if (batch < 0) return HDC_ERR_PARAM;
+    if (batch == 0) return HDC_OK;
+    return prepare_walk([&]() {
+        return dtype == HDC_C128
+                   ? conv_nd<double>(dims, no_data(0), no_data(1), (void*)no_data(2), ax, 0, batch, (void*)no_data(9), 0, nullptr)
+                   : conv_nd<float>(dims, no_data(0), no_data(1), (void*)no_data(2), ax, 0, batch, (void*)no_data(9), 0, nullptr);
+    });
+}
+
+HDC_EXPORT int hdc_prepare_window(int dims, const int64_t* L, const int64_t* M, const int64_t* m, const int64_t* p,
+                                  const int64_t* q, const int64_t* D, const int64_t* o, const int64_t* Lw, int dtype,
+                                  int64_t batch)
+{
+    if (!o || !Lw) return HDC_ERR_PARAM;
+    Axis ax[HDC_MAX_DIMS];
+    int rc = resolve_all(dims, L, M, m, p, q, D, dtype, ax, o, Lw);
+    if (rc != HDC_OK) return rc;
+    if (batch < 0) return HDC_ERR_PARAM;
+    if (batch == 0) return HDC_OK;
+    return prepare_walk([&]() {
+        return dtype == HDC_C128
+                   ? conv_nd<double>(dims, no_data(0), no_data(1), (void*)no_data(2), ax, 0, batch, (void*)no_data(9), 0, nullptr)
+                   : conv_nd<float>(dims, no_data(0), no_data(1), (void*)no_data(2), ax, 0, batch, (void*)no_data(9), 0, nullptr);
+    });
+}
+
+HDC_EXPORT int hdc_prepare_hermitian(int64_t K, const int64_t* m, const int64_t* D, int dtype, int64_t batch)
+{
+    if (K < 1 || !m) return HDC_ERR_PARAM;
+    int64_t L[2], M[2], o[2], Lw[2];
+    hermitian_axes(K, L, M, o, Lw);
+    return hdc_prepare_window(2, L, M, m, nullptr, nullptr, D, o, Lw, dtype, batch);
+}
+
+HDC_EXPORT int hdc_prepare_unequal(int dims, const int64_t* Lf, const int64_t* Lg, const int64_t* M, const int64_t* m,
+                                   const int64_t* lam, const int64_t* D, const int64_t* o, const int64_t* Lw, int dtype,
+                                   int64_t batch)
+{
+    Axis ax[HDC_MAX_DIMS];
+    int rc = resolve_all_uneq(dims, Lf, Lg, M, m, lam, D, o, Lw, dtype, ax);
+    if (rc != HDC_OK) return rc;
+    if (batch < 0) return HDC_ERR_PARAM;
+    if (batch == 0) return HDC_OK;
+    return prepare_walk([&]() {
+        return dtype == HDC_C128
+                   ? conv_nd<double>(dims, no_data(0), no_data(1), (void*)no_data(2), ax, 0, batch, (void*)no_data(9), 0, nullptr)
+                   : conv_nd<float>(dims, no_data(0), no_data(1), (void*)no_data(2), ax, 0, batch, (void*)no_data(9), 0, nullptr);
+    });
+}
+
+HDC_EXPORT int hdc_prepare_multi(int dims, int n, int op, const int64_t* L, const int64_t* M, const int64_t* m,
+                                 const int64_t* p, const int64_t* q, const int64_t* D, int dtype, int64_t batch)
+{
+    Axis ax[HDC_MAX_DIMS];
+    int rc = resolve_all_multi(dims, n, op, L, M, m, p, q, D, dtype, ax);
+    if (rc != HDC_OK) return rc;
+    if (batch < 0) return HDC_ERR_PARAM;
+    if (batch == 0) return HDC_OK;
+    const void* xs[kMaxInputs];
+    for (int i = 0; i < n; ++i) xs[i] = no_data(i);
+    return prepare_walk([&]() {
+        return dtype == HDC_C128
+                   ? conv_nd_multi<double>(dims, n, op, xs, (void*)no_data(kMaxInputs), ax, batch, (void*)no_data(9), 0, nullptr)
+                   : conv_nd_multi<float>(dims, n, op, xs, (void*)no_data(kMaxInputs), ax, batch, (void*)no_data(9), 0, nullptr);
+    });
+}
+
+HDC_EXPORT int hdc_prepare_real(int dims, const int64_t* L, const int64_t* M, const int64_t* m, const int64_t* p,
+                                const int64_t* q, const int64_t* D, int dtype, int64_t batch)
+{
+    Axis ax[HDC_MAX_DIMS];
+    int rc = resolve_all(dims, L, M, m, p, q, D, dtype, ax);
+    if (rc != HDC_OK) return rc;
+    if (batch < 0) return HDC_ERR_PARAM;
+    if (batch == 0) return HDC_OK;
+    return prepare_walk([&]() {
+        return dtype == HDC_C128
+                   ? conv_nd_real<double>(dims, no_data(0), no_data(1), (void*)no_data(2), ax, batch, (void*)no_data(9), 0, nullptr)
+                   : conv_nd_real<float>(dims, no_data(0), no_data(1), (void*)no_data(2), ax, batch, (void*)no_data(9), 0, nullptr);
+    });
 }
 
 HDC_EXPORT int hdc_release_caches(void)

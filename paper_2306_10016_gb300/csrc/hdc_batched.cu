@@ -228,6 +228,8 @@ void free_plan(hdc_batched* b)
 template <typename T> int build(hdc_batched* b)
 {
     using V = cx<T>;
+    // creating a batched plan makes the twiddle tables its kernel reads
+    TableScope tables(kTablesCreate);
     std::vector<BConv<V>> convs((size_t)b->n);
     std::vector<BItem> items[4];
     std::vector<std::pair<double, int64_t>> cost;

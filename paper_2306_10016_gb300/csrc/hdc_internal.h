@@ -60,6 +60,34 @@ inline bool rows_r16(int64_t n) { return n >= 16 * (int64_t)kMaxThreads; }
 template <class V> constexpr bool kHas16 = sizeof(V) == 8;
 template <class V> inline bool takes_r16(const FftPlan& fp) { return kHas16<V> && fp.nst > 0 && fp.rad[0] == 16; }
 
+// ------------------------------------------------------- twiddle tables
+// The convolution entry points only look their twiddle tables up: a missing
+// table makes the call return HDC_ERR_NOT_PREPARED before anything is
+// launched, so no convolution call allocates device memory or synchronises.
+// The preparation calls (hdc_prepare*, plan creation, the tuners, batched
+// plans) make the missing tables.  The mode belongs to the calling host
+// thread; a TableScope sets it for its lifetime (scopes nest).
+enum TableMode {
+    kTablesLookup = 0,  // look up only (the default)
+    kTablesCreate = 1,  // make missing tables, then launch as usual
+    kTablesPrepare = 2  // make missing tables and launch nothing: the walk of
+                        // a call by hdc_prepare*, whose launchers return right
+                        // after fetching their tables (no pointer is read)
+};
+struct TableScope {
+    int saved;
+    explicit TableScope(int mode);
+    ~TableScope();
+};
+int table_mode();
+inline bool preparing() { return table_mode() == kTablesPrepare; }
+// Set when a lookup finds no table (turned into HDC_ERR_NOT_PREPARED by the
+// entry point, which clears it).
+bool& tables_missing();
+// 256 MiB a tuner writes before each timed replay to evict L2 (made on first
+// use in a table-making mode, like a table); *bytes gets its size.
+void* tuning_flush_buffer(size_t* bytes);
+
 // ------------------------------------------------------ launch statistics
 // Every launcher counts its launches and the model flops / algorithmic
 // bytes of the launch; when timing is on it also brackets the launch with

@@ -186,6 +186,7 @@ cudaError_t launch_residue_rows(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_
     const double Lrow = (double)((L < p * m) ? L : p * m);
     const double Lfrow = (double)((Lf < p * m) ? Lf : p * m);
     const double fold = (p == 1 && q == 1 && Lf == L) ? 0.0 : 8.0 * (Lrow + Lfrow);
+    if (preparing()) return cudaSuccess;
     LaunchScope ls(K_RESIDUE_ROWS, st, (double)(B * Dg) * (3.0 * fft_flops((double)m) + 6.0 * m + fold),
                    (B * (Lrow + Lfrow) + (double)(Dg * B * m)) * sizeof(V));
     kern<<<(unsigned)blocks, thr, smem, st>>>(f, g, h, B, ld_f, ld_g, Lf, L, (int)m, (int)p, (int)q, (int)r0,
@@ -239,6 +240,7 @@ cudaError_t launch_residue_rows_lam(const cx<T>* f, const cx<T>* g, cx<T>* h, in
     // lam mf products, and the folds (8 flops per valid element per residue)
     const double Lgr = (double)((Lg < pg * mg) ? Lg : pg * mg);
     const double Lfr = (double)((Lf < pf * mf) ? Lf : pf * mf);
+    if (preparing()) return cudaSuccess;
     LaunchScope ls(K_RESIDUE_ROWS, st,
                    (double)(B * Dg) * (2.0 * fft_flops((double)mg) + lam * fft_flops((double)mf) + 6.0 * mg +
                                        8.0 * (Lgr + lam * Lfr)),
@@ -290,6 +292,7 @@ cudaError_t launch_residue_rows_multi(const cx<T>* const* xs, int nin, int op, c
     const double Lrow = (double)((L < p * m) ? L : p * m);
     const double fold = (p == 1 && q == 1) ? 0.0 : 8.0 * nin * Lrow;
     const double pointwise = op == 0 ? 6.0 * (nin - 1) * m : (6.0 * (nin / 2) + 2.0 * (nin / 2 - 1)) * m;
+    if (preparing()) return cudaSuccess;
     LaunchScope ls(K_RESIDUE_ROWS, st, (double)(B * Dg) * ((nin + 1.0) * fft_flops((double)m) + pointwise + fold),
                    (nin * B * Lrow + (double)(Dg * B * m)) * sizeof(V));
     kern<<<(unsigned)blocks, thr, smem, st>>>(in, nin, op, h, B, ld, L, (int)m, (int)p, (int)q, (int)r0, (int)Dg,
@@ -611,6 +614,7 @@ cudaError_t launch_fold_fft_cols(const ColSide<T>* sides, int nside, int64_t B, 
         }
     }
     const int64_t blocks = (int64_t)nct * Dg * sides[0].lam * nside * B;
+    if (preparing()) return cudaSuccess; // the walk of hdc_prepare*: tables made, nothing launched
     ColMapsK maps;
     memset(&maps, 0, sizeof maps);
     const int tma_rows = g_fold_tma ? make_fold_maps<V>(&maps, k, nside, B, Cn, ma, C) : 0;
@@ -669,6 +673,7 @@ cudaError_t launch_ifft_cols(cx<T>* y, int64_t B, int64_t Cn, int64_t ma, int64_
     auto kern = takes_r16<V>(fp) ? k_ifft_cols<V, kHas16<V>> : k_ifft_cols<V, false>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     const int64_t blocks = (int64_t)nct * D * B;
+    if (preparing()) return cudaSuccess;
     LaunchScope ls(K_IFFT_COLS, st, (double)(D * B) * (double)Cn * fft_flops((double)ma),
                    2.0 * D * B * ma * Cn * sizeof(V));
     kern<<<(unsigned)blocks, thr, smem, st>>>(y, B, Cn, (int)ma, (int)q, Nf, (int)D, C, nct, pre, twNf,
@@ -710,6 +715,7 @@ cudaError_t launch_unfold(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstride
     const int64_t total = ma * Cn * B;
     const int64_t blocks = (total + thr - 1) / thr;
     const double nout = (double)(hi - lo);
+    if (preparing()) return cudaSuccess;
     LaunchScope ls(K_UNFOLD, st, (double)(Dg * B) * 8.0 * nout + (last ? 2.0 * B * nout : 0.0),
                    ((double)(Dg * B * ma * Cn) + (first ? 1.0 : 2.0) * B * nout) * sizeof(V));
     k_unfold<V, 4><<<(unsigned)blocks, thr, 0, st>>>(out, h, B, bstride, Cn, ma, (int)p, (int)q, Nf,
@@ -771,6 +777,7 @@ cudaError_t launch_ifft_unfold(cx<T>* y, cx<T>* out, int64_t B, int64_t bstride,
     auto kern = takes_r16<V>(fp) ? k_ifft_unfold_cols<V, kHas16<V>> : k_ifft_unfold_cols<V, false>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     const double nout = (double)(hi - lo);
+    if (preparing()) return cudaSuccess;
     LaunchScope ls(K_IFFT_UNFOLD, st,
                    (double)(Dg * B) * ((double)Cn * fft_flops((double)ma) + 8.0 * nout) + (last ? 2.0 * B * nout : 0.0),
                    ((double)(Dg * B * ma * Cn) + (first ? 1.0 : 2.0) * B * nout) * sizeof(V));
@@ -792,6 +799,7 @@ template <typename T> cudaError_t launch_pack_real(const T* f, const T* g, cx<T>
 {
     if (n <= 0) return cudaSuccess;
     const int thr = 256;
+    if (preparing()) return cudaSuccess;
     LaunchScope ls(K_UNFOLD, st, 0.0, (double)n * (2.0 * sizeof(T) + sizeof(cx<T>)));
     k_pack_real<T><<<(unsigned)((n + thr - 1) / thr), thr, 0, st>>>(f, g, z, n);
     return cudaGetLastError();
@@ -830,6 +838,7 @@ cudaError_t launch_residue_rows_real(const cx<T>* z, cx<T>* h, int64_t B, int64_
     // model per kept residue: two forward FFTs (one when self-paired, counted
     // as two), one inverse, the pair product, the folds of z
     const double Lrow = (double)((L < p * m) ? L : p * m);
+    if (preparing()) return cudaSuccess;
     LaunchScope ls(K_RESIDUE_ROWS, st, (double)(B * Dg) * (3.0 * fft_flops((double)m) + 14.0 * m + 16.0 * Lrow),
                    (B * Lrow + (double)(Dg * B * m)) * sizeof(V));
     kern<<<(unsigned)(B * Dg), thr, smem, st>>>(z, h, B, ld, L, (int)m, (int)p, (int)q, (int)r0, twN, twm, twml, fp);
@@ -877,6 +886,7 @@ cudaError_t launch_rows_real_pair(const cx<T>* ya, const cx<T>* yb, cx<T>* yh, i
     auto kern = k_rows_real_pair<V>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     const int64_t rows = Dg * B * m1;
+    if (preparing()) return cudaSuccess;
     LaunchScope ls(K_RESIDUE_ROWS, st, (double)rows * (3.0 * fft_flops((double)m2) + 14.0 * m2),
                    3.0 * rows * m2 * sizeof(V));
     kern<<<(unsigned)rows, thr, smem, st>>>(ya, yb, yh, B, (int)m1, (int)m2, (int)q, (int)r0, twm, twml, fp);
@@ -918,6 +928,7 @@ cudaError_t launch_pair_rows_real(const cx<T>* wa, const cx<T>* wb, cx<T>* wf, c
     const int64_t n = Dg * B * m0 * Cn;
     if (n <= 0) return cudaSuccess;
     const int thr = 256;
+    if (preparing()) return cudaSuccess;
     LaunchScope ls(K_UNFOLD, st, 8.0 * n, 4.0 * n * sizeof(cx<T>));
     k_pair_rows_real<cx<T>><<<(unsigned)((n + thr - 1) / thr), thr, 0, st>>>(wa, wb, wf, wg, B, Cn, (int)m0, (int)q,
                                                                            (int)r0, (int)Dg);
@@ -981,6 +992,7 @@ cudaError_t launch_unfold_real(T* out, const cx<T>* h, int64_t B, int64_t bstrid
     const int thr = 256;
     const int64_t total = ma * Cn * B;
     const double nout = (double)(hi - lo);
+    if (preparing()) return cudaSuccess;
     LaunchScope ls(K_UNFOLD, st, (double)(Dg * B) * 8.0 * nout,
                    ((double)(Dg * B * ma * Cn) * sizeof(V) + (first ? 1.0 : 2.0) * B * nout * sizeof(T)));
     k_unfold_real<V><<<(unsigned)((total + thr - 1) / thr), thr, 0, st>>>(out, h, B, bstride, Cn, ma, (int)p, (int)q,
@@ -1121,6 +1133,7 @@ cudaError_t launch_residue_rows_tw(const cx<T>* f, const cx<T>* g, cx<T>* h, int
     const int64_t blocks = B * Dg;
     const double Lrow = (double)((L < p * m) ? L : p * m);
     const double fold = (p == 1 && q == 1) ? 0.0 : 16.0 * Lrow;
+    if (preparing()) return cudaSuccess;
     LaunchScope ls(K_RESIDUE_ROWS, st, (double)(B * Dg) * (3.0 * fft_flops((double)m) + 6.0 * m + fold),
                    (2.0 * B * Lrow + (double)(Dg * B * m)) * sizeof(V));
     kern<<<(unsigned)blocks, thr, smem, st>>>(f, g, h, B, ld_in, ld_in, L, L, (int)m, (int)p, (int)q, (int)r0,
@@ -1140,6 +1153,7 @@ cudaError_t launch_unfold_tw(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstr
     const int thr = 256;
     const int64_t total = ma * Cn * B;
     const int64_t blocks = (total + thr - 1) / thr;
+    if (preparing()) return cudaSuccess;
     LaunchScope ls(K_UNFOLD, st, (double)(Dg * B) * 8.0 * Lvalid + (last ? 2.0 * B * Lvalid : 0.0),
                    ((double)(Dg * B * ma * Cn) + (first ? 1.0 : 2.0) * B * Lvalid) * sizeof(V));
     k_unfold<V, 4><<<(unsigned)blocks, thr, 0, st>>>(out, h, B, bstride, Cn, ma, (int)p, (int)q, Nf, cs, cc,

@@ -9,6 +9,7 @@
 #include <atomic>
 #include <cmath>
 #include <mutex>
+#include <unordered_set>
 #include <vector>
 
 #include "hdc.h"
@@ -29,6 +30,13 @@ KStat g_k[K_COUNT];
 std::atomic<int> g_timing{ 0 };
 std::atomic<int64_t> g_total{ 0 };
 std::vector<cudaEvent_t> g_pool;
+// Events recorded inside a stream capture: an instantiated graph keeps
+// recording them on every replay for as long as it lives, and the library
+// cannot tell when the caller destroys it.  They are therefore never handed
+// out again (a recycled one would be recorded by the graph and by a later
+// launch alike, and both timings would be wrong); they stay allocated until
+// the process exits.
+std::unordered_set<cudaEvent_t> g_captured;
 const char* g_names[K_COUNT] = { "k_twiddle", "k_residue_rows", "k_fold_fft_cols", "k_ifft_cols", "k_unfold",
                                  "k_batched", "k_ifft_unfold_cols", "k_fold_fft_cols_tma" };
 
@@ -37,9 +45,10 @@ const char* g_names[K_COUNT] = { "k_twiddle", "k_residue_rows", "k_fold_fft_cols
 void record(cudaEvent_t e, cudaStream_t st)
 {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive) {
+        g_captured.insert(e);
         cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
-    else
+    } else
         cudaEventRecord(e, st);
 }
 
@@ -89,10 +98,9 @@ HDC_EXPORT int hdc_stats_reset(void)
 {
     std::lock_guard<std::mutex> lk(g_mu);
     for (auto& k : g_k) {
-        for (auto& pr : k.ev) {
-            g_pool.push_back(pr.first);
-            g_pool.push_back(pr.second);
-        }
+        for (auto& pr : k.ev)
+            for (cudaEvent_t e : { pr.first, pr.second })
+                if (!g_captured.count(e)) g_pool.push_back(e);
         k = KStat();
     }
     g_total.store(0);

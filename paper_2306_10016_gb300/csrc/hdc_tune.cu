@@ -92,9 +92,11 @@ std::vector<hdc_tuple> candidates(int64_t L, int64_t M, int dtype, double max_ra
     if (out.empty()) return out;
     best = out[0].model_flops;
     for (auto& t : out) best = std::min(best, t.model_flops);
+    // explicit padding (m = nextgood(M), q = 1) is always a candidate: it is
+    // the path the hybrid choice has to beat, and the search keeps it on ties
     std::vector<hdc_tuple> kept;
     for (auto& t : out)
-        if (t.model_flops <= max_ratio * best) kept.push_back(t);
+        if (t.model_flops <= max_ratio * best || (t.q == 1 && t.m == top)) kept.push_back(t);
     std::sort(kept.begin(), kept.end(),
               [](const hdc_tuple& a, const hdc_tuple& b) { return a.model_flops < b.model_flops; });
     return kept;
@@ -342,21 +344,45 @@ int resolve_M_uneq(int dims, const int64_t* Lf, const int64_t* Lg, const int64_t
     return HDC_OK;
 }
 
-// Median device time (ms) of `reps` calls after `warmup` untimed ones, or
-// < 0 if a call fails.
+// Median device time (ms) of one call, timed the way the throughput
+// measurement times a step: `warmup` eager calls on `st` (they also make the
+// candidate's twiddle tables), then the call captured once in a CUDA graph
+// on a private stream and replayed `reps` times, each replay preceded by a
+// write of a 256 MiB buffer that evicts the 129 MB L2 (outside the events).
+// Eager timing would add the host's launch gaps to small problems and keep
+// their data in L2, which favoured tuples the replayed step then ran slower.
+// call(s) enqueues the convolution on stream s.  < 0 if a call fails.
 template <class CallFn> double median_ms(CallFn call, int warmup, int reps, cudaStream_t st)
 {
+    // a search may allocate: the candidates' twiddle tables are made as the
+    // first call of each one meets them
+    hdc::TableScope tables(hdc::kTablesCreate);
     for (int w = 0; w < warmup; ++w)
-        if (call() != HDC_OK) return -1.0;
-    std::vector<float> ts;
-    cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess) return -1.0;
-    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return -1.0; }
+        if (call(st) != HDC_OK) return -1.0;
+    size_t fbytes = 0;
+    void* flush = hdc::tuning_flush_buffer(&fbytes);
+    if (!flush || cudaStreamSynchronize(st) != cudaSuccess) return -1.0;
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return -1.0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     double res = -1.0;
+    std::vector<float> ts;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const int rc = call(cs);
+        const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+        if (rc != HDC_OK || ec != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) goto done;
+    } else {
+        goto done;
+    }
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) goto done;
+    if (cudaGraphLaunch(exec, cs) != cudaSuccess) goto done;   // the first replay uploads the graph
     for (int r = 0; r < reps; ++r) {
-        cudaEventRecord(e0, st);
-        if (call() != HDC_OK) break;
-        cudaEventRecord(e1, st);
+        if (cudaMemsetAsync(flush, r & 0xff, fbytes, cs) != cudaSuccess) break;
+        cudaEventRecord(e0, cs);
+        if (cudaGraphLaunch(exec, cs) != cudaSuccess) break;
+        cudaEventRecord(e1, cs);
         if (cudaEventSynchronize(e1) != cudaSuccess) break;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
@@ -366,8 +392,14 @@ template <class CallFn> double median_ms(CallFn call, int warmup, int reps, cuda
         std::sort(ts.begin(), ts.end());
         res = ts[ts.size() / 2];
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+done:
+    cudaStreamSynchronize(cs);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    cudaGetLastError();
     return res;
 }
 
@@ -380,8 +412,9 @@ double time_config(int dims, const void* f, const void* g, void* h, const int64_
     for (int i = 0; i < dims; ++i) { m[i] = t[i].m; p[i] = t[i].p; q[i] = t[i].q; D[i] = t[i].D; }
     size_t need = 0;
     if (hdc_workspace_size(dims, L, M, m, p, q, D, dtype, batch, 0, &need) != HDC_OK || need > ws_bytes) return -1.0;
-    return median_ms([&]() { return hdc_convnd(dims, f, g, h, L, M, m, p, q, D, 0, dtype, batch, ws, ws_bytes, st); },
-                     warmup, reps, st);
+    return median_ms(
+        [&](cudaStream_t s) { return hdc_convnd(dims, f, g, h, L, M, m, p, q, D, 0, dtype, batch, ws, ws_bytes, s); },
+        warmup, reps, st);
 }
 
 double time_config_uneq(int dims, const void* f, const void* g, void* h, const int64_t* Lf, const int64_t* Lg,
@@ -395,9 +428,9 @@ double time_config_uneq(int dims, const void* f, const void* g, void* h, const i
         need > ws_bytes)
         return -1.0;
     return median_ms(
-        [&]() {
+        [&](cudaStream_t s) {
             return hdc_convnd_unequal(dims, f, g, h, Lf, Lg, M, m, lam, D, nullptr, nullptr, dtype, batch, ws,
-                                      ws_bytes, st);
+                                      ws_bytes, s);
         },
         warmup, reps, st);
 }
@@ -412,7 +445,9 @@ double time_config_multi(int dims, int n, int op, const void* const* xs, void* h
     if (hdc_workspace_size_multi(dims, n, op, L, M, m, p, q, D, dtype, batch, &need) != HDC_OK || need > ws_bytes)
         return -1.0;
     return median_ms(
-        [&]() { return hdc_convnd_multi(dims, n, op, xs, h, L, M, m, p, q, D, dtype, batch, ws, ws_bytes, st); },
+        [&](cudaStream_t s) {
+            return hdc_convnd_multi(dims, n, op, xs, h, L, M, m, p, q, D, dtype, batch, ws, ws_bytes, s);
+        },
         warmup, reps, st);
 }
 
@@ -425,8 +460,9 @@ double time_config_real(int dims, const void* f, const void* g, void* h, const i
     size_t need = 0;
     if (hdc_workspace_size_real(dims, L, M, m, p, q, D, dtype, batch, &need) != HDC_OK || need > ws_bytes)
         return -1.0;
-    return median_ms([&]() { return hdc_convnd_real(dims, f, g, h, L, M, m, p, q, D, dtype, batch, ws, ws_bytes, st); },
-                     warmup, reps, st);
+    return median_ms(
+        [&](cudaStream_t s) { return hdc_convnd_real(dims, f, g, h, L, M, m, p, q, D, dtype, batch, ws, ws_bytes, s); },
+        warmup, reps, st);
 }
 
 // The separable search of Section 4.2 over per-axis candidate lists c[ax]
@@ -436,6 +472,13 @@ double time_config_real(int dims, const void* f, const void* g, void* h, const i
 // below q.  time(t) is the median ms of the whole call for the tuple array
 // t (< 0: unusable).  trials (cap records of dims tuples) gets every timed
 // configuration, *ntrials their count.
+// Explicit padding (Section 3.1): one residue of the whole padded length.
+bool is_explicit(const hdc_tuple& t) { return t.q == 1; }
+bool is_explicit(const hdc_unequal_tuple& t) { return t.q == 1 && t.lam == 1; }
+// A faster tuple replaces explicit padding only if it is faster by more than
+// this fraction (the spread of the median of replays is below it).
+constexpr double kTieFraction = 0.01;
+
 template <class Tup, class TimeFn>
 int separable_search(int dims, const std::vector<Tup>* c, TimeFn time, Tup* best, Tup* trials, int64_t cap,
                      int64_t* ntrials)
@@ -481,6 +524,13 @@ int separable_search(int dims, const std::vector<Tup>* c, TimeFn time, Tup* best
                 if (ms < bms) { bms = ms; bax = t[ax]; }
             }
         }
+        // ties go to explicit padding
+        for (const auto& tm : timed)
+            if (is_explicit(tm.second) && tm.first <= bms * (1.0 + kTieFraction)) {
+                bax = tm.second;
+                bms = tm.first;
+                break;
+            }
         cur[ax] = bax;
         best_ms = bms;
     }
@@ -843,6 +893,8 @@ HDC_EXPORT int hdc_tune_convnd_proxy(int dims, const int64_t* L, const int64_t* 
 // Search bounds of plans made with HDC_TUNE_EXHAUSTIVE: candidates within
 // 1.5x of the smallest model flops, m >= 16.
 constexpr double kPlanRatio = 1.5;
+// timed replays per candidate (median)
+constexpr int kPlanReps = 5;
 constexpr int64_t kPlanMmin = 16;
 // HDC_TUNE_RANDOM: a quarter of each axis' candidates (at least 3), drawn
 // with this seed; HDC_TUNE_PROXY: the other axes cut to 32 points.
@@ -998,7 +1050,7 @@ static int predict_mlp(int dims, const int64_t* L, const int64_t* M, int dtype, 
             hdc_tuple trial[HDC_MAX_DIMS];
             for (int j = 0; j < dims; ++j) trial[j] = t[j];
             trial[i] = c;
-            const double ms = time_config(dims, bf, bg, bh, L, M, trial, dtype, batch, bw, wsb, 1, 3, st);
+            const double ms = time_config(dims, bf, bg, bh, L, M, trial, dtype, batch, bw, wsb, 1, kPlanReps, st);
             if (timed) ++*timed;
             if (ms >= 0 && (best < 0 || ms < best)) { best = ms; pick = c; }
         }
@@ -1059,7 +1111,7 @@ HDC_EXPORT int hdc_plan_create(hdc_plan** out, int dims, const int64_t* L, const
             }
             cudaMemsetAsync(bf, 0, tot * esz, st);
             cudaMemsetAsync(bg, 0, tot * esz, st);
-            rc = hdc_tune_convnd(dims, L, M, dtype, batch, bf, bg, bh, bw, wsb, 1, 3, kPlanRatio, kPlanMmin, stream, pl.t, nullptr,
+            rc = hdc_tune_convnd(dims, L, M, dtype, batch, bf, bg, bh, bw, wsb, 1, kPlanReps, kPlanRatio, kPlanMmin, stream, pl.t, nullptr,
                                  0, &pl.timed);
             cudaStreamSynchronize(st);
             cudaFree(bf); cudaFree(bg); cudaFree(bh); cudaFree(bw);
@@ -1085,10 +1137,10 @@ HDC_EXPORT int hdc_plan_create(hdc_plan** out, int dims, const int64_t* L, const
             cudaMemsetAsync(bf, 0, tot * esz, st);
             cudaMemsetAsync(bg, 0, tot * esz, st);
             if (mode == HDC_TUNE_RANDOM)
-                rc = hdc_tune_convnd_random(dims, L, M, dtype, batch, bf, bg, bh, bw, wsb, 1, 3, kPlanRatio, kPlanMmin,
+                rc = hdc_tune_convnd_random(dims, L, M, dtype, batch, bf, bg, bh, bw, wsb, 1, kPlanReps, kPlanRatio, kPlanMmin,
                                             0, kPlanSeed, stream, pl.t, nullptr, 0, &pl.timed);
             else
-                rc = hdc_tune_convnd_proxy(dims, L, M, dtype, batch, bf, bg, bh, bw, wsb, 1, 3, kPlanRatio, kPlanMmin,
+                rc = hdc_tune_convnd_proxy(dims, L, M, dtype, batch, bf, bg, bh, bw, wsb, 1, kPlanReps, kPlanRatio, kPlanMmin,
                                            kPlanProxy, stream, pl.t, &pl.timed);
             cudaStreamSynchronize(st);
             cudaFree(bf); cudaFree(bg); cudaFree(bh); cudaFree(bw);
@@ -1106,6 +1158,16 @@ HDC_EXPORT int hdc_plan_create(hdc_plan** out, int dims, const int64_t* L, const
     for (int i = 0; i < dims; ++i) { mm[i] = pl.t[i].m; pp[i] = pl.t[i].p; qq[i] = pl.t[i].q; DD[i] = pl.t[i].D; }
     int rc = hdc_workspace_size(dims, L, M, mm, pp, qq, DD, dtype, batch, 1, &pl.ws);
     if (rc != HDC_OK) return rc;
+    // the tables hdc_plan_execute reads are made here, so executing the plan
+    // allocates nothing (and may be captured in a CUDA graph from the start);
+    // on a host without a CUDA device the plan holds its parameters only
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0) {
+        rc = hdc_prepare(dims, L, M, mm, pp, qq, DD, dtype, batch);
+        if (rc != HDC_OK) return rc;
+    } else {
+        cudaGetLastError();
+    }
     hdc_plan* p = new (std::nothrow) hdc_plan(pl);
     if (!p) return HDC_ERR_ALLOC;
     *out = p;
