@@ -55,11 +55,13 @@ HBM_GBS = _measured_hbm_gbs()
 # 2 flops per FMA: peak = SMs x units x 2 x max SM clock.
 FP64_FMA_PER_CLK = 2
 FP32_FMA_PER_CLK = 128
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# dominant kernel, averaged over its launches in one ncu capture of this
-# sweep's timed steps (eager launches); to be re-taken whenever that kernel
-# changes (and None until then).
-NCU_TRAFFIC_PER_LAUNCH: dict = {"k_residue_rows": 4.442e+07}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) over algorithmic
+# bytes of one launch of the dominant kernel, from one ncu capture of its
+# largest launch in the sweep (L = 2^22: k_residue_rows over 4096 rows of
+# 2048 points; profiles/launches_fp64_sweep.md); the roofline's traffic per
+# launch is this ratio times the step's average algorithmic bytes per launch.
+# To be re-taken whenever that kernel changes (and None until then).
+NCU_DRAM_PER_ALG_BYTE: dict = {"k_residue_rows": 358809344 / 402653184}
 
 
 def _good(n: int) -> bool:
@@ -503,13 +505,14 @@ def main():
 
     # --- per-size hybrid vs explicit (device time, FP64)
     # per size, the tuned and the explicit tuple timed alternately (three
-    # rounds, median), each as graph replays of ten calls after an L2 flush
+    # rounds of 15 graph replays of one call, each after an L2 flush, as the
+    # tuner times its candidates; median)
     per_size = []
     for L, pt, pe, (f, g, h) in zip(sizes, plans64, plans_ex, ins64):
         th, te = [], []
         for _ in range(3):
-            th.append(time_sweep([pt], [(f, g, h)], 3, 1, reps=10)[0])
-            te.append(time_sweep([pe], [(f, g, h)], 3, 1, reps=10)[0])
+            th += time_sweep([pt], [(f, g, h)], 15, 1, reps=1)[2]
+            te += time_sweep([pe], [(f, g, h)], 15, 1, reps=1)[2]
         prm = pt.params[0]
         per_size.append({"L": L, "m": prm["m"], "p": prm["p"], "q": prm["q"], "D": prm["D"],
                          "hybrid_ms": round(statistics.median(th), 5),
@@ -584,6 +587,7 @@ def main():
                 ev.append((e0, e1))
             torch.cuda.synchronize(dev)
             ok = hdc.BatchedPlan.status(wsb) == 0
+            phases = [round(x, 4) for x in hdc.BatchedPlan.phase_ms(wsb)]
             hh = ha.cpu().numpy().astype(np.complex128)
             pending.append((f"batched_{'fp64' if dcode == hdc.HDC_C128 else 'fp32'}_{name}",
                             [hh[offs[i]:offs[i + 1]] for i in sel], "batched", batched_ref))
@@ -592,6 +596,7 @@ def main():
             fl = sum(pp["q"] * (15 * pp["m"] * math.log2(pp["m"]) + 6 * pp["m"] + 24 * pp["L"]) + 2 * pp["L"]
                      for pp in plan.params)
             res[name] = {"value": world * tot / (msb * 1e-3), "ms": round(msb, 4), "status_ok": ok,
+                         "phase_ms_last_replay": phases,
                          "model_tflops": round(fl / (msb * 1e-3) / 1e12, 4)}
             del graph, plan, wsb
         res["convolutions"] = nconv
@@ -975,7 +980,12 @@ def main():
     total_ms = sum(v["ms"] for v in kstats.values())
     roofline = {
         "bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
-        "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC_PER_LAUNCH.get(dom), "kernel": dom,
+        "frac": round(achieved / peak, 4),
+        "traffic": (NCU_DRAM_PER_ALG_BYTE[dom] * d["bytes"] / max(1, d["launches"])
+                    if dom in NCU_DRAM_PER_ALG_BYTE else None),
+        "traffic_basis": "DRAM bytes per algorithmic byte of the kernel's largest sweep launch (one ncu capture, "
+                         "L = 2^22) times the average algorithmic bytes per launch",
+        "kernel": dom,
         "algorithmic_bytes_per_launch": d["bytes"] / max(1, d["launches"]),
         "peak_basis": "152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz (unit counts and max clock)",
         "peak_measured_fma_probe": round(fp64_probe, 4),

@@ -677,7 +677,7 @@ int hdc_batched_tune(int64_t n, const int64_t* L, int dtype,
  * hdc_mlp_q_class(k), outputs [n_q, n_q + 2) score D = q versus D = 1.
  * Parameters: one float vector, per layer W[i][o] (row-major) then b[o].
  * Device memory of the network is library-owned (create/destroy). */
-#define HDC_MLP_FEATURES 8
+#define HDC_MLP_FEATURES 12
 #define HDC_MLP_HIDDEN 64
 typedef struct hdc_mlp hdc_mlp;
 int hdc_mlp_create(hdc_mlp** net, int n_in, int n_hidden, int n_out);
@@ -706,7 +706,11 @@ int hdc_mlp_destroy(hdc_mlp* net);
 int hdc_mlp_num_q_classes(void);
 int64_t hdc_mlp_q_class(int k);
 int hdc_mlp_q_to_class(int64_t q);
-/* HDC_MLP_FEATURES features per axis of a problem (dims x 8 floats). */
+/* HDC_MLP_FEATURES features per axis of a problem (dims x 12 floats): log2 L,
+ * M / L, innermost or not, log2 of the inner and outer extents, dims, dtype,
+ * log2 of all outputs, and for q = 1..4 the padding of q residues of the
+ * smallest good m >= ceil(M / q) (plus 1 where m exceeds an outer axis'
+ * column-tile limit). */
 int hdc_mlp_axis_features(int dims, const int64_t* L, const int64_t* M,
                           int dtype, int64_t batch, float* out);
 /* (m, p, q, D) of one axis from its logits: the most likely residue class
@@ -753,6 +757,18 @@ int hdc_stats_get(int id, int64_t* launches, double* ms, double* flops,
  * (0 when no kernel gave up) in *status after synchronising with the
  * device's current work, and clears it if `clear` is non-zero. */
 int hdc_set_tma(int enable);
+
+/* A 1-D convolution of equal-length inputs with only a few rows (rows x C
+ * at most the SM count) whose m-point residue fits a cluster (m = m1 m2 with
+ * C dividing both) may run whole on thread-block clusters of C = 2..16
+ * blocks: per row one cluster takes every residue from fold to unfold in one
+ * launch, its transforms split over the blocks and transposed through
+ * distributed shared memory, the outputs written once.  Same results as the
+ * other routes.  hdc_set_cluster(mode) for later calls: 0 never, 1 (the
+ * default) for residues of 256 to 1024 points, where it is the faster route,
+ * 2 wherever the residue fits; HDC_ERR_PARAM for another mode.  Not
+ * thread-safe against calls in flight on other host threads. */
+int hdc_set_cluster(int mode);
 int hdc_device_status(int* status, int clear);
 
 /* ------------------------------------------------------------ measurement

@@ -217,6 +217,7 @@ _SIGS += [
     ("hdc_last_cuda_error", C.c_int, []),
     ("hdc_last_cuda_error_name", C.c_char_p, []),
     ("hdc_set_tma", C.c_int, [C.c_int]),
+    ("hdc_set_cluster", C.c_int, [C.c_int]),
     ("hdc_device_status", C.c_int, [C.POINTER(C.c_int), C.c_int]),
     ("hdc_stats_reset", C.c_int, []),
     ("hdc_stats_timing", C.c_int, [C.c_int]),
@@ -1093,7 +1094,7 @@ class BatchedPlan:
 
 # ------------------------------------------------------ learned predictor
 
-MLP_FEATURES = 8
+MLP_FEATURES = 12
 MLP_HIDDEN = 64
 
 
@@ -1157,8 +1158,16 @@ class MLP:
         _check(lib().hdc_mlp_get_grads(self._h, a.ctypes.data_as(C.POINTER(C.c_float))), "mlp_get_grads")
         return a
 
+    def _check_inputs(self, X, *labels):
+        if X.dim() != 2 or X.shape[1] != self.n_in or X.dtype != _torch().float32 or not X.is_contiguous():
+            raise ValueError(f"X must be a contiguous float32 (n, {self.n_in}) tensor")
+        for y in labels:
+            if y.shape != (X.shape[0],) or y.dtype != _torch().int32:
+                raise ValueError("labels must be int32 (n,) tensors")
+
     def forward(self, X, stream=None):
         torch = _torch()
+        self._check_inputs(X)
         out = torch.empty((X.shape[0], self.n_out), dtype=torch.float32, device=X.device)
         st = stream if stream is not None else torch.cuda.current_stream(X.device)
         _check(lib().hdc_mlp_forward(self._h, X.data_ptr(), X.shape[0], out.data_ptr(), st.cuda_stream), "mlp_forward")
@@ -1167,6 +1176,7 @@ class MLP:
     def loss_grad(self, X, yq, yd, loss_out, stream=None):
         """Device tensors: X float32 (n, n_in), yq / yd int32 (n,), loss_out float32 (1,)."""
         torch = _torch()
+        self._check_inputs(X, yq, yd)
         st = stream if stream is not None else torch.cuda.current_stream(X.device)
         _check(lib().hdc_mlp_loss_grad(self._h, X.data_ptr(), yq.data_ptr(), yd.data_ptr(), X.shape[0],
                                        self.n_out - 2, loss_out.data_ptr(), st.cuda_stream), "mlp_loss_grad")
@@ -1194,6 +1204,13 @@ def set_tma(enable: bool) -> None:
     """Allow (default) or forbid the TMA-staged loads of the strided fold
     for later launches; both paths give the same result."""
     _check(lib().hdc_set_tma(int(bool(enable))), "set_tma")
+
+
+def set_cluster(mode) -> None:
+    """hdc_set_cluster: the thread-block-cluster route of short 1-D
+    convolutions never (False / 0), where it is faster (True / 1, the
+    default) or wherever it fits (2); same results either way."""
+    _check(lib().hdc_set_cluster(int(mode)), "hdc_set_cluster")
 
 
 def device_status(clear: bool = True) -> int:

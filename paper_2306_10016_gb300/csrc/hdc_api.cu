@@ -439,6 +439,23 @@ template <typename T> struct Ins {
     int op;
 };
 
+// Whole convolutions on thread-block clusters (launch_conv_cluster) for a
+// few short rows: when B rows of C blocks each leave the GPU's SMs unfilled
+// (B C <= the SM count), the one-block-per-residue routes would run with a
+// handful of blocks, each bound by one SM's FP64 rate.
+template <typename T> static bool use_cluster(const Axis& a, int64_t B)
+{
+    // measured against the split route with L2 evicted before each call: the
+    // cluster route wins for residues of at most 1024 points (the L = 1024
+    // configuration, m = 512: 132 against 190 us) and loses above
+    const int mode = cluster_route_mode();
+    if (mode == 0 || a.m < 256 || (mode == 1 && a.m > 1024)) return false;
+    int C = 0;
+    int64_t m1 = 0, m2 = 0;
+    if (!cluster_shape<T>(a.m, a.pout, &C, &m1, &m2)) return false;
+    return B * C <= (int64_t)sm_count();
+}
+
 // 1-D convolution of B rows (input row strides ld_f for x[0], ld_g for the
 // others, output row stride ldo) along a contiguous axis; outputs
 // [a.o, a.o + a.Lw) of every row.  Residues [r_lo, r_hi) of g only (all:
@@ -452,6 +469,9 @@ static cudaError_t run_rows(const Ins<T>& in, cx<T>* out, int64_t B, int64_t ld_
     if (r_hi < 0) r_hi = a.q;
     const cx<T>* f = in.x[0];
     const cx<T>* g = in.x[1];
+    if (in.n == 2 && a.lam == 1 && a.Lf == a.L && use_cluster<T>(a, B))
+        return launch_conv_cluster<T>(f, g, out, B, ld_f, ld_g, ldo, a.L, a.o, a.o + a.Lw, a.m, a.p, a.q, r_lo, r_hi,
+                                      scale, st);
     int64_t m1 = 0, m2 = 0;
     route(a, B, a.dtype, &m1, &m2);
     if (m1 == 0) {
@@ -1017,32 +1037,72 @@ HDC_EXPORT int hdc_convnd_window(int dims, const void* f, const void* g, void* h
     return conv_nd<float>(dims, f, g, h, ax, 0, batch, workspace, ws_bytes_given, st);
 }
 
-// Centered Hermitian 2-D convolution as a windowed linear convolution of the
-// index-shifted full spectra (shift c = K - 1 per axis): outputs kx in
-// [-c, c] are the window [c, 3c] of axis 0, ky in [0, c] the window [2c, 3c]
-// of axis 1; both alias-free with M = 3K - 2 (the 3/2 padding ratio).
-static void hermitian_axes(int64_t K, int64_t L[2], int64_t M[2], int64_t o[2], int64_t Lw[2])
+// The half-stored route of the centered Hermitian convolution: the outer
+// axis (kx, 2K - 1 points shifted by c, padded to M = 3K - 2, window
+// [c, 3c]) through the residue kernels of the N-D route on the K stored
+// half columns; the inner axis (ky) through launch_hermitian_rows, which
+// transforms the two fields of a row in one packed transform, multiplies the
+// real fields and inverse-transforms a pair of rows at once.
+template <typename T> static int herm_resolve(int64_t K, const int64_t* m, const int64_t* D, int dtype, Axis* ax,
+                                              Axis* ay)
 {
-    const int64_t c = K - 1;
-    L[0] = L[1] = 2 * K - 1;
-    M[0] = M[1] = 3 * K - 2;
-    o[0] = c;
-    o[1] = 2 * c;
-    Lw[0] = 2 * K - 1;
-    Lw[1] = K;
+    const int64_t c = K - 1, L = 2 * K - 1, M = 3 * K - 2;
+    int rc = resolve_axis(L, M, m[0], 0, 0, D ? D[0] : 0, dtype, ax, c, L);
+    if (rc != HDC_OK) return rc;
+    rc = resolve_axis(L, M, m[1], 0, 0, 0, dtype, ay, c, L);
+    if (rc != HDC_OK) return rc;
+    // the outer transform runs in one column tile; the inner one, with both
+    // packed rows and the pair's 2K - 1 outputs, in one block's shared memory
+    if (m[0] > max_col_fft<T>() || m[1] > max_row_fft<T>()) return HDC_ERR_UNSUPPORTED_SIZE;
+    if ((3 * smem_len<cx<T>>(m[1]) + 2 * K - 1) * (int64_t)sizeof(cx<T>) > 200 * 1024)
+        return HDC_ERR_UNSUPPORTED_SIZE;
+    return HDC_OK;
+}
+
+static int herm_resolve_any(int64_t K, const int64_t* m, const int64_t* D, int dtype, Axis* ax, Axis* ay)
+{
+    if (K < 1 || !m) return HDC_ERR_PARAM;
+    if (dtype == HDC_C128) return herm_resolve<double>(K, m, D, dtype, ax, ay);
+    if (dtype == HDC_C64) return herm_resolve<float>(K, m, D, dtype, ax, ay);
+    return HDC_ERR_DTYPE;
+}
+
+static size_t herm_ws_bytes(const Axis& ax, int64_t K, int64_t B, size_t esz)
+{
+    return align_up((size_t)(3 * ax.D * B * ax.m * K) * esz) + 256;
+}
+
+template <typename T>
+static cudaError_t run_hermitian(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t B, int64_t K, const Axis& ax,
+                                 const Axis& ay, cx<T>* ws, cudaStream_t st)
+{
+    const int64_t Cn = K, L = 2 * K - 1;
+    const int64_t rows = ax.D * B * ax.m;
+    cx<T>* wf = ws;
+    cx<T>* wg = wf + rows * Cn;
+    cx<T>* wh = wg + rows * Cn;
+    const double scale = 1.0 / (double)ax.N;
+    for (int64_t r0 = 0; r0 < ax.q; r0 += ax.D) {
+        const int64_t Dg = (ax.D < ax.q - r0) ? ax.D : (ax.q - r0);
+        const int first = (r0 == 0), last = (r0 + Dg >= ax.q);
+        const ColSide<T> sides[2] = { ColSide<T>{ f, wf, L * Cn, L * Cn, (int)ax.p, (int)ax.q, 0, 1 },
+                                      ColSide<T>{ g, wg, L * Cn, L * Cn, (int)ax.p, (int)ax.q, 0, 1 } };
+        HDC_TRY(launch_fold_fft_cols<T>(sides, 2, B, Cn, ax.m, ax.N, 1, 0, r0, Dg, 0, st));
+        HDC_TRY(launch_hermitian_rows<T>(wf, wg, wh, Dg * B, B, ax.m, K, ay.m, ay.p, ay.q, ax.N, ax.q, r0, st));
+        HDC_TRY(launch_ifft_unfold<T>(wh, out, B, L * Cn, Cn, ax.m, ax.pout, ax.q, ax.N, 1, 0, ax.o * Cn,
+                                      (ax.o + ax.Lw) * Cn, r0, Dg, first, last, scale, 0, st));
+    }
+    return cudaSuccess;
 }
 
 HDC_EXPORT int hdc_workspace_size_hermitian(int64_t K, const int64_t* m, const int64_t* D, int dtype, int64_t batch,
                                             size_t* bytes)
 {
-    if (K < 1 || !m || !bytes || batch < 0) return HDC_ERR_PARAM;
-    int64_t L[2], M[2], o[2], Lw[2];
-    hermitian_axes(K, L, M, o, Lw);
-    size_t conv = 0;
-    int rc = hdc_workspace_size_window(2, L, M, m, nullptr, nullptr, D, o, Lw, dtype, batch, &conv);
+    if (!bytes || batch < 0) return HDC_ERR_PARAM;
+    Axis ax, ay;
+    int rc = herm_resolve_any(K, m, D, dtype, &ax, &ay);
     if (rc != HDC_OK) return rc;
-    const size_t esz = dtype == HDC_C128 ? 16 : 8;
-    *bytes = 2 * align_up((size_t)(batch * L[0] * L[1]) * esz) + conv + 256;
+    *bytes = herm_ws_bytes(ax, K, batch, dtype == HDC_C128 ? 16 : 8);
     return HDC_OK;
 }
 
@@ -1050,37 +1110,26 @@ HDC_EXPORT int hdc_conv2d_hermitian(const void* f, const void* g, void* h, int64
                                     const int64_t* D, int dtype, int64_t batch, void* workspace,
                                     size_t ws_bytes_given, void* stream)
 {
-    if (K < 1 || !m) return HDC_ERR_PARAM;
-    int64_t L[2], M[2], o[2], Lw[2];
-    hermitian_axes(K, L, M, o, Lw);
-    Axis ax[2];
-    int rc = resolve_all(2, L, M, m, nullptr, nullptr, D, dtype, ax, o, Lw);
+    Axis ax, ay;
+    int rc = herm_resolve_any(K, m, D, dtype, &ax, &ay);
     if (rc != HDC_OK) return rc;
     if (batch < 0) return HDC_ERR_PARAM;
     if (batch == 0) return HDC_OK;
-    if (!f || !g || !h || h == f || h == g) return HDC_ERR_PARAM;
-    size_t need = 0;
-    rc = hdc_workspace_size_hermitian(K, m, D, dtype, batch, &need);
-    if (rc != HDC_OK) return rc;
-    if (!workspace || ws_bytes_given < need) return HDC_ERR_WORKSPACE;
-    const size_t esz = dtype == HDC_C128 ? 16 : 8;
-    const size_t arr = align_up((size_t)(batch * L[0] * L[1]) * esz);
-    uintptr_t base = ((uintptr_t)workspace + 255) & ~(uintptr_t)255;
-    void* ff = (void*)base;
-    void* gg = (void*)(base + arr);
-    void* w = (void*)(base + 2 * arr);
-    const size_t wbytes = ws_bytes_given - (size_t)((uintptr_t)w - (uintptr_t)workspace);
-    cudaStream_t st = (cudaStream_t)stream;
-    if (dtype == HDC_C128) {
-        if (launch_hermitian_expand<double>((const cx<double>*)f, (cx<double>*)ff, K, batch, st) != cudaSuccess ||
-            launch_hermitian_expand<double>((const cx<double>*)g, (cx<double>*)gg, K, batch, st) != cudaSuccess)
-            return HDC_ERR_CUDA;
-        return conv_nd<double>(2, ff, gg, h, ax, 0, batch, w, wbytes, st);
+    if (!preparing()) {
+        if (!f || !g || !h || h == f || h == g) return HDC_ERR_PARAM;
+        const uintptr_t al = dtype == HDC_C128 ? 15 : 7;
+        if (((uintptr_t)f & al) || ((uintptr_t)g & al) || ((uintptr_t)h & al)) return HDC_ERR_PARAM;
+        if (!workspace || ws_bytes_given < herm_ws_bytes(ax, K, batch, dtype == HDC_C128 ? 16 : 8))
+            return HDC_ERR_WORKSPACE;
     }
-    if (launch_hermitian_expand<float>((const cx<float>*)f, (cx<float>*)ff, K, batch, st) != cudaSuccess ||
-        launch_hermitian_expand<float>((const cx<float>*)g, (cx<float>*)gg, K, batch, st) != cudaSuccess)
-        return HDC_ERR_CUDA;
-    return conv_nd<float>(2, ff, gg, h, ax, 0, batch, w, wbytes, st);
+    uintptr_t base = ((uintptr_t)workspace + 255) & ~(uintptr_t)255;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = dtype == HDC_C128
+                        ? run_hermitian<double>((const cx<double>*)f, (const cx<double>*)g, (cx<double>*)h, batch, K,
+                                                ax, ay, (cx<double>*)base, st)
+                        : run_hermitian<float>((const cx<float>*)f, (const cx<float>*)g, (cx<float>*)h, batch, K, ax,
+                                               ay, (cx<float>*)base, st);
+    return cuda_rc(e);
 }
 
 HDC_EXPORT int hdc_convnd_residues(int dims, const void* f, const void* g, void* h, const int64_t* L,
@@ -1257,10 +1306,15 @@ HDC_EXPORT int hdc_prepare_window(int dims, const int64_t* L, const int64_t* M, 
 
 HDC_EXPORT int hdc_prepare_hermitian(int64_t K, const int64_t* m, const int64_t* D, int dtype, int64_t batch)
 {
-    if (K < 1 || !m) return HDC_ERR_PARAM;
-    int64_t L[2], M[2], o[2], Lw[2];
-    hermitian_axes(K, L, M, o, Lw);
-    return hdc_prepare_window(2, L, M, m, nullptr, nullptr, D, o, Lw, dtype, batch);
+    Axis ax, ay;
+    int rc = herm_resolve_any(K, m, D, dtype, &ax, &ay);
+    if (rc != HDC_OK) return rc;
+    if (batch < 0) return HDC_ERR_PARAM;
+    if (batch == 0) return HDC_OK;
+    return prepare_walk([&]() {
+        return hdc_conv2d_hermitian(no_data(0), no_data(1), (void*)no_data(2), K, m, D, dtype, batch,
+                                    (void*)no_data(9), 0, nullptr);
+    });
 }
 
 HDC_EXPORT int hdc_prepare_unequal(int dims, const int64_t* Lf, const int64_t* Lg, const int64_t* M, const int64_t* m,

@@ -1,0 +1,361 @@
+// hdc_cluster.cu -- whole 1-D convolutions of short rows on a thread-block
+// cluster: every residue's fold, forward transforms, product, inverse
+// transform and unfold run in one launch, with the m-point transforms spread
+// over the cluster's C blocks and exchanged through distributed shared
+// memory, and each output written once at the end.
+//
+// A row's transforms on one block are bound by that SM's FP64 rate (two
+// lanes per clock), so a short convolution on the one-block-per-residue
+// routes takes tens of microseconds however little work it has; spread over
+// C SMs the same work takes about 1/C of that, and nothing goes back to
+// global memory between the steps (Section 2.2, Eq. 1 and Eq. 2: the
+// residues are independent until the unfold sum, which is kept on chip).
+//
+// The m-point DFT of a residue is taken in four steps, m = m1 m2,
+// s = s1 m2 + s2, l = l1 + m1 l2:
+//   W[l1 + m1 l2] = sum_{s2} zeta_{m2}^{l2 s2} zeta_m^{l1 s2} sum_{s1} zeta_{m1}^{l1 s1} w[s1 m2 + s2].
+// Block c of the cluster owns the columns s2 in [c w2, (c+1) w2) (w2 = m2/C)
+// for the fold, the m1-point column transforms, the inverse column
+// transforms and the unfold, and the rows l1 in [c w1, (c+1) w1)
+// (w1 = m1/C) for the m2-point row transforms and the product; the
+// transpose between the two layouts reads the other blocks' tiles with
+// plain loads from their shared memory (no multicast).  Residues run one
+// after another (r increasing, the summation order of the other routes), so
+// the on-chip footprint is one residue's: the paper's D = 1.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <mutex>
+#include <map>
+#include <stdint.h>
+
+#include "hdc.h"
+#include "hdc_fft.cuh"
+#include "hdc_internal.h"
+
+#define HDC_EXPORT extern "C" __attribute__((visibility("default")))
+
+namespace cg = cooperative_groups;
+
+namespace hdc {
+
+// The cluster route (hdc_set_cluster): 0 off, 1 where it is the faster
+// route, 2 wherever the residue fits a cluster.
+static std::atomic<int> g_cluster_route{ 1 };
+int cluster_route_mode() { return g_cluster_route.load(); }
+
+template <class V> struct ClusterArgs {
+    const V* f;
+    const V* g;
+    V* out;
+    int64_t ld_f, ld_g, ldo;  // row strides
+    int64_t L;                // valid input elements per row
+    int64_t lo, hi;           // output window [lo, hi) of each row
+    int m, m1, m2, p, q, pout;
+    int r_lo, r_hi;           // residues [r_lo, r_hi)
+    typename real_of<V>::type scale;
+    TwTab<V> twN;             // zeta_N^k, N = q m
+    const V* tw1;             // stage tables of the m1-point transform
+    const V* tw1l;
+    const V* tw2;             // ... of the m2-point transform
+    const V* tw2l;
+    FftPlan fp1, fp2;
+};
+
+// Shared memory: four tiles of m / C elements (X0, X1: the column tiles of
+// f and g; Y0, Y1: their row tiles) and pout tiles of output accumulators.
+template <class V>
+__global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_constant__ ClusterArgs<V> a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks();
+    const int c = (int)cluster.block_rank();
+    const int64_t b = blockIdx.x / C;
+    const int w1 = a.m1 / C, w2 = a.m2 / C;
+    const int tile = a.m / C;
+    const int tl = (int)smem_len<V>(tile);
+    V* X0 = reinterpret_cast<V*>(smraw);
+    V* X1 = X0 + tl;
+    V* Y0 = X1 + tl;
+    V* Y1 = Y0 + tl;
+    V* acc = Y1 + tl;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const V* fr = a.f + b * a.ld_f;
+    const V* gr = a.g + b * a.ld_g;
+    for (int e = tid; e < a.pout * tile; e += nthr) acc[e] = czero<V>();
+    for (int r = a.r_lo; r < a.r_hi; ++r) {
+        // fold (Eq. 1 inner sum, then zeta_N^{r s}) of f and g into this
+        // block's columns: element (s1, cl) at s1 w2 + cl, s = s1 m2 + c w2 + cl
+        for (int e = tid; e < tile; e += nthr) {
+            const int s1 = e / w2, cl = e - s1 * w2;
+            const int64_t s = (int64_t)s1 * a.m2 + (int64_t)c * w2 + cl;
+            V af = s < a.L ? fr[s] : czero<V>(), ag = s < a.L ? gr[s] : czero<V>();
+            for (int t = 1; t < a.p; ++t) {
+                const int64_t j = (int64_t)t * a.m + s;
+                if (j >= a.L) break;
+                if (r == 0) {
+                    af = cadd(af, fr[j]);
+                    ag = cadd(ag, gr[j]);
+                } else {
+                    const V w = twn(a.twN, (((int64_t)r * t) % a.q) * a.m);
+                    af = cfma(fr[j], w, af);
+                    ag = cfma(gr[j], w, ag);
+                }
+            }
+            if (r != 0) {
+                const V w = twn(a.twN, (int64_t)r * s);
+                af = cmul(af, w);
+                ag = cmul(ag, w);
+            }
+            X0[sidx<V, true>(e)] = af;
+            X1[sidx<V, true>(e)] = ag;
+        }
+        __syncthreads();
+        // m1-point transforms of the w2 columns (Y1 as the scratch half: no
+        // other block reads it)
+        fft_smem<V, false, true>(X0, Y1, a.fp1, w2, w2, 1, a.tw1, a.tw1l, tid, nthr);
+        fft_smem<V, false, true>(X1, Y1, a.fp1, w2, w2, 1, a.tw1, a.tw1l, tid, nthr);
+        cluster.sync();
+        // transpose: rows l1 = c w1 + rl of every column s2, from the block
+        // that owns s2, times zeta_m^{l1 s2} (= zeta_N^{q l1 s2}); element
+        // (s2, rl) at s2 w1 + rl
+        for (int e = tid; e < tile; e += nthr) {
+            const int rl = e / a.m2, s2 = e - rl * a.m2;
+            const int src = s2 / w2, scl = s2 - src * w2;
+            const int l1 = c * w1 + rl;
+            const V* rx0 = cluster.map_shared_rank(X0, src);
+            const V* rx1 = cluster.map_shared_rank(X1, src);
+            const int k = sidx<V, true>(l1 * w2 + scl);
+            V v0 = rx0[k], v1 = rx1[k];
+            if (l1 != 0 && s2 != 0) {
+                const V w = twn(a.twN, (int64_t)a.q * l1 * s2);
+                v0 = cmul(v0, w);
+                v1 = cmul(v1, w);
+            }
+            Y0[sidx<V, true>(s2 * w1 + rl)] = v0;
+            Y1[sidx<V, true>(s2 * w1 + rl)] = v1;
+        }
+        // every block has read the column tiles before they are reused
+        cluster.sync();
+        // m2-point transforms of the w1 rows, product (Section 2.4), inverse
+        fft_smem<V, false, true>(Y0, X0, a.fp2, w1, w1, 1, a.tw2, a.tw2l, tid, nthr);
+        fft_smem<V, false, true>(Y1, X0, a.fp2, w1, w1, 1, a.tw2, a.tw2l, tid, nthr);
+        for (int e = tid; e < tile; e += nthr) {
+            const int k = sidx<V, true>(e);
+            Y0[k] = cmul(Y0[k], Y1[k]);
+        }
+        __syncthreads();
+        fft_smem<V, true, true>(Y0, X0, a.fp2, w1, w1, 1, a.tw2, a.tw2l, tid, nthr);
+        cluster.sync();
+        // transpose back: this block's columns s2 = c w2 + cl of every row l1,
+        // times conj(zeta_m^{l1 s2}); element (l1, cl) at l1 w2 + cl.  The
+        // next residue's writes to Y0 come after its first cluster barrier,
+        // which every block reaches only after this loop.
+        for (int e = tid; e < tile; e += nthr) {
+            const int cl = e / a.m1, l1 = e - cl * a.m1;
+            const int src = l1 / w1, rl = l1 - src * w1;
+            const int s2 = c * w2 + cl;
+            const V* ry0 = cluster.map_shared_rank(Y0, src);
+            V v = ry0[sidx<V, true>(s2 * w1 + rl)];
+            if (l1 != 0 && s2 != 0) v = cmulc(v, twn(a.twN, (int64_t)a.q * l1 * s2));
+            X0[sidx<V, true>(l1 * w2 + cl)] = v;
+        }
+        __syncthreads();
+        // inverse m1-point transforms: h_r[s1 m2 + s2] of this block's columns
+        fft_smem<V, true, true>(X0, Y1, a.fp1, w2, w2, 1, a.tw1, a.tw1l, tid, nthr);
+        // unfold (Eq. 2 outer sums): output j = t m + s gets
+        // conj(zeta_N^{r s}) conj(zeta_q^{r t}) h_r[s], residues in increasing r
+        for (int e = tid; e < tile; e += nthr) {
+            const int s1 = e / w2, cl = e - s1 * w2;
+            const int64_t s = (int64_t)s1 * a.m2 + (int64_t)c * w2 + cl;
+            V hv = X0[sidx<V, true>(e)];
+            if (r != 0) hv = cmulc(hv, twn(a.twN, (int64_t)r * s));
+            for (int t = 0; t < a.pout; ++t) {
+                const int64_t j = (int64_t)t * a.m + s;
+                if (j >= a.hi) break;
+                if (j < a.lo) continue;
+                const V v = (r != 0 && t != 0) ? cmulc(hv, twn(a.twN, (((int64_t)r * t) % a.q) * a.m)) : hv;
+                acc[t * tile + e] = cadd(acc[t * tile + e], v);
+            }
+        }
+        // the thread that reads X0[e] here is the one that writes it in the
+        // next fold, and acc entries are per thread: no barrier needed
+    }
+    // no block leaves while another may still read its shared memory
+    cluster.sync();
+    for (int t = 0; t < a.pout; ++t)
+        for (int e = tid; e < tile; e += nthr) {
+            const int s1 = e / w2, cl = e - s1 * w2;
+            const int64_t j = (int64_t)t * a.m + (int64_t)s1 * a.m2 + (int64_t)c * w2 + cl;
+            if (j >= a.lo && j < a.hi) a.out[b * a.ldo + (j - a.lo)] = cscale(acc[t * tile + e], a.scale);
+        }
+}
+
+// ------------------------------------------------------------------ host
+
+// Bytes of dynamic shared memory of one block.
+template <typename T> static size_t cluster_smem(int64_t m, int C, int64_t pout)
+{
+    return (size_t)((4 + pout) * smem_len<cx<T>>(m / C)) * sizeof(cx<T>);
+}
+
+// Whether a 16-block cluster of this kernel with `smem` bytes per block can
+// be resident (a non-portable size; remembered per device).
+template <class V> static bool cluster16_ok(size_t smem, int thr)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, size_t>, bool> known;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(dev, smem * 1024 + (size_t)thr);
+    auto it = known.find(key);
+    if (it != known.end()) return it->second;
+    bool ok = cudaFuncSetAttribute(k_conv_cluster<V>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+              cudaSuccess;
+    if (ok && smem > 48 * 1024)
+        ok = cudaFuncSetAttribute(k_conv_cluster<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+             cudaSuccess;
+    if (ok) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(16);
+        cfg.blockDim = dim3(thr);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 16;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        ok = cudaOccupancyMaxActiveClusters(&n, k_conv_cluster<V>, &cfg) == cudaSuccess && n > 0;
+    }
+    cudaGetLastError();
+    known[key] = ok;
+    return ok;
+}
+
+// Threads of one block: one per radix-8 butterfly of the tile, 64..256.
+static int cluster_threads(int64_t tile)
+{
+    int thr = (int)((tile / 8 + 31) / 32 * 32);
+    return thr < 64 ? 64 : (thr > kMaxThreads ? kMaxThreads : thr);
+}
+
+// The cluster's shape for an m-point residue with pout output blocks: C in
+// {16, 8, 4, 2} (the largest that divides both factors and leaves tiles of at
+// least 32 elements; 16, a non-portable cluster size, only where the device
+// can hold such a cluster), m = m1 m2 with C | m1, C | m2 and m1 <= m2 as close to
+// sqrt(m) as allowed, shared memory within the per-block limit.  False when
+// none exists.
+template <typename T> bool cluster_shape(int64_t m, int64_t pout, int* Co, int64_t* m1o, int64_t* m2o)
+{
+    constexpr size_t kMaxSmem = 200 * 1024;
+    for (int C : { 16, 8, 4, 2 }) {
+        if (m % ((int64_t)C * C) != 0 || m / C < 32 || cluster_smem<T>(m, C, pout) > kMaxSmem) continue;
+        if (C == 16 && !cluster16_ok<cx<T>>(cluster_smem<T>(m, C, pout), cluster_threads(m / C))) continue;
+        int64_t best = -1;
+        for (int64_t m1 = C; m1 * m1 <= m; m1 += C)
+            if (m % m1 == 0 && (m / m1) % C == 0) best = m1;
+        if (best < 0) continue;
+        *Co = C;
+        *m1o = best;
+        *m2o = m / best;
+        return true;
+    }
+    return false;
+}
+template bool cluster_shape<double>(int64_t, int64_t, int*, int64_t*, int64_t*);
+template bool cluster_shape<float>(int64_t, int64_t, int*, int64_t*, int64_t*);
+
+template <typename T>
+cudaError_t launch_conv_cluster(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t B, int64_t ld_f, int64_t ld_g,
+                                int64_t ldo, int64_t L, int64_t lo, int64_t hi, int64_t m, int64_t p, int64_t q,
+                                int64_t r_lo, int64_t r_hi, double scale, cudaStream_t st)
+{
+    using V = cx<T>;
+    if (B <= 0 || r_hi <= r_lo) return cudaSuccess;
+    const int64_t pout = (hi + m - 1) / m;
+    int C = 0;
+    int64_t m1 = 0, m2 = 0;
+    if (!cluster_shape<T>(m, pout, &C, &m1, &m2)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+    ClusterArgs<V> a;
+    a.twN = tw_table<T>(q * m, &e);
+    if (e != cudaSuccess) return e;
+    a.tw1 = twiddles_fft<T>(m1, false, &e);
+    if (e != cudaSuccess) return e;
+    a.tw1l = twiddles_fft<T>(m1, true, &e);
+    if (e != cudaSuccess) return e;
+    a.tw2 = twiddles_fft<T>(m2, false, &e);
+    if (e != cudaSuccess) return e;
+    a.tw2l = twiddles_fft<T>(m2, true, &e);
+    if (e != cudaSuccess) return e;
+    a.fp1 = fft_plan<T>(m1);
+    a.fp2 = fft_plan<T>(m2);
+    a.f = f;
+    a.g = g;
+    a.out = out;
+    a.ld_f = ld_f;
+    a.ld_g = ld_g;
+    a.ldo = ldo;
+    a.L = L;
+    a.lo = lo;
+    a.hi = hi;
+    a.m = (int)m;
+    a.m1 = (int)m1;
+    a.m2 = (int)m2;
+    a.p = (int)p;
+    a.q = (int)q;
+    a.pout = (int)pout;
+    a.r_lo = (int)r_lo;
+    a.r_hi = (int)r_hi;
+    a.scale = (T)scale;
+    const int thr = cluster_threads(m / C);
+    const size_t smem_c = cluster_smem<T>(m, C, pout);
+    if (smem_c > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(k_conv_cluster<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c)) !=
+            cudaSuccess)
+        return e;
+    if (preparing()) return cudaSuccess;
+    // model: per row and residue 3 m-point FFTs, the product, the folds of f
+    // and g and the unfold (8 flops per element each), the final scaling
+    const double Lrow = (double)(L < p * m ? L : p * m);
+    LaunchScope ls(K_CLUSTER, st,
+                   (double)B * (r_hi - r_lo) * (3.0 * fft_flops((double)m) + 6.0 * m + 16.0 * Lrow + 8.0 * (hi - lo)) +
+                       2.0 * B * (hi - lo),
+                   (double)B * (2.0 * Lrow + (double)(hi - lo)) * sizeof(V));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(B * C));
+    cfg.blockDim = dim3(thr);
+    cfg.dynamicSmemBytes = smem_c;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_conv_cluster<V>, a);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+template cudaError_t launch_conv_cluster<double>(const cx<double>*, const cx<double>*, cx<double>*, int64_t, int64_t,
+                                                 int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,
+                                                 int64_t, int64_t, int64_t, double, cudaStream_t);
+template cudaError_t launch_conv_cluster<float>(const cx<float>*, const cx<float>*, cx<float>*, int64_t, int64_t,
+                                                int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,
+                                                int64_t, int64_t, int64_t, double, cudaStream_t);
+
+} // namespace hdc
+
+HDC_EXPORT int hdc_set_cluster(int mode)
+{
+    if (mode < 0 || mode > 2) return HDC_ERR_PARAM;
+    hdc::g_cluster_route.store(mode);
+    return HDC_OK;
+}

@@ -96,7 +96,7 @@ void* tuning_flush_buffer(size_t* bytes);
 // K_FOLD_TMA counts the launches of k_fold_fft_cols that stage their tiles
 // with TMA copies (K_FOLD_FFT_COLS those on plain loads).
 enum KernelId { K_TWIDDLE = 0, K_RESIDUE_ROWS, K_FOLD_FFT_COLS, K_IFFT_COLS, K_UNFOLD, K_BATCHED, K_IFFT_UNFOLD,
-                K_FOLD_TMA, K_COUNT };
+                K_FOLD_TMA, K_CLUSTER, K_HERMITIAN_ROWS, K_COUNT };
 
 struct LaunchScope {
     int kid;
@@ -207,6 +207,33 @@ cudaError_t launch_unfold_real(T* out, const cx<T>* h, int64_t B, int64_t bstrid
                                int64_t p, int64_t q, int64_t Nf, int64_t cs, int64_t cc, int64_t lo, int64_t hi,
                                int64_t r0, int64_t Dg, int first, int last, double scale, cudaStream_t st);
 
+// Whole 1-D convolutions of B short rows on thread-block clusters (one
+// cluster per row): residues [r_lo, r_hi) of f and g (row strides ld_f,
+// ld_g, L valid elements, m-point transforms, p fold blocks, q residues)
+// from fold to unfold in one launch, the outputs [lo, hi) of each row
+// written once (times scale) to out (row stride ldo).  cluster_shape tells
+// whether an m-point residue (pout = ceil(hi / m) output blocks) fits a
+// cluster: C blocks, m = m1 m2 with C dividing both.
+template <typename T> bool cluster_shape(int64_t m, int64_t pout, int* C, int64_t* m1, int64_t* m2);
+int cluster_route_mode();
+template <typename T>
+cudaError_t launch_conv_cluster(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t B, int64_t ld_f, int64_t ld_g,
+                                int64_t ldo, int64_t L, int64_t lo, int64_t hi, int64_t m, int64_t p, int64_t q,
+                                int64_t r_lo, int64_t r_hi, double scale, cudaStream_t st);
+
+// Inner axis of the centered Hermitian 2-D convolution (K = c + 1 stored
+// ky >= 0 values per row): rows (rr, b, l) of wf / wg at ((rr B + b) mx + l) K
+// hold F_s, G_s of outer bin x = qx l + r0 + rr (Nx = qx mx points); per pair
+// of rows the packed fold and my-point transforms of every ky residue (py
+// fold blocks, qy residues), the real products, one packed inverse transform
+// and unfold of the outputs ky + 2c in [c, 3c], split by symmetry; the
+// k >= 0 halves times zeta_Nx^{2 c x} and 1 / (qy my) go to the same rows of
+// wh.  nblk = (outer residues of the pass) x B.
+template <typename T>
+cudaError_t launch_hermitian_rows(const cx<T>* wf, const cx<T>* wg, cx<T>* wh, int64_t nblk, int64_t B, int64_t mx,
+                                  int64_t K, int64_t my, int64_t py, int64_t qy, int64_t Nx, int64_t qx, int64_t r0,
+                                  cudaStream_t st);
+
 // In-place inverse FFT of size ma along the strided axis of y[rr][b][l][c],
 // preceded by multiplication with conj(zeta_{Nf/q}^{l c}) if pre != 0.
 template <typename T>
@@ -234,10 +261,6 @@ cudaError_t launch_unfold(cx<T>* out, const cx<T>* h, int64_t B, int64_t bstride
                           int64_t ma, int64_t p, int64_t q, int64_t Nf, int64_t cs, int64_t cc,
                           int64_t lo, int64_t hi, int64_t r0, int64_t D, int first, int last, double scale,
                           cudaStream_t st);
-
-// Full (2K-1) x (2K-1) centered spectrum from its ky >= 0 half, B arrays.
-template <typename T>
-cudaError_t launch_hermitian_expand(const cx<T>* half, cx<T>* full, int64_t K, int64_t B, cudaStream_t st);
 
 // The same launches with caller-provided twiddle tables (no library cache):
 // twN = zeta_{q m}^k (q m entries), twm / twml the packed stage tables of the

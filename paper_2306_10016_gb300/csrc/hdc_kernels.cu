@@ -1006,38 +1006,6 @@ cudaError_t launch_unfold_real(T* out, const cx<T>* h, int64_t B, int64_t bstrid
 // its half half[b][x][ky] (ky in [0, c]): f(kx, ky) for ky >= 0, and
 // conj(f(-kx, -ky)) for ky < 0 (the spectrum of a real field).
 
-template <class V>
-__global__ void k_hermitian_expand(const V* __restrict__ half, V* __restrict__ full, int64_t K, int64_t B)
-{
-    const int64_t n = 2 * K - 1, c = K - 1;
-    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (gid >= B * n * n) return;
-    const int64_t b = gid / (n * n);
-    const int64_t e = gid - b * n * n;
-    const int64_t x = e / n, y = e - x * n;
-    const V* hb = half + b * n * K;
-    V v;
-    if (y >= c) {
-        v = hb[x * K + (y - c)];
-    } else {
-        const V w = hb[(2 * c - x) * K + (c - y)];
-        v = mkc<V>(w.x, -w.y);
-    }
-    full[gid] = v;
-}
-
-template <typename T>
-cudaError_t launch_hermitian_expand(const cx<T>* half, cx<T>* full, int64_t K, int64_t B, cudaStream_t st)
-{
-    const int thr = 256;
-    const int64_t tot = B * (2 * K - 1) * (2 * K - 1);
-    if (tot <= 0) return cudaSuccess;
-    k_hermitian_expand<cx<T>><<<(unsigned)((tot + thr - 1) / thr), thr, 0, st>>>(half, full, K, B);
-    return cudaGetLastError();
-}
-template cudaError_t launch_hermitian_expand<double>(const cx<double>*, cx<double>*, int64_t, int64_t, cudaStream_t);
-template cudaError_t launch_hermitian_expand<float>(const cx<float>*, cx<float>*, int64_t, int64_t, cudaStream_t);
-
 // ---------------------------------------- launchers with caller twiddles
 // The same kernels with the twiddle tables passed in (for callers that keep
 // the tables in memory of their own instead of the library cache).

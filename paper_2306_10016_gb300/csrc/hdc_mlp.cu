@@ -387,10 +387,15 @@ HDC_EXPORT int hdc_mlp_q_to_class(int64_t q)
     return best;
 }
 
-// Per-axis features (HDC_MLP_FEATURES = 8 per axis): log2 L / 24,
+// Per-axis features (HDC_MLP_FEATURES = 12 per axis): log2 L / 24,
 // M / L - 2, 1 if innermost, log2 of the inner column count / 24, log2 of
 // the rows above (outer extents times batch) / 24, dims / 3, 1 for FP64,
-// log2 of all outputs / 24.
+// log2 of all outputs / 24, then for q = 1, 2, 3, 4 the padding that q
+// residues of the smallest good size m >= ceil(M / q) add,
+// 4 log2(q m / M) -- a scale-free description of which residue counts pad
+// M well, which carries over from short training axes to long ones -- with
+// 1 added when that m exceeds the column-tile limit of an axis that has
+// inner axes (the tuple is then not available there).
 HDC_EXPORT int hdc_mlp_axis_features(int dims, const int64_t* L, const int64_t* M, int dtype, int64_t batch,
                                      float* out)
 {
@@ -400,11 +405,12 @@ HDC_EXPORT int hdc_mlp_axis_features(int dims, const int64_t* L, const int64_t* 
         if (L[i] < 1 || M[i] < 1) return HDC_ERR_PARAM;
         total *= (double)L[i];
     }
+    const int64_t outer_lim = hdc_max_outer_fft_size(dtype);
     for (int i = 0; i < dims; ++i) {
         double inner = 1.0, outer = (double)batch;
         for (int j = i + 1; j < dims; ++j) inner *= (double)L[j];
         for (int j = 0; j < i; ++j) outer *= (double)L[j];
-        float* f = out + (int64_t)i * 8;
+        float* f = out + (int64_t)i * HDC_MLP_FEATURES;
         f[0] = (float)(std::log2((double)L[i]) / 24.0);
         f[1] = (float)((double)M[i] / (double)L[i] - 2.0);
         f[2] = i == dims - 1 ? 1.f : 0.f;
@@ -413,6 +419,12 @@ HDC_EXPORT int hdc_mlp_axis_features(int dims, const int64_t* L, const int64_t* 
         f[5] = (float)dims / 3.f;
         f[6] = dtype == HDC_C128 ? 1.f : 0.f;
         f[7] = (float)(std::log2(total) / 24.0);
+        for (int q = 1; q <= 4; ++q) {
+            const int64_t m = hdc_next_good_size((M[i] + q - 1) / q);
+            double v = m > 0 ? 4.0 * std::log2((double)q * (double)m / (double)M[i]) : 4.0;
+            if (i < dims - 1 && m > outer_lim) v += 1.0;
+            f[7 + q] = (float)v;
+        }
     }
     return HDC_OK;
 }

@@ -38,7 +38,8 @@ std::vector<cudaEvent_t> g_pool;
 // the process exits.
 std::unordered_set<cudaEvent_t> g_captured;
 const char* g_names[K_COUNT] = { "k_twiddle", "k_residue_rows", "k_fold_fft_cols", "k_ifft_cols", "k_unfold",
-                                 "k_batched", "k_ifft_unfold_cols", "k_fold_fft_cols_tma" };
+                                 "k_batched", "k_ifft_unfold_cols", "k_fold_fft_cols_tma", "k_conv_cluster",
+                                 "k_hermitian_rows" };
 
 // Inside a stream capture an event record must be an external record node
 // for the event to carry a time stamp when the graph replays.

@@ -52,13 +52,23 @@ def good_sizes(lo: int, hi: int):
 
 def training_problems(seed: int, n_rect: int):
     """All squares with sides in the 7-smooth sizes of [16, 512], skinny
-    rectangles of heights 4..32, and n_rect seeded rectangles."""
+    rectangles of heights 4..32, n_rect seeded rectangles, and rectangles of
+    height 16 and 32 whose long side runs through the 7-smooth sizes of
+    (512, 4096]: every training problem holds at most 512 x 512 outputs, but
+    axes as long as those of the larger problems the predictor is used on
+    appear in them (the paper's transfer from rectangles to squares,
+    Section 5.3 and Section 6.2)."""
     sides = good_sizes(16, 512)
     probs = [(s, s) for s in sides]
     for s in sides[::3]:
         for h in (4, 8, 16, 32):
             probs.append((s, h))
             probs.append((h, s))
+    for s in good_sizes(513, 4096)[::2]:
+        for h in (16, 32):
+            if s * h <= 512 * 512:
+                probs.append((s, h))
+                probs.append((h, s))
     u = synth.uniform01(seed, 2 * n_rect)
     for k in range(n_rect):
         a = sides[int(u[2 * k] * len(sides))]
@@ -143,7 +153,7 @@ def train(X, yq, yd, steps=3000, lr=3e-3, seed=230610016, log=None, checkpoint=N
     import torch
 
     import paper_2306_10016_gb300 as hdc
-    net = hdc.MLP()
+    net = hdc.MLP(n_in=X.shape[1])
     if resume and os.path.exists(resume):
         net.load(resume)
     else:
@@ -217,6 +227,10 @@ def _rule_params(L, q, dtype=None):
     return out
 
 
+# seed and count of the seeded training rectangles (the packaged dataset's)
+TRAIN_SEED = synth.BASE_SEED + 5
+TRAIN_RECTANGLES = 240
+
 EVAL_PROBLEMS = [(768, 768), (1024, 1024), (2048, 512), (2048, 1024), (3072, 1536), (4096, 2048),
                  (32, 32, 32), (64, 64, 64), (128, 128, 128), (256, 256, 256)]
 
@@ -279,6 +293,159 @@ def evaluate(weights, problems=None, dtype=None, reps=5, log=None):
     return {"rows": rows, "summary": {k2: stats(k2) for k2 in KEYS}}
 
 
+# ------------------------------------------------ held-out timing records
+# The predictor's top class is judged on problems larger than any it was
+# trained on, by device times measured once on the GPU and kept with the
+# package: per problem the grid search's choice and time, and the time of
+# every combination of per-axis choices m = nextgood(ceil(M / q_k)) with
+# D = q (and D = 1 in 2-D) over the residue-count classes q_k (q_k <= 4 in
+# 3-D), plus the packaged network's own choice.  Regret of any choice in
+# the table is then computed on the host.
+
+def _graph_ms(run, reps=5):
+    """Median device time (ms) of run(stream) replayed from a CUDA graph, L2
+    evicted before each replay (as the tuner and the throughput measurement
+    time)."""
+    import torch
+    flush = _graph_ms.flush
+    if flush is None:
+        flush = _graph_ms.flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        run(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        run(side)
+    graph.replay()
+    st = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        graph.replay()
+        e1.record(st)
+        ts.append((e0, e1))
+    torch.cuda.synchronize()
+    del graph
+    return float(np.median([a.elapsed_time(b) for a, b in ts]))
+
+
+_graph_ms.flush = None
+
+
+def combo_key(prm):
+    return "|".join(f"{p['m']}:{p['D']}" for p in prm)
+
+
+def axis_options(L, dims, a, dtype, with_one):
+    """The (m, p, q, D) one axis can take from the q classes (deduplicated
+    by (m, D)); D = q, and D = 1 too when with_one."""
+    import ctypes
+
+    import paper_2306_10016_gb300 as hdc
+    M = 2 * L - 1
+    max_m = hdc.max_outer_fft_size(dtype) if a < dims - 1 else 0
+    out, seen = [], set()
+    for k, qk in enumerate(hdc.mlp_q_classes()):
+        if dims == 3 and qk > 4:
+            continue
+        for one in ((0, 1) if with_one else (0,)):
+            v = [ctypes.c_int64() for _ in range(4)]
+            rc = hdc.lib().hdc_mlp_decode_class(k, one, L, M, dtype, max_m, *[ctypes.byref(x) for x in v])
+            if rc != 0:
+                continue
+            m, p, q, D = (x.value for x in v)
+            if (m, D) not in seen:
+                seen.add((m, D))
+                out.append(dict(m=m, p=p, q=q, D=D))
+    return out
+
+
+def top_class_params(shape, dtype, logits_fn):
+    """The network's most likely valid choice per axis (what HDC_PREDICT_MLP
+    plans), from logits_fn(X) -> logits of the axes' features."""
+    import paper_2306_10016_gb300 as hdc
+    dims = len(shape)
+    X = hdc.mlp_axis_features(list(shape), [2 * x - 1 for x in shape], dtype)
+    lg = logits_fn(X)
+    out = []
+    for a, L in enumerate(shape):
+        max_m = hdc.max_outer_fft_size(dtype) if a < dims - 1 else 0
+        out.append(hdc.mlp_decode_axis(lg[a], L, 2 * L - 1, dtype, max_m))
+    return out
+
+
+def timing_records(weights, problems=None, dtype=None, reps=5, log=None):
+    import itertools
+
+    import torch
+
+    import paper_2306_10016_gb300 as hdc
+    dtype = hdc.HDC_C128 if dtype is None else dtype
+    tdt = torch.complex128 if dtype == hdc.HDC_C128 else torch.complex64
+    recs = []
+    for k, shape in enumerate(problems or EVAL_PROBLEMS):
+        dims = len(shape)
+        f = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 90 + k, shape)).to("cuda", tdt)
+        g = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 9090 + k, shape)).to("cuda", tdt)
+        h = torch.empty_like(f)
+        L = list(shape)
+        Mv = [2 * x - 1 for x in L]
+
+        def t_of(prm):
+            m = [p["m"] for p in prm]
+            D = [p["D"] for p in prm]
+            ws = torch.empty(max(1, hdc.workspace_size(L, Mv, m, D=D, dtype=dtype)), dtype=torch.uint8,
+                             device="cuda")
+            return _graph_ms(lambda s_: hdc.convnd(f, g, dims, m, D=D, out=h, workspace=ws, stream=s_), reps)
+
+        t0 = time.perf_counter()
+        best, trials = hdc.tune(f, g, dims, max_ratio=1.5, reps=reps)
+        t_search = time.perf_counter() - t0
+        search = [dict(m=b["m"], p=b["p"], q=b["q"], D=b["D"]) for b in best]
+        opts = [axis_options(x, dims, a, dtype, dims < 3) for a, x in enumerate(L)]
+        table = {}
+        configs = [list(c) for c in itertools.product(*opts)]
+        net = hdc.Plan(L, dtype=dtype, mode=hdc.HDC_PREDICT_MLP, tuning_db=str(weights)).params if weights else None
+        extra = [search, _rule_params(shape, 1, dtype), _rule_params(shape, 2, dtype)] + ([net] if net else [])
+        for prm in configs + extra:
+            key = combo_key(prm)
+            if key not in table:
+                table[key] = round(t_of(prm), 5)
+        rec = {"shape": L, "dtype": int(dtype), "search": search, "search_ms": table[combo_key(search)],
+               "search_s": round(t_search, 2), "search_timed": len(trials),
+               "explicit": combo_key(_rule_params(shape, 1, dtype)), "q2": combo_key(_rule_params(shape, 2, dtype)),
+               "network": combo_key(net) if net else None, "ms": table}
+        recs.append(rec)
+        if log:
+            log(f"records {shape}: {len(table)} configurations, search {rec['search_ms']} ms")
+        del f, g, h
+        torch.cuda.empty_cache()
+    return recs
+
+
+def regret_table(records, choose):
+    """Regret T(choice) / T(grid search) - 1 (clamped at 0) per record, for
+    choose(record) -> configuration key (or None when not in the table), and
+    the geometric mean, 90th percentile and maximum."""
+    r = []
+    for rec in records:
+        key = choose(rec)
+        if key is None or key not in rec["ms"]:
+            r.append(float("nan"))
+            continue
+        best = min(rec["search_ms"], min(rec["ms"].values()))
+        r.append(max(0.0, rec["ms"][key] / rec["search_ms"] - 1.0) if best > 0 else float("nan"))
+    a = np.array(r)
+    ok = a[np.isfinite(a)]
+    return {"per_problem": r, "geomean": float(np.exp(np.mean(np.log1p(ok))) - 1.0) if ok.size else None,
+            "p90": float(np.quantile(ok, 0.9)) if ok.size else None, "max": float(ok.max()) if ok.size else None,
+            "missing": int(a.size - ok.size)}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
@@ -288,6 +455,7 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--weights", default=None)
     ap.add_argument("--eval", action="store_true")
+    ap.add_argument("--records", default=None, help="write held-out timing records (json.gz) of the weights")
     a = ap.parse_args(argv)
     os.makedirs(a.out, exist_ok=True)
 
@@ -299,7 +467,7 @@ def main(argv=None):
     report = {}
     if a.collect:
         t0 = time.perf_counter()
-        recs = collect(training_problems(synth.BASE_SEED + 5, a.collect), log=log)
+        recs = collect(training_problems(TRAIN_SEED, a.collect), log=log)
         report["collect_s"] = round(time.perf_counter() - t0, 1)
         with open(ds_path, "w") as fh:
             json.dump(recs, fh)
@@ -316,6 +484,18 @@ def main(argv=None):
         counts = np.bincount(yq, minlength=net.n_out - 2)
         report["train_accuracy"] = {"q": aq, "D": ad, "q_majority_rule": float(counts.max() / counts.sum())}
         log(f"train accuracy q {aq:.3f} D {ad:.3f} (majority {report['train_accuracy']['q_majority_rule']:.3f})")
+    if a.records:
+        t0 = time.perf_counter()
+        recs = timing_records(w_path, log=log)
+        report["records_s"] = round(time.perf_counter() - t0, 1)
+        import gzip
+        with gzip.open(a.records, "wt") as fh:
+            json.dump(recs, fh)
+        report["records_regret"] = {
+            "network": regret_table(recs, lambda r: r["network"]),
+            "explicit": regret_table(recs, lambda r: r["explicit"]),
+            "q2": regret_table(recs, lambda r: r["q2"])}
+        log(json.dumps(report["records_regret"]))
     if a.eval:
         report["eval"] = evaluate(w_path, log=log)
         log(json.dumps(report["eval"]["summary"]))

@@ -77,8 +77,8 @@ def test_adam_step_vs_oracle(hdc):
 
 def test_training_learns_a_separable_rule(hdc):
     from paper_2306_10016_gb300.predictor import accuracy, train
-    n, nq = 400, 8
-    X = (2 * synth.uniform01(11, n * 8) - 1).reshape(n, 8).astype(np.float32)
+    n, nq, F = 400, 8, hdc.MLP_FEATURES
+    X = (2 * synth.uniform01(11, n * F) - 1).reshape(n, F).astype(np.float32)
     yq = np.clip(((X[:, 0] + 1) * 4).astype(np.int32), 0, nq - 1)   # class from the first feature
     yd = (X[:, 1] > 0).astype(np.int32)
     net, hist = train(X, yq, yd, steps=600, lr=1e-2)
@@ -89,7 +89,7 @@ def test_training_learns_a_separable_rule(hdc):
 
 def test_checkpoint_resume_is_exact(hdc, tmp_path):
     from paper_2306_10016_gb300.predictor import init_params
-    X, yq, yd = _data(32, 8, 8, 12)
+    X, yq, yd = _data(32, hdc.MLP_FEATURES, 8, 12)
     Xd, yqd, ydd = torch.from_numpy(X).cuda(), torch.from_numpy(yq).cuda(), torch.from_numpy(yd).cuda()
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
 
@@ -100,7 +100,7 @@ def test_checkpoint_resume_is_exact(hdc, tmp_path):
         torch.cuda.synchronize()
 
     a = hdc.MLP()
-    a.set_params(init_params(8, 64, a.n_out, 3))
+    a.set_params(init_params(hdc.MLP_FEATURES, 64, a.n_out, 3))
     steps(a, 10)
     a.save(tmp_path / "ck.bin")
     steps(a, 10)
@@ -114,7 +114,8 @@ def test_plan_predict_mlp(hdc, tmp_path):
     """A network trained to always answer q = 2, D = q drives a plan whose
     convolution is correct."""
     from paper_2306_10016_gb300.predictor import train
-    X = (2 * synth.uniform01(21, 200 * 8) - 1).reshape(200, 8).astype(np.float32)
+    F = hdc.MLP_FEATURES
+    X = (2 * synth.uniform01(21, 200 * F) - 1).reshape(200, F).astype(np.float32)
     yq = np.full(200, hdc.mlp_q_to_class(2), dtype=np.int32)
     yd = np.zeros(200, dtype=np.int32)
     train(X, yq, yd, steps=200, lr=1e-2, checkpoint=str(tmp_path / "w.bin"))

@@ -82,3 +82,49 @@ def test_residue_shards_allreduce_to_convolution(tmp_path, L, m, q):
         got = np.load(tmp_path / f"r{r}.npy")
         assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-13
         assert float(np.load(tmp_path / f"t{r}.npy")[0]) == float(world)
+
+
+def _batch_rank_main(rank, world, port, out_dir):
+    import torch.distributed as dist
+
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    Ls = [int(x) for x in synth.log_uniform_lengths(31, 24, 8, 300)]
+    ms = [max(4, -(-(2 * L - 1) // 2)) for L in Ls]          # q = 2 (hybrid) per convolution
+    costs = [sharding.model_flops(L, m, -(-(2 * L - 1) // m)) for L, m in zip(Ls, ms)]
+    mine = sharding.shard_batch(costs, world)[rank]
+    # this rank's convolutions by the residue method (O5), no exchange of data
+    res = {}
+    for i in mine:
+        L, m = Ls[i], ms[i]
+        f = synth.unit_disk(1000 + i, (L,))
+        g = synth.unit_disk(2000 + i, (L,))
+        res[i] = oracle.conv_hybrid(f, g, m, -(-L // m), -(-(2 * L - 1) // m))
+    got = [None] * world
+    dist.all_gather_object(got, res)
+    if rank == 0:
+        merged = {}
+        for d in got:
+            assert not (set(d) & set(merged))          # every convolution on one rank only
+            merged.update(d)
+        np.save(os.path.join(out_dir, "batch.npy"), np.array([merged[i] for i in range(len(Ls))], dtype=object),
+                allow_pickle=True)
+    dist.destroy_process_group()
+
+
+def test_shard_batch_end_to_end_on_two_ranks(tmp_path):
+    """A batch of uneven convolutions split by shard_batch over two gloo
+    ranks, each computed on its rank alone: together every convolution once,
+    each equal to the direct sum (O1)."""
+    import torch.multiprocessing as mp
+
+    import oracle
+    mp.spawn(_batch_rank_main, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    out = np.load(tmp_path / "batch.npy", allow_pickle=True)
+    Ls = [int(x) for x in synth.log_uniform_lengths(31, 24, 8, 300)]
+    assert len(out) == len(Ls)
+    for i, L in enumerate(Ls):
+        ref = oracle.conv_direct(synth.unit_disk(1000 + i, (L,)), synth.unit_disk(2000 + i, (L,)))
+        assert np.max(np.abs(out[i] - ref)) / np.max(np.abs(ref)) < 1e-13, (i, L)

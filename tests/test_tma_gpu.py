@@ -29,14 +29,20 @@ def hdc():
 
 def _both(hdc, run):
     """run() on plain loads, then with TMA allowed; returns both outputs and
-    the number of TMA-staged fold launches of the second run."""
-    hdc.set_tma(False)
-    a = run().cpu().numpy()
-    hdc.set_tma(True)
-    hdc.stats_reset()
-    b = run().cpu().numpy()
-    torch.cuda.synchronize()
-    n_tma = hdc.stats()["k_fold_fft_cols_tma"]["launches"]
+    the number of TMA-staged fold launches of the second run.  The
+    thread-block-cluster route (which has no strided fold) is turned off, so
+    short single rows take the split route whose fold this file tests."""
+    hdc.set_cluster(0)
+    try:
+        hdc.set_tma(False)
+        a = run().cpu().numpy()
+        hdc.set_tma(True)
+        hdc.stats_reset()
+        b = run().cpu().numpy()
+        torch.cuda.synchronize()
+        n_tma = hdc.stats()["k_fold_fft_cols_tma"]["launches"]
+    finally:
+        hdc.set_cluster(1)
     assert hdc.device_status() == 0
     return a, b, n_tma
 
