@@ -765,9 +765,12 @@ int hdc_set_tma(int enable);
  * launch, its transforms split over the blocks and transposed through
  * distributed shared memory, the outputs written once.  Same results as the
  * other routes.  hdc_set_cluster(mode) for later calls: 0 never, 1 (the
- * default) for residues of 256 to 1024 points, where it is the faster route,
- * 2 wherever the residue fits; HDC_ERR_PARAM for another mode.  Not
- * thread-safe against calls in flight on other host threads. */
+ * default) where it is the faster route (small residues in few passes: in
+ * FP64 up to 8192 points with one residue, 4096 with two in one pass, and
+ * calls that would otherwise run several passes one after another; in FP32
+ * one residue up to 16384 points and multi-pass calls), 2 wherever the
+ * residue fits; HDC_ERR_PARAM for another mode.  Not thread-safe against
+ * calls in flight on other host threads. */
 int hdc_set_cluster(int mode);
 int hdc_device_status(int* status, int clear);
 

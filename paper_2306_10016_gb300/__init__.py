@@ -363,15 +363,33 @@ def dtype_code(t) -> int:
     raise TypeError(f"unsupported dtype {t}: use torch.complex64 or torch.complex128")
 
 
+_PREPARED = set()
+
+
+def _plain(a):
+    if a is None or isinstance(a, (int, float)):
+        return a
+    try:
+        return tuple(a)
+    except TypeError:
+        return repr(a)
+
+
 def _prepare(name: str, *args) -> None:
     """Make the twiddle tables a convolution call reads (hdc_prepare*) on the
     current device, unless a stream capture is running: the convolution
     calls themselves allocate nothing, and a table made during a capture
-    would break it (the call then fails with HDC_ERR_NOT_PREPARED)."""
+    would break it (the call then fails with HDC_ERR_NOT_PREPARED).  Calls
+    already prepared on this device are remembered, so a repeated call costs
+    a set lookup."""
     torch = _torch()
+    key = (name, torch.cuda.current_device(), tuple(_plain(a) for a in args))
+    if key in _PREPARED:
+        return
     if torch.cuda.is_current_stream_capturing():
         return
     _check(getattr(lib(), name)(*args), name)
+    _PREPARED.add(key)
 
 
 def prepare(L, m, M=None, p=0, q=0, D=0, dtype=HDC_C128, batch=1) -> None:
@@ -1269,3 +1287,4 @@ def conv1d_noalloc(f, g, m, M=None, p=0, q=0, D=0, out=None, stream=None):
 
 def release_caches() -> None:
     _check(lib().hdc_release_caches(), "release_caches")
+    _PREPARED.clear()

@@ -41,14 +41,17 @@ template <typename T> cudaError_t launch_twiddle_colmajor(cx<T>* tw, int64_t ma,
 
 // ----------------------------------------------------------- FFT plans
 
-FftPlan make_fft_plan(int64_t n, bool r16)
+FftPlan make_fft_plan(int64_t n, bool r16, bool r2)
 {
     FftPlan fp;
     memset(&fp, 0, sizeof(fp));
     fp.n = (int)n;
     int64_t k = n;
     int ns = 0;
-    if (r16) {
+    if (r2) {
+        // latency plan: radix 2 throughout the power-of-two part
+        while (k % 2 == 0 && ns < HDC_MAX_STAGES) { fp.rad[ns++] = 2; k /= 2; }
+    } else if (r16) {
         // radix-16 stages only where they save a stage over radix 8 on the
         // power-of-two part 2^e: ceil(e / 4) < ceil(e / 3)
         int e = 0;
@@ -155,17 +158,26 @@ template <typename T> static const cx<T>* twiddle_table(int64_t n, bool lf, cuda
 // or twiddle-merged form; cached like the full tables.
 template <typename T> const cx<T>* twiddles_fft(int64_t n, bool lf, cudaError_t* err, bool r16ok)
 {
-    // two plans of one size differ at most in their radix-16 stages, which
+    return twiddles_fft_plan<T>(fft_plan<T>(n, r16ok), lf, err);
+}
+template const cx<double>* twiddles_fft<double>(int64_t, bool, cudaError_t*, bool);
+template const cx<float>* twiddles_fft<float>(int64_t, bool, cudaError_t*, bool);
+
+template <typename T> const cx<T>* twiddles_fft_plan(const FftPlan& fp, bool lf, cudaError_t* err)
+{
+    // the plans of one size differ in their first radices (16, 8 or 2), which
     // the key tells apart
-    const FftPlan fp = fft_plan<T>(n, r16ok);
-    const int kind = (sizeof(T) == 8 ? 1 : 0) + (lf ? 2 : 0) + 4 + (fp.nst > 0 && fp.rad[0] == 16 ? 8 : 0);
+    const int64_t n = fp.n;
+    const int first = fp.nst > 0 ? fp.rad[0] : 0;
+    const int kind = (sizeof(T) == 8 ? 1 : 0) + (lf ? 2 : 0) + 4 + (first == 16 ? 8 : 0) +
+                     (first == 2 && n % 4 == 0 && fp.nst > 1 && fp.rad[1] == 2 ? 16 : 0);
     return reinterpret_cast<const cx<T>*>(cached_table(
         n, kind, (size_t)fp.tlen * sizeof(cx<T>),
         [&](void* p, cudaStream_t s) { return launch_twiddle_fft_into<T>(reinterpret_cast<cx<T>*>(p), fp, lf, s); },
         err));
 }
-template const cx<double>* twiddles_fft<double>(int64_t, bool, cudaError_t*, bool);
-template const cx<float>* twiddles_fft<float>(int64_t, bool, cudaError_t*, bool);
+template const cx<double>* twiddles_fft_plan<double>(const FftPlan&, bool, cudaError_t*);
+template const cx<float>* twiddles_fft_plan<float>(const FftPlan&, bool, cudaError_t*);
 
 // An FP32 fold/unfold table of N entries is kept whole up to this size; a
 // larger one is two tables of about sqrt(N) entries (TwTab).
@@ -440,20 +452,35 @@ template <typename T> struct Ins {
 };
 
 // Whole convolutions on thread-block clusters (launch_conv_cluster) for a
-// few short rows: when B rows of C blocks each leave the GPU's SMs unfilled
-// (B C <= the SM count), the one-block-per-residue routes would run with a
-// handful of blocks, each bound by one SM's FP64 rate.
+// few short rows (B rows of C blocks each at most the SM count), where they
+// are the faster route.  Measured on single rows with L2 evicted before each
+// call: a cluster residue costs about 11 us in FP64 (twice that above 4096
+// points), the launch about 17 us; a pass of the split route's four kernels
+// about 50 us whatever its size.  So (mode 1) in FP64 the cluster takes
+// residues of 256 .. 8192 points when q u <= 2 passes + 1 (u = 1 up to 4096
+// points, else 2; passes = ceil(q / D)): explicit padding up to 8192
+// points, q = 2 in one pass up to 4096, and every residue count when D = 1
+// runs the split route's passes one after another (the L = 1024 configuration
+// with (512, 2, 4, 1): 70 against 189 us).  FP32, four times cheaper per
+// split-route pass, takes it for one residue up to 16384 points and for D = 1
+// multi-pass calls.
 template <typename T> static bool use_cluster(const Axis& a, int64_t B)
 {
-    // measured against the split route with L2 evicted before each call: the
-    // cluster route wins for residues of at most 1024 points (the L = 1024
-    // configuration, m = 512: 132 against 190 us) and loses above
     const int mode = cluster_route_mode();
-    if (mode == 0 || a.m < 256 || (mode == 1 && a.m > 1024)) return false;
+    if (mode == 0 || a.m < 256) return false;
     int C = 0;
     int64_t m1 = 0, m2 = 0;
-    if (!cluster_shape<T>(a.m, a.pout, &C, &m1, &m2)) return false;
-    return B * C <= (int64_t)sm_count();
+    if (!cluster_shape<T>(a.m, a.pout, a.q, &C, &m1, &m2)) return false;
+    if (B * C > (int64_t)sm_count()) return false;
+    if (mode == 2) return true;
+    const int64_t passes = (a.q + a.D - 1) / a.D;
+    if (sizeof(T) == 8) {
+        if (a.m > 8192) return false;
+        const int64_t u = a.m > 4096 ? 2 : 1;
+        return a.q * u <= 2 * passes + 1;
+    }
+    if (a.m > 16384) return false;
+    return a.q == 1 || (passes > 1 && a.q <= 2 * passes + 1);
 }
 
 // 1-D convolution of B rows (input row strides ld_f for x[0], ld_g for the

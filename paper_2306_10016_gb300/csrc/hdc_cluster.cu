@@ -63,8 +63,32 @@ template <class V> struct ClusterArgs {
     FftPlan fp1, fp2;
 };
 
-// Shared memory: four tiles of m / C elements (X0, X1: the column tiles of
-// f and g; Y0, Y1: their row tiles) and pout tiles of output accumulators.
+// Shared memory of one block (elements): the column tile X and the row tile
+// Y (each holds f and g side by side: two tiles of m / C), a scratch half S
+// of the same size for the transforms (no other block reads it), pout tiles
+// of output accumulators, and copies of every twiddle the block reads: the
+// stage tables of both transform sizes (plain and scale-tangent forms), the
+// four-step twiddles of both transposes (a tile each), the residue's fold
+// and unfold twiddles zeta_N^{r s} of the block's elements (a tile, made
+// again for every residue) and zeta_q^k (q entries).  With the twiddles in
+// shared memory, a residue waits on global memory only once, in the fold.
+struct ClusterSmem {
+    int tl2, tile, pout, t1, t2, q; // tl2: elements of a two-tile buffer
+    __host__ __device__ int x() const { return 0; }
+    __host__ __device__ int y() const { return tl2; }
+    __host__ __device__ int scratch() const { return 2 * tl2; }
+    __host__ __device__ int acc() const { return 3 * tl2; }
+    __host__ __device__ int tw1() const { return acc() + pout * tile; }
+    __host__ __device__ int tw1l() const { return tw1() + t1; }
+    __host__ __device__ int tw2() const { return tw1l() + t1; }
+    __host__ __device__ int tw2l() const { return tw2() + t2; }
+    __host__ __device__ int fw() const { return tw2l() + t2; }
+    __host__ __device__ int bw() const { return fw() + tile; }
+    __host__ __device__ int ft() const { return bw() + tile; }
+    __host__ __device__ int qt() const { return ft() + tile; }
+    __host__ __device__ int total() const { return qt() + q; }
+};
+
 template <class V>
 __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_constant__ ClusterArgs<V> a)
 {
@@ -75,113 +99,156 @@ __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_const
     const int64_t b = blockIdx.x / C;
     const int w1 = a.m1 / C, w2 = a.m2 / C;
     const int tile = a.m / C;
-    const int tl = (int)smem_len<V>(tile);
-    V* X0 = reinterpret_cast<V*>(smraw);
-    V* X1 = X0 + tl;
-    V* Y0 = X1 + tl;
-    V* Y1 = Y0 + tl;
-    V* acc = Y1 + tl;
+    const ClusterSmem L{ (int)smem_len<V>(2 * tile), tile, a.pout, a.fp1.tlen, a.fp2.tlen, a.q };
+    V* sm = reinterpret_cast<V*>(smraw);
+    // X: element (s1, col) at s1 (2 w2) + col, f in columns [0, w2), g in
+    // [w2, 2 w2); Y: element (s2, col) at s2 (2 w1) + col, f in [0, w1), g in
+    // [w1, 2 w1)
+    V* X = sm + L.x();
+    V* Y = sm + L.y();
+    V* S = sm + L.scratch();
+    V* acc = sm + L.acc();
+    V* T1 = sm + L.tw1();
+    V* T1l = sm + L.tw1l();
+    V* T2 = sm + L.tw2();
+    V* T2l = sm + L.tw2l();
+    V* FW = sm + L.fw();
+    V* BW = sm + L.bw();
+    V* FT = sm + L.ft();
+    V* QT = sm + L.qt();
+    const int xw = 2 * w2, yw = 2 * w1;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const V* fr = a.f + b * a.ld_f;
     const V* gr = a.g + b * a.ld_g;
+    // the block's copies of its twiddles (loads issued together)
+    for (int e = tid; e < L.t1; e += nthr) {
+        T1[e] = __ldg(a.tw1 + e);
+        T1l[e] = __ldg(a.tw1l + e);
+    }
+    for (int e = tid; e < L.t2; e += nthr) {
+        T2[e] = __ldg(a.tw2 + e);
+        T2l[e] = __ldg(a.tw2l + e);
+    }
+    for (int e = tid; e < tile; e += nthr) {
+        // forward transpose element (rl, s2): zeta_m^{l1 s2}, l1 = c w1 + rl
+        const int rl = e / a.m2, s2f = e - rl * a.m2;
+        FW[e] = twn(a.twN, (int64_t)a.q * (c * w1 + rl) * s2f);
+        // backward transpose element (cl, l1): zeta_m^{l1 s2}, s2 = c w2 + cl
+        const int cl = e / a.m1, l1 = e - cl * a.m1;
+        BW[e] = twn(a.twN, (int64_t)a.q * l1 * (c * w2 + cl));
+    }
+    for (int e = tid; e < a.q; e += nthr) QT[e] = twn(a.twN, (int64_t)e * a.m);
     for (int e = tid; e < a.pout * tile; e += nthr) acc[e] = czero<V>();
+    __syncthreads();
     for (int r = a.r_lo; r < a.r_hi; ++r) {
         // fold (Eq. 1 inner sum, then zeta_N^{r s}) of f and g into this
-        // block's columns: element (s1, cl) at s1 w2 + cl, s = s1 m2 + c w2 + cl
+        // block's columns s = s1 m2 + c w2 + cl; the residue's twiddle of each
+        // element is kept for the unfold
         for (int e = tid; e < tile; e += nthr) {
             const int s1 = e / w2, cl = e - s1 * w2;
             const int64_t s = (int64_t)s1 * a.m2 + (int64_t)c * w2 + cl;
+            const V wrs = twn(a.twN, (int64_t)r * s);
             V af = s < a.L ? fr[s] : czero<V>(), ag = s < a.L ? gr[s] : czero<V>();
             for (int t = 1; t < a.p; ++t) {
                 const int64_t j = (int64_t)t * a.m + s;
                 if (j >= a.L) break;
-                if (r == 0) {
-                    af = cadd(af, fr[j]);
-                    ag = cadd(ag, gr[j]);
-                } else {
-                    const V w = twn(a.twN, (((int64_t)r * t) % a.q) * a.m);
-                    af = cfma(fr[j], w, af);
-                    ag = cfma(gr[j], w, ag);
-                }
+                const V w = QT[(r * t) % a.q];
+                af = cfma(fr[j], w, af);
+                ag = cfma(gr[j], w, ag);
             }
-            if (r != 0) {
-                const V w = twn(a.twN, (int64_t)r * s);
-                af = cmul(af, w);
-                ag = cmul(ag, w);
-            }
-            X0[sidx<V, true>(e)] = af;
-            X1[sidx<V, true>(e)] = ag;
+            FT[e] = wrs;
+            X[sidx<V, true>(s1 * xw + cl)] = cmul(af, wrs);
+            X[sidx<V, true>(s1 * xw + w2 + cl)] = cmul(ag, wrs);
         }
         __syncthreads();
-        // m1-point transforms of the w2 columns (Y1 as the scratch half: no
-        // other block reads it)
-        fft_smem<V, false, true>(X0, Y1, a.fp1, w2, w2, 1, a.tw1, a.tw1l, tid, nthr);
-        fft_smem<V, false, true>(X1, Y1, a.fp1, w2, w2, 1, a.tw1, a.tw1l, tid, nthr);
+        // m1-point transforms of the 2 w2 columns (f and g at once)
+        fft_smem<V, false, true, false, true>(X, S, a.fp1, xw, xw, 1, T1, T1l, tid, nthr);
         cluster.sync();
         // transpose: rows l1 = c w1 + rl of every column s2, from the block
-        // that owns s2, times zeta_m^{l1 s2} (= zeta_N^{q l1 s2}); element
-        // (s2, rl) at s2 w1 + rl
-        for (int e = tid; e < tile; e += nthr) {
-            const int rl = e / a.m2, s2 = e - rl * a.m2;
-            const int src = s2 / w2, scl = s2 - src * w2;
-            const int l1 = c * w1 + rl;
-            const V* rx0 = cluster.map_shared_rank(X0, src);
-            const V* rx1 = cluster.map_shared_rank(X1, src);
-            const int k = sidx<V, true>(l1 * w2 + scl);
-            V v0 = rx0[k], v1 = rx1[k];
-            if (l1 != 0 && s2 != 0) {
-                const V w = twn(a.twN, (int64_t)a.q * l1 * s2);
-                v0 = cmul(v0, w);
-                v1 = cmul(v1, w);
+        // that owns s2, times zeta_m^{l1 s2}.  Four elements per thread are
+        // loaded before any is stored, so the loads from the other blocks'
+        // shared memory are in flight together.
+        constexpr int U = 4;
+        for (int e0 = tid; e0 < tile; e0 += U * nthr) {
+            V v0[U], v1[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * nthr;
+                if (e < tile) {
+                    const int rl = e / a.m2, s2 = e - rl * a.m2;
+                    const int src = s2 / w2, scl = s2 - src * w2;
+                    const V* rx = cluster.map_shared_rank(X, src);
+                    const int row = (c * w1 + rl) * xw;
+                    v0[u] = rx[sidx<V, true>(row + scl)];
+                    v1[u] = rx[sidx<V, true>(row + w2 + scl)];
+                }
             }
-            Y0[sidx<V, true>(s2 * w1 + rl)] = v0;
-            Y1[sidx<V, true>(s2 * w1 + rl)] = v1;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * nthr;
+                if (e < tile) {
+                    const int rl = e / a.m2, s2 = e - rl * a.m2;
+                    const V w = FW[e];
+                    Y[sidx<V, true>(s2 * yw + rl)] = cmul(v0[u], w);
+                    Y[sidx<V, true>(s2 * yw + w1 + rl)] = cmul(v1[u], w);
+                }
+            }
         }
         // every block has read the column tiles before they are reused
         cluster.sync();
-        // m2-point transforms of the w1 rows, product (Section 2.4), inverse
-        fft_smem<V, false, true>(Y0, X0, a.fp2, w1, w1, 1, a.tw2, a.tw2l, tid, nthr);
-        fft_smem<V, false, true>(Y1, X0, a.fp2, w1, w1, 1, a.tw2, a.tw2l, tid, nthr);
+        // m2-point transforms of the 2 w1 rows, product (Section 2.4), inverse
+        fft_smem<V, false, true, false, true>(Y, S, a.fp2, yw, yw, 1, T2, T2l, tid, nthr);
         for (int e = tid; e < tile; e += nthr) {
-            const int k = sidx<V, true>(e);
-            Y0[k] = cmul(Y0[k], Y1[k]);
+            const int s2 = e / w1, rl = e - s2 * w1;
+            const int kf = sidx<V, true>(s2 * yw + rl), kg = sidx<V, true>(s2 * yw + w1 + rl);
+            Y[kf] = cmul(Y[kf], Y[kg]);
         }
         __syncthreads();
-        fft_smem<V, true, true>(Y0, X0, a.fp2, w1, w1, 1, a.tw2, a.tw2l, tid, nthr);
+        fft_smem<V, true, true, false, true>(Y, S, a.fp2, w1, yw, 1, T2, T2l, tid, nthr);
         cluster.sync();
         // transpose back: this block's columns s2 = c w2 + cl of every row l1,
-        // times conj(zeta_m^{l1 s2}); element (l1, cl) at l1 w2 + cl.  The
-        // next residue's writes to Y0 come after its first cluster barrier,
-        // which every block reaches only after this loop.
-        for (int e = tid; e < tile; e += nthr) {
-            const int cl = e / a.m1, l1 = e - cl * a.m1;
-            const int src = l1 / w1, rl = l1 - src * w1;
-            const int s2 = c * w2 + cl;
-            const V* ry0 = cluster.map_shared_rank(Y0, src);
-            V v = ry0[sidx<V, true>(s2 * w1 + rl)];
-            if (l1 != 0 && s2 != 0) v = cmulc(v, twn(a.twN, (int64_t)a.q * l1 * s2));
-            X0[sidx<V, true>(l1 * w2 + cl)] = v;
+        // times conj(zeta_m^{l1 s2}).  The next residue's writes to Y come
+        // after its first cluster barrier, which every block reaches only
+        // after this loop.
+        for (int e0 = tid; e0 < tile; e0 += U * nthr) {
+            V v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * nthr;
+                if (e < tile) {
+                    const int cl = e / a.m1, l1 = e - cl * a.m1;
+                    const int src = l1 / w1, rl = l1 - src * w1;
+                    v[u] = cluster.map_shared_rank(Y, src)[sidx<V, true>((c * w2 + cl) * yw + rl)];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * nthr;
+                if (e < tile) {
+                    const int cl = e / a.m1, l1 = e - cl * a.m1;
+                    X[sidx<V, true>(l1 * xw + cl)] = cmulc(v[u], BW[e]);
+                }
+            }
         }
         __syncthreads();
         // inverse m1-point transforms: h_r[s1 m2 + s2] of this block's columns
-        fft_smem<V, true, true>(X0, Y1, a.fp1, w2, w2, 1, a.tw1, a.tw1l, tid, nthr);
+        fft_smem<V, true, true, false, true>(X, S, a.fp1, w2, xw, 1, T1, T1l, tid, nthr);
         // unfold (Eq. 2 outer sums): output j = t m + s gets
         // conj(zeta_N^{r s}) conj(zeta_q^{r t}) h_r[s], residues in increasing r
         for (int e = tid; e < tile; e += nthr) {
             const int s1 = e / w2, cl = e - s1 * w2;
             const int64_t s = (int64_t)s1 * a.m2 + (int64_t)c * w2 + cl;
-            V hv = X0[sidx<V, true>(e)];
-            if (r != 0) hv = cmulc(hv, twn(a.twN, (int64_t)r * s));
+            const V hv = cmulc(X[sidx<V, true>(s1 * xw + cl)], FT[e]);
             for (int t = 0; t < a.pout; ++t) {
                 const int64_t j = (int64_t)t * a.m + s;
                 if (j >= a.hi) break;
                 if (j < a.lo) continue;
-                const V v = (r != 0 && t != 0) ? cmulc(hv, twn(a.twN, (((int64_t)r * t) % a.q) * a.m)) : hv;
+                const V v = t != 0 ? cmulc(hv, QT[(r * t) % a.q]) : hv;
                 acc[t * tile + e] = cadd(acc[t * tile + e], v);
             }
         }
-        // the thread that reads X0[e] here is the one that writes it in the
-        // next fold, and acc entries are per thread: no barrier needed
+        // the thread that reads X and FT[e] of element e here writes them in
+        // the next fold, and acc entries are per thread: no barrier needed
     }
     // no block leaves while another may still read its shared memory
     cluster.sync();
@@ -195,10 +262,13 @@ __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_const
 
 // ------------------------------------------------------------------ host
 
-// Bytes of dynamic shared memory of one block.
-template <typename T> static size_t cluster_smem(int64_t m, int C, int64_t pout)
+// Bytes of dynamic shared memory of one block (ClusterSmem).
+template <typename T> static size_t cluster_smem(int64_t m, int C, int64_t m1, int64_t m2, int64_t pout, int64_t q)
 {
-    return (size_t)((4 + pout) * smem_len<cx<T>>(m / C)) * sizeof(cx<T>);
+    const int64_t tile = m / C;
+    const ClusterSmem L{ (int)smem_len<cx<T>>(2 * tile), (int)tile, (int)pout, fft_plan_latency<T>(m1).tlen,
+                         fft_plan_latency<T>(m2).tlen, (int)q };
+    return (size_t)L.total() * sizeof(cx<T>);
 }
 
 // Whether a 16-block cluster of this kernel with `smem` bytes per block can
@@ -238,29 +308,32 @@ template <class V> static bool cluster16_ok(size_t smem, int thr)
     return ok;
 }
 
-// Threads of one block: one per radix-8 butterfly of the tile, 64..256.
-static int cluster_threads(int64_t tile)
+// Threads of one block: one per butterfly of a stage over both inputs'
+// tiles (radix 2 in FP64, radix 8 in FP32; fft_plan_latency), 64..256.
+template <typename T> static int cluster_threads(int64_t tile)
 {
-    int thr = (int)((tile / 8 + 31) / 32 * 32);
+    int thr = (int)(((sizeof(T) == 8 ? tile : tile / 4) + 31) / 32 * 32);
     return thr < 64 ? 64 : (thr > kMaxThreads ? kMaxThreads : thr);
 }
 
-// The cluster's shape for an m-point residue with pout output blocks: C in
-// {16, 8, 4, 2} (the largest that divides both factors and leaves tiles of at
-// least 32 elements; 16, a non-portable cluster size, only where the device
-// can hold such a cluster), m = m1 m2 with C | m1, C | m2 and m1 <= m2 as close to
-// sqrt(m) as allowed, shared memory within the per-block limit.  False when
-// none exists.
-template <typename T> bool cluster_shape(int64_t m, int64_t pout, int* Co, int64_t* m1o, int64_t* m2o)
+// The cluster's shape for an m-point residue with pout output blocks and q
+// residues: C in {16, 8, 4, 2} (the largest that divides both factors and
+// leaves tiles of at least 32 elements; 16, a non-portable cluster size,
+// only where the device can hold such a cluster), m = m1 m2 with C | m1,
+// C | m2 and m1 <= m2 as close to sqrt(m) as allowed, shared memory within
+// the per-block limit.  False when none exists.
+template <typename T> bool cluster_shape(int64_t m, int64_t pout, int64_t q, int* Co, int64_t* m1o, int64_t* m2o)
 {
     constexpr size_t kMaxSmem = 200 * 1024;
     for (int C : { 16, 8, 4, 2 }) {
-        if (m % ((int64_t)C * C) != 0 || m / C < 32 || cluster_smem<T>(m, C, pout) > kMaxSmem) continue;
-        if (C == 16 && !cluster16_ok<cx<T>>(cluster_smem<T>(m, C, pout), cluster_threads(m / C))) continue;
+        if (m % ((int64_t)C * C) != 0 || m / C < 32) continue;
         int64_t best = -1;
         for (int64_t m1 = C; m1 * m1 <= m; m1 += C)
             if (m % m1 == 0 && (m / m1) % C == 0) best = m1;
         if (best < 0) continue;
+        const size_t smem = cluster_smem<T>(m, C, best, m / best, pout, q);
+        if (smem > kMaxSmem) continue;
+        if (C == 16 && !cluster16_ok<cx<T>>(smem, cluster_threads<T>(m / C))) continue;
         *Co = C;
         *m1o = best;
         *m2o = m / best;
@@ -268,8 +341,8 @@ template <typename T> bool cluster_shape(int64_t m, int64_t pout, int* Co, int64
     }
     return false;
 }
-template bool cluster_shape<double>(int64_t, int64_t, int*, int64_t*, int64_t*);
-template bool cluster_shape<float>(int64_t, int64_t, int*, int64_t*, int64_t*);
+template bool cluster_shape<double>(int64_t, int64_t, int64_t, int*, int64_t*, int64_t*);
+template bool cluster_shape<float>(int64_t, int64_t, int64_t, int*, int64_t*, int64_t*);
 
 template <typename T>
 cudaError_t launch_conv_cluster(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t B, int64_t ld_f, int64_t ld_g,
@@ -281,21 +354,21 @@ cudaError_t launch_conv_cluster(const cx<T>* f, const cx<T>* g, cx<T>* out, int6
     const int64_t pout = (hi + m - 1) / m;
     int C = 0;
     int64_t m1 = 0, m2 = 0;
-    if (!cluster_shape<T>(m, pout, &C, &m1, &m2)) return cudaErrorInvalidValue;
+    if (!cluster_shape<T>(m, pout, q, &C, &m1, &m2)) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
     ClusterArgs<V> a;
     a.twN = tw_table<T>(q * m, &e);
     if (e != cudaSuccess) return e;
-    a.tw1 = twiddles_fft<T>(m1, false, &e);
+    a.fp1 = fft_plan_latency<T>(m1);
+    a.fp2 = fft_plan_latency<T>(m2);
+    a.tw1 = twiddles_fft_plan<T>(a.fp1, false, &e);
     if (e != cudaSuccess) return e;
-    a.tw1l = twiddles_fft<T>(m1, true, &e);
+    a.tw1l = twiddles_fft_plan<T>(a.fp1, true, &e);
     if (e != cudaSuccess) return e;
-    a.tw2 = twiddles_fft<T>(m2, false, &e);
+    a.tw2 = twiddles_fft_plan<T>(a.fp2, false, &e);
     if (e != cudaSuccess) return e;
-    a.tw2l = twiddles_fft<T>(m2, true, &e);
+    a.tw2l = twiddles_fft_plan<T>(a.fp2, true, &e);
     if (e != cudaSuccess) return e;
-    a.fp1 = fft_plan<T>(m1);
-    a.fp2 = fft_plan<T>(m2);
     a.f = f;
     a.g = g;
     a.out = out;
@@ -314,8 +387,8 @@ cudaError_t launch_conv_cluster(const cx<T>* f, const cx<T>* g, cx<T>* out, int6
     a.r_lo = (int)r_lo;
     a.r_hi = (int)r_hi;
     a.scale = (T)scale;
-    const int thr = cluster_threads(m / C);
-    const size_t smem_c = cluster_smem<T>(m, C, pout);
+    const int thr = cluster_threads<T>(m / C);
+    const size_t smem_c = cluster_smem<T>(m, C, m1, m2, pout, q);
     if (smem_c > 48 * 1024 &&
         (e = cudaFuncSetAttribute(k_conv_cluster<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c)) !=
             cudaSuccess)

@@ -73,6 +73,13 @@ template <class V, bool INV> __device__ __forceinline__ V rot90(V a)
 }
 
 template <class V> __device__ __forceinline__ V ldg_c(const V* p) { return __ldg(p); }
+// A twiddle-table entry: through the read-only cache from global memory, or
+// (TS) a plain load from a copy the kernel keeps in shared memory.
+template <class V, bool TS> __device__ __forceinline__ V ld_tw(const V* p)
+{
+    if constexpr (TS) return *p;
+    else return __ldg(p);
+}
 
 // ------------------------------------------------------------ radix DFTs
 // v[k] <- sum_j zeta_R^{+-jk} v[j], in registers.
@@ -301,27 +308,28 @@ template <class V, bool INV> __device__ __forceinline__ void lf_bfly(V& a, V& b,
     b = mkc<V>(fma(-w.sx, px, a0.x), fma(-w.sy, py, a0.y));
 }
 
-template <class V, bool INV> __device__ __forceinline__ LfW<V> lf_load(const V* __restrict__ twl, int i)
+template <class V, bool INV, bool TS = false> __device__ __forceinline__ LfW<V> lf_load(const V* __restrict__ twl, int i)
 {
-    return lf_prep<V, INV>(ldg_c(twl + i));
+    return lf_prep<V, INV>(ld_tw<V, TS>(twl + i));
 }
 
 // DFT_R of (W^r x_r), W = zeta_n^k (k < n/R), as R/2 log2 R twiddle-merged
 // butterflies; twl[e] = zeta_n^e in the form above.  Outputs in natural order.
-template <class V, int R, bool INV> struct DftLF;
+template <class V, int R, bool INV, bool TS = false> struct DftLF;
 
-template <class V, bool INV> struct DftLF<V, 2, INV> {
+template <class V, bool INV, bool TS> struct DftLF<V, 2, INV, TS> {
     static __device__ __forceinline__ void run(V* v, const V* __restrict__ twl, int k, int n)
     {
-        lf_bfly<V, INV>(v[0], v[1], lf_load<V, INV>(twl, k));
+        lf_bfly<V, INV>(v[0], v[1], lf_load<V, INV, TS>(twl, k));
     }
 };
 
-template <class V, bool INV> struct DftLF<V, 4, INV> {
+template <class V, bool INV, bool TS> struct DftLF<V, 4, INV, TS> {
     // B_r = x_r +- W^2 x_{r+2}; X_0, X_2 = B_0+ +- W B_1+; X_1, X_3 = B_0- +- (i W) B_1-
     static __device__ __forceinline__ void run(V* v, const V* __restrict__ twl, int k, int n)
     {
-        const LfW<V> w2 = lf_load<V, INV>(twl, 2 * k), w1 = lf_load<V, INV>(twl, k), wi = lf_load<V, INV>(twl, k + n / 4);
+        const LfW<V> w2 = lf_load<V, INV, TS>(twl, 2 * k), w1 = lf_load<V, INV, TS>(twl, k),
+                     wi = lf_load<V, INV, TS>(twl, k + n / 4);
         lf_bfly<V, INV>(v[0], v[2], w2);
         lf_bfly<V, INV>(v[1], v[3], w2);
         lf_bfly<V, INV>(v[0], v[1], w1);  // v0 = X0, v1 = X2
@@ -332,26 +340,26 @@ template <class V, bool INV> struct DftLF<V, 4, INV> {
     }
 };
 
-template <class V, bool INV> struct DftLF<V, 8, INV> {
+template <class V, bool INV, bool TS> struct DftLF<V, 8, INV, TS> {
     // B_r = x_r +- W^4 x_{r+4}; evens: E_r = B_r+ +- W^2 B_{r+2}+, X_0/4 = E_0+ +- W E_1+,
     // X_2/6 = E_0- +- (iW) E_1-; odds (V = zeta_8 W): F_r = B_r- +- (i W^2) B_{r+2}-,
     // X_1/5 = F_0+ +- (zeta_8 W) F_1+, X_3/7 = F_0- +- (zeta_8^3 W) F_1-
     static __device__ __forceinline__ void run(V* v, const V* __restrict__ twl, int k, int n)
     {
         const int e8 = n / 8;
-        const LfW<V> w4 = lf_load<V, INV>(twl, 4 * k);
+        const LfW<V> w4 = lf_load<V, INV, TS>(twl, 4 * k);
         lf_bfly<V, INV>(v[0], v[4], w4);
         lf_bfly<V, INV>(v[1], v[5], w4);
         lf_bfly<V, INV>(v[2], v[6], w4);
         lf_bfly<V, INV>(v[3], v[7], w4);
         // v0..3 = B+, v4..7 = B-
-        const LfW<V> w2 = lf_load<V, INV>(twl, 2 * k), w2i = lf_load<V, INV>(twl, 2 * k + 2 * e8);
+        const LfW<V> w2 = lf_load<V, INV, TS>(twl, 2 * k), w2i = lf_load<V, INV, TS>(twl, 2 * k + 2 * e8);
         lf_bfly<V, INV>(v[0], v[2], w2);   // E0+, E0-
         lf_bfly<V, INV>(v[1], v[3], w2);   // E1+, E1-
         lf_bfly<V, INV>(v[4], v[6], w2i);  // F0+, F0-
         lf_bfly<V, INV>(v[5], v[7], w2i);  // F1+, F1-
-        const LfW<V> w1 = lf_load<V, INV>(twl, k), wi = lf_load<V, INV>(twl, k + 2 * e8);
-        const LfW<V> z1 = lf_load<V, INV>(twl, k + e8), z3 = lf_load<V, INV>(twl, k + 3 * e8);
+        const LfW<V> w1 = lf_load<V, INV, TS>(twl, k), wi = lf_load<V, INV, TS>(twl, k + 2 * e8);
+        const LfW<V> z1 = lf_load<V, INV, TS>(twl, k + e8), z3 = lf_load<V, INV, TS>(twl, k + 3 * e8);
         lf_bfly<V, INV>(v[0], v[1], w1);   // X0, X4
         lf_bfly<V, INV>(v[2], v[3], wi);   // X2, X6
         lf_bfly<V, INV>(v[4], v[5], z1);   // X1, X5
@@ -439,7 +447,7 @@ template <class V> __host__ __device__ constexpr int64_t smem_len(int64_t n)
 }
 
 // tw / twl: the stage's sub-table zeta_{Ns R}^e (plain / twiddle-merged form).
-template <class V, int R, bool INV, bool SWZ>
+template <class V, int R, bool INV, bool SWZ, bool TS = false>
 __device__ __forceinline__ void fft_stage(const V* src, V* dst, int n, int ncol, int ld, int cs, int Ns,
                                           const V* __restrict__ tw, const V* __restrict__ twl, int tid, int nthr)
 {
@@ -456,15 +464,15 @@ __device__ __forceinline__ void fft_stage(const V* src, V* dst, int n, int ncol,
         const int jm = j % Ns;
         if (kLF && Ns > 1) {
             // every butterfly of the stage carries its twiddles (W = 1 when jm = 0)
-            DftLF<V, kLF ? R : 2, INV>::run(v, twl, jm, Ns * R);
+            DftLF<V, kLF ? R : 2, INV, TS>::run(v, twl, jm, Ns * R);
         } else if constexpr (R == 16) {
             if (jm != 0) {
                 // four table entries w^1, w^2, w^4, w^8 (w = zeta_{Ns R}^jm)
                 // and the other powers as their products: at most four
                 // correctly rounded factors per twiddle, a quarter of the
                 // table loads of one entry per input
-                const V w1 = ldg_c(tw + jm), w2 = ldg_c(tw + 2 * jm);
-                const V w4 = ldg_c(tw + 4 * jm), w8 = ldg_c(tw + 8 * jm);
+                const V w1 = ld_tw<V, TS>(tw + jm), w2 = ld_tw<V, TS>(tw + 2 * jm);
+                const V w4 = ld_tw<V, TS>(tw + 4 * jm), w8 = ld_tw<V, TS>(tw + 8 * jm);
                 const V w3 = cmul(w1, w2), w5 = cmul(w1, w4), w6 = cmul(w2, w4), w7 = cmul(w3, w4);
                 const V wp[8] = { czero<V>(), w1, w2, w3, w4, w5, w6, w7 };
 #pragma unroll
@@ -481,7 +489,7 @@ __device__ __forceinline__ void fft_stage(const V* src, V* dst, int n, int ncol,
             if (jm != 0) {
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    const V w = ldg_c(tw + r * jm);
+                    const V w = ld_tw<V, TS>(tw + r * jm);
                     v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
                 }
             }
@@ -501,8 +509,8 @@ __device__ __forceinline__ void fft_stage(const V* src, V* dst, int n, int ncol,
 // the last stage wrote it (buf after an even number of stages, tmp after an
 // odd one), which is returned, and the block is synchronised.  R16: the
 // kernel is built with the radix-16 stage (FP32 only); a plan that has one
-// must be run with R16.
-template <class V, bool INV, bool SWZ = false, bool R16 = false>
+// must be run with R16.  TS: tw and twl point to shared memory.
+template <class V, bool INV, bool SWZ = false, bool R16 = false, bool TS = false>
 __device__ __forceinline__ V* fft_smem_any(V* buf, V* tmp, const FftPlan& fp, int ncol, int ld, int cs,
                                            const V* __restrict__ tw, const V* __restrict__ twl, int tid, int nthr)
 {
@@ -516,14 +524,15 @@ __device__ __forceinline__ V* fft_smem_any(V* buf, V* tmp, const FftPlan& fp, in
         const V* tl = twl + fp.toff[s];
         switch (R) {
         case 16:  // FP32 plans only; compiled into the kernels that take them
-            if constexpr (R16 && sizeof(V) == 8) fft_stage<V, 16, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr);
+            if constexpr (R16 && sizeof(V) == 8)
+                fft_stage<V, 16, INV, SWZ, TS>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr);
             break;
-        case 8: fft_stage<V, 8, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
-        case 4: fft_stage<V, 4, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
-        case 2: fft_stage<V, 2, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
-        case 3: fft_stage<V, 3, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
-        case 5: fft_stage<V, 5, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
-        case 7: fft_stage<V, 7, INV, SWZ>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
+        case 8: fft_stage<V, 8, INV, SWZ, TS>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
+        case 4: fft_stage<V, 4, INV, SWZ, TS>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
+        case 2: fft_stage<V, 2, INV, SWZ, TS>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
+        case 3: fft_stage<V, 3, INV, SWZ, TS>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
+        case 5: fft_stage<V, 5, INV, SWZ, TS>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
+        case 7: fft_stage<V, 7, INV, SWZ, TS>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
         default: break;
         }
         Ns *= R;
@@ -535,11 +544,11 @@ __device__ __forceinline__ V* fft_smem_any(V* buf, V* tmp, const FftPlan& fp, in
 }
 
 // The same with the result copied back into buf when it ended in tmp.
-template <class V, bool INV, bool SWZ = false, bool R16 = false>
+template <class V, bool INV, bool SWZ = false, bool R16 = false, bool TS = false>
 __device__ __forceinline__ void fft_smem(V* buf, V* tmp, const FftPlan& fp, int ncol, int ld, int cs,
                                          const V* __restrict__ tw, const V* __restrict__ twl, int tid, int nthr)
 {
-    const V* a = fft_smem_any<V, INV, SWZ, R16>(buf, tmp, fp, ncol, ld, cs, tw, twl, tid, nthr);
+    const V* a = fft_smem_any<V, INV, SWZ, R16, TS>(buf, tmp, fp, ncol, ld, cs, tw, twl, tid, nthr);
     if (a != buf) {
         const int tot = fp.n * ncol;
         for (int e = tid; e < tot; e += nthr) {

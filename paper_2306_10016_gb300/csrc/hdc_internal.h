@@ -41,7 +41,7 @@ template <typename T> constexpr int64_t max_col_fft() { return kColMaxBytes / (2
 
 // Stages of an n-point transform: radix 8 first (16 first when r16), then 4,
 // 2, 7, 5, 3, with the offsets of their twiddle sub-tables.
-FftPlan make_fft_plan(int64_t n, bool r16 = false);
+FftPlan make_fft_plan(int64_t n, bool r16 = false, bool r2 = false);
 // The plan the kernels use for element type T.  FP32 transforms whose
 // kernel is built with radix-16 stages (r16ok) take them where they save a
 // stage: FP32 stages are bound by shared-memory passes, which radix 16 makes
@@ -50,6 +50,18 @@ FftPlan make_fft_plan(int64_t n, bool r16 = false);
 template <typename T> inline FftPlan fft_plan(int64_t n, bool r16ok = false)
 {
     return make_fft_plan(n, sizeof(T) == 4 && r16ok);
+}
+// The plan of a transform whose latency matters more than its instruction
+// count (a few blocks, each on one SM): in FP64, whose warp instructions
+// issue at half a lane per clock per SM sub-partition, a radix-8 stage keeps
+// a thread on one butterfly for about 72 FMAs while radix-2 stages, with the
+// same FMAs per point in all (3 per point and stage in the twiddle-merged
+// form), spread over four times the threads with 6 FMAs each; so FP64
+// latency plans take radix 2 throughout the power-of-two part.  FP32 keeps
+// its usual plan.
+template <typename T> inline FftPlan fft_plan_latency(int64_t n)
+{
+    return make_fft_plan(n, false, sizeof(T) == 8);
 }
 // A row transform runs n / 8 threads (at most kMaxThreads): below 16
 // kMaxThreads points a radix-16 stage would leave some of them idle, so rows
@@ -116,6 +128,8 @@ template <typename T> const cx<T>* twiddles(int64_t n, cudaError_t* err);
 // butterflies (lf = true, see lf_bfly): what fft_smem reads; of the plan
 // fft_plan<T>(n, r16ok).
 template <typename T> const cx<T>* twiddles_fft(int64_t n, bool lf, cudaError_t* err, bool r16ok = false);
+// The same tables for any plan of the transform (cached per plan shape).
+template <typename T> const cx<T>* twiddles_fft_plan(const FftPlan& fp, bool lf, cudaError_t* err);
 // zeta_N^k for the folds and unfolds: one table, or two for a large N (TwTab).
 template <typename T> TwTab<cx<T>> tw_table(int64_t N, cudaError_t* err);
 // zeta_{ma Cn}^{l c} at c ma + l (l < ma, c < Cn): the four-step twiddles of an
@@ -212,9 +226,9 @@ cudaError_t launch_unfold_real(T* out, const cx<T>* h, int64_t B, int64_t bstrid
 // ld_g, L valid elements, m-point transforms, p fold blocks, q residues)
 // from fold to unfold in one launch, the outputs [lo, hi) of each row
 // written once (times scale) to out (row stride ldo).  cluster_shape tells
-// whether an m-point residue (pout = ceil(hi / m) output blocks) fits a
-// cluster: C blocks, m = m1 m2 with C dividing both.
-template <typename T> bool cluster_shape(int64_t m, int64_t pout, int* C, int64_t* m1, int64_t* m2);
+// whether an m-point residue (pout = ceil(hi / m) output blocks, q residues)
+// fits a cluster: C blocks, m = m1 m2 with C dividing both.
+template <typename T> bool cluster_shape(int64_t m, int64_t pout, int64_t q, int* C, int64_t* m1, int64_t* m2);
 int cluster_route_mode();
 template <typename T>
 cudaError_t launch_conv_cluster(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t B, int64_t ld_f, int64_t ld_g,

@@ -37,6 +37,10 @@ __device__ int g_device_status = 0;
 // TMA-staged loads in the strided fold (hdc_set_tma).
 static std::atomic<int> g_fold_tma{ 1 };
 
+static int sm_count();
+template <typename T> static bool latency_launch(int64_t blocks);
+static int latency_threads(int64_t elems);
+
 // ------------------------------------------------------------- twiddles
 
 template <class V>
@@ -171,12 +175,13 @@ cudaError_t launch_residue_rows(const cx<T>* f, const cx<T>* g, cx<T>* h, int64_
     cudaError_t e = cudaSuccess;
     const TwTab<V> twN = tw_table<T>(q * m, &e);
     if (e != cudaSuccess) return e;
-    const V* twm = twiddles_fft<T>(m, false, &e, rows_r16(m));
+    const bool lat = latency_launch<T>(B * Dg);
+    const FftPlan fp = lat ? fft_plan_latency<T>(m) : fft_plan<T>(m, rows_r16(m));
+    const V* twm = twiddles_fft_plan<T>(fp, false, &e);
     if (e != cudaSuccess) return e;
-    const V* twml = twiddles_fft<T>(m, true, &e, rows_r16(m));
+    const V* twml = twiddles_fft_plan<T>(fp, true, &e);
     if (e != cudaSuccess) return e;
-    const FftPlan fp = fft_plan<T>(m, rows_r16(m));
-    const int thr = threads_for(m);
+    const int thr = lat ? latency_threads(m) : threads_for(m);
     const size_t smem = (size_t)(3 * smem_len<V>(m)) * sizeof(V);
     auto kern = takes_r16<V>(fp) ? k_residue_rows<V, kHas16<V>> : k_residue_rows<V, false>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
@@ -307,13 +312,35 @@ cudaError_t launch_residue_rows_multi(const cx<T>* const* xs, int nin, int op, c
 // transforms want the registers.
 template <class V> constexpr int kColBlocks = sizeof(V) == 8 ? 3 : 2;
 
+// SMs of the current device (asked once per device and remembered).
 static int sm_count()
 {
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
-                                                  cudaSuccess)
-        sms = 152;
+    constexpr int kDevs = 64;
+    static std::atomic<int> known[kDevs];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevs) return 152;
+    int sms = known[dev].load();
+    if (sms > 0) return sms;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
+    known[dev].store(sms);
     return sms;
+}
+
+// An FP64 launch of at most two waves (two blocks per SM) waits on the
+// serial FFT stages of its blocks rather than on the FP64 pipe's throughput:
+// it takes the radix-2 latency plan (fft_plan_latency: the same FMAs per
+// point, spread over four times the threads) and one thread per radix-2
+// butterfly of a stage, up to kMaxThreads.  Larger launches keep radix 8.
+template <typename T> static bool latency_launch(int64_t blocks)
+{
+    return sizeof(T) == 8 && blocks <= 4 * (int64_t)sm_count();
+}
+static int latency_threads(int64_t elems)
+{
+    int64_t t = (elems / 2 + 31) / 32 * 32;
+    if (t < 64) t = 64;
+    if (t > kMaxThreads) t = kMaxThreads;
+    return (int)t;
 }
 
 // Column tile width C.  FP32 passes wait on memory: the widest power of two
@@ -590,18 +617,20 @@ cudaError_t launch_fold_fft_cols(const ColSide<T>* sides, int nside, int64_t B, 
     cudaError_t e = cudaSuccess;
     const TwTab<V> twNf = tw_table<T>(Nf, &e);
     if (e != cudaSuccess) return e;
-    const V* twma = twiddles_fft<T>(ma, false, &e, true);
+    const int Cw = col_tile<T>(Cn, ma, col_tile_target<T>(), Dg * sides[0].lam * nside * B);
+    const bool lat = latency_launch<T>(((Cn + Cw - 1) / Cw) * Dg * sides[0].lam * nside * B);
+    const FftPlan fp = lat ? fft_plan_latency<T>(ma) : fft_plan<T>(ma, true);
+    const V* twma = twiddles_fft_plan<T>(fp, false, &e);
     if (e != cudaSuccess) return e;
-    const V* twmal = twiddles_fft<T>(ma, true, &e, true);
+    const V* twmal = twiddles_fft_plan<T>(fp, true, &e);
     if (e != cudaSuccess) return e;
-    const FftPlan fp = fft_plan<T>(ma, true);
     bool same_q = true;
     for (int i = 1; i < nside; ++i) same_q = same_q && sides[i].q == sides[0].q && sides[i].lam == 1;
     const V* tpm = (same_q && sides[0].lam == 1) ? fourstep_table<T>(post, Nf, q0, ma, Cn, &e) : nullptr;
     if (e != cudaSuccess) return e;
-    const int C = col_tile<T>(Cn, ma, col_tile_target<T>(), Dg * sides[0].lam * nside * B);
+    const int C = Cw;
     const int nct = (int)((Cn + C - 1) / C);
-    const int thr = threads_for(ma * C);
+    const int thr = lat ? latency_threads(ma * C) : threads_for(ma * C);
     const size_t smem = (size_t)(2 * smem_len<V>(ma * C)) * sizeof(V);
     ColSidesK<V> k;
     double flops = 0.0, bytes = 0.0;
@@ -659,16 +688,17 @@ cudaError_t launch_ifft_cols(cx<T>* y, int64_t B, int64_t Cn, int64_t ma, int64_
     cudaError_t e = cudaSuccess;
     const TwTab<V> twNf = tw_table<T>(Nf, &e);
     if (e != cudaSuccess) return e;
-    const V* twma = twiddles_fft<T>(ma, false, &e, true);
-    if (e != cudaSuccess) return e;
-    const V* twmal = twiddles_fft<T>(ma, true, &e, true);
-    if (e != cudaSuccess) return e;
-    const FftPlan fp = fft_plan<T>(ma, true);
-    const V* tpm = fourstep_table<T>(pre, Nf, q, ma, Cn, &e);
-    if (e != cudaSuccess) return e;
     const int C = col_tile<T>(Cn, ma, col_tile_target<T>(), D * B);
     const int nct = (int)((Cn + C - 1) / C);
-    const int thr = threads_for(ma * C);
+    const bool lat = latency_launch<T>((int64_t)nct * D * B);
+    const FftPlan fp = lat ? fft_plan_latency<T>(ma) : fft_plan<T>(ma, true);
+    const V* twma = twiddles_fft_plan<T>(fp, false, &e);
+    if (e != cudaSuccess) return e;
+    const V* twmal = twiddles_fft_plan<T>(fp, true, &e);
+    if (e != cudaSuccess) return e;
+    const V* tpm = fourstep_table<T>(pre, Nf, q, ma, Cn, &e);
+    if (e != cudaSuccess) return e;
+    const int thr = lat ? latency_threads(ma * C) : threads_for(ma * C);
     const size_t smem = (size_t)(2 * smem_len<V>(ma * C)) * sizeof(V);
     auto kern = takes_r16<V>(fp) ? k_ifft_cols<V, kHas16<V>> : k_ifft_cols<V, false>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
@@ -765,14 +795,15 @@ cudaError_t launch_ifft_unfold(cx<T>* y, cx<T>* out, int64_t B, int64_t bstride,
     cudaError_t e = cudaSuccess;
     const TwTab<V> twNf = tw_table<T>(Nf, &e);
     if (e != cudaSuccess) return e;
-    const V* twma = twiddles_fft<T>(ma, false, &e, true);
+    const bool lat = latency_launch<T>(B * nct);
+    const FftPlan fp = lat ? fft_plan_latency<T>(ma) : fft_plan<T>(ma, true);
+    const V* twma = twiddles_fft_plan<T>(fp, false, &e);
     if (e != cudaSuccess) return e;
-    const V* twmal = twiddles_fft<T>(ma, true, &e, true);
+    const V* twmal = twiddles_fft_plan<T>(fp, true, &e);
     if (e != cudaSuccess) return e;
-    const FftPlan fp = fft_plan<T>(ma, true);
     const V* tpm = fourstep_table<T>(pre, Nf, q, ma, Cn, &e);
     if (e != cudaSuccess) return e;
-    const int thr = threads_for(ma * C);
+    const int thr = lat ? latency_threads(ma * C) : threads_for(ma * C);
     const size_t smem = (size_t)(2 * smem_len<V>(ma * C)) * sizeof(V);
     auto kern = takes_r16<V>(fp) ? k_ifft_unfold_cols<V, kHas16<V>> : k_ifft_unfold_cols<V, false>;
     if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
