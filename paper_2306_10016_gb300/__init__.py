@@ -364,6 +364,7 @@ def dtype_code(t) -> int:
 
 
 _PREPARED = set()
+_CLUSTER_MODE = [1]     # the route rule of hdc_set_cluster: it decides which tables a call reads
 
 
 def _plain(a):
@@ -383,7 +384,7 @@ def _prepare(name: str, *args) -> None:
     already prepared on this device are remembered, so a repeated call costs
     a set lookup."""
     torch = _torch()
-    key = (name, torch.cuda.current_device(), tuple(_plain(a) for a in args))
+    key = (name, torch.cuda.current_device(), _CLUSTER_MODE[0], tuple(_plain(a) for a in args))
     if key in _PREPARED:
         return
     if torch.cuda.is_current_stream_capturing():
@@ -1229,6 +1230,7 @@ def set_cluster(mode) -> None:
     convolutions never (False / 0), where it is faster (True / 1, the
     default) or wherever it fits (2); same results either way."""
     _check(lib().hdc_set_cluster(int(mode)), "hdc_set_cluster")
+    _CLUSTER_MODE[0] = int(mode)
 
 
 def device_status(clear: bool = True) -> int:

@@ -1081,7 +1081,7 @@ template <typename T> static int herm_resolve(int64_t K, const int64_t* m, const
     // the outer transform runs in one column tile; the inner one, with both
     // packed rows and the pair's 2K - 1 outputs, in one block's shared memory
     if (m[0] > max_col_fft<T>() || m[1] > max_row_fft<T>()) return HDC_ERR_UNSUPPORTED_SIZE;
-    if ((3 * smem_len<cx<T>>(m[1]) + 2 * K - 1) * (int64_t)sizeof(cx<T>) > 200 * 1024)
+    if ((2 * smem_len<cx<T>>(2 * m[1]) + 2 * K - 1) * (int64_t)sizeof(cx<T>) > 200 * 1024)
         return HDC_ERR_UNSUPPORTED_SIZE;
     return HDC_OK;
 }
@@ -1115,7 +1115,7 @@ static cudaError_t run_hermitian(const cx<T>* f, const cx<T>* g, cx<T>* out, int
         const ColSide<T> sides[2] = { ColSide<T>{ f, wf, L * Cn, L * Cn, (int)ax.p, (int)ax.q, 0, 1 },
                                       ColSide<T>{ g, wg, L * Cn, L * Cn, (int)ax.p, (int)ax.q, 0, 1 } };
         HDC_TRY(launch_fold_fft_cols<T>(sides, 2, B, Cn, ax.m, ax.N, 1, 0, r0, Dg, 0, st));
-        HDC_TRY(launch_hermitian_rows<T>(wf, wg, wh, Dg * B, B, ax.m, K, ay.m, ay.p, ay.q, ax.N, ax.q, r0, st));
+        HDC_TRY(launch_hermitian_rows<T>(wf, wg, wh, Dg * B, B, ax.m, K, ay.m, ay.q, ax.N, ax.q, r0, st));
         HDC_TRY(launch_ifft_unfold<T>(wh, out, B, L * Cn, Cn, ax.m, ax.pout, ax.q, ax.N, 1, 0, ax.o * Cn,
                                       (ax.o + ax.Lw) * Cn, r0, Dg, first, last, scale, 0, st));
     }

@@ -24,6 +24,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <new>
 #include <vector>
 
@@ -51,6 +52,72 @@ template <class V> struct BConv {
 struct BItem {
     int conv, a, b, c;
 };
+
+// One (convolution, residue) of a group of fused rows of one transform size
+// (a phase-1 item with conv < 0: members [a, a + b) of the member list, m = c).
+struct BMember {
+    int conv, r;
+};
+
+// A group of k fused residue rows of one transform size m, as the k
+// columns of one tile (element s of column j at s k + j): each column's fold
+// (Eq. 1 inner sum and zeta_N^{r s}, its own convolution's inputs and
+// parameters), the m-point FFTs of all columns at once, the products, the
+// inverse FFT; column j's unscaled result to its residue's workspace row.
+// A short transform alone would keep most of the block's threads idle at
+// every stage (a 128-point FFT has 16 radix-8 butterflies); k of them fill it.
+template <class V>
+__device__ __forceinline__ void residue_rows_group(const BConv<V>* __restrict__ convs,
+                                                   const BMember* __restrict__ mem, int k, int m,
+                                                   const V* const* __restrict__ fp_, const V* const* __restrict__ gp_,
+                                                   V* ws, V* smem, int tid, int nthr)
+{
+    const int n = k * m;
+    V* sa = smem;
+    V* sb = sa + smem_len<V>(n);
+    V* sc = sb + smem_len<V>(n);
+    for (int e = tid; e < n; e += nthr) {
+        const int j = e / m, s = e - j * m;
+        const BMember mb = mem[j];
+        const BConv<V>& cv = convs[mb.conv];
+        const V* fr = fp_[mb.conv];
+        const V* gr = gp_[mb.conv];
+        const int r = mb.r;
+        V af = s < cv.L ? fr[s] : czero<V>(), ag = s < cv.L ? gr[s] : czero<V>();
+        for (int t = 1; t < cv.p; ++t) {
+            const int64_t jj = (int64_t)t * m + s;
+            if (jj >= cv.L) break;
+            if (r == 0) {
+                af = cadd(af, fr[jj]);
+                ag = cadd(ag, gr[jj]);
+            } else {
+                const V w = twn(cv.twN, (((int64_t)r * t) % cv.q) * m);
+                af = cfma(fr[jj], w, af);
+                ag = cfma(gr[jj], w, ag);
+            }
+        }
+        if (r != 0) {
+            const V w = twn(cv.twN, (int64_t)r * s);
+            af = cmul(af, w);
+            ag = cmul(ag, w);
+        }
+        sa[s * k + j] = af;
+        sb[s * k + j] = ag;
+    }
+    __syncthreads();
+    const BConv<V>& c0 = convs[mem[0].conv]; // every member has this m: same plan and tables
+    fft_smem<V, false>(sa, sc, c0.fpm, k, k, 1, c0.twm, c0.twml, tid, nthr);
+    fft_smem<V, false>(sb, sc, c0.fpm, k, k, 1, c0.twm, c0.twml, tid, nthr);
+    for (int e = tid; e < n; e += nthr) sa[e] = cmul(sa[e], sb[e]);
+    __syncthreads();
+    fft_smem<V, true>(sa, sc, c0.fpm, k, k, 1, c0.twm, c0.twml, tid, nthr);
+    for (int e = tid; e < n; e += nthr) {
+        const int j = e / m, s = e - j * m;
+        const BMember mb = mem[j];
+        (ws + convs[mb.conv].ws_off + (int64_t)mb.r * m)[s] = sa[s * k + j];
+    }
+    __syncthreads();
+}
 
 // Workspace header (the first 256 bytes): phase counters, barrier, status,
 // and the global-timer readings that split the launch into its phases: t[0]
@@ -101,7 +168,8 @@ __device__ __forceinline__ bool grid_barrier(BHeader* hd, unsigned int target, l
 template <class V>
 __global__ void __launch_bounds__(kMaxThreads)
 k_batched(const BConv<V>* __restrict__ convs, const BItem* __restrict__ it0, const BItem* __restrict__ it1,
-          const BItem* __restrict__ it2, const BItem* __restrict__ it3, int n0, int n1, int n2, int n3,
+          const BItem* __restrict__ it2, const BItem* __restrict__ it3, const BMember* __restrict__ members,
+          int n0, int n1, int n2, int n3,
           const V* const* __restrict__ fp_, const V* const* __restrict__ gp_, V* const* __restrict__ hp_, V* ws,
           BHeader* hd, long long spin_limit, int extra_arrivals)
 {
@@ -122,6 +190,10 @@ k_batched(const BConv<V>* __restrict__ convs, const BItem* __restrict__ it0, con
             __syncthreads();
             if (idx >= n) break;
             const BItem itm = items[idx];
+            if (ph == 1 && itm.conv < 0) {
+                residue_rows_group<V>(convs, members + itm.a, itm.b, itm.c, fp_, gp_, ws, smem, tid, nthr);
+                continue;
+            }
             const BConv<V>& cv = convs[itm.conv];
             V* cws = ws + cv.ws_off;
             if (ph == 0) {
@@ -181,6 +253,7 @@ struct hdc_batched {
     std::vector<int64_t> L, m, p, q, m1, m2;
     void* d_conv = nullptr;
     void* d_items[4] = { nullptr, nullptr, nullptr, nullptr };
+    void* d_members = nullptr;
     int nitems[4] = { 0, 0, 0, 0 };
     size_t ws = 0;     // bytes, header included
     size_t smem = 0;   // dynamic shared memory of the launch
@@ -221,6 +294,7 @@ void free_plan(hdc_batched* b)
 {
     if (!b) return;
     cudaFree(b->d_conv);
+    cudaFree(b->d_members);
     for (auto& p : b->d_items) cudaFree(p);
     delete b;
 }
@@ -283,22 +357,57 @@ template <typename T> int build(hdc_batched* b)
     // largest convolutions first in every phase: the tail of each phase is
     // made of small items
     std::sort(cost.begin(), cost.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    // fused residue rows of at most kGroupElems / 2 points are grouped by
+    // size, kGroupElems / m rows to an item (the group's three tiles fit the
+    // launch's shared memory)
+    const int64_t kGroupElems = kBatchedSmem / (3 * (int64_t)sizeof(V));
+    std::vector<BMember> members;
+    std::vector<std::pair<double, BItem>> rows1;
+    std::map<int, std::vector<BMember>> small;
     for (auto& ce : cost) {
         const int64_t i = ce.second;
         const BConv<V>& cv = convs[(size_t)i];
         const int ci = (int)i;
+        const double rcost = (double)cv.m * std::log2((double)cv.m + 1.0) + (double)cv.L;
         if (cv.m1) {
             for (int r = 0; r < cv.q; ++r)
                 for (int w = 0; w < 2; ++w)
                     for (int ct = 0; ct < cv.nct; ++ct) items[0].push_back({ ci, r, w, ct });
-            for (int row = 0; row < cv.q * cv.m1; ++row) items[1].push_back({ ci, row, 0, 0 });
+            for (int row = 0; row < cv.q * cv.m1; ++row)
+                rows1.push_back({ (double)cv.m2 * std::log2((double)cv.m2 + 1.0), BItem{ ci, row, 0, 0 } });
             for (int r = 0; r < cv.q; ++r)
                 for (int ct = 0; ct < cv.nct; ++ct) items[2].push_back({ ci, r, 0, ct });
+        } else if (2 * (int64_t)cv.m <= kGroupElems) {
+            for (int r = 0; r < cv.q; ++r) small[cv.m].push_back({ ci, r });
         } else {
-            for (int r = 0; r < cv.q; ++r) items[1].push_back({ ci, r, 0, 0 });
+            for (int r = 0; r < cv.q; ++r) rows1.push_back({ rcost, BItem{ ci, r, 0, 0 } });
         }
         const int nch = (cv.per + kUnfoldChunk - 1) / kUnfoldChunk;
         for (int k = 0; k < nch; ++k) items[3].push_back({ ci, k, 0, 0 });
+    }
+    for (auto& kv : small) {
+        const int m = kv.first;
+        const int kmax = (int)(kGroupElems / m);
+        const auto& v = kv.second;
+        for (size_t g0 = 0; g0 < v.size(); g0 += kmax) {
+            const int k = (int)std::min<size_t>(kmax, v.size() - g0);
+            BItem it{ -1, (int)members.size(), k, m };
+            smem = std::max(smem, (size_t)(3 * smem_len<V>((int64_t)k * m)) * sizeof(V));
+            double gc = 0.0;
+            for (int j = 0; j < k; ++j) {
+                members.push_back(v[g0 + j]);
+                gc += (double)m * std::log2((double)m + 1.0) + (double)convs[(size_t)v[g0 + j].conv].L;
+            }
+            rows1.push_back({ gc, it });
+        }
+    }
+    std::stable_sort(rows1.begin(), rows1.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    for (auto& ri : rows1) items[1].push_back(ri.second);
+    if (!members.empty()) {
+        if (cudaMalloc(&b->d_members, members.size() * sizeof(BMember)) != cudaSuccess) return HDC_ERR_ALLOC;
+        if (cudaMemcpy(b->d_members, members.data(), members.size() * sizeof(BMember), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return HDC_ERR_CUDA;
     }
     if (cudaMalloc(&b->d_conv, convs.size() * sizeof(BConv<V>)) != cudaSuccess) return HDC_ERR_ALLOC;
     if (cudaMemcpy(b->d_conv, convs.data(), convs.size() * sizeof(BConv<V>), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -357,7 +466,8 @@ int launch(hdc_batched* b, const void* const* f, const void* const* g, void* con
     const BItem* i1 = (const BItem*)b->d_items[1];
     const BItem* i2 = (const BItem*)b->d_items[2];
     const BItem* i3 = (const BItem*)b->d_items[3];
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_batched<V>, cv, i0, i1, i2, i3, b->nitems[0], b->nitems[1],
+    const BMember* mem = (const BMember*)b->d_members;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_batched<V>, cv, i0, i1, i2, i3, mem, b->nitems[0], b->nitems[1],
                                        b->nitems[2], b->nitems[3], (const V* const*)f, (const V* const*)g,
                                        (V* const*)h, data, hd, b->spin_limit, b->extra_arrivals);
     return e == cudaSuccess ? HDC_OK : HDC_ERR_CUDA;
@@ -476,12 +586,25 @@ HDC_EXPORT int hdc_batched_tune(int64_t n, const int64_t* L, int dtype, const vo
     if (n < 1 || !L || !f_host || !g_host || !h_host || !m_out || reps < 1 || max_cands < 1) return HDC_ERR_PARAM;
     if (dtype != HDC_C64 && dtype != HDC_C128) return HDC_ERR_DTYPE;
     cudaStream_t st = (cudaStream_t)stream;
-    // A class's schedule is its residue count q: every member gets its own
-    // m = nextgood(ceil(M_i / q)), so the FFT size follows each length.
+    // A class's schedule is its residue count q and a size rule: every member
+    // gets its own m >= ceil(M_i / q), either the next 2^a 3^b 5^c 7^d (the
+    // least padding) or the next 2^a or 3 2^a (more padding, but transforms
+    // of radix-8, -4 and -2 stages and at most one radix-3 one, which cost
+    // fewer FP64 instructions per point than radix 3, 5 and 7), so the FFT
+    // size follows each length.  A schedule is encoded as 2 q + rule.
     static const int64_t qs[] = { 1, 2, 3, 4, 5, 6, 8, 10, 12, 16 };
-    auto m_for = [&](int64_t Li, int64_t q) -> int64_t {
+    auto m_for = [&](int64_t Li, int64_t sched) -> int64_t {
+        const int64_t q = sched / 2;
         const int64_t M = 2 * Li - 1;
-        const int64_t m = hdc_next_good_size((M + q - 1) / q);
+        const int64_t lo = (M + q - 1) / q;
+        int64_t m = hdc_next_good_size(lo);
+        if (sched % 2) {
+            int64_t p2 = 1;
+            while (p2 < lo) p2 *= 2;
+            int64_t t3 = 3;
+            while (t3 < lo) t3 *= 2;
+            m = std::min(p2, t3);
+        }
         if (m < 1) return -1;
         const bool ok = dtype == HDC_C128 ? batched_ok<double>(m) : batched_ok<float>(m);
         return ok ? m : -1;
@@ -501,9 +624,12 @@ HDC_EXPORT int hdc_batched_tune(int64_t n, const int64_t* L, int dtype, const vo
         for (int64_t q : qs) {
             if ((int64_t)cands[k].size() >= max_cands) break;
             // q is usable when every member has an m >= 16 that the kernel supports
-            bool ok = (2 * Lmin - 1 + q - 1) / q >= 16 || q == 1;
-            for (int64_t i : members[k]) ok = ok && m_for(L[i], q) > 0;
-            if (ok) cands[k].push_back(q);
+            if (!((2 * Lmin - 1 + q - 1) / q >= 16 || q == 1)) continue;
+            for (int rule = 0; rule < 2 && (int64_t)cands[k].size() < max_cands; ++rule) {
+                bool ok = true;
+                for (int64_t i : members[k]) ok = ok && m_for(L[i], 2 * q + rule) > 0;
+                if (ok) cands[k].push_back(2 * q + rule);
+            }
         }
         if (cands[k].empty()) return HDC_ERR_UNSUPPORTED_SIZE;
         for (int64_t i : members[k]) m_out[i] = m_for(L[i], cands[k][0]);

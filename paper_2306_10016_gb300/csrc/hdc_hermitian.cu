@@ -41,7 +41,7 @@ template <class V> struct HermRowsArgs {
     V* wh;            // output rows, K values each
     int64_t B;        // problems per outer-residue block
     int64_t mx;       // rows per (outer residue, problem) block
-    int K, my, py, qy, qx, pout; // pout = ceil((3c + 1) / my) output blocks
+    int K, my, qy, qx;
     int64_t Nx, Ny;
     int r0;           // first outer residue of the pass
     typename real_of<V>::type scale; // 1 / Ny
@@ -54,16 +54,27 @@ template <class V> struct HermRowsArgs {
 // f + i g
 template <class V> __device__ __forceinline__ V pack_fg(V f, V g) { return mkc<V>(f.x - g.y, f.y + g.x); }
 
-// Element j (< 2c + 1) of the packed row z = F_s + i G_s of outer bin x:
-// stored for j >= c, mirrored with e = zeta_Nx^{2 c x} below.
+// The packed row z = F_s + i G_s of outer bin x at ky in [-c, c], times
+// zeta_Nx^{-c x} (= conj sx): stored for ky >= 0; for ky < 0 the mirror
+// rule gives conj z(-ky) zeta_Nx^{2 c x} zeta_Nx^{-c x} = conj z(-ky) sx.
 template <class V>
-__device__ __forceinline__ V herm_z(const V* F, const V* G, int64_t j, int c, V e)
+__device__ __forceinline__ V herm_z(const V* F, const V* G, int64_t ky, V sx)
 {
-    if (j >= c) return pack_fg(F[j - c], G[j - c]);
-    const V f = F[c - j], g = G[c - j];
-    return cmul(pack_fg(mkc<V>(f.x, -f.y), mkc<V>(g.x, -g.y)), e);
+    if (ky >= 0) return cmulc(pack_fg(F[ky], G[ky]), sx);
+    const V f = F[-ky], g = G[-ky];
+    return cmul(pack_fg(mkc<V>(f.x, -f.y), mkc<V>(g.x, -g.y)), sx);
 }
 
+// Shared memory: Z, the two packed rows side by side (element s of row t at
+// 2 s + t), a scratch half T of the same size (the transforms of both rows
+// run as one two-column transform), and, with several ky residues, the
+// 2c + 1 output accumulators.
+//
+// Both ky sequences are laid out cyclically (ky at ky mod Ny), so the
+// forward transform of z times zeta_Nx^{-c x} is u + i v directly and the
+// inverse transform of w1 + i w2 holds the outputs ky at ky mod Ny: the
+// phases zeta^{-c y} and zeta^{2 c y} of the window frame become index
+// shifts (a product by zeta_N^{a y} on the bins is a cyclic shift by a).
 template <class V>
 __global__ void __launch_bounds__(kMaxThreads) k_hermitian_rows(const __grid_constant__ HermRowsArgs<V> a)
 {
@@ -76,11 +87,11 @@ __global__ void __launch_bounds__(kMaxThreads) k_hermitian_rows(const __grid_con
     const int rr = (int)(blk / a.B);
     const int rx = a.r0 + rr;
     const int c = a.K - 1, my = a.my, qy = a.qy;
-    const int plen = (int)smem_len<V>(my);
-    V* z1 = reinterpret_cast<V*>(smraw);
-    V* z2 = z1 + plen;
-    V* tmp = z2 + plen;
-    V* acc = tmp + plen;                              // outputs n = c .. 3c
+    const int64_t Ny = a.Ny;
+    const int zlen = (int)smem_len<V>(2 * my);
+    V* Z = reinterpret_cast<V*>(smraw);
+    V* Tm = Z + zlen;
+    V* acc = Tm + zlen;                               // ky + c, ky in [-c, c] (qy > 1)
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int64_t row1 = blk * a.mx + l1;
     const V* F1 = a.wf + row1 * a.K;
@@ -91,55 +102,55 @@ __global__ void __launch_bounds__(kMaxThreads) k_hermitian_rows(const __grid_con
     const int64_t x1 = (int64_t)a.qx * l1 + rx, x2 = x1 + a.qx;
     const V e1 = twn(a.twNx, (2 * (int64_t)c * x1) % a.Nx), e2 = twn(a.twNx, (2 * (int64_t)c * x2) % a.Nx);
     const V s1 = twn(a.twNx, ((int64_t)c * x1) % a.Nx), s2 = twn(a.twNx, ((int64_t)c * x2) % a.Nx);
-    const int64_t n_in = 2 * (int64_t)c + 1;
-    for (int e = tid; e < 2 * c + 1; e += nthr) acc[e] = czero<V>();
+    if (qy > 1)
+        for (int e = tid; e < 2 * c + 1; e += nthr) acc[e] = czero<V>();
+    const V* Qr = nullptr;
     for (int r = 0; r < qy; ++r) {
-        // fold (Eq. 1 inner sum, then zeta_Ny^{r s}) of both packed rows
-        for (int s = tid; s < my; s += nthr) {
-            V a1 = s < n_in ? herm_z(F1, G1, s, c, e1) : czero<V>();
-            V a2 = (two && s < n_in) ? herm_z(F2, G2, s, c, e2) : czero<V>();
-            for (int t = 1; t < a.py; ++t) {
-                const int64_t j = (int64_t)t * my + s;
-                if (j >= n_in) break;
-                const V w = twn(a.twNy, (((int64_t)r * t) % qy) * my);
-                a1 = cfma(herm_z(F1, G1, j, c, e1), w, a1);
-                if (two) a2 = cfma(herm_z(F2, G2, j, c, e2), w, a2);
+        // fold (Eq. 1 inner sum, then zeta_Ny^{r s}) of both packed rows:
+        // element (s, t) of the two-column tile, thread e on row t = e & 1
+        for (int e = tid; e < 2 * my; e += nthr) {
+            const int s = e >> 1, t1 = e & 1;
+            const V* F = t1 ? F2 : F1;
+            const V* G = t1 ? G2 : G1;
+            const V sx = t1 ? s2 : s1;
+            V v = czero<V>();
+            if (!t1 || two) {
+                for (int t = 0; t < qy; ++t) {
+                    const int64_t i = (int64_t)t * my + s;
+                    int64_t ky;
+                    if (i <= c) ky = i;
+                    else if (i >= Ny - c) ky = i - Ny;
+                    else continue;
+                    const V z = herm_z(F, G, ky, sx);
+                    v = (r == 0 || t == 0) ? cadd(v, z) : cfma(z, twn(a.twNy, (((int64_t)r * t) % qy) * my), v);
+                }
+                if (r != 0) v = cmul(v, twn(a.twNy, (int64_t)r * s));
             }
-            if (r != 0) {
-                const V w = twn(a.twNy, (int64_t)r * s);
-                a1 = cmul(a1, w);
-                a2 = cmul(a2, w);
-            }
-            z1[sidx<V, true>(s)] = a1;
-            z2[sidx<V, true>(s)] = a2;
+            Z[sidx<V, true>(e)] = v;
         }
         __syncthreads();
-        fft_smem<V, false, true>(z1, tmp, a.fp, 1, 1, my, a.twm, a.twml, tid, nthr);
-        fft_smem<V, false, true>(z2, tmp, a.fp, 1, 1, my, a.twm, a.twml, tid, nthr);
-        // bins y = qy l + r: the fields u + i v of each row, their real
-        // products, packed and shifted back to the window's frame
+        // both rows' my-point transforms at once (two columns): bins
+        // y = qy l + r of u + i v per row; the real products, packed
+        fft_smem<V, false, true>(Z, Tm, a.fp, 2, 2, 1, a.twm, a.twml, tid, nthr);
         for (int l = tid; l < my; l += nthr) {
-            const int64_t y = (int64_t)qy * l + r;
-            const V py = twn(a.twNy, ((int64_t)c * y) % a.Ny);
-            const V p2 = twn(a.twNy, (2 * (int64_t)c * y) % a.Ny);
-            const int k = sidx<V, true>(l);
-            const V uv1 = cmulc(cmulc(z1[k], s1), py);
-            const V uv2 = cmulc(cmulc(z2[k], s2), py);
-            const T w1 = uv1.x * uv1.y, w2 = uv2.x * uv2.y;
-            z1[k] = cmul(mkc<V>(w1, w2), p2);
+            const V uv1 = Z[sidx<V, true>(2 * l)], uv2 = Z[sidx<V, true>(2 * l + 1)];
+            Tm[sidx<V, true>(l)] = mkc<V>(uv1.x * uv1.y, uv2.x * uv2.y);
         }
         __syncthreads();
-        fft_smem<V, true, true>(z1, tmp, a.fp, 1, 1, my, a.twm, a.twml, tid, nthr);
-        // unfold (Eq. 2 outer sums) into the outputs n in [c, 3c]
+        Qr = fft_smem_any<V, true, true>(Tm, Z, a.fp, 1, 1, my, a.twm, a.twml, tid, nthr);
+        if (qy == 1) break;                           // the outputs stay in Qr
+        // unfold (Eq. 2 outer sums): output ky at cyclic index i = ky mod Ny
         for (int s = tid; s < my; s += nthr) {
-            V hv = z1[sidx<V, true>(s)];
+            V hv = Qr[sidx<V, true>(s)];
             if (r != 0) hv = cmulc(hv, twn(a.twNy, (int64_t)r * s));
-            for (int t = 0; t < a.pout; ++t) {
-                const int64_t n = (int64_t)t * my + s;
-                if (n > 3 * (int64_t)c) break;
-                if (n < c) continue;
+            for (int t = 0; t < qy; ++t) {
+                const int64_t i = (int64_t)t * my + s;
+                int64_t ky;
+                if (i <= c) ky = i;
+                else if (i >= Ny - c) ky = i - Ny;
+                else continue;
                 const V v = (r != 0 && t != 0) ? cmulc(hv, twn(a.twNy, (((int64_t)r * t) % qy) * my)) : hv;
-                acc[n - c] = cadd(acc[n - c], v);
+                acc[ky + c] = cadd(acc[ky + c], v);
             }
         }
         __syncthreads();
@@ -148,7 +159,14 @@ __global__ void __launch_bounds__(kMaxThreads) k_hermitian_rows(const __grid_con
     // k >= 0 halves, scaled by 1 / Ny and times zeta_Nx^{2 c x}
     V* H1 = a.wh + row1 * a.K;
     for (int k = tid; k <= c; k += nthr) {
-        const V A = acc[c + k], Bm = acc[c - k];
+        V A, Bm;
+        if (qy == 1) {
+            A = Qr[sidx<V, true>(k)];
+            Bm = Qr[sidx<V, true>(k == 0 ? 0 : my - k)];
+        } else {
+            A = acc[c + k];
+            Bm = acc[c - k];
+        }
         const T h = (T)0.5 * a.scale;
         const V h1 = mkc<V>(h * (A.x + Bm.x), h * (A.y - Bm.y));
         H1[k] = cmul(h1, e1);
@@ -162,7 +180,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_hermitian_rows(const __grid_con
 
 template <typename T>
 cudaError_t launch_hermitian_rows(const cx<T>* wf, const cx<T>* wg, cx<T>* wh, int64_t nblk, int64_t B, int64_t mx,
-                                  int64_t K, int64_t my, int64_t py, int64_t qy, int64_t Nx, int64_t qx, int64_t r0,
+                                  int64_t K, int64_t my, int64_t qy, int64_t Nx, int64_t qx, int64_t r0,
                                   cudaStream_t st)
 {
     using V = cx<T>;
@@ -185,17 +203,16 @@ cudaError_t launch_hermitian_rows(const cx<T>* wf, const cx<T>* wg, cx<T>* wh, i
     a.mx = mx;
     a.K = (int)K;
     a.my = (int)my;
-    a.py = (int)py;
     a.qy = (int)qy;
     a.qx = (int)qx;
-    a.pout = (int)((3 * (K - 1) + 1 + my - 1) / my);
     a.Nx = Nx;
     a.Ny = qy * my;
     a.r0 = (int)r0;
     a.scale = (T)(1.0 / (double)(qy * my));
-    int thr = (int)((my / 8 + 31) / 32 * 32);
+    // one thread per radix-8 butterfly of the two-column transform
+    int thr = (int)((2 * my / 8 + 31) / 32 * 32);
     thr = thr < 64 ? 64 : (thr > kMaxThreads ? kMaxThreads : thr);
-    const size_t smem = (size_t)(3 * smem_len<V>(my) + 2 * K - 1) * sizeof(V);
+    const size_t smem = (size_t)(2 * smem_len<V>(2 * my) + (qy > 1 ? 2 * K - 1 : 0)) * sizeof(V);
     if (smem > 48 * 1024 &&
         (e = cudaFuncSetAttribute(k_hermitian_rows<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
             cudaSuccess)
@@ -214,9 +231,9 @@ cudaError_t launch_hermitian_rows(const cx<T>* wf, const cx<T>* wg, cx<T>* wh, i
 }
 template cudaError_t launch_hermitian_rows<double>(const cx<double>*, const cx<double>*, cx<double>*, int64_t, int64_t,
                                                    int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,
-                                                   int64_t, cudaStream_t);
+                                                   cudaStream_t);
 template cudaError_t launch_hermitian_rows<float>(const cx<float>*, const cx<float>*, cx<float>*, int64_t, int64_t,
                                                   int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,
-                                                  int64_t, cudaStream_t);
+                                                  cudaStream_t);
 
 } // namespace hdc

@@ -238,14 +238,15 @@ cudaError_t launch_conv_cluster(const cx<T>* f, const cx<T>* g, cx<T>* out, int6
 // Inner axis of the centered Hermitian 2-D convolution (K = c + 1 stored
 // ky >= 0 values per row): rows (rr, b, l) of wf / wg at ((rr B + b) mx + l) K
 // hold F_s, G_s of outer bin x = qx l + r0 + rr (Nx = qx mx points); per pair
-// of rows the packed fold and my-point transforms of every ky residue (py
-// fold blocks, qy residues), the real products, one packed inverse transform
-// and unfold of the outputs ky + 2c in [c, 3c], split by symmetry; the
+// of rows the packed fold and my-point transforms of every ky residue (qy
+// residues, ky laid out cyclically over Ny = qy my >= 3c + 1 points), the
+// real products, one packed inverse transform and unfold of the outputs
+// ky in [-c, c], split by symmetry; the
 // k >= 0 halves times zeta_Nx^{2 c x} and 1 / (qy my) go to the same rows of
 // wh.  nblk = (outer residues of the pass) x B.
 template <typename T>
 cudaError_t launch_hermitian_rows(const cx<T>* wf, const cx<T>* wg, cx<T>* wh, int64_t nblk, int64_t B, int64_t mx,
-                                  int64_t K, int64_t my, int64_t py, int64_t qy, int64_t Nx, int64_t qx, int64_t r0,
+                                  int64_t K, int64_t my, int64_t qy, int64_t Nx, int64_t qx, int64_t r0,
                                   cudaStream_t st);
 
 // In-place inverse FFT of size ma along the strided axis of y[rr][b][l][c],

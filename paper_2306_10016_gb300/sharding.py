@@ -36,6 +36,16 @@ def shard_batch(costs, world: int):
     return [sorted(x) for x in out]
 
 
+def shard_copies(costs, world: int):
+    """A job of `world` copies of a list of independent items (weak scaling:
+    the work per rank stays one list's worth) dealt out by shard_batch; per
+    rank its (copy, item) pairs in item order.  With equal copies every rank
+    gets one copy of every item."""
+    units = [(c, i) for c in range(world) for i in range(len(costs))]
+    parts = shard_batch([costs[i] for _, i in units], world)
+    return [sorted((units[k] for k in p), key=lambda u: (u[1], u[0])) for p in parts]
+
+
 def residue_ranges(q: int, world: int):
     """Contiguous residue ranges [lo, hi) of nearly equal size, one per rank
     (ranks beyond q get an empty range)."""

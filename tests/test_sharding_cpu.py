@@ -22,6 +22,19 @@ def test_shard_batch_covers_and_balances():
         assert max(loads) - min(loads) <= max(costs) + 1e-9
 
 
+def test_shard_copies_weak_scaling():
+    """N copies of the 25-size sweep over N ranks: every (copy, size) once,
+    and each rank one copy of every size (the work per rank of one sweep)."""
+    sizes = sorted([1 << k for k in range(10, 23)] + [3 << k for k in range(9, 21)])
+    costs = [sharding.model_flops(L, L, 2) for L in sizes]
+    for world in (1, 2, 4, 8):
+        parts = sharding.shard_copies(costs, world)
+        flat = sorted(u for p in parts for u in p)
+        assert flat == sorted((c, i) for c in range(world) for i in range(len(sizes)))
+        for p in parts:
+            assert [i for _, i in p] == list(range(len(sizes)))
+
+
 def test_residue_ranges_partition():
     for q in (1, 2, 5, 8, 13):
         for world in (1, 2, 3, 4, 16):
