@@ -515,19 +515,50 @@ def main():
         del fz, gz, hz, wz
 
     # --- per-size hybrid vs explicit (device time, FP64)
-    # per size, the tuned and the explicit tuple timed alternately (three
-    # rounds of 15 graph replays of one call, each after an L2 flush, as the
-    # tuner times its candidates; median)
+    def ab_times(pa, pb, f, g, h, n=45):
+        """The calls of two plans on the same data, each captured in a CUDA
+        graph with ONE shared workspace (so both run on the same addresses),
+        then replayed alternately (A B, B A, ...), each replay after an L2
+        flush, n times each; the medians."""
+        ws = torch.empty(max(1, pa.workspace_bytes, pb.workspace_bytes), dtype=torch.uint8, device=dev)
+        side = torch.cuda.Stream(dev)
+        graphs = []
+        for p_ in (pa, pb):
+            with torch.cuda.stream(side):
+                p_.execute(f, g, out=h, workspace=ws, stream=side)
+            torch.cuda.synchronize(dev)
+            gr = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gr, stream=side):
+                p_.execute(f, g, out=h, workspace=ws, stream=side)
+            gr.replay()
+            graphs.append(gr)
+        torch.cuda.synchronize(dev)
+        st = torch.cuda.current_stream(dev)
+        ev = ([], [])
+        for i in range(n):
+            # A B, then B A: the order within a pair alternates
+            for k in ((0, 1) if i % 2 == 0 else (1, 0)):
+                gr = graphs[k]
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                gr.replay()
+                e1.record(st)
+                ev[k].append((e0, e1))
+        torch.cuda.synchronize(dev)
+        del graphs
+        return [statistics.median(a.elapsed_time(b) for a, b in e) for e in ev]
+
+    # per size, the tuned and the explicit tuple on the same workspace,
+    # replayed alternately (45 each, L2 flushed before each; median)
     per_size = []
     for L, pt, pe, (f, g, h) in zip(sizes, plans64, plans_ex, ins64):
-        th, te = [], []
-        for _ in range(3):
-            th += time_sweep([pt], [(f, g, h)], 15, 1, reps=1)[2]
-            te += time_sweep([pe], [(f, g, h)], 15, 1, reps=1)[2]
+        th_ms, te_ms = ab_times(pt, pe, f, g, h)
         prm = pt.params[0]
         per_size.append({"L": L, "m": prm["m"], "p": prm["p"], "q": prm["q"], "D": prm["D"],
-                         "hybrid_ms": round(statistics.median(th), 5),
-                         "explicit_ms": round(statistics.median(te), 5),
+                         "hybrid_ms": round(th_ms, 5),
+                         "explicit_ms": round(te_ms, 5),
                          "same_tuple_as_explicit": prm["q"] == 1 and prm["m"] == pe.params[0]["m"],
                          "valid_tuples": valid_tuple_count(L), "timed_tuples": pt.timed})
     del ins64
@@ -539,6 +570,15 @@ def main():
     ms32 = rank_max(ms32)
     check_sweep("sweep_fp32", ins32)
     _, _, _, kstats32 = time_sweep(plans32, ins32, 1, 1, stats=True)
+    # per size, the tuned FP32 call alone (15 single-call replays after an L2
+    # flush each, median), with the route's launches
+    per_size32 = []
+    for L, pt, (f, g, h) in zip(sizes, plans32, ins32):
+        hdc.stats_reset()
+        _, nl, tl, _ = time_sweep([pt], [(f, g, h)], 15, 1, reps=1)
+        prm = pt.params[0]
+        per_size32.append({"L": L, "m": prm["m"], "p": prm["p"], "q": prm["q"], "D": prm["D"],
+                           "ms": round(statistics.median(tl), 5), "launches": nl // 15})
     del ins32
 
     # --- batched: 4096 convolutions, L log-uniform in [64, 65536], one
@@ -1094,6 +1134,7 @@ def main():
         "batched_fp32": batched32,
         "config1_fp64": cfg1,
         "per_size_fp64": per_size,
+        "per_size_fp32": per_size32,
         "max_rel_err": max_err,
         "roofline": roofline,
         "cpu_baseline": cpu,

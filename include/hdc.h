@@ -474,9 +474,14 @@ int hdc_tune_workspace_size(int dims, const int64_t* L, const int64_t* M,
 
 /* Time candidates on the caller's device buffers (f, g, h: batch x L;
  * workspace of hdc_tune_workspace_size) with `warmup` untimed and `reps`
- * timed runs each (median, CUDA events on `stream`; synchronises).  Axes are
- * searched one at a time, last axis first, the others held at their best so
- * far; the three fastest m of each axis are re-timed with D = 1, 2, 4, ... < q.
+ * timed runs each (median of CUDA-graph replays with the L2 evicted before
+ * each, on a private stream; more replays, up to 41, while the sample holds
+ * less than 1 ms; synchronises `stream`).  Axes are searched one at a time,
+ * last axis first, the others held at their best so far; the four fastest
+ * candidates of an axis and its explicit one are timed twice more,
+ * interleaved, and keep the median of three; the three fastest m are then
+ * re-timed with D = 1, 2, 4, ... < q; a time within 1 % of the best goes to
+ * explicit padding.
  * best[dims] receives the choice; trials (optional, cap records of dims
  * tuples each) every timed configuration, *ntrials their count. */
 int hdc_tune_convnd(int dims, const int64_t* L, const int64_t* M, int dtype,

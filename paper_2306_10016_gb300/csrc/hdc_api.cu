@@ -470,7 +470,7 @@ template <typename T> static bool use_cluster(const Axis& a, int64_t B)
     if (mode == 0 || a.m < 256) return false;
     int C = 0;
     int64_t m1 = 0, m2 = 0;
-    if (!cluster_shape<T>(a.m, a.pout, a.q, &C, &m1, &m2)) return false;
+    if (!cluster_shape<T>(a.m, a.pout, a.q, a.p, &C, &m1, &m2)) return false;
     if (B * C > (int64_t)sm_count()) return false;
     if (mode == 2) return true;
     const int64_t passes = (a.q + a.D - 1) / a.D;

@@ -45,6 +45,22 @@ namespace hdc {
 static std::atomic<int> g_cluster_route{ 1 };
 int cluster_route_mode() { return g_cluster_route.load(); }
 
+// x / d for x >= 0: a shift when d is a power of two (sh >= 0), else a
+// division (about twenty integer instructions)
+struct IDiv {
+    int d, sh;
+    __device__ __forceinline__ int div(int x) const { return sh >= 0 ? (x >> sh) : x / d; }
+};
+static IDiv make_idiv(int d)
+{
+    IDiv r{ d, -1 };
+    if (d > 0 && (d & (d - 1)) == 0) {
+        r.sh = 0;
+        while ((1 << r.sh) < d) ++r.sh;
+    }
+    return r;
+}
+
 template <class V> struct ClusterArgs {
     const V* f;
     const V* g;
@@ -61,6 +77,8 @@ template <class V> struct ClusterArgs {
     const V* tw2;             // ... of the m2-point transform
     const V* tw2l;
     FftPlan fp1, fp2;
+    IDiv dm1, dm2, dw1, dw2;  // m1, m2, m1 / C, m2 / C
+    int stage;                // the inputs are staged in shared memory
 };
 
 // Shared memory of one block (elements): the column tile X and the row tile
@@ -73,7 +91,7 @@ template <class V> struct ClusterArgs {
 // again for every residue) and zeta_q^k (q entries).  With the twiddles in
 // shared memory, a residue waits on global memory only once, in the fold.
 struct ClusterSmem {
-    int tl2, tile, pout, t1, t2, q; // tl2: elements of a two-tile buffer
+    int tl2, tile, pout, t1, t2, q, p; // tl2: elements of a two-tile buffer
     __host__ __device__ int x() const { return 0; }
     __host__ __device__ int y() const { return tl2; }
     __host__ __device__ int scratch() const { return 2 * tl2; }
@@ -85,9 +103,31 @@ struct ClusterSmem {
     __host__ __device__ int fw() const { return tw2l() + t2; }
     __host__ __device__ int bw() const { return fw() + tile; }
     __host__ __device__ int ft() const { return bw() + tile; }
-    __host__ __device__ int qt() const { return ft() + tile; }
+    __host__ __device__ int ft2() const { return ft() + tile; }
+    __host__ __device__ int in() const { return ft2() + tile; }
+    __host__ __device__ int qt() const { return in() + 2 * p * tile; } // p = 0: inputs not staged
     __host__ __device__ int total() const { return qt() + q; }
 };
+
+// Asynchronous 8- or 16-byte copy from global to shared memory (cp.async,
+// completed by this thread's cp_async_wait_all).
+template <class V> __device__ __forceinline__ void cp_async_el(V* smem, const V* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (sizeof(V) == 16)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// zeta_N^k into shared memory: by cp.async from a whole table, else (a
+// large FP32 table kept as two) computed here
+template <class V> __device__ __forceinline__ void twn_to_smem(V* dst, const TwTab<V>& t, int64_t k)
+{
+    if (t.full) cp_async_el(dst, t.full + k);
+    else *dst = twn(t, k);
+}
 
 template <class V>
 __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_constant__ ClusterArgs<V> a)
@@ -99,7 +139,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_const
     const int64_t b = blockIdx.x / C;
     const int w1 = a.m1 / C, w2 = a.m2 / C;
     const int tile = a.m / C;
-    const ClusterSmem L{ (int)smem_len<V>(2 * tile), tile, a.pout, a.fp1.tlen, a.fp2.tlen, a.q };
+    const ClusterSmem L{ (int)smem_len<V>(2 * tile), tile, a.pout, a.fp1.tlen, a.fp2.tlen, a.q, a.stage ? a.p : 0 };
     V* sm = reinterpret_cast<V*>(smraw);
     // X: element (s1, col) at s1 (2 w2) + col, f in columns [0, w2), g in
     // [w2, 2 w2); Y: element (s2, col) at s2 (2 w1) + col, f in [0, w1), g in
@@ -115,6 +155,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_const
     V* FW = sm + L.fw();
     V* BW = sm + L.bw();
     V* FT = sm + L.ft();
+    V* FT2 = sm + L.ft2();
+    V* INF = sm + L.in();           // f at t m + s, element (t, e) at t tile + e
+    V* ING = INF + a.p * tile;      // g
     V* QT = sm + L.qt();
     const int xw = 2 * w2, yw = 2 * w1;
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -131,34 +174,66 @@ __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_const
     }
     for (int e = tid; e < tile; e += nthr) {
         // forward transpose element (rl, s2): zeta_m^{l1 s2}, l1 = c w1 + rl
-        const int rl = e / a.m2, s2f = e - rl * a.m2;
+        const int rl = a.dm2.div(e), s2f = e - rl * a.m2;
         FW[e] = twn(a.twN, (int64_t)a.q * (c * w1 + rl) * s2f);
         // backward transpose element (cl, l1): zeta_m^{l1 s2}, s2 = c w2 + cl
-        const int cl = e / a.m1, l1 = e - cl * a.m1;
+        const int cl = a.dm1.div(e), l1 = e - cl * a.m1;
         BW[e] = twn(a.twN, (int64_t)a.q * l1 * (c * w2 + cl));
     }
     for (int e = tid; e < a.q; e += nthr) QT[e] = twn(a.twN, (int64_t)e * a.m);
     for (int e = tid; e < a.pout * tile; e += nthr) acc[e] = czero<V>();
+    // the elements of f and g this block folds (the same for every residue;
+    // staged unless the block's shared memory cannot hold them) and the
+    // first residue's fold twiddles zeta_N^{r s}; later residues' twiddles
+    // are copied during the residue before (cp.async), so with staged inputs
+    // no residue waits on global memory
+    for (int e = tid; e < tile; e += nthr) {
+        const int s1 = a.dw2.div(e), cl = e - s1 * w2;
+        const int64_t s = (int64_t)s1 * a.m2 + (int64_t)c * w2 + cl;
+        if (a.stage)
+            for (int t = 0; t < a.p; ++t) {
+                const int64_t j = (int64_t)t * a.m + s;
+                INF[t * tile + e] = j < a.L ? fr[j] : czero<V>();
+                ING[t * tile + e] = j < a.L ? gr[j] : czero<V>();
+            }
+        twn_to_smem(FT + e, a.twN, (int64_t)a.r_lo * s);
+    }
+    cp_async_wait_all();
     __syncthreads();
     for (int r = a.r_lo; r < a.r_hi; ++r) {
+        // this residue's twiddles (FTc) and the next one's (FTn); a thread
+        // reads only the entries it copied itself
+        V* FTc = ((r - a.r_lo) & 1) ? FT2 : FT;
+        V* FTn = ((r - a.r_lo) & 1) ? FT : FT2;
+        cp_async_wait_all();
+        const int rq = r % a.q;
         // fold (Eq. 1 inner sum, then zeta_N^{r s}) of f and g into this
-        // block's columns s = s1 m2 + c w2 + cl; the residue's twiddle of each
-        // element is kept for the unfold
+        // block's columns s = s1 m2 + c w2 + cl
         for (int e = tid; e < tile; e += nthr) {
-            const int s1 = e / w2, cl = e - s1 * w2;
+            const int s1 = a.dw2.div(e), cl = e - s1 * w2;
             const int64_t s = (int64_t)s1 * a.m2 + (int64_t)c * w2 + cl;
-            const V wrs = twn(a.twN, (int64_t)r * s);
-            V af = s < a.L ? fr[s] : czero<V>(), ag = s < a.L ? gr[s] : czero<V>();
+            const V wrs = FTc[e];
+            V af, ag;
+            if (a.stage) {
+                af = INF[e];
+                ag = ING[e];
+            } else {
+                af = s < a.L ? fr[s] : czero<V>();
+                ag = s < a.L ? gr[s] : czero<V>();
+            }
+            int qi = 0;                  // (r t) mod q
             for (int t = 1; t < a.p; ++t) {
                 const int64_t j = (int64_t)t * a.m + s;
                 if (j >= a.L) break;
-                const V w = QT[(r * t) % a.q];
-                af = cfma(fr[j], w, af);
-                ag = cfma(gr[j], w, ag);
+                qi += rq;
+                if (qi >= a.q) qi -= a.q;
+                const V w = QT[qi];
+                af = cfma(a.stage ? INF[t * tile + e] : fr[j], w, af);
+                ag = cfma(a.stage ? ING[t * tile + e] : gr[j], w, ag);
             }
-            FT[e] = wrs;
             X[sidx<V, true>(s1 * xw + cl)] = cmul(af, wrs);
             X[sidx<V, true>(s1 * xw + w2 + cl)] = cmul(ag, wrs);
+            if (r + 1 < a.r_hi) twn_to_smem(FTn + e, a.twN, (int64_t)(r + 1) * s);
         }
         __syncthreads();
         // m1-point transforms of the 2 w2 columns (f and g at once)
@@ -175,8 +250,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_const
             for (int u = 0; u < U; ++u) {
                 const int e = e0 + u * nthr;
                 if (e < tile) {
-                    const int rl = e / a.m2, s2 = e - rl * a.m2;
-                    const int src = s2 / w2, scl = s2 - src * w2;
+                    const int rl = a.dm2.div(e), s2 = e - rl * a.m2;
+                    const int src = a.dw2.div(s2), scl = s2 - src * w2;
                     const V* rx = cluster.map_shared_rank(X, src);
                     const int row = (c * w1 + rl) * xw;
                     v0[u] = rx[sidx<V, true>(row + scl)];
@@ -187,19 +262,21 @@ __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_const
             for (int u = 0; u < U; ++u) {
                 const int e = e0 + u * nthr;
                 if (e < tile) {
-                    const int rl = e / a.m2, s2 = e - rl * a.m2;
+                    const int rl = a.dm2.div(e), s2 = e - rl * a.m2;
                     const V w = FW[e];
                     Y[sidx<V, true>(s2 * yw + rl)] = cmul(v0[u], w);
                     Y[sidx<V, true>(s2 * yw + w1 + rl)] = cmul(v1[u], w);
                 }
             }
         }
-        // every block has read the column tiles before they are reused
-        cluster.sync();
+        // no cluster barrier here: this block's column tiles X are next
+        // written by the transpose back, after the barrier below, which every
+        // block reaches only after its own forward transpose
+        __syncthreads();
         // m2-point transforms of the 2 w1 rows, product (Section 2.4), inverse
         fft_smem<V, false, true, false, true>(Y, S, a.fp2, yw, yw, 1, T2, T2l, tid, nthr);
         for (int e = tid; e < tile; e += nthr) {
-            const int s2 = e / w1, rl = e - s2 * w1;
+            const int s2 = a.dw1.div(e), rl = e - s2 * w1;
             const int kf = sidx<V, true>(s2 * yw + rl), kg = sidx<V, true>(s2 * yw + w1 + rl);
             Y[kf] = cmul(Y[kf], Y[kg]);
         }
@@ -216,8 +293,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_const
             for (int u = 0; u < U; ++u) {
                 const int e = e0 + u * nthr;
                 if (e < tile) {
-                    const int cl = e / a.m1, l1 = e - cl * a.m1;
-                    const int src = l1 / w1, rl = l1 - src * w1;
+                    const int cl = a.dm1.div(e), l1 = e - cl * a.m1;
+                    const int src = a.dw1.div(l1), rl = l1 - src * w1;
                     v[u] = cluster.map_shared_rank(Y, src)[sidx<V, true>((c * w2 + cl) * yw + rl)];
                 }
             }
@@ -225,7 +302,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_const
             for (int u = 0; u < U; ++u) {
                 const int e = e0 + u * nthr;
                 if (e < tile) {
-                    const int cl = e / a.m1, l1 = e - cl * a.m1;
+                    const int cl = a.dm1.div(e), l1 = e - cl * a.m1;
                     X[sidx<V, true>(l1 * xw + cl)] = cmulc(v[u], BW[e]);
                 }
             }
@@ -236,25 +313,30 @@ __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_const
         // unfold (Eq. 2 outer sums): output j = t m + s gets
         // conj(zeta_N^{r s}) conj(zeta_q^{r t}) h_r[s], residues in increasing r
         for (int e = tid; e < tile; e += nthr) {
-            const int s1 = e / w2, cl = e - s1 * w2;
+            const int s1 = a.dw2.div(e), cl = e - s1 * w2;
             const int64_t s = (int64_t)s1 * a.m2 + (int64_t)c * w2 + cl;
-            const V hv = cmulc(X[sidx<V, true>(s1 * xw + cl)], FT[e]);
+            const V hv = cmulc(X[sidx<V, true>(s1 * xw + cl)], FTc[e]);
+            int qi = 0;                  // (r t) mod q
             for (int t = 0; t < a.pout; ++t) {
                 const int64_t j = (int64_t)t * a.m + s;
                 if (j >= a.hi) break;
+                if (t != 0) {
+                    qi += rq;
+                    if (qi >= a.q) qi -= a.q;
+                }
                 if (j < a.lo) continue;
-                const V v = t != 0 ? cmulc(hv, QT[(r * t) % a.q]) : hv;
+                const V v = t != 0 ? cmulc(hv, QT[qi]) : hv;
                 acc[t * tile + e] = cadd(acc[t * tile + e], v);
             }
         }
-        // the thread that reads X and FT[e] of element e here writes them in
+        // the thread that reads X and FTc[e] of element e here writes them in
         // the next fold, and acc entries are per thread: no barrier needed
     }
     // no block leaves while another may still read its shared memory
     cluster.sync();
     for (int t = 0; t < a.pout; ++t)
         for (int e = tid; e < tile; e += nthr) {
-            const int s1 = e / w2, cl = e - s1 * w2;
+            const int s1 = a.dw2.div(e), cl = e - s1 * w2;
             const int64_t j = (int64_t)t * a.m + (int64_t)s1 * a.m2 + (int64_t)c * w2 + cl;
             if (j >= a.lo && j < a.hi) a.out[b * a.ldo + (j - a.lo)] = cscale(acc[t * tile + e], a.scale);
         }
@@ -263,11 +345,12 @@ __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_const
 // ------------------------------------------------------------------ host
 
 // Bytes of dynamic shared memory of one block (ClusterSmem).
-template <typename T> static size_t cluster_smem(int64_t m, int C, int64_t m1, int64_t m2, int64_t pout, int64_t q)
+template <typename T>
+static size_t cluster_smem(int64_t m, int C, int64_t m1, int64_t m2, int64_t pout, int64_t q, int64_t p)
 {
     const int64_t tile = m / C;
     const ClusterSmem L{ (int)smem_len<cx<T>>(2 * tile), (int)tile, (int)pout, fft_plan_latency<T>(m1).tlen,
-                         fft_plan_latency<T>(m2).tlen, (int)q };
+                         fft_plan_latency<T>(m2).tlen, (int)q, (int)p };
     return (size_t)L.total() * sizeof(cx<T>);
 }
 
@@ -322,7 +405,8 @@ template <typename T> static int cluster_threads(int64_t tile)
 // only where the device can hold such a cluster), m = m1 m2 with C | m1,
 // C | m2 and m1 <= m2 as close to sqrt(m) as allowed, shared memory within
 // the per-block limit.  False when none exists.
-template <typename T> bool cluster_shape(int64_t m, int64_t pout, int64_t q, int* Co, int64_t* m1o, int64_t* m2o)
+template <typename T>
+bool cluster_shape(int64_t m, int64_t pout, int64_t q, int64_t p, int* Co, int64_t* m1o, int64_t* m2o, bool* stage)
 {
     constexpr size_t kMaxSmem = 200 * 1024;
     for (int C : { 16, 8, 4, 2 }) {
@@ -331,18 +415,25 @@ template <typename T> bool cluster_shape(int64_t m, int64_t pout, int64_t q, int
         for (int64_t m1 = C; m1 * m1 <= m; m1 += C)
             if (m % m1 == 0 && (m / m1) % C == 0) best = m1;
         if (best < 0) continue;
-        const size_t smem = cluster_smem<T>(m, C, best, m / best, pout, q);
+        // the inputs staged in shared memory where they fit
+        bool stg = true;
+        size_t smem = cluster_smem<T>(m, C, best, m / best, pout, q, p);
+        if (smem > kMaxSmem) {
+            stg = false;
+            smem = cluster_smem<T>(m, C, best, m / best, pout, q, 0);
+        }
         if (smem > kMaxSmem) continue;
         if (C == 16 && !cluster16_ok<cx<T>>(smem, cluster_threads<T>(m / C))) continue;
         *Co = C;
         *m1o = best;
         *m2o = m / best;
+        if (stage) *stage = stg;
         return true;
     }
     return false;
 }
-template bool cluster_shape<double>(int64_t, int64_t, int64_t, int*, int64_t*, int64_t*);
-template bool cluster_shape<float>(int64_t, int64_t, int64_t, int*, int64_t*, int64_t*);
+template bool cluster_shape<double>(int64_t, int64_t, int64_t, int64_t, int*, int64_t*, int64_t*, bool*);
+template bool cluster_shape<float>(int64_t, int64_t, int64_t, int64_t, int*, int64_t*, int64_t*, bool*);
 
 template <typename T>
 cudaError_t launch_conv_cluster(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t B, int64_t ld_f, int64_t ld_g,
@@ -354,7 +445,8 @@ cudaError_t launch_conv_cluster(const cx<T>* f, const cx<T>* g, cx<T>* out, int6
     const int64_t pout = (hi + m - 1) / m;
     int C = 0;
     int64_t m1 = 0, m2 = 0;
-    if (!cluster_shape<T>(m, pout, q, &C, &m1, &m2)) return cudaErrorInvalidValue;
+    bool stage = false;
+    if (!cluster_shape<T>(m, pout, q, p, &C, &m1, &m2, &stage)) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
     ClusterArgs<V> a;
     a.twN = tw_table<T>(q * m, &e);
@@ -387,8 +479,13 @@ cudaError_t launch_conv_cluster(const cx<T>* f, const cx<T>* g, cx<T>* out, int6
     a.r_lo = (int)r_lo;
     a.r_hi = (int)r_hi;
     a.scale = (T)scale;
+    a.dm1 = make_idiv((int)m1);
+    a.dm2 = make_idiv((int)m2);
+    a.dw1 = make_idiv((int)(m1 / C));
+    a.dw2 = make_idiv((int)(m2 / C));
+    a.stage = stage ? 1 : 0;
     const int thr = cluster_threads<T>(m / C);
-    const size_t smem_c = cluster_smem<T>(m, C, m1, m2, pout, q);
+    const size_t smem_c = cluster_smem<T>(m, C, m1, m2, pout, q, stage ? p : 0);
     if (smem_c > 48 * 1024 &&
         (e = cudaFuncSetAttribute(k_conv_cluster<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c)) !=
             cudaSuccess)

@@ -435,7 +435,7 @@ struct FftPlan {
 template <class V, bool SWZ> __device__ __forceinline__ int sidx(int x)
 {
     constexpr int S = 128 / (int)sizeof(V);
-    return SWZ ? x ^ ((x / S) & (S - 1)) : x;
+    return SWZ ? x ^ (int)(((unsigned)x / (unsigned)S) & (unsigned)(S - 1)) : x;
 }
 
 // shared-memory elements a buffer of n logical elements occupies (whole bank
@@ -447,21 +447,25 @@ template <class V> __host__ __device__ constexpr int64_t smem_len(int64_t n)
 }
 
 // tw / twl: the stage's sub-table zeta_{Ns R}^e (plain / twiddle-merged form).
+// csh / nsh: log2 of ncol / Ns when it is a power of two, else -1 (the
+// index arithmetic then takes shifts and masks instead of divisions, which
+// cost about twenty integer instructions each per butterfly).
 template <class V, int R, bool INV, bool SWZ, bool TS = false>
-__device__ __forceinline__ void fft_stage(const V* src, V* dst, int n, int ncol, int ld, int cs, int Ns,
-                                          const V* __restrict__ tw, const V* __restrict__ twl, int tid, int nthr)
+__device__ __forceinline__ void fft_stage(const V* src, V* dst, int n, int ncol, int ld, int cs, int Ns, int csh,
+                                          int nsh, const V* __restrict__ tw, const V* __restrict__ twl, int tid,
+                                          int nthr)
 {
     constexpr bool kLF = (R == 2 || R == 4 || R == 8);
     const int nb = n / R;
     const int total = nb * ncol;
     for (int b = tid; b < total; b += nthr) {
-        const int j = b / ncol;
+        const int j = csh >= 0 ? (b >> csh) : b / ncol;
         const int c = b - j * ncol;
         const int base = c * cs;
         V v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = src[sidx<V, SWZ>(base + (j + r * nb) * ld)];
-        const int jm = j % Ns;
+        const int jm = nsh >= 0 ? (j & (Ns - 1)) : j % Ns;
         if (kLF && Ns > 1) {
             // every butterfly of the stage carries its twiddles (W = 1 when jm = 0)
             DftLF<V, kLF ? R : 2, INV, TS>::run(v, twl, jm, Ns * R);
@@ -514,7 +518,8 @@ template <class V, bool INV, bool SWZ = false, bool R16 = false, bool TS = false
 __device__ __forceinline__ V* fft_smem_any(V* buf, V* tmp, const FftPlan& fp, int ncol, int ld, int cs,
                                            const V* __restrict__ tw, const V* __restrict__ twl, int tid, int nthr)
 {
-    int Ns = 1;
+    int Ns = 1, nsh = 0;
+    const int csh = (ncol & (ncol - 1)) == 0 ? __ffs(ncol) - 1 : -1;
     const int n = fp.n;
     V* a = buf;
     V* b = tmp;
@@ -525,17 +530,18 @@ __device__ __forceinline__ V* fft_smem_any(V* buf, V* tmp, const FftPlan& fp, in
         switch (R) {
         case 16:  // FP32 plans only; compiled into the kernels that take them
             if constexpr (R16 && sizeof(V) == 8)
-                fft_stage<V, 16, INV, SWZ, TS>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr);
+                fft_stage<V, 16, INV, SWZ, TS>(a, b, n, ncol, ld, cs, Ns, csh, nsh, ts, tl, tid, nthr);
             break;
-        case 8: fft_stage<V, 8, INV, SWZ, TS>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
-        case 4: fft_stage<V, 4, INV, SWZ, TS>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
-        case 2: fft_stage<V, 2, INV, SWZ, TS>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
-        case 3: fft_stage<V, 3, INV, SWZ, TS>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
-        case 5: fft_stage<V, 5, INV, SWZ, TS>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
-        case 7: fft_stage<V, 7, INV, SWZ, TS>(a, b, n, ncol, ld, cs, Ns, ts, tl, tid, nthr); break;
+        case 8: fft_stage<V, 8, INV, SWZ, TS>(a, b, n, ncol, ld, cs, Ns, csh, nsh, ts, tl, tid, nthr); break;
+        case 4: fft_stage<V, 4, INV, SWZ, TS>(a, b, n, ncol, ld, cs, Ns, csh, nsh, ts, tl, tid, nthr); break;
+        case 2: fft_stage<V, 2, INV, SWZ, TS>(a, b, n, ncol, ld, cs, Ns, csh, nsh, ts, tl, tid, nthr); break;
+        case 3: fft_stage<V, 3, INV, SWZ, TS>(a, b, n, ncol, ld, cs, Ns, csh, nsh, ts, tl, tid, nthr); break;
+        case 5: fft_stage<V, 5, INV, SWZ, TS>(a, b, n, ncol, ld, cs, Ns, csh, nsh, ts, tl, tid, nthr); break;
+        case 7: fft_stage<V, 7, INV, SWZ, TS>(a, b, n, ncol, ld, cs, Ns, csh, nsh, ts, tl, tid, nthr); break;
         default: break;
         }
         Ns *= R;
+        nsh = (nsh >= 0 && (R & (R - 1)) == 0) ? nsh + __ffs(R) - 1 : -1;
         V* t = a;
         a = b;
         b = t;

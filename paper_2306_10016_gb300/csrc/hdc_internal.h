@@ -226,9 +226,12 @@ cudaError_t launch_unfold_real(T* out, const cx<T>* h, int64_t B, int64_t bstrid
 // ld_g, L valid elements, m-point transforms, p fold blocks, q residues)
 // from fold to unfold in one launch, the outputs [lo, hi) of each row
 // written once (times scale) to out (row stride ldo).  cluster_shape tells
-// whether an m-point residue (pout = ceil(hi / m) output blocks, q residues)
-// fits a cluster: C blocks, m = m1 m2 with C dividing both.
-template <typename T> bool cluster_shape(int64_t m, int64_t pout, int64_t q, int* C, int64_t* m1, int64_t* m2);
+// whether an m-point residue (pout = ceil(hi / m) output blocks, q residues,
+// p fold blocks) fits a cluster: C blocks, m = m1 m2 with C dividing both;
+// *stage (optional): the inputs fit in shared memory too.
+template <typename T>
+bool cluster_shape(int64_t m, int64_t pout, int64_t q, int64_t p, int* C, int64_t* m1, int64_t* m2,
+                   bool* stage = nullptr);
 int cluster_route_mode();
 template <typename T>
 cudaError_t launch_conv_cluster(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t B, int64_t ld_f, int64_t ld_g,

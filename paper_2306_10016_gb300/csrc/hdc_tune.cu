@@ -352,6 +352,9 @@ int resolve_M_uneq(int dims, const int64_t* Lf, const int64_t* Lg, const int64_t
 // Eager timing would add the host's launch gaps to small problems and keep
 // their data in L2, which favoured tuples the replayed step then ran slower.
 // call(s) enqueues the convolution on stream s.  < 0 if a call fails.
+constexpr double kMinSampleMs = 1.0;
+constexpr int kMaxReps = 41;
+
 template <class CallFn> double median_ms(CallFn call, int warmup, int reps, cudaStream_t st)
 {
     // a search may allocate: the candidates' twiddle tables are made as the
@@ -378,19 +381,32 @@ template <class CallFn> double median_ms(CallFn call, int warmup, int reps, cuda
     }
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) goto done;
     if (cudaGraphLaunch(exec, cs) != cudaSuccess) goto done;   // the first replay uploads the graph
-    for (int r = 0; r < reps; ++r) {
-        if (cudaMemsetAsync(flush, r & 0xff, fbytes, cs) != cudaSuccess) break;
-        cudaEventRecord(e0, cs);
-        if (cudaGraphLaunch(exec, cs) != cudaSuccess) break;
-        cudaEventRecord(e1, cs);
-        if (cudaEventSynchronize(e1) != cudaSuccess) break;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        ts.push_back(ms);
-    }
-    if ((int)ts.size() == reps && reps > 0) {
-        std::sort(ts.begin(), ts.end());
-        res = ts[ts.size() / 2];
+    // `reps` replays, then more (up to kMaxReps) until about kMinSampleMs of
+    // replays are in the sample: a 30 us call timed 5 times is a 0.15 ms
+    // sample, whose median moves by a few percent from run to run
+    {
+        int want = reps;
+        for (int r = 0; r < want; ++r) {
+            if (cudaMemsetAsync(flush, r & 0xff, fbytes, cs) != cudaSuccess) break;
+            cudaEventRecord(e0, cs);
+            if (cudaGraphLaunch(exec, cs) != cudaSuccess) break;
+            cudaEventRecord(e1, cs);
+            if (cudaEventSynchronize(e1) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ts.push_back(ms);
+            if (r + 1 == reps && reps > 0) {
+                std::vector<float> tmp(ts);
+                std::sort(tmp.begin(), tmp.end());
+                const double med = tmp[tmp.size() / 2];
+                if (med > 0.0 && med * reps < kMinSampleMs)
+                    want = (int)std::min<double>(kMaxReps, std::ceil(kMinSampleMs / med));
+            }
+        }
+        if ((int)ts.size() == want && want > 0) {
+            std::sort(ts.begin(), ts.end());
+            res = ts[ts.size() / 2];
+        }
     }
 done:
     cudaStreamSynchronize(cs);
@@ -509,6 +525,32 @@ int separable_search(int dims, const std::vector<Tup>* c, TimeFn time, Tup* best
         }
         if (timed.empty()) return HDC_ERR_CUDA;
         std::sort(timed.begin(), timed.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+        // the leaders and the explicit candidate are timed twice more,
+        // interleaved, and keep the median of their three times: a drift of
+        // the clock or of the memory system during the search then cannot
+        // decide between them
+        {
+            std::vector<size_t> again;
+            for (size_t k = 0; k < timed.size(); ++k)
+                if (k < 4 || is_explicit(timed[k].second)) again.push_back(k);
+            std::vector<std::vector<double>> smp(again.size());
+            for (size_t j = 0; j < again.size(); ++j) smp[j].push_back(timed[again[j]].first);
+            for (int round = 0; round < 2; ++round)
+                for (size_t j = 0; j < again.size(); ++j) {
+                    Tup t[HDC_MAX_DIMS];
+                    for (int i = 0; i < dims; ++i) t[i] = cur[i];
+                    t[ax] = timed[again[j]].second;
+                    const double ms = time(t);
+                    if (ms < 0) continue;
+                    record(t, ms);
+                    smp[j].push_back(ms);
+                }
+            for (size_t j = 0; j < again.size(); ++j) {
+                std::sort(smp[j].begin(), smp[j].end());
+                timed[again[j]].first = smp[j][(smp[j].size() - 1) / 2];
+            }
+            std::sort(timed.begin(), timed.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+        }
         Tup bax = timed[0].second;
         double bms = timed[0].first;
         for (size_t k = 0; k < timed.size() && k < 3; ++k) {
