@@ -79,6 +79,7 @@ template <class V> struct ClusterArgs {
     FftPlan fp1, fp2;
     IDiv dm1, dm2, dw1, dw2;  // m1, m2, m1 / C, m2 / C
     int stage;                // the inputs are staged in shared memory
+    int lg1, lg2;             // log2 m1, log2 m2 (the shuffle transforms)
 };
 
 // Shared memory of one block (elements): the column tile X and the row tile
@@ -129,7 +130,82 @@ template <class V> __device__ __forceinline__ void twn_to_smem(V* dst, const TwT
     else *dst = twn(t, k);
 }
 
-template <class V>
+// n-point transforms (n = 2^lg <= 32) held one point per lane by groups
+// of n consecutive lanes, with no block barrier: radix-2 stages take the
+// partner's value (point i ^ h) by a warp shuffle, and every lane of the
+// warp must take part.  twl: the packed table of the n-point radix-2 plan
+// in the twiddle-merged form (the stage of span h = 2^s >= 2 at offset
+// 2^{s+1} - 4, entry k = zeta_{2h}^k).
+//
+// Decimation in time: lane i enters with x[bitrev(i)] and leaves with
+// X[i]; at span h each lane forms its own output a + w b (lower lane) or
+// a - w b (upper lane) of its pair, w = zeta_{2h}^{i mod h}: 4 FMAs.
+template <class V, bool INV> __device__ __forceinline__ V warp_dit(V x, int i, int lg, const V* twl)
+{
+    using T = typename real_of<V>::type;
+    for (int st = 0; st < lg; ++st) {
+        const int h = 1 << st;
+        V y;
+        y.x = __shfl_xor_sync(0xffffffffu, x.x, h);
+        y.y = __shfl_xor_sync(0xffffffffu, x.y, h);
+        const bool up = (i & h) != 0;
+        const V a = up ? y : x, b = up ? x : y;
+        if (st == 0) {
+            const T sg = up ? (T)-1 : (T)1;
+            x = mkc<V>(fma(sg, b.x, a.x), fma(sg, b.y, a.y));
+        } else {
+            const LfW<V> w = lf_load<V, INV, true>(twl + ((2 << st) - 4), i & (h - 1));
+            const T ux = INV ? fma(w.tt, b.y, b.x) : fma(-w.tt, b.y, b.x);
+            const T uy = INV ? fma(-w.tt, b.x, b.y) : fma(w.tt, b.x, b.y);
+            const T px = w.f1 ? uy : ux;
+            const T py = w.f1 ? ux : uy;
+            x = mkc<V>(fma(flip_sign_if(w.sx, up), px, a.x), fma(flip_sign_if(w.sy, up), py, a.y));
+        }
+    }
+    return x;
+}
+
+// Decimation in frequency: lane i enters with x[i] and leaves with
+// X[bitrev(i)]; at span h the lower lane of a pair keeps a + b and the upper
+// one (a - b) w, w = zeta_{2h}^{i mod h} (w = 1 for the lower lane, so both
+// run the same 6 FP64 instructions).
+template <class V, bool INV> __device__ __forceinline__ V warp_dif(V x, int i, int lg, const V* twl)
+{
+    using T = typename real_of<V>::type;
+    for (int st = lg - 1; st >= 0; --st) {
+        const int h = 1 << st;
+        V y;
+        y.x = __shfl_xor_sync(0xffffffffu, x.x, h);
+        y.y = __shfl_xor_sync(0xffffffffu, x.y, h);
+        const bool up = (i & h) != 0;
+        const V a = up ? y : x, b = up ? x : y;
+        const T sg = up ? (T)-1 : (T)1;
+        const V d = mkc<V>(fma(sg, b.x, a.x), fma(sg, b.y, a.y));
+        if (st == 0) {
+            x = d;
+        } else {
+            LfW<V> w;
+            if (up) {
+                w = lf_load<V, INV, true>(twl + ((2 << st) - 4), i & (h - 1));
+            } else {
+                w.sx = (T)1;
+                w.sy = (T)1;
+                w.tt = (T)0;
+                w.f1 = false;
+            }
+            const T ux = INV ? fma(w.tt, d.y, d.x) : fma(-w.tt, d.y, d.x);
+            const T uy = INV ? fma(-w.tt, d.x, d.y) : fma(w.tt, d.x, d.y);
+            const T px = w.f1 ? uy : ux;
+            const T py = w.f1 ? ux : uy;
+            x = mkc<V>(w.sx * px, w.sy * py);
+        }
+    }
+    return x;
+}
+
+// W: the m1- and m2-point transforms (powers of two up to 32) by warp
+// shuffles (warp_cols_fft) instead of the shared-memory stages.
+template <class V, bool W>
 __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_constant__ ClusterArgs<V> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -160,6 +236,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_const
     V* ING = INF + a.p * tile;      // g
     V* QT = sm + L.qt();
     const int xw = 2 * w2, yw = 2 * w1;
+    const int lgC = __ffs(C) - 1, lgw1 = a.lg1 - lgC, lgw2 = a.lg2 - lgC; // C, m1, m2: powers of two (W)
     const int tid = threadIdx.x, nthr = blockDim.x;
     const V* fr = a.f + b * a.ld_f;
     const V* gr = a.g + b * a.ld_g;
@@ -200,137 +277,246 @@ __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_const
     }
     cp_async_wait_all();
     __syncthreads();
-    for (int r = a.r_lo; r < a.r_hi; ++r) {
-        // this residue's twiddles (FTc) and the next one's (FTn); a thread
-        // reads only the entries it copied itself
-        V* FTc = ((r - a.r_lo) & 1) ? FT2 : FT;
-        V* FTn = ((r - a.r_lo) & 1) ? FT : FT2;
-        cp_async_wait_all();
-        const int rq = r % a.q;
-        // fold (Eq. 1 inner sum, then zeta_N^{r s}) of f and g into this
-        // block's columns s = s1 m2 + c w2 + cl
-        for (int e = tid; e < tile; e += nthr) {
-            const int s1 = a.dw2.div(e), cl = e - s1 * w2;
-            const int64_t s = (int64_t)s1 * a.m2 + (int64_t)c * w2 + cl;
-            const V wrs = FTc[e];
-            V af, ag;
-            if (a.stage) {
-                af = INF[e];
-                ag = ING[e];
-            } else {
-                af = s < a.L ? fr[s] : czero<V>();
-                ag = s < a.L ? gr[s] : czero<V>();
-            }
-            int qi = 0;                  // (r t) mod q
-            for (int t = 1; t < a.p; ++t) {
-                const int64_t j = (int64_t)t * a.m + s;
-                if (j >= a.L) break;
-                qi += rq;
-                if (qi >= a.q) qi -= a.q;
-                const V w = QT[qi];
-                af = cfma(a.stage ? INF[t * tile + e] : fr[j], w, af);
-                ag = cfma(a.stage ? ING[t * tile + e] : gr[j], w, ag);
-            }
-            X[sidx<V, true>(s1 * xw + cl)] = cmul(af, wrs);
-            X[sidx<V, true>(s1 * xw + w2 + cl)] = cmul(ag, wrs);
-            if (r + 1 < a.r_hi) twn_to_smem(FTn + e, a.twN, (int64_t)(r + 1) * s);
-        }
-        __syncthreads();
-        // m1-point transforms of the 2 w2 columns (f and g at once)
-        fft_smem<V, false, true, false, true>(X, S, a.fp1, xw, xw, 1, T1, T1l, tid, nthr);
-        cluster.sync();
-        // transpose: rows l1 = c w1 + rl of every column s2, from the block
-        // that owns s2, times zeta_m^{l1 s2}.  Four elements per thread are
-        // loaded before any is stored, so the loads from the other blocks'
-        // shared memory are in flight together.
-        constexpr int U = 4;
-        for (int e0 = tid; e0 < tile; e0 += U * nthr) {
-            V v0[U], v1[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int e = e0 + u * nthr;
-                if (e < tile) {
-                    const int rl = a.dm2.div(e), s2 = e - rl * a.m2;
-                    const int src = a.dw2.div(s2), scl = s2 - src * w2;
-                    const V* rx = cluster.map_shared_rank(X, src);
-                    const int row = (c * w1 + rl) * xw;
-                    v0[u] = rx[sidx<V, true>(row + scl)];
-                    v1[u] = rx[sidx<V, true>(row + w2 + scl)];
+    if constexpr (W) {
+        // The shuffle transforms: no tile goes through shared memory between
+        // the fold and the push, or between the product and the push.
+        // Lane (col, i) of the column phases holds point i of column col of
+        // the two-tile X (f in columns [0, w2), g in [w2, 2 w2)); lane
+        // (col, i) of the row phases point i of column col of Y.
+        const int ccol = tid >> a.lg1, ci = tid & (a.m1 - 1);
+        const int cside = ccol >= w2 ? 1 : 0, ccl = ccol - cside * w2;
+        const int ci_rev = (int)(__brev((unsigned)ci) >> (32 - a.lg1));
+        const bool cact = tid < xw * a.m1, cwarp = (tid & ~31) < xw * a.m1;
+        const int rcol = tid >> a.lg2, ri = tid & (a.m2 - 1);
+        const bool ract = tid < yw * a.m2, rwarp = (tid & ~31) < yw * a.m2;
+        const bool iwarp = (tid & ~31) < w1 * a.m2;     // inverse row transforms (f rows)
+        const bool uwarp = (tid & ~31) < w2 * a.m1;     // inverse column transforms (f columns)
+        const V* in_side = cside ? ING : INF;
+        const V* g_side = cside ? gr : fr;
+        for (int r = a.r_lo; r < a.r_hi; ++r) {
+            V* FTc = ((r - a.r_lo) & 1) ? FT2 : FT;
+            V* FTn = ((r - a.r_lo) & 1) ? FT : FT2;
+            const int rq = r % a.q;
+            // fold (Eq. 1 inner sum, then zeta_N^{r s}) of element s1 =
+            // bitrev(i) of this lane's column (the order the transform
+            // reads), then the m1-point transform; result l1 = i goes to
+            // the block that owns row l1, times zeta_m^{l1 s2}
+            if (cwarp) {
+                V x = czero<V>();
+                if (cact) {
+                    const int e = ci_rev * w2 + ccl;
+                    const int64_t s = (int64_t)ci_rev * a.m2 + (int64_t)c * w2 + ccl;
+                    x = a.stage ? in_side[e] : (s < a.L ? g_side[s] : czero<V>());
+                    int qi = 0;                  // (r t) mod q
+                    for (int t = 1; t < a.p; ++t) {
+                        const int64_t j = (int64_t)t * a.m + s;
+                        if (j >= a.L) break;
+                        qi += rq;
+                        if (qi >= a.q) qi -= a.q;
+                        x = cfma(a.stage ? in_side[t * tile + e] : g_side[j], QT[qi], x);
+                    }
+                    x = cmul(x, FTc[e]);
+                }
+                x = warp_dit<V, false>(x, ci, a.lg1, T1l);
+                if (cact) {
+                    V* yd = cluster.map_shared_rank(Y, ci >> lgw1);
+                    yd[sidx<V, true>((c * w2 + ccl) * yw + cside * w1 + (ci & (w1 - 1)))] =
+                        cmul(x, BW[ccl * a.m1 + ci]);
                 }
             }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int e = e0 + u * nthr;
-                if (e < tile) {
-                    const int rl = a.dm2.div(e), s2 = e - rl * a.m2;
-                    const V w = FW[e];
-                    Y[sidx<V, true>(s2 * yw + rl)] = cmul(v0[u], w);
-                    Y[sidx<V, true>(s2 * yw + w1 + rl)] = cmul(v1[u], w);
+            cluster.sync();
+            // the next residue's fold twiddles, copied while the rows run
+            // (every read of the buffer they replace came before the barrier)
+            if (r + 1 < a.r_hi)
+                for (int e = tid; e < tile; e += nthr) {
+                    const int s1 = a.dw2.div(e), cl = e - s1 * w2;
+                    twn_to_smem(FTn + e, a.twN, (int64_t)(r + 1) * ((int64_t)s1 * a.m2 + (int64_t)c * w2 + cl));
+                }
+            // m2-point transforms of the rows (decimation in frequency: lane
+            // i ends with bin bitrev(i)); g's bins through shared memory to
+            // the lane of f with the same i, product (Section 2.4), inverse
+            // transform (decimation in time: lane i ends with s2 = i), result
+            // to the block that owns column s2, times conj(zeta_m^{l1 s2})
+            V y = czero<V>();
+            if (rwarp) {
+                if (ract) y = Y[sidx<V, true>(ri * yw + rcol)];
+                y = warp_dif<V, false>(y, ri, a.lg2, T2l);
+                if (ract && rcol >= w1) Y[sidx<V, true>(ri * yw + rcol)] = y;
+            }
+            __syncthreads();
+            if (iwarp) {
+                const bool fact = tid < w1 * a.m2;
+                if (fact) y = cmul(y, Y[sidx<V, true>(ri * yw + rcol + w1)]);
+                y = warp_dit<V, true>(y, ri, a.lg2, T2l);
+                if (fact) {
+                    V* xd = cluster.map_shared_rank(X, ri >> lgw2);
+                    xd[sidx<V, true>((c * w1 + rcol) * xw + (ri & (w2 - 1)))] = cmulc(y, FW[rcol * a.m2 + ri]);
                 }
             }
-        }
-        // no cluster barrier here: this block's column tiles X are next
-        // written by the transpose back, after the barrier below, which every
-        // block reaches only after its own forward transpose
-        __syncthreads();
-        // m2-point transforms of the 2 w1 rows, product (Section 2.4), inverse
-        fft_smem<V, false, true, false, true>(Y, S, a.fp2, yw, yw, 1, T2, T2l, tid, nthr);
-        for (int e = tid; e < tile; e += nthr) {
-            const int s2 = a.dw1.div(e), rl = e - s2 * w1;
-            const int kf = sidx<V, true>(s2 * yw + rl), kg = sidx<V, true>(s2 * yw + w1 + rl);
-            Y[kf] = cmul(Y[kf], Y[kg]);
-        }
-        __syncthreads();
-        fft_smem<V, true, true, false, true>(Y, S, a.fp2, w1, yw, 1, T2, T2l, tid, nthr);
-        cluster.sync();
-        // transpose back: this block's columns s2 = c w2 + cl of every row l1,
-        // times conj(zeta_m^{l1 s2}).  The next residue's writes to Y come
-        // after its first cluster barrier, which every block reaches only
-        // after this loop.
-        for (int e0 = tid; e0 < tile; e0 += U * nthr) {
-            V v[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int e = e0 + u * nthr;
-                if (e < tile) {
-                    const int cl = a.dm1.div(e), l1 = e - cl * a.m1;
-                    const int src = a.dw1.div(l1), rl = l1 - src * w1;
-                    v[u] = cluster.map_shared_rank(Y, src)[sidx<V, true>((c * w2 + cl) * yw + rl)];
+            cp_async_wait_all();
+            cluster.sync();
+            // inverse m1-point transforms of this block's columns (lane i
+            // loads row bitrev(i), ends with h_r[s], s1 = i), then the
+            // unfold (Eq. 2 outer sums): output j = t m + s gets
+            // conj(zeta_N^{r s}) conj(zeta_q^{r t}) h_r[s]
+            if (uwarp) {
+                const bool uact = tid < w2 * a.m1;
+                V x = uact ? X[sidx<V, true>(ci_rev * xw + ccol)] : czero<V>();
+                x = warp_dit<V, true>(x, ci, a.lg1, T1l);
+                if (uact) {
+                    const int e = ci * w2 + ccol;
+                    const int64_t s = (int64_t)ci * a.m2 + (int64_t)c * w2 + ccol;
+                    const V hv = cmulc(x, FTc[e]);
+                    int qi = 0;
+                    for (int t = 0; t < a.pout; ++t) {
+                        const int64_t j = (int64_t)t * a.m + s;
+                        if (j >= a.hi) break;
+                        if (t != 0) {
+                            qi += rq;
+                            if (qi >= a.q) qi -= a.q;
+                        }
+                        if (j < a.lo) continue;
+                        const V v = t != 0 ? cmulc(hv, QT[qi]) : hv;
+                        acc[t * tile + e] = cadd(acc[t * tile + e], v);
+                    }
                 }
             }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int e = e0 + u * nthr;
-                if (e < tile) {
-                    const int cl = a.dm1.div(e), l1 = e - cl * a.m1;
-                    X[sidx<V, true>(l1 * xw + cl)] = cmulc(v[u], BW[e]);
-                }
-            }
+            // X is next written by the other blocks after the next residue's
+            // first barrier; FTc is next overwritten after that barrier too
         }
-        __syncthreads();
-        // inverse m1-point transforms: h_r[s1 m2 + s2] of this block's columns
-        fft_smem<V, true, true, false, true>(X, S, a.fp1, w2, xw, 1, T1, T1l, tid, nthr);
-        // unfold (Eq. 2 outer sums): output j = t m + s gets
-        // conj(zeta_N^{r s}) conj(zeta_q^{r t}) h_r[s], residues in increasing r
-        for (int e = tid; e < tile; e += nthr) {
-            const int s1 = a.dw2.div(e), cl = e - s1 * w2;
-            const int64_t s = (int64_t)s1 * a.m2 + (int64_t)c * w2 + cl;
-            const V hv = cmulc(X[sidx<V, true>(s1 * xw + cl)], FTc[e]);
-            int qi = 0;                  // (r t) mod q
-            for (int t = 0; t < a.pout; ++t) {
-                const int64_t j = (int64_t)t * a.m + s;
-                if (j >= a.hi) break;
-                if (t != 0) {
+    } else {
+        for (int r = a.r_lo; r < a.r_hi; ++r) {
+            // this residue's twiddles (FTc) and the next one's (FTn); a thread
+            // reads only the entries it copied itself
+            V* FTc = ((r - a.r_lo) & 1) ? FT2 : FT;
+            V* FTn = ((r - a.r_lo) & 1) ? FT : FT2;
+            cp_async_wait_all();
+            const int rq = r % a.q;
+            // fold (Eq. 1 inner sum, then zeta_N^{r s}) of f and g into this
+            // block's columns s = s1 m2 + c w2 + cl
+            for (int e = tid; e < tile; e += nthr) {
+                const int s1 = a.dw2.div(e), cl = e - s1 * w2;
+                const int64_t s = (int64_t)s1 * a.m2 + (int64_t)c * w2 + cl;
+                const V wrs = FTc[e];
+                V af, ag;
+                if (a.stage) {
+                    af = INF[e];
+                    ag = ING[e];
+                } else {
+                    af = s < a.L ? fr[s] : czero<V>();
+                    ag = s < a.L ? gr[s] : czero<V>();
+                }
+                int qi = 0;                  // (r t) mod q
+                for (int t = 1; t < a.p; ++t) {
+                    const int64_t j = (int64_t)t * a.m + s;
+                    if (j >= a.L) break;
                     qi += rq;
                     if (qi >= a.q) qi -= a.q;
+                    const V w = QT[qi];
+                    af = cfma(a.stage ? INF[t * tile + e] : fr[j], w, af);
+                    ag = cfma(a.stage ? ING[t * tile + e] : gr[j], w, ag);
                 }
-                if (j < a.lo) continue;
-                const V v = t != 0 ? cmulc(hv, QT[qi]) : hv;
-                acc[t * tile + e] = cadd(acc[t * tile + e], v);
+                X[sidx<V, true>(s1 * xw + cl)] = cmul(af, wrs);
+                X[sidx<V, true>(s1 * xw + w2 + cl)] = cmul(ag, wrs);
+                if (r + 1 < a.r_hi) twn_to_smem(FTn + e, a.twN, (int64_t)(r + 1) * s);
             }
+            __syncthreads();
+            // m1-point transforms of the 2 w2 columns (f and g at once)
+            fft_smem<V, false, true, false, true>(X, S, a.fp1, xw, xw, 1, T1, T1l, tid, nthr);
+            cluster.sync();
+            // transpose: rows l1 = c w1 + rl of every column s2, from the block
+            // that owns s2, times zeta_m^{l1 s2}.  Four elements per thread are
+            // loaded before any is stored, so the loads from the other blocks'
+            // shared memory are in flight together.
+            constexpr int U = 4;
+            for (int e0 = tid; e0 < tile; e0 += U * nthr) {
+                V v0[U], v1[U];
+    #pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int e = e0 + u * nthr;
+                    if (e < tile) {
+                        const int rl = a.dm2.div(e), s2 = e - rl * a.m2;
+                        const int src = a.dw2.div(s2), scl = s2 - src * w2;
+                        const V* rx = cluster.map_shared_rank(X, src);
+                        const int row = (c * w1 + rl) * xw;
+                        v0[u] = rx[sidx<V, true>(row + scl)];
+                        v1[u] = rx[sidx<V, true>(row + w2 + scl)];
+                    }
+                }
+    #pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int e = e0 + u * nthr;
+                    if (e < tile) {
+                        const int rl = a.dm2.div(e), s2 = e - rl * a.m2;
+                        const V w = FW[e];
+                        Y[sidx<V, true>(s2 * yw + rl)] = cmul(v0[u], w);
+                        Y[sidx<V, true>(s2 * yw + w1 + rl)] = cmul(v1[u], w);
+                    }
+                }
+            }
+            // no cluster barrier here: this block's column tiles X are next
+            // written by the transpose back, after the barrier below, which every
+            // block reaches only after its own forward transpose
+            __syncthreads();
+            // m2-point transforms of the 2 w1 rows, product (Section 2.4), inverse
+            fft_smem<V, false, true, false, true>(Y, S, a.fp2, yw, yw, 1, T2, T2l, tid, nthr);
+            for (int e = tid; e < tile; e += nthr) {
+                const int s2 = a.dw1.div(e), rl = e - s2 * w1;
+                const int kf = sidx<V, true>(s2 * yw + rl), kg = sidx<V, true>(s2 * yw + w1 + rl);
+                Y[kf] = cmul(Y[kf], Y[kg]);
+            }
+            __syncthreads();
+            fft_smem<V, true, true, false, true>(Y, S, a.fp2, w1, yw, 1, T2, T2l, tid, nthr);
+            cluster.sync();
+            // transpose back: this block's columns s2 = c w2 + cl of every row l1,
+            // times conj(zeta_m^{l1 s2}).  The next residue's writes to Y come
+            // after its first cluster barrier, which every block reaches only
+            // after this loop.
+            for (int e0 = tid; e0 < tile; e0 += U * nthr) {
+                V v[U];
+    #pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int e = e0 + u * nthr;
+                    if (e < tile) {
+                        const int cl = a.dm1.div(e), l1 = e - cl * a.m1;
+                        const int src = a.dw1.div(l1), rl = l1 - src * w1;
+                        v[u] = cluster.map_shared_rank(Y, src)[sidx<V, true>((c * w2 + cl) * yw + rl)];
+                    }
+                }
+    #pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int e = e0 + u * nthr;
+                    if (e < tile) {
+                        const int cl = a.dm1.div(e), l1 = e - cl * a.m1;
+                        X[sidx<V, true>(l1 * xw + cl)] = cmulc(v[u], BW[e]);
+                    }
+                }
+            }
+            __syncthreads();
+            // inverse m1-point transforms: h_r[s1 m2 + s2] of this block's columns
+            fft_smem<V, true, true, false, true>(X, S, a.fp1, w2, xw, 1, T1, T1l, tid, nthr);
+            // unfold (Eq. 2 outer sums): output j = t m + s gets
+            // conj(zeta_N^{r s}) conj(zeta_q^{r t}) h_r[s], residues in increasing r
+            for (int e = tid; e < tile; e += nthr) {
+                const int s1 = a.dw2.div(e), cl = e - s1 * w2;
+                const int64_t s = (int64_t)s1 * a.m2 + (int64_t)c * w2 + cl;
+                const V hv = cmulc(X[sidx<V, true>(s1 * xw + cl)], FTc[e]);
+                int qi = 0;                  // (r t) mod q
+                for (int t = 0; t < a.pout; ++t) {
+                    const int64_t j = (int64_t)t * a.m + s;
+                    if (j >= a.hi) break;
+                    if (t != 0) {
+                        qi += rq;
+                        if (qi >= a.q) qi -= a.q;
+                    }
+                    if (j < a.lo) continue;
+                    const V v = t != 0 ? cmulc(hv, QT[qi]) : hv;
+                    acc[t * tile + e] = cadd(acc[t * tile + e], v);
+                }
+            }
+            // the thread that reads X and FTc[e] of element e here writes them in
+            // the next fold, and acc entries are per thread: no barrier needed
         }
-        // the thread that reads X and FTc[e] of element e here writes them in
-        // the next fold, and acc entries are per thread: no barrier needed
     }
     // no block leaves while another may still read its shared memory
     cluster.sync();
@@ -344,32 +530,50 @@ __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_const
 
 // ------------------------------------------------------------------ host
 
+// Whether the cluster kernel takes the shuffle transforms for this shape:
+// m1 and m2 powers of two up to 32 and one thread per point of both
+// inputs' tiles.
+static bool cluster_warp_ffts(int64_t m, int C, int64_t m1, int64_t m2)
+{
+    auto pow2 = [](int64_t x) { return x > 0 && (x & (x - 1)) == 0; };
+    return pow2(m1) && pow2(m2) && m2 <= 32 && 2 * (m / C) <= kMaxThreads;
+}
+
+// The transform plans of the cluster kernel: radix 2 throughout with the
+// shuffle transforms (whose twiddles are the radix-2 stage tables), else
+// the latency plans.
+template <typename T> static FftPlan cluster_plan(int64_t n, bool warp_ffts)
+{
+    return warp_ffts ? make_fft_plan(n, false, true) : fft_plan_latency<T>(n);
+}
+
 // Bytes of dynamic shared memory of one block (ClusterSmem).
 template <typename T>
 static size_t cluster_smem(int64_t m, int C, int64_t m1, int64_t m2, int64_t pout, int64_t q, int64_t p)
 {
     const int64_t tile = m / C;
-    const ClusterSmem L{ (int)smem_len<cx<T>>(2 * tile), (int)tile, (int)pout, fft_plan_latency<T>(m1).tlen,
-                         fft_plan_latency<T>(m2).tlen, (int)q, (int)p };
+    const bool wf = cluster_warp_ffts(m, C, m1, m2);
+    const ClusterSmem L{ (int)smem_len<cx<T>>(2 * tile), (int)tile, (int)pout, cluster_plan<T>(m1, wf).tlen,
+                         cluster_plan<T>(m2, wf).tlen, (int)q, (int)p };
     return (size_t)L.total() * sizeof(cx<T>);
 }
 
 // Whether a 16-block cluster of this kernel with `smem` bytes per block can
 // be resident (a non-portable size; remembered per device).
-template <class V> static bool cluster16_ok(size_t smem, int thr)
+template <class V, bool W> static bool cluster16_ok(size_t smem, int thr)
 {
     static std::mutex mu;
     static std::map<std::pair<int, size_t>, bool> known;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
     std::lock_guard<std::mutex> lk(mu);
-    auto key = std::make_pair(dev, smem * 1024 + (size_t)thr);
+    auto key = std::make_pair(dev, (smem * 1024 + (size_t)thr) * 2 + (W ? 1 : 0));
     auto it = known.find(key);
     if (it != known.end()) return it->second;
-    bool ok = cudaFuncSetAttribute(k_conv_cluster<V>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+    bool ok = cudaFuncSetAttribute(k_conv_cluster<V, W>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
               cudaSuccess;
     if (ok && smem > 48 * 1024)
-        ok = cudaFuncSetAttribute(k_conv_cluster<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+        ok = cudaFuncSetAttribute(k_conv_cluster<V, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
              cudaSuccess;
     if (ok) {
         cudaLaunchConfig_t cfg = {};
@@ -384,7 +588,7 @@ template <class V> static bool cluster16_ok(size_t smem, int thr)
         cfg.attrs = at;
         cfg.numAttrs = 1;
         int n = 0;
-        ok = cudaOccupancyMaxActiveClusters(&n, k_conv_cluster<V>, &cfg) == cudaSuccess && n > 0;
+        ok = cudaOccupancyMaxActiveClusters(&n, k_conv_cluster<V, W>, &cfg) == cudaSuccess && n > 0;
     }
     cudaGetLastError();
     known[key] = ok;
@@ -392,10 +596,11 @@ template <class V> static bool cluster16_ok(size_t smem, int thr)
 }
 
 // Threads of one block: one per butterfly of a stage over both inputs'
-// tiles (radix 2 in FP64, radix 8 in FP32; fft_plan_latency), 64..256.
-template <typename T> static int cluster_threads(int64_t tile)
+// tiles (radix 2 in FP64, radix 8 in FP32; fft_plan_latency), 64..256; with
+// the shuffle transforms one per point of both tiles.
+template <typename T> static int cluster_threads(int64_t tile, bool warp_ffts)
 {
-    int thr = (int)(((sizeof(T) == 8 ? tile : tile / 4) + 31) / 32 * 32);
+    int thr = (int)(((warp_ffts ? 2 * tile : (sizeof(T) == 8 ? tile : tile / 4)) + 31) / 32 * 32);
     return thr < 64 ? 64 : (thr > kMaxThreads ? kMaxThreads : thr);
 }
 
@@ -423,7 +628,10 @@ bool cluster_shape(int64_t m, int64_t pout, int64_t q, int64_t p, int* Co, int64
             smem = cluster_smem<T>(m, C, best, m / best, pout, q, 0);
         }
         if (smem > kMaxSmem) continue;
-        if (C == 16 && !cluster16_ok<cx<T>>(smem, cluster_threads<T>(m / C))) continue;
+        const bool wf = cluster_warp_ffts(m, C, best, m / best);
+        if (C == 16 && !(wf ? cluster16_ok<cx<T>, true>(smem, cluster_threads<T>(m / C, true))
+                            : cluster16_ok<cx<T>, false>(smem, cluster_threads<T>(m / C, false))))
+            continue;
         *Co = C;
         *m1o = best;
         *m2o = m / best;
@@ -451,8 +659,9 @@ cudaError_t launch_conv_cluster(const cx<T>* f, const cx<T>* g, cx<T>* out, int6
     ClusterArgs<V> a;
     a.twN = tw_table<T>(q * m, &e);
     if (e != cudaSuccess) return e;
-    a.fp1 = fft_plan_latency<T>(m1);
-    a.fp2 = fft_plan_latency<T>(m2);
+    const bool wf = cluster_warp_ffts(m, C, m1, m2);
+    a.fp1 = cluster_plan<T>(m1, wf);
+    a.fp2 = cluster_plan<T>(m2, wf);
     a.tw1 = twiddles_fft_plan<T>(a.fp1, false, &e);
     if (e != cudaSuccess) return e;
     a.tw1l = twiddles_fft_plan<T>(a.fp1, true, &e);
@@ -484,10 +693,15 @@ cudaError_t launch_conv_cluster(const cx<T>* f, const cx<T>* g, cx<T>* out, int6
     a.dw1 = make_idiv((int)(m1 / C));
     a.dw2 = make_idiv((int)(m2 / C));
     a.stage = stage ? 1 : 0;
-    const int thr = cluster_threads<T>(m / C);
+    a.lg1 = 0;
+    while ((int64_t(1) << a.lg1) < m1) ++a.lg1;
+    a.lg2 = 0;
+    while ((int64_t(1) << a.lg2) < m2) ++a.lg2;
+    const int thr = cluster_threads<T>(m / C, wf);
+    auto kern = wf ? k_conv_cluster<V, true> : k_conv_cluster<V, false>;
     const size_t smem_c = cluster_smem<T>(m, C, m1, m2, pout, q, stage ? p : 0);
     if (smem_c > 48 * 1024 &&
-        (e = cudaFuncSetAttribute(k_conv_cluster<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c)) !=
+        (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c)) !=
             cudaSuccess)
         return e;
     if (preparing()) return cudaSuccess;
@@ -510,7 +724,7 @@ cudaError_t launch_conv_cluster(const cx<T>* f, const cx<T>* g, cx<T>* out, int6
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_conv_cluster<V>, a);
+    e = cudaLaunchKernelEx(&cfg, kern, a);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
