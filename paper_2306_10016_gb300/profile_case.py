@@ -2,11 +2,16 @@
 
     python -m paper_2306_10016_gb300.profile_case --L 4194304 --m 2097152 \\
         --dtype f64 --reps 3 [--dims 1] [--D 0] [--batch 1]
+    python -m paper_2306_10016_gb300.profile_case --L 1024 --m 512 --p 2 --q 4 --D 1
+    python -m paper_2306_10016_gb300.profile_case --hermitian 512 --m 512 1536
     python -m paper_2306_10016_gb300.profile_case --sweep --reps 2 [--dtype f64]
 
 Inputs are seeded unit-disk values; each repetition is one hdc_convnd call
-on the current stream, followed by a synchronisation.  Prints the device
-time of every repetition.
+(--p, --q, --D fix the tuple per axis) on the current stream, followed by a
+synchronisation.  Prints the device time of every repetition.
+
+--hermitian K runs the centered Hermitian 2-D convolution of two seeded
+half-plane spectra of (2K - 1) x K points instead, m per axis from --m.
 
 --sweep runs the 1-D sweep of the throughput measurement instead (L = 2^10
 .. 2^22 and 3 * 2^9 .. 3 * 2^20, M = 2L - 1, the tuned parameters of each
@@ -69,6 +74,9 @@ def main():
     ap.add_argument("--L", type=int, nargs="+")
     ap.add_argument("--m", type=int, nargs="+")
     ap.add_argument("--D", type=int, nargs="+", default=None)
+    ap.add_argument("--p", type=int, nargs="+", default=None)
+    ap.add_argument("--q", type=int, nargs="+", default=None)
+    ap.add_argument("--hermitian", type=int, default=0, metavar="K")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--reps", type=int, default=3)
@@ -79,8 +87,25 @@ def main():
     if a.sweep:
         run_sweep(a, tdt, dcode)
         return
+    if a.hermitian:
+        K = a.hermitian
+        m = a.m if a.m else [K, K]
+        f = torch.from_numpy(synth.hermitian_normal(synth.BASE_SEED + 32, K)).to("cuda", tdt)
+        g = torch.from_numpy(synth.hermitian_normal(synth.BASE_SEED + 33, K)).to("cuda", tdt)
+        h = torch.empty_like(f)
+        times = []
+        for _ in range(a.reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            hdc.conv2d_hermitian(f, g, m=m, out=h)
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        print(json.dumps({"hermitian": K, "m": m, "dtype": a.dtype, "ms": times}))
+        return
     if not a.L or not a.m:
-        ap.error("--L and --m are required without --sweep")
+        ap.error("--L and --m are required without --sweep or --hermitian")
     dims = len(a.L)
     shape = ([a.batch] if a.batch > 1 else []) + a.L
     f = torch.from_numpy(synth.unit_disk(synth.BASE_SEED + 7, shape)).to("cuda", tdt)
@@ -92,7 +117,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        hdc.convnd(f, g, dims, a.m, D=D, out=h)
+        hdc.convnd(f, g, dims, a.m, p=a.p if a.p else 0, q=a.q if a.q else 0, D=D, out=h)
         e1.record()
         e1.synchronize()
         times.append(e0.elapsed_time(e1))

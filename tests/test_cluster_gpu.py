@@ -80,8 +80,9 @@ def test_cluster_route_exact_integers(hdc):
         assert np.array_equal(np.rint(h.imag).astype(np.int64), hi)
 
 
-def test_cluster_route_window_and_residue_shares(hdc):
-    L, m = 3000, 2048
+@pytest.mark.parametrize("L,m", [(3000, 2048), (1000, 512)])
+def test_cluster_route_window_and_residue_shares(hdc, L, m):
+    """m = 2048: shared-memory transforms; m = 512: the warp-shuffle ones."""
     fn = synth.unit_disk(35001, (L,))
     gn = synth.unit_disk(35002, (L,))
     f = torch.from_numpy(fn).cuda()
@@ -90,10 +91,11 @@ def test_cluster_route_window_and_residue_shares(hdc):
     hdc.set_cluster(2)
     try:
         hdc.stats_reset()
-        hw = hdc.convnd_window(f, g, 1, m, 1000, 3500).cpu().numpy()
+        lo, n = L // 3, L + L // 6
+        hw = hdc.convnd_window(f, g, 1, m, lo, n).cpu().numpy()
         torch.cuda.synchronize()
         assert hdc.stats()["k_conv_cluster"]["launches"] == 1
-        assert rel_max_err(hw, full[1000:4500]) <= 1e-12
+        assert rel_max_err(hw, full[lo:lo + n]) <= 1e-12
         # the shares of disjoint residue ranges add up to the convolution
         q = -(-(2 * L - 1) // m)
         parts = [hdc.convnd_residues(f, g, 1, m, lo, hi) for lo, hi in ((0, 1), (1, q))]
