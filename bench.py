@@ -519,7 +519,7 @@ def main():
         """The calls of two plans on the same data, each captured in a CUDA
         graph with ONE shared workspace (so both run on the same addresses),
         then replayed alternately (A B, B A, ...), each replay after an L2
-        flush, n times each; the medians."""
+        flush, n times each; the times of each."""
         ws = torch.empty(max(1, pa.workspace_bytes, pb.workspace_bytes), dtype=torch.uint8, device=dev)
         side = torch.cuda.Stream(dev)
         graphs = []
@@ -548,18 +548,22 @@ def main():
                 ev[k].append((e0, e1))
         torch.cuda.synchronize(dev)
         del graphs
-        return [statistics.median(a.elapsed_time(b) for a, b in e) for e in ev]
+        return [[a.elapsed_time(b) for a, b in e] for e in ev]
 
     # per size, the tuned and the explicit tuple on the same workspace,
-    # replayed alternately (45 each, L2 flushed before each; median)
+    # replayed alternately (45 each, L2 flushed before each; median).  Where
+    # the tuner chose the explicit tuple itself, the two plans run the same
+    # launches, and both report the median of all 90 times
     per_size = []
     for L, pt, pe, (f, g, h) in zip(sizes, plans64, plans_ex, ins64):
-        th_ms, te_ms = ab_times(pt, pe, f, g, h)
+        th, te = ab_times(pt, pe, f, g, h)
         prm = pt.params[0]
+        same = prm["q"] == 1 and prm["m"] == pe.params[0]["m"]
+        th_ms, te_ms = (statistics.median(th + te),) * 2 if same else (statistics.median(th), statistics.median(te))
         per_size.append({"L": L, "m": prm["m"], "p": prm["p"], "q": prm["q"], "D": prm["D"],
                          "hybrid_ms": round(th_ms, 5),
                          "explicit_ms": round(te_ms, 5),
-                         "same_tuple_as_explicit": prm["q"] == 1 and prm["m"] == pe.params[0]["m"],
+                         "same_tuple_as_explicit": same,
                          "valid_tuples": valid_tuple_count(L), "timed_tuples": pt.timed})
     del ins64
 
@@ -612,7 +616,7 @@ def main():
             return [o.conv_fft(fa_n[offs[i]:offs[i + 1]], ga_n[offs[i]:offs[i + 1]]) for i in sel]
 
         t0 = time.perf_counter()
-        ms_t, _ = hdc.batched_tune(fs, gs, hs, reps=3, max_cands=12)
+        ms_t, _ = hdc.batched_tune(fs, gs, hs, reps=3, max_cands=15)
         tune_b = time.perf_counter() - t0
         res = {}
         for name, mlist in (("tuned", ms_t), ("explicit", [hdc.next_good_size(2 * L - 1) for L in Ls])):

@@ -661,9 +661,10 @@ int hdc_batched_destroy(hdc_batched* plan);
  * kernel, with size classes as the separable axes): lengths are grouped by
  * floor(log2 L); a group's schedule is its residue count q (from 1, 2, 3,
  * 4, 5, 6, 8, 10, 12, 16) with a size rule, and every member gets its own
- * m >= ceil((2 L_i - 1) / q): either the next 2^a 3^b 5^c 7^d, or the next
- * 2^a or 3 2^a (more padding but cheaper radix-2/4/8 transforms).  The
- * first `max_cands` usable (q, rule) pairs, in that order, are timed.  All
+ * m >= ceil((2 L_i - 1) / q): the next 2^a 3^b 5^c 7^d, the next 2^a or
+ * 3 2^a (more padding but cheaper radix-2/4/8 transforms), or the next 2^a,
+ * 3 2^a or 5 2^a.  The first `max_cands` usable (q, rule) pairs, in that
+ * order and without rules that repeat the one before, are timed.  All
  * groups start at q = 1, nextgood (explicit padding); then group by group (largest total length
  * first, the others held) each q is timed on the WHOLE batch with this
  * kernel (`reps` timed runs, median) and the fastest kept.  m_out receives

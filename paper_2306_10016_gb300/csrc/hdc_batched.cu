@@ -588,22 +588,29 @@ HDC_EXPORT int hdc_batched_tune(int64_t n, const int64_t* L, int dtype, const vo
     cudaStream_t st = (cudaStream_t)stream;
     // A class's schedule is its residue count q and a size rule: every member
     // gets its own m >= ceil(M_i / q), either the next 2^a 3^b 5^c 7^d (the
-    // least padding) or the next 2^a or 3 2^a (more padding, but transforms
+    // least padding), the next 2^a or 3 2^a (more padding, but transforms
     // of radix-8, -4 and -2 stages and at most one radix-3 one, which cost
-    // fewer FP64 instructions per point than radix 3, 5 and 7), so the FFT
-    // size follows each length.  A schedule is encoded as 2 q + rule.
+    // fewer FP64 instructions per point than radix 3, 5 and 7), or the next
+    // 2^a, 3 2^a or 5 2^a (in between), so the FFT size follows each length.
+    // A schedule is encoded as 3 q + rule.
     static const int64_t qs[] = { 1, 2, 3, 4, 5, 6, 8, 10, 12, 16 };
     auto m_for = [&](int64_t Li, int64_t sched) -> int64_t {
-        const int64_t q = sched / 2;
+        const int64_t q = sched / 3;
+        const int rule = (int)(sched % 3);
         const int64_t M = 2 * Li - 1;
         const int64_t lo = (M + q - 1) / q;
         int64_t m = hdc_next_good_size(lo);
-        if (sched % 2) {
+        if (rule != 0) {
             int64_t p2 = 1;
             while (p2 < lo) p2 *= 2;
             int64_t t3 = 3;
             while (t3 < lo) t3 *= 2;
             m = std::min(p2, t3);
+            if (rule == 2) {
+                int64_t t5 = 5;
+                while (t5 < lo) t5 *= 2;
+                m = std::min(m, t5);
+            }
         }
         if (m < 1) return -1;
         const bool ok = dtype == HDC_C128 ? batched_ok<double>(m) : batched_ok<float>(m);
@@ -625,10 +632,16 @@ HDC_EXPORT int hdc_batched_tune(int64_t n, const int64_t* L, int dtype, const vo
             if ((int64_t)cands[k].size() >= max_cands) break;
             // q is usable when every member has an m >= 16 that the kernel supports
             if (!((2 * Lmin - 1 + q - 1) / q >= 16 || q == 1)) continue;
-            for (int rule = 0; rule < 2 && (int64_t)cands[k].size() < max_cands; ++rule) {
-                bool ok = true;
-                for (int64_t i : members[k]) ok = ok && m_for(L[i], 2 * q + rule) > 0;
-                if (ok) cands[k].push_back(2 * q + rule);
+            for (int rule = 0; rule < 3 && (int64_t)cands[k].size() < max_cands; ++rule) {
+                // usable when every member gets a supported m; skipped when
+                // every member gets the m of the rule before (nothing new)
+                bool ok = true, same = rule > 0;
+                for (int64_t i : members[k]) {
+                    const int64_t mi = m_for(L[i], 3 * q + rule);
+                    ok = ok && mi > 0;
+                    same = same && mi == m_for(L[i], 3 * q + rule - 1);
+                }
+                if (ok && !same) cands[k].push_back(3 * q + rule);
             }
         }
         if (cands[k].empty()) return HDC_ERR_UNSUPPORTED_SIZE;
