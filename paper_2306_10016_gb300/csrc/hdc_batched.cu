@@ -228,7 +228,7 @@ k_batched(const BConv<V>* __restrict__ convs, const BItem* __restrict__ it0, con
                 const int64_t cc = cv.m1 ? 1 : 0;
                 using T = typename real_of<V>::type;
                 for (int64_t e = e0 + tid; e < e1; e += nthr) {
-                    const int64_t i = e / Cn, c = e - i * Cn;
+                    const int64_t i = div_idx(e, Cn), c = e - i * Cn;
                     unfold_elem<V, 4>(hp_[itm.conv], cws, cv.m, Cn, ma, i, c, cv.p, cv.q, cv.N, cs, cc, (int64_t)0,
                                       cv.L, 0, cv.q, 1, 1, (T)(1.0 / (double)cv.N), cv.twN);
                 }

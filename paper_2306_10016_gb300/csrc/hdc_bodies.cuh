@@ -43,7 +43,7 @@ __device__ __forceinline__ void residue_row_body(const V* fr, const V* gr, V* hr
                     af = cadd(af, fv);
                     ag = cadd(ag, gv);
                 } else {
-                    const V w = twn(twN, (((int64_t)r * t) % q) * m);
+                    const V w = twn(twN, rt_mod(r, t, q) * m);
                     af = cfma(fv, w, af);
                     ag = cfma(gv, w, ag);
                 }
@@ -95,7 +95,7 @@ __device__ __forceinline__ void fold_row(const V* x, int64_t L, int m, int p, in
             const int64_t j = (int64_t)t * m + s;
             if (j >= L) break;
             if (r == 0) a = cadd(a, x[j]);
-            else a = cfma(x[j], twn(twN, (((int64_t)r * t) % q) * m), a);
+            else a = cfma(x[j], twn(twN, rt_mod(r, t, q) * m), a);
         }
         if (r != 0) a = cmul(a, twn(twN, (int64_t)r * s));
         dst[sidx<V, true>(s)] = a;
@@ -288,7 +288,7 @@ __device__ __forceinline__ void fft_cols_store_body(V* buf, V* tmp, V* yb, int64
     const V* res = buf;
     if (ma > 1) res = fft_smem_any<V, false, false, R16>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);
     for (int e = tid; e < ma * C; e += nthr) {
-        const int l = e / C, cl = e - l * C;
+        const int l = div_idx(e, C), cl = e - l * C;
         const int64_t c = c0 + cl;
         if (c >= Cn) continue;
         V v = res[e];
@@ -325,7 +325,7 @@ __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int e = e0 + u * nthr;
-            const int i = e / C, cl = e - i * C;
+            const int i = div_idx(e, C), cl = e - i * C;
             const int64_t c = c0 + cl;
             base[u] = (e < n && c < Cn) ? (int64_t)i * Cn + c : -1;
         }
@@ -339,8 +339,8 @@ __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn
                     xb[u] = (t + 1 < p && base[u] >= 0 && base[u] + off2 < Lvalid) ? x[base[u] + off2] : czero<V>();
                 }
                 // block t = 0 carries zeta_q^0 = 1: no multiplication
-                const V wa = (r == 0 || t == 0) ? czero<V>() : twn(twNf, (((int64_t)r * t) % q) * mq);
-                const V wb = r == 0 ? czero<V>() : twn(twNf, (((int64_t)r * (t + 1)) % q) * mq);
+                const V wa = (r == 0 || t == 0) ? czero<V>() : twn(twNf, rt_mod(r, t, q) * mq);
+                const V wb = r == 0 ? czero<V>() : twn(twNf, rt_mod(r, (t + 1), q) * mq);
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     if (t == 0) acc[u] = xa[u];
@@ -356,7 +356,7 @@ __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn
             for (int t = 1; t < p; ++t) {
                 const int64_t off = (int64_t)t * ma * Cn;
                 if (off >= Lvalid) break;
-                const V w = r == 0 ? czero<V>() : twn(twNf, (((int64_t)r * t) % q) * mq);
+                const V w = r == 0 ? czero<V>() : twn(twNf, rt_mod(r, t, q) * mq);
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     if (base[u] < 0 || base[u] + off >= Lvalid) continue;
@@ -371,7 +371,7 @@ __device__ __forceinline__ void fold_fft_cols_body(const V* x, V* yb, int64_t Cn
             if (e >= n) break;
             V a = acc[u];
             if (r != 0 && base[u] >= 0) {
-                const int i = e / C, cl = e - i * C;
+                const int i = div_idx(e, C), cl = e - i * C;
                 a = cmul(a, twn(twNf, (int64_t)r * (i * cs + (c0 + cl) * cc)));
             }
             buf[e] = a;
@@ -401,7 +401,7 @@ __device__ __forceinline__ void ifft_cols_body(V* yb, int64_t Cn, int ma, int q,
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int e = e0 + u * nthr;
-            const int l = e / C, cl = e - l * C;
+            const int l = div_idx(e, C), cl = e - l * C;
             const int64_t c = c0 + cl;
             v[u] = (e < n && c < Cn) ? yb[(int64_t)l * Cn + c] : czero<V>();
         }
@@ -409,7 +409,7 @@ __device__ __forceinline__ void ifft_cols_body(V* yb, int64_t Cn, int ma, int q,
         for (int u = 0; u < U; ++u) {
             const int e = e0 + u * nthr;
             if (e >= n) break;
-            const int l = e / C, cl = e - l * C;
+            const int l = div_idx(e, C), cl = e - l * C;
             const int64_t c = c0 + cl;
             if (pre && l != 0 && c != 0 && c < Cn)
                     v[u] = cmulc(v[u], (sizeof(V) == 16 && tpm) ? __ldg(tpm + c * ma + l) : twn(twNf, (int64_t)l * c * q));
@@ -420,7 +420,7 @@ __device__ __forceinline__ void ifft_cols_body(V* yb, int64_t Cn, int ma, int q,
     const V* res = buf;
     if (ma > 1) res = fft_smem_any<V, true, false, R16>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);
     for (int e = tid; e < ma * C; e += nthr) {
-        const int s = e / C, cl = e - s * C;
+        const int s = div_idx(e, C), cl = e - s * C;
         const int64_t c = c0 + cl;
         if (c < Cn) yb[(int64_t)s * Cn + c] = res[e];
     }
@@ -458,7 +458,7 @@ __device__ __forceinline__ void ifft_unfold_cols_body(const V* y, int64_t rstrid
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int e = e0 + u * nthr;
-                const int l = e / C, cl = e - l * C;
+                const int l = div_idx(e, C), cl = e - l * C;
                 const int64_t c = c0 + cl;
                 v[u] = (e < n && c < Cn) ? yb[(int64_t)l * Cn + c] : czero<V>();
             }
@@ -466,7 +466,7 @@ __device__ __forceinline__ void ifft_unfold_cols_body(const V* y, int64_t rstrid
             for (int u = 0; u < U; ++u) {
                 const int e = e0 + u * nthr;
                 if (e >= n) break;
-                const int l = e / C, cl = e - l * C;
+                const int l = div_idx(e, C), cl = e - l * C;
                 const int64_t c = c0 + cl;
                 if (pre && l != 0 && c != 0 && c < Cn)
                     v[u] = cmulc(v[u], (sizeof(V) == 16 && tpm) ? __ldg(tpm + c * ma + l) : twn(twNf, (int64_t)l * c * q));
@@ -478,7 +478,7 @@ __device__ __forceinline__ void ifft_unfold_cols_body(const V* y, int64_t rstrid
         if (ma > 1) res = fft_smem_any<V, true, false, R16>(buf, tmp, fp, C, C, 1, twma, twmal, tid, nthr);
         const bool init = first && rr == 0, fin = last && rr == Dg - 1;
         for (int e = tid; e < n; e += nthr) {
-            const int i = e / C, cl = e - i * C;
+            const int i = div_idx(e, C), cl = e - i * C;
             const int64_t c = c0 + cl;
             if (c >= Cn) continue;
             V hv = res[e];
@@ -487,7 +487,7 @@ __device__ __forceinline__ void ifft_unfold_cols_body(const V* y, int64_t rstrid
                 const int64_t lin = ((int64_t)t * ma + i) * Cn + c;
                 if (lin >= hi) break;
                 if (lin < lo) continue;
-                V v = (r != 0 && t != 0) ? cmulc(hv, twn(twNf, (((int64_t)r * t) % q) * mq)) : hv;
+                V v = (r != 0 && t != 0) ? cmulc(hv, twn(twNf, rt_mod(r, t, q) * mq)) : hv;
                 if (!init) v = cadd(ob[lin - lo], v);
                 if (fin) v = cscale(v, scale);
                 ob[lin - lo] = v;
@@ -537,7 +537,7 @@ __device__ __forceinline__ void unfold_elem(V* ob, const V* __restrict__ h, int6
                     const int t = t0 + tt;
                     if (t < p) {
                         if (r == 0 || t == 0) acc[tt] = cadd(acc[tt], hv);
-                        else acc[tt] = cfmac(hv, twn(twNf, (((int64_t)r * t) % q) * mq), acc[tt]);
+                        else acc[tt] = cfmac(hv, twn(twNf, rt_mod(r, t, q) * mq), acc[tt]);
                     }
                 }
             }

@@ -432,6 +432,31 @@ struct FftPlan {
 // keep the plain layout, where neighbouring threads already take
 // neighbouring columns and the index arithmetic measured slower.
 
+// x / d for x >= 0, d > 0 without a runtime division where it can: a shift
+// when d is a power of two, a 32-bit division when both fit in 31 bits (a
+// 64-bit division costs several times the instructions of a 32-bit one,
+// and both many times a shift).  The tests on d are the same for every
+// thread of a launch.
+__device__ __forceinline__ int div_idx(int x, int d)
+{
+    return (d & (d - 1)) == 0 ? (x >> (__ffs(d) - 1)) : x / d;
+}
+__device__ __forceinline__ int64_t div_idx(int64_t x, int64_t d)
+{
+    if ((d & (d - 1)) == 0) return x >> (__ffsll(d) - 1);
+    if (((x | d) >> 31) == 0) return (int64_t)((unsigned)x / (unsigned)d);
+    return x / d;
+}
+
+// (r t) mod q for the fold and unfold twiddles zeta_q^{r t}: the product in
+// 64 bits, the remainder by a 32-bit division when the product fits
+__device__ __forceinline__ int64_t rt_mod(int64_t r, int64_t t, int64_t q)
+{
+    const int64_t rt = r * t;
+    if (((rt | q) >> 31) == 0) return (int64_t)((unsigned)rt % (unsigned)q);
+    return rt % q;
+}
+
 template <class V, bool SWZ> __device__ __forceinline__ int sidx(int x)
 {
     constexpr int S = 128 / (int)sizeof(V);
@@ -558,7 +583,7 @@ __device__ __forceinline__ void fft_smem(V* buf, V* tmp, const FftPlan& fp, int 
     if (a != buf) {
         const int tot = fp.n * ncol;
         for (int e = tid; e < tot; e += nthr) {
-            const int i = e / ncol, c = e - i * ncol;
+            const int i = div_idx(e, ncol), c = e - i * ncol;
             buf[sidx<V, SWZ>(c * cs + i * ld)] = a[sidx<V, SWZ>(c * cs + i * ld)];
         }
         __syncthreads();

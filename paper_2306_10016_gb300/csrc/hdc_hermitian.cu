@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_hermitian_rows(const __grid_con
                     else if (i >= Ny - c) ky = i - Ny;
                     else continue;
                     const V z = herm_z(F, G, ky, sx);
-                    v = (r == 0 || t == 0) ? cadd(v, z) : cfma(z, twn(a.twNy, (((int64_t)r * t) % qy) * my), v);
+                    v = (r == 0 || t == 0) ? cadd(v, z) : cfma(z, twn(a.twNy, rt_mod(r, t, qy) * my), v);
                 }
                 if (r != 0) v = cmul(v, twn(a.twNy, (int64_t)r * s));
             }
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_hermitian_rows(const __grid_con
                 if (i <= c) ky = i;
                 else if (i >= Ny - c) ky = i - Ny;
                 else continue;
-                const V v = (r != 0 && t != 0) ? cmulc(hv, twn(a.twNy, (((int64_t)r * t) % qy) * my)) : hv;
+                const V v = (r != 0 && t != 0) ? cmulc(hv, twn(a.twNy, rt_mod(r, t, qy) * my)) : hv;
                 acc[ky + c] = cadd(acc[ky + c], v);
             }
         }

@@ -400,7 +400,7 @@ __device__ __forceinline__ void fold_staged_tile(V* buf, int stride, const V* x,
     const int64_t afull = Lvalid / Cn;
     const int n = ma * C;
     for (int e = tid; e < n; e += nthr) {
-        const int i = e / C, cl = e - i * C;
+        const int i = div_idx(e, C), cl = e - i * C;
         const int64_t c = c0 + cl;
         V acc = czero<V>();
         for (int t = 0; t < p; ++t) {
@@ -411,7 +411,7 @@ __device__ __forceinline__ void fold_staged_tile(V* buf, int stride, const V* x,
             // block t = 0 carries zeta_q^0 = 1: no multiplication
             if (t == 0) acc = v;
             else if (r == 0) acc = cadd(acc, v);
-            else acc = cfma(v, twn(twNf, (((int64_t)r * t) % q) * mq), acc);
+            else acc = cfma(v, twn(twNf, rt_mod(r, t, q) * mq), acc);
         }
         if (r != 0 && c < Cn) acc = cmul(acc, twn(twNf, (int64_t)r * (i * cs + c * cc)));
         buf[e] = acc;
@@ -722,9 +722,9 @@ k_unfold(V* out, const V* __restrict__ h, int64_t B, int64_t bstride, int64_t Cn
     const int64_t per = ma * Cn;
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (gid >= per * B) return;
-    const int64_t b = gid / per;
+    const int64_t b = div_idx(gid, per);
     const int64_t e = gid - b * per;
-    const int64_t i = e / Cn, c = e - i * Cn;
+    const int64_t i = div_idx(e, Cn), c = e - i * Cn;
     unfold_elem<V, PT>(out + b * bstride, h + b * per, B * per, Cn, ma, i, c, p, q, Nf, cs, cc, lo, hi, r0, Dg,
                        first, last, scale, twNf);
 }
@@ -936,9 +936,9 @@ __global__ void k_pair_rows_real(const V* __restrict__ wa, const V* __restrict__
     const int64_t per = (int64_t)m0 * Cn;
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (gid >= (int64_t)Dg * B * per) return;
-    const int64_t blkrow = gid / per;
+    const int64_t blkrow = div_idx(gid, per);
     const int64_t e = gid - blkrow * per;
-    const int l0 = (int)(e / Cn);
+    const int l0 = (int)div_idx(e, Cn);
     const int64_t c = e - (int64_t)l0 * Cn;
     const int rr = (int)(blkrow / B);
     const int r = r0 + rr;
@@ -981,9 +981,9 @@ __global__ void k_unfold_real(typename real_of<V>::type* out, const V* __restric
     const int64_t per = ma * Cn;
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (gid >= per * B) return;
-    const int64_t b = gid / per;
+    const int64_t b = div_idx(gid, per);
     const int64_t e = gid - b * per;
-    const int64_t i = e / Cn, c = e - i * Cn;
+    const int64_t i = div_idx(e, Cn), c = e - i * Cn;
     const int64_t mq = Nf / q;
     T* ob = out + b * bstride;
     const V* hb = h + b * per;
@@ -999,7 +999,7 @@ __global__ void k_unfold_real(typename real_of<V>::type* out, const V* __restric
             V hv = hb[(int64_t)rr * hstride + i * Cn + c];
             if (r != 0) {
                 hv = cmulc(hv, twn(twNf, (int64_t)r * (i * cs + c * cc)));
-                if (t != 0) hv = cmulc(hv, twn(twNf, (((int64_t)r * t) % q) * mq));
+                if (t != 0) hv = cmulc(hv, twn(twNf, rt_mod(r, t, q) * mq));
             }
             acc += w * hv.x;
         }
