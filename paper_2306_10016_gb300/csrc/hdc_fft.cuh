@@ -46,25 +46,28 @@ template <class V> __device__ __forceinline__ V czero() { return mkc<V>(0, 0); }
 template <class V> __device__ __forceinline__ V cadd(V a, V b) { return mkc<V>(a.x + b.x, a.y + b.y); }
 template <class V> __device__ __forceinline__ V csub(V a, V b) { return mkc<V>(a.x - b.x, a.y - b.y); }
 template <class V> __device__ __forceinline__ V cscale(V a, typename real_of<V>::type s) { return mkc<V>(a.x * s, a.y * s); }
+// The complex products in explicit FMAs: the same rounding wherever the
+// compiler inlines them (left to contraction, two kernels that share a body
+// could round the same product differently).
 // a * w
 template <class V> __device__ __forceinline__ V cmul(V a, V w)
 {
-    return mkc<V>(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+    return mkc<V>(fma(a.x, w.x, -(a.y * w.y)), fma(a.x, w.y, a.y * w.x));
 }
 // a * conj(w)
 template <class V> __device__ __forceinline__ V cmulc(V a, V w)
 {
-    return mkc<V>(a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y);
+    return mkc<V>(fma(a.x, w.x, a.y * w.y), fma(a.y, w.x, -(a.x * w.y)));
 }
 // acc + a * w
 template <class V> __device__ __forceinline__ V cfma(V a, V w, V acc)
 {
-    return mkc<V>(acc.x + a.x * w.x - a.y * w.y, acc.y + a.x * w.y + a.y * w.x);
+    return mkc<V>(fma(a.x, w.x, fma(-a.y, w.y, acc.x)), fma(a.x, w.y, fma(a.y, w.x, acc.y)));
 }
 // acc + a * conj(w)
 template <class V> __device__ __forceinline__ V cfmac(V a, V w, V acc)
 {
-    return mkc<V>(acc.x + a.x * w.x + a.y * w.y, acc.y + a.y * w.x - a.x * w.y);
+    return mkc<V>(fma(a.x, w.x, fma(a.y, w.y, acc.x)), fma(a.y, w.x, fma(-a.x, w.y, acc.y)));
 }
 // multiply by +i (forward) or -i (inverse)
 template <class V, bool INV> __device__ __forceinline__ V rot90(V a)
