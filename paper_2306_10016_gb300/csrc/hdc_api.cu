@@ -463,17 +463,22 @@ template <typename T> struct Ins {
 // runs the split route's passes one after another (the L = 1024 configuration
 // with (512, 2, 4, 1): 70 against 189 us).  FP32, four times cheaper per
 // split-route pass, takes it for one residue up to 16384 points and for D = 1
-// multi-pass calls.
+// multi-pass calls.  Residues of at most 4096 points (powers of two) run
+// their transforms as warp shuffles (FP64: 21 us for L = 1024 with
+// m = 2048, 48 us on the split route; FP32: 17 us with m = 1024, q = 2,
+// against 31 us), and take the cluster in either precision up to q = 4.
 template <typename T> static bool use_cluster(const Axis& a, int64_t B)
 {
     const int mode = cluster_route_mode();
     if (mode == 0 || a.m < 256) return false;
     int C = 0;
     int64_t m1 = 0, m2 = 0;
-    if (!cluster_shape<T>(a.m, a.pout, a.q, a.p, &C, &m1, &m2)) return false;
+    bool warp = false;
+    if (!cluster_shape<T>(a.m, a.pout, a.q, a.p, &C, &m1, &m2, nullptr, &warp)) return false;
     if (B * C > (int64_t)sm_count()) return false;
     if (mode == 2) return true;
     const int64_t passes = (a.q + a.D - 1) / a.D;
+    if (warp && a.q <= 4) return true;
     if (sizeof(T) == 8) {
         if (a.m > 8192) return false;
         const int64_t u = a.m > 4096 ? 2 : 1;

@@ -130,82 +130,108 @@ template <class V> __device__ __forceinline__ void twn_to_smem(V* dst, const TwT
     else *dst = twn(t, k);
 }
 
-// n-point transforms (n = 2^lg <= 32) held one point per lane by groups
-// of n consecutive lanes, with no block barrier: radix-2 stages take the
-// partner's value (point i ^ h) by a warp shuffle, and every lane of the
-// warp must take part.  twl: the packed table of the n-point radix-2 plan
-// in the twiddle-merged form (the stage of span h = 2^s >= 2 at offset
+// n-point transforms (n = 2^lg <= 64) held in registers by groups of
+// G = min(n, 32) consecutive lanes, K = n / G points per lane (lane i holds
+// the points p = i + G k), with no block barrier: radix-2 stages of span
+// h < G take the partner's value (point p ^ h) by a warp shuffle, and every
+// lane of the warp must take part; with K = 2 the stage of span n / 2 pairs
+// a lane's own two points.  twl: the packed table of the n-point radix-2
+// plan in the twiddle-merged form (the stage of span h = 2^s >= 2 at offset
 // 2^{s+1} - 4, entry k = zeta_{2h}^k).
-//
-// Decimation in time: lane i enters with x[bitrev(i)] and leaves with
-// X[i]; at span h each lane forms its own output a + w b (lower lane) or
-// a - w b (upper lane) of its pair, w = zeta_{2h}^{i mod h}: 4 FMAs.
-template <class V, bool INV> __device__ __forceinline__ V warp_dit(V x, int i, int lg, const V* twl)
-{
-    using T = typename real_of<V>::type;
-    for (int st = 0; st < lg; ++st) {
-        const int h = 1 << st;
-        V y;
-        y.x = __shfl_xor_sync(0xffffffffu, x.x, h);
-        y.y = __shfl_xor_sync(0xffffffffu, x.y, h);
-        const bool up = (i & h) != 0;
-        const V a = up ? y : x, b = up ? x : y;
-        if (st == 0) {
-            const T sg = up ? (T)-1 : (T)1;
-            x = mkc<V>(fma(sg, b.x, a.x), fma(sg, b.y, a.y));
-        } else {
-            const LfW<V> w = lf_load<V, INV, true>(twl + ((2 << st) - 4), i & (h - 1));
-            const T ux = INV ? fma(w.tt, b.y, b.x) : fma(-w.tt, b.y, b.x);
-            const T uy = INV ? fma(-w.tt, b.x, b.y) : fma(w.tt, b.x, b.y);
-            const T px = w.f1 ? uy : ux;
-            const T py = w.f1 ? ux : uy;
-            x = mkc<V>(fma(flip_sign_if(w.sx, up), px, a.x), fma(flip_sign_if(w.sy, up), py, a.y));
-        }
-    }
-    return x;
-}
 
-// Decimation in frequency: lane i enters with x[i] and leaves with
-// X[bitrev(i)]; at span h the lower lane of a pair keeps a + b and the upper
-// one (a - b) w, w = zeta_{2h}^{i mod h} (w = 1 for the lower lane, so both
-// run the same 6 FP64 instructions).
-template <class V, bool INV> __device__ __forceinline__ V warp_dif(V x, int i, int lg, const V* twl)
+// one decimation-in-time stage of span h = 2^st < G: each lane forms its own
+// output a + w b (lower lane) or a - w b (upper lane) of its pair,
+// w = zeta_{2h}^{p mod h}: 4 FMAs
+template <class V, bool INV> __device__ __forceinline__ V dit_stage(V x, int i, int st, const V* twl)
 {
     using T = typename real_of<V>::type;
-    for (int st = lg - 1; st >= 0; --st) {
-        const int h = 1 << st;
-        V y;
-        y.x = __shfl_xor_sync(0xffffffffu, x.x, h);
-        y.y = __shfl_xor_sync(0xffffffffu, x.y, h);
-        const bool up = (i & h) != 0;
-        const V a = up ? y : x, b = up ? x : y;
+    const int h = 1 << st;
+    V y;
+    y.x = __shfl_xor_sync(0xffffffffu, x.x, h);
+    y.y = __shfl_xor_sync(0xffffffffu, x.y, h);
+    const bool up = (i & h) != 0;
+    const V a = up ? y : x, b = up ? x : y;
+    if (st == 0) {
         const T sg = up ? (T)-1 : (T)1;
-        const V d = mkc<V>(fma(sg, b.x, a.x), fma(sg, b.y, a.y));
-        if (st == 0) {
-            x = d;
-        } else {
-            LfW<V> w;
-            if (up) {
-                w = lf_load<V, INV, true>(twl + ((2 << st) - 4), i & (h - 1));
-            } else {
-                w.sx = (T)1;
-                w.sy = (T)1;
-                w.tt = (T)0;
-                w.f1 = false;
-            }
-            const T ux = INV ? fma(w.tt, d.y, d.x) : fma(-w.tt, d.y, d.x);
-            const T uy = INV ? fma(-w.tt, d.x, d.y) : fma(w.tt, d.x, d.y);
-            const T px = w.f1 ? uy : ux;
-            const T py = w.f1 ? ux : uy;
-            x = mkc<V>(w.sx * px, w.sy * py);
-        }
+        return mkc<V>(fma(sg, b.x, a.x), fma(sg, b.y, a.y));
     }
-    return x;
+    const LfW<V> w = lf_load<V, INV, true>(twl + ((2 << st) - 4), i & (h - 1));
+    const T ux = INV ? fma(w.tt, b.y, b.x) : fma(-w.tt, b.y, b.x);
+    const T uy = INV ? fma(-w.tt, b.x, b.y) : fma(w.tt, b.x, b.y);
+    const T px = w.f1 ? uy : ux;
+    const T py = w.f1 ? ux : uy;
+    return mkc<V>(fma(flip_sign_if(w.sx, up), px, a.x), fma(flip_sign_if(w.sy, up), py, a.y));
 }
 
-// W: the m1- and m2-point transforms (powers of two up to 32) by warp
-// shuffles (warp_cols_fft) instead of the shared-memory stages.
-template <class V, bool W>
+// d w in the twiddle-merged form
+template <class V, bool INV> __device__ __forceinline__ V lf_apply(V d, const LfW<V>& w)
+{
+    using T = typename real_of<V>::type;
+    const T ux = INV ? fma(w.tt, d.y, d.x) : fma(-w.tt, d.y, d.x);
+    const T uy = INV ? fma(-w.tt, d.x, d.y) : fma(w.tt, d.x, d.y);
+    const T px = w.f1 ? uy : ux;
+    const T py = w.f1 ? ux : uy;
+    return mkc<V>(w.sx * px, w.sy * py);
+}
+
+// one decimation-in-frequency stage of span h = 2^st < G: the lower lane of
+// a pair keeps a + b and the upper one (a - b) w, w = zeta_{2h}^{p mod h}
+// (w = 1 for the lower lane, so both run the same 6 FP64 instructions)
+template <class V, bool INV> __device__ __forceinline__ V dif_stage(V x, int i, int st, const V* twl)
+{
+    using T = typename real_of<V>::type;
+    const int h = 1 << st;
+    V y;
+    y.x = __shfl_xor_sync(0xffffffffu, x.x, h);
+    y.y = __shfl_xor_sync(0xffffffffu, x.y, h);
+    const bool up = (i & h) != 0;
+    const V a = up ? y : x, b = up ? x : y;
+    const T sg = up ? (T)-1 : (T)1;
+    const V d = mkc<V>(fma(sg, b.x, a.x), fma(sg, b.y, a.y));
+    if (st == 0) return d;
+    LfW<V> w;
+    if (up) {
+        w = lf_load<V, INV, true>(twl + ((2 << st) - 4), i & (h - 1));
+    } else {
+        w.sx = (T)1;
+        w.sy = (T)1;
+        w.tt = (T)0;
+        w.f1 = false;
+    }
+    return lf_apply<V, INV>(d, w);
+}
+
+// Decimation in time: point p enters as x[bitrev(p)] and leaves as X[p].
+template <class V, bool INV> __device__ __forceinline__ void warp_dit(V* x, int i, int lg, int K, const V* twl)
+{
+    const int lgG = lg - (K - 1);
+    for (int st = 0; st < lgG; ++st) {
+        x[0] = dit_stage<V, INV>(x[0], i, st, twl);
+        if (K == 2) x[1] = dit_stage<V, INV>(x[1], i, st, twl);
+    }
+    // span n / 2: points i and i + n / 2, both in this lane
+    if (K == 2) lf_bfly<V, INV>(x[0], x[1], lf_load<V, INV, true>(twl + ((2 << (lg - 1)) - 4), i));
+}
+
+// Decimation in frequency: point p enters as x[p] and leaves as X[bitrev(p)].
+template <class V, bool INV> __device__ __forceinline__ void warp_dif(V* x, int i, int lg, int K, const V* twl)
+{
+    const int lgG = lg - (K - 1);
+    if (K == 2) {
+        const V a = x[0], b = x[1];
+        x[0] = cadd(a, b);
+        x[1] = lf_apply<V, INV>(csub(a, b), lf_load<V, INV, true>(twl + ((2 << (lg - 1)) - 4), i));
+    }
+    for (int st = lgG - 1; st >= 0; --st) {
+        x[0] = dif_stage<V, INV>(x[0], i, st, twl);
+        if (K == 2) x[1] = dif_stage<V, INV>(x[1], i, st, twl);
+    }
+}
+
+// KW > 0: the m1- and m2-point transforms (powers of two up to 32 points
+// for KW = 1, up to 64 for KW = 2) by warp shuffles (warp_dit, warp_dif)
+// instead of the shared-memory stages.
+template <class V, int KW>
 __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_constant__ ClusterArgs<V> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -236,6 +262,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_const
     V* ING = INF + a.p * tile;      // g
     V* QT = sm + L.qt();
     const int xw = 2 * w2, yw = 2 * w1;
+    constexpr bool W = KW > 0;
     const int lgC = __ffs(C) - 1, lgw1 = a.lg1 - lgC, lgw2 = a.lg2 - lgC; // C, m1, m2: powers of two (W)
     const int tid = threadIdx.x, nthr = blockDim.x;
     const V* fr = a.f + b * a.ld_f;
@@ -279,50 +306,59 @@ __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_const
     __syncthreads();
     if constexpr (W) {
         // The shuffle transforms: no tile goes through shared memory between
-        // the fold and the push, or between the product and the push.
-        // Lane (col, i) of the column phases holds point i of column col of
-        // the two-tile X (f in columns [0, w2), g in [w2, 2 w2)); lane
-        // (col, i) of the row phases point i of column col of Y.
-        const int ccol = tid >> a.lg1, ci = tid & (a.m1 - 1);
+        // the fold and the push, or between the product and the push.  In
+        // the column phases the lanes of group col (G1 of them) hold the
+        // m1 points of column col of the two-tile X (f in columns [0, w2),
+        // g in [w2, 2 w2)), point p = i + G1 k in slot k; in the row phases
+        // the G2 lanes of group col the m2 points of column col of Y.
+        const int K1 = (KW == 2 && a.m1 > 32) ? 2 : 1, K2 = (KW == 2 && a.m2 > 32) ? 2 : 1;
+        const int G1 = a.m1 / K1, G2 = a.m2 / K2;
+        const int lgG1 = a.lg1 - (K1 - 1), lgG2 = a.lg2 - (K2 - 1);
+        const int ccol = tid >> lgG1, ci = tid & (G1 - 1);
         const int cside = ccol >= w2 ? 1 : 0, ccl = ccol - cside * w2;
-        const int ci_rev = (int)(__brev((unsigned)ci) >> (32 - a.lg1));
-        const bool cact = tid < xw * a.m1, cwarp = (tid & ~31) < xw * a.m1;
-        const int rcol = tid >> a.lg2, ri = tid & (a.m2 - 1);
-        const bool ract = tid < yw * a.m2, rwarp = (tid & ~31) < yw * a.m2;
-        const bool iwarp = (tid & ~31) < w1 * a.m2;     // inverse row transforms (f rows)
-        const bool uwarp = (tid & ~31) < w2 * a.m1;     // inverse column transforms (f columns)
+        const bool cact = tid < xw * G1, cwarp = (tid & ~31) < xw * G1;
+        const int rcol = tid >> lgG2, ri = tid & (G2 - 1);
+        const bool ract = tid < yw * G2, rwarp = (tid & ~31) < yw * G2;
+        const bool iwarp = (tid & ~31) < w1 * G2;       // inverse row transforms (f rows)
+        const bool uwarp = (tid & ~31) < w2 * G1;       // inverse column transforms (f columns)
         const V* in_side = cside ? ING : INF;
         const V* g_side = cside ? gr : fr;
+        auto rev1 = [&](int p) { return (int)(__brev((unsigned)p) >> (32 - a.lg1)); };
         for (int r = a.r_lo; r < a.r_hi; ++r) {
             V* FTc = ((r - a.r_lo) & 1) ? FT2 : FT;
             V* FTn = ((r - a.r_lo) & 1) ? FT : FT2;
             const int rq = r % a.q;
             // fold (Eq. 1 inner sum, then zeta_N^{r s}) of element s1 =
-            // bitrev(i) of this lane's column (the order the transform
-            // reads), then the m1-point transform; result l1 = i goes to
-            // the block that owns row l1, times zeta_m^{l1 s2}
+            // bitrev(p) of this lane's column for each of its points p (the
+            // order the transform reads), then the m1-point transform;
+            // result l1 = p goes to the block that owns row l1, times
+            // zeta_m^{l1 s2}
             if (cwarp) {
-                V x = czero<V>();
-                if (cact) {
-                    const int e = ci_rev * w2 + ccl;
-                    const int64_t s = (int64_t)ci_rev * a.m2 + (int64_t)c * w2 + ccl;
-                    x = a.stage ? in_side[e] : (s < a.L ? g_side[s] : czero<V>());
-                    int qi = 0;                  // (r t) mod q
-                    for (int t = 1; t < a.p; ++t) {
-                        const int64_t j = (int64_t)t * a.m + s;
-                        if (j >= a.L) break;
-                        qi += rq;
-                        if (qi >= a.q) qi -= a.q;
-                        x = cfma(a.stage ? in_side[t * tile + e] : g_side[j], QT[qi], x);
+                V x[2] = { czero<V>(), czero<V>() };
+                if (cact)
+                    _Pragma("unroll") for (int k = 0; k < 2; ++k) if (k < K1) {
+                        const int s1 = rev1(ci + G1 * k);
+                        const int e = s1 * w2 + ccl;
+                        const int64_t s = (int64_t)s1 * a.m2 + (int64_t)c * w2 + ccl;
+                        V v = a.stage ? in_side[e] : (s < a.L ? g_side[s] : czero<V>());
+                        int qi = 0;              // (r t) mod q
+                        for (int t = 1; t < a.p; ++t) {
+                            const int64_t j = (int64_t)t * a.m + s;
+                            if (j >= a.L) break;
+                            qi += rq;
+                            if (qi >= a.q) qi -= a.q;
+                            v = cfma(a.stage ? in_side[t * tile + e] : g_side[j], QT[qi], v);
+                        }
+                        x[k] = cmul(v, FTc[e]);
                     }
-                    x = cmul(x, FTc[e]);
-                }
-                x = warp_dit<V, false>(x, ci, a.lg1, T1l);
-                if (cact) {
-                    V* yd = cluster.map_shared_rank(Y, ci >> lgw1);
-                    yd[sidx<V, true>((c * w2 + ccl) * yw + cside * w1 + (ci & (w1 - 1)))] =
-                        cmul(x, BW[ccl * a.m1 + ci]);
-                }
+                warp_dit<V, false>(x, ci, a.lg1, K1, T1l);
+                if (cact)
+                    _Pragma("unroll") for (int k = 0; k < 2; ++k) if (k < K1) {
+                        const int l1 = ci + G1 * k;
+                        V* yd = cluster.map_shared_rank(Y, l1 >> lgw1);
+                        yd[sidx<V, true>((c * w2 + ccl) * yw + cside * w1 + (l1 & (w1 - 1)))] =
+                            cmul(x[k], BW[ccl * a.m1 + l1]);
+                    }
             }
             cluster.sync();
             // the next residue's fold twiddles, copied while the rows run
@@ -332,54 +368,63 @@ __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_const
                     const int s1 = a.dw2.div(e), cl = e - s1 * w2;
                     twn_to_smem(FTn + e, a.twN, (int64_t)(r + 1) * ((int64_t)s1 * a.m2 + (int64_t)c * w2 + cl));
                 }
-            // m2-point transforms of the rows (decimation in frequency: lane
-            // i ends with bin bitrev(i)); g's bins through shared memory to
-            // the lane of f with the same i, product (Section 2.4), inverse
-            // transform (decimation in time: lane i ends with s2 = i), result
+            // m2-point transforms of the rows (decimation in frequency: point
+            // p ends as bin bitrev(p)); g's bins through shared memory to the
+            // lane of f with the same points, product (Section 2.4), inverse
+            // transform (decimation in time: point p ends as s2 = p), result
             // to the block that owns column s2, times conj(zeta_m^{l1 s2})
-            V y = czero<V>();
+            V y[2] = { czero<V>(), czero<V>() };
             if (rwarp) {
-                if (ract) y = Y[sidx<V, true>(ri * yw + rcol)];
-                y = warp_dif<V, false>(y, ri, a.lg2, T2l);
-                if (ract && rcol >= w1) Y[sidx<V, true>(ri * yw + rcol)] = y;
+                if (ract)
+                    _Pragma("unroll") for (int k = 0; k < 2; ++k) if (k < K2) y[k] = Y[sidx<V, true>((ri + G2 * k) * yw + rcol)];
+                warp_dif<V, false>(y, ri, a.lg2, K2, T2l);
+                if (ract && rcol >= w1)
+                    _Pragma("unroll") for (int k = 0; k < 2; ++k) if (k < K2) Y[sidx<V, true>((ri + G2 * k) * yw + rcol)] = y[k];
             }
             __syncthreads();
             if (iwarp) {
-                const bool fact = tid < w1 * a.m2;
-                if (fact) y = cmul(y, Y[sidx<V, true>(ri * yw + rcol + w1)]);
-                y = warp_dit<V, true>(y, ri, a.lg2, T2l);
-                if (fact) {
-                    V* xd = cluster.map_shared_rank(X, ri >> lgw2);
-                    xd[sidx<V, true>((c * w1 + rcol) * xw + (ri & (w2 - 1)))] = cmulc(y, FW[rcol * a.m2 + ri]);
-                }
+                const bool fact = tid < w1 * G2;
+                if (fact)
+                    _Pragma("unroll") for (int k = 0; k < 2; ++k) if (k < K2) y[k] = cmul(y[k], Y[sidx<V, true>((ri + G2 * k) * yw + rcol + w1)]);
+                warp_dit<V, true>(y, ri, a.lg2, K2, T2l);
+                if (fact)
+                    _Pragma("unroll") for (int k = 0; k < 2; ++k) if (k < K2) {
+                        const int s2 = ri + G2 * k;
+                        V* xd = cluster.map_shared_rank(X, s2 >> lgw2);
+                        xd[sidx<V, true>((c * w1 + rcol) * xw + (s2 & (w2 - 1)))] = cmulc(y[k], FW[rcol * a.m2 + s2]);
+                    }
             }
             cp_async_wait_all();
             cluster.sync();
-            // inverse m1-point transforms of this block's columns (lane i
-            // loads row bitrev(i), ends with h_r[s], s1 = i), then the
-            // unfold (Eq. 2 outer sums): output j = t m + s gets
+            // inverse m1-point transforms of this block's columns (point p
+            // loads row bitrev(p), ends as h_r[s], s1 = p), then the unfold
+            // (Eq. 2 outer sums): output j = t m + s gets
             // conj(zeta_N^{r s}) conj(zeta_q^{r t}) h_r[s]
             if (uwarp) {
-                const bool uact = tid < w2 * a.m1;
-                V x = uact ? X[sidx<V, true>(ci_rev * xw + ccol)] : czero<V>();
-                x = warp_dit<V, true>(x, ci, a.lg1, T1l);
-                if (uact) {
-                    const int e = ci * w2 + ccol;
-                    const int64_t s = (int64_t)ci * a.m2 + (int64_t)c * w2 + ccol;
-                    const V hv = cmulc(x, FTc[e]);
-                    int qi = 0;
-                    for (int t = 0; t < a.pout; ++t) {
-                        const int64_t j = (int64_t)t * a.m + s;
-                        if (j >= a.hi) break;
-                        if (t != 0) {
-                            qi += rq;
-                            if (qi >= a.q) qi -= a.q;
+                const bool uact = tid < w2 * G1;
+                V x[2] = { czero<V>(), czero<V>() };
+                if (uact)
+                    _Pragma("unroll") for (int k = 0; k < 2; ++k) if (k < K1) x[k] = X[sidx<V, true>(rev1(ci + G1 * k) * xw + ccol)];
+                warp_dit<V, true>(x, ci, a.lg1, K1, T1l);
+                if (uact)
+                    _Pragma("unroll") for (int k = 0; k < 2; ++k) if (k < K1) {
+                        const int s1 = ci + G1 * k;
+                        const int e = s1 * w2 + ccol;
+                        const int64_t s = (int64_t)s1 * a.m2 + (int64_t)c * w2 + ccol;
+                        const V hv = cmulc(x[k], FTc[e]);
+                        int qi = 0;
+                        for (int t = 0; t < a.pout; ++t) {
+                            const int64_t j = (int64_t)t * a.m + s;
+                            if (j >= a.hi) break;
+                            if (t != 0) {
+                                qi += rq;
+                                if (qi >= a.q) qi -= a.q;
+                            }
+                            if (j < a.lo) continue;
+                            const V v = t != 0 ? cmulc(hv, QT[qi]) : hv;
+                            acc[t * tile + e] = cadd(acc[t * tile + e], v);
                         }
-                        if (j < a.lo) continue;
-                        const V v = t != 0 ? cmulc(hv, QT[qi]) : hv;
-                        acc[t * tile + e] = cadd(acc[t * tile + e], v);
                     }
-                }
             }
             // X is next written by the other blocks after the next residue's
             // first barrier; FTc is next overwritten after that barrier too
@@ -530,13 +575,23 @@ __global__ void __launch_bounds__(kMaxThreads) k_conv_cluster(const __grid_const
 
 // ------------------------------------------------------------------ host
 
+// Lanes the shuffle transforms of an m1 x m2 residue on C blocks need: the
+// larger of the column phases (2 m2 / C columns of min(m1, 32) lanes) and
+// the row phases (2 m1 / C columns of min(m2, 32) lanes).
+static int64_t cluster_warp_lanes(int C, int64_t m1, int64_t m2)
+{
+    const int64_t c = 2 * (m2 / C) * (m1 < 32 ? m1 : 32), r = 2 * (m1 / C) * (m2 < 32 ? m2 : 32);
+    return c > r ? c : r;
+}
+
 // Whether the cluster kernel takes the shuffle transforms for this shape:
-// m1 and m2 powers of two up to 32 and one thread per point of both
-// inputs' tiles.
+// m1 and m2 powers of two up to 64 (at most two points per lane) and at
+// most kMaxThreads lanes.
 static bool cluster_warp_ffts(int64_t m, int C, int64_t m1, int64_t m2)
 {
     auto pow2 = [](int64_t x) { return x > 0 && (x & (x - 1)) == 0; };
-    return pow2(m1) && pow2(m2) && m2 <= 32 && 2 * (m / C) <= kMaxThreads;
+    (void)m;
+    return pow2(m1) && pow2(m2) && m1 <= 64 && m2 <= 64 && cluster_warp_lanes(C, m1, m2) <= kMaxThreads;
 }
 
 // The transform plans of the cluster kernel: radix 2 throughout with the
@@ -545,6 +600,13 @@ static bool cluster_warp_ffts(int64_t m, int C, int64_t m1, int64_t m2)
 template <typename T> static FftPlan cluster_plan(int64_t n, bool warp_ffts)
 {
     return warp_ffts ? make_fft_plan(n, false, true) : fft_plan_latency<T>(n);
+}
+
+// The kernel variant: 0 shared-memory transforms, 1 shuffle transforms of
+// at most 32 points (one point per lane), 2 of up to 64 (two per lane).
+static int cluster_kw(bool warp_ffts, int64_t m1, int64_t m2)
+{
+    return !warp_ffts ? 0 : ((m1 > 32 || m2 > 32) ? 2 : 1);
 }
 
 // Bytes of dynamic shared memory of one block (ClusterSmem).
@@ -560,20 +622,20 @@ static size_t cluster_smem(int64_t m, int C, int64_t m1, int64_t m2, int64_t pou
 
 // Whether a 16-block cluster of this kernel with `smem` bytes per block can
 // be resident (a non-portable size; remembered per device).
-template <class V, bool W> static bool cluster16_ok(size_t smem, int thr)
+template <class V, int KW> static bool cluster16_ok(size_t smem, int thr)
 {
     static std::mutex mu;
     static std::map<std::pair<int, size_t>, bool> known;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
     std::lock_guard<std::mutex> lk(mu);
-    auto key = std::make_pair(dev, (smem * 1024 + (size_t)thr) * 2 + (W ? 1 : 0));
+    auto key = std::make_pair(dev, (smem * 1024 + (size_t)thr) * 4 + (size_t)KW);
     auto it = known.find(key);
     if (it != known.end()) return it->second;
-    bool ok = cudaFuncSetAttribute(k_conv_cluster<V, W>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+    bool ok = cudaFuncSetAttribute(k_conv_cluster<V, KW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
               cudaSuccess;
     if (ok && smem > 48 * 1024)
-        ok = cudaFuncSetAttribute(k_conv_cluster<V, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+        ok = cudaFuncSetAttribute(k_conv_cluster<V, KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
              cudaSuccess;
     if (ok) {
         cudaLaunchConfig_t cfg = {};
@@ -588,7 +650,7 @@ template <class V, bool W> static bool cluster16_ok(size_t smem, int thr)
         cfg.attrs = at;
         cfg.numAttrs = 1;
         int n = 0;
-        ok = cudaOccupancyMaxActiveClusters(&n, k_conv_cluster<V, W>, &cfg) == cudaSuccess && n > 0;
+        ok = cudaOccupancyMaxActiveClusters(&n, k_conv_cluster<V, KW>, &cfg) == cudaSuccess && n > 0;
     }
     cudaGetLastError();
     known[key] = ok;
@@ -597,10 +659,11 @@ template <class V, bool W> static bool cluster16_ok(size_t smem, int thr)
 
 // Threads of one block: one per butterfly of a stage over both inputs'
 // tiles (radix 2 in FP64, radix 8 in FP32; fft_plan_latency), 64..256; with
-// the shuffle transforms one per point of both tiles.
-template <typename T> static int cluster_threads(int64_t tile, bool warp_ffts)
+// the shuffle transforms the lanes they need (cluster_warp_lanes).
+template <typename T> static int cluster_threads(int64_t m, int C, int64_t m1, int64_t m2, bool warp_ffts)
 {
-    int thr = (int)(((warp_ffts ? 2 * tile : (sizeof(T) == 8 ? tile : tile / 4)) + 31) / 32 * 32);
+    const int64_t tile = m / C;
+    int thr = (int)(((warp_ffts ? cluster_warp_lanes(C, m1, m2) : (sizeof(T) == 8 ? tile : tile / 4)) + 31) / 32 * 32);
     return thr < 64 ? 64 : (thr > kMaxThreads ? kMaxThreads : thr);
 }
 
@@ -611,7 +674,8 @@ template <typename T> static int cluster_threads(int64_t tile, bool warp_ffts)
 // C | m2 and m1 <= m2 as close to sqrt(m) as allowed, shared memory within
 // the per-block limit.  False when none exists.
 template <typename T>
-bool cluster_shape(int64_t m, int64_t pout, int64_t q, int64_t p, int* Co, int64_t* m1o, int64_t* m2o, bool* stage)
+bool cluster_shape(int64_t m, int64_t pout, int64_t q, int64_t p, int* Co, int64_t* m1o, int64_t* m2o, bool* stage,
+                   bool* warp)
 {
     constexpr size_t kMaxSmem = 200 * 1024;
     for (int C : { 16, 8, 4, 2 }) {
@@ -629,19 +693,23 @@ bool cluster_shape(int64_t m, int64_t pout, int64_t q, int64_t p, int* Co, int64
         }
         if (smem > kMaxSmem) continue;
         const bool wf = cluster_warp_ffts(m, C, best, m / best);
-        if (C == 16 && !(wf ? cluster16_ok<cx<T>, true>(smem, cluster_threads<T>(m / C, true))
-                            : cluster16_ok<cx<T>, false>(smem, cluster_threads<T>(m / C, false))))
+        const int thr16 = cluster_threads<T>(m, C, best, m / best, wf);
+        const int kw = cluster_kw(wf, best, m / best);
+        if (C == 16 && !(kw == 2 ? cluster16_ok<cx<T>, 2>(smem, thr16)
+                                 : (kw == 1 ? cluster16_ok<cx<T>, 1>(smem, thr16)
+                                            : cluster16_ok<cx<T>, 0>(smem, thr16))))
             continue;
         *Co = C;
         *m1o = best;
         *m2o = m / best;
         if (stage) *stage = stg;
+        if (warp) *warp = wf;
         return true;
     }
     return false;
 }
-template bool cluster_shape<double>(int64_t, int64_t, int64_t, int64_t, int*, int64_t*, int64_t*, bool*);
-template bool cluster_shape<float>(int64_t, int64_t, int64_t, int64_t, int*, int64_t*, int64_t*, bool*);
+template bool cluster_shape<double>(int64_t, int64_t, int64_t, int64_t, int*, int64_t*, int64_t*, bool*, bool*);
+template bool cluster_shape<float>(int64_t, int64_t, int64_t, int64_t, int*, int64_t*, int64_t*, bool*, bool*);
 
 template <typename T>
 cudaError_t launch_conv_cluster(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t B, int64_t ld_f, int64_t ld_g,
@@ -697,8 +765,9 @@ cudaError_t launch_conv_cluster(const cx<T>* f, const cx<T>* g, cx<T>* out, int6
     while ((int64_t(1) << a.lg1) < m1) ++a.lg1;
     a.lg2 = 0;
     while ((int64_t(1) << a.lg2) < m2) ++a.lg2;
-    const int thr = cluster_threads<T>(m / C, wf);
-    auto kern = wf ? k_conv_cluster<V, true> : k_conv_cluster<V, false>;
+    const int thr = cluster_threads<T>(m, C, m1, m2, wf);
+    const int kw = cluster_kw(wf, m1, m2);
+    auto kern = kw == 2 ? k_conv_cluster<V, 2> : (kw == 1 ? k_conv_cluster<V, 1> : k_conv_cluster<V, 0>);
     const size_t smem_c = cluster_smem<T>(m, C, m1, m2, pout, q, stage ? p : 0);
     if (smem_c > 48 * 1024 &&
         (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c)) !=

@@ -228,10 +228,11 @@ cudaError_t launch_unfold_real(T* out, const cx<T>* h, int64_t B, int64_t bstrid
 // written once (times scale) to out (row stride ldo).  cluster_shape tells
 // whether an m-point residue (pout = ceil(hi / m) output blocks, q residues,
 // p fold blocks) fits a cluster: C blocks, m = m1 m2 with C dividing both;
-// *stage (optional): the inputs fit in shared memory too.
+// *stage (optional): the inputs fit in shared memory too; *warp (optional):
+// the transforms run as warp shuffles (m1, m2 powers of two up to 64).
 template <typename T>
 bool cluster_shape(int64_t m, int64_t pout, int64_t q, int64_t p, int* C, int64_t* m1, int64_t* m2,
-                   bool* stage = nullptr);
+                   bool* stage = nullptr, bool* warp = nullptr);
 int cluster_route_mode();
 template <typename T>
 cudaError_t launch_conv_cluster(const cx<T>* f, const cx<T>* g, cx<T>* out, int64_t B, int64_t ld_f, int64_t ld_g,

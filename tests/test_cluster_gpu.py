@@ -46,6 +46,8 @@ CASES = [
     # explicit padding, implicit q = 2, ragged L, and the largest residues
     (1, 1024, 512), (1, 1024, 256), (1, 1024, 2048), (1, 2048, 2048), (3, 3000, 1024), (2, 5000, 8192),
     (1, 16384, 16384), (1, 6000, 12288),
+    # two points per lane in the shuffle transforms: 32 x 64 and 64 x 64
+    (2, 1500, 2048), (2, 3000, 4096),
 ]
 
 
@@ -80,9 +82,10 @@ def test_cluster_route_exact_integers(hdc):
         assert np.array_equal(np.rint(h.imag).astype(np.int64), hi)
 
 
-@pytest.mark.parametrize("L,m", [(3000, 2048), (1000, 512)])
+@pytest.mark.parametrize("L,m", [(6000, 8192), (3000, 2048), (1000, 512)])
 def test_cluster_route_window_and_residue_shares(hdc, L, m):
-    """m = 2048: shared-memory transforms; m = 512: the warp-shuffle ones."""
+    """m = 8192: shared-memory transforms; m = 2048 and 512: the warp-shuffle
+    ones (two points and one point per lane)."""
     fn = synth.unit_disk(35001, (L,))
     gn = synth.unit_disk(35002, (L,))
     f = torch.from_numpy(fn).cuda()
