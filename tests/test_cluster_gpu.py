@@ -48,6 +48,9 @@ CASES = [
     (1, 16384, 16384), (1, 6000, 12288),
     # two points per lane in the shuffle transforms: 32 x 64 and 64 x 64
     (2, 1500, 2048), (2, 3000, 4096),
+    # many residues and fold blocks on the shuffle path (q = 20, p = 10;
+    # FP32 fold twiddles from the split table, N = 81920)
+    (1, 40000, 4096),
 ]
 
 
