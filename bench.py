@@ -993,10 +993,18 @@ def main():
     e2e_streams = [torch.cuda.Stream(dev) for _ in range(n_e2e_streams)]
     wsh_ts = [torch.empty(wsh, dtype=torch.uint8, device=dev) for _ in range(n_e2e_streams)]
 
+    # issue order: the sizes up through every second one, then back down
+    # through the others, so the step starts with a small host-to-device
+    # copy and ends with a small device-to-host one, and every large size's
+    # copies overlap the kernels of its neighbours
+    by_size = sorted(range(len(sizes)), key=lambda i: sizes[i])
+    e2e_order = by_size[0::2] + by_size[1::2][::-1]
+
     def e2e_step():
-        for i, (L, p, (f, g, h)) in enumerate(zip(sizes, plans64, pinned)):
+        for k_, i in enumerate(e2e_order):
+            L, p, (f, g, h) = sizes[i], plans64[i], pinned[i]
             prm = p.params[0]
-            k = i % n_e2e_streams
+            k = k_ % n_e2e_streams
             hdc.convnd_host(f, g, h, 1, prm["m"], p=prm["p"], q=prm["q"], D=prm["D"], workspace=wsh_ts[k],
                             stream=e2e_streams[k], sync=False)
         for s_ in e2e_streams:
