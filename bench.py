@@ -40,6 +40,8 @@ sys.path.insert(0, ROOT)
 METRIC = "conv outputs/s & %roofline, tuned hybrid vs explicit, FP64 err≤1e-12"
 UNIT = "outputs/s"
 SM_COUNT = 152
+# streams the timed sweep steps issue their independent sizes over
+SWEEP_STREAMS = 3
 SM_MAX_MHZ = 2070.0
 
 
@@ -374,17 +376,36 @@ def main():
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
 
-    def time_sweep(plans, ins, steps, warmup, stats=False, nvtx=None, reps=1):
+    def time_sweep(plans, ins, steps, warmup, stats=False, nvtx=None, reps=1, nstreams=1):
         """Warm up eagerly, capture one step (every size once, `reps` times) in
         a CUDA graph, then time `steps` replays with events, flushing L2 before
-        each; returns the time per repetition."""
+        each; returns the time per repetition.  nstreams > 1: the sizes of a
+        step are independent convolutions, issued over that many streams
+        (forked from the step's stream and joined back, a workspace each) in
+        the order small-large-small, so the short launches of the small sizes
+        run beside the others instead of one after another."""
+        nst = 1 if (stats or len(plans) == 1) else nstreams
         wsb = max(p.workspace_bytes for p in plans)
-        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        wss = [torch.empty(wsb, dtype=torch.uint8, device=dev) for _ in range(nst)]
+        ws = wss[0]
         side = torch.cuda.Stream(dev)
+        extra = [torch.cuda.Stream(dev) for _ in range(nst - 1)]
+        by_size = sorted(range(len(plans)), key=lambda i: ins[i][0].numel())
+        order = by_size[0::2] + by_size[1::2][::-1]
 
         def step(st):
-            for p, (f, g, h) in zip(plans, ins):
-                p.execute(f, g, out=h, workspace=ws, stream=st)
+            if nst == 1:
+                for p, (f, g, h) in zip(plans, ins):
+                    p.execute(f, g, out=h, workspace=ws, stream=st)
+                return
+            for s_ in extra:
+                s_.wait_stream(st)
+            streams = [st] + extra
+            for k_, i in enumerate(order):
+                f, g, h = ins[i]
+                plans[i].execute(f, g, out=h, workspace=wss[k_ % nst], stream=streams[k_ % nst])
+            for s_ in extra:
+                st.wait_stream(s_)
 
         with torch.cuda.stream(side):
             for _ in range(warmup):
@@ -472,7 +493,8 @@ def main():
     # the headline and the explicit comparison are timed without per-kernel
     # events (event records in the graph would add to every launch); the
     # per-kernel split of the roofline comes from a second, instrumented run
-    ms64, launches, ms_list, _ = time_sweep(plans64, ins64, args.steps, args.warmup, nvtx="hdc_fp64_timed")
+    ms64, launches, ms_list, _ = time_sweep(plans64, ins64, args.steps, args.warmup, nvtx="hdc_fp64_timed",
+                                            nstreams=SWEEP_STREAMS)
     clocks = sampler.stop()
     check_sweep("sweep_fp64", ins64)
     _, _, _, kstats = time_sweep(plans64, ins64, args.steps, 1, stats=True)
@@ -493,7 +515,7 @@ def main():
 
     # --- explicit padding, FP64
     plans_ex = make_plans(hdc.HDC_C128, hdc.HDC_EXPLICIT)
-    ms_ex, _, _, _ = time_sweep(plans_ex, ins64, args.steps, args.warmup)
+    ms_ex, _, _, _ = time_sweep(plans_ex, ins64, args.steps, args.warmup, nstreams=SWEEP_STREAMS)
     ms_ex = rank_max(ms_ex)
     check_sweep("explicit_fp64", ins64)
 
@@ -570,7 +592,7 @@ def main():
     # --- FP32 tuned hybrid
     ins32 = make_inputs(torch.complex64)
     plans32 = make_plans(hdc.HDC_C64, hdc.HDC_TUNE_EXHAUSTIVE)
-    ms32, _, _, _ = time_sweep(plans32, ins32, args.steps, args.warmup)
+    ms32, _, _, _ = time_sweep(plans32, ins32, args.steps, args.warmup, nstreams=SWEEP_STREAMS)
     ms32 = rank_max(ms32)
     check_sweep("sweep_fp32", ins32)
     _, _, _, kstats32 = time_sweep(plans32, ins32, 1, 1, stats=True)
@@ -1136,7 +1158,8 @@ def main():
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name("FP64"), "sizes": len(sizes), "outputs_per_step": outs,
                    "launch": ("eager launches per timed step" if args.eager else
-                              "one step captured in a CUDA graph, replayed per timed step"),
+                              "one step captured in a CUDA graph, replayed per timed step")
+                   + f"; the independent sizes issued over {SWEEP_STREAMS} streams (small-large-small order)",
                    "l2": "flushed between timed steps (256 MiB write)", "tuning": "grid search (Section 4.2), "
                    "candidates within 1.5x of the least model flops, m >= 16", "tuning_s": round(tune_s, 1),
                    "parallelism": (f"shard_batch x{world} (sweep copies and batched convolutions; "
