@@ -776,8 +776,10 @@ int hdc_set_tma(int enable);
  * default) where it is the faster route (small residues in few passes: in
  * FP64 up to 8192 points with one residue, 4096 with two in one pass, and
  * calls that would otherwise run several passes one after another; in FP32
- * one residue up to 16384 points and multi-pass calls), 2 wherever the
- * residue fits; HDC_ERR_PARAM for another mode.  Not thread-safe against
+ * one residue up to 16384 points and multi-pass calls; in both, residues of
+ * a power of two up to 4096 points, whose transforms run as warp shuffles,
+ * up to four residues), 2 wherever the residue fits; HDC_ERR_PARAM for
+ * another mode.  Not thread-safe against
  * calls in flight on other host threads. */
 int hdc_set_cluster(int mode);
 int hdc_device_status(int* status, int clear);
